@@ -1,0 +1,264 @@
+"""Pins for the CPU oracle: each test ties it to something other than itself.
+
+* Figure 1 of the paper (§2.1): the three-line scene and its four printed
+  vectors; the dense sampling of the same scene (7 cells, the cube Q3 minus
+  vertex 000, 9 edges; the paper notes vector 000 has no point).
+* Figure 2 of the paper (§3.2): the six printed vectors and their two
+  Hamming-1 pairs.
+* Exact sign evaluation against Python's arbitrary-precision integers, at the
+  int32 / int64 extremes and on exact ties (a . p = b).
+* Sort + unique against Python's ``sorted(set(...))`` (§3.2 reduces to it).
+* Neighbours against brute force over all pairs (the naive algorithm of §3.1,
+  i.e. the heuristic with h = 0), for l across word boundaries.
+* Closed forms: the full hypercube Q_l has l * 2^(l-1) edges.
+* Invariants: distance exactly 1, i < j, no repeats, degree <= l,
+  |E| <= U l / 2 (§2.2); output unchanged by shuffling or duplicating X (§3.2,
+  multiset robustness); the arrangement bound sum_{k<=d} C(l,k) on U.
+* Planted chains: surviving planted Hamming-1 pairs are edges; every edge lies
+  within one chain.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_06029_gb300 import inputs
+from tests.helpers import (as_u64_rows, brute_force_edges, ints_to_rows, paper_string_to_int,
+                           popcount64, rows_to_ints)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_fig1():
+    cons, pts = [], []
+    with open(os.path.join(GOLDEN, "fig1_three_lines.txt")) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "constraint":
+                cons.append([int(x) for x in t[1:]])
+            elif t[0] == "point":
+                pts.append((t[1], int(t[2]), int(t[3]), t[4]))
+    a = np.array([c[:2] for c in cons], dtype=np.int32)
+    b = np.array([c[2] for c in cons], dtype=np.int64)
+    return a, b, pts
+
+
+def _read_fig2():
+    vecs = []
+    with open(os.path.join(GOLDEN, "fig2_six_vectors.txt")) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            vecs.append((t[0], t[1]))
+    return vecs
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+def test_fig1_printed_vectors(word_bits):
+    a, b, pts = _read_fig1()
+    P = np.array([[x, y] for _, x, y, _ in pts], dtype=np.int32)
+    keys = oracle.pack_signs(P, a, b, word_bits)
+    got = rows_to_ints(keys, word_bits)
+    want = [paper_string_to_int(v) for *_, v in pts]
+    assert got == want
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+def test_fig1_cells_and_edges(word_bits):
+    a, b, pts = _read_fig1()
+    P = np.array([[x, y] for _, x, y, _ in pts], dtype=np.int32)
+    cells, edges = oracle.build(P, a, b, word_bits)
+    names = {paper_string_to_int(v): n for n, _, _, v in pts}
+    # value order: C (100 -> 1) < B (110 -> 3) < D (101 -> 5) < A (111 -> 7)
+    assert [names[v] for v in rows_to_ints(cells, word_bits)] == ["C", "B", "D", "A"]
+    # the 4-cycle C-B-A-D-C; A-C and B-D are at distance 2
+    assert edges.tolist() == [[0, 1], [0, 2], [1, 3], [2, 3]]
+
+
+def test_fig1_dense_sampling_gives_cube_minus_000():
+    a, b, _ = _read_fig1()
+    g = np.arange(-40, 61, dtype=np.int32)
+    P = np.stack(np.meshgrid(g, g, indexing="ij"), axis=-1).reshape(-1, 2)
+    cells, edges = oracle.build(P, a, b, 64)
+    vals = rows_to_ints(cells, 64)
+    assert vals == [1, 2, 3, 4, 5, 6, 7]  # every pattern but 000 (§2.1)
+    assert len(edges) == 9  # Q3 has 12 edges, vertex 000 takes 3
+
+
+def test_fig2_pairs():
+    vecs = _read_fig2()
+    vals = sorted(paper_string_to_int(v) for v, _ in vecs)
+    cells = ints_to_rows(vals, 6, 64)
+    edges = oracle.neighbors(cells, 6, 64)
+    named = [(vals[i], vals[j]) for i, j in edges.tolist()]
+    p = paper_string_to_int
+    assert named == [(p("110100"), p("110110")), (p("110110"), p("110111"))]
+
+
+def _python_signs(pts, a, b):
+    out = []
+    for p in pts.tolist():
+        v = 0
+        for i, (ai, bi) in enumerate(zip(a.tolist(), b.tolist())):
+            if sum(x * y for x, y in zip(ai, p)) >= bi:
+                v |= 1 << i
+        out.append(v)
+    return out
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+@pytest.mark.parametrize("ell,d", [(1, 1), (7, 2), (32, 3), (33, 4), (64, 3), (65, 2), (130, 3)])
+def test_pack_matches_bigint(ell, d, word_bits):
+    rng = np.random.default_rng(ell * 10 + d)
+    n = 60
+    i32 = np.iinfo(np.int32)
+    i64 = np.iinfo(np.int64)
+    pts = rng.integers(-50, 51, size=(n, d)).astype(np.int32)
+    pts[:5] = i32.max
+    pts[5:10] = i32.min
+    a = rng.integers(-50, 51, size=(ell, d)).astype(np.int32)
+    a[0] = i32.min
+    b = rng.integers(-3000, 3001, size=ell).astype(np.int64)
+    b[-1] = i64.min if ell > 1 else b[-1]
+    if ell > 2:
+        b[1] = i64.max
+    keys = oracle.pack_signs(pts, a, b, word_bits)
+    assert rows_to_ints(keys, word_bits) == _python_signs(pts, a, b)
+
+
+def test_ties_count_as_satisfied():
+    # a . p == b exactly: the constraint a . p >= b holds, so the bit is 1
+    # and one unit below the offset it fails, so the bit is 0
+    a = np.array([[3, -7], [0, 0], [-2, 4]], dtype=np.int32)
+    pts = np.array([[7, 3], [0, 0], [5, 2], [7, 2]], dtype=np.int32)
+    b = np.array([0, 0, -2], dtype=np.int64)
+    keys = oracle.pack_signs(pts, a, b, 64)
+    # (7,3): 0>=0, 0>=0, -2>=-2 | (0,0): ties everywhere | (5,2): 1, 0, -2>=-2
+    # (7,2): 7>=0, 0>=0, -6<-2
+    assert rows_to_ints(keys, 64) == [0b111, 0b111, 0b111, 0b011]
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+@pytest.mark.parametrize("ell", [1, 3, 31, 32, 33, 64, 65, 130])
+def test_dedup_is_sorted_set(ell, word_bits):
+    rng = np.random.default_rng(ell)
+    pool = [int(rng.integers(0, 1 << min(ell, 62))) << max(0, ell - 62) for _ in range(37)]
+    pool = [v & ((1 << ell) - 1) for v in pool]
+    vals = [pool[int(i)] for i in rng.integers(0, len(pool), size=500)]
+    keys = ints_to_rows(vals, ell, word_bits)
+    cells, pc = oracle.dedup(keys, ell, word_bits, point_cell=True)
+    want = sorted(set(vals))
+    assert rows_to_ints(cells, word_bits) == want
+    assert [want[i] for i in pc.tolist()] == vals
+
+
+def _clustered(rng, n, ell, n_seeds, flips):
+    seeds = [int.from_bytes(rng.bytes((ell + 7) // 8), "little") & ((1 << ell) - 1)
+             for _ in range(n_seeds)]
+    vals = []
+    for _ in range(n):
+        v = seeds[int(rng.integers(0, n_seeds))]
+        for _ in range(int(rng.integers(0, flips + 1))):
+            v ^= 1 << int(rng.integers(0, ell))
+        vals.append(v)
+    return vals
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+@pytest.mark.parametrize("ell", [1, 2, 5, 31, 32, 33, 63, 64, 65, 70, 130])
+def test_neighbors_match_brute_force(ell, word_bits):
+    rng = np.random.default_rng(1000 + ell)
+    vals = sorted(set(_clustered(rng, 700, ell, 12, 3)))
+    cells = ints_to_rows(vals, ell, word_bits)
+    got = oracle.neighbors(cells, ell, word_bits)
+    want = brute_force_edges(as_u64_rows(cells, ell, word_bits))
+    assert got.tolist() == want.tolist()
+    assert len(got) > 0
+
+
+@pytest.mark.parametrize("ell", range(1, 11))
+def test_hypercube_closed_form(ell):
+    cells = ints_to_rows(list(range(1 << ell)), ell, 64)
+    edges = oracle.neighbors(cells, ell, 64)
+    assert len(edges) == ell * (1 << (ell - 1))
+    deg = np.bincount(edges.reshape(-1), minlength=1 << ell)
+    assert (deg == ell).all()
+
+
+def _check_invariants(cells_u64, edges, ell):
+    u = cells_u64.shape[0]
+    e = edges.astype(np.int64)
+    if len(e):
+        assert (e[:, 0] < e[:, 1]).all()
+        assert e.max() < u
+        x = cells_u64[e[:, 0]] ^ cells_u64[e[:, 1]]
+        assert (popcount64(x).sum(axis=1) == 1).all()
+        assert len({tuple(r) for r in e.tolist()}) == len(e)
+        order = np.lexsort((e[:, 1], e[:, 0]))
+        assert (order == np.arange(len(e))).all()
+        assert np.bincount(e.reshape(-1), minlength=u).max() <= ell
+    assert len(e) <= u * ell / 2
+
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+def test_multiset_and_shuffle_invariance(word_bits):
+    sc = inputs.planes_3d(n=3000, ell=40, seed=11)
+    keys = oracle.pack_signs(sc.pts, sc.a, sc.b, word_bits)
+    cells = oracle.dedup(keys, 40, word_bits)
+    edges = oracle.neighbors(cells, 40, word_bits)
+    rng = np.random.default_rng(5)
+    mixed = np.concatenate([keys, keys[rng.integers(0, len(keys), 4000)]])
+    mixed = mixed[rng.permutation(len(mixed))]
+    cells2 = oracle.dedup(mixed, 40, word_bits)
+    edges2 = oracle.neighbors(cells2, 40, word_bits)
+    assert np.array_equal(cells, cells2) and np.array_equal(edges, edges2)
+    _check_invariants(as_u64_rows(cells, 40, word_bits), edges, 40)
+
+
+def test_arrangement_bounds_lines_and_planes():
+    for sc, word_bits in [(inputs.lines_2d(n=20_000), 32), (inputs.planes_3d(n=200_000), 64)]:
+        cells, edges = oracle.build(sc.pts, sc.a, sc.b, word_bits)
+        bound = sum(math.comb(sc.ell, k) for k in range(sc.d + 1))
+        assert 1 < len(cells) <= bound
+        _check_invariants(as_u64_rows(cells, sc.ell, word_bits), edges, sc.ell)
+        assert len(edges) > len(cells) // 2  # a sampled arrangement is well connected
+
+
+def test_rows_subset_matches_full():
+    sc = inputs.planes_3d(n=5000, ell=64, seed=3)
+    cells, edges = oracle.build(sc.pts, sc.a, sc.b, 64)
+    rows = np.array([0, 5, 17, len(cells) - 1], dtype=np.int64)
+    sub = oracle.neighbors(cells, 64, 64, rows=rows)
+    want = edges[np.isin(edges[:, 0], rows)]
+    assert sub.tolist() == want.tolist()
+
+
+def test_planted_chains():
+    ch = inputs.chains(n_seeds=300, chain_len=15, ell=130, seed=9)
+    cells = oracle.dedup(ch.keys, ch.ell, 64)
+    edges = oracle.neighbors(cells, ch.ell, 64)
+    vals = rows_to_ints(cells, 64)
+    index = {v: i for i, v in enumerate(vals)}
+    base_vals = rows_to_ints(ch.base, 64)
+    eset = {tuple(e) for e in edges.tolist()}
+    planted_kept = 0
+    for p, c in ch.planted.tolist():
+        x, y = base_vals[p], base_vals[c]
+        if x == y:
+            continue
+        i, j = sorted((index[x], index[y]))
+        assert (i, j) in eset
+        planted_kept += 1
+    assert planted_kept > 0.95 * len(ch.planted)
+    chain_of = {}
+    for r, v in enumerate(base_vals):
+        chain_of.setdefault(v, set()).add(r // 16)
+    for i, j in edges.tolist():
+        assert chain_of[vals[i]] & chain_of[vals[j]]
+    assert len(vals) == len(set(base_vals))
