@@ -1,0 +1,177 @@
+/*
+ * cellgraph.h -- C-ABI of libcellgraph.so, a CUDA (sm_103a) implementation of
+ * the cell-graph construction of "Massively Parallel Construction of the Cell
+ * Graph" (Kaczmarski, Rzazewski, Wolant).
+ *
+ * The method, in the paper's terms:
+ *   - a scene is a system of l constraints c_0..c_{l-1}; a sampled point P is
+ *     represented by the l-bit vector v_P whose bit i is 1 iff P satisfies c_i
+ *     (§2.1, Figure 1). Here every constraint is the closed half-space
+ *     a_i . p >= b_i with integer a_i, p, b_i, evaluated exactly;
+ *   - the cells are the distinct vectors (§2.1); the multiset X of sampled
+ *     vectors is sorted and its duplicates removed (§3.2);
+ *   - the cell graph G_X has an edge between two cells iff their Hamming
+ *     distance is exactly 1 (§2.2); each unordered pair is reported once, even
+ *     when X holds duplicates (§2.2). The search flips each bit of each cell and
+ *     looks the result up (Algorithm 4).
+ *
+ * Conventions shared by every call:
+ *   - Packing: bit i of a vector lives in word i / B at bit position i % B,
+ *     with B = word_bits (32 or 64). A vector takes W = ceil(l / B) words; the
+ *     bits >= l of the last word are zero. Arrays of vectors are row-major
+ *     [count][W].
+ *   - Order: vectors compare as the unsigned integers sum_i x(i) 2^i (the last
+ *     word is the most significant). Cells are numbered 0..U-1 in that order.
+ *   - Edges: pairs (i, j) of cell numbers with i < j, stored as uint32[E][2], in
+ *     lexicographic (i, j) order. Every edge is found from its endpoint i, whose
+ *     bit k is 0 while j's is 1.
+ *   - Memory: every array argument is DEVICE memory owned by the caller, except
+ *     where a parameter says "host". The library never frees caller memory.
+ *   - Streams: work is enqueued on `stream` (a cudaStream_t; 0 is the legacy
+ *     default stream). Calls that return counts through host pointers wait for
+ *     their own work on that stream before returning.
+ *   - Capacities: when an output array is too small the call returns
+ *     CG_ERR_CAPACITY, still writes the required count(s), and writes nothing
+ *     past the given capacity.
+ *   - Errors: every call returns a cg_status; cg_last_error() gives a message
+ *     for the calling thread's last failure. Invalid arguments are rejected
+ *     before any work is enqueued.
+ *   - Sizes: n < 2^32 - 1 points/vectors (cell numbers are uint32), 1 <= d <= 4,
+ *     1 <= l <= 4096. Coordinates, normals (int32) and offsets (int64) may take
+ *     any value of their type: the sign tests are exact.
+ */
+#ifndef CELLGRAPH_H
+#define CELLGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int cg_status;
+#define CG_OK 0
+#define CG_ERR_INVALID_ARG 1 /* bad pointer, size, word_bits, strategy, ... */
+#define CG_ERR_CAPACITY 3    /* an output array is too small; counts were written */
+#define CG_ERR_OOM 4         /* a library-owned allocation failed */
+#define CG_ERR_CUDA 5        /* a CUDA runtime call or kernel launch failed */
+#define CG_ERR_TIMEOUT 6     /* a bounded device-side wait ran out */
+#define CG_ERR_INTERNAL 7    /* a device-side consistency check failed */
+
+/* Lookup strategies for the neighbour search (cg_neighbors_h1). */
+#define CG_STRATEGY_AUTO 0   /* library choice (currently HASH) */
+#define CG_STRATEGY_HASH 1   /* open-addressing table keyed on the vector (l <= 64)
+                                or on a GF(2)-linear 64-bit fingerprint (l > 64);
+                                every candidate is verified against the full vector */
+#define CG_STRATEGY_SORTED 2 /* binary search in the sorted cell array */
+
+/* Message describing the calling thread's last failed call ("" if none). */
+const char* cg_last_error(void);
+
+/* Library version string. */
+const char* cg_version(void);
+
+/* Number of kernels this library has launched in this process (all devices,
+ * all threads). Host-side counter; used to report launches per step. */
+uint64_t cg_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Step 1 -- sign vectors (§2.1, Figure 1).
+ * keys[p] = packed [a_i . pts[p] >= b_i] for i = 0..l-1, evaluated exactly.
+ *   pts   int32[n][d] row-major, device.
+ *   a     int32[l][d] row-major (constraint normals), device.
+ *   b     int64[l] (constraint offsets), device.
+ *   keys  [n][W] words of word_bits bits, device, written entirely.
+ * n = 0 is allowed (nothing is written). No workspace; asynchronous.
+ * ------------------------------------------------------------------------- */
+cg_status cg_pack_signs(const int32_t* pts, int64_t n, int d, const int32_t* a,
+                        const int64_t* b, int ell, int word_bits, void* keys,
+                        void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Step 2 -- cells: sort the multiset of vectors and remove duplicates (§3.2).
+ *   keys        [n][W] words (word_bits), device, read only.
+ *   cells       [cells_cap][W] words, device: the U distinct vectors in order.
+ *   n_cells     host: receives U.
+ *   point_cell  nullable, uint32[n], device: cell number of every input vector.
+ *   ws          device workspace of *ws_bytes bytes. With ws == NULL the call
+ *               only writes the required size to *ws_bytes and returns.
+ * Blocks until the work on `stream` is done (U is returned through a host
+ * pointer). U > cells_cap gives CG_ERR_CAPACITY with *n_cells = U.
+ * ------------------------------------------------------------------------- */
+cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, void* cells,
+                         int64_t cells_cap, int64_t* n_cells, uint32_t* point_cell,
+                         void* ws, size_t* ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Steps 3-4 -- Hamming-1 neighbour search and edge compaction (§2.2,
+ * Algorithm 4): for every cell i and every bit k with x_i(k) = 0, the vector
+ * x_i with bit k set is looked up among the cells; each hit j gives edge (i, j).
+ *   cells      [n_cells][W] words, device: sorted ascending and unique (the
+ *              output of cg_dedup_cells); unsorted input gives unspecified edges.
+ *   edges      uint32[edges_cap][2], device.
+ *   n_edges    host: receives E.
+ *   strategy   CG_STRATEGY_*.
+ *   ws, ws_bytes  as for cg_dedup_cells.
+ * Blocks until done. E > edges_cap gives CG_ERR_CAPACITY with *n_edges = E.
+ * ------------------------------------------------------------------------- */
+cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_bits,
+                          uint32_t* edges, int64_t edges_cap, int64_t* n_edges, int strategy,
+                          void* ws, size_t* ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Context: owns a device memory pool that grows on demand, the pinned host
+ * words used to return counts, and the table-size hints learned from earlier
+ * calls. One context serves one device; calls on one context must not overlap
+ * (use one context per host thread).
+ * ------------------------------------------------------------------------- */
+typedef struct cg_ctx cg_ctx;
+
+/* Creates a context on `device` (a CUDA device ordinal). */
+cg_status cg_ctx_create(cg_ctx** out, int device);
+/* Frees the context and its pool. Waits for nothing; the caller must make
+ * sure no work that uses the pool is still running. */
+cg_status cg_ctx_destroy(cg_ctx* ctx);
+/* Bytes of device memory the context currently holds. */
+cg_status cg_ctx_pool_bytes(const cg_ctx* ctx, size_t* bytes);
+
+/* Stage timing: with timing enabled, cg_build records CUDA events on its
+ * stream between its stages and, once the build has finished, adds each
+ * stage's duration to a per-stage total. cg_ctx_set_timing resets the totals.
+ * cg_ctx_stage_times returns the number of stages in *n, the number of timed
+ * builds in *builds (nullable) and, for the first `cap` stages, the total ms
+ * (nullable) and the stage names (nullable; static strings owned by the
+ * library). The stage "pack_dedup" holds exactly the fused sign+dedup kernel. */
+cg_status cg_ctx_set_timing(cg_ctx* ctx, int enable);
+cg_status cg_ctx_stage_times(cg_ctx* ctx, double* ms, const char** names, int cap, int* n,
+                             int64_t* builds);
+
+/* ---------------------------------------------------------------------------
+ * Steps 1-4 for one scene: points -> cells -> edges (§2.1, §3.2, §2.2,
+ * Algorithm 4), with the vectors never written to memory when l <= 64.
+ *   pts, a, b   as for cg_pack_signs (device).
+ *   cells       [cells_cap][W] words (word_bits), device.
+ *   edges       uint32[edges_cap][2], device.
+ *   n_cells, n_edges   host: receive U and E.
+ * Blocks until done. Returns CG_ERR_CAPACITY (with both counts written) when
+ * either output is too small; nothing is written past a capacity.
+ * ------------------------------------------------------------------------- */
+cg_status cg_build(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                   const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                   int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
+                   void* stream);
+
+/* Same as cg_build with every array in HOST memory (pinned or pageable): the
+ * call copies the inputs to the context's device pool, builds, and copies the
+ * cells and edges back. Blocks until the copies are done. */
+cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                        const int64_t* b, int ell, int word_bits, void* cells,
+                        int64_t cells_cap, int64_t* n_cells, uint32_t* edges,
+                        int64_t edges_cap, int64_t* n_edges, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CELLGRAPH_H */

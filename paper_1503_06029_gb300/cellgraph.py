@@ -1,0 +1,316 @@
+"""ctypes binding of libcellgraph.so (C-ABI in include/cellgraph.h).
+
+Argument marshalling only: every step runs in the CUDA library. Tensors are
+torch CUDA tensors (device memory and the current stream come from torch);
+vectors use int64 tensors for 64-bit words and int32 tensors for 32-bit words
+(the bits are the unsigned words of the C-ABI), edges are int32 [E, 2] holding
+the uint32 cell numbers.
+
+There is no CPU fallback: if the library is missing or cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcellgraph.so")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_CAPACITY = 3
+ERR_OOM = 4
+ERR_CUDA = 5
+ERR_TIMEOUT = 6
+ERR_INTERNAL = 7
+
+STRATEGY = {"auto": 0, "hash": 1, "sorted": 2}
+
+EXPORTS = [
+    "cg_last_error", "cg_version", "cg_launch_count", "cg_pack_signs", "cg_dedup_cells",
+    "cg_neighbors_h1", "cg_ctx_create", "cg_ctx_destroy", "cg_ctx_pool_bytes", "cg_build",
+    "cg_build_host", "cg_ctx_set_timing", "cg_ctx_stage_times",
+]
+
+
+class CellGraphError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libcellgraph.so (raises if it is missing) and declares signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise CellGraphError(-1, f"{path} is not built (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        P, I64, I, S = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+        PI64 = ctypes.POINTER(ctypes.c_int64)
+        PS = ctypes.POINTER(ctypes.c_size_t)
+        lib.cg_last_error.restype = ctypes.c_char_p
+        lib.cg_version.restype = ctypes.c_char_p
+        lib.cg_launch_count.restype = ctypes.c_uint64
+        lib.cg_pack_signs.argtypes = [P, I64, I, P, P, I, I, P, P]
+        lib.cg_dedup_cells.argtypes = [P, I64, I, I, P, I64, PI64, P, P, PS, P]
+        lib.cg_neighbors_h1.argtypes = [P, I64, I, I, P, I64, PI64, I, P, PS, P]
+        lib.cg_ctx_create.argtypes = [ctypes.POINTER(P), I]
+        lib.cg_ctx_destroy.argtypes = [P]
+        lib.cg_ctx_pool_bytes.argtypes = [P, PS]
+        build_args = [P, P, I64, I, P, P, I, I, P, I64, PI64, P, I64, PI64, P]
+        lib.cg_build.argtypes = build_args
+        lib.cg_build_host.argtypes = build_args
+        lib.cg_ctx_set_timing.argtypes = [P, I]
+        lib.cg_ctx_stage_times.argtypes = [P, P, P, I, ctypes.POINTER(ctypes.c_int), PI64]
+        for name in EXPORTS[3:]:
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(st: int):
+    if st != OK:
+        raise CellGraphError(st, load_library().cg_last_error().decode())
+
+
+def version() -> str:
+    return load_library().cg_version().decode()
+
+
+def launch_count() -> int:
+    return int(load_library().cg_launch_count())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+
+
+def words(ell: int, word_bits: int) -> int:
+    return (ell + word_bits - 1) // word_bits
+
+
+def word_dtype(word_bits: int):
+    torch = _torch()
+    if word_bits == 64:
+        return torch.int64
+    if word_bits == 32:
+        return torch.int32
+    raise ValueError("word_bits must be 32 or 64")
+
+
+def pack_signs(pts, a, b, word_bits: int = 64, out=None, stream=None):
+    """Sign vectors of the points (§2.1): returns [N, W] words on the device."""
+    torch = _torch()
+    lib = load_library()
+    n, d = pts.shape
+    ell = a.shape[0]
+    if out is None:
+        out = torch.empty((n, words(ell, word_bits)), dtype=word_dtype(word_bits),
+                          device=pts.device)
+    _check(lib.cg_pack_signs(_dev(pts, torch.int32, "pts"), n, d, _dev(a, torch.int32, "a"),
+                             _dev(b, torch.int64, "b"), ell, word_bits,
+                             _dev(out, word_dtype(word_bits), "keys"), _stream_ptr(stream)))
+    return out
+
+
+def dedup_cells(keys, ell: int, word_bits: int = 64, point_cell: bool = False, stream=None):
+    """Sorted distinct vectors (§3.2); optionally the cell number of every row."""
+    torch = _torch()
+    lib = load_library()
+    n = keys.shape[0]
+    kp = _dev(keys, word_dtype(word_bits), "keys")
+    need = ctypes.c_size_t(0)
+    st = ctypes.c_void_p(None)
+    _check(lib.cg_dedup_cells(kp, n, ell, word_bits, None, 0, None, None, None,
+                              ctypes.byref(need), st))
+    ws = torch.empty(need.value, dtype=torch.uint8, device=keys.device)
+    cells = torch.empty((max(n, 1), words(ell, word_bits)), dtype=word_dtype(word_bits),
+                        device=keys.device)
+    pc = torch.empty(max(n, 1), dtype=torch.int32, device=keys.device) if point_cell else None
+    nc = ctypes.c_int64(0)
+    _check(lib.cg_dedup_cells(kp, n, ell, word_bits, _dev(cells, word_dtype(word_bits), "cells"),
+                              cells.shape[0], ctypes.byref(nc),
+                              _dev(pc, torch.int32, "point_cell") if pc is not None else None,
+                              ctypes.c_void_p(ws.data_ptr()), ctypes.byref(need),
+                              _stream_ptr(stream)))
+    cells = cells[: nc.value]
+    if point_cell:
+        return cells, pc[:n]
+    return cells
+
+
+def neighbors_h1(cells, ell: int, word_bits: int = 64, strategy: str = "auto", edges_cap=None,
+                 stream=None):
+    """Edges (i, j), i < j, of the cell graph over sorted distinct ``cells``
+    (§2.2, Algorithm 4), as an int32 [E, 2] device tensor."""
+    torch = _torch()
+    lib = load_library()
+    u = cells.shape[0]
+    cp = _dev(cells, word_dtype(word_bits), "cells")
+    need = ctypes.c_size_t(0)
+    _check(lib.cg_neighbors_h1(cp, u, ell, word_bits, None, 0, None, STRATEGY[strategy], None,
+                               ctypes.byref(need), ctypes.c_void_p(None)))
+    ws = torch.empty(need.value, dtype=torch.uint8, device=cells.device)
+    cap = edges_cap if edges_cap is not None else max(1, u * min(ell, 64) // 2 + 1)
+    while True:
+        edges = torch.empty((cap, 2), dtype=torch.int32, device=cells.device)
+        ne = ctypes.c_int64(0)
+        rc = lib.cg_neighbors_h1(cp, u, ell, word_bits, _dev(edges, torch.int32, "edges"), cap,
+                                 ctypes.byref(ne), STRATEGY[strategy],
+                                 ctypes.c_void_p(ws.data_ptr()), ctypes.byref(need),
+                                 _stream_ptr(stream))
+        if rc == ERR_CAPACITY:
+            cap = ne.value
+            continue
+        _check(rc)
+        return edges[: ne.value]
+
+
+def arrangement_cells_bound(n: int, d: int, ell: int) -> int:
+    """min(n, sum_{k<=d} C(l, k)): the number of cells of l hyperplanes in
+    R^d, used only as a first guess for output sizes."""
+    return max(1, min(n, sum(math.comb(ell, k) for k in range(d + 1))))
+
+
+class Context:
+    """A library context (device pool, pinned count words, learned sizes) plus
+    output-capacity bookkeeping for ``build``."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p(None)
+        _check(self._lib.cg_ctx_create(ctypes.byref(self._h), device))
+        self.device = device
+        self._caps = {}
+
+    def close(self):
+        if self._h:
+            self._lib.cg_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pool_bytes(self) -> int:
+        v = ctypes.c_size_t(0)
+        _check(self._lib.cg_ctx_pool_bytes(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_timing(self, enable: bool):
+        _check(self._lib.cg_ctx_set_timing(self._h, int(enable)))
+
+    def stage_times(self):
+        """({stage name: total ms}, number of builds) since timing was enabled."""
+        cap = 16
+        ms = (ctypes.c_double * cap)()
+        names = (ctypes.c_char_p * cap)()
+        n = ctypes.c_int(0)
+        builds = ctypes.c_int64(0)
+        _check(self._lib.cg_ctx_stage_times(self._h, ctypes.cast(ms, ctypes.c_void_p),
+                                            ctypes.cast(names, ctypes.c_void_p), cap,
+                                            ctypes.byref(n), ctypes.byref(builds)))
+        return {names[k].decode(): float(ms[k]) for k in range(min(n.value, cap))}, builds.value
+
+    def _initial_caps(self, n, d, ell):
+        u = arrangement_cells_bound(n, d, ell)
+        return max(1, u), max(1, u * min(ell, 64) // 2)
+
+    def build(self, pts, a, b, word_bits: int = 64, stream=None, outputs=None):
+        """Cells and edges of one scene (device tensors in, device tensors out).
+        ``outputs`` may pass preallocated (cells, edges) buffers."""
+        torch = _torch()
+        n, d = pts.shape
+        ell = a.shape[0]
+        key = (n, d, ell, word_bits)
+        ccap, ecap = self._caps.get(key) or self._initial_caps(n, d, ell)
+        args = (_dev(pts, torch.int32, "pts"), n, d, _dev(a, torch.int32, "a"),
+                _dev(b, torch.int64, "b"), ell, word_bits)
+        while True:
+            if outputs is not None and outputs[0].shape[0] >= ccap and outputs[1].shape[0] >= ecap:
+                cells, edges = outputs
+                ccap, ecap = cells.shape[0], edges.shape[0]
+            else:
+                cells = torch.empty((ccap, words(ell, word_bits)), dtype=word_dtype(word_bits),
+                                    device=pts.device)
+                edges = torch.empty((ecap, 2), dtype=torch.int32, device=pts.device)
+            nc = ctypes.c_int64(0)
+            ne = ctypes.c_int64(0)
+            rc = self._lib.cg_build(self._h, *args, _dev(cells, word_dtype(word_bits), "cells"),
+                                    ccap, ctypes.byref(nc), _dev(edges, torch.int32, "edges"),
+                                    ecap, ctypes.byref(ne), _stream_ptr(stream))
+            if rc == ERR_CAPACITY:
+                ccap, ecap = max(ccap, nc.value), max(ecap, ne.value)
+                self._caps[key] = (ccap, ecap)
+                outputs = None
+                continue
+            _check(rc)
+            self._caps[key] = (max(ccap, nc.value), max(ecap, ne.value))
+            return cells[: nc.value], edges[: ne.value]
+
+    def build_host(self, pts: np.ndarray, a: np.ndarray, b: np.ndarray, word_bits: int = 64,
+                   stream=None, outputs=None):
+        """Same as ``build`` with numpy arrays in and out (the C-ABI copies)."""
+        pts = np.ascontiguousarray(pts, dtype=np.int32)
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        b = np.ascontiguousarray(b, dtype=np.int64)
+        n, d = pts.shape
+        ell = a.shape[0]
+        key = ("host", n, d, ell, word_bits)
+        ccap, ecap = self._caps.get(key) or self._initial_caps(n, d, ell)
+        wdt = np.uint64 if word_bits == 64 else np.uint32
+        while True:
+            if outputs is not None and outputs[0].shape[0] >= ccap and outputs[1].shape[0] >= ecap:
+                cells, edges = outputs
+                ccap, ecap = cells.shape[0], edges.shape[0]
+            else:
+                cells = np.empty((ccap, words(ell, word_bits)), dtype=wdt)
+                edges = np.empty((ecap, 2), dtype=np.uint32)
+            nc = ctypes.c_int64(0)
+            ne = ctypes.c_int64(0)
+            s = _stream_ptr(stream) if stream is not None or _torch().cuda.is_available() else None
+            rc = self._lib.cg_build_host(
+                self._h, ctypes.c_void_p(pts.ctypes.data), n, d, ctypes.c_void_p(a.ctypes.data),
+                ctypes.c_void_p(b.ctypes.data), ell, word_bits, ctypes.c_void_p(cells.ctypes.data),
+                ccap, ctypes.byref(nc), ctypes.c_void_p(edges.ctypes.data), ecap,
+                ctypes.byref(ne), s)
+            if rc == ERR_CAPACITY:
+                ccap, ecap = max(ccap, nc.value), max(ecap, ne.value)
+                self._caps[key] = (ccap, ecap)
+                outputs = None
+                continue
+            _check(rc)
+            self._caps[key] = (max(ccap, nc.value), max(ecap, ne.value))
+            return cells[: nc.value], edges[: ne.value]

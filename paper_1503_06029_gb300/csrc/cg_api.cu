@@ -1,0 +1,777 @@
+// C-ABI of libcellgraph (include/cellgraph.h): argument checks, workspace
+// layout, the order of the steps, and the read-back of counts.
+//
+// Step order (one scene): sign vectors (§2.1) -> duplicate removal and sorting
+// (§3.2) -> Hamming-1 search from every cell (Algorithm 4) -> edge compaction.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/cellgraph.h"
+#include "cg_internal.cuh"
+
+namespace cg {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(uint64_t(n), std::memory_order_relaxed); }
+
+int sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+    v = 1;
+  cache[dev] = v;
+  return v;
+}
+
+}  // namespace cg
+
+using namespace cg;
+
+namespace {
+
+thread_local std::string t_err;
+
+cg_status fail(cg_status st, const std::string& msg) {
+  t_err = msg;
+  return st;
+}
+
+cg_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(CG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CG_CUDA(call, where)                         \
+  do {                                               \
+    cudaError_t _e = (call);                         \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+size_t next_pow2(size_t v) {
+  size_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Carves aligned sub-arrays out of one workspace; with base == nullptr it only
+// measures.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  void* take_bytes(size_t bytes) { return take<char>(bytes); }
+};
+
+bool check_common(int64_t n, int ell, int word_bits, std::string* why) {
+  if (n < 0 || uint64_t(n) >= 0xffffffffull) {
+    *why = "n must satisfy 0 <= n < 2^32 - 1";
+    return false;
+  }
+  if (ell < 1 || ell > 4096) {
+    *why = "l must satisfy 1 <= l <= 4096";
+    return false;
+  }
+  if (word_bits != 32 && word_bits != 64) {
+    *why = "word_bits must be 32 or 64";
+    return false;
+  }
+  return true;
+}
+
+// ------------------------------ layouts ---------------------------------
+
+// Small vectors (l <= 64): table + list + sort + neighbour buffers.
+struct SmallWs {
+  DevCounters* ctr;
+  uint64_t* tkeys;
+  uint32_t* tvals;
+  uint64_t* ulist;
+  uint64_t* sortbuf;
+  void* radix;
+  uint32_t* masks;
+  uint32_t* counts;
+  unsigned long long* offsets;
+  void* scan;
+  uint64_t* cells;  // given cells (neighbour search only)
+  size_t cap, ucap;
+};
+
+SmallWs carve_small(Carve& c, size_t cap, size_t ucap, int ell, bool dedup, bool neigh,
+                    bool given_cells) {
+  SmallWs w{};
+  w.cap = cap;
+  w.ucap = ucap;
+  const int nh = (ell + 31) / 32;
+  w.ctr = c.take<DevCounters>(1);
+  w.tkeys = c.take<uint64_t>(cap);
+  w.tvals = c.take<uint32_t>(cap);
+  if (dedup) {
+    w.ulist = c.take<uint64_t>(ucap);
+    w.sortbuf = c.take<uint64_t>(ucap);
+    w.radix = c.take_bytes(radix_scratch_bytes(ucap));
+  }
+  if (given_cells) w.cells = c.take<uint64_t>(ucap);
+  if (neigh) {
+    w.masks = c.take<uint32_t>(ucap * nh);
+    w.counts = c.take<uint32_t>(ucap);
+    w.offsets = c.take<unsigned long long>(ucap);
+    w.scan = c.take_bytes(scan_scratch_bytes(ucap));
+  }
+  return w;
+}
+
+struct WideWs {
+  DevCounters* ctr;
+  uint64_t* keys64;  // converted input vectors (or the caller's, when word_bits == 64)
+  uint64_t* slots;
+  uint32_t* idx0;
+  uint32_t* idx1;
+  uint64_t* kw0;
+  uint64_t* kw1;
+  void* radix;
+  uint64_t* cells;
+  uint32_t* rank;
+  uint64_t* fp;
+  uint32_t* masks;
+  uint32_t* counts;
+  unsigned long long* offsets;
+  void* scan;
+  size_t cap, ucap;
+};
+
+WideWs carve_wide(Carve& c, size_t n, size_t cap, size_t ucap, int ell, bool need_keys64,
+                  bool dedup, bool rank, bool neigh) {
+  WideWs w{};
+  w.cap = cap;
+  w.ucap = ucap;
+  const int w64 = (ell + 63) / 64;
+  const int nh = (ell + 31) / 32;
+  w.ctr = c.take<DevCounters>(1);
+  if (need_keys64) w.keys64 = c.take<uint64_t>(n * w64);
+  w.slots = c.take<uint64_t>(cap);
+  if (dedup) {
+    w.idx0 = c.take<uint32_t>(ucap);
+    w.idx1 = c.take<uint32_t>(ucap);
+    w.kw0 = c.take<uint64_t>(ucap);
+    w.kw1 = c.take<uint64_t>(ucap);
+    w.radix = c.take_bytes(radix_scratch_bytes(ucap));
+  }
+  w.cells = c.take<uint64_t>(ucap * w64);
+  if (rank) w.rank = c.take<uint32_t>(n);
+  if (neigh) {
+    w.fp = c.take<uint64_t>(ucap);
+    w.masks = c.take<uint32_t>(ucap * nh);
+    w.counts = c.take<uint32_t>(ucap);
+    w.offsets = c.take<unsigned long long>(ucap);
+    w.scan = c.take_bytes(scan_scratch_bytes(ucap));
+  }
+  return w;
+}
+
+cg_status read_counters(DevCounters* dev, DevCounters* host, cudaStream_t s) {
+  CG_CUDA(cudaMemcpyAsync(host, dev, sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
+          "reading counters");
+  CG_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+  if (host->error)
+    return fail(CG_ERR_INTERNAL, "device-side consistency check failed (code " +
+                                     std::to_string(host->error) + ")");
+  return CG_OK;
+}
+
+// ----------------------------- pipelines ---------------------------------
+
+// Steps 3-4 over internal sorted rows (small); ctr->n_unique holds U.
+cg_status neighbors_small_steps(const SmallWs& w, int ell, int strategy, uint32_t* edges,
+                                int64_t edges_cap, cudaStream_t s) {
+  SmallTable t{w.tkeys, w.tvals, uint32_t(w.cap - 1), nullptr, 0, w.ctr};
+  const uint64_t* cells = w.cells;
+  CG_CUDA(launch_neighbors_small(cells, t, ell, strategy, w.masks, w.counts, w.ucap, s),
+          "neighbour search");
+  CG_CUDA(scan_exclusive_u32(w.counts, w.offsets, &w.ctr->n_unique, w.ucap, &w.ctr->n_edges,
+                             w.scan, s),
+          "edge offsets");
+  CG_CUDA(launch_emit_small(cells, t, ell, strategy, w.masks, w.offsets, edges, edges_cap,
+                            w.ucap, s),
+          "edge output");
+  return CG_OK;
+}
+
+cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t* edges,
+                               int64_t edges_cap, cudaStream_t s) {
+  const int w64 = (ell + 63) / 64;
+  WideTable t{w.slots, uint32_t(w.cap - 1), nullptr, 0, w.ctr};
+  if (strategy != CG_STRATEGY_SORTED) {
+    CG_CUDA(launch_fill_u64(w.slots, kEmpty, w.cap, s), "clearing table");
+    CG_CUDA(launch_index_wide(w.cells, w64, ell, t, w.fp, w.ucap, s), "fingerprint index");
+  }
+  CG_CUDA(launch_neighbors_wide(w.cells, w64, ell, t, w.fp, strategy, w.masks, w.counts, w.ucap,
+                                s),
+          "neighbour search");
+  CG_CUDA(scan_exclusive_u32(w.counts, w.offsets, &w.ctr->n_unique, w.ucap, &w.ctr->n_edges,
+                             w.scan, s),
+          "edge offsets");
+  CG_CUDA(launch_emit_wide(w.cells, w64, ell, t, w.fp, strategy, w.masks, w.offsets, edges,
+                           edges_cap, w.ucap, s),
+          "edge output");
+  return CG_OK;
+}
+
+// Step 2 on small vectors already in the table (ulist holds them in insertion
+// order): sort, number, write.
+cg_status dedup_small_tail(SmallWs& w, int ell, cudaStream_t s) {
+  bool in1 = false;
+  CG_CUDA(radix_sort_u64(w.ulist, w.sortbuf, nullptr, nullptr, &w.ctr->n_unique, w.ucap, ell,
+                         w.radix, s, &in1),
+          "sorting cells");
+  w.cells = in1 ? w.sortbuf : w.ulist;
+  SmallTable t{w.tkeys, w.tvals, uint32_t(w.cap - 1), w.ulist, uint32_t(w.ucap), w.ctr};
+  CG_CUDA(launch_rank_small(w.cells, t, w.ucap, s), "numbering cells");
+  return CG_OK;
+}
+
+// Step 2 for wide vectors in keys64: insert, sort representatives, gather rows.
+cg_status dedup_wide_steps(WideWs& w, const uint64_t* keys64, int64_t n, int ell, bool rank,
+                           cudaStream_t s) {
+  const int w64 = (ell + 63) / 64;
+  WideTable t{w.slots, uint32_t(w.cap - 1), w.idx0, uint32_t(w.ucap), w.ctr};
+  CG_CUDA(launch_fill_u64(w.slots, kEmpty, w.cap, s), "clearing table");
+  CG_CUDA(launch_insert_wide(keys64, n, w64, t, s), "inserting vectors");
+  uint32_t* sorted = nullptr;
+  CG_CUDA(sort_wide(keys64, w64, ell, w.idx0, w.idx1, w.kw0, w.kw1, &w.ctr->n_unique, w.ucap,
+                    w.radix, s, &sorted),
+          "sorting cells");
+  CG_CUDA(launch_gather_rows(keys64, w64, sorted, &w.ctr->n_unique, w.ucap, w.cells, s),
+          "gathering cells");
+  if (rank) CG_CUDA(launch_rank_by_row(sorted, &w.ctr->n_unique, w.ucap, w.rank, s), "ranks");
+  return CG_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (dev >= 0 && cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+// ------------------------------- context ---------------------------------
+
+struct cg_ctx {
+  int device = 0;
+  void* pool = nullptr;
+  size_t pool_bytes = 0;
+  void* io = nullptr;  // device copies of host inputs/outputs (cg_build_host)
+  size_t io_bytes = 0;
+  DevCounters* host_ctr = nullptr;  // pinned
+  // Table capacity learned per (n, l, d) after an overflow.
+  std::map<std::tuple<int64_t, int, int>, size_t> cap_hint;
+  // Stage timing (CUDA events on the build's stream), off by default.
+  bool timing = false;
+  static constexpr int kMaxMarks = 16;
+  cudaEvent_t ev[kMaxMarks] = {};
+  const char* mark_name[kMaxMarks] = {};
+  int n_marks = 0;
+  // Per-stage totals over the builds since timing was (re)enabled.
+  std::vector<std::pair<const char*, double>> stage_ms;
+  int64_t timed_builds = 0;
+};
+
+namespace {
+void mark(cg_ctx* ctx, const char* name, cudaStream_t s) {
+  if (!ctx || !ctx->timing || ctx->n_marks >= cg_ctx::kMaxMarks) return;
+  cudaEventRecord(ctx->ev[ctx->n_marks], s);
+  ctx->mark_name[ctx->n_marks] = name;
+  ++ctx->n_marks;
+}
+
+// Adds the stage durations of a build whose stream has been synchronised.
+void accumulate_marks(cg_ctx* ctx) {
+  if (!ctx->timing || ctx->n_marks < 2) return;
+  for (int k = 1; k < ctx->n_marks; ++k) {
+    float v = 0.0f;
+    if (cudaEventElapsedTime(&v, ctx->ev[k - 1], ctx->ev[k]) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0.0f;
+    }
+    bool found = false;
+    for (auto& e : ctx->stage_ms) {
+      if (std::strcmp(e.first, ctx->mark_name[k]) == 0) {
+        e.second += v;
+        found = true;
+        break;
+      }
+    }
+    if (!found) ctx->stage_ms.emplace_back(ctx->mark_name[k], double(v));
+  }
+  ++ctx->timed_builds;
+}
+}  // namespace
+
+static cg_status ensure_pool(cg_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->pool_bytes) return CG_OK;
+  if (ctx->pool) {
+    CG_CUDA(cudaDeviceSynchronize(), "pool growth sync");
+    cudaFree(ctx->pool);
+    ctx->pool = nullptr;
+    ctx->pool_bytes = 0;
+  }
+  size_t want = bytes + bytes / 4;
+  if (cudaMalloc(&ctx->pool, want) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->pool = nullptr;
+    return fail(CG_ERR_OOM, "device pool allocation of " + std::to_string(want) + " bytes failed");
+  }
+  ctx->pool_bytes = want;
+  return CG_OK;
+}
+
+static cg_status ensure_io(cg_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->io_bytes) return CG_OK;
+  if (ctx->io) {
+    CG_CUDA(cudaDeviceSynchronize(), "io growth sync");
+    cudaFree(ctx->io);
+    ctx->io = nullptr;
+    ctx->io_bytes = 0;
+  }
+  if (cudaMalloc(&ctx->io, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->io = nullptr;
+    return fail(CG_ERR_OOM, "device I/O allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  ctx->io_bytes = bytes;
+  return CG_OK;
+}
+
+extern "C" {
+
+const char* cg_last_error(void) { return t_err.c_str(); }
+
+const char* cg_version(void) { return "cellgraph 0.1 (sm_103a)"; }
+
+uint64_t cg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+cg_status cg_ctx_create(cg_ctx** out, int device) {
+  if (!out) return fail(CG_ERR_INVALID_ARG, "out is NULL");
+  int nd = 0;
+  CG_CUDA(cudaGetDeviceCount(&nd), "cudaGetDeviceCount");
+  if (device < 0 || device >= nd) return fail(CG_ERR_INVALID_ARG, "no such device");
+  DeviceGuard g(device);
+  cg_ctx* c = new cg_ctx();
+  c->device = device;
+  if (cudaMallocHost(&c->host_ctr, sizeof(DevCounters)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(CG_ERR_OOM, "pinned host allocation failed");
+  }
+  *out = c;
+  return CG_OK;
+}
+
+cg_status cg_ctx_destroy(cg_ctx* ctx) {
+  if (!ctx) return CG_OK;
+  DeviceGuard g(ctx->device);
+  if (ctx->pool) cudaFree(ctx->pool);
+  if (ctx->io) cudaFree(ctx->io);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->host_ctr) cudaFreeHost(ctx->host_ctr);
+  delete ctx;
+  return CG_OK;
+}
+
+cg_status cg_ctx_set_timing(cg_ctx* ctx, int enable) {
+  if (!ctx) return fail(CG_ERR_INVALID_ARG, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  if (enable && !ctx->ev[0]) {
+    for (auto& e : ctx->ev) CG_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+  }
+  ctx->timing = enable != 0;
+  ctx->n_marks = 0;
+  ctx->stage_ms.clear();
+  ctx->timed_builds = 0;
+  return CG_OK;
+}
+
+cg_status cg_ctx_stage_times(cg_ctx* ctx, double* ms, const char** names, int cap, int* n,
+                             int64_t* builds) {
+  if (!ctx || !n) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  *n = int(ctx->stage_ms.size());
+  if (builds) *builds = ctx->timed_builds;
+  for (int k = 0; k < *n && k < cap; ++k) {
+    if (ms) ms[k] = ctx->stage_ms[size_t(k)].second;
+    if (names) names[k] = ctx->stage_ms[size_t(k)].first;
+  }
+  return CG_OK;
+}
+
+cg_status cg_ctx_pool_bytes(const cg_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  *bytes = ctx->pool_bytes + ctx->io_bytes;
+  return CG_OK;
+}
+
+cg_status cg_pack_signs(const int32_t* pts, int64_t n, int d, const int32_t* a, const int64_t* b,
+                        int ell, int word_bits, void* keys, void* stream) {
+  std::string why;
+  if (!check_common(n, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
+  if (d < 1 || d > 4) return fail(CG_ERR_INVALID_ARG, "d must satisfy 1 <= d <= 4");
+  if (n > 0 && (!pts || !a || !b || !keys)) return fail(CG_ERR_INVALID_ARG, "NULL array");
+  if (n == 0) return CG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  PackArgs pa{pts, n, d, a, b, ell};
+  CG_CUDA(launch_pack_store(pa, word_bits, keys, s), "sign vectors");
+  return CG_OK;
+}
+
+cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, void* cells,
+                         int64_t cells_cap, int64_t* n_cells, uint32_t* point_cell, void* ws,
+                         size_t* ws_bytes, void* stream) {
+  std::string why;
+  if (!check_common(n, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
+  if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
+  const size_t un = size_t(n > 0 ? n : 1);
+  const size_t cap = std::max<size_t>(1024, next_pow2(2 * un));
+  const size_t ucap = un;
+  const bool small = ell <= 64;
+  const bool convert = !small && word_bits == 32;
+  {
+    Carve c{nullptr};
+    if (small) carve_small(c, cap, ucap, ell, true, false, false);
+    else carve_wide(c, un, cap, ucap, ell, convert, true, point_cell != nullptr, false);
+    if (!ws) {
+      *ws_bytes = c.off + 256;
+      return CG_OK;
+    }
+    if (*ws_bytes < c.off) return fail(CG_ERR_INVALID_ARG, "workspace too small");
+  }
+  if (!n_cells) return fail(CG_ERR_INVALID_ARG, "n_cells is NULL");
+  if (n > 0 && !keys) return fail(CG_ERR_INVALID_ARG, "keys is NULL");
+  if (cells_cap < 0 || (cells_cap > 0 && !cells)) return fail(CG_ERR_INVALID_ARG, "cells");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carve c{static_cast<char*>(ws)};
+  DevCounters host{};
+  if (small) {
+    SmallWs w = carve_small(c, cap, ucap, ell, true, false, false);
+    CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
+    CG_CUDA(launch_fill_u64(w.tkeys, kEmpty, cap, s), "clearing table");
+    SmallTable t{w.tkeys, w.tvals, uint32_t(cap - 1), w.ulist, uint32_t(ucap), w.ctr};
+    CG_CUDA(launch_insert_small(keys, n, word_bits, ell, t, s), "inserting vectors");
+    cg_status st = dedup_small_tail(w, ell, s);
+    if (st) return st;
+    CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
+            "writing cells");
+    if (point_cell)
+      CG_CUDA(launch_point_cell_small(keys, n, word_bits, ell, t, point_cell, s), "point cells");
+    st = read_counters(w.ctr, &host, s);
+    if (st) return st;
+  } else {
+    WideWs w = carve_wide(c, un, cap, ucap, ell, convert, true, point_cell != nullptr, false);
+    const uint64_t* k64 = static_cast<const uint64_t*>(keys);
+    if (convert) {
+      CG_CUDA(launch_keys_to_u64(keys, n, word_bits, ell, w.keys64, s), "converting vectors");
+      k64 = w.keys64;
+    }
+    CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
+    cg_status st = dedup_wide_steps(w, k64, n, ell, point_cell != nullptr, s);
+    if (st) return st;
+    CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
+            "writing cells");
+    if (point_cell) {
+      WideTable t{w.slots, uint32_t(cap - 1), w.idx0, uint32_t(ucap), w.ctr};
+      CG_CUDA(launch_point_cell_wide(k64, n, (ell + 63) / 64, t, w.rank, point_cell, s),
+              "point cells");
+    }
+    st = read_counters(w.ctr, &host, s);
+    if (st) return st;
+  }
+  if (host.overflow) return fail(CG_ERR_INTERNAL, "dedup table overflow");
+  *n_cells = host.n_unique;
+  if (int64_t(host.n_unique) > cells_cap)
+    return fail(CG_ERR_CAPACITY, "cells_cap " + std::to_string(cells_cap) + " < U = " +
+                                     std::to_string(host.n_unique));
+  return CG_OK;
+}
+
+cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_bits,
+                          uint32_t* edges, int64_t edges_cap, int64_t* n_edges, int strategy,
+                          void* ws, size_t* ws_bytes, void* stream) {
+  std::string why;
+  if (!check_common(n_cells, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
+  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_SORTED)
+    return fail(CG_ERR_INVALID_ARG, "unknown strategy");
+  if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
+  const size_t un = size_t(n_cells > 0 ? n_cells : 1);
+  const size_t cap = std::max<size_t>(1024, next_pow2(2 * un));
+  const bool small = ell <= 64;
+  {
+    Carve c{nullptr};
+    if (small) carve_small(c, cap, un, ell, false, true, true);
+    else carve_wide(c, un, cap, un, ell, false, false, false, true);
+    if (!ws) {
+      *ws_bytes = c.off + 256;
+      return CG_OK;
+    }
+    if (*ws_bytes < c.off) return fail(CG_ERR_INVALID_ARG, "workspace too small");
+  }
+  if (!n_edges) return fail(CG_ERR_INVALID_ARG, "n_edges is NULL");
+  if (n_cells > 0 && !cells) return fail(CG_ERR_INVALID_ARG, "cells is NULL");
+  if (edges_cap < 0 || (edges_cap > 0 && !edges)) return fail(CG_ERR_INVALID_ARG, "edges");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carve c{static_cast<char*>(ws)};
+  DevCounters host{};
+  if (small) {
+    SmallWs w = carve_small(c, cap, un, ell, false, true, true);
+    CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
+    CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
+    if (strategy != CG_STRATEGY_SORTED) {
+      CG_CUDA(launch_fill_u64(w.tkeys, kEmpty, cap, s), "clearing table");
+      SmallTable t{w.tkeys, w.tvals, uint32_t(cap - 1), nullptr, 0, w.ctr};
+      CG_CUDA(launch_index_small(w.cells, t, un, s), "indexing cells");
+    }
+    cg_status st = neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
+    if (st) return st;
+    st = read_counters(w.ctr, &host, s);
+    if (st) return st;
+  } else {
+    WideWs w = carve_wide(c, un, cap, un, ell, false, false, false, true);
+    CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
+    CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
+    cg_status st = neighbors_wide_steps(w, ell, strategy, edges, edges_cap, s);
+    if (st) return st;
+    st = read_counters(w.ctr, &host, s);
+    if (st) return st;
+  }
+  if (host.overflow) return fail(CG_ERR_INTERNAL, "lookup table overflow");
+  *n_edges = int64_t(host.n_edges);
+  if (int64_t(host.n_edges) > edges_cap)
+    return fail(CG_ERR_CAPACITY, "edges_cap " + std::to_string(edges_cap) + " < E = " +
+                                     std::to_string(host.n_edges));
+  return CG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+size_t arrangement_bound(int64_t n, int d, int ell) {
+  // sum_{k<=d} C(l, k), saturating; number of cells of l hyperplanes in R^d.
+  double s = 0, c = 1;
+  for (int k = 0; k <= d; ++k) {
+    if (k > 0) c = c * double(ell - k + 1) / double(k);
+    s += c;
+  }
+  double est = s;
+  if (ell < 60) est = std::min(est, double(uint64_t(1) << ell));
+  est = std::min(est, double(n));
+  return size_t(est < 1 ? 1 : est);
+}
+
+// Enqueues the whole build; returns after reading the counters.
+cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                     const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                     uint32_t* edges, int64_t edges_cap, size_t cap, cudaStream_t s,
+                     DevCounters* host) {
+  const size_t un = size_t(n > 0 ? n : 1);
+  const size_t ucap = std::min(un, cap / 2);
+  const bool small = ell <= 64;
+  Carve m{nullptr};
+  if (small) carve_small(m, cap, ucap, ell, true, true, false);
+  else carve_wide(m, un, cap, ucap, ell, true, true, false, true);
+  cg_status st = ensure_pool(ctx, m.off + 256);
+  if (st) return st;
+  Carve c{static_cast<char*>(ctx->pool)};
+  PackArgs pa{pts, n, d, a, b, ell};
+  ctx->n_marks = 0;
+  mark(ctx, "start", s);
+  if (small) {
+    SmallWs w = carve_small(c, cap, ucap, ell, true, true, false);
+    CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
+    CG_CUDA(launch_fill_u64(w.tkeys, kEmpty, cap, s), "clearing table");
+    mark(ctx, "clear", s);
+    SmallTable t{w.tkeys, w.tvals, uint32_t(cap - 1), w.ulist, uint32_t(ucap), w.ctr};
+    if (n > 0) CG_CUDA(launch_pack_insert(pa, t, s), "sign vectors + dedup");
+    mark(ctx, "pack_dedup", s);
+    st = dedup_small_tail(w, ell, s);
+    if (st) return st;
+    CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
+            "writing cells");
+    mark(ctx, "sort_number", s);
+    st = neighbors_small_steps(w, ell, CG_STRATEGY_HASH, edges, edges_cap, s);
+    if (st) return st;
+    mark(ctx, "neighbors_edges", s);
+    st = read_counters(w.ctr, host, s);
+    if (st == CG_OK) accumulate_marks(ctx);
+    return st;
+  }
+  WideWs w = carve_wide(c, un, cap, ucap, ell, true, true, false, true);
+  CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
+  if (n > 0) CG_CUDA(launch_pack_store(pa, 64, w.keys64, s), "sign vectors");
+  mark(ctx, "pack", s);
+  st = dedup_wide_steps(w, w.keys64, n, ell, false, s);
+  if (st) return st;
+  CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
+          "writing cells");
+  mark(ctx, "dedup_sort", s);
+  st = neighbors_wide_steps(w, ell, CG_STRATEGY_HASH, edges, edges_cap, s);
+  if (st) return st;
+  mark(ctx, "neighbors_edges", s);
+  st = read_counters(w.ctr, host, s);
+  if (st == CG_OK) accumulate_marks(ctx);
+  return st;
+}
+
+cg_status build_checked(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                        const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                        int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
+                        cudaStream_t s) {
+  const size_t un = size_t(n > 0 ? n : 1);
+  const size_t full = std::max<size_t>(1024, next_pow2(2 * un));
+  const auto key = std::make_tuple(n, ell, d);
+  size_t cap = std::max<size_t>(1024, next_pow2(2 * arrangement_bound(n, d, ell)));
+  auto it = ctx->cap_hint.find(key);
+  if (it != ctx->cap_hint.end()) cap = std::max(cap, it->second);
+  cap = std::min(cap, full);
+  for (;;) {
+    DevCounters* host = ctx->host_ctr;
+    cg_status st = build_once(ctx, pts, n, d, a, b, ell, word_bits, cells, cells_cap, edges,
+                              edges_cap, cap, s, host);
+    if (st) return st;
+    if (host->overflow) {
+      if (cap >= full) return fail(CG_ERR_INTERNAL, "table overflow at full capacity");
+      cap = std::min(full, cap * 4);
+      ctx->cap_hint[key] = cap;
+      continue;
+    }
+    *n_cells = host->n_unique;
+    *n_edges = int64_t(host->n_edges);
+    if (int64_t(host->n_unique) > cells_cap || int64_t(host->n_edges) > edges_cap)
+      return fail(CG_ERR_CAPACITY, "output capacity: U = " + std::to_string(host->n_unique) +
+                                       " (cap " + std::to_string(cells_cap) + "), E = " +
+                                       std::to_string(host->n_edges) + " (cap " +
+                                       std::to_string(edges_cap) + ")");
+    return CG_OK;
+  }
+}
+
+bool check_build_args(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                      const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                      int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
+                      std::string* why) {
+  if (!ctx) {
+    *why = "ctx is NULL";
+    return false;
+  }
+  if (!check_common(n, ell, word_bits, why)) return false;
+  if (d < 1 || d > 4) {
+    *why = "d must satisfy 1 <= d <= 4";
+    return false;
+  }
+  if (n > 0 && (!pts || !a || !b)) {
+    *why = "NULL input array";
+    return false;
+  }
+  if (!n_cells || !n_edges) {
+    *why = "NULL count pointer";
+    return false;
+  }
+  if (cells_cap < 0 || (cells_cap > 0 && !cells) || edges_cap < 0 || (edges_cap > 0 && !edges)) {
+    *why = "bad output array or capacity";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+cg_status cg_build(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                   const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                   int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
+                   void* stream) {
+  std::string why;
+  if (!check_build_args(ctx, pts, n, d, a, b, ell, word_bits, cells, cells_cap, n_cells, edges,
+                        edges_cap, n_edges, &why))
+    return fail(CG_ERR_INVALID_ARG, why);
+  DeviceGuard g(ctx->device);
+  return build_checked(ctx, pts, n, d, a, b, ell, word_bits, cells, cells_cap, n_cells, edges,
+                       edges_cap, n_edges, static_cast<cudaStream_t>(stream));
+}
+
+cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                        const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                        int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
+                        void* stream) {
+  std::string why;
+  if (!check_build_args(ctx, pts, n, d, a, b, ell, word_bits, cells, cells_cap, n_cells, edges,
+                        edges_cap, n_edges, &why))
+    return fail(CG_ERR_INVALID_ARG, why);
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int wc = (ell + word_bits - 1) / word_bits;
+  const size_t cell_bytes = size_t(cells_cap) * wc * (word_bits / 8);
+  const size_t edge_bytes = size_t(edges_cap) * 2 * sizeof(uint32_t);
+  // Inputs and outputs live in the context's I/O buffer, apart from the work
+  // pool (which the build may regrow).
+  Carve m{nullptr};
+  m.take<int32_t>(size_t(n) * d);
+  m.take<int32_t>(size_t(ell) * d);
+  m.take<int64_t>(size_t(ell));
+  m.take_bytes(cell_bytes);
+  m.take_bytes(edge_bytes);
+  cg_status st = ensure_io(ctx, m.off + 256);
+  if (st) return st;
+  Carve c{static_cast<char*>(ctx->io)};
+  int32_t* dpts = c.take<int32_t>(size_t(n) * d);
+  int32_t* da = c.take<int32_t>(size_t(ell) * d);
+  int64_t* db = c.take<int64_t>(size_t(ell));
+  void* dcells = c.take_bytes(cell_bytes);
+  uint32_t* dedges = static_cast<uint32_t*>(c.take_bytes(edge_bytes));
+  if (n > 0)
+    CG_CUDA(cudaMemcpyAsync(dpts, pts, size_t(n) * d * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            s),
+            "copying points");
+  CG_CUDA(cudaMemcpyAsync(da, a, size_t(ell) * d * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+          "copying normals");
+  CG_CUDA(cudaMemcpyAsync(db, b, size_t(ell) * sizeof(int64_t), cudaMemcpyHostToDevice, s),
+          "copying offsets");
+  st = build_checked(ctx, dpts, n, d, da, db, ell, word_bits, dcells, cells_cap, n_cells, dedges,
+                     edges_cap, n_edges, s);
+  if (st != CG_OK && st != CG_ERR_CAPACITY) return st;
+  const size_t u = size_t(std::min<int64_t>(*n_cells, cells_cap));
+  const size_t e = size_t(std::min<int64_t>(*n_edges, edges_cap));
+  if (st == CG_OK) {
+    if (u) CG_CUDA(cudaMemcpyAsync(cells, dcells, u * wc * (word_bits / 8), cudaMemcpyDeviceToHost,
+                                   s),
+                   "copying cells");
+    if (e) CG_CUDA(cudaMemcpyAsync(edges, dedges, e * 2 * sizeof(uint32_t),
+                                   cudaMemcpyDeviceToHost, s),
+                   "copying edges");
+    CG_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+  }
+  return st;
+}
+
+}  // extern "C"

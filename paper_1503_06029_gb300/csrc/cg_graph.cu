@@ -1,0 +1,755 @@
+// Steps 2-4 of the cell-graph construction around the sort: hash-based
+// duplicate removal (§3.2: duplicates of X are removed so that each pair is
+// output once, §2.2), the Hamming-1 search (Algorithm 4: flip one bit of a cell,
+// look the result up) and the compaction of hits into the edge list.
+//
+// Vectors of l <= 64 bits are handled as single 64-bit words ("small"): the
+// tables hold the vectors themselves. Longer vectors ("wide", W = ceil(l/64)
+// words) are referenced by row number; their lookup table is keyed on a
+// GF(2)-linear fingerprint, so the fingerprint of a one-bit change is one XOR
+// away, and every fingerprint match is verified word by word.
+//
+// Every kernel after the dedup step reads U from device memory and returns
+// early if the dedup step overflowed its capacity.
+#include "cg_internal.cuh"
+
+namespace cg {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+int grid_for(size_t items, int per_block, int blocks_per_sm = 8) {
+  const size_t want = (items + per_block - 1) / per_block;
+  const size_t cap = size_t(sm_count()) * blocks_per_sm;
+  size_t g = want < cap ? want : cap;
+  return int(g < 1 ? 1 : g);
+}
+
+// 64-bit word j of row r of a caller-layout array of ceil(l/word_bits) words.
+__device__ __forceinline__ uint64_t load_word(const void* base, int64_t r, int j, int word_bits,
+                                              int w_caller) {
+  if (word_bits == 64) return static_cast<const uint64_t*>(base)[r * w_caller + j];
+  const uint32_t* p = static_cast<const uint32_t*>(base) + r * w_caller;
+  const uint64_t lo = p[2 * j];
+  const uint64_t hi = (2 * j + 1 < w_caller) ? p[2 * j + 1] : 0u;
+  return lo | (hi << 32);
+}
+
+// ------------------------------- utilities -------------------------------
+
+__global__ void fill_u64(uint64_t* p, uint64_t v, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    p[i] = v;
+}
+
+__global__ void zero_counters(DevCounters* c) {
+  if (threadIdx.x < sizeof(DevCounters) / 4) reinterpret_cast<uint32_t*>(c)[threadIdx.x] = 0;
+}
+
+// Bits >= l of a caller's row are ignored (cleared on load).
+__device__ __forceinline__ uint64_t valid_bits(int j, int w64, int ell) {
+  return (j == w64 - 1 && (ell & 63)) ? ((1ull << (ell & 63)) - 1) : ~0ull;
+}
+
+__global__ void keys_to_u64(const void* keys, int64_t n, int word_bits, int w_caller, int w64,
+                            int ell, uint64_t* out) {
+  const int64_t total = n * w64;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = t / w64;
+    const int j = int(t - r * w64);
+    out[t] = load_word(keys, r, j, word_bits, w_caller) & valid_bits(j, w64, ell);
+  }
+}
+
+__global__ void load_cells(const void* cells, int64_t n, int word_bits, int w_caller, int w64,
+                           int ell, uint64_t* out, DevCounters* ctr) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_unique = unsigned(n);
+  const int64_t total = n * w64;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = t / w64;
+    const int j = int(t - r * w64);
+    out[t] = load_word(cells, r, j, word_bits, w_caller) & valid_bits(j, w64, ell);
+  }
+}
+
+__global__ void write_cells(const uint64_t* cells, int w64, int word_bits, int w_caller,
+                            void* out, int64_t cap, const DevCounters* ctr) {
+  if (ctr->overflow) return;
+  const int64_t u = ctr->n_unique;
+  if (u > cap) return;  // capacity error: the host reports it, nothing is written
+  const int64_t total = u * w_caller;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = t / w_caller;
+    const int j = int(t - r * w_caller);
+    if (word_bits == 64) {
+      static_cast<uint64_t*>(out)[t] = cells[r * w64 + j];
+    } else {
+      static_cast<uint32_t*>(out)[t] = uint32_t(cells[r * w64 + j / 2] >> (32 * (j & 1)));
+    }
+  }
+}
+
+// ------------------------------- small path ------------------------------
+
+struct SmallHash {
+  const uint64_t* keys;
+  const uint32_t* vals;
+  uint32_t mask;
+  const DevCounters* ctr;
+  __device__ __forceinline__ int64_t find(uint64_t y) const {
+    if (y == kEmpty) return ctr->ones_present ? int64_t(ctr->ones_rank) : -1;
+    uint32_t slot = uint32_t(mix64(y)) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+      const uint64_t cur = keys[slot];
+      if (cur == y) return vals[slot];
+      if (cur == kEmpty) return -1;
+      slot = (slot + 1) & mask;
+    }
+    return -1;
+  }
+};
+
+struct SmallSorted {
+  const uint64_t* cells;
+  const DevCounters* ctr;
+  __device__ __forceinline__ int64_t find(uint64_t y) const {
+    uint32_t lo = 0, hi = ctr->n_unique;
+    while (lo < hi) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      const uint64_t v = cells[mid];
+      if (v < y) lo = mid + 1;
+      else hi = mid;
+    }
+    return (lo < ctr->n_unique && cells[lo] == y) ? int64_t(lo) : -1;
+  }
+};
+
+__global__ void insert_small(const void* keys, int64_t n, int word_bits, int w_caller,
+                             SmallTable t) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n;
+       p += int64_t(gridDim.x) * blockDim.x)
+    small_insert(t, load_word(keys, p, 0, word_bits, w_caller));
+}
+
+// Finds the slot of a vector known to be in the table.
+__device__ __forceinline__ int64_t small_slot(const SmallTable& t, uint64_t key) {
+  uint32_t slot = uint32_t(mix64(key)) & t.mask;
+  for (uint32_t probe = 0; probe <= t.mask; ++probe) {
+    const uint64_t cur = t.keys[slot];
+    if (cur == key) return slot;
+    if (cur == kEmpty) return -1;
+    slot = (slot + 1) & t.mask;
+  }
+  return -1;
+}
+
+__global__ void rank_small(const uint64_t* cells, SmallTable t) {
+  if (t.ctr->overflow) return;
+  const uint32_t u = t.ctr->n_unique;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
+    const uint64_t key = cells[i];
+    if (key == kEmpty) {
+      t.ctr->ones_rank = i;
+      continue;
+    }
+    const int64_t slot = small_slot(t, key);
+    if (slot < 0) {
+      atomicOr(&t.ctr->error, 1u);
+      continue;
+    }
+    t.vals[slot] = i;
+  }
+}
+
+__global__ void index_small(const uint64_t* cells, SmallTable t) {
+  const uint32_t u = t.ctr->n_unique;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
+    const uint64_t key = cells[i];
+    if (key == kEmpty) {
+      t.ctr->ones_present = 1u;
+      t.ctr->ones_rank = i;
+      continue;
+    }
+    uint32_t slot = uint32_t(mix64(key)) & t.mask;
+    bool placed = false;
+    for (uint32_t probe = 0; probe <= t.mask; ++probe) {
+      const unsigned long long old =
+          atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + slot),
+                    static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(key));
+      if (old == kEmpty) {
+        t.vals[slot] = i;
+        placed = true;
+        break;
+      }
+      if (old == key) break;  // repeated cell: input is not unique
+      slot = (slot + 1) & t.mask;
+    }
+    if (!placed) atomicOr(&t.ctr->error, 2u);
+  }
+}
+
+__global__ void point_cell_small(const void* keys, int64_t n, int word_bits, int w_caller,
+                                 SmallTable t, uint32_t* point_cell) {
+  if (t.ctr->overflow) return;
+  const SmallHash h{t.keys, t.vals, t.mask, t.ctr};
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t j = h.find(load_word(keys, p, 0, word_bits, w_caller));
+    if (j < 0) atomicOr(&t.ctr->error, 4u);
+    point_cell[p] = uint32_t(j);
+  }
+}
+
+// One warp per cell; lane l of chunk h tests bit k = 32h + l (Algorithm 4,
+// one thread per bit). Only zero bits are flipped, so each edge is found once,
+// from its smaller endpoint.
+template <class L>
+__global__ void __launch_bounds__(kThreads)
+    neighbors_small(const uint64_t* __restrict__ cells, L look, const DevCounters* ctr, int ell,
+                    uint32_t* __restrict__ masks, uint32_t* __restrict__ counts) {
+  if (ctr->overflow) return;
+  const uint32_t u = ctr->n_unique;
+  const int nh = (ell + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < u; i += warps) {
+    const uint64_t x = cells[i];
+    uint32_t total = 0;
+    for (int h = 0; h < nh; ++h) {
+      const int k = h * 32 + lane;
+      bool hit = false;
+      if (k < ell && !((x >> k) & 1ull)) hit = look.find(x | (1ull << k)) >= 0;
+      const uint32_t m = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) masks[uint64_t(i) * nh + h] = m;
+      total += __popc(m);
+    }
+    if (lane == 0) counts[i] = total;
+  }
+}
+
+template <class L>
+__global__ void __launch_bounds__(kThreads)
+    emit_small(const uint64_t* __restrict__ cells, L look, DevCounters* ctr, int ell,
+               const uint32_t* __restrict__ masks, const unsigned long long* __restrict__ offsets,
+               uint32_t* __restrict__ edges, int64_t cap) {
+  if (ctr->overflow) return;
+  const uint32_t u = ctr->n_unique;
+  const int nh = (ell + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < u; i += warps) {
+    const uint64_t x = cells[i];
+    unsigned long long off = offsets[i];
+    for (int h = 0; h < nh; ++h) {
+      const uint32_t m = masks[uint64_t(i) * nh + h];
+      if ((m >> lane) & 1u) {
+        const int k = h * 32 + lane;
+        const int64_t j = look.find(x | (1ull << k));
+        if (j < 0) atomicOr(&ctr->error, 8u);
+        const unsigned long long r = off + __popc(m & lanemask_lt());
+        if (r < (unsigned long long)cap) {
+          edges[2 * r] = i;
+          edges[2 * r + 1] = uint32_t(j);
+        }
+      }
+      off += __popc(m);
+    }
+  }
+}
+
+// ------------------------------- wide path -------------------------------
+
+__device__ __forceinline__ uint64_t hash_row(const uint64_t* r, int w) {
+  uint64_t h = 0x9e3779b97f4a7c15ull * uint64_t(w);
+  for (int j = 0; j < w; ++j) h = mix64(h ^ r[j]);
+  return h;
+}
+
+__device__ __forceinline__ bool rows_equal(const uint64_t* x, const uint64_t* y, int w) {
+  for (int j = 0; j < w; ++j)
+    if (x[j] != y[j]) return false;
+  return true;
+}
+
+__global__ void insert_wide(const uint64_t* __restrict__ keys, int64_t n, int w, WideTable t) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const uint64_t* kp = keys + p * w;
+    const uint64_t h = hash_row(kp, w);
+    const uint32_t tag = uint32_t(h >> 32);
+    const uint64_t entry = (uint64_t(tag) << 32) | uint64_t(p);
+    uint32_t slot = uint32_t(h) & t.mask;
+    bool done = false;
+    for (uint32_t probe = 0; probe <= t.mask && !done; ++probe) {
+      uint64_t cur = t.slots[slot];
+      if (cur == kEmpty) {
+        cur = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + slot),
+                        static_cast<unsigned long long>(kEmpty),
+                        static_cast<unsigned long long>(entry));
+        if (cur == kEmpty) {
+          const unsigned int idx = atomicAdd(&t.ctr->n_unique, 1u);
+          if (idx < t.ucap) t.ulist[idx] = uint32_t(p);
+          else atomicOr(&t.ctr->overflow, 1u);
+          done = true;
+          break;
+        }
+      }
+      if (uint32_t(cur >> 32) == tag && rows_equal(keys + uint64_t(uint32_t(cur)) * w, kp, w)) {
+        done = true;
+        break;
+      }
+      slot = (slot + 1) & t.mask;
+    }
+    if (!done) atomicOr(&t.ctr->overflow, 1u);
+  }
+}
+
+__global__ void gather_word(const uint64_t* __restrict__ keys, int w, int j,
+                            const uint32_t* __restrict__ idx, const unsigned int* n_dev,
+                            uint32_t max_n, uint64_t* __restrict__ out) {
+  const uint32_t n = min(*n_dev, max_n);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = keys[uint64_t(idx[i]) * w + j];
+}
+
+__global__ void gather_rows(const uint64_t* __restrict__ keys, int w,
+                            const uint32_t* __restrict__ idx, const unsigned int* n_dev,
+                            uint32_t max_n, uint64_t* __restrict__ out) {
+  const uint64_t total = uint64_t(min(*n_dev, max_n)) * w;
+  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < total;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t r = t / w;
+    out[t] = keys[uint64_t(idx[r]) * w + (t - r * w)];
+  }
+}
+
+__global__ void rank_by_row(const uint32_t* __restrict__ idx, const unsigned int* n_dev,
+                            uint32_t max_n, uint32_t* __restrict__ rank) {
+  const uint32_t n = min(*n_dev, max_n);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    rank[idx[i]] = i;
+}
+
+__global__ void point_cell_wide(const uint64_t* __restrict__ keys, int64_t n, int w, WideTable t,
+                                const uint32_t* __restrict__ rank, uint32_t* point_cell) {
+  if (t.ctr->overflow) return;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const uint64_t* kp = keys + p * w;
+    const uint64_t h = hash_row(kp, w);
+    const uint32_t tag = uint32_t(h >> 32);
+    uint32_t slot = uint32_t(h) & t.mask;
+    int64_t found = -1;
+    for (uint32_t probe = 0; probe <= t.mask; ++probe) {
+      const uint64_t cur = t.slots[slot];
+      if (cur == kEmpty) break;
+      if (uint32_t(cur >> 32) == tag && rows_equal(keys + uint64_t(uint32_t(cur)) * w, kp, w)) {
+        found = uint32_t(cur);
+        break;
+      }
+      slot = (slot + 1) & t.mask;
+    }
+    if (found < 0) atomicOr(&t.ctr->error, 16u);
+    point_cell[p] = found < 0 ? 0xffffffffu : rank[found];
+  }
+}
+
+// Per-block table of fp_bit(k) for k < l in shared memory.
+__device__ __forceinline__ void load_fp_bits(uint64_t* hbits, int ell) {
+  for (int k = threadIdx.x; k < ell; k += blockDim.x) hbits[k] = fp_bit(k);
+  __syncthreads();
+}
+
+// Fingerprint of every cell (warp per cell, lanes over words) and insertion
+// of (fingerprint tag, cell number) into the table.
+__global__ void __launch_bounds__(kThreads)
+    index_wide(const uint64_t* __restrict__ cells, int w, int ell, WideTable t,
+               uint64_t* __restrict__ fp) {
+  extern __shared__ uint64_t hbits[];
+  load_fp_bits(hbits, ell);
+  if (t.ctr->overflow) return;
+  const uint32_t u = t.ctr->n_unique;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < u; i += warps) {
+    uint64_t f = 0;
+    for (int j = lane; j < w; j += 32) {
+      uint64_t x = cells[uint64_t(i) * w + j] & valid_bits(j, w, ell);
+      while (x) {
+        const int b = __ffsll(static_cast<long long>(x)) - 1;
+        f ^= hbits[64 * j + b];
+        x &= x - 1;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f ^= __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) {
+      fp[i] = f;
+      const uint64_t entry = (f & 0xffffffff00000000ull) | uint64_t(i);
+      uint32_t slot = uint32_t(f) & t.mask;
+      bool placed = false;
+      for (uint32_t probe = 0; probe <= t.mask; ++probe) {
+        const unsigned long long old = atomicCAS(
+            reinterpret_cast<unsigned long long*>(t.slots + slot),
+            static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(entry));
+        if (old == kEmpty) {
+          placed = true;
+          break;
+        }
+        slot = (slot + 1) & t.mask;
+      }
+      if (!placed) atomicOr(&t.ctr->overflow, 1u);
+    }
+  }
+}
+
+// Does cells[j] equal cells[i] with bit k flipped?
+__device__ __forceinline__ bool is_flip(const uint64_t* cells, int w, uint32_t i, uint32_t j,
+                                        int k) {
+  const uint64_t* xi = cells + uint64_t(i) * w;
+  const uint64_t* xj = cells + uint64_t(j) * w;
+  for (int q = 0; q < w; ++q) {
+    const uint64_t want = xi[q] ^ (q == (k >> 6) ? (1ull << (k & 63)) : 0ull);
+    if (xj[q] != want) return false;
+  }
+  return true;
+}
+
+struct WideHash {
+  const uint64_t* cells;
+  const uint64_t* fp;
+  const uint64_t* slots;
+  uint32_t mask;
+  int w;
+  __device__ __forceinline__ int64_t find(uint32_t i, int k, const uint64_t* hbits) const {
+    const uint64_t f = fp[i] ^ hbits[k];
+    const uint32_t tag = uint32_t(f >> 32);
+    uint32_t slot = uint32_t(f) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+      const uint64_t cur = slots[slot];
+      if (cur == kEmpty) return -1;
+      if (uint32_t(cur >> 32) == tag && is_flip(cells, w, i, uint32_t(cur), k))
+        return uint32_t(cur);
+      slot = (slot + 1) & mask;
+    }
+    return -1;
+  }
+};
+
+struct WideSorted {
+  const uint64_t* cells;
+  const DevCounters* ctr;
+  int w;
+  // Three-way compare of cells[m] with (cells[i] xor e_k), most significant word first.
+  __device__ __forceinline__ int cmp(uint32_t m, uint32_t i, int k) const {
+    const uint64_t* xm = cells + uint64_t(m) * w;
+    const uint64_t* xi = cells + uint64_t(i) * w;
+    for (int q = w - 1; q >= 0; --q) {
+      const uint64_t t = xi[q] ^ (q == (k >> 6) ? (1ull << (k & 63)) : 0ull);
+      if (xm[q] != t) return xm[q] < t ? -1 : 1;
+    }
+    return 0;
+  }
+  __device__ __forceinline__ int64_t find(uint32_t i, int k, const uint64_t*) const {
+    uint32_t lo = 0, hi = ctr->n_unique;
+    while (lo < hi) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      if (cmp(mid, i, k) < 0) lo = mid + 1;
+      else hi = mid;
+    }
+    return (lo < ctr->n_unique && cmp(lo, i, k) == 0) ? int64_t(lo) : -1;
+  }
+};
+
+template <class L>
+__global__ void __launch_bounds__(kThreads)
+    neighbors_wide(const uint64_t* __restrict__ cells, int w, int ell, L look,
+                   const DevCounters* ctr, uint32_t* __restrict__ masks,
+                   uint32_t* __restrict__ counts) {
+  extern __shared__ uint64_t hbits[];
+  load_fp_bits(hbits, ell);
+  if (ctr->overflow) return;
+  const uint32_t u = ctr->n_unique;
+  const int nh = (ell + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < u; i += warps) {
+    uint32_t total = 0;
+    for (int h = 0; h < nh; ++h) {
+      const int k = h * 32 + lane;
+      const uint64_t xw = cells[uint64_t(i) * w + (h >> 1)];
+      bool hit = false;
+      if (k < ell && !((xw >> (k & 63)) & 1ull)) hit = look.find(i, k, hbits) >= 0;
+      const uint32_t m = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) masks[uint64_t(i) * nh + h] = m;
+      total += __popc(m);
+    }
+    if (lane == 0) counts[i] = total;
+  }
+}
+
+template <class L>
+__global__ void __launch_bounds__(kThreads)
+    emit_wide(const uint64_t* __restrict__ cells, int w, int ell, L look, DevCounters* ctr,
+              const uint32_t* __restrict__ masks, const unsigned long long* __restrict__ offsets,
+              uint32_t* __restrict__ edges, int64_t cap) {
+  extern __shared__ uint64_t hbits[];
+  load_fp_bits(hbits, ell);
+  if (ctr->overflow) return;
+  const uint32_t u = ctr->n_unique;
+  const int nh = (ell + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < u; i += warps) {
+    unsigned long long off = offsets[i];
+    for (int h = 0; h < nh; ++h) {
+      const uint32_t m = masks[uint64_t(i) * nh + h];
+      if ((m >> lane) & 1u) {
+        const int k = h * 32 + lane;
+        const int64_t j = look.find(i, k, hbits);
+        if (j < 0) atomicOr(&ctr->error, 32u);
+        const unsigned long long r = off + __popc(m & lanemask_lt());
+        if (r < (unsigned long long)cap) {
+          edges[2 * r] = i;
+          edges[2 * r + 1] = uint32_t(j);
+        }
+      }
+      off += __popc(m);
+    }
+  }
+}
+
+template <class F>
+cudaError_t finish(F) {
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ------------------------------- launchers -------------------------------
+
+cudaError_t launch_fill_u64(uint64_t* p, uint64_t v, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  fill_u64<<<grid_for(n, kThreads * 4, 16), kThreads, 0, s>>>(p, v, n);
+  return finish(0);
+}
+
+cudaError_t launch_zero_counters(DevCounters* c, cudaStream_t s) {
+  zero_counters<<<1, 32, 0, s>>>(c);
+  return finish(0);
+}
+
+cudaError_t launch_keys_to_u64(const void* keys, int64_t n, int word_bits, int ell, uint64_t* out,
+                               cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int w64 = (ell + 63) / 64;
+  const int wc = (ell + word_bits - 1) / word_bits;
+  keys_to_u64<<<grid_for(size_t(n) * w64, kThreads), kThreads, 0, s>>>(keys, n, word_bits, wc,
+                                                                          w64, ell, out);
+  return finish(0);
+}
+
+cudaError_t launch_load_cells(const void* cells, int64_t n, int word_bits, int ell, uint64_t* out,
+                              DevCounters* ctr, cudaStream_t s) {
+  const int w64 = (ell + 63) / 64;
+  const int wc = (ell + word_bits - 1) / word_bits;
+  load_cells<<<grid_for(size_t(n) * w64 + 1, kThreads), kThreads, 0, s>>>(
+      cells, n, word_bits, wc, w64, ell, out, ctr);
+  return finish(0);
+}
+
+cudaError_t launch_write_cells(const uint64_t* cells, int ell, int word_bits, void* out,
+                               int64_t cap, const DevCounters* ctr, size_t max_n, cudaStream_t s) {
+  if (max_n == 0 || cap == 0) return cudaSuccess;
+  const int w64 = (ell + 63) / 64;
+  const int wc = (ell + word_bits - 1) / word_bits;
+  write_cells<<<grid_for(max_n * wc, kThreads), kThreads, 0, s>>>(cells, w64, word_bits, wc, out,
+                                                                   cap, ctr);
+  return finish(0);
+}
+
+cudaError_t launch_insert_small(const void* keys, int64_t n, int word_bits, int ell,
+                                const SmallTable& t, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int wc = (ell + word_bits - 1) / word_bits;
+  insert_small<<<grid_for(size_t(n), kThreads), kThreads, 0, s>>>(keys, n, word_bits, wc, t);
+  return finish(0);
+}
+
+cudaError_t launch_rank_small(const uint64_t* cells, const SmallTable& t, size_t max_n,
+                              cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  rank_small<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(cells, t);
+  return finish(0);
+}
+
+cudaError_t launch_index_small(const uint64_t* cells, const SmallTable& t, size_t max_n,
+                               cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  index_small<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(cells, t);
+  return finish(0);
+}
+
+cudaError_t launch_point_cell_small(const void* keys, int64_t n, int word_bits, int ell,
+                                    const SmallTable& t, uint32_t* point_cell, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int wc = (ell + word_bits - 1) / word_bits;
+  point_cell_small<<<grid_for(size_t(n), kThreads), kThreads, 0, s>>>(keys, n, word_bits, wc, t,
+                                                                      point_cell);
+  return finish(0);
+}
+
+cudaError_t launch_neighbors_small(const uint64_t* cells, const SmallTable& t, int ell,
+                                   int strategy, uint32_t* masks, uint32_t* counts, size_t max_n,
+                                   cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const int g = grid_for(max_n, kThreads / 32);
+  if (strategy == 2) {
+    neighbors_small<<<g, kThreads, 0, s>>>(cells, SmallSorted{cells, t.ctr}, t.ctr, ell, masks,
+                                           counts);
+  } else {
+    neighbors_small<<<g, kThreads, 0, s>>>(cells, SmallHash{t.keys, t.vals, t.mask, t.ctr}, t.ctr,
+                                           ell, masks, counts);
+  }
+  return finish(0);
+}
+
+cudaError_t launch_emit_small(const uint64_t* cells, const SmallTable& t, int ell, int strategy,
+                              const uint32_t* masks, const unsigned long long* offsets,
+                              uint32_t* edges, int64_t edges_cap, size_t max_n, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const int g = grid_for(max_n, kThreads / 32);
+  if (strategy == 2) {
+    emit_small<<<g, kThreads, 0, s>>>(cells, SmallSorted{cells, t.ctr}, t.ctr, ell, masks,
+                                      offsets, edges, edges_cap);
+  } else {
+    emit_small<<<g, kThreads, 0, s>>>(cells, SmallHash{t.keys, t.vals, t.mask, t.ctr}, t.ctr, ell,
+                                      masks, offsets, edges, edges_cap);
+  }
+  return finish(0);
+}
+
+cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const WideTable& t,
+                               cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  insert_wide<<<grid_for(size_t(n), kThreads), kThreads, 0, s>>>(keys, n, w64, t);
+  return finish(0);
+}
+
+cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
+                      uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
+                      void* scratch, cudaStream_t s, uint32_t** sorted_idx) {
+  uint32_t* cur = idx0;
+  uint32_t* other = idx1;
+  *sorted_idx = cur;
+  if (max_n == 0) return cudaSuccess;
+  for (int j = 0; j < w64; ++j) {
+    const int bits = (j == w64 - 1) ? ell - 64 * (w64 - 1) : 64;
+    gather_word<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(keys, w64, j, cur, n_dev,
+                                                               uint32_t(max_n), kw0);
+    count_launch();
+    bool in1 = false;
+    cudaError_t e = radix_sort_u64(kw0, kw1, cur, other, n_dev, max_n, bits, scratch, s, &in1);
+    if (e != cudaSuccess) return e;
+    if (in1) std::swap(cur, other);
+  }
+  *sorted_idx = cur;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,
+                               const unsigned int* n_dev, size_t max_n, uint64_t* out,
+                               cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  gather_rows<<<grid_for(max_n * w64, kThreads), kThreads, 0, s>>>(keys, w64, idx, n_dev,
+                                                                    uint32_t(max_n), out);
+  return finish(0);
+}
+
+cudaError_t launch_rank_by_row(const uint32_t* idx, const unsigned int* n_dev, size_t max_n,
+                               uint32_t* rank, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  rank_by_row<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(idx, n_dev, uint32_t(max_n), rank);
+  return finish(0);
+}
+
+cudaError_t launch_point_cell_wide(const uint64_t* keys, int64_t n, int w64, const WideTable& t,
+                                   const uint32_t* rank, uint32_t* point_cell, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  point_cell_wide<<<grid_for(size_t(n), kThreads), kThreads, 0, s>>>(keys, n, w64, t, rank,
+                                                                     point_cell);
+  return finish(0);
+}
+
+static size_t hbits_bytes(int ell) { return size_t(ell) * sizeof(uint64_t); }
+
+static cudaError_t allow_smem(const void* kern, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
+cudaError_t launch_index_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,
+                              uint64_t* fp, size_t max_n, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const size_t smem = hbits_bytes(ell);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(index_wide), smem);
+  if (e != cudaSuccess) return e;
+  index_wide<<<grid_for(max_n, kThreads / 32), kThreads, smem, s>>>(cells, w64, ell, t, fp);
+  return finish(0);
+}
+
+cudaError_t launch_neighbors_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,
+                                  const uint64_t* fp, int strategy, uint32_t* masks,
+                                  uint32_t* counts, size_t max_n, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const size_t smem = hbits_bytes(ell);
+  const int g = grid_for(max_n, kThreads / 32);
+  cudaError_t e;
+  if (strategy == 2) {
+    auto k = neighbors_wide<WideSorted>;
+    if ((e = allow_smem(reinterpret_cast<const void*>(k), smem)) != cudaSuccess) return e;
+    k<<<g, kThreads, smem, s>>>(cells, w64, ell, WideSorted{cells, t.ctr, w64}, t.ctr, masks,
+                                counts);
+  } else {
+    auto k = neighbors_wide<WideHash>;
+    if ((e = allow_smem(reinterpret_cast<const void*>(k), smem)) != cudaSuccess) return e;
+    k<<<g, kThreads, smem, s>>>(cells, w64, ell, WideHash{cells, fp, t.slots, t.mask, w64}, t.ctr,
+                                masks, counts);
+  }
+  return finish(0);
+}
+
+cudaError_t launch_emit_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,
+                             const uint64_t* fp, int strategy, const uint32_t* masks,
+                             const unsigned long long* offsets, uint32_t* edges,
+                             int64_t edges_cap, size_t max_n, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const size_t smem = hbits_bytes(ell);
+  const int g = grid_for(max_n, kThreads / 32);
+  cudaError_t e;
+  if (strategy == 2) {
+    auto k = emit_wide<WideSorted>;
+    if ((e = allow_smem(reinterpret_cast<const void*>(k), smem)) != cudaSuccess) return e;
+    k<<<g, kThreads, smem, s>>>(cells, w64, ell, WideSorted{cells, t.ctr, w64}, t.ctr, masks,
+                                offsets, edges, edges_cap);
+  } else {
+    auto k = emit_wide<WideHash>;
+    if ((e = allow_smem(reinterpret_cast<const void*>(k), smem)) != cudaSuccess) return e;
+    k<<<g, kThreads, smem, s>>>(cells, w64, ell, WideHash{cells, fp, t.slots, t.mask, w64}, t.ctr,
+                                masks, offsets, edges, edges_cap);
+  }
+  return finish(0);
+}
+
+}  // namespace cg

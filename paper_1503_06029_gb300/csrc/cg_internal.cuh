@@ -1,0 +1,227 @@
+// Internal declarations shared by the CUDA translation units of libcellgraph.
+// Nothing here is part of the C-ABI (include/cellgraph.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <utility>
+#include <algorithm>
+
+namespace cg {
+
+// Empty slot marker of the open-addressing tables. For vectors of l <= 64
+// bits the table stores the vector itself, so the all-ones vector (possible
+// only when l == 64) is tracked by a flag in DevCounters instead of a slot.
+constexpr uint64_t kEmpty = ~0ull;
+
+// Device-resident counters of one build. Zeroed by the first kernel of a build.
+struct DevCounters {
+  unsigned int n_unique;      // U: distinct vectors inserted
+  unsigned int overflow;      // a table or list ran past its capacity
+  unsigned long long n_edges; // E
+  unsigned int ones_present;  // the all-ones vector (l == 64) is a cell
+  unsigned int ones_rank;     // its cell number
+  unsigned int error;         // device-side consistency failures (bit set)
+  unsigned int pad[9];
+};
+static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
+
+// ---------------------------------------------------------------------------
+// Hashing (device). mix64 is the 64-bit finaliser of MurmurHash3 (Appleby,
+// public domain); splitmix64 is the output function of SplitMix64 (Steele, Lea,
+// Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Random 64-bit value attached to bit k; the fingerprint of a vector is the XOR
+// of the values of its set bits, so flipping bit k XORs the fingerprint with
+// fp_bit(k) (a GF(2)-linear hash).
+__host__ __device__ __forceinline__ uint64_t fp_bit(int k) {
+  return splitmix64(0x5eed0c0ffee00000ull + uint64_t(k));
+}
+
+// ---------------------------------------------------------------------------
+// Launch bookkeeping (cg_api.cu).
+// ---------------------------------------------------------------------------
+void count_launch(int n = 1);
+int sm_count();  // SMs of the current device (cached per device)
+
+// ---------------------------------------------------------------------------
+// Step 1: sign vectors (cg_pack.cu).
+// ---------------------------------------------------------------------------
+struct PackArgs {
+  const int32_t* pts;
+  int64_t n;
+  int d;
+  const int32_t* a;
+  const int64_t* b;
+  int ell;
+};
+
+// keys[n][W] in word_bits-bit words.
+cudaError_t launch_pack_store(const PackArgs& pa, int word_bits, void* keys, cudaStream_t s);
+
+// Fused steps 1-2 for l <= 64: every vector goes straight into the table
+// (no vector is written to memory); distinct vectors are appended to ulist.
+struct SmallTable {
+  uint64_t* keys;      // [cap], kEmpty = free
+  uint32_t* vals;      // [cap], cell number of the key in the same slot
+  uint32_t mask;       // cap - 1 (cap a power of two)
+  uint64_t* ulist;     // [ucap] distinct vectors, in insertion order
+  uint32_t ucap;
+  DevCounters* ctr;
+};
+cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStream_t s);
+
+
+// ---------------------------------------------------------------------------
+// Device helpers used by several translation units.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+// Appends a newly inserted distinct vector to the table's list.
+__device__ __forceinline__ void small_append(const SmallTable& t, uint64_t key) {
+  const unsigned int idx = atomicAdd(&t.ctr->n_unique, 1u);
+  if (idx < t.ucap) {
+    t.ulist[idx] = key;
+  } else {
+    atomicOr(&t.ctr->overflow, 1u);
+  }
+}
+
+// Inserts one vector (l <= 64) into the dedup table; the first inserter of a
+// value appends it to the list of cells (§3.2: duplicates are removed).
+// Linear probing; a table that is full raises the overflow flag.
+__device__ __forceinline__ void small_insert(const SmallTable& t, uint64_t key) {
+  if (key == kEmpty) {
+    if (atomicExch(&t.ctr->ones_present, 1u) == 0u) small_append(t, key);
+    return;
+  }
+  uint32_t slot = uint32_t(mix64(key)) & t.mask;
+  for (uint32_t probe = 0; probe <= t.mask; ++probe) {
+    const uint64_t cur = t.keys[slot];
+    if (cur == key) return;
+    if (cur == kEmpty) {
+      const unsigned long long old =
+          atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + slot),
+                    static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(key));
+      if (old == kEmpty) {
+        small_append(t, key);
+        return;
+      }
+      if (old == key) return;
+    }
+    slot = (slot + 1) & t.mask;
+  }
+  atomicOr(&t.ctr->overflow, 1u);
+}
+#endif
+
+// ---------------------------------------------------------------------------
+// Sorting and scanning (cg_sort.cu). Counts are read from device memory so
+// that no host synchronisation is needed between steps.
+// ---------------------------------------------------------------------------
+// Scratch sizes (bytes) for up to `max_n` items.
+size_t radix_scratch_bytes(size_t max_n);
+size_t scan_scratch_bytes(size_t max_n);
+
+// Stable LSD radix sort of keys (with optional uint32 payload) by bits
+// [0, bits) of the keys, 8 bits per pass. Items: *n_dev (device). Buffers
+// keys0/keys1 (and vals0/vals1) alternate; *result_in_1 tells where the sorted
+// data ends up (host-known: depends only on the pass count).
+cudaError_t radix_sort_u64(uint64_t* keys0, uint64_t* keys1, uint32_t* vals0, uint32_t* vals1,
+                           const unsigned int* n_dev, size_t max_n, int bits, void* scratch,
+                           cudaStream_t s, bool* result_in_1);
+
+// out[i] = sum_{j<i} in[j] for i < *n_dev; *total = sum of all (device).
+cudaError_t scan_exclusive_u32(const uint32_t* in, unsigned long long* out,
+                               const unsigned int* n_dev, size_t max_n,
+                               unsigned long long* total, void* scratch, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Cells and edges (cg_graph.cu).
+// ---------------------------------------------------------------------------
+cudaError_t launch_fill_u64(uint64_t* p, uint64_t v, size_t n, cudaStream_t s);
+cudaError_t launch_zero_counters(DevCounters* c, cudaStream_t s);
+
+// Insert stored vectors (l <= 64) into a SmallTable (dedup).
+cudaError_t launch_insert_small(const void* keys, int64_t n, int word_bits, int ell,
+                                const SmallTable& t, cudaStream_t s);
+// vals[slot(cells[i])] = i for i < U; also records the all-ones cell.
+cudaError_t launch_rank_small(const uint64_t* cells, const SmallTable& t, size_t max_n,
+                              cudaStream_t s);
+// Insert already-unique cells (internal rows, count ctr->n_unique) with their
+// numbers; a repeated cell sets ctr->error.
+cudaError_t launch_index_small(const uint64_t* cells, const SmallTable& t, size_t max_n,
+                               cudaStream_t s);
+// point_cell[p] = cell number of keys[p].
+cudaError_t launch_point_cell_small(const void* keys, int64_t n, int word_bits, int ell,
+                                    const SmallTable& t, uint32_t* point_cell, cudaStream_t s);
+// Copy U cells (u64, internal) to the caller's layout when U <= cap.
+cudaError_t launch_write_cells(const uint64_t* cells, int ell, int word_bits, void* out,
+                               int64_t cap, const DevCounters* ctr, size_t max_n, cudaStream_t s);
+// Load caller-layout cells into internal u64 rows; sets ctr->n_unique = n.
+cudaError_t launch_load_cells(const void* cells, int64_t n, int word_bits, int ell,
+                              uint64_t* out, DevCounters* ctr, cudaStream_t s);
+
+// Neighbour search. masks: [U][ceil(l/32)] hit bits; counts: [U].
+cudaError_t launch_neighbors_small(const uint64_t* cells, const SmallTable& t, int ell,
+                                   int strategy, uint32_t* masks, uint32_t* counts,
+                                   size_t max_n, cudaStream_t s);
+cudaError_t launch_emit_small(const uint64_t* cells, const SmallTable& t, int ell, int strategy,
+                              const uint32_t* masks, const unsigned long long* offsets,
+                              uint32_t* edges, int64_t edges_cap, size_t max_n, cudaStream_t s);
+
+// Vectors of l > 64 bits (W = ceil(l/64) words).
+struct WideTable {
+  uint64_t* slots;  // [cap]: (tag << 32) | index, kEmpty = free
+  uint32_t mask;
+  uint32_t* ulist;  // [ucap] representative input rows, insertion order
+  uint32_t ucap;
+  DevCounters* ctr;
+};
+cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const WideTable& t,
+                               cudaStream_t s);
+// Sort representatives by value: idx0/idx1 permuted, kw0/kw1 word scratch.
+cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
+                      uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
+                      void* scratch, cudaStream_t s, uint32_t** sorted_idx);
+cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,
+                               const unsigned int* n_dev, size_t max_n, uint64_t* out,
+                               cudaStream_t s);
+cudaError_t launch_rank_by_row(const uint32_t* idx, const unsigned int* n_dev, size_t max_n,
+                               uint32_t* rank_by_row, cudaStream_t s);
+cudaError_t launch_point_cell_wide(const uint64_t* keys, int64_t n, int w64, const WideTable& t,
+                                   const uint32_t* rank_by_row, uint32_t* point_cell,
+                                   cudaStream_t s);
+// Fingerprint table over sorted cells: fp[i] and slots (tag, i).
+cudaError_t launch_index_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,
+                              uint64_t* fp, size_t max_n, cudaStream_t s);
+cudaError_t launch_neighbors_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,
+                                  const uint64_t* fp, int strategy, uint32_t* masks,
+                                  uint32_t* counts, size_t max_n, cudaStream_t s);
+cudaError_t launch_emit_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,
+                             const uint64_t* fp, int strategy, const uint32_t* masks,
+                             const unsigned long long* offsets, uint32_t* edges,
+                             int64_t edges_cap, size_t max_n, cudaStream_t s);
+
+// Convert caller-layout keys ([n][W] of word_bits) to internal u64 rows.
+cudaError_t launch_keys_to_u64(const void* keys, int64_t n, int word_bits, int ell,
+                               uint64_t* out, cudaStream_t s);
+
+}  // namespace cg

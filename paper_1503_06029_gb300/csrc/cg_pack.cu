@@ -1,0 +1,324 @@
+// Step 1 of the cell-graph construction: sign vectors (§2.1, Figure 1).
+//
+// Bit i of point p's vector is [a_i . p >= b_i]. The test is exact for every
+// int32 point/normal and int64 offset. The kernel decides almost every bit with
+// d packed fp32 FMAs (fma.rn.f32x2, two points per instruction) and falls back
+// to 128-bit integer arithmetic only where the fp32 value is too close to zero
+// for its rounding error bound to fix the sign:
+//
+//   With u = 2^-24, rounded inputs a^ = fl(a_k), p^ = fl(p_k), c^ = fl(-b) and
+//   the chain t = fma(a^_{d-1}, p^_{d-1}, ... fma(a^_0, p^_0, c^)), the error
+//   |t - (a.p - b)| is at most (gamma_d (1+u)^2 + 2u + u^2) T with
+//   T = sum_k |a_k||p_k| + |b| and gamma_d = d u / (1 - d u) (standard
+//   floating-point error analysis of an FMA dot product, e.g. Higham,
+//   "Accuracy and Stability of Numerical Algorithms", ch. 3). For d <= 4 this is
+//   below E = (d + 4) u T.
+//
+// T is bounded per tile of points from the tile's largest |p_k| (rounded
+// upwards). Each constraint row is then scaled by 2^-e, the power of two with
+// E 2^-e < 1; the scaling is exact, so |t'| >= 2 proves the sign. |t'| >= 2 is
+// exactly "bit 30 of the float is set", which lets one LOP3 accumulate the
+// certainty test of two results; a thread whose accumulated bit 30 is clear
+// re-evaluates the uncertain bits of that 32-constraint chunk exactly.
+//
+// Bits are collected with a funnel shift of the float sign bit (constraints are
+// visited from the highest to the lowest index of the chunk), which yields the
+// complement of the vector; padding constraints (i >= l) evaluate to -4 and so
+// produce 0 bits.
+#include "cg_internal.cuh"
+
+namespace cg {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPts = 4;  // points per thread: two f32x2 pairs
+constexpr int kTilePts = kThreads * kPts;
+
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  return uint64_t(__float_as_uint(lo)) | (uint64_t(__float_as_uint(hi)) << 32);
+}
+
+__device__ __forceinline__ uint32_t uabs32(int32_t v) {
+  return v < 0 ? 0u - uint32_t(v) : uint32_t(v);
+}
+__device__ __forceinline__ uint64_t uabs64(int64_t v) {
+  return v < 0 ? 0ull - uint64_t(v) : uint64_t(v);
+}
+
+// Exact [a_row . p >= b] with 128-bit accumulation.
+template <int D>
+__device__ __forceinline__ bool exact_ge(const int32_t* __restrict__ a_row, int64_t b,
+                                         const int32_t (&p)[D]) {
+  __int128 s = -static_cast<__int128>(b);
+#pragma unroll
+  for (int k = 0; k < D; ++k) s += static_cast<__int128>(int64_t(a_row[k]) * int64_t(p[k]));
+  return s >= 0;
+}
+
+// Per-constraint scaled coefficients, duplicated for f32x2:
+// [a0 a0 a1 a1 ... a_{D-1} a_{D-1} c c] padded to whole float4s.
+template <int D>
+struct Coef {
+  static constexpr int kFloats = 2 * (D + 1);
+  static constexpr int kQuads = (kFloats + 3) / 4;
+};
+
+// Writes constraint t's coefficients for a tile whose |p_k| <= M[k].
+template <int D>
+__device__ void build_coef(const PackArgs& pa, int t, const uint32_t (&M)[D], float4* dst) {
+  float v[Coef<D>::kQuads * 4];
+#pragma unroll
+  for (int q = 0; q < Coef<D>::kQuads * 4; ++q) v[q] = 0.0f;
+  float c;
+  if (t >= pa.ell) {
+    c = -4.0f;  // padding: certain, negative, bit 0
+  } else {
+    const int32_t* ar = pa.a + int64_t(t) * D;
+    const int64_t bt = pa.b[t];
+    float T = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      T = __fmaf_ru(__uint2float_ru(uabs32(ar[k])), __uint2float_ru(M[k]), T);
+    T = __fadd_ru(T, __ull2float_ru(uabs64(bt)));
+    if (T == 0.0f) {
+      c = 4.0f;  // every point of the tile gives a . p - b == 0 exactly: bit 1
+    } else {
+      const float E = __fmul_ru(T, float(D + 4) * 0x1p-24f);
+      int e;
+      frexpf(E, &e);  // E = m 2^e, 0.5 <= m < 1, so E 2^-e < 1
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float ak = ldexpf(__int2float_rn(ar[k]), -e);
+        v[2 * k] = ak;
+        v[2 * k + 1] = ak;
+      }
+      c = ldexpf(-__ll2float_rn(bt), -e);
+    }
+  }
+  v[2 * D] = c;
+  v[2 * D + 1] = c;
+#pragma unroll
+  for (int q = 0; q < Coef<D>::kQuads; ++q)
+    dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// Writes the words of each point to keys[n][W] (word_bits 32 or 64).
+struct StoreSink {
+  void* keys;
+  int word_bits;
+  int w;  // words per vector in word_bits units
+  __device__ void word(int64_t p, int chunk, uint32_t bits, uint32_t& lo_stash, bool last) const {
+    if (word_bits == 32) {
+      static_cast<uint32_t*>(keys)[p * w + chunk] = bits;
+    } else if ((chunk & 1) == 0 && !last) {
+      lo_stash = bits;
+    } else {
+      const uint64_t v = (chunk & 1) ? (uint64_t(lo_stash) | (uint64_t(bits) << 32)) : bits;
+      static_cast<uint64_t*>(keys)[p * w + (chunk >> 1)] = v;
+    }
+  }
+  __device__ void done(int64_t, uint64_t) const {}
+  static constexpr bool kKeepKey = false;
+};
+
+// Inserts each l <= 64 vector into the dedup table (§3.2: duplicates removed).
+struct InsertSink {
+  SmallTable t;
+  __device__ void word(int64_t, int, uint32_t, uint32_t&, bool) const {}
+  __device__ void done(int64_t, uint64_t key) const;
+  static constexpr bool kKeepKey = true;
+};
+
+}  // namespace
+
+namespace {
+
+__device__ void InsertSink::done(int64_t, uint64_t key) const { small_insert(t, key); }
+
+template <int D, class Sink>
+__global__ void __launch_bounds__(kThreads)
+    pack_kernel(PackArgs pa, Sink sink, int n_chunks, int vec_ok) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kQ = Coef<D>::kQuads;
+  float4* coef = reinterpret_cast<float4*>(smem_raw);
+  uint32_t* wmax = reinterpret_cast<uint32_t*>(coef + size_t(n_chunks) * 32 * kQ);  // [8][D]
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t n = pa.n;
+  const int64_t n_tiles = (n + kTilePts - 1) / kTilePts;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t p0 = tile * kTilePts + int64_t(threadIdx.x) * kPts;
+    int32_t pi[kPts][D];
+    if (vec_ok && p0 + kPts <= n) {
+      // kPts * D int32 = D int4, 16-byte aligned (p0 * D * 4 is a multiple of 16).
+      const int4* src = reinterpret_cast<const int4*>(pa.pts + p0 * D);
+      int32_t tmp[kPts * D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const int4 v = __ldg(src + q);
+        tmp[4 * q] = v.x;
+        tmp[4 * q + 1] = v.y;
+        tmp[4 * q + 2] = v.z;
+        tmp[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int q = 0; q < kPts; ++q)
+#pragma unroll
+        for (int k = 0; k < D; ++k) pi[q][k] = tmp[q * D + k];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kPts; ++q)
+#pragma unroll
+        for (int k = 0; k < D; ++k) pi[q][k] = (p0 + q < n) ? __ldg(pa.pts + (p0 + q) * D + k) : 0;
+    }
+
+    // Largest |p_k| of the tile, per coordinate.
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      uint32_t m = 0;
+#pragma unroll
+      for (int q = 0; q < kPts; ++q) m = max(m, uabs32(pi[q][k]));
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (lane == 0) wmax[warp * D + k] = m;
+    }
+    __syncthreads();  // also: every thread is done with the previous tile's coef
+    {
+      uint32_t M[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        uint32_t m = 0;
+        for (int w = 0; w < kThreads / 32; ++w) m = max(m, wmax[w * D + k]);
+        M[k] = m;
+      }
+      for (int t = threadIdx.x; t < n_chunks * 32; t += kThreads)
+        build_coef<D>(pa, t, M, coef + size_t(t) * kQ);
+    }
+    __syncthreads();
+
+    uint64_t X[kPts / 2][D];
+#pragma unroll
+    for (int h = 0; h < kPts / 2; ++h)
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        X[h][k] = pack2(__int2float_rn(pi[2 * h][k]), __int2float_rn(pi[2 * h + 1][k]));
+
+    uint32_t stash[kPts] = {0, 0, 0, 0};
+    uint64_t key[kPts] = {0, 0, 0, 0};
+    for (int chunk = 0; chunk < n_chunks; ++chunk) {
+      uint32_t w[kPts] = {0, 0, 0, 0};
+      uint32_t cert = 0xffffffffu;
+      const float4* cc = coef + size_t(chunk) * 32 * kQ;
+#pragma unroll 8
+      for (int j = 31; j >= 0; --j) {
+        float4 q4[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) q4[q] = cc[j * kQ + q];
+        const float* f = reinterpret_cast<const float*>(q4);
+        uint64_t A[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) A[k] = pack2(f[2 * k], f[2 * k + 1]);
+        const uint64_t C = pack2(f[2 * D], f[2 * D + 1]);
+#pragma unroll
+        for (int h = 0; h < kPts / 2; ++h) {
+          uint64_t acc = C;
+#pragma unroll
+          for (int k = 0; k < D; ++k) acc = ffma2(A[k], X[h][k], acc);
+          const uint32_t lo = uint32_t(acc);
+          const uint32_t hi = uint32_t(acc >> 32);
+          w[2 * h] = __funnelshift_l(lo, w[2 * h], 1);
+          w[2 * h + 1] = __funnelshift_l(hi, w[2 * h + 1], 1);
+          cert &= lo & hi;
+        }
+      }
+      if (!(cert & 0x40000000u)) {
+        // Some |t'| < 2 in this chunk: settle those bits exactly.
+        for (int q = 0; q < kPts; ++q) {
+          if (p0 + q >= n) continue;
+          for (int j = 0; j < 32; ++j) {
+            const int t = chunk * 32 + j;
+            if (t >= pa.ell) break;
+            const float* f = reinterpret_cast<const float*>(cc + j * kQ);
+            float acc = f[2 * D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc = fmaf(f[2 * k], __int2float_rn(pi[q][k]), acc);
+            if (fabsf(acc) < 2.0f) {
+              const bool ge = exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], pi[q]);
+              w[q] = ge ? (w[q] & ~(1u << j)) : (w[q] | (1u << j));
+            }
+          }
+        }
+      }
+      const bool last = chunk == n_chunks - 1;
+#pragma unroll
+      for (int q = 0; q < kPts; ++q) {
+        const uint32_t bits = ~w[q];
+        if (Sink::kKeepKey) {
+          if (chunk == 0) key[q] = bits;
+          else key[q] |= uint64_t(bits) << 32;
+        } else if (p0 + q < n) {
+          sink.word(p0 + q, chunk, bits, stash[q], last);
+        }
+      }
+    }
+    if (Sink::kKeepKey) {
+#pragma unroll
+      for (int q = 0; q < kPts; ++q)
+        if (p0 + q < n) sink.done(p0 + q, key[q]);
+    }
+  }
+}
+
+template <int D, class Sink>
+cudaError_t launch_d(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
+  if (pa.n == 0) return cudaSuccess;
+  const int n_chunks = (pa.ell + 31) / 32;
+  const size_t smem = size_t(n_chunks) * 32 * Coef<D>::kQuads * sizeof(float4) +
+                      sizeof(uint32_t) * (kThreads / 32) * D;
+  auto kern = pack_kernel<D, Sink>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (err != cudaSuccess) return err;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const int64_t n_tiles = (pa.n + kTilePts - 1) / kTilePts;
+  const int64_t grid = std::min<int64_t>(n_tiles, int64_t(sm_count()) * per_sm);
+  const int vec_ok = (reinterpret_cast<uintptr_t>(pa.pts) % 16) == 0;
+  kern<<<unsigned(grid), kThreads, smem, s>>>(pa, sink, n_chunks, vec_ok);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <class Sink>
+cudaError_t launch_any(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
+  switch (pa.d) {
+    case 1: return launch_d<1>(pa, sink, s);
+    case 2: return launch_d<2>(pa, sink, s);
+    case 3: return launch_d<3>(pa, sink, s);
+    case 4: return launch_d<4>(pa, sink, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pack_store(const PackArgs& pa, int word_bits, void* keys, cudaStream_t s) {
+  StoreSink sink{keys, word_bits, (pa.ell + word_bits - 1) / word_bits};
+  return launch_any(pa, sink, s);
+}
+
+cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStream_t s) {
+  if (pa.ell > 64) return cudaErrorInvalidValue;
+  InsertSink sink{t};
+  return launch_any(pa, sink, s);
+}
+
+}  // namespace cg

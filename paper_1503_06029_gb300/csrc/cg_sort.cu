@@ -1,0 +1,321 @@
+// Sorting and scanning for step 2 (cells, §3.2: "sorting ... using the radix
+// sort algorithm") and step 4 (edge offsets).
+//
+// Stable LSD radix sort, 8-bit digits, one histogram kernel and one scatter
+// kernel per pass (plus a device-wide scan of the per-tile histograms when
+// there are more than kInlineTiles tiles). Item counts are read from device
+// memory, so a whole build can be enqueued without reading anything back.
+#include "cg_internal.cuh"
+
+namespace cg {
+namespace {
+
+constexpr int kRThreads = 256;
+constexpr int kRItems = 8;
+constexpr int kRTile = kRThreads * kRItems;  // 2048 items per tile
+constexpr int kInlineTiles = 64;             // scatter sums histograms itself below this
+constexpr int kSThreads = 256;
+constexpr int kSItems = 16;
+constexpr int kSTile = kSThreads * kSItems;  // 4096 items per scan block
+
+// Item count read from device memory: mul * ceil(min(*n, cap) / div).
+struct Count {
+  const unsigned int* n;
+  unsigned int mul;
+  unsigned int div;
+  uint64_t cap;  // the count never exceeds the buffers sized for it
+  __device__ __forceinline__ uint64_t get() const {
+    const uint64_t v = uint64_t(*n) < cap ? uint64_t(*n) : cap;
+    return uint64_t(mul) * ((v + div - 1) / div);
+  }
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Inclusive warp scan of 64-bit values.
+__device__ __forceinline__ unsigned long long warp_incl(unsigned long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan over the block (blockDim.x <= 1024); returns the exclusive
+// prefix of `v` and the block total through *total.
+__device__ unsigned long long block_excl(unsigned long long v, unsigned long long* total) {
+  __shared__ unsigned long long wsum[32];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  const unsigned long long inc = warp_incl(v);
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long s = lane < nw ? wsum[lane] : 0ull;
+    s = warp_incl(s);
+    if (lane < nw) wsum[lane] = s;
+  }
+  __syncthreads();
+  const unsigned long long before = warp > 0 ? wsum[warp - 1] : 0ull;
+  if (total) *total = wsum[nw - 1];
+  __syncthreads();
+  return before + inc - v;
+}
+
+// --------------------------------- scan ---------------------------------
+
+__global__ void __launch_bounds__(kSThreads)
+    scan_reduce(const uint32_t* __restrict__ in, Count cnt, unsigned long long* partial) {
+  const uint64_t n = cnt.get();
+  const uint64_t base = uint64_t(blockIdx.x) * kSTile;
+  if (base >= n) return;
+  unsigned long long s = 0;
+  for (int j = 0; j < kSItems; ++j) {
+    const uint64_t i = base + uint64_t(j) * kSThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  unsigned long long tot;
+  block_excl(s, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024)
+    scan_partials(unsigned long long* partial, Count cnt, unsigned long long* total) {
+  const uint64_t n = cnt.get();
+  const uint64_t nb = (n + kSTile - 1) / kSTile;
+  unsigned long long carry = 0;
+  for (uint64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    const uint64_t i = b0 + threadIdx.x;
+    const unsigned long long v = i < nb ? partial[i] : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl(v, &tot);
+    if (i < nb) partial[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(kSThreads)
+    scan_down(const uint32_t* __restrict__ in, Count cnt, const unsigned long long* partial,
+              unsigned long long* out) {
+  const uint64_t n = cnt.get();
+  const uint64_t base = uint64_t(blockIdx.x) * kSTile;
+  if (base >= n) return;
+  // Thread t owns items base + t*kSItems .. +kSItems-1 (consecutive).
+  uint32_t v[kSItems];
+  unsigned long long s = 0;
+  const uint64_t first = base + uint64_t(threadIdx.x) * kSItems;
+#pragma unroll
+  for (int j = 0; j < kSItems; ++j) {
+    v[j] = (first + j < n) ? in[first + j] : 0u;
+    s += v[j];
+  }
+  unsigned long long run = partial[blockIdx.x] + block_excl(s, nullptr);
+#pragma unroll
+  for (int j = 0; j < kSItems; ++j) {
+    if (first + j < n) out[first + j] = run;
+    run += v[j];
+  }
+}
+
+cudaError_t scan_impl(const uint32_t* in, unsigned long long* out, Count cnt, size_t max_n,
+                      unsigned long long* total, void* scratch, cudaStream_t s) {
+  const size_t nb = (max_n + kSTile - 1) / kSTile;
+  if (nb == 0) {
+    // Nothing can be scanned; still define the total.
+    scan_partials<<<1, 1024, 0, s>>>(static_cast<unsigned long long*>(scratch), cnt, total);
+    count_launch();
+    return cudaGetLastError();
+  }
+  auto* partial = static_cast<unsigned long long*>(scratch);
+  scan_reduce<<<unsigned(nb), kSThreads, 0, s>>>(in, cnt, partial);
+  scan_partials<<<1, 1024, 0, s>>>(partial, cnt, total);
+  scan_down<<<unsigned(nb), kSThreads, 0, s>>>(in, cnt, partial, out);
+  count_launch(3);
+  return cudaGetLastError();
+}
+
+// --------------------------------- radix ---------------------------------
+
+__global__ void __launch_bounds__(kRThreads)
+    radix_hist(const uint64_t* __restrict__ kin, const unsigned int* n_dev, uint32_t max_n,
+               int shift, uint32_t* hist) {
+  __shared__ uint32_t h[256];
+  const uint32_t n = min(*n_dev, max_n);
+  const uint32_t tiles = (n + kRTile - 1) / kRTile;
+  const uint32_t t = blockIdx.x;
+  if (t >= tiles) return;
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t base = uint64_t(t) * kRTile;
+#pragma unroll
+  for (int j = 0; j < kRItems; ++j) {
+    const uint64_t i = base + uint64_t(j) * kRThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(kin[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[uint64_t(threadIdx.x) * tiles + t] = h[threadIdx.x];
+}
+
+// Scatter of one pass. Items of a tile are read "warp-striped" (warp w owns a
+// contiguous run of 256 items, lane l the items w*256 + j*32 + l), and ranked
+// in that order, which is the input order: the sort is stable.
+template <bool kVals>
+__global__ void __launch_bounds__(kRThreads)
+    radix_scatter(const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout,
+                  const uint32_t* __restrict__ vin, uint32_t* __restrict__ vout,
+                  const unsigned int* n_dev, uint32_t max_n, int shift,
+                  const uint32_t* __restrict__ hist,
+                  const unsigned long long* __restrict__ scanned) {
+  __shared__ uint32_t wcnt[kRThreads / 32][256];
+  __shared__ uint32_t toff[256];
+  const uint32_t n = min(*n_dev, max_n);
+  const uint32_t tiles = (n + kRTile - 1) / kRTile;
+  const uint32_t t = blockIdx.x;
+  if (t >= tiles) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int d = threadIdx.x;
+
+  // Global offset of digit d for this tile.
+  if (scanned) {
+    toff[d] = uint32_t(scanned[uint64_t(d) * tiles + t]);
+  } else {
+    unsigned long long tot = 0, before = 0;
+    for (uint32_t u = 0; u < tiles; ++u) {
+      const uint32_t c = hist[uint64_t(d) * tiles + u];
+      if (u < t) before += c;
+      tot += c;
+    }
+    const unsigned long long dbase = block_excl(tot, nullptr);
+    toff[d] = uint32_t(dbase + before);
+  }
+#pragma unroll
+  for (int w = 0; w < kRThreads / 32; ++w) wcnt[w][d] = 0;
+  __syncthreads();
+
+  const uint64_t base = uint64_t(t) * kRTile + uint64_t(warp) * (kRItems * 32);
+  uint64_t key[kRItems];
+  uint32_t val[kRItems];
+  uint32_t loc[kRItems];
+  uint32_t dig[kRItems];
+#pragma unroll
+  for (int j = 0; j < kRItems; ++j) {
+    const uint64_t i = base + uint64_t(j) * 32 + lane;
+    const bool ok = i < n;
+    key[j] = ok ? kin[i] : 0ull;
+    if (kVals) val[j] = ok ? vin[i] : 0u;
+    const uint32_t dj = ok ? uint32_t((key[j] >> shift) & 255u) : 256u;
+    dig[j] = dj;
+    const uint32_t peers = __match_any_sync(0xffffffffu, dj);
+    const uint32_t rank = __popc(peers & lanemask_lt());
+    const int leader = __ffs(peers) - 1;
+    uint32_t b = 0;
+    if (ok) b = wcnt[warp][dj];
+    __syncwarp();
+    if (ok && lane == leader) wcnt[warp][dj] = b + __popc(peers);
+    __syncwarp();
+    loc[j] = b + rank;
+  }
+  __syncthreads();
+  {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kRThreads / 32; ++w) {
+      const uint32_t c = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kRItems; ++j) {
+    if (dig[j] < 256u) {
+      const uint32_t pos = toff[dig[j]] + wcnt[warp][dig[j]] + loc[j];
+      kout[pos] = key[j];
+      if (kVals) vout[pos] = val[j];
+    }
+  }
+}
+
+}  // namespace
+
+size_t scan_scratch_bytes(size_t max_n) {
+  return ((max_n + kSTile - 1) / kSTile + 1) * sizeof(unsigned long long);
+}
+
+size_t radix_scratch_bytes(size_t max_n) {
+  const size_t tiles = (max_n + kRTile - 1) / kRTile + 1;
+  size_t bytes = 256 * tiles * sizeof(uint32_t);
+  bytes = (bytes + 255) & ~size_t(255);
+  if (tiles > kInlineTiles) {
+    bytes += 256 * tiles * sizeof(unsigned long long);
+    bytes = (bytes + 255) & ~size_t(255);
+    bytes += scan_scratch_bytes(256 * tiles);
+  }
+  return bytes;
+}
+
+cudaError_t scan_exclusive_u32(const uint32_t* in, unsigned long long* out,
+                               const unsigned int* n_dev, size_t max_n,
+                               unsigned long long* total, void* scratch, cudaStream_t s) {
+  return scan_impl(in, out, Count{n_dev, 1, 1, max_n}, max_n, total, scratch, s);
+}
+
+cudaError_t radix_sort_u64(uint64_t* keys0, uint64_t* keys1, uint32_t* vals0, uint32_t* vals1,
+                           const unsigned int* n_dev, size_t max_n, int bits, void* scratch,
+                           cudaStream_t s, bool* result_in_1) {
+  const int passes = (bits + 7) / 8;
+  *result_in_1 = (passes & 1) != 0;
+  if (max_n == 0 || passes == 0) {
+    *result_in_1 = false;
+    return cudaSuccess;
+  }
+  const size_t tiles = (max_n + kRTile - 1) / kRTile;
+  char* sp = static_cast<char*>(scratch);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(sp);
+  size_t off = (256 * (tiles + 1) * sizeof(uint32_t) + 255) & ~size_t(255);
+  unsigned long long* scanned = nullptr;
+  void* scan_scratch = nullptr;
+  if (tiles > kInlineTiles) {
+    scanned = reinterpret_cast<unsigned long long*>(sp + off);
+    off += (256 * (tiles + 1) * sizeof(unsigned long long) + 255) & ~size_t(255);
+    scan_scratch = sp + off;
+  }
+  uint64_t* kin = keys0;
+  uint64_t* kout = keys1;
+  uint32_t* vin = vals0;
+  uint32_t* vout = vals1;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    radix_hist<<<unsigned(tiles), kRThreads, 0, s>>>(kin, n_dev, uint32_t(max_n), shift, hist);
+    count_launch();
+    if (scanned) {
+      cudaError_t e = scan_impl(hist, scanned, Count{n_dev, 256, kRTile, max_n}, 256 * tiles,
+                                nullptr, scan_scratch, s);
+      if (e != cudaSuccess) return e;
+    }
+    if (vals0) {
+      radix_scatter<true><<<unsigned(tiles), kRThreads, 0, s>>>(
+          kin, kout, vin, vout, n_dev, uint32_t(max_n), shift, hist, scanned);
+    } else {
+      radix_scatter<false><<<unsigned(tiles), kRThreads, 0, s>>>(
+          kin, kout, nullptr, nullptr, n_dev, uint32_t(max_n), shift, hist, scanned);
+    }
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace cg

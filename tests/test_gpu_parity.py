@@ -1,0 +1,380 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Everything here is integer and bit-level work, so the bar is bit-exact: packed
+vectors, cells (in value order) and edge lists (in lexicographic order) must be
+identical, element by element, to the oracle's on the same seeded inputs.
+
+Sizes span several tiles and ragged tails (the sign kernel's tile is 1024
+points, the radix tile 2048 items, the scan block 4096 items). The full-size
+cases run the workloads at the sizes the benchmark times: the whole 2^24-point
+3-D arrangement through the oracle, and the 5,242,880-vector chain workload
+through sampled rows plus properties that hold at any size.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_06029_gb300 import cellgraph, inputs
+from tests.helpers import as_u64_rows, popcount64, rows_to_ints
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ctx(dev):
+    c = cellgraph.Context(0)
+    yield c
+    c.close()
+
+
+def T(x, dev):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def words_np(t, word_bits):
+    return t.cpu().numpy().view(np.uint64 if word_bits == 64 else np.uint32)
+
+
+def words_dev(x, word_bits, dev):
+    dt = np.int64 if word_bits == 64 else np.int32
+    return T(np.ascontiguousarray(x).view(dt), dev)
+
+
+def edges_np(t):
+    return t.cpu().numpy().view(np.uint32).reshape(-1, 2)
+
+
+def random_scene(seed, n, d, ell, coef=1000, off=10**6, coord=1000):
+    return inputs.arrangement(seed, n, d, ell, coef, off, coord)
+
+
+def tie_scene(seed, n, d, ell):
+    """Points on and one unit off the constraints (a . p - b in {-1, 0, 1}),
+    plus int32/int64 extremes: every bit near the fp32 filter's boundary."""
+    rng = np.random.default_rng(seed)
+    a = rng.integers(-2**31, 2**31, size=(ell, d), dtype=np.int64).astype(np.int32)
+    a[: ell // 4] = rng.integers(-3, 4, size=(ell // 4, d))
+    pts = rng.integers(-2**31, 2**31, size=(n, d), dtype=np.int64).astype(np.int32)
+    pts[: n // 3] = rng.integers(-5, 6, size=(n // 3, d))
+    pts[n // 3: n // 3 + 8] = np.iinfo(np.int32).max
+    pts[n // 3 + 8: n // 3 + 16] = np.iinfo(np.int32).min
+    # offsets through chosen points, so that ties and near-ties happen
+    anchor = pts[rng.integers(0, n, size=ell)]
+    b = (a.astype(object) * anchor.astype(object)).sum(axis=1) + rng.integers(-1, 2, size=ell)
+    b = np.array([max(min(int(v), 2**63 - 1), -2**63) for v in b], dtype=np.int64)
+    b[0] = np.iinfo(np.int64).min
+    if ell > 1:
+        b[1] = np.iinfo(np.int64).max
+    a[2 % ell] = 0  # a constant constraint: 0 >= b
+    b[2 % ell] = 0
+    return inputs.Scene(pts=pts, a=a, b=b)
+
+
+# ------------------------------- step 1 ----------------------------------
+
+PACK_CASES = [
+    ("lines", 20_000, 2, 16, 32),
+    ("lines", 20_000, 2, 16, 64),
+    ("planes", 200_003, 3, 64, 64),
+    ("planes", 70_001, 3, 65, 64),
+    ("planes", 50_000, 3, 100, 32),
+    ("planes", 30_011, 3, 256, 64),
+    ("rand", 4099, 1, 7, 64),
+    ("rand", 4099, 4, 33, 32),
+    ("rand", 1, 2, 1, 64),
+    ("rand", 1023, 3, 31, 32),
+]
+
+
+@pytest.mark.parametrize("kind,n,d,ell,wb", PACK_CASES)
+def test_pack_signs_matches_oracle(dev, kind, n, d, ell, wb):
+    if kind == "lines":
+        sc = inputs.lines_2d(n=n, ell=ell)
+    elif kind == "planes":
+        sc = inputs.planes_3d(n=n, ell=ell, seed=7)
+    else:
+        sc = random_scene(ell * 31 + d, n, d, ell)
+    got = words_np(cellgraph.pack_signs(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), wb), wb)
+    want = oracle.pack_signs(sc.pts, sc.a, sc.b, wb)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("d,ell", [(1, 40), (2, 64), (3, 97), (4, 130)])
+def test_pack_signs_ties_and_extremes(dev, d, ell):
+    sc = tie_scene(100 + d, 5000, d, ell)
+    got = words_np(cellgraph.pack_signs(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 64), 64)
+    want = oracle.pack_signs(sc.pts, sc.a, sc.b, 64)
+    assert np.array_equal(got, want)
+
+
+def test_pack_signs_unaligned_points(dev):
+    sc = inputs.planes_3d(n=10_001, ell=64, seed=5)
+    buf = T(np.concatenate([[0], sc.pts.reshape(-1)]).astype(np.int32), dev)
+    pts = buf[1:].view(-1, 3)  # 4-byte offset: not 16-byte aligned
+    got = words_np(cellgraph.pack_signs(pts, T(sc.a, dev), T(sc.b, dev), 64), 64)
+    assert np.array_equal(got, oracle.pack_signs(sc.pts, sc.a, sc.b, 64))
+
+
+# ------------------------------- step 2 ----------------------------------
+
+def _dedup_case(kind, wb):
+    if kind == "lines":
+        sc = inputs.lines_2d()
+        return oracle.pack_signs(sc.pts, sc.a, sc.b, wb), 16
+    if kind == "planes64":
+        sc = inputs.planes_3d(n=300_000, ell=64, seed=8)
+        return oracle.pack_signs(sc.pts, sc.a, sc.b, wb), 64
+    if kind == "planes200":
+        sc = inputs.planes_3d(n=100_000, ell=200, seed=9)
+        return oracle.pack_signs(sc.pts, sc.a, sc.b, wb), 200
+    if kind == "chains":
+        ch = inputs.chains(n_seeds=3000, ell=1024, seed=10)
+        keys = ch.keys if wb == 64 else ch.keys.view(np.uint32)
+        return keys, 1024
+    if kind == "chains130":
+        ch = inputs.chains(n_seeds=5000, ell=130, seed=11)
+        return ch.keys, 130
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind,wb", [("lines", 32), ("lines", 64), ("planes64", 64),
+                                     ("planes200", 64), ("planes200", 32), ("chains", 64),
+                                     ("chains", 32), ("chains130", 64)])
+def test_dedup_matches_oracle(dev, kind, wb):
+    keys, ell = _dedup_case(kind, wb)
+    cells, pc = cellgraph.dedup_cells(words_dev(keys, wb, dev), ell, wb, point_cell=True)
+    want, want_pc = oracle.dedup(keys, ell, wb, point_cell=True)
+    assert np.array_equal(words_np(cells, wb), want)
+    assert np.array_equal(pc.cpu().numpy().view(np.uint32), want_pc)
+
+
+def test_dedup_all_duplicates_and_empty(dev):
+    keys = np.full((5000, 1), 12345, dtype=np.uint64)
+    cells = cellgraph.dedup_cells(words_dev(keys, 64, dev), 20, 64)
+    assert words_np(cells, 64).tolist() == [[12345]]
+    empty = cellgraph.dedup_cells(words_dev(np.zeros((0, 1), np.uint64), 64, dev), 20, 64)
+    assert empty.shape[0] == 0
+
+
+# ------------------------------ steps 3-4 --------------------------------
+
+@pytest.mark.parametrize("strategy", ["hash", "sorted"])
+@pytest.mark.parametrize("kind,wb", [("lines", 32), ("planes64", 64), ("planes200", 64),
+                                     ("planes200", 32), ("chains", 64), ("chains130", 64)])
+def test_neighbors_match_oracle(dev, kind, wb, strategy):
+    keys, ell = _dedup_case(kind, wb)
+    cells = oracle.dedup(keys, ell, wb)
+    got = cellgraph.neighbors_h1(words_dev(cells, wb, dev), ell, wb, strategy=strategy)
+    want = oracle.neighbors(cells, ell, wb)
+    assert np.array_equal(edges_np(got), want)
+    assert len(want) > 0
+
+
+def test_neighbors_hypercube(dev):
+    ell = 12
+    cells = np.arange(1 << ell, dtype=np.uint64).reshape(-1, 1)
+    got = edges_np(cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64))
+    assert len(got) == ell * (1 << (ell - 1))
+    assert np.array_equal(got, oracle.neighbors(cells, ell, 64))
+
+
+def test_neighbors_edge_capacity(dev):
+    keys, ell = _dedup_case("planes64", 64)
+    cells = oracle.dedup(keys, ell, 64)
+    want = oracle.neighbors(cells, ell, 64)
+    small = cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64, edges_cap=10)
+    assert np.array_equal(edges_np(small), want)  # binding retried with the reported E
+
+
+# ------------------------------ full build -------------------------------
+
+BUILD_CASES = [
+    ("lines", 20_000, 16, 32),
+    ("lines", 20_000, 16, 64),
+    ("planes", 1, 64, 64),
+    ("planes", 1000, 8, 64),
+    ("planes", 262_147, 64, 64),
+    ("planes", 100_000, 33, 32),
+    ("planes", 60_000, 100, 64),
+    ("planes", 40_000, 256, 64),
+    ("planes", 20_000, 1, 64),
+]
+
+
+@pytest.mark.parametrize("kind,n,ell,wb", BUILD_CASES)
+def test_build_matches_oracle(ctx, dev, kind, n, ell, wb):
+    sc = inputs.lines_2d(n=n, ell=ell) if kind == "lines" else inputs.planes_3d(n=n, ell=ell,
+                                                                               seed=12)
+    cells, edges = ctx.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), wb)
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, wb)
+    assert np.array_equal(words_np(cells, wb), want_c)
+    assert np.array_equal(edges_np(edges), want_e)
+
+
+def test_build_ties_and_extremes(ctx, dev):
+    for d, ell in [(2, 40), (3, 64), (4, 97)]:
+        sc = tie_scene(200 + d, 30_000, d, ell)
+        cells, edges = ctx.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
+        want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+        assert np.array_equal(words_np(cells, 64), want_c)
+        assert np.array_equal(edges_np(edges), want_e)
+
+
+def test_build_all_ones_vector(ctx, dev):
+    # l = 64, constraints 1..63 always hold (0 >= 0); constraint 0 is x >= 0:
+    # the cells are ~0 - 1 and ~0 (the all-ones vector, kept off the table).
+    a = np.zeros((64, 2), np.int32)
+    a[0] = (1, 0)
+    b = np.zeros(64, np.int64)
+    pts = np.array([[5, 1], [-5, 2], [0, 0], [-1, 9]] * 700, np.int32)
+    cells, edges = ctx.build(T(pts, dev), T(a, dev), T(b, dev), 64)
+    assert words_np(cells, 64).reshape(-1).tolist() == [2**64 - 2, 2**64 - 1]
+    assert edges_np(edges).tolist() == [[0, 1]]
+    want_c, want_e = oracle.build(pts, a, b, 64)
+    assert np.array_equal(words_np(cells, 64), want_c) and np.array_equal(edges_np(edges), want_e)
+
+
+def test_build_degenerate_inputs(ctx, dev):
+    sc = inputs.planes_3d(n=0, ell=20)
+    cells, edges = ctx.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
+    assert cells.shape[0] == 0 and edges.shape[0] == 0
+    pts = np.tile(np.array([[3, -4, 5]], np.int32), (9000, 1))  # one point, repeated
+    sc = inputs.planes_3d(n=1, ell=70)
+    cells, edges = ctx.build(T(pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
+    want_c, want_e = oracle.build(pts, sc.a, sc.b, 64)
+    assert np.array_equal(words_np(cells, 64), want_c) and len(want_c) == 1
+    assert edges.shape[0] == 0
+
+
+def test_build_overflowing_first_guess(ctx, dev):
+    # Degenerate arrangement with many coincident, oppositely oriented planes:
+    # more distinct vectors than the cell bound the first table size assumes.
+    rng = np.random.default_rng(3)
+    base = rng.integers(-50, 51, size=(8, 2)).astype(np.int32)
+    a = np.concatenate([base, -base, base, -base])
+    b = np.zeros(32, np.int64)
+    pts = rng.integers(-300, 301, size=(50_000, 2)).astype(np.int32)
+    cells, edges = ctx.build(T(pts, dev), T(a, dev), T(b, dev), 64)
+    want_c, want_e = oracle.build(pts, a, b, 64)
+    assert np.array_equal(words_np(cells, 64), want_c)
+    assert np.array_equal(edges_np(edges), want_e)
+
+
+def test_build_capacity_contract(ctx, dev):
+    """Too-small outputs: CG_ERR_CAPACITY, both counts written, nothing written
+    past either capacity."""
+    sc = inputs.planes_3d(n=50_000, ell=64, seed=4)
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+    lib = cellgraph.load_library()
+    cells = torch.full((10, 1), -7, dtype=torch.int64, device=dev)
+    edges = torch.full((20, 2), -7, dtype=torch.int32, device=dev)
+    nc, ne = ctypes.c_int64(0), ctypes.c_int64(0)
+    pts, a, b = T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev)
+    P = ctypes.c_void_p
+    rc = lib.cg_build(ctx._h, P(pts.data_ptr()), sc.n, 3, P(a.data_ptr()), P(b.data_ptr()), 64,
+                      64, P(cells.data_ptr()), 5, ctypes.byref(nc), P(edges.data_ptr()), 8,
+                      ctypes.byref(ne), P(torch.cuda.current_stream().cuda_stream))
+    assert rc == cellgraph.ERR_CAPACITY
+    assert nc.value == len(want_c) and ne.value == len(want_e)
+    assert (cells[5:] == -7).all() and (edges[8:] == -7).all()
+
+
+def test_build_host_matches_oracle(ctx, dev):
+    for sc, wb in [(inputs.lines_2d(), 32), (inputs.planes_3d(n=123_457, ell=64, seed=6), 64)]:
+        cells, edges = ctx.build_host(sc.pts, sc.a, sc.b, wb)
+        want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, wb)
+        assert np.array_equal(cells, want_c)
+        assert np.array_equal(edges, want_e)
+
+
+def test_build_is_deterministic(ctx, dev):
+    sc = inputs.planes_3d(n=500_000, ell=64, seed=13)
+    args = (T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
+    c1, e1 = ctx.build(*args)
+    c2, e2 = ctx.build(*args)
+    assert torch.equal(c1, c2) and torch.equal(e1, e2)
+
+
+# ------------------------------ full sizes -------------------------------
+
+def test_full_size_planes_3d(ctx, dev):
+    """The benchmark workload: l = 64 planes, N = 2^24 points, whole oracle."""
+    sc = inputs.planes_3d()
+    cells, edges = ctx.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+    assert np.array_equal(words_np(cells, 64), want_c)
+    assert np.array_equal(edges_np(edges), want_e)
+    assert len(want_c) <= 43_745  # sum_{k<=3} C(64, k)
+
+
+def test_full_size_lines_2d(ctx, dev):
+    sc = inputs.lines_2d()
+    cells, edges = ctx.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 32)
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 32)
+    assert np.array_equal(words_np(cells, 32), want_c)
+    assert np.array_equal(edges_np(edges), want_e)
+
+
+def test_full_size_chains(dev):
+    """l = 1024, N = 5,242,880: cells against the oracle in full; edges against
+    the oracle on 3,000 sampled cells, plus properties of the whole list."""
+    ch = inputs.chains()
+    keys_d = words_dev(ch.keys, 64, dev)
+    cells = cellgraph.dedup_cells(keys_d, 1024, 64)
+    del keys_d
+    edges = cellgraph.neighbors_h1(cells, 1024, 64)
+    got_c = words_np(cells, 64)
+    got_e = edges_np(edges).astype(np.int64)
+    want_c = oracle.dedup(ch.keys, 1024, 64)
+    assert np.array_equal(got_c, want_c)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(len(want_c), size=3000, replace=False))
+    want_rows = oracle.neighbors(want_c, 1024, 64, rows=rows)
+    sel = got_e[np.isin(got_e[:, 0], rows)]
+    assert np.array_equal(sel.astype(np.uint32), want_rows)
+    # properties of the whole list: i < j, sorted, unique, distance exactly 1
+    assert (got_e[:, 0] < got_e[:, 1]).all()
+    key = got_e[:, 0] * len(got_c) + got_e[:, 1]
+    assert (np.diff(key) > 0).all()
+    for lo in range(0, len(got_e), 1 << 19):
+        blk = got_e[lo: lo + (1 << 19)]
+        x = got_c[blk[:, 0]] ^ got_c[blk[:, 1]]
+        assert (popcount64(x).sum(axis=1) == 1).all()
+    # planted chain edges that survive are present
+    order = np.lexsort(tuple(got_c[:, j] for j in range(got_c.shape[1])))
+    assert (order == np.arange(len(got_c))).all()
+    base_par = ch.base[ch.planted[:, 0]]
+    base_chi = ch.base[ch.planted[:, 1]]
+    dist = popcount64(base_par ^ base_chi).sum(axis=1)
+    keep = dist == 1
+    assert keep.mean() > 0.99
+    # locate rows through a 64-bit linear fingerprint, then verify whole rows
+    w = np.random.default_rng(1).integers(1, 2**63, size=got_c.shape[1], dtype=np.uint64) | 1
+    fc = (got_c * w).sum(axis=1, dtype=np.uint64)
+    fo = np.argsort(fc, kind="stable")
+    fs = fc[fo]
+
+    def find(q):
+        fq = (q * w).sum(axis=1, dtype=np.uint64)
+        idx = fo[np.clip(np.searchsorted(fs, fq), 0, len(fs) - 1)]
+        assert (got_c[idx] == q).all()
+        return idx.astype(np.int64)
+
+    pi, ci = find(base_par[keep]), find(base_chi[keep])
+    lo_, hi_ = np.minimum(pi, ci), np.maximum(pi, ci)
+    planted = lo_ * len(got_c) + hi_
+    assert np.isin(planted, key).all()
