@@ -50,62 +50,116 @@ def _peaks():
 
 
 class ClockSampler:
-    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    """Samples SM clocks and clock-event (throttle) reasons while the timed
+    region runs: NVML through ctypes every ~2 ms (the timed region can be a few
+    ms long), plus nvidia-smi at 200 ms when the region is long enough."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    SMI_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
-        self.lines = []
-        self.proc = None
-        self.thread = None
+    def __init__(self, cuda_index: int):
+        self.cuda_index = cuda_index
+        self.sm, self.reason_bits, self.max_mhz = [], 0, None
+        self.smi_lines = []
+        self._stop = threading.Event()
+        self._nvml = None
+        self._handle = None
+
+    def _nvml_open(self):
+        import ctypes
+
+        import torch
+
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return False
+        h = ctypes.c_void_p()
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(self.cuda_index).uuid)
+        if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(self.cuda_index, ctypes.byref(h)) != 0:
+                return False
+        self._nvml, self._handle = lib, h
+        v = ctypes.c_uint(0)
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(v)) == 0:
+            self.max_mhz = float(v.value)
+        return True
+
+    def _poll(self):
+        import ctypes
+
+        lib, h = self._nvml, self._handle
+        v = ctypes.c_uint(0)
+        r = ctypes.c_ulonglong(0)
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or getattr(
+            lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(v)) == 0:
+                self.sm.append(float(v.value))
+            if get_reasons(h, ctypes.byref(r)) == 0:
+                self.reason_bits |= int(r.value)
+            time.sleep(0.002)
+
+    def _smi(self):
+        for line in self._proc.stdout:
+            self.smi_lines.append(line.strip())
 
     def __enter__(self):
+        self._threads = []
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            if self._nvml_open():
+                t = threading.Thread(target=self._poll, daemon=True)
+                t.start()
+                self._threads.append(t)
         except Exception:
-            self.proc = None
+            self._nvml = None
+        self._proc = None
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.SMI_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            t = threading.Thread(target=self._smi, daemon=True)
+            t.start()
+            self._threads.append(t)
+        except Exception:
+            self._proc = None
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *exc):
-        if self.proc:
-            self.proc.terminate()
+        self._stop.set()
+        if self._proc:
+            self._proc.terminate()
             try:
-                self.proc.wait(timeout=5)
+                self._proc.wait(timeout=5)
             except Exception:
-                self.proc.kill()
-            self.thread.join(timeout=5)
+                self._proc.kill()
+        for t in self._threads:
+            t.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        reasons = {name for bit, name in self.REASONS.items() if self.reason_bits & bit}
+        sm = list(self.sm)
+        for ln in self.smi_lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
             try:
                 sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                self.max_mhz = max(self.max_mhz or 0.0, float(parts[1]))
             except ValueError:
                 continue
-            for name, v in zip(names, parts[4:8]):
+            for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"], parts[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"],
+                    "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "nvidia_smi_samples": len(self.smi_lines)}
 
 
 def _dist():

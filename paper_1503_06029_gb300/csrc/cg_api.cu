@@ -109,8 +109,13 @@ struct SmallWs {
   uint32_t* counts;
   unsigned long long* offsets;
   void* scan;
-  uint64_t* cells;  // given cells (neighbour search only)
+  uint64_t* cells;  // sorted cells (given cells for the neighbour search)
+  unsigned long long* status;  // look-back words of the single-pass edge kernel
   size_t cap, ucap;
+  SmallTable table(bool with_list) const {
+    return SmallTable{tkeys, tvals, uint32_t(cap - 1), table_shift(cap),
+                      with_list ? ulist : nullptr, with_list ? uint32_t(ucap) : 0u, ctr};
+  }
 };
 
 SmallWs carve_small(Carve& c, size_t cap, size_t ucap, int ell, bool dedup, bool neigh,
@@ -128,12 +133,8 @@ SmallWs carve_small(Carve& c, size_t cap, size_t ucap, int ell, bool dedup, bool
     w.radix = c.take_bytes(radix_scratch_bytes(ucap));
   }
   if (given_cells) w.cells = c.take<uint64_t>(ucap);
-  if (neigh) {
-    w.masks = c.take<uint32_t>(ucap * nh);
-    w.counts = c.take<uint32_t>(ucap);
-    w.offsets = c.take<unsigned long long>(ucap);
-    w.scan = c.take_bytes(scan_scratch_bytes(ucap));
-  }
+  if (neigh) w.status = c.take<unsigned long long>(ne_status_words(ucap));
+  (void)nh;
   return w;
 }
 
@@ -189,6 +190,8 @@ cg_status read_counters(DevCounters* dev, DevCounters* host, cudaStream_t s) {
   CG_CUDA(cudaMemcpyAsync(host, dev, sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
           "reading counters");
   CG_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+  if (host->error & kErrTimeout)
+    return fail(CG_ERR_TIMEOUT, "a bounded device-side wait ran out");
   if (host->error)
     return fail(CG_ERR_INTERNAL, "device-side consistency check failed (code " +
                                      std::to_string(host->error) + ")");
@@ -200,16 +203,9 @@ cg_status read_counters(DevCounters* dev, DevCounters* host, cudaStream_t s) {
 // Steps 3-4 over internal sorted rows (small); ctr->n_unique holds U.
 cg_status neighbors_small_steps(const SmallWs& w, int ell, int strategy, uint32_t* edges,
                                 int64_t edges_cap, cudaStream_t s) {
-  SmallTable t{w.tkeys, w.tvals, uint32_t(w.cap - 1), nullptr, 0, w.ctr};
-  const uint64_t* cells = w.cells;
-  CG_CUDA(launch_neighbors_small(cells, t, ell, strategy, w.masks, w.counts, w.ucap, s),
-          "neighbour search");
-  CG_CUDA(scan_exclusive_u32(w.counts, w.offsets, &w.ctr->n_unique, w.ucap, &w.ctr->n_edges,
-                             w.scan, s),
-          "edge offsets");
-  CG_CUDA(launch_emit_small(cells, t, ell, strategy, w.masks, w.offsets, edges, edges_cap,
-                            w.ucap, s),
-          "edge output");
+  CG_CUDA(launch_neighbors_emit_small(w.cells, w.table(false), ell, strategy, w.status, edges,
+                                      edges_cap, w.ucap, s),
+          "neighbour search and edge output");
   return CG_OK;
 }
 
@@ -234,15 +230,22 @@ cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t*
 }
 
 // Step 2 on small vectors already in the table (ulist holds them in insertion
-// order): sort, number, write.
-cg_status dedup_small_tail(SmallWs& w, int ell, cudaStream_t s) {
+// order): sort, number, write the caller's copy.
+cg_status dedup_small_tail(SmallWs& w, int ell, int word_bits, void* user_cells,
+                           int64_t user_cap, cudaStream_t s) {
+  w.cells = w.sortbuf;
+  ClusterSortOut o{w.cells, user_cells, user_cap, word_bits, ell, w.table(true)};
+  bool done = false;
+  CG_CUDA(cluster_sort_small(w.ulist, w.ucap, ell, o, s, &done), "sorting cells (cluster)");
+  if (done) return CG_OK;
   bool in1 = false;
   CG_CUDA(radix_sort_u64(w.ulist, w.sortbuf, nullptr, nullptr, &w.ctr->n_unique, w.ucap, ell,
                          w.radix, s, &in1),
           "sorting cells");
   w.cells = in1 ? w.sortbuf : w.ulist;
-  SmallTable t{w.tkeys, w.tvals, uint32_t(w.cap - 1), w.ulist, uint32_t(w.ucap), w.ctr};
-  CG_CUDA(launch_rank_small(w.cells, t, w.ucap, s), "numbering cells");
+  CG_CUDA(launch_rank_small(w.cells, w.table(true), w.ucap, s), "numbering cells");
+  CG_CUDA(launch_write_cells(w.cells, ell, word_bits, user_cells, user_cap, w.ctr, w.ucap, s),
+          "writing cells");
   return CG_OK;
 }
 
@@ -459,7 +462,7 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
   {
     Carve c{nullptr};
     if (small) carve_small(c, cap, ucap, ell, true, false, false);
-    else carve_wide(c, un, cap, ucap, ell, convert, true, point_cell != nullptr, false);
+    else carve_wide(c, un, cap, ucap, ell, convert, true, true, false);
     if (!ws) {
       *ws_bytes = c.off + 256;
       return CG_OK;
@@ -474,20 +477,17 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
   DevCounters host{};
   if (small) {
     SmallWs w = carve_small(c, cap, ucap, ell, true, false, false);
-    CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
-    CG_CUDA(launch_fill_u64(w.tkeys, kEmpty, cap, s), "clearing table");
-    SmallTable t{w.tkeys, w.tvals, uint32_t(cap - 1), w.ulist, uint32_t(ucap), w.ctr};
+    CG_CUDA(launch_clear_build(w.tkeys, cap, nullptr, 0, w.ctr, s), "clearing table");
+    SmallTable t = w.table(true);
     CG_CUDA(launch_insert_small(keys, n, word_bits, ell, t, s), "inserting vectors");
-    cg_status st = dedup_small_tail(w, ell, s);
+    cg_status st = dedup_small_tail(w, ell, word_bits, cells, cells_cap, s);
     if (st) return st;
-    CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
-            "writing cells");
     if (point_cell)
       CG_CUDA(launch_point_cell_small(keys, n, word_bits, ell, t, point_cell, s), "point cells");
     st = read_counters(w.ctr, &host, s);
     if (st) return st;
   } else {
-    WideWs w = carve_wide(c, un, cap, ucap, ell, convert, true, point_cell != nullptr, false);
+    WideWs w = carve_wide(c, un, cap, ucap, ell, convert, true, true, false);
     const uint64_t* k64 = static_cast<const uint64_t*>(keys);
     if (convert) {
       CG_CUDA(launch_keys_to_u64(keys, n, word_bits, ell, w.keys64, s), "converting vectors");
@@ -543,13 +543,13 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
   DevCounters host{};
   if (small) {
     SmallWs w = carve_small(c, cap, un, ell, false, true, true);
-    CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
+    CG_CUDA(launch_clear_build(strategy != CG_STRATEGY_SORTED ? w.tkeys : nullptr,
+                               strategy != CG_STRATEGY_SORTED ? cap : 0, w.status,
+                               ne_status_words(un), w.ctr, s),
+            "clearing table");
     CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
-    if (strategy != CG_STRATEGY_SORTED) {
-      CG_CUDA(launch_fill_u64(w.tkeys, kEmpty, cap, s), "clearing table");
-      SmallTable t{w.tkeys, w.tvals, uint32_t(cap - 1), nullptr, 0, w.ctr};
-      CG_CUDA(launch_index_small(w.cells, t, un, s), "indexing cells");
-    }
+    if (strategy != CG_STRATEGY_SORTED)
+      CG_CUDA(launch_index_small(w.cells, w.table(false), un, s), "indexing cells");
     cg_status st = neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
     if (st) return st;
     st = read_counters(w.ctr, &host, s);
@@ -607,16 +607,13 @@ cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const in
   mark(ctx, "start", s);
   if (small) {
     SmallWs w = carve_small(c, cap, ucap, ell, true, true, false);
-    CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
-    CG_CUDA(launch_fill_u64(w.tkeys, kEmpty, cap, s), "clearing table");
+    CG_CUDA(launch_clear_build(w.tkeys, cap, w.status, ne_status_words(ucap), w.ctr, s),
+            "clearing table");
     mark(ctx, "clear", s);
-    SmallTable t{w.tkeys, w.tvals, uint32_t(cap - 1), w.ulist, uint32_t(ucap), w.ctr};
-    if (n > 0) CG_CUDA(launch_pack_insert(pa, t, s), "sign vectors + dedup");
+    if (n > 0) CG_CUDA(launch_pack_insert(pa, w.table(true), s), "sign vectors + dedup");
     mark(ctx, "pack_dedup", s);
-    st = dedup_small_tail(w, ell, s);
+    st = dedup_small_tail(w, ell, word_bits, cells, cells_cap, s);
     if (st) return st;
-    CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
-            "writing cells");
     mark(ctx, "sort_number", s);
     st = neighbors_small_steps(w, ell, CG_STRATEGY_HASH, edges, edges_cap, s);
     if (st) return st;

@@ -105,10 +105,11 @@ struct SmallHash {
   const uint64_t* keys;
   const uint32_t* vals;
   uint32_t mask;
+  int shift;
   const DevCounters* ctr;
   __device__ __forceinline__ int64_t find(uint64_t y) const {
     if (y == kEmpty) return ctr->ones_present ? int64_t(ctr->ones_rank) : -1;
-    uint32_t slot = uint32_t(mix64(y)) & mask;
+    uint32_t slot = home_slot(y, shift);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
       const uint64_t cur = keys[slot];
       if (cur == y) return vals[slot];
@@ -141,17 +142,6 @@ __global__ void insert_small(const void* keys, int64_t n, int word_bits, int w_c
     small_insert(t, load_word(keys, p, 0, word_bits, w_caller));
 }
 
-// Finds the slot of a vector known to be in the table.
-__device__ __forceinline__ int64_t small_slot(const SmallTable& t, uint64_t key) {
-  uint32_t slot = uint32_t(mix64(key)) & t.mask;
-  for (uint32_t probe = 0; probe <= t.mask; ++probe) {
-    const uint64_t cur = t.keys[slot];
-    if (cur == key) return slot;
-    if (cur == kEmpty) return -1;
-    slot = (slot + 1) & t.mask;
-  }
-  return -1;
-}
 
 __global__ void rank_small(const uint64_t* cells, SmallTable t) {
   if (t.ctr->overflow) return;
@@ -162,7 +152,7 @@ __global__ void rank_small(const uint64_t* cells, SmallTable t) {
       t.ctr->ones_rank = i;
       continue;
     }
-    const int64_t slot = small_slot(t, key);
+    const int64_t slot = small_find_slot(t.keys, t.mask, t.shift, key);
     if (slot < 0) {
       atomicOr(&t.ctr->error, 1u);
       continue;
@@ -180,7 +170,7 @@ __global__ void index_small(const uint64_t* cells, SmallTable t) {
       t.ctr->ones_rank = i;
       continue;
     }
-    uint32_t slot = uint32_t(mix64(key)) & t.mask;
+    uint32_t slot = home_slot(key, t.shift);
     bool placed = false;
     for (uint32_t probe = 0; probe <= t.mask; ++probe) {
       const unsigned long long old =
@@ -201,7 +191,7 @@ __global__ void index_small(const uint64_t* cells, SmallTable t) {
 __global__ void point_cell_small(const void* keys, int64_t n, int word_bits, int w_caller,
                                  SmallTable t, uint32_t* point_cell) {
   if (t.ctr->overflow) return;
-  const SmallHash h{t.keys, t.vals, t.mask, t.ctr};
+  const SmallHash h{t.keys, t.vals, t.mask, t.shift, t.ctr};
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n;
        p += int64_t(gridDim.x) * blockDim.x) {
     const int64_t j = h.find(load_word(keys, p, 0, word_bits, w_caller));
@@ -264,6 +254,128 @@ __global__ void __launch_bounds__(kThreads)
       }
       off += __popc(m);
     }
+  }
+}
+
+__global__ void clear_build(uint64_t* table, size_t cap, unsigned long long* status,
+                            size_t n_status, DevCounters* ctr) {
+  if (blockIdx.x == 0 && threadIdx.x < sizeof(DevCounters) / 4)
+    reinterpret_cast<uint32_t*>(ctr)[threadIdx.x] = 0;
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < cap; i += stride)
+    table[i] = kEmpty;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n_status; i += stride)
+    status[i] = 0;
+}
+
+// Steps 3-4 in one pass (l <= 64). Work is handed out in chunks of 32 cells
+// by an atomic ticket, so every chunk's predecessors are already running.
+// For a chunk: the warps find the hits of their cells (one lane per bit, hits
+// kept in shared memory), warp 0 scans the 32 counts, publishes the chunk's
+// total, and looks back over the predecessors' published totals (decoupled
+// look-back, Merrill & Garland 2016) for the chunk's first edge position;
+// then the block writes its edges. The look-back wait is bounded.
+constexpr int kNEThreads = 256;
+constexpr int kNECells = 32;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr unsigned kSpinLimit = 1u << 22;
+
+template <class L>
+__global__ void __launch_bounds__(kNEThreads)
+    neighbors_emit_small(const uint64_t* __restrict__ cells, L look, DevCounters* ctr, int ell,
+                         unsigned long long* status, uint32_t* __restrict__ edges, int64_t cap,
+                         uint32_t max_n) {
+  __shared__ uint32_t hits[kNECells][64];
+  __shared__ uint32_t cnt[kNECells];
+  __shared__ uint32_t off[kNECells];
+  __shared__ uint32_t s_chunk;
+  __shared__ unsigned long long s_base;
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  const uint32_t nchunks = (u + kNECells - 1) / kNECells;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int nh = (ell + 31) >> 5;
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(&ctr->ticket, 1u);
+    __syncthreads();
+    const uint32_t c = s_chunk;
+    if (c >= nchunks) break;
+    for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
+      const uint32_t i = c * kNECells + cl;
+      uint32_t total = 0;
+      if (i < u) {
+        const uint64_t x = cells[i];
+        for (int h = 0; h < nh; ++h) {
+          const int k = h * 32 + lane;
+          int64_t j = -1;
+          if (k < ell && !((x >> k) & 1ull)) j = look.find(x | (1ull << k));
+          const uint32_t m = __ballot_sync(0xffffffffu, j >= 0);
+          if (j >= 0) hits[cl][total + __popc(m & lanemask_lt())] = uint32_t(j);
+          total += __popc(m);
+        }
+      }
+      if (lane == 0) cnt[cl] = total;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t v = cnt[lane];
+      uint32_t inc = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      off[lane] = inc - v;
+      const unsigned long long T = __shfl_sync(0xffffffffu, inc, 31);
+      if (lane == 0) {
+        unsigned long long base = 0;
+        if (c == 0) {
+          atomicExch(&status[0], kFlagPre | T);
+        } else {
+          atomicExch(&status[c], kFlagAgg | T);
+          int64_t p = int64_t(c) - 1;
+          unsigned iters = 0;
+          while (p >= 0) {
+            const unsigned long long sv =
+                *reinterpret_cast<volatile unsigned long long*>(&status[p]);
+            const unsigned long long f = sv & ~kValMask;
+            if (f == 0) {
+              if (++iters > kSpinLimit) {
+                atomicOr(&ctr->error, kErrTimeout);
+                break;
+              }
+              __nanosleep(64);
+              continue;
+            }
+            base += sv & kValMask;
+            if (f == kFlagPre) break;
+            --p;
+          }
+          atomicExch(&status[c], kFlagPre | (base + T));
+        }
+        s_base = base;
+        if (c == nchunks - 1) ctr->n_edges = base + T;
+      }
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+    for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
+      const uint32_t i = c * kNECells + cl;
+      const uint32_t m = cnt[cl];
+      const unsigned long long o = base + off[cl];
+      for (uint32_t r = lane; r < m; r += 32) {
+        const unsigned long long e = o + r;
+        if (e < (unsigned long long)cap) {
+          edges[2 * e] = i;
+          edges[2 * e + 1] = hits[cl][r];
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -550,6 +662,33 @@ cudaError_t launch_zero_counters(DevCounters* c, cudaStream_t s) {
   return finish(0);
 }
 
+cudaError_t launch_clear_build(uint64_t* table, size_t cap, unsigned long long* status,
+                               size_t n_status, DevCounters* ctr, cudaStream_t s) {
+  clear_build<<<grid_for(std::max(cap, n_status) + 1, kThreads * 4, 16), kThreads, 0, s>>>(
+      table, cap, status, n_status, ctr);
+  return finish(0);
+}
+
+size_t ne_status_words(size_t max_n) { return (max_n + kNECells - 1) / kNECells + 1; }
+
+cudaError_t launch_neighbors_emit_small(const uint64_t* cells, const SmallTable& t, int ell,
+                                        int strategy, unsigned long long* status,
+                                        uint32_t* edges, int64_t edges_cap, size_t max_n,
+                                        cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  if (ell > 64) return cudaErrorInvalidValue;
+  const int g = grid_for(max_n, kNECells, 4);
+  if (strategy == 2) {
+    neighbors_emit_small<<<g, kNEThreads, 0, s>>>(cells, SmallSorted{cells, t.ctr}, t.ctr, ell,
+                                                  status, edges, edges_cap, uint32_t(max_n));
+  } else {
+    neighbors_emit_small<<<g, kNEThreads, 0, s>>>(
+        cells, SmallHash{t.keys, t.vals, t.mask, t.shift, t.ctr}, t.ctr, ell, status, edges,
+        edges_cap, uint32_t(max_n));
+  }
+  return finish(0);
+}
+
 cudaError_t launch_keys_to_u64(const void* keys, int64_t n, int word_bits, int ell, uint64_t* out,
                                cudaStream_t s) {
   if (n == 0) return cudaSuccess;
@@ -619,7 +758,7 @@ cudaError_t launch_neighbors_small(const uint64_t* cells, const SmallTable& t, i
     neighbors_small<<<g, kThreads, 0, s>>>(cells, SmallSorted{cells, t.ctr}, t.ctr, ell, masks,
                                            counts);
   } else {
-    neighbors_small<<<g, kThreads, 0, s>>>(cells, SmallHash{t.keys, t.vals, t.mask, t.ctr}, t.ctr,
+    neighbors_small<<<g, kThreads, 0, s>>>(cells, SmallHash{t.keys, t.vals, t.mask, t.shift, t.ctr}, t.ctr,
                                            ell, masks, counts);
   }
   return finish(0);
@@ -634,7 +773,7 @@ cudaError_t launch_emit_small(const uint64_t* cells, const SmallTable& t, int el
     emit_small<<<g, kThreads, 0, s>>>(cells, SmallSorted{cells, t.ctr}, t.ctr, ell, masks,
                                       offsets, edges, edges_cap);
   } else {
-    emit_small<<<g, kThreads, 0, s>>>(cells, SmallHash{t.keys, t.vals, t.mask, t.ctr}, t.ctr, ell,
+    emit_small<<<g, kThreads, 0, s>>>(cells, SmallHash{t.keys, t.vals, t.mask, t.shift, t.ctr}, t.ctr, ell,
                                       masks, offsets, edges, edges_cap);
   }
   return finish(0);

@@ -24,8 +24,12 @@ struct DevCounters {
   unsigned int ones_present;  // the all-ones vector (l == 64) is a cell
   unsigned int ones_rank;     // its cell number
   unsigned int error;         // device-side consistency failures (bit set)
-  unsigned int pad[9];
+  unsigned int ticket;        // work counter of the single-pass edge kernel
+  unsigned int pad[8];
 };
+
+// Bits of DevCounters::error.
+constexpr unsigned kErrTimeout = 64u;  // a bounded device-side wait ran out
 static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
 
 // ---------------------------------------------------------------------------
@@ -77,23 +81,37 @@ struct PackArgs {
 // keys[n][W] in word_bits-bit words.
 cudaError_t launch_pack_store(const PackArgs& pa, int word_bits, void* keys, cudaStream_t s);
 
-// Fused steps 1-2 for l <= 64: every vector goes straight into the table
-// (no vector is written to memory); distinct vectors are appended to ulist.
+// Open-addressing table for vectors of l <= 64 bits (the vector is the key).
+// Home slot: Fibonacci hashing, the top log2(cap) bits of key * 2^64/phi
+// (Knuth, TAOCP vol. 3, 6.4); linear probing.
 struct SmallTable {
   uint64_t* keys;      // [cap], kEmpty = free
   uint32_t* vals;      // [cap], cell number of the key in the same slot
   uint32_t mask;       // cap - 1 (cap a power of two)
+  int shift;           // 64 - log2(cap)
   uint64_t* ulist;     // [ucap] distinct vectors, in insertion order
   uint32_t ucap;
   DevCounters* ctr;
 };
-cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStream_t s);
 
+inline int table_shift(size_t cap) {
+  int b = 0;
+  while ((size_t(1) << b) < cap) ++b;
+  return 64 - b;
+}
+
+// Fused steps 1-2 for l <= 64: every vector goes straight into the table
+// (no vector is written to memory); distinct vectors are appended to ulist.
+cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Device helpers used by several translation units.
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
+__device__ __forceinline__ uint32_t home_slot(uint64_t key, int shift) {
+  return uint32_t((key * 0x9E3779B97F4A7C15ull) >> shift);
+}
+
 // Appends a newly inserted distinct vector to the table's list.
 __device__ __forceinline__ void small_append(const SmallTable& t, uint64_t key) {
   const unsigned int idx = atomicAdd(&t.ctr->n_unique, 1u);
@@ -104,17 +122,17 @@ __device__ __forceinline__ void small_append(const SmallTable& t, uint64_t key) 
   }
 }
 
-// Inserts one vector (l <= 64) into the dedup table; the first inserter of a
-// value appends it to the list of cells (§3.2: duplicates are removed).
-// Linear probing; a table that is full raises the overflow flag.
-__device__ __forceinline__ void small_insert(const SmallTable& t, uint64_t key) {
+// Inserts one vector (l <= 64) into the dedup table, starting at `slot` whose
+// content `cur` the caller has already read; the first inserter of a value
+// appends it to the list of cells (§3.2: duplicates are removed). A table that
+// is full raises the overflow flag.
+__device__ __forceinline__ void small_insert_from(const SmallTable& t, uint64_t key,
+                                                  uint32_t slot, uint64_t cur) {
   if (key == kEmpty) {
     if (atomicExch(&t.ctr->ones_present, 1u) == 0u) small_append(t, key);
     return;
   }
-  uint32_t slot = uint32_t(mix64(key)) & t.mask;
   for (uint32_t probe = 0; probe <= t.mask; ++probe) {
-    const uint64_t cur = t.keys[slot];
     if (cur == key) return;
     if (cur == kEmpty) {
       const unsigned long long old =
@@ -127,8 +145,27 @@ __device__ __forceinline__ void small_insert(const SmallTable& t, uint64_t key) 
       if (old == key) return;
     }
     slot = (slot + 1) & t.mask;
+    cur = t.keys[slot];
   }
   atomicOr(&t.ctr->overflow, 1u);
+}
+
+__device__ __forceinline__ void small_insert(const SmallTable& t, uint64_t key) {
+  const uint32_t slot = home_slot(key, t.shift);
+  small_insert_from(t, key, slot, key == kEmpty ? 0ull : t.keys[slot]);
+}
+
+// Slot holding `key` (known to be in the table), or -1.
+__device__ __forceinline__ int64_t small_find_slot(const uint64_t* keys, uint32_t mask, int shift,
+                                                   uint64_t key) {
+  uint32_t slot = home_slot(key, shift);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const uint64_t cur = keys[slot];
+    if (cur == key) return slot;
+    if (cur == kEmpty) return -1;
+    slot = (slot + 1) & mask;
+  }
+  return -1;
 }
 #endif
 
@@ -178,6 +215,33 @@ cudaError_t launch_write_cells(const uint64_t* cells, int ell, int word_bits, vo
 // Load caller-layout cells into internal u64 rows; sets ctr->n_unique = n.
 cudaError_t launch_load_cells(const void* cells, int64_t n, int word_bits, int ell,
                               uint64_t* out, DevCounters* ctr, cudaStream_t s);
+
+// Clears a build's table (kEmpty), the look-back status words and the counters.
+cudaError_t launch_clear_build(uint64_t* table, size_t cap, unsigned long long* status,
+                               size_t n_status, DevCounters* ctr, cudaStream_t s);
+
+// Sorts the U <= max_n distinct vectors of `in` (l <= 64) inside one thread-block
+// cluster (keys held in distributed shared memory), then writes the sorted
+// cells, the caller's copy (when U <= user_cap) and the cell numbers into the
+// table. Returns false in *done when max_n is too large for one cluster.
+struct ClusterSortOut {
+  uint64_t* cells;
+  void* user_cells;
+  int64_t user_cap;
+  int word_bits;
+  int ell;
+  SmallTable t;
+};
+cudaError_t cluster_sort_small(const uint64_t* in, size_t max_n, int bits,
+                               const ClusterSortOut& o, cudaStream_t s, bool* done);
+
+// Steps 3-4 in one kernel for l <= 64: hit search, scan with decoupled
+// look-back (status: ceil(max_n / 32) words, zeroed) and edge output.
+size_t ne_status_words(size_t max_n);
+cudaError_t launch_neighbors_emit_small(const uint64_t* cells, const SmallTable& t, int ell,
+                                        int strategy, unsigned long long* status,
+                                        uint32_t* edges, int64_t edges_cap, size_t max_n,
+                                        cudaStream_t s);
 
 // Neighbour search. masks: [U][ceil(l/32)] hit bits; counts: [U].
 cudaError_t launch_neighbors_small(const uint64_t* cells, const SmallTable& t, int ell,

@@ -127,19 +127,9 @@ struct StoreSink {
   static constexpr bool kKeepKey = false;
 };
 
-// Inserts each l <= 64 vector into the dedup table (§3.2: duplicates removed).
-struct InsertSink {
-  SmallTable t;
-  __device__ void word(int64_t, int, uint32_t, uint32_t&, bool) const {}
-  __device__ void done(int64_t, uint64_t key) const;
-  static constexpr bool kKeepKey = true;
-};
-
 }  // namespace
 
 namespace {
-
-__device__ void InsertSink::done(int64_t, uint64_t key) const { small_insert(t, key); }
 
 template <int D, class Sink>
 __global__ void __launch_bounds__(kThreads)
@@ -275,6 +265,311 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fast path for l <= 64 (NCH = 1 or 2 chunks of 32 constraints): 8 points per
+// thread (four f32x2 pairs), every loop fully unrolled, no block barrier after
+// the set-up. The coefficient rows are built once per block for a bound taken
+// from the block's first points (rounded up to a power of two); a warp whose
+// points exceed that bound builds its own rows in a private slice of shared
+// memory, so the error bound always covers the points it is applied to.
+// ---------------------------------------------------------------------------
+constexpr int kFP = 8;  // points per thread (upper bound over the variants)
+constexpr int kFThreads = 256;
+constexpr int kFWarps = kFThreads / 32;
+
+__device__ __forceinline__ uint32_t pow2_ceil(uint32_t m) {
+  return m <= 1 ? m : (1u << (32 - __clz(m - 1)));
+}
+
+template <int D, int P>
+__device__ __forceinline__ void load_points(const PackArgs& pa, int64_t p0, int vec_ok,
+                                            int32_t (&pi)[P][D]) {
+  if (vec_ok && p0 + P <= pa.n) {
+    const int4* src = reinterpret_cast<const int4*>(pa.pts + p0 * D);
+    int32_t tmp[P * D];
+#pragma unroll
+    for (int q = 0; q < P * D / 4; ++q) {
+      const int4 v = __ldg(src + q);
+      tmp[4 * q] = v.x;
+      tmp[4 * q + 1] = v.y;
+      tmp[4 * q + 2] = v.z;
+      tmp[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+      for (int k = 0; k < D; ++k) pi[q][k] = tmp[q * D + k];
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        pi[q][k] = (p0 + q < pa.n) ? __ldg(pa.pts + (p0 + q) * D + k) : 0;
+  }
+}
+
+// Words of l <= 64 vectors written to keys (64-bit: one word per point;
+// 32-bit: NCH words per point).
+template <int NCH>
+struct FastStore {
+  void* keys;
+  int word_bits;
+  template <int P>
+  __device__ __forceinline__ void finish(int64_t p0, int64_t n, const uint64_t (&key)[P]) const {
+    if (word_bits == 64) {
+      uint64_t* out = static_cast<uint64_t*>(keys) + p0;
+      if (p0 + P <= n && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+#pragma unroll
+        for (int q = 0; q < P; q += 2)
+          *reinterpret_cast<ulonglong2*>(out + q) = make_ulonglong2(key[q], key[q + 1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+          if (p0 + q < n) out[q] = key[q];
+      }
+    } else {
+      uint32_t* out = static_cast<uint32_t*>(keys) + p0 * NCH;
+#pragma unroll
+      for (int q = 0; q < P; ++q)
+        if (p0 + q < n) {
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) out[q * NCH + c] = uint32_t(key[q] >> (32 * c));
+        }
+    }
+  }
+};
+
+// Inserts the vectors into the dedup table: the home slots of all of a
+// thread's vectors are read first (all loads in flight); only vectors not
+// found there take the probing/CAS path.
+struct FastInsert {
+  SmallTable t;
+  template <int P>
+  __device__ __forceinline__ void finish(int64_t p0, int64_t n, const uint64_t (&key)[P]) const {
+    uint32_t slot[P];
+    uint64_t cur[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) slot[q] = home_slot(key[q], t.shift);
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+      cur[q] = (p0 + q < n && key[q] != kEmpty) ? t.keys[slot[q]] : 0ull;
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+      if (p0 + q < n && (key[q] == kEmpty || cur[q] != key[q]))
+        small_insert_from(t, key[q], slot[q], cur[q]);
+  }
+};
+
+// P points per thread (P/2 f32x2 pairs when F2, else scalar FFMA); the
+// 32-constraint loop is unrolled UJ times.
+template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 8>
+__global__ void __launch_bounds__(kFThreads)
+    pack_fast_kernel(PackArgs pa, Sink sink, int vec_ok) {
+  constexpr int kQ = Coef<D>::kQuads;
+  constexpr int kRows = NCH * 32;
+  constexpr int kWarpPts = 32 * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* blk = reinterpret_cast<float4*>(smem_raw);
+  float4* priv = blk + (1 + (threadIdx.x >> 5)) * (kRows * kQ);
+  __shared__ uint32_t mblk[D];
+  const int lane = threadIdx.x & 31;
+  const int64_t n = pa.n;
+  const int64_t n_wt = (n + kWarpPts - 1) / kWarpPts;
+  const int64_t stride = int64_t(gridDim.x) * kFWarps;
+  int64_t wt = int64_t(blockIdx.x) * kFWarps + (threadIdx.x >> 5);
+
+  // Block set-up: bound from every warp's first tile, rows for that bound.
+  if (threadIdx.x < D) mblk[threadIdx.x] = 0;
+  __syncthreads();
+  {
+    int32_t pi[P][D];
+    load_points<D, P>(pa, wt * kWarpPts + lane * P, vec_ok, pi);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      uint32_t m = 0;
+#pragma unroll
+      for (int q = 0; q < P; ++q) m = max(m, uabs32(pi[q][k]));
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (lane == 0) atomicMax(&mblk[k], m);
+    }
+  }
+  __syncthreads();
+  uint32_t Mb[D], Mp[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    Mb[k] = pow2_ceil(mblk[k]);
+    Mp[k] = 0;
+  }
+  for (int t = threadIdx.x; t < kRows; t += kFThreads) build_coef<D>(pa, t, Mb, blk + t * kQ);
+  __syncthreads();
+  bool priv_ok = false;
+
+  for (; wt < n_wt; wt += stride) {
+    const int64_t p0 = wt * kWarpPts + int64_t(lane) * P;
+    int32_t pi[P][D];
+    load_points<D, P>(pa, p0, vec_ok, pi);
+    uint32_t mw[D];
+    bool fits_blk = true, fits_priv = priv_ok;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      uint32_t m = 0;
+#pragma unroll
+      for (int q = 0; q < P; ++q) m = max(m, uabs32(pi[q][k]));
+      mw[k] = __reduce_max_sync(0xffffffffu, m);
+      fits_blk = fits_blk && mw[k] <= Mb[k];
+      fits_priv = fits_priv && mw[k] <= Mp[k];
+    }
+    const float4* cf = blk;
+    if (!fits_blk) {
+      if (!fits_priv) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) Mp[k] = pow2_ceil(mw[k]);
+        for (int t = lane; t < kRows; t += 32) build_coef<D>(pa, t, Mp, priv + t * kQ);
+        __syncwarp();
+        priv_ok = true;
+      }
+      cf = priv;
+    }
+    uint64_t X[P / 2][D];
+    float Xs[P][D];
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+      for (int k = 0; k < D; ++k) Xs[q][k] = __int2float_rn(pi[q][k]);
+#pragma unroll
+    for (int h = 0; h < P / 2; ++h)
+#pragma unroll
+      for (int k = 0; k < D; ++k) X[h][k] = pack2(Xs[2 * h][k], Xs[2 * h + 1][k]);
+
+    uint64_t key[P];
+#pragma unroll 1
+    for (int c = 0; c < NCH; ++c) {
+      uint32_t w[P];
+#pragma unroll
+      for (int q = 0; q < P; ++q) w[q] = 0;
+      uint32_t cert = 0xffffffffu;
+      const float4* cc = cf + c * 32 * kQ;
+#pragma unroll UJ
+      for (int j = 31; j >= 0; --j) {
+        float4 q4[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) q4[q] = cc[j * kQ + q];
+        const float* f = reinterpret_cast<const float*>(q4);
+        if (F2) {
+          uint64_t A[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) A[k] = pack2(f[2 * k], f[2 * k + 1]);
+          const uint64_t C = pack2(f[2 * D], f[2 * D + 1]);
+#pragma unroll
+          for (int h = 0; h < P / 2; ++h) {
+            uint64_t acc = C;
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc = ffma2(A[k], X[h][k], acc);
+            const uint32_t lo = uint32_t(acc);
+            const uint32_t hi = uint32_t(acc >> 32);
+            w[2 * h] = __funnelshift_l(lo, w[2 * h], 1);
+            w[2 * h + 1] = __funnelshift_l(hi, w[2 * h + 1], 1);
+            cert &= lo & hi;
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < P / 2; ++h) {
+            float a0 = f[2 * D], a1 = f[2 * D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              a0 = fmaf(f[2 * k], Xs[2 * h][k], a0);
+              a1 = fmaf(f[2 * k], Xs[2 * h + 1][k], a1);
+            }
+            const uint32_t lo = __float_as_uint(a0);
+            const uint32_t hi = __float_as_uint(a1);
+            w[2 * h] = __funnelshift_l(lo, w[2 * h], 1);
+            w[2 * h + 1] = __funnelshift_l(hi, w[2 * h + 1], 1);
+            cert &= lo & hi;
+          }
+        }
+      }
+      if (!(cert & 0x40000000u)) {
+        // Some |t'| < 2 in this chunk: settle those bits exactly.
+#pragma unroll 1
+        for (int q = 0; q < P; ++q) {
+          if (p0 + q >= n) continue;
+          int32_t pq[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) pq[k] = __ldg(pa.pts + (p0 + q) * D + k);
+#pragma unroll 1
+          for (int j = 0; j < 32; ++j) {
+            const int t = c * 32 + j;
+            if (t >= pa.ell) break;
+            const float* f = reinterpret_cast<const float*>(cc + j * kQ);
+            float acc = f[2 * D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc = fmaf(f[2 * k], __int2float_rn(pq[k]), acc);
+            if (fabsf(acc) < 2.0f) {
+              const bool ge = exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], pq);
+              w[q] = ge ? (w[q] & ~(1u << j)) : (w[q] | (1u << j));
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        if (c == 0) key[q] = ~w[q];
+        else key[q] |= uint64_t(~w[q]) << 32;
+      }
+    }
+    sink.template finish<P>(p0, n, key);
+  }
+}
+
+template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 8>
+cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
+  const size_t smem = size_t(1 + kFWarps) * NCH * 32 * Coef<D>::kQuads * sizeof(float4);
+  auto kern = pack_fast_kernel<D, NCH, Sink, P, F2, UJ>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFThreads, smem);
+  if (err != cudaSuccess) return err;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const int64_t n_wt = (pa.n + 32 * P - 1) / (32 * P);
+  const int64_t want = (n_wt + kFWarps - 1) / kFWarps;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sm_count()) * per_sm));
+  const int vec_ok = (reinterpret_cast<uintptr_t>(pa.pts) % 16) == 0;
+  kern<<<unsigned(grid), kFThreads, smem, s>>>(pa, sink, vec_ok);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <class SinkFor>
+cudaError_t launch_fast_any(const PackArgs& pa, SinkFor make, cudaStream_t s) {
+  const bool two = pa.ell > 32;
+  switch (pa.d) {
+    case 1: return two ? launch_fast<1, 2>(pa, make.template get<2>(), s)
+                       : launch_fast<1, 1>(pa, make.template get<1>(), s);
+    case 2: return two ? launch_fast<2, 2>(pa, make.template get<2>(), s)
+                       : launch_fast<2, 1>(pa, make.template get<1>(), s);
+    case 3: return two ? launch_fast<3, 2>(pa, make.template get<2>(), s)
+                       : launch_fast<3, 1>(pa, make.template get<1>(), s);
+    case 4: return two ? launch_fast<4, 2>(pa, make.template get<2>(), s)
+                       : launch_fast<4, 1>(pa, make.template get<1>(), s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+struct MakeStore {
+  void* keys;
+  int word_bits;
+  template <int NCH>
+  FastStore<NCH> get() const { return FastStore<NCH>{keys, word_bits}; }
+};
+
+struct MakeInsert {
+  SmallTable t;
+  template <int NCH>
+  FastInsert get() const { return FastInsert{t}; }
+};
+
 template <int D, class Sink>
 cudaError_t launch_d(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
   if (pa.n == 0) return cudaSuccess;
@@ -311,14 +606,16 @@ cudaError_t launch_any(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_pack_store(const PackArgs& pa, int word_bits, void* keys, cudaStream_t s) {
+  if (pa.n == 0) return cudaSuccess;
+  if (pa.ell <= 64) return launch_fast_any(pa, MakeStore{keys, word_bits}, s);
   StoreSink sink{keys, word_bits, (pa.ell + word_bits - 1) / word_bits};
   return launch_any(pa, sink, s);
 }
 
 cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStream_t s) {
   if (pa.ell > 64) return cudaErrorInvalidValue;
-  InsertSink sink{t};
-  return launch_any(pa, sink, s);
+  if (pa.n == 0) return cudaSuccess;
+  return launch_fast_any(pa, MakeInsert{t}, s);
 }
 
 }  // namespace cg

@@ -5,6 +5,8 @@
 // kernel per pass (plus a device-wide scan of the per-tile histograms when
 // there are more than kInlineTiles tiles). Item counts are read from device
 // memory, so a whole build can be enqueued without reading anything back.
+#include <cooperative_groups.h>
+
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -245,6 +247,153 @@ __global__ void __launch_bounds__(kRThreads)
   }
 }
 
+// ------------------------- one-cluster radix sort -------------------------
+//
+// For up to a few hundred thousand distinct vectors the multi-launch radix sort
+// is launch-bound. Here one thread-block cluster (8 or 16 CTAs, one per SM)
+// holds all keys in its distributed shared memory: CTA r owns positions
+// [r*per, (r+1)*per). Each 8-bit pass: local histograms -> cluster barrier ->
+// every CTA reads all histograms over DSMEM and derives its digit offsets ->
+// stable warp-level ranking -> each key is stored straight into the shared
+// memory of the CTA that owns its new position -> cluster barrier. A pass
+// whose digit is the same for every key is skipped.
+
+constexpr int kCThreads = 512;
+constexpr int kCWarps = kCThreads / 32;
+
+__global__ void __launch_bounds__(kCThreads)
+    cluster_sort_kernel(const uint64_t* __restrict__ in, uint32_t max_n, int bits,
+                        ClusterSortOut o, uint32_t per_cap) {
+  namespace cgx = cooperative_groups;
+  cgx::cluster_group cluster = cgx::this_cluster();
+  extern __shared__ __align__(16) uint64_t cbuf[];
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t wcnt[kCWarps][256];
+  __shared__ uint32_t toff[256];
+  __shared__ uint32_t wtot[8];
+  __shared__ int skip;
+  const DevCounters* ctr = o.t.ctr;
+  if (ctr->overflow) return;  // same value for every CTA of the cluster
+  const uint32_t C = cluster.num_blocks();
+  const uint32_t r = cluster.block_rank();
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const uint32_t n = min(ctr->n_unique, max_n);
+  const uint32_t per = (n + C - 1) / C;
+  const uint32_t lo = min(r * per, n);
+  const uint32_t cnt = min(lo + per, n) - lo;
+  uint64_t* cur = cbuf;
+  uint64_t* nxt = cbuf + per_cap;
+  for (uint32_t i = tid; i < cnt; i += kCThreads) cur[i] = in[lo + i];
+  const uint32_t sw = (cnt + kCWarps - 1) / kCWarps;  // items per warp (contiguous)
+  const uint32_t wlo = min(warp * sw, cnt);
+  const uint32_t whi = min(wlo + sw, cnt);
+
+  const int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    if (tid < 256) hist[tid] = 0;
+    if (tid == 0) skip = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < cnt; i += kCThreads) atomicAdd(&hist[(cur[i] >> shift) & 255u], 1u);
+    cluster.sync();
+    uint32_t tot = 0, before = 0;
+    if (tid < 256) {
+      for (uint32_t q = 0; q < C; ++q) {
+        const uint32_t v = cluster.map_shared_rank(hist, q)[tid];
+        tot += v;
+        if (q < r) before += v;
+      }
+      if (n > 0 && tot == n) skip = 1;
+    }
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o2);
+      if (lane >= o2) inc += t;
+    }
+    if (tid < 256 && lane == 31) wtot[warp] = inc;
+    for (int w = 0; w < kCWarps; ++w)
+      if (tid < 256) wcnt[w][tid] = 0;
+    __syncthreads();
+    if (tid < 256) {
+      uint32_t bw = 0;
+      for (int w = 0; w < warp; ++w) bw += wtot[w];
+      toff[tid] = bw + inc - tot + before;
+    }
+    __syncthreads();
+    if (!skip) {
+      // Count per warp and digit, in item order.
+      for (uint32_t b = wlo; b < whi; b += 32) {
+        const uint32_t i = b + lane;
+        const bool ok = i < whi;
+        const uint32_t d = ok ? uint32_t((cur[i] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      if (tid < 256) {
+        uint32_t run = toff[tid];
+        for (int w = 0; w < kCWarps; ++w) {
+          const uint32_t c = wcnt[w][tid];
+          wcnt[w][tid] = run;
+          run += c;
+        }
+      }
+      __syncthreads();
+      // Rank and store into the owner CTA's buffer.
+      for (uint32_t b = wlo; b < whi; b += 32) {
+        const uint32_t i = b + lane;
+        const bool ok = i < whi;
+        const uint64_t key = ok ? cur[i] : 0ull;
+        const uint32_t d = ok ? uint32_t((key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t pos = 0;
+        if (ok) pos = wcnt[warp][d] + __popc(peers & lanemask_lt());
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+        __syncwarp();
+        if (ok) {
+          const uint32_t dst = pos / per;
+          cluster.map_shared_rank(nxt, dst)[pos - dst * per] = key;
+        }
+      }
+    }
+    cluster.sync();
+    if (!skip) {
+      uint64_t* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  }
+
+  // Outputs: internal cells, the caller's copy, and the cell numbers.
+  const bool user = o.user_cells && int64_t(n) <= o.user_cap;
+  const int wc = (o.ell + o.word_bits - 1) / o.word_bits;
+  for (uint32_t i = tid; i < cnt; i += kCThreads) {
+    const uint64_t key = cur[i];
+    const uint32_t g = lo + i;
+    o.cells[g] = key;
+    if (user) {
+      if (o.word_bits == 64) {
+        static_cast<uint64_t*>(o.user_cells)[g] = key;
+      } else {
+        uint32_t* u32 = static_cast<uint32_t*>(o.user_cells) + uint64_t(g) * wc;
+        for (int c = 0; c < wc; ++c) u32[c] = uint32_t(key >> (32 * c));
+      }
+    }
+    if (key == kEmpty) {
+      o.t.ctr->ones_rank = g;
+    } else {
+      const int64_t slot = small_find_slot(o.t.keys, o.t.mask, o.t.shift, key);
+      if (slot >= 0) o.t.vals[slot] = g;
+      else atomicOr(&o.t.ctr->error, 1u);
+    }
+  }
+}
+
 }  // namespace
 
 size_t scan_scratch_bytes(size_t max_n) {
@@ -314,6 +463,62 @@ cudaError_t radix_sort_u64(uint64_t* keys0, uint64_t* keys1, uint32_t* vals0, ui
     if (e != cudaSuccess) return e;
     std::swap(kin, kout);
     std::swap(vin, vout);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace cg
+
+namespace cg {
+
+cudaError_t cluster_sort_small(const uint64_t* in, size_t max_n, int bits,
+                               const ClusterSortOut& o, cudaStream_t s, bool* done) {
+  *done = false;
+  constexpr size_t kStaticSmem = 20 * 1024;
+  constexpr size_t kMaxDyn = 227 * 1024 - kStaticSmem;
+  static int cluster16 = -1;  // 1 if a 16-CTA cluster of this kernel can run
+  for (int C : {16, 8}) {
+    const size_t per = (max_n + C - 1) / C;
+    const size_t dyn = 2 * std::max<size_t>(per, 1) * sizeof(uint64_t);
+    if (dyn > kMaxDyn) continue;
+    auto kern = cluster_sort_kernel;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(dyn));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(kCThreads, 1, 1);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (C == 16) {
+      if (cluster16 == 0) continue;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        cluster16 = 0;
+        continue;
+      }
+      int nclusters = 0;
+      e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+      if (e != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        cluster16 = 0;
+        continue;
+      }
+      cluster16 = 1;
+    }
+    e = cudaLaunchKernelEx(&cfg, kern, in, uint32_t(max_n), bits, o, uint32_t(per));
+    count_launch();
+    if (e != cudaSuccess) return e;
+    *done = true;
+    return cudaGetLastError();
   }
   return cudaSuccess;
 }

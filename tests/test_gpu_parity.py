@@ -362,15 +362,26 @@ def test_full_size_chains(dev):
     dist = popcount64(base_par ^ base_chi).sum(axis=1)
     keep = dist == 1
     assert keep.mean() > 0.99
-    # locate rows through a 64-bit linear fingerprint, then verify whole rows
-    w = np.random.default_rng(1).integers(1, 2**63, size=got_c.shape[1], dtype=np.uint64) | 1
-    fc = (got_c * w).sum(axis=1, dtype=np.uint64)
+    # locate rows through a 64-bit row hash (MurmurHash3 finaliser of every
+    # word, XOR-combined), then verify whole rows
+    def row_hash(rows):
+        h = np.zeros(rows.shape[0], dtype=np.uint64)
+        for j in range(rows.shape[1]):
+            x = rows[:, j] ^ np.uint64((0x9E3779B97F4A7C15 * (j + 1)) % 2**64)
+            x = x ^ (x >> np.uint64(33))
+            x = x * np.uint64(0xFF51AFD7ED558CCD)
+            x = x ^ (x >> np.uint64(33))
+            x = x * np.uint64(0xC4CEB9FE1A85EC53)
+            x = x ^ (x >> np.uint64(33))
+            h ^= x
+        return h
+
+    fc = row_hash(got_c)
     fo = np.argsort(fc, kind="stable")
     fs = fc[fo]
 
     def find(q):
-        fq = (q * w).sum(axis=1, dtype=np.uint64)
-        idx = fo[np.clip(np.searchsorted(fs, fq), 0, len(fs) - 1)]
+        idx = fo[np.clip(np.searchsorted(fs, row_hash(q)), 0, len(fs) - 1)]
         assert (got_c[idx] == q).all()
         return idx.astype(np.int64)
 
