@@ -170,6 +170,30 @@ cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const
                         int64_t cells_cap, int64_t* n_cells, uint32_t* edges,
                         int64_t edges_cap, int64_t* n_edges, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free neighbour search. The paper has no counterpart: this is a
+ * deployment variant of cg_neighbors_h1 (HASH strategy, 1 <= l <= 64) for
+ * callers that cannot allocate device memory at the point of the call (fixed
+ * memory budgets, real-time loops, hosts whose allocator belongs to another
+ * framework). All scratch (hash table, look-back words, counters) lives in one
+ * fixed array of about 2.1 MB compiled into the library, present on every
+ * device that loads it until the process exits; the call itself allocates
+ * nothing. Arguments, outputs, ordering and errors are those of
+ * cg_neighbors_h1, plus:
+ *   - at most CG_NOALLOC_MAX_CELLS cells; more gives CG_ERR_INVALID_ARG before
+ *     any work is enqueued;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - every call reuses the same array (each call clears what must start at
+ *     zero); calls whose work overlaps on the GPU race and give undefined
+ *     results, so serialise them.
+ * ------------------------------------------------------------------------- */
+#define CG_NOALLOC_MAX_CELLS 65536
+cg_status cg_neighbors_h1_noalloc(const void* cells, int64_t n_cells, int ell, int word_bits,
+                                  uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

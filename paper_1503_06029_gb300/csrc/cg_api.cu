@@ -367,6 +367,10 @@ static cg_status ensure_io(cg_ctx* ctx, size_t bytes) {
   return CG_OK;
 }
 
+namespace cg {
+void set_last_error(const char* msg) { t_err = msg; }
+}  // namespace cg
+
 extern "C" {
 
 const char* cg_last_error(void) { return t_err.c_str(); }

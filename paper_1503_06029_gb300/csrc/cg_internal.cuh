@@ -64,6 +64,7 @@ __host__ __device__ __forceinline__ uint64_t fp_bit(int k) {
 // Launch bookkeeping (cg_api.cu).
 // ---------------------------------------------------------------------------
 void count_launch(int n = 1);
+void set_last_error(const char* msg);  // message returned by cg_last_error()
 int sm_count();  // SMs of the current device (cached per device)
 
 // ---------------------------------------------------------------------------
