@@ -5,6 +5,7 @@
 // (§3.2) -> Hamming-1 search from every cell (Algorithm 4) -> edge compaction.
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -111,6 +112,7 @@ struct SmallWs {
   void* scan;
   uint64_t* cells;  // sorted cells (given cells for the neighbour search)
   unsigned long long* status;  // look-back words of the single-pass edge kernel
+  uint32_t* spill;             // tiles left by the tensor-core sign kernel
   size_t cap, ucap;
   SmallTable table(bool with_list) const {
     return SmallTable{tkeys, tvals, uint32_t(cap - 1), table_shift(cap),
@@ -119,7 +121,7 @@ struct SmallWs {
 };
 
 SmallWs carve_small(Carve& c, size_t cap, size_t ucap, int ell, bool dedup, bool neigh,
-                    bool given_cells) {
+                    bool given_cells, size_t n_points = 0) {
   SmallWs w{};
   w.cap = cap;
   w.ucap = ucap;
@@ -134,6 +136,7 @@ SmallWs carve_small(Carve& c, size_t cap, size_t ucap, int ell, bool dedup, bool
   }
   if (given_cells) w.cells = c.take<uint64_t>(ucap);
   if (neigh) w.status = c.take<unsigned long long>(ne_status_words(ucap));
+  if (n_points) w.spill = c.take<uint32_t>((n_points + 127) / 128 + 1);
   (void)nh;
   return w;
 }
@@ -601,7 +604,7 @@ cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const in
   const size_t ucap = std::min(un, cap / 2);
   const bool small = ell <= 64;
   Carve m{nullptr};
-  if (small) carve_small(m, cap, ucap, ell, true, true, false);
+  if (small) carve_small(m, cap, ucap, ell, true, true, false, un);
   else carve_wide(m, un, cap, ucap, ell, true, true, false, true);
   cg_status st = ensure_pool(ctx, m.off + 256);
   if (st) return st;
@@ -610,11 +613,19 @@ cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const in
   ctx->n_marks = 0;
   mark(ctx, "start", s);
   if (small) {
-    SmallWs w = carve_small(c, cap, ucap, ell, true, true, false);
+    SmallWs w = carve_small(c, cap, ucap, ell, true, true, false, un);
     CG_CUDA(launch_clear_build(w.tkeys, cap, w.status, ne_status_words(ucap), w.ctr, s),
             "clearing table");
     mark(ctx, "clear", s);
-    if (n > 0) CG_CUDA(launch_pack_insert(pa, w.table(true), s), "sign vectors + dedup");
+    if (n > 0) {
+      // FMA sign kernel by default; CG_SIGN_KERNEL=tc selects the tensor-core
+      // one (exact as well; slower on the benchmark workload).
+      const char* sk = std::getenv("CG_SIGN_KERNEL");
+      const bool tc = sk && std::strcmp(sk, "tc") == 0;
+      CG_CUDA(tc ? launch_pack_tc_insert(pa, w.table(true), w.spill, s)
+                 : launch_pack_insert(pa, w.table(true), s),
+              "sign vectors + dedup");
+    }
     mark(ctx, "pack_dedup", s);
     st = dedup_small_tail(w, ell, word_bits, cells, cells_cap, s);
     if (st) return st;

@@ -25,7 +25,8 @@ struct DevCounters {
   unsigned int ones_rank;     // its cell number
   unsigned int error;         // device-side consistency failures (bit set)
   unsigned int ticket;        // work counter of the single-pass edge kernel
-  unsigned int pad[8];
+  unsigned int tc_spill;      // tiles the tensor-core sign kernel left to the fp32 one
+  unsigned int pad[7];
 };
 
 // Bits of DevCounters::error.
@@ -77,6 +78,10 @@ struct PackArgs {
   const int32_t* a;
   const int64_t* b;
   int ell;
+  // Optional list of 128-point tiles to process (instead of all points):
+  // tiles[0 .. *n_tiles) are tile numbers (points [128 t, 128 t + 128)).
+  const uint32_t* tiles = nullptr;
+  const unsigned int* n_tiles = nullptr;
 };
 
 // keys[n][W] in word_bits-bit words.
@@ -104,6 +109,11 @@ inline int table_shift(size_t cap) {
 // Fused steps 1-2 for l <= 64: every vector goes straight into the table
 // (no vector is written to memory); distinct vectors are appended to ulist.
 cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStream_t s);
+// Same on the tensor cores (cg_pack_tc.cu): l <= 64, d <= 4; tiles outside the
+// exact-split ranges are evaluated in fp32 with exact re-evaluation.
+// spill_tiles: ceil(n / 128) words of scratch.
+cudaError_t launch_pack_tc_insert(const PackArgs& pa, const SmallTable& t, uint32_t* spill_tiles,
+                                  cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Device helpers used by several translation units.

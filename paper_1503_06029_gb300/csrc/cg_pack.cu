@@ -273,7 +273,6 @@ __global__ void __launch_bounds__(kThreads)
 // points exceed that bound builds its own rows in a private slice of shared
 // memory, so the error bound always covers the points it is applied to.
 // ---------------------------------------------------------------------------
-constexpr int kFP = 8;  // points per thread (upper bound over the variants)
 constexpr int kFThreads = 256;
 constexpr int kFWarps = kFThreads / 32;
 
@@ -374,16 +373,22 @@ __global__ void __launch_bounds__(kFThreads)
   __shared__ uint32_t mblk[D];
   const int lane = threadIdx.x & 31;
   const int64_t n = pa.n;
-  const int64_t n_wt = (n + kWarpPts - 1) / kWarpPts;
+  // Work items: all warp tiles, or (when a tile list is given, P == 4) the
+  // listed 128-point tiles.
+  const bool listed = pa.tiles != nullptr && P == 4;
+  if (pa.tiles != nullptr && P != 4) return;
+  const int64_t n_all = (n + kWarpPts - 1) / kWarpPts;
+  const int64_t n_wt = listed ? (int64_t(*pa.n_tiles) < n_all ? int64_t(*pa.n_tiles) : n_all) : n_all;
   const int64_t stride = int64_t(gridDim.x) * kFWarps;
-  int64_t wt = int64_t(blockIdx.x) * kFWarps + (threadIdx.x >> 5);
+  int64_t it = int64_t(blockIdx.x) * kFWarps + (threadIdx.x >> 5);
 
   // Block set-up: bound from every warp's first tile, rows for that bound.
   if (threadIdx.x < D) mblk[threadIdx.x] = 0;
   __syncthreads();
   {
     int32_t pi[P][D];
-    load_points<D, P>(pa, wt * kWarpPts + lane * P, vec_ok, pi);
+    const int64_t wt0 = it < n_wt ? (listed ? int64_t(pa.tiles[it]) : it) : n_all;
+    load_points<D, P>(pa, wt0 * kWarpPts + lane * P, vec_ok, pi);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       uint32_t m = 0;
@@ -404,7 +409,8 @@ __global__ void __launch_bounds__(kFThreads)
   __syncthreads();
   bool priv_ok = false;
 
-  for (; wt < n_wt; wt += stride) {
+  for (; it < n_wt; it += stride) {
+    const int64_t wt = listed ? int64_t(pa.tiles[it]) : it;
     const int64_t p0 = wt * kWarpPts + int64_t(lane) * P;
     int32_t pi[P][D];
     load_points<D, P>(pa, p0, vec_ok, pi);

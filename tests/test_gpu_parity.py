@@ -234,6 +234,48 @@ def test_build_ties_and_extremes(ctx, dev):
         assert np.array_equal(edges_np(edges), want_e)
 
 
+def test_build_ties_inside_tensor_range(ctx, dev):
+    """Exact ties (a . p = b) and off-by-one values with every magnitude inside
+    the range of the exact fp16 split: the tensor-core path must decide them."""
+    rng = np.random.default_rng(31)
+    ell, n = 64, 200_000
+    a = rng.integers(-1024, 1025, size=(ell, 3)).astype(np.int32)
+    pts = rng.integers(-(1 << 19), (1 << 19) + 1, size=(n, 3)).astype(np.int32)
+    anchors = pts[rng.integers(0, n, size=ell)]
+    b = (a.astype(np.int64) * anchors).sum(axis=1) + rng.integers(-1, 2, size=ell)
+    pts[: n // 2] = anchors[rng.integers(0, ell, size=n // 2)]  # many points on planes
+    cells, edges = ctx.build(T(pts, dev), T(a, dev), T(b.astype(np.int64), dev), 64)
+    want_c, want_e = oracle.build(pts, a, b, 64)
+    assert np.array_equal(words_np(cells, 64), want_c)
+    assert np.array_equal(edges_np(edges), want_e)
+
+
+def test_build_mixed_tile_ranges(ctx, dev):
+    """Some 128-point tiles hold coordinates beyond the exact-split range
+    (|p| >= 2^22): those tiles go through the fp32 path, the rest through the
+    tensor cores; together they must still match the oracle."""
+    sc = inputs.planes_3d(n=300_000, ell=64, seed=41)
+    pts = sc.pts.copy()
+    rng = np.random.default_rng(5)
+    far = rng.choice(len(pts), size=300, replace=False)
+    pts[far] = rng.integers(-(1 << 26), 1 << 26, size=(300, 3)).astype(np.int32)
+    cells, edges = ctx.build(T(pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
+    want_c, want_e = oracle.build(pts, sc.a, sc.b, 64)
+    assert np.array_equal(words_np(cells, 64), want_c)
+    assert np.array_equal(edges_np(edges), want_e)
+
+
+@pytest.mark.parametrize("kernel", ["tc", "ffma"])
+def test_build_both_sign_kernels(ctx, dev, kernel, monkeypatch):
+    monkeypatch.setenv("CG_SIGN_KERNEL", kernel)
+    for sc, wb in [(inputs.lines_2d(), 32), (inputs.planes_3d(n=250_001, ell=64, seed=42), 64),
+                   (inputs.planes_3d(n=99_999, ell=20, seed=43), 64)]:
+        cells, edges = ctx.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), wb)
+        want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, wb)
+        assert np.array_equal(words_np(cells, wb), want_c)
+        assert np.array_equal(edges_np(edges), want_e)
+
+
 def test_build_all_ones_vector(ctx, dev):
     # l = 64, constraints 1..63 always hold (0 >= 0); constraint 0 is x >= 0:
     # the cells are ~0 - 1 and ~0 (the all-ones vector, kept off the table).
