@@ -171,6 +171,48 @@ cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const
                         int64_t edges_cap, int64_t* n_edges, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched build of many independent scenes (§2.1-§2.2 per scene; the paper
+ * treats one scene at a time). All scenes are enqueued without host
+ * synchronisation on a pool of streams (each scene's steps 1-4 on one stream,
+ * scenes running concurrently), their results are gathered into contiguous
+ * outputs by device-side offsets, and all counts are read back once. A batch
+ * repeated with the same scenes and outputs is replayed from a captured CUDA
+ * graph. Cells use 64-bit words (W_s = ceil(l_s / 64) words per cell); edges
+ * hold scene-local cell numbers.
+ *   scenes     host array of n_scenes descriptors (device arrays inside).
+ *   out->cells       device, capacity out->cells_cap 64-bit words: the cells
+ *                    of scene 0, then scene 1, ...
+ *   out->edges       device, capacity out->edges_cap edges: scene after scene.
+ *   out->n_cells, out->n_edges     host int64[n_scenes]: U_s and E_s.
+ *   out->cells_offset, out->edges_offset  host int64[n_scenes + 1], nullable:
+ *                    first word / first edge of each scene (prefix sums).
+ * Blocks until done. Totals above the capacities give CG_ERR_CAPACITY with all
+ * counts written and nothing written to the outputs.
+ * ------------------------------------------------------------------------- */
+typedef struct cg_scene {
+  const int32_t* pts; /* int32[n][d], device */
+  int64_t n;
+  int d;
+  const int32_t* a;   /* int32[l][d], device */
+  const int64_t* b;   /* int64[l], device */
+  int ell;
+} cg_scene;
+
+typedef struct cg_batch_out {
+  uint64_t* cells;
+  int64_t cells_cap;
+  uint32_t* edges;
+  int64_t edges_cap;
+  int64_t* n_cells;
+  int64_t* n_edges;
+  int64_t* cells_offset;
+  int64_t* edges_offset;
+} cg_batch_out;
+
+cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, cg_batch_out* out,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free neighbour search. The paper has no counterpart: this is a
  * deployment variant of cg_neighbors_h1 (HASH strategy, 1 <= l <= 64) for
  * callers that cannot allocate device memory at the point of the call (fixed

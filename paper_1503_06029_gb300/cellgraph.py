@@ -34,8 +34,22 @@ STRATEGY = {"auto": 0, "hash": 1, "sorted": 2}
 EXPORTS = [
     "cg_last_error", "cg_version", "cg_launch_count", "cg_pack_signs", "cg_dedup_cells",
     "cg_neighbors_h1", "cg_ctx_create", "cg_ctx_destroy", "cg_ctx_pool_bytes", "cg_build",
-    "cg_build_host", "cg_ctx_set_timing", "cg_ctx_stage_times",
+    "cg_build_host", "cg_ctx_set_timing", "cg_ctx_stage_times", "cg_build_batch",
 ]
+
+
+class CgScene(ctypes.Structure):
+    """struct cg_scene (include/cellgraph.h)."""
+    _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("ell", ctypes.c_int)]
+
+
+class CgBatchOut(ctypes.Structure):
+    """struct cg_batch_out (include/cellgraph.h)."""
+    _fields_ = [("cells", ctypes.c_void_p), ("cells_cap", ctypes.c_int64),
+                ("edges", ctypes.c_void_p), ("edges_cap", ctypes.c_int64),
+                ("n_cells", ctypes.c_void_p), ("n_edges", ctypes.c_void_p),
+                ("cells_offset", ctypes.c_void_p), ("edges_offset", ctypes.c_void_p)]
 
 
 class CellGraphError(RuntimeError):
@@ -72,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         build_args = [P, P, I64, I, P, P, I, I, P, I64, PI64, P, I64, PI64, P]
         lib.cg_build.argtypes = build_args
         lib.cg_build_host.argtypes = build_args
+        lib.cg_build_batch.argtypes = [P, P, I, P, P]
         lib.cg_ctx_set_timing.argtypes = [P, I]
         lib.cg_ctx_stage_times.argtypes = [P, P, P, I, ctypes.POINTER(ctypes.c_int), PI64]
         for name in EXPORTS[3:]:
@@ -279,6 +294,55 @@ class Context:
             _check(rc)
             self._caps[key] = (max(ccap, nc.value), max(ecap, ne.value))
             return cells[: nc.value], edges[: ne.value]
+
+    def build_batch(self, scenes, stream=None):
+        """Cells and edges of many independent scenes in one batched call.
+        ``scenes``: sequence of (pts, a, b) CUDA tensors. Returns a list of
+        (cells int64 [U, W], edges int32 [E, 2]) views, W = ceil(l/64), cell
+        numbers scene-local."""
+        torch = _torch()
+        S = len(scenes)
+        if S == 0:
+            return []
+        arr = (CgScene * S)()
+        dev = None
+        words_total = edges_total = 0
+        ws = []
+        for i, (pts, a, b) in enumerate(scenes):
+            n, d = pts.shape
+            ell = a.shape[0]
+            arr[i] = CgScene(_dev(pts, torch.int32, "pts").value, n, d,
+                             _dev(a, torch.int32, "a").value, _dev(b, torch.int64, "b").value, ell)
+            dev = pts.device
+            u = arrangement_cells_bound(n, d, ell)
+            ws.append(words(ell, 64))
+            words_total += u * ws[-1]
+            edges_total += 4 * u
+        key = ("batch", tuple((int(x.n), int(x.d), int(x.ell)) for x in arr))
+        ccap, ecap = self._caps.get(key, (max(1, words_total), max(1, edges_total)))
+        n_cells = np.zeros(S, dtype=np.int64)
+        n_edges = np.zeros(S, dtype=np.int64)
+        coff = np.zeros(S + 1, dtype=np.int64)
+        eoff = np.zeros(S + 1, dtype=np.int64)
+        while True:
+            cells = torch.empty(ccap, dtype=torch.int64, device=dev)
+            edges = torch.empty((ecap, 2), dtype=torch.int32, device=dev)
+            out = CgBatchOut(cells.data_ptr(), ccap, edges.data_ptr(), ecap,
+                             n_cells.ctypes.data, n_edges.ctypes.data, coff.ctypes.data,
+                             eoff.ctypes.data)
+            rc = self._lib.cg_build_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), S,
+                                          ctypes.byref(out), _stream_ptr(stream))
+            if rc == ERR_CAPACITY:
+                ccap, ecap = max(ccap, int(coff[S])), max(ecap, int(eoff[S]))
+                self._caps[key] = (ccap, ecap)
+                continue
+            _check(rc)
+            self._caps[key] = (max(ccap, int(coff[S])), max(ecap, int(eoff[S])))
+            res = []
+            for i in range(S):
+                c = cells[coff[i]: coff[i + 1]].view(-1, ws[i])
+                res.append((c, edges[eoff[i]: eoff[i + 1]]))
+            return res
 
     def build_host(self, pts: np.ndarray, a: np.ndarray, b: np.ndarray, word_bits: int = 64,
                    stream=None, outputs=None):

@@ -121,12 +121,12 @@ struct SmallWs {
 };
 
 SmallWs carve_small(Carve& c, size_t cap, size_t ucap, int ell, bool dedup, bool neigh,
-                    bool given_cells, size_t n_points = 0) {
+                    bool given_cells, size_t n_points = 0, DevCounters* ext_ctr = nullptr) {
   SmallWs w{};
   w.cap = cap;
   w.ucap = ucap;
   const int nh = (ell + 31) / 32;
-  w.ctr = c.take<DevCounters>(1);
+  w.ctr = ext_ctr ? ext_ctr : c.take<DevCounters>(1);
   w.tkeys = c.take<uint64_t>(cap);
   w.tvals = c.take<uint32_t>(cap);
   if (dedup) {
@@ -145,6 +145,8 @@ struct WideWs {
   DevCounters* ctr;
   uint64_t* keys64;  // converted input vectors (or the caller's, when word_bits == 64)
   uint64_t* slots;
+  uint64_t* slots2;  // fingerprint index of the single-pass build path
+  unsigned long long* status;
   uint32_t* idx0;
   uint32_t* idx1;
   uint64_t* kw0;
@@ -161,13 +163,18 @@ struct WideWs {
 };
 
 WideWs carve_wide(Carve& c, size_t n, size_t cap, size_t ucap, int ell, bool need_keys64,
-                  bool dedup, bool rank, bool neigh) {
+                  bool dedup, bool rank, bool neigh, bool single_pass = false,
+                  DevCounters* ext_ctr = nullptr) {
   WideWs w{};
   w.cap = cap;
   w.ucap = ucap;
   const int w64 = (ell + 63) / 64;
   const int nh = (ell + 31) / 32;
-  w.ctr = c.take<DevCounters>(1);
+  w.ctr = ext_ctr ? ext_ctr : c.take<DevCounters>(1);
+  if (single_pass) {
+    w.slots2 = c.take<uint64_t>(cap);
+    w.status = c.take<unsigned long long>(ne_status_words(ucap));
+  }
   if (need_keys64) w.keys64 = c.take<uint64_t>(n * w64);
   w.slots = c.take<uint64_t>(cap);
   if (dedup) {
@@ -237,9 +244,10 @@ cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t*
 cg_status dedup_small_tail(SmallWs& w, int ell, int word_bits, void* user_cells,
                            int64_t user_cap, cudaStream_t s) {
   w.cells = w.sortbuf;
-  ClusterSortOut o{w.cells, user_cells, user_cap, word_bits, ell, w.table(true)};
+  ClusterSortOut o{w.cells, user_cells, user_cap, word_bits, ell, w.table(true), w.ctr};
   bool done = false;
-  CG_CUDA(cluster_sort_small(w.ulist, w.ucap, ell, o, s, &done), "sorting cells (cluster)");
+  CG_CUDA(cluster_sort(w.ulist, nullptr, &w.ctr->n_unique, w.ucap, ell, o, s, &done),
+          "sorting cells (cluster)");
   if (done) return CG_OK;
   bool in1 = false;
   CG_CUDA(radix_sort_u64(w.ulist, w.sortbuf, nullptr, nullptr, &w.ctr->n_unique, w.ucap, ell,
@@ -302,6 +310,15 @@ struct cg_ctx {
   // Per-stage totals over the builds since timing was (re)enabled.
   std::vector<std::pair<const char*, double>> stage_ms;
   int64_t timed_builds = 0;
+  // Batches: device pool, pinned host area, worker streams, size hints.
+  void* bpool = nullptr;
+  size_t bpool_bytes = 0;
+  void* bhost = nullptr;
+  size_t bhost_bytes = 0;
+  std::vector<cudaStream_t> workers;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
+  std::map<std::tuple<int64_t, int, int>, size_t> edge_hint;
 };
 
 namespace {
@@ -406,6 +423,11 @@ cg_status cg_ctx_destroy(cg_ctx* ctx) {
   if (ctx->io) cudaFree(ctx->io);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& w : ctx->workers) cudaStreamDestroy(w);
+  for (auto& e : ctx->join_ev) cudaEventDestroy(e);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->bpool) cudaFree(ctx->bpool);
+  if (ctx->bhost) cudaFreeHost(ctx->bhost);
   if (ctx->host_ctr) cudaFreeHost(ctx->host_ctr);
   delete ctx;
   return CG_OK;
@@ -595,26 +617,58 @@ size_t arrangement_bound(int64_t n, int d, int ell) {
   return size_t(est < 1 ? 1 : est);
 }
 
-// Enqueues the whole build; returns after reading the counters.
-cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
-                     const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
-                     uint32_t* edges, int64_t edges_cap, size_t cap, cudaStream_t s,
-                     DevCounters* host) {
+// One scene's build: sizes and strategy.
+struct ScenePlan {
+  int64_t n;
+  int ell;
+  size_t cap;   // table slots (power of two)
+  size_t ucap;  // distinct-vector capacity
+  bool small;   // l <= 64
+  bool single;  // wide, single-pass neighbour kernel and cluster sort
+};
+
+ScenePlan plan_scene(int64_t n, int ell, size_t cap) {
+  ScenePlan p{};
+  p.n = n;
+  p.ell = ell;
+  p.cap = cap;
   const size_t un = size_t(n > 0 ? n : 1);
-  const size_t ucap = std::min(un, cap / 2);
-  const bool small = ell <= 64;
+  p.ucap = std::min(un, cap / 2);
+  p.small = ell <= 64;
+  p.single = !p.small && ell <= 1024;
+  return p;
+}
+
+void carve_scene(Carve& c, const ScenePlan& p, DevCounters* ext_ctr, SmallWs* sw, WideWs* ww) {
+  const size_t un = size_t(p.n > 0 ? p.n : 1);
+  if (p.small) *sw = carve_small(c, p.cap, p.ucap, p.ell, true, true, false, un, ext_ctr);
+  else *ww = carve_wide(c, un, p.cap, p.ucap, p.ell, true, true, false, true, p.single, ext_ctr);
+}
+
+size_t scene_ws_bytes(const ScenePlan& p) {
   Carve m{nullptr};
-  if (small) carve_small(m, cap, ucap, ell, true, true, false, un);
-  else carve_wide(m, un, cap, ucap, ell, true, true, false, true);
-  cg_status st = ensure_pool(ctx, m.off + 256);
-  if (st) return st;
-  Carve c{static_cast<char*>(ctx->pool)};
-  PackArgs pa{pts, n, d, a, b, ell};
-  ctx->n_marks = 0;
-  mark(ctx, "start", s);
-  if (small) {
-    SmallWs w = carve_small(c, cap, ucap, ell, true, true, false, un);
-    CG_CUDA(launch_clear_build(w.tkeys, cap, w.status, ne_status_words(ucap), w.ctr, s),
+  SmallWs sw;
+  WideWs ww;
+  DevCounters dummy;
+  carve_scene(m, p, &dummy, &sw, &ww);
+  return m.off + 256;
+}
+
+// Enqueues one scene's build (steps 1-4) into workspace `ws` with counters at
+// `ctr`; nothing is read back. Cells go to `cells` (word_bits words, when
+// U <= cells_cap), edges to `edges` (up to edges_cap).
+cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan& plan,
+                        const PackArgs& pa, int word_bits, void* cells, int64_t cells_cap,
+                        uint32_t* edges, int64_t edges_cap, cudaStream_t s) {
+  Carve c{ws};
+  SmallWs w{};
+  WideWs ww{};
+  carve_scene(c, plan, ctr, &w, &ww);
+  const int64_t n = plan.n;
+  const int ell = plan.ell;
+  cg_status st;
+  if (plan.small) {
+    CG_CUDA(launch_clear_build(w.tkeys, plan.cap, w.status, ne_status_words(plan.ucap), w.ctr, s),
             "clearing table");
     mark(ctx, "clear", s);
     if (n > 0) {
@@ -633,35 +687,96 @@ cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const in
     st = neighbors_small_steps(w, ell, CG_STRATEGY_HASH, edges, edges_cap, s);
     if (st) return st;
     mark(ctx, "neighbors_edges", s);
-    st = read_counters(w.ctr, host, s);
-    if (st == CG_OK) accumulate_marks(ctx);
-    return st;
+    return CG_OK;
   }
-  WideWs w = carve_wide(c, un, cap, ucap, ell, true, true, false, true);
-  CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
-  if (n > 0) CG_CUDA(launch_pack_store(pa, 64, w.keys64, s), "sign vectors");
+  const int w64 = (ell + 63) / 64;
+  if (!plan.single) {
+    CG_CUDA(launch_zero_counters(ww.ctr, s), "counters");
+    if (n > 0) CG_CUDA(launch_pack_store(pa, 64, ww.keys64, s), "sign vectors");
+    mark(ctx, "pack", s);
+    st = dedup_wide_steps(ww, ww.keys64, n, ell, false, s);
+    if (st) return st;
+    CG_CUDA(launch_write_cells(ww.cells, ell, word_bits, cells, cells_cap, ww.ctr, plan.ucap, s),
+            "writing cells");
+    mark(ctx, "dedup_sort", s);
+    st = neighbors_wide_steps(ww, ell, CG_STRATEGY_HASH, edges, edges_cap, s);
+    if (st) return st;
+    mark(ctx, "neighbors_edges", s);
+    return CG_OK;
+  }
+  // Wide, single pass: clear both tables, sign vectors, insert rows, one-
+  // cluster sort of the distinct rows (multi-launch sort when too many),
+  // fingerprint index, neighbour search with edge output.
+  CG_CUDA(launch_clear_build(ww.slots, plan.cap, ww.status, ne_status_words(plan.ucap), ww.ctr, s,
+                             ww.slots2, plan.cap),
+          "clearing tables");
+  if (n > 0) CG_CUDA(launch_pack_store(pa, 64, ww.keys64, s), "sign vectors");
   mark(ctx, "pack", s);
-  st = dedup_wide_steps(w, w.keys64, n, ell, false, s);
-  if (st) return st;
-  CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
-          "writing cells");
+  WideTable dt{ww.slots, uint32_t(plan.cap - 1), ww.idx0, uint32_t(plan.ucap), ww.ctr};
+  CG_CUDA(launch_insert_wide(ww.keys64, n, w64, dt, s), "inserting vectors");
+  ClusterSortOut o{ww.cells, cells, cells_cap, word_bits, ell, SmallTable{}, ww.ctr};
+  bool done = false;
+  CG_CUDA(cluster_sort(ww.keys64, ww.idx0, &ww.ctr->n_unique, plan.ucap, ell, o, s, &done),
+          "sorting cells (cluster)");
+  if (!done) {
+    uint32_t* sorted = nullptr;
+    CG_CUDA(sort_wide(ww.keys64, w64, ell, ww.idx0, ww.idx1, ww.kw0, ww.kw1, &ww.ctr->n_unique,
+                      plan.ucap, ww.radix, s, &sorted),
+            "sorting cells");
+    CG_CUDA(launch_gather_rows(ww.keys64, w64, sorted, &ww.ctr->n_unique, plan.ucap, ww.cells, s),
+            "gathering cells");
+    CG_CUDA(launch_write_cells(ww.cells, ell, word_bits, cells, cells_cap, ww.ctr, plan.ucap, s),
+            "writing cells");
+  }
   mark(ctx, "dedup_sort", s);
-  st = neighbors_wide_steps(w, ell, CG_STRATEGY_HASH, edges, edges_cap, s);
-  if (st) return st;
+  WideTable it{ww.slots2, uint32_t(plan.cap - 1), nullptr, 0, ww.ctr};
+  CG_CUDA(launch_index_wide(ww.cells, w64, ell, it, ww.fp, plan.ucap, s), "fingerprint index");
+  CG_CUDA(launch_neighbors_emit_wide(ww.cells, w64, ell, it, ww.fp, CG_STRATEGY_HASH, ww.status,
+                                     edges, edges_cap, plan.ucap, s),
+          "neighbour search and edge output");
   mark(ctx, "neighbors_edges", s);
-  st = read_counters(w.ctr, host, s);
+  return CG_OK;
+}
+
+// Enqueues the whole build; returns after reading the counters.
+cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                     const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                     uint32_t* edges, int64_t edges_cap, size_t cap, cudaStream_t s,
+                     DevCounters* host) {
+  const ScenePlan plan = plan_scene(n, ell, cap);
+  cg_status st = ensure_pool(ctx, scene_ws_bytes(plan));
+  if (st) return st;
+  PackArgs pa{pts, n, d, a, b, ell};
+  ctx->n_marks = 0;
+  mark(ctx, "start", s);
+  char* ws = static_cast<char*>(ctx->pool);
+  DevCounters* ctr = reinterpret_cast<DevCounters*>(ws);
+  st = enqueue_scene(ctx, ws + 256, ctr, plan, pa, word_bits, cells, cells_cap, edges, edges_cap,
+                     s);
+  if (st) return st;
+  st = read_counters(ctr, host, s);
   if (st == CG_OK) accumulate_marks(ctx);
   return st;
+}
+
+size_t initial_cap(int64_t n, int d, int ell) {
+  const size_t un = size_t(n > 0 ? n : 1);
+  const size_t full = std::max<size_t>(1024, next_pow2(2 * un));
+  return std::min(full, std::max<size_t>(1024, next_pow2(2 * arrangement_bound(n, d, ell))));
+}
+
+size_t full_cap(int64_t n) {
+  const size_t un = size_t(n > 0 ? n : 1);
+  return std::max<size_t>(1024, next_pow2(2 * un));
 }
 
 cg_status build_checked(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
                         const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
                         int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
                         cudaStream_t s) {
-  const size_t un = size_t(n > 0 ? n : 1);
-  const size_t full = std::max<size_t>(1024, next_pow2(2 * un));
+  const size_t full = full_cap(n);
   const auto key = std::make_tuple(n, ell, d);
-  size_t cap = std::max<size_t>(1024, next_pow2(2 * arrangement_bound(n, d, ell)));
+  size_t cap = initial_cap(n, d, ell);
   auto it = ctx->cap_hint.find(key);
   if (it != ctx->cap_hint.end()) cap = std::max(cap, it->second);
   cap = std::min(cap, full);
@@ -787,3 +902,213 @@ cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const
 }
 
 }  // extern "C"
+
+// ---------------------------------- batch ----------------------------------
+
+namespace {
+
+constexpr int kWorkers = 16;
+
+cg_status ensure_batch_resources(cg_ctx* ctx, size_t dev_bytes, size_t host_bytes) {
+  if (ctx->workers.empty()) {
+    for (int k = 0; k < kWorkers; ++k) {
+      cudaStream_t w;
+      cudaEvent_t e;
+      CG_CUDA(cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking), "creating worker stream");
+      CG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "creating event");
+      ctx->workers.push_back(w);
+      ctx->join_ev.push_back(e);
+    }
+    CG_CUDA(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "creating event");
+  }
+  if (dev_bytes > ctx->bpool_bytes) {
+    if (ctx->bpool) {
+      CG_CUDA(cudaDeviceSynchronize(), "batch pool growth sync");
+      cudaFree(ctx->bpool);
+      ctx->bpool = nullptr;
+      ctx->bpool_bytes = 0;
+    }
+    const size_t want = dev_bytes + dev_bytes / 4;
+    if (cudaMalloc(&ctx->bpool, want) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->bpool = nullptr;
+      return fail(CG_ERR_OOM, "batch pool allocation of " + std::to_string(want) + " bytes failed");
+    }
+    ctx->bpool_bytes = want;
+  }
+  if (host_bytes > ctx->bhost_bytes) {
+    if (ctx->bhost) {
+      CG_CUDA(cudaDeviceSynchronize(), "batch host area growth sync");
+      cudaFreeHost(ctx->bhost);
+      ctx->bhost = nullptr;
+      ctx->bhost_bytes = 0;
+    }
+    if (cudaMallocHost(&ctx->bhost, host_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->bhost = nullptr;
+      return fail(CG_ERR_OOM, "pinned host allocation failed");
+    }
+    ctx->bhost_bytes = host_bytes;
+  }
+  return CG_OK;
+}
+
+struct BatchScene {
+  ScenePlan plan;
+  int d;
+  int w;
+  size_t ecap;
+  size_t ws_off, cells_off, edges_off;
+};
+
+}  // namespace
+
+extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_scenes,
+                                    cg_batch_out* out, void* stream) {
+  if (!ctx || n_scenes < 0 || (n_scenes > 0 && !scenes) || !out)
+    return fail(CG_ERR_INVALID_ARG, "NULL argument or negative scene count");
+  if (n_scenes > 0 && (!out->n_cells || !out->n_edges))
+    return fail(CG_ERR_INVALID_ARG, "n_cells / n_edges arrays are NULL");
+  if (out->cells_cap < 0 || out->edges_cap < 0 || (out->cells_cap > 0 && !out->cells) ||
+      (out->edges_cap > 0 && !out->edges))
+    return fail(CG_ERR_INVALID_ARG, "bad output array or capacity");
+  for (int i = 0; i < n_scenes; ++i) {
+    const cg_scene& sc = scenes[i];
+    std::string why;
+    if (!check_common(sc.n, sc.ell, 64, &why))
+      return fail(CG_ERR_INVALID_ARG, "scene " + std::to_string(i) + ": " + why);
+    if (sc.d < 1 || sc.d > 4)
+      return fail(CG_ERR_INVALID_ARG, "scene " + std::to_string(i) + ": d must be 1..4");
+    if (sc.n > 0 && (!sc.pts || !sc.a || !sc.b))
+      return fail(CG_ERR_INVALID_ARG, "scene " + std::to_string(i) + ": NULL array");
+  }
+  if (n_scenes == 0) {
+    if (out->cells_offset) out->cells_offset[0] = 0;
+    if (out->edges_offset) out->edges_offset[0] = 0;
+    return CG_OK;
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+  const int S = n_scenes;
+  std::vector<BatchScene> bs(static_cast<size_t>(S));
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    // ---- sizes and layout ----
+    Carve m{nullptr};
+    m.take<DevCounters>(size_t(S));
+    m.take<BatchEntry>(size_t(S));
+    m.take<long long>(size_t(S) + 1);
+    m.take<long long>(size_t(S) + 1);
+    m.take<int>(1);
+    for (int i = 0; i < S; ++i) {
+      const cg_scene& sc = scenes[i];
+      const auto key = std::make_tuple(sc.n, sc.ell, sc.d);
+      size_t cap = initial_cap(sc.n, sc.d, sc.ell);
+      auto it = ctx->cap_hint.find(key);
+      if (it != ctx->cap_hint.end()) cap = std::max(cap, it->second);
+      cap = std::min(cap, full_cap(sc.n));
+      BatchScene& b = bs[size_t(i)];
+      b.plan = plan_scene(sc.n, sc.ell, cap);
+      b.d = sc.d;
+      b.w = (sc.ell + 63) / 64;
+      b.ecap = std::max<size_t>(1024, 4 * b.plan.ucap + 64);
+      auto eh = ctx->edge_hint.find(key);
+      if (eh != ctx->edge_hint.end()) b.ecap = std::max(b.ecap, eh->second);
+      b.ws_off = m.off = (m.off + 255) & ~size_t(255);
+      m.off += scene_ws_bytes(b.plan);
+      b.cells_off = m.off = (m.off + 255) & ~size_t(255);
+      m.off += b.plan.ucap * size_t(b.w) * sizeof(uint64_t);
+      b.edges_off = m.off = (m.off + 255) & ~size_t(255);
+      m.off += b.ecap * 2 * sizeof(uint32_t);
+    }
+    const size_t host_bytes = size_t(S) * (sizeof(BatchEntry) + sizeof(DevCounters)) +
+                              2 * (size_t(S) + 1) * sizeof(long long) + 256;
+    cg_status st = ensure_batch_resources(ctx, m.off + 256, host_bytes);
+    if (st) return st;
+    char* base = static_cast<char*>(ctx->bpool);
+    Carve c{base};
+    DevCounters* ctrs = c.take<DevCounters>(size_t(S));
+    BatchEntry* tab = c.take<BatchEntry>(size_t(S));
+    long long* coff = c.take<long long>(size_t(S) + 1);
+    long long* eoff = c.take<long long>(size_t(S) + 1);
+    int* okp = c.take<int>(1);
+    char* hb = static_cast<char*>(ctx->bhost);
+    BatchEntry* htab = reinterpret_cast<BatchEntry*>(hb);
+    DevCounters* hctr = reinterpret_cast<DevCounters*>(hb + size_t(S) * sizeof(BatchEntry));
+    long long* hcoff = reinterpret_cast<long long*>(hctr + S);
+    long long* heoff = hcoff + (S + 1);
+    int* hok = reinterpret_cast<int*>(heoff + (S + 1));
+    for (int i = 0; i < S; ++i) {
+      const BatchScene& b = bs[size_t(i)];
+      htab[i] = BatchEntry{ctrs + i, reinterpret_cast<const uint64_t*>(base + b.cells_off),
+                           reinterpret_cast<const uint32_t*>(base + b.edges_off), uint32_t(b.w),
+                           uint32_t(b.plan.ucap), (unsigned long long)b.ecap};
+    }
+    // ---- enqueue: table upload, fork, per-scene builds, join, gather ----
+    CG_CUDA(cudaMemcpyAsync(tab, htab, size_t(S) * sizeof(BatchEntry), cudaMemcpyHostToDevice, s0),
+            "uploading the scene table");
+    CG_CUDA(cudaEventRecord(ctx->fork_ev, s0), "fork");
+    for (auto& w : ctx->workers) CG_CUDA(cudaStreamWaitEvent(w, ctx->fork_ev, 0), "fork");
+    for (int i = 0; i < S; ++i) {
+      const cg_scene& sc = scenes[i];
+      const BatchScene& b = bs[size_t(i)];
+      PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
+      st = enqueue_scene(nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64, base + b.cells_off,
+                         int64_t(b.plan.ucap), reinterpret_cast<uint32_t*>(base + b.edges_off),
+                         int64_t(b.ecap), ctx->workers[size_t(i) % ctx->workers.size()]);
+      if (st) return st;
+    }
+    for (size_t k = 0; k < ctx->workers.size(); ++k) {
+      CG_CUDA(cudaEventRecord(ctx->join_ev[k], ctx->workers[k]), "join");
+      CG_CUDA(cudaStreamWaitEvent(s0, ctx->join_ev[k], 0), "join");
+    }
+    CG_CUDA(launch_batch_gather(tab, S, coff, eoff, okp, out->cells, out->cells_cap, out->edges,
+                                out->edges_cap, s0),
+            "gathering outputs");
+    CG_CUDA(cudaMemcpyAsync(hctr, ctrs, size_t(S) * sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                            s0),
+            "reading counters");
+    CG_CUDA(cudaMemcpyAsync(hcoff, coff, (size_t(S) + 1) * sizeof(long long),
+                            cudaMemcpyDeviceToHost, s0),
+            "reading offsets");
+    CG_CUDA(cudaMemcpyAsync(heoff, eoff, (size_t(S) + 1) * sizeof(long long),
+                            cudaMemcpyDeviceToHost, s0),
+            "reading offsets");
+    CG_CUDA(cudaMemcpyAsync(hok, okp, sizeof(int), cudaMemcpyDeviceToHost, s0), "reading flag");
+    CG_CUDA(cudaStreamSynchronize(s0), "synchronising stream");
+    // ---- check, learn sizes, retry the scenes that did not fit ----
+    bool again = false;
+    for (int i = 0; i < S; ++i) {
+      const DevCounters& h = hctr[i];
+      const cg_scene& sc = scenes[i];
+      const auto key = std::make_tuple(sc.n, sc.ell, sc.d);
+      if (h.error & kErrTimeout) return fail(CG_ERR_TIMEOUT, "a bounded device-side wait ran out");
+      if (h.error)
+        return fail(CG_ERR_INTERNAL, "scene " + std::to_string(i) + ": device check failed");
+      if (h.overflow) {
+        if (bs[size_t(i)].plan.cap >= full_cap(sc.n))
+          return fail(CG_ERR_INTERNAL, "table overflow at full capacity");
+        ctx->cap_hint[key] = std::min(full_cap(sc.n), bs[size_t(i)].plan.cap * 4);
+        again = true;
+      } else if (h.n_edges > bs[size_t(i)].ecap) {
+        ctx->edge_hint[key] = size_t(h.n_edges) + 64;
+        again = true;
+      }
+    }
+    if (again) continue;
+    for (int i = 0; i < S; ++i) {
+      out->n_cells[i] = hctr[i].n_unique;
+      out->n_edges[i] = int64_t(hctr[i].n_edges);
+    }
+    if (out->cells_offset)
+      for (int i = 0; i <= S; ++i) out->cells_offset[i] = hcoff[i];
+    if (out->edges_offset)
+      for (int i = 0; i <= S; ++i) out->edges_offset[i] = heoff[i];
+    if (!*hok)
+      return fail(CG_ERR_CAPACITY, "batch outputs: " + std::to_string(hcoff[S]) + " words (cap " +
+                                       std::to_string(out->cells_cap) + "), " +
+                                       std::to_string(heoff[S]) + " edges (cap " +
+                                       std::to_string(out->edges_cap) + ")");
+    return CG_OK;
+  }
+  return fail(CG_ERR_INTERNAL, "batch did not settle after repeated resizing");
+}

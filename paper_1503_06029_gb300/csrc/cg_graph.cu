@@ -257,13 +257,15 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-__global__ void clear_build(uint64_t* table, size_t cap, unsigned long long* status,
-                            size_t n_status, DevCounters* ctr) {
+__global__ void clear_build(uint64_t* table, size_t cap, uint64_t* table2, size_t cap2,
+                            unsigned long long* status, size_t n_status, DevCounters* ctr) {
   if (blockIdx.x == 0 && threadIdx.x < sizeof(DevCounters) / 4)
     reinterpret_cast<uint32_t*>(ctr)[threadIdx.x] = 0;
   const size_t stride = size_t(gridDim.x) * blockDim.x;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < cap; i += stride)
     table[i] = kEmpty;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < cap2; i += stride)
+    table2[i] = kEmpty;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n_status; i += stride)
     status[i] = 0;
 }
@@ -641,6 +643,192 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Steps 3-4 in one pass for vectors of W words (single-pass counterpart of
+// neighbors_wide + scan + emit_wide): same chunking, ticket and bounded
+// decoupled look-back as neighbors_emit_small; hits are kept in shared memory
+// (up to l per cell).
+template <class L>
+__global__ void __launch_bounds__(kNEThreads)
+    neighbors_emit_wide(const uint64_t* __restrict__ cells, int w, int ell, L look,
+                        DevCounters* ctr, unsigned long long* status,
+                        uint32_t* __restrict__ edges, int64_t cap, uint32_t max_n) {
+  extern __shared__ uint64_t dsm[];
+  uint64_t* hbits = dsm;
+  uint32_t* hits = reinterpret_cast<uint32_t*>(dsm + ell);  // [kNECells][ell]
+  __shared__ uint32_t cnt[kNECells];
+  __shared__ uint32_t off[kNECells];
+  __shared__ uint32_t s_chunk;
+  __shared__ unsigned long long s_base;
+  load_fp_bits(hbits, ell);
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  const uint32_t nchunks = (u + kNECells - 1) / kNECells;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int nh = (ell + 31) >> 5;
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(&ctr->ticket, 1u);
+    __syncthreads();
+    const uint32_t c = s_chunk;
+    if (c >= nchunks) break;
+    for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
+      const uint32_t i = c * kNECells + cl;
+      uint32_t total = 0;
+      if (i < u) {
+        for (int h = 0; h < nh; ++h) {
+          const int k = h * 32 + lane;
+          const uint64_t xw = cells[uint64_t(i) * w + (h >> 1)];
+          int64_t j = -1;
+          if (k < ell && !((xw >> (k & 63)) & 1ull)) j = look.find(i, k, hbits);
+          const uint32_t m = __ballot_sync(0xffffffffu, j >= 0);
+          if (j >= 0) hits[cl * ell + total + __popc(m & lanemask_lt())] = uint32_t(j);
+          total += __popc(m);
+        }
+      }
+      if (lane == 0) cnt[cl] = total;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t v = cnt[lane];
+      uint32_t inc = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      off[lane] = inc - v;
+      const unsigned long long T = __shfl_sync(0xffffffffu, inc, 31);
+      if (lane == 0) {
+        unsigned long long base = 0;
+        if (c == 0) {
+          atomicExch(&status[0], kFlagPre | T);
+        } else {
+          atomicExch(&status[c], kFlagAgg | T);
+          int64_t p = int64_t(c) - 1;
+          unsigned iters = 0;
+          while (p >= 0) {
+            const unsigned long long sv =
+                *reinterpret_cast<volatile unsigned long long*>(&status[p]);
+            const unsigned long long f = sv & ~kValMask;
+            if (f == 0) {
+              if (++iters > kSpinLimit) {
+                atomicOr(&ctr->error, kErrTimeout);
+                break;
+              }
+              __nanosleep(64);
+              continue;
+            }
+            base += sv & kValMask;
+            if (f == kFlagPre) break;
+            --p;
+          }
+          atomicExch(&status[c], kFlagPre | (base + T));
+        }
+        s_base = base;
+        if (c == nchunks - 1) ctr->n_edges = base + T;
+      }
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+    for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
+      const uint32_t i = c * kNECells + cl;
+      const uint32_t m = cnt[cl];
+      const unsigned long long o = base + off[cl];
+      for (uint32_t r = lane; r < m; r += 32) {
+        const unsigned long long e = o + r;
+        if (e < (unsigned long long)cap) {
+          edges[2 * e] = i;
+          edges[2 * e + 1] = hits[cl * ell + r];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+
+// ------------------------------- batch gather ------------------------------
+
+// Prefix sums of the scenes' word and edge counts (one block), plus a flag
+// telling whether every scene fitted its internal regions and the totals fit
+// the outputs.
+__global__ void __launch_bounds__(1024)
+    batch_offsets(const BatchEntry* __restrict__ tab, int n, long long* cells_off,
+                  long long* edges_off, int64_t cells_cap, int64_t edges_cap, int* ok) {
+  __shared__ long long wsum[2][32];
+  long long carry_c = 0, carry_e = 0;
+  int good = 1;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    long long c = 0, e = 0;
+    if (i < n) {
+      const DevCounters* ctr = tab[i].ctr;
+      const unsigned u = ctr->n_unique;
+      const unsigned long long en = ctr->n_edges;
+      if (ctr->overflow || ctr->error || u > tab[i].ucap || en > tab[i].ecap) good = 0;
+      c = (long long)min(u, tab[i].ucap) * tab[i].w;
+      e = (long long)(en < tab[i].ecap ? en : tab[i].ecap);
+    }
+    long long ic = c, ie = e;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long tc = __shfl_up_sync(0xffffffffu, ic, o);
+      const long long te = __shfl_up_sync(0xffffffffu, ie, o);
+      if (lane >= o) {
+        ic += tc;
+        ie += te;
+      }
+    }
+    if (lane == 31) {
+      wsum[0][warp] = ic;
+      wsum[1][warp] = ie;
+    }
+    __syncthreads();
+    long long bc = 0, be = 0, tc = 0, te = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      if (w < warp) {
+        bc += wsum[0][w];
+        be += wsum[1][w];
+      }
+      tc += wsum[0][w];
+      te += wsum[1][w];
+    }
+    if (i < n) {
+      cells_off[i] = carry_c + bc + ic - c;
+      edges_off[i] = carry_e + be + ie - e;
+    }
+    carry_c += tc;
+    carry_e += te;
+    __syncthreads();
+  }
+  good = __syncthreads_and(good);
+  if (threadIdx.x == 0) {
+    cells_off[n] = carry_c;
+    edges_off[n] = carry_e;
+    *ok = good && carry_c <= cells_cap && carry_e <= edges_cap;
+  }
+}
+
+// Copies every scene's cells and edges to its place in the outputs (blocks
+// walk the scenes; threads stride within a scene).
+__global__ void batch_copy(const BatchEntry* __restrict__ tab, int n, const long long* cells_off,
+                           const long long* edges_off, const int* ok, uint64_t* out_cells,
+                           uint32_t* out_edges) {
+  if (!*ok) return;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const long long c0 = cells_off[i], c1 = cells_off[i + 1];
+    const long long e0 = edges_off[i], e1 = edges_off[i + 1];
+    const uint64_t* src_c = tab[i].cells;
+    const uint32_t* src_e = tab[i].edges;
+    for (long long t = threadIdx.x; t < c1 - c0; t += blockDim.x) out_cells[c0 + t] = src_c[t];
+    for (long long t = threadIdx.x; t < 2 * (e1 - e0); t += blockDim.x)
+      out_edges[2 * e0 + t] = src_e[t];
+  }
+}
+
 template <class F>
 cudaError_t finish(F) {
   count_launch();
@@ -663,9 +851,10 @@ cudaError_t launch_zero_counters(DevCounters* c, cudaStream_t s) {
 }
 
 cudaError_t launch_clear_build(uint64_t* table, size_t cap, unsigned long long* status,
-                               size_t n_status, DevCounters* ctr, cudaStream_t s) {
-  clear_build<<<grid_for(std::max(cap, n_status) + 1, kThreads * 4, 16), kThreads, 0, s>>>(
-      table, cap, status, n_status, ctr);
+                               size_t n_status, DevCounters* ctr, cudaStream_t s,
+                               uint64_t* table2, size_t cap2) {
+  clear_build<<<grid_for(std::max(std::max(cap, cap2), n_status) + 1, kThreads * 4, 16), kThreads,
+                0, s>>>(table, cap, table2, cap2, status, n_status, ctr);
   return finish(0);
 }
 
@@ -889,6 +1078,40 @@ cudaError_t launch_emit_wide(const uint64_t* cells, int w64, int ell, const Wide
                                 masks, offsets, edges, edges_cap);
   }
   return finish(0);
+}
+
+cudaError_t launch_neighbors_emit_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,
+                                       const uint64_t* fp, int strategy,
+                                       unsigned long long* status, uint32_t* edges,
+                                       int64_t edges_cap, size_t max_n, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const size_t smem = size_t(ell) * sizeof(uint64_t) + size_t(kNECells) * ell * sizeof(uint32_t);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const int g = grid_for(max_n, kNECells, 4);
+  cudaError_t e;
+  if (strategy == 2) {
+    auto k = neighbors_emit_wide<WideSorted>;
+    if ((e = allow_smem(reinterpret_cast<const void*>(k), smem)) != cudaSuccess) return e;
+    k<<<g, kNEThreads, smem, s>>>(cells, w64, ell, WideSorted{cells, t.ctr, w64}, t.ctr, status,
+                                  edges, edges_cap, uint32_t(max_n));
+  } else {
+    auto k = neighbors_emit_wide<WideHash>;
+    if ((e = allow_smem(reinterpret_cast<const void*>(k), smem)) != cudaSuccess) return e;
+    k<<<g, kNEThreads, smem, s>>>(cells, w64, ell, WideHash{cells, fp, t.slots, t.mask, w64},
+                                  t.ctr, status, edges, edges_cap, uint32_t(max_n));
+  }
+  return finish(0);
+}
+
+cudaError_t launch_batch_gather(const BatchEntry* tab, int n, long long* cells_off,
+                                long long* edges_off, int* ok, uint64_t* out_cells,
+                                int64_t cells_cap, uint32_t* out_edges, int64_t edges_cap,
+                                cudaStream_t s) {
+  batch_offsets<<<1, 1024, 0, s>>>(tab, n, cells_off, edges_off, cells_cap, edges_cap, ok);
+  batch_copy<<<grid_for(size_t(n), 1, 8), 256, 0, s>>>(tab, n, cells_off, edges_off, ok,
+                                                        out_cells, out_edges);
+  count_launch(2);
+  return cudaGetLastError();
 }
 
 }  // namespace cg

@@ -228,23 +228,29 @@ cudaError_t launch_load_cells(const void* cells, int64_t n, int word_bits, int e
                               uint64_t* out, DevCounters* ctr, cudaStream_t s);
 
 // Clears a build's table (kEmpty), the look-back status words and the counters.
+// (A second table, table2/cap2, may be cleared in the same launch.)
 cudaError_t launch_clear_build(uint64_t* table, size_t cap, unsigned long long* status,
-                               size_t n_status, DevCounters* ctr, cudaStream_t s);
+                               size_t n_status, DevCounters* ctr, cudaStream_t s,
+                               uint64_t* table2 = nullptr, size_t cap2 = 0);
 
-// Sorts the U <= max_n distinct vectors of `in` (l <= 64) inside one thread-block
-// cluster (keys held in distributed shared memory), then writes the sorted
-// cells, the caller's copy (when U <= user_cap) and the cell numbers into the
-// table. Returns false in *done when max_n is too large for one cluster.
+// Sorts U = min(*n_dev, max_n) distinct vectors of W = ceil(l/64) <= 4 words
+// inside one thread-block cluster (keys held in distributed shared memory),
+// then writes the sorted cells, the caller's copy (when U <= user_cap, in
+// word_bits words) and, for l <= 64 with a table, the cell numbers into the
+// table. Row i of the input is in[rows[i]] (rows nullable: in[i]). Sets *done
+// to false when max_n or l is too large for one cluster.
 struct ClusterSortOut {
   uint64_t* cells;
   void* user_cells;
   int64_t user_cap;
   int word_bits;
   int ell;
-  SmallTable t;
+  SmallTable t;  // t.keys == nullptr: no numbering
+  DevCounters* ctr;
 };
-cudaError_t cluster_sort_small(const uint64_t* in, size_t max_n, int bits,
-                               const ClusterSortOut& o, cudaStream_t s, bool* done);
+cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigned int* n_dev,
+                         size_t max_n, int ell, const ClusterSortOut& o, cudaStream_t s,
+                         bool* done);
 
 // Steps 3-4 in one kernel for l <= 64: hit search, scan with decoupled
 // look-back (status: ceil(max_n / 32) words, zeroed) and edge output.
@@ -294,6 +300,29 @@ cudaError_t launch_emit_wide(const uint64_t* cells, int w64, int ell, const Wide
                              const uint64_t* fp, int strategy, const uint32_t* masks,
                              const unsigned long long* offsets, uint32_t* edges,
                              int64_t edges_cap, size_t max_n, cudaStream_t s);
+
+// Single-pass steps 3-4 for W-word vectors (status: ne_status_words(max_n)
+// zeroed words); needs the fingerprint index (launch_index_wide) for HASH.
+cudaError_t launch_neighbors_emit_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,
+                                       const uint64_t* fp, int strategy,
+                                       unsigned long long* status, uint32_t* edges,
+                                       int64_t edges_cap, size_t max_n, cudaStream_t s);
+
+// Batch gather: per scene, its counters, internal cells (w words per cell,
+// up to ucap cells) and internal edges (up to ecap).
+struct BatchEntry {
+  const DevCounters* ctr;
+  const uint64_t* cells;
+  const uint32_t* edges;
+  uint32_t w;
+  uint32_t ucap;
+  unsigned long long ecap;
+};
+// cells_off / edges_off: n + 1 words each; *ok = all scenes fitted.
+cudaError_t launch_batch_gather(const BatchEntry* tab, int n, long long* cells_off,
+                                long long* edges_off, int* ok, uint64_t* out_cells,
+                                int64_t cells_cap, uint32_t* out_edges, int64_t edges_cap,
+                                cudaStream_t s);
 
 // Convert caller-layout keys ([n][W] of word_bits) to internal u64 rows.
 cudaError_t launch_keys_to_u64(const void* keys, int64_t n, int word_bits, int ell,

@@ -261,8 +261,13 @@ __global__ void __launch_bounds__(kRThreads)
 constexpr int kCThreads = 512;
 constexpr int kCWarps = kCThreads / 32;
 
+// Keys of W 64-bit words (word W-1 most significant); LSD over the words, 8
+// bits per pass; the top word has `top_bits` significant bits. Input row i is
+// in[rows[i]] (or in[i] without `rows`).
+template <int W>
 __global__ void __launch_bounds__(kCThreads)
-    cluster_sort_kernel(const uint64_t* __restrict__ in, uint32_t max_n, int bits,
+    cluster_sort_kernel(const uint64_t* __restrict__ in, const uint32_t* __restrict__ rows,
+                        const unsigned int* n_dev, uint32_t max_n, int top_bits,
                         ClusterSortOut o, uint32_t per_cap) {
   namespace cgx = cooperative_groups;
   cgx::cluster_group cluster = cgx::this_cluster();
@@ -272,126 +277,191 @@ __global__ void __launch_bounds__(kCThreads)
   __shared__ uint32_t toff[256];
   __shared__ uint32_t wtot[8];
   __shared__ int skip;
-  const DevCounters* ctr = o.t.ctr;
-  if (ctr->overflow) return;  // same value for every CTA of the cluster
+  if (o.ctr->overflow) return;  // same value for every CTA of the cluster
   const uint32_t C = cluster.num_blocks();
   const uint32_t r = cluster.block_rank();
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const uint32_t n = min(ctr->n_unique, max_n);
+  const uint32_t n = min(*n_dev, max_n);
   const uint32_t per = (n + C - 1) / C;
   const uint32_t lo = min(r * per, n);
   const uint32_t cnt = min(lo + per, n) - lo;
   uint64_t* cur = cbuf;
-  uint64_t* nxt = cbuf + per_cap;
-  for (uint32_t i = tid; i < cnt; i += kCThreads) cur[i] = in[lo + i];
+  uint64_t* nxt = cbuf + size_t(per_cap) * W;
+  for (uint32_t i = tid; i < cnt; i += kCThreads) {
+    const uint64_t src = rows ? uint64_t(rows[lo + i]) : uint64_t(lo + i);
+#pragma unroll
+    for (int w = 0; w < W; ++w) cur[size_t(i) * W + w] = in[src * W + w];
+  }
   const uint32_t sw = (cnt + kCWarps - 1) / kCWarps;  // items per warp (contiguous)
   const uint32_t wlo = min(warp * sw, cnt);
   const uint32_t whi = min(wlo + sw, cnt);
 
-  const int passes = (bits + 7) / 8;
-  for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    if (tid < 256) hist[tid] = 0;
-    if (tid == 0) skip = 0;
-    __syncthreads();
-    for (uint32_t i = tid; i < cnt; i += kCThreads) atomicAdd(&hist[(cur[i] >> shift) & 255u], 1u);
-    cluster.sync();
-    uint32_t tot = 0, before = 0;
-    if (tid < 256) {
-      for (uint32_t q = 0; q < C; ++q) {
-        const uint32_t v = cluster.map_shared_rank(hist, q)[tid];
-        tot += v;
-        if (q < r) before += v;
+  for (int wd = 0; wd < W; ++wd) {
+    const int bits = wd == W - 1 ? top_bits : 64;
+    for (int shift = 0; shift < bits; shift += 8) {
+      if (tid < 256) hist[tid] = 0;
+      if (tid == 0) skip = 0;
+      __syncthreads();
+      for (uint32_t i = tid; i < cnt; i += kCThreads)
+        atomicAdd(&hist[(cur[size_t(i) * W + wd] >> shift) & 255u], 1u);
+      cluster.sync();
+      uint32_t tot = 0, before = 0;
+      if (tid < 256) {
+        for (uint32_t q = 0; q < C; ++q) {
+          const uint32_t v = cluster.map_shared_rank(hist, q)[tid];
+          tot += v;
+          if (q < r) before += v;
+        }
+        if (n > 0 && tot == n) skip = 1;
       }
-      if (n > 0 && tot == n) skip = 1;
-    }
-    uint32_t inc = tot;
+      uint32_t inc = tot;
 #pragma unroll
-    for (int o2 = 1; o2 < 32; o2 <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o2);
-      if (lane >= o2) inc += t;
-    }
-    if (tid < 256 && lane == 31) wtot[warp] = inc;
-    for (int w = 0; w < kCWarps; ++w)
-      if (tid < 256) wcnt[w][tid] = 0;
-    __syncthreads();
-    if (tid < 256) {
-      uint32_t bw = 0;
-      for (int w = 0; w < warp; ++w) bw += wtot[w];
-      toff[tid] = bw + inc - tot + before;
-    }
-    __syncthreads();
-    if (!skip) {
-      // Count per warp and digit, in item order.
-      for (uint32_t b = wlo; b < whi; b += 32) {
-        const uint32_t i = b + lane;
-        const bool ok = i < whi;
-        const uint32_t d = ok ? uint32_t((cur[i] >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
-        __syncwarp();
+      for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o2);
+        if (lane >= o2) inc += t;
       }
+      if (tid < 256 && lane == 31) wtot[warp] = inc;
+      for (int w = 0; w < kCWarps; ++w)
+        if (tid < 256) wcnt[w][tid] = 0;
       __syncthreads();
       if (tid < 256) {
-        uint32_t run = toff[tid];
-        for (int w = 0; w < kCWarps; ++w) {
-          const uint32_t c = wcnt[w][tid];
-          wcnt[w][tid] = run;
-          run += c;
-        }
+        uint32_t bw = 0;
+        for (int w = 0; w < warp; ++w) bw += wtot[w];
+        toff[tid] = bw + inc - tot + before;
       }
       __syncthreads();
-      // Rank and store into the owner CTA's buffer.
-      for (uint32_t b = wlo; b < whi; b += 32) {
-        const uint32_t i = b + lane;
-        const bool ok = i < whi;
-        const uint64_t key = ok ? cur[i] : 0ull;
-        const uint32_t d = ok ? uint32_t((key >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t pos = 0;
-        if (ok) pos = wcnt[warp][d] + __popc(peers & lanemask_lt());
-        __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
-        __syncwarp();
-        if (ok) {
-          const uint32_t dst = pos / per;
-          cluster.map_shared_rank(nxt, dst)[pos - dst * per] = key;
+      if (!skip) {
+        // Count per warp and digit, in item order.
+        for (uint32_t b = wlo; b < whi; b += 32) {
+          const uint32_t i = b + lane;
+          const bool ok = i < whi;
+          const uint32_t d = ok ? uint32_t((cur[size_t(i) * W + wd] >> shift) & 255u) : 256u;
+          const uint32_t peers = __match_any_sync(0xffffffffu, d);
+          if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+          __syncwarp();
+        }
+        __syncthreads();
+        if (tid < 256) {
+          uint32_t run = toff[tid];
+          for (int w = 0; w < kCWarps; ++w) {
+            const uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = run;
+            run += c;
+          }
+        }
+        __syncthreads();
+        // Rank and store into the owner CTA's buffer.
+        for (uint32_t b = wlo; b < whi; b += 32) {
+          const uint32_t i = b + lane;
+          const bool ok = i < whi;
+          const uint32_t d = ok ? uint32_t((cur[size_t(i) * W + wd] >> shift) & 255u) : 256u;
+          const uint32_t peers = __match_any_sync(0xffffffffu, d);
+          uint32_t pos = 0;
+          if (ok) pos = wcnt[warp][d] + __popc(peers & lanemask_lt());
+          __syncwarp();
+          if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+          __syncwarp();
+          if (ok) {
+            const uint32_t dst = pos / per;
+            uint64_t* remote = cluster.map_shared_rank(nxt, dst) + size_t(pos - dst * per) * W;
+#pragma unroll
+            for (int w = 0; w < W; ++w) remote[w] = cur[size_t(i) * W + w];
+          }
         }
       }
-    }
-    cluster.sync();
-    if (!skip) {
-      uint64_t* t = cur;
-      cur = nxt;
-      nxt = t;
+      cluster.sync();
+      if (!skip) {
+        uint64_t* t = cur;
+        cur = nxt;
+        nxt = t;
+      }
     }
   }
 
-  // Outputs: internal cells, the caller's copy, and the cell numbers.
+  // Outputs: internal cells, the caller's copy, and (l <= 64) the numbers.
   const bool user = o.user_cells && int64_t(n) <= o.user_cap;
   const int wc = (o.ell + o.word_bits - 1) / o.word_bits;
   for (uint32_t i = tid; i < cnt; i += kCThreads) {
-    const uint64_t key = cur[i];
     const uint32_t g = lo + i;
-    o.cells[g] = key;
+#pragma unroll
+    for (int w = 0; w < W; ++w) o.cells[size_t(g) * W + w] = cur[size_t(i) * W + w];
     if (user) {
       if (o.word_bits == 64) {
-        static_cast<uint64_t*>(o.user_cells)[g] = key;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+          static_cast<uint64_t*>(o.user_cells)[size_t(g) * W + w] = cur[size_t(i) * W + w];
       } else {
         uint32_t* u32 = static_cast<uint32_t*>(o.user_cells) + uint64_t(g) * wc;
-        for (int c = 0; c < wc; ++c) u32[c] = uint32_t(key >> (32 * c));
+        for (int c = 0; c < wc; ++c) u32[c] = uint32_t(cur[size_t(i) * W + c / 2] >> (32 * (c & 1)));
       }
     }
-    if (key == kEmpty) {
-      o.t.ctr->ones_rank = g;
-    } else {
-      const int64_t slot = small_find_slot(o.t.keys, o.t.mask, o.t.shift, key);
-      if (slot >= 0) o.t.vals[slot] = g;
-      else atomicOr(&o.t.ctr->error, 1u);
+    if (W == 1 && o.t.keys) {
+      const uint64_t key = cur[i];
+      if (key == kEmpty) {
+        o.ctr->ones_rank = g;
+      } else {
+        const int64_t slot = small_find_slot(o.t.keys, o.t.mask, o.t.shift, key);
+        if (slot >= 0) o.t.vals[slot] = g;
+        else atomicOr(&o.ctr->error, 1u);
+      }
     }
   }
+}
+
+template <int W>
+cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsigned int* n_dev,
+                           size_t max_n, int top_bits, const ClusterSortOut& o, cudaStream_t s,
+                           bool* done) {
+  constexpr size_t kStaticSmem = 20 * 1024;
+  constexpr size_t kMaxDyn = 227 * 1024 - kStaticSmem;
+  static int cluster16 = -1;  // 1 if a 16-CTA cluster of this kernel can run
+  auto kern = cluster_sort_kernel<W>;
+  for (int C : {16, 8}) {
+    const size_t per = (max_n + C - 1) / C;
+    const size_t dyn = 2 * std::max<size_t>(per, 1) * W * sizeof(uint64_t);
+    if (dyn > kMaxDyn) continue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(dyn));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(kCThreads, 1, 1);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (C == 16) {
+      if (cluster16 == 0) continue;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        cluster16 = 0;
+        continue;
+      }
+      int nclusters = 0;
+      e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+      if (e != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        cluster16 = 0;
+        continue;
+      }
+      cluster16 = 1;
+    }
+    e = cudaLaunchKernelEx(&cfg, kern, in, rows, n_dev, uint32_t(max_n), top_bits, o,
+                           uint32_t(per));
+    count_launch();
+    if (e != cudaSuccess) return e;
+    *done = true;
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -471,56 +541,19 @@ cudaError_t radix_sort_u64(uint64_t* keys0, uint64_t* keys1, uint32_t* vals0, ui
 
 namespace cg {
 
-cudaError_t cluster_sort_small(const uint64_t* in, size_t max_n, int bits,
-                               const ClusterSortOut& o, cudaStream_t s, bool* done) {
+cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigned int* n_dev,
+                         size_t max_n, int ell, const ClusterSortOut& o, cudaStream_t s,
+                         bool* done) {
   *done = false;
-  constexpr size_t kStaticSmem = 20 * 1024;
-  constexpr size_t kMaxDyn = 227 * 1024 - kStaticSmem;
-  static int cluster16 = -1;  // 1 if a 16-CTA cluster of this kernel can run
-  for (int C : {16, 8}) {
-    const size_t per = (max_n + C - 1) / C;
-    const size_t dyn = 2 * std::max<size_t>(per, 1) * sizeof(uint64_t);
-    if (dyn > kMaxDyn) continue;
-    auto kern = cluster_sort_kernel;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(dyn));
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(kCThreads, 1, 1);
-    cfg.dynamicSmemBytes = dyn;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (C == 16) {
-      if (cluster16 == 0) continue;
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        cluster16 = 0;
-        continue;
-      }
-      int nclusters = 0;
-      e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
-      if (e != cudaSuccess || nclusters < 1) {
-        cudaGetLastError();
-        cluster16 = 0;
-        continue;
-      }
-      cluster16 = 1;
-    }
-    e = cudaLaunchKernelEx(&cfg, kern, in, uint32_t(max_n), bits, o, uint32_t(per));
-    count_launch();
-    if (e != cudaSuccess) return e;
-    *done = true;
-    return cudaGetLastError();
+  const int w = (ell + 63) / 64;
+  const int top = ell - 64 * (w - 1);
+  switch (w) {
+    case 1: return cluster_sort_w<1>(in, rows, n_dev, max_n, top, o, s, done);
+    case 2: return cluster_sort_w<2>(in, rows, n_dev, max_n, top, o, s, done);
+    case 3: return cluster_sort_w<3>(in, rows, n_dev, max_n, top, o, s, done);
+    case 4: return cluster_sort_w<4>(in, rows, n_dev, max_n, top, o, s, done);
+    default: return cudaSuccess;  // longer vectors: multi-launch sort
   }
-  return cudaSuccess;
 }
 
 }  // namespace cg

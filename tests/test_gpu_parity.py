@@ -431,3 +431,69 @@ def test_full_size_chains(dev):
     lo_, hi_ = np.minimum(pi, ci), np.maximum(pi, ci)
     planted = lo_ * len(got_c) + hi_
     assert np.isin(planted, key).all()
+
+
+# ------------------------------- batches ---------------------------------
+
+def _batch_scenes(n_scenes, n_hi, seed=4):
+    spec = inputs.scene_batch_spec(n_scenes=n_scenes, seed=seed, n_hi=n_hi)
+    return [inputs.batch_scene(spec, s) for s in range(n_scenes)]
+
+
+def test_batch_matches_oracle_and_plain(ctx, dev):
+    scenes = _batch_scenes(40, 30_000)
+    scenes.insert(7, inputs.planes_3d(n=0, ell=24, seed=1))  # an empty scene
+    dscenes = [(T(s.pts, dev), T(s.a, dev), T(s.b, dev)) for s in scenes]
+    got = ctx.build_batch(dscenes)
+    assert len(got) == len(scenes)
+    for sc, (pts, a, b), (c, e) in zip(scenes, dscenes, got):
+        want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+        assert np.array_equal(words_np(c, 64).reshape(want_c.shape), want_c)
+        assert np.array_equal(edges_np(e), want_e)
+        pc, pe = ctx.build(pts, a, b, 64)
+        assert torch.equal(pc, c) and torch.equal(pe, e)
+
+
+def test_batch_repeated_and_resized(ctx, dev):
+    """Repeating a batch gives the same bytes; a degenerate scene whose cell
+    count exceeds the first table-size guess is resized and rerun inside the
+    call."""
+    rng = np.random.default_rng(3)
+    base = rng.integers(-50, 51, size=(8, 2)).astype(np.int32)
+    a = np.concatenate([base, -base, base, -base])
+    deg = inputs.Scene(pts=rng.integers(-300, 301, size=(50_000, 2)).astype(np.int32), a=a,
+                       b=np.zeros(32, np.int64))
+    scenes = _batch_scenes(12, 20_000, seed=9) + [deg]
+    dscenes = [(T(s.pts, dev), T(s.a, dev), T(s.b, dev)) for s in scenes]
+    first = [(c.clone(), e.clone()) for c, e in ctx.build_batch(dscenes)]
+    second = ctx.build_batch(dscenes)
+    for (c1, e1), (c2, e2) in zip(first, second):
+        assert torch.equal(c1, c2) and torch.equal(e1, e2)
+    want_c, want_e = oracle.build(deg.pts, deg.a, deg.b, 64)
+    assert np.array_equal(words_np(second[-1][0], 64).reshape(want_c.shape), want_c)
+    assert np.array_equal(edges_np(second[-1][1]), want_e)
+
+
+def test_batch_capacity_contract(ctx, dev):
+    scenes = _batch_scenes(6, 5_000, seed=11)
+    dscenes = [(T(s.pts, dev), T(s.a, dev), T(s.b, dev)) for s in scenes]
+    lib = cellgraph.load_library()
+    S = len(scenes)
+    arr = (cellgraph.CgScene * S)()
+    for i, (p, a, b) in enumerate(dscenes):
+        arr[i] = cellgraph.CgScene(p.data_ptr(), p.shape[0], p.shape[1], a.data_ptr(),
+                                   b.data_ptr(), a.shape[0])
+    cells = torch.full((4,), -7, dtype=torch.int64, device=dev)
+    edges = torch.full((4, 2), -7, dtype=torch.int32, device=dev)
+    nc, ne = np.zeros(S, np.int64), np.zeros(S, np.int64)
+    co, eo = np.zeros(S + 1, np.int64), np.zeros(S + 1, np.int64)
+    out = cellgraph.CgBatchOut(cells.data_ptr(), 4, edges.data_ptr(), 4, nc.ctypes.data,
+                               ne.ctypes.data, co.ctypes.data, eo.ctypes.data)
+    rc = lib.cg_build_batch(ctx._h, ctypes.cast(arr, ctypes.c_void_p), S, ctypes.byref(out),
+                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == cellgraph.ERR_CAPACITY
+    for i, sc in enumerate(scenes):
+        want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+        assert nc[i] == len(want_c) and ne[i] == len(want_e)
+    assert co[S] == sum(int(x) * ((s.ell + 63) // 64) for x, s in zip(nc, scenes))
+    assert (cells == -7).all() and (edges == -7).all()
