@@ -186,6 +186,65 @@ def cpu_baseline(sample_points: int, seed: int = 2):
                       f"({len(cells)} cells, {len(edges)} edges), {dt:.2f} s single-threaded"}
 
 
+def batch_compare(ctx, dev, steps: int):
+    """The batched workload: 1,024 independent 3-D scenes, l log-uniform in
+    [8, 256] (multiple of 8), N log-uniform in [1e3, 1e6], all resident. Times
+    one cg_build_batch call per step against one pass of plain cg_build calls
+    over the same scenes on the same GPU."""
+    import torch
+
+    from paper_1503_06029_gb300 import inputs
+
+    spec = inputs.scene_batch_spec()
+    scenes = []
+    for s in range(len(spec.n)):
+        sc = inputs.batch_scene(spec, s)
+        scenes.append((torch.from_numpy(sc.pts).to(dev), torch.from_numpy(sc.a).to(dev),
+                       torch.from_numpy(sc.b).to(dev)))
+    total = int(spec.n.sum())
+    stream = torch.cuda.current_stream()
+    for _ in range(3):  # sizes learned, then captured, then replayed
+        res = ctx.build_batch(scenes)
+    cells = sum(int(c.shape[0]) for c, _ in res)
+    edges = sum(int(e.shape[0]) for _, e in res)
+    launches0 = cg_launches()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(steps):
+        ctx.build_batch(scenes)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = t0.elapsed_time(t1) / steps
+    batch_launches = (cg_launches() - launches0) // steps
+    outs = []
+    for pts, a, b in scenes:
+        c, e = ctx.build(pts, a, b, 64)
+        outs.append((torch.empty_like(c), torch.empty_like(e)))
+    passes = max(1, steps // 4)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(passes):
+        for (pts, a, b), o in zip(scenes, outs):
+            ctx.build(pts, a, b, 64, outputs=o)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = t0.elapsed_time(t1) / passes
+    return {"workload": "1,024 scenes, l in [8,256], N in [1e3,1e6] log-uniform, d=3",
+            "points": total, "cells": cells, "edges": edges,
+            "batched": {"value": total / (batch_ms * 1e-3) / 1e6, "unit": UNIT,
+                        "ms_per_batch": batch_ms, "gpu_launches_per_batch": batch_launches},
+            "plain": {"value": total / (plain_ms * 1e-3) / 1e6, "unit": UNIT,
+                      "ms_per_batch": plain_ms, "calls": len(scenes)},
+            "speedup": plain_ms / batch_ms}
+
+
+def cg_launches():
+    from paper_1503_06029_gb300 import cellgraph
+
+    return cellgraph.launch_count()
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -339,6 +398,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
+    if not args.no_batch:
+        line["batch"] = batch_compare(ctx, dev, max(3, args.steps // 2))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     ctx.close()
@@ -359,6 +420,7 @@ def main():
     p.add_argument("--cpu-sample", type=int, default=1 << 23)
     p.add_argument("--ref-sample", type=int, default=1 << 20)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")

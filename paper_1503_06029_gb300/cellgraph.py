@@ -227,6 +227,7 @@ class Context:
         _check(self._lib.cg_ctx_create(ctypes.byref(self._h), device))
         self.device = device
         self._caps = {}
+        self._bufs = {}
 
     def close(self):
         if self._h:
@@ -299,7 +300,9 @@ class Context:
         """Cells and edges of many independent scenes in one batched call.
         ``scenes``: sequence of (pts, a, b) CUDA tensors. Returns a list of
         (cells int64 [U, W], edges int32 [E, 2]) views, W = ceil(l/64), cell
-        numbers scene-local."""
+        numbers scene-local. The views share output buffers that the context
+        reuses for the next batch of the same scenes (which then replays a
+        captured CUDA graph): copy results that must outlive that call."""
         torch = _torch()
         S = len(scenes)
         if S == 0:
@@ -325,8 +328,13 @@ class Context:
         coff = np.zeros(S + 1, dtype=np.int64)
         eoff = np.zeros(S + 1, dtype=np.int64)
         while True:
-            cells = torch.empty(ccap, dtype=torch.int64, device=dev)
-            edges = torch.empty((ecap, 2), dtype=torch.int32, device=dev)
+            bufs = self._bufs.get(key)
+            if bufs is None or bufs[0].shape[0] < ccap or bufs[1].shape[0] < ecap:
+                bufs = (torch.empty(ccap, dtype=torch.int64, device=dev),
+                        torch.empty((ecap, 2), dtype=torch.int32, device=dev))
+                self._bufs[key] = bufs
+            cells, edges = bufs
+            ccap, ecap = cells.shape[0], edges.shape[0]
             out = CgBatchOut(cells.data_ptr(), ccap, edges.data_ptr(), ecap,
                              n_cells.ctypes.data, n_edges.ctypes.data, coff.ctypes.data,
                              eoff.ctypes.data)

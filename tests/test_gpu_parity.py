@@ -466,9 +466,11 @@ def test_batch_repeated_and_resized(ctx, dev):
     scenes = _batch_scenes(12, 20_000, seed=9) + [deg]
     dscenes = [(T(s.pts, dev), T(s.a, dev), T(s.b, dev)) for s in scenes]
     first = [(c.clone(), e.clone()) for c, e in ctx.build_batch(dscenes)]
-    second = ctx.build_batch(dscenes)
-    for (c1, e1), (c2, e2) in zip(first, second):
-        assert torch.equal(c1, c2) and torch.equal(e1, e2)
+    for _ in range(3):  # eager, then captured into a CUDA graph, then replayed
+        again = ctx.build_batch(dscenes)
+        for (c1, e1), (c2, e2) in zip(first, again):
+            assert torch.equal(c1, c2) and torch.equal(e1, e2)
+    second = again
     want_c, want_e = oracle.build(deg.pts, deg.a, deg.b, 64)
     assert np.array_equal(words_np(second[-1][0], 64).reshape(want_c.shape), want_c)
     assert np.array_equal(edges_np(second[-1][1]), want_e)
