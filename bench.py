@@ -166,6 +166,23 @@ class ClockSampler:
                 "nvidia_smi_samples": len(self.smi_lines)}
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """Largest x over all ranks of the process group (x itself without one)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank
+    processes units_per_rank, the job takes the slowest rank's seconds."""
+    return world * units_per_rank / seconds / 1e6
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -241,6 +258,93 @@ def batch_compare(ctx, dev, steps: int):
             "plain": {"value": total / (plain_ms * 1e-3) / 1e6, "unit": UNIT,
                       "ms_per_batch": plain_ms, "calls": len(scenes)},
             "speedup": plain_ms / batch_ms}
+
+
+def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
+                  loads=(0.25, 0.5, 0.9), pool_scenes: int = 256):
+    """Serving: Poisson arrivals (exponential gaps, seed 5) of scenes drawn as
+    in the batched workload, offered at fractions of the measured batched
+    capacity (scenes/s). Requests go through the request server with host
+    inputs in pinned memory (copied by the server after admission); a second
+    thread waits for each request in arrival order, checks its counts against
+    a plain build of the same scene, and releases it. Latency = completion on
+    the device minus submission on the host."""
+    import numpy as np
+    import torch
+
+    from paper_1503_06029_gb300 import cellgraph, inputs
+
+    spec = inputs.scene_batch_spec()
+    pool = []
+    for s in range(pool_scenes):
+        sc = inputs.batch_scene(spec, s)
+        pool.append(tuple(torch.from_numpy(x).pin_memory().numpy() for x in (sc.pts, sc.a, sc.b)))
+    ctx = cellgraph.Context(dev.index or 0)
+    want = []
+    for pts, a, b in pool:
+        c, e = ctx.build(*(torch.from_numpy(x).to(dev) for x in (pts, a, b)), 64)
+        want.append((int(c.shape[0]), int(e.shape[0])))
+    ctx.close()
+    out = {"workload": "Poisson stream of scenes drawn like the batched workload "
+                       f"(a pool of {pool_scenes} scenes, cycled), host inputs in pinned memory",
+           "capacity_scenes_per_s": capacity_scenes_per_s, "levels": []}
+    with cellgraph.Server(dev.index or 0, hbm_budget_bytes=16 << 30, max_inflight=16) as srv:
+        for k in range(32):  # warm-up: kernels loaded, pool memory cached
+            t = srv.submit(*pool[k % pool_scenes])
+            srv.wait(t)
+            srv.release(t)
+        for load in loads:
+            rate = load * capacity_scenes_per_s
+            arrivals = inputs.poisson_arrivals(n_requests, rate, seed=5)
+            tickets = [None] * n_requests
+            lat, mism = [], [0]
+            first_submit, last_done = [None], [0.0]
+
+            def drain():
+                for i in range(n_requests):
+                    while tickets[i] is None:
+                        time.sleep(0)
+                    srv.wait(tickets[i])
+                    r = srv.result(tickets[i])
+                    if r["status"] or (r["n_cells"], r["n_edges"]) != want[i % pool_scenes]:
+                        mism[0] += 1
+                    lat.append(r["done_us"] - r["submit_us"])
+                    if first_submit[0] is None:
+                        first_submit[0] = r["submit_us"]
+                    last_done[0] = max(last_done[0], r["done_us"])
+                    srv.release(tickets[i])
+
+            th = threading.Thread(target=drain)
+            th.start()
+            t0 = time.perf_counter()
+            for i in range(n_requests):
+                gap = arrivals[i] - (time.perf_counter() - t0)
+                if gap > 3e-4:
+                    time.sleep(gap - 2e-4)  # lets the draining thread run
+                while time.perf_counter() - t0 < arrivals[i]:
+                    pass
+                tickets[i] = srv.submit(*pool[i % pool_scenes])
+            th.join()
+            pts_total = sum(int(pool[i % pool_scenes][0].shape[0]) for i in range(n_requests))
+            span_s = (last_done[0] - first_submit[0]) * 1e-6
+            st = srv.stats()
+            lat_ms = np.array(lat) * 1e-3
+            out["levels"].append({
+                "offered_load": load, "offered_scenes_per_s": rate, "requests": n_requests,
+                "p50_ms": float(np.percentile(lat_ms, 50)),
+                "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mean_ms": float(lat_ms.mean()),
+                "sustained": {"value": pts_total / span_s / 1e6, "unit": UNIT,
+                              "scenes_per_s": n_requests / span_s},
+                "count_mismatches": mism[0], "max_running": st["max_running"],
+                "peak_bytes": st["peak_bytes"]})
+    return out
+
+
+def inputs_spec_n():
+    from paper_1503_06029_gb300 import inputs
+
+    return inputs.scene_batch_spec().n
 
 
 def cg_launches():
@@ -336,12 +440,8 @@ def run_ours(args):
     launches = cellgraph.launch_count() - launches0
     stages, builds = ctx.stage_times()
     ctx.set_timing(False)
-    ms = start.elapsed_time(stop) / args.steps
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(start.elapsed_time(stop) / args.steps, pg, dev)
+    value = job_value(world, n, ms * 1e-3)
 
     # ---- end to end through the C-ABI with host buffers ----
     pin = lambda x: torch.from_numpy(x).pin_memory().numpy()
@@ -358,11 +458,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         hc, he = ctx.build_host(h_pts, h_a, h_b, 64, outputs=h_out)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if pg:
-        t = torch.tensor([e2e_s], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, pg, dev)
     h2d = sc.pts.nbytes + sc.a.nbytes + sc.b.nbytes
     d2h = hc.nbytes + he.nbytes
 
@@ -397,13 +493,16 @@ def run_ours(args):
                      "frac": compulsory / (ms * 1e-3) / 1e9 / hbm_peak,
                      "peak_kind": peak_kind},
         "stages_ms": {k: v / max(1, builds) for k, v in stages.items()},
-        "e2e": {"value": world * n / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_value(world, n, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
     if not args.no_batch:
         line["batch"] = batch_compare(ctx, dev, max(3, args.steps // 2))
+        if not args.no_serve:
+            cap = len(inputs_spec_n()) / (line["batch"]["batched"]["ms_per_batch"] * 1e-3)
+            line["serve"] = serve_measure(dev, cap, n_requests=args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     ctx.close()
@@ -421,10 +520,13 @@ def main():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=N_POINTS)
-    p.add_argument("--cpu-sample", type=int, default=1 << 23)
+    p.add_argument("--cpu-sample", type=int, default=1 << 24)
     p.add_argument("--ref-sample", type=int, default=1 << 20)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the batched-vs-plain comparison (and serving)")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serve-requests", type=int, default=2000)
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be >= 3")

@@ -213,6 +213,106 @@ cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, cg_b
                          void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Serving: a request loop that builds independent scenes (§2.1-§2.2 per scene)
+ * as they arrive. The paper has no counterpart; this is the deployment form of
+ * cg_build for a stream of requests.
+ *
+ * Continuous batching: a scheduler thread owned by the server admits queued
+ * requests in arrival order as soon as a slot (one of max_inflight streams)
+ * and enough of the HBM budget are free, and enqueues each admitted scene's
+ * steps 1-4 on its slot's stream, so the work of requests that arrived at
+ * different times runs on the device at the same time. A request is charged
+ * its whole device footprint (copied inputs, workspace, cells and edges at
+ * capacity) from admission; the workspace is returned when it completes, the
+ * cells and edges stay on the device (charged) until cg_server_release. The
+ * budget therefore bounds everything the server holds. Admission never
+ * changes a result: each request's output is exactly what cg_build gives for
+ * the same scene (64-bit words), alone or in any mix.
+ *
+ * A request whose table or edge capacity turns out too small is re-run with
+ * larger capacities before it completes (it is re-queued at the head).
+ * Results: cells uint64[U][ceil(l/64)] in value order and edges uint32[E][2]
+ * in (i, j) order, as for cg_build.
+ * ------------------------------------------------------------------------- */
+typedef struct cg_server cg_server;
+
+/* Request states reported by cg_server_poll. */
+#define CG_REQ_QUEUED 0
+#define CG_REQ_RUNNING 1
+#define CG_REQ_DONE 2
+#define CG_REQ_FAILED 3
+
+typedef struct cg_server_result {
+  cg_status status;       /* CG_OK, or why the request failed */
+  int64_t n_cells;        /* U */
+  int64_t n_edges;        /* E */
+  int words;              /* 64-bit words per cell, ceil(l / 64) */
+  const uint64_t* cells;  /* device, valid until cg_server_release */
+  const uint32_t* edges;  /* device, valid until cg_server_release */
+  double submit_us;       /* host steady clock, microseconds since server creation: */
+  double admit_us;        /*   submitted, admitted (first time), and the moment the */
+  double done_us;         /*   device finished the last step (completion callback) */
+  int retries;            /* re-runs after a capacity overflow */
+} cg_server_result;
+
+typedef struct cg_server_stats {
+  int64_t submitted, completed, failed, retried;
+  int64_t queued, running;        /* now */
+  size_t bytes_in_use;            /* charged against the budget now */
+  size_t peak_bytes;              /* maximum of bytes_in_use so far */
+  int max_running;                /* most requests running at once so far */
+} cg_server_stats;
+
+/* Creates a server on `device` that holds at most hbm_budget_bytes of device
+ * memory for requests and runs at most max_inflight requests at once
+ * (1..64). Starts the scheduler thread. */
+cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight,
+                           cg_server** out);
+
+/* Queues one scene. inputs_on_host != 0: pts/a/b are HOST arrays (pinned for
+ * asynchronous copies), copied to the request's device memory after
+ * admission; 0: they are device arrays used in place. Either way they must
+ * stay valid and unchanged until the request is DONE or FAILED. Writes the
+ * request's ticket (> 0). Invalid scenes are rejected here
+ * (CG_ERR_INVALID_ARG); a scene whose footprint exceeds the whole budget is
+ * accepted and then FAILED with CG_ERR_CAPACITY. */
+cg_status cg_server_submit(cg_server* srv, const cg_scene* scene, int inputs_on_host,
+                           int64_t* ticket);
+
+/* Writes the request's state (CG_REQ_*). Unknown or released tickets give
+ * CG_ERR_INVALID_ARG. */
+cg_status cg_server_poll(cg_server* srv, int64_t ticket, int* state);
+
+/* Waits until the request is DONE or FAILED, at most timeout_s seconds
+ * (< 0: no limit). Returns CG_OK when it finished (check the result's status),
+ * CG_ERR_TIMEOUT when the time ran out first. */
+cg_status cg_server_wait(cg_server* srv, int64_t ticket, double timeout_s);
+
+/* Result of a DONE or FAILED request (CG_ERR_INVALID_ARG while it is still
+ * queued or running). */
+cg_status cg_server_result_get(cg_server* srv, int64_t ticket, cg_server_result* out);
+
+/* Copies a DONE request's cells and edges to caller memory (host or device;
+ * nullable when the capacity is 0); blocks until copied. Caps smaller than
+ * U*words words / E edges give CG_ERR_CAPACITY and copy nothing. */
+cg_status cg_server_copy(cg_server* srv, int64_t ticket, uint64_t* cells, int64_t cells_cap,
+                         uint32_t* edges, int64_t edges_cap);
+
+/* Frees a finished request's device result and forgets the ticket. */
+cg_status cg_server_release(cg_server* srv, int64_t ticket);
+
+cg_status cg_server_get_stats(cg_server* srv, cg_server_stats* out);
+
+/* Host-side fault injection for tests: the next `count` device allocations the
+ * scheduler makes report failure, so the requests that needed them FAIL with
+ * CG_ERR_OOM while the server keeps serving the others. No GPU fault is made. */
+cg_status cg_server_inject_alloc_failures(cg_server* srv, int count);
+
+/* Stops admitting, lets running requests finish, fails queued ones, frees all
+ * device memory of the server (results included) and joins its thread. */
+cg_status cg_server_destroy(cg_server* srv);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free neighbour search. The paper has no counterpart: this is a
  * deployment variant of cg_neighbors_h1 (HASH strategy, 1 <= l <= 64) for
  * callers that cannot allocate device memory at the point of the call (fixed

@@ -35,7 +35,12 @@ EXPORTS = [
     "cg_last_error", "cg_version", "cg_launch_count", "cg_pack_signs", "cg_dedup_cells",
     "cg_neighbors_h1", "cg_ctx_create", "cg_ctx_destroy", "cg_ctx_pool_bytes", "cg_build",
     "cg_build_host", "cg_ctx_set_timing", "cg_ctx_stage_times", "cg_build_batch",
+    "cg_server_create", "cg_server_submit", "cg_server_poll", "cg_server_wait",
+    "cg_server_result_get", "cg_server_copy", "cg_server_release", "cg_server_get_stats",
+    "cg_server_inject_alloc_failures", "cg_server_destroy",
 ]
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
 class CgScene(ctypes.Structure):
@@ -50,6 +55,24 @@ class CgBatchOut(ctypes.Structure):
                 ("edges", ctypes.c_void_p), ("edges_cap", ctypes.c_int64),
                 ("n_cells", ctypes.c_void_p), ("n_edges", ctypes.c_void_p),
                 ("cells_offset", ctypes.c_void_p), ("edges_offset", ctypes.c_void_p)]
+
+
+class CgServerResult(ctypes.Structure):
+    """struct cg_server_result (include/cellgraph.h)."""
+    _fields_ = [("status", ctypes.c_int), ("n_cells", ctypes.c_int64),
+                ("n_edges", ctypes.c_int64), ("words", ctypes.c_int),
+                ("cells", ctypes.c_void_p), ("edges", ctypes.c_void_p),
+                ("submit_us", ctypes.c_double), ("admit_us", ctypes.c_double),
+                ("done_us", ctypes.c_double), ("retries", ctypes.c_int)]
+
+
+class CgServerStats(ctypes.Structure):
+    """struct cg_server_stats (include/cellgraph.h)."""
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("retried", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("max_running", ctypes.c_int)]
 
 
 class CellGraphError(RuntimeError):
@@ -89,6 +112,16 @@ def load_library(path: str = LIB_PATH):
         lib.cg_build_batch.argtypes = [P, P, I, P, P]
         lib.cg_ctx_set_timing.argtypes = [P, I]
         lib.cg_ctx_stage_times.argtypes = [P, P, P, I, ctypes.POINTER(ctypes.c_int), PI64]
+        lib.cg_server_create.argtypes = [I, S, I, ctypes.POINTER(P)]
+        lib.cg_server_submit.argtypes = [P, P, I, PI64]
+        lib.cg_server_poll.argtypes = [P, I64, ctypes.POINTER(ctypes.c_int)]
+        lib.cg_server_wait.argtypes = [P, I64, ctypes.c_double]
+        lib.cg_server_result_get.argtypes = [P, I64, P]
+        lib.cg_server_copy.argtypes = [P, I64, P, I64, P, I64]
+        lib.cg_server_release.argtypes = [P, I64]
+        lib.cg_server_get_stats.argtypes = [P, P]
+        lib.cg_server_inject_alloc_failures.argtypes = [P, I]
+        lib.cg_server_destroy.argtypes = [P]
         for name in EXPORTS[3:]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -386,3 +419,106 @@ class Context:
             _check(rc)
             self._caps[key] = (max(ccap, nc.value), max(ecap, ne.value))
             return cells[: nc.value], edges[: ne.value]
+
+
+class Server:
+    """Request server (cg_server_* in include/cellgraph.h): scenes are queued,
+    admitted under an HBM budget as slots free up, and built concurrently on
+    the device; results stay device-resident until released.
+
+    ``submit`` takes numpy arrays (host inputs, copied by the server after
+    admission; pinned memory makes the copies asynchronous) or CUDA tensors
+    (used in place). The arrays are kept referenced until the request is
+    released."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 8 << 30, max_inflight: int = 16):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.cg_server_create(device, hbm_budget_bytes, max_inflight, ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(self._lib.cg_server_destroy(self._h))
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, pts, a, b) -> int:
+        torch = _torch()
+        if isinstance(pts, torch.Tensor):
+            n, d = pts.shape
+            sc = CgScene(_dev(pts, torch.int32, "pts").value, n, d,
+                         _dev(a, torch.int32, "a").value, _dev(b, torch.int64, "b").value,
+                         a.shape[0])
+            on_host = 0
+            keep = (pts, a, b)
+        else:
+            keep = tuple(np.ascontiguousarray(x, dtype=t) for x, t in
+                         ((pts, np.int32), (a, np.int32), (b, np.int64)))
+            p_, a_, b_ = keep
+            n, d = p_.shape
+            sc = CgScene(p_.ctypes.data if n else 0, n, d, a_.ctypes.data, b_.ctypes.data,
+                         a_.shape[0])
+            on_host = 1
+        t = ctypes.c_int64(0)
+        _check(self._lib.cg_server_submit(self._h, ctypes.byref(sc), on_host, ctypes.byref(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        st = ctypes.c_int(0)
+        _check(self._lib.cg_server_poll(self._h, ticket, ctypes.byref(st)))
+        return st.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> bool:
+        """True when the request finished, False when the timeout ran out."""
+        rc = self._lib.cg_server_wait(self._h, ticket, float(timeout_s))
+        if rc == ERR_TIMEOUT:
+            return False
+        _check(rc)
+        return True
+
+    def result(self, ticket: int) -> dict:
+        r = CgServerResult()
+        _check(self._lib.cg_server_result_get(self._h, ticket, ctypes.byref(r)))
+        msg = self._lib.cg_last_error().decode() if r.status else ""
+        return {"status": r.status, "error": msg, "n_cells": r.n_cells, "n_edges": r.n_edges,
+                "words": r.words, "submit_us": r.submit_us, "admit_us": r.admit_us,
+                "done_us": r.done_us, "retries": r.retries}
+
+    def fetch(self, ticket: int):
+        """(cells uint64 [U, W], edges uint32 [E, 2]) of a finished request, as
+        numpy arrays on the host."""
+        r = self.result(ticket)
+        if r["status"]:
+            raise CellGraphError(r["status"], r["error"])
+        cells = np.empty((r["n_cells"], r["words"]), dtype=np.uint64)
+        edges = np.empty((r["n_edges"], 2), dtype=np.uint32)
+        _check(self._lib.cg_server_copy(self._h, ticket, cells.ctypes.data, cells.size,
+                                        edges.ctypes.data, edges.shape[0]))
+        return cells, edges
+
+    def release(self, ticket: int):
+        _check(self._lib.cg_server_release(self._h, ticket))
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = CgServerStats()
+        _check(self._lib.cg_server_get_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in CgServerStats._fields_}
+
+    def inject_alloc_failures(self, count: int):
+        _check(self._lib.cg_server_inject_alloc_failures(self._h, count))

@@ -1023,8 +1023,7 @@ cudaError_t launch_point_cell_wide(const uint64_t* keys, int64_t n, int w64, con
 static size_t hbits_bytes(int ell) { return size_t(ell) * sizeof(uint64_t); }
 
 static cudaError_t allow_smem(const void* kern, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  return ensure_smem_limit(kern, bytes);
 }
 
 cudaError_t launch_index_wide(const uint64_t* cells, int w64, int ell, const WideTable& t,

@@ -67,6 +67,13 @@ __host__ __device__ __forceinline__ uint64_t fp_bit(int k) {
 void count_launch(int n = 1);
 void set_last_error(const char* msg);  // message returned by cg_last_error()
 int sm_count();  // SMs of the current device (cached per device)
+// Raises kern's dynamic shared memory limit on the current device to at least
+// `bytes` (a runtime call only the first time a larger size is needed;
+// thread-safe).
+cudaError_t ensure_smem_limit(const void* kern, size_t bytes);
+// Resident blocks per SM of kern for a block size and dynamic shared memory
+// size, on the current device (computed once, then cached; thread-safe).
+cudaError_t blocks_per_sm(const void* kern, int threads, size_t smem, int* out);
 
 // ---------------------------------------------------------------------------
 // Step 1: sign vectors (cg_pack.cu).

@@ -531,11 +531,9 @@ template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 8>
 cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
   const size_t smem = size_t(1 + kFWarps) * NCH * 32 * Coef<D>::kQuads * sizeof(float4);
   auto kern = pack_fast_kernel<D, NCH, Sink, P, F2, UJ>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-  if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFThreads, smem);
+  cudaError_t err =
+      blocks_per_sm(reinterpret_cast<const void*>(kern), kFThreads, smem, &per_sm);
   if (err != cudaSuccess) return err;
   per_sm = per_sm < 1 ? 1 : per_sm;
   const int64_t n_wt = (pa.n + 32 * P - 1) / (32 * P);
@@ -583,11 +581,8 @@ cudaError_t launch_d(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
   const size_t smem = size_t(n_chunks) * 32 * Coef<D>::kQuads * sizeof(float4) +
                       sizeof(uint32_t) * (kThreads / 32) * D;
   auto kern = pack_kernel<D, Sink>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-  if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  cudaError_t err = blocks_per_sm(reinterpret_cast<const void*>(kern), kThreads, smem, &per_sm);
   if (err != cudaSuccess) return err;
   per_sm = per_sm < 1 ? 1 : per_sm;
   const int64_t n_tiles = (pa.n + kTilePts - 1) / kTilePts;

@@ -472,8 +472,7 @@ cudaError_t launch_tc_dn(const PackArgs& pa, const Sink& sink, TcSpill spill, un
   constexpr int kPerSm = 512 / NC;
   const size_t smem = std::max(sizeof(TcShared) + 1024, size_t(216 * 1024) / kPerSm);
   auto kern = pack_tc_kernel<D, NC, Sink>;
-  cudaError_t err =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t err = ensure_smem_limit(reinterpret_cast<const void*>(kern), smem);
   if (err != cudaSuccess) return err;
   const int64_t ntiles = (pa.n + kTilePts - 1) / kTilePts;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, int64_t(sm_count()) * kPerSm));

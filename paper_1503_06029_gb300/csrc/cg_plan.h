@@ -1,0 +1,42 @@
+// Host-side planning and enqueueing of one scene's build (steps 1-4), shared by
+// the single-scene, batch and server entry points.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cellgraph.h"
+#include "cg_internal.cuh"
+
+namespace cg {
+
+// One scene's build: sizes and strategy.
+struct ScenePlan {
+  int64_t n;
+  int ell;
+  size_t cap;   // table slots (power of two)
+  size_t ucap;  // distinct-vector capacity
+  bool small;   // l <= 64
+  bool single;  // wide, single-pass neighbour kernel and cluster sort
+};
+
+ScenePlan plan_scene(int64_t n, int ell, size_t cap);
+
+// Device workspace of one scene (without its counters and outputs).
+size_t scene_ws_bytes(const ScenePlan& p);
+
+// First table capacity tried for a scene of n points, d dimensions and l
+// constraints (from the arrangement bound), and the capacity that always fits.
+size_t initial_cap(int64_t n, int d, int ell);
+size_t full_cap(int64_t n);
+
+// Enqueues one scene's build into workspace `ws` with counters at `ctr`;
+// nothing is read back. Cells go to `cells` (word_bits words, when
+// U <= cells_cap), edges to `edges` (up to edges_cap). ctx (nullable) only
+// receives stage-timing marks.
+cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan& plan,
+                        const PackArgs& pa, int word_bits, void* cells, int64_t cells_cap,
+                        uint32_t* edges, int64_t edges_cap, cudaStream_t s);
+
+}  // namespace cg

@@ -422,8 +422,7 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
     const size_t per = (max_n + C - 1) / C;
     const size_t dyn = 2 * std::max<size_t>(per, 1) * W * sizeof(uint64_t);
     if (dyn > kMaxDyn) continue;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(dyn));
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(kern), dyn);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
@@ -437,8 +436,9 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (C == 16) {
-      if (cluster16 == 0) continue;
+    if (C == 16 && cluster16 == 0) continue;
+    if (C == 16 && cluster16 < 0) {
+      // First use: allow 16-CTA clusters and check that one fits on an SM set.
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) {
         cudaGetLastError();
@@ -456,8 +456,14 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
     }
     e = cudaLaunchKernelEx(&cfg, kern, in, rows, n_dev, uint32_t(max_n), top_bits, o,
                            uint32_t(per));
-    count_launch();
+    if (e != cudaSuccess && C == 16) {
+      // A 16-CTA cluster with this much shared memory does not fit: the launch
+      // is refused before it starts; use 8-CTA clusters instead.
+      cudaGetLastError();
+      continue;
+    }
     if (e != cudaSuccess) return e;
+    count_launch();
     *done = true;
     return cudaGetLastError();
   }

@@ -302,9 +302,32 @@ def test_build_degenerate_inputs(ctx, dev):
     assert edges.shape[0] == 0
 
 
-def test_build_overflowing_first_guess(ctx, dev):
+@pytest.mark.parametrize("ell", [64, 200])
+def test_build_overflowing_first_guess(dev, ell, monkeypatch):
+    """A first table guess of 1024 slots (512 vectors) overflows; the build is
+    re-run with 4x the capacity until it fits, with the same output."""
+    monkeypatch.setenv("CG_FIRST_TABLE_CAP", "1024")
+    sc = inputs.planes_3d(n=300_000, ell=ell, seed=12)
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+    assert len(want_c) > 512
+    c2 = cellgraph.Context(0)
+    try:
+        cells, edges = c2.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
+        assert np.array_equal(words_np(cells, 64).reshape(want_c.shape), want_c)
+        assert np.array_equal(edges_np(edges), want_e)
+        scenes = _batch_scenes(6, 100_000, seed=13) + [sc]
+        got = c2.build_batch([(T(x.pts, dev), T(x.a, dev), T(x.b, dev)) for x in scenes])
+        for x, (c, e) in zip(scenes, got):
+            wc, we = oracle.build(x.pts, x.a, x.b, 64)
+            assert np.array_equal(words_np(c, 64).reshape(wc.shape), wc)
+            assert np.array_equal(edges_np(e), we)
+    finally:
+        c2.close()
+
+
+def test_build_coincident_opposite_planes(ctx, dev):
     # Degenerate arrangement with many coincident, oppositely oriented planes:
-    # more distinct vectors than the cell bound the first table size assumes.
+    # points on them carry vectors that no open cell has.
     rng = np.random.default_rng(3)
     base = rng.integers(-50, 51, size=(8, 2)).astype(np.int32)
     a = np.concatenate([base, -base, base, -base])
