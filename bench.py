@@ -341,6 +341,45 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
     return out
 
 
+def chains_measure(dev, steps: int, strategies=("hash", "pivot")):
+    """Long vectors: l = 1024 (16 words), 2^18 random seeds with 15-step
+    single-flip chains, 25% duplicated, N = 5,242,880 vectors resident on the
+    device. One step = cg_dedup_cells + cg_neighbors_h1 (counts read back),
+    per lookup strategy of the neighbour search."""
+    import numpy as np
+    import torch
+
+    from paper_1503_06029_gb300 import cellgraph, inputs
+
+    ch = inputs.chains()
+    n = int(ch.keys.shape[0])
+    keys = torch.from_numpy(ch.keys.view(np.int64)).to(dev)
+    del ch
+    out = {"workload": "chains: l=1024 (16 x uint64), 2^18 seeds x 16 chain members + 25% "
+                       "duplicates, N=5,242,880", "n": n, "strategies": {}}
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for strat in strategies:
+        for _ in range(2):
+            cells = cellgraph.dedup_cells(keys, 1024, 64)
+            edges = cellgraph.neighbors_h1(cells, 1024, 64, strategy=strat)
+        d_ms = n_ms = 0.0
+        for _ in range(steps):
+            ev[0].record(stream)
+            cells = cellgraph.dedup_cells(keys, 1024, 64)
+            ev[1].record(stream)
+            edges = cellgraph.neighbors_h1(cells, 1024, 64, strategy=strat)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            d_ms += ev[0].elapsed_time(ev[1]) / steps
+            n_ms += ev[1].elapsed_time(ev[2]) / steps
+        out["cells"], out["edges"] = int(cells.shape[0]), int(edges.shape[0])
+        out["strategies"][strat] = {"value": n / ((d_ms + n_ms) * 1e-3) / 1e6, "unit": UNIT,
+                                    "ms_per_step": d_ms + n_ms, "dedup_ms": d_ms,
+                                    "neighbors_ms": n_ms}
+    return out
+
+
 def inputs_spec_n():
     from paper_1503_06029_gb300 import inputs
 
@@ -498,6 +537,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
+    if not args.no_chains:
+        line["chains"] = chains_measure(dev, max(3, args.steps // 4))
     if not args.no_batch:
         line["batch"] = batch_compare(ctx, dev, max(3, args.steps // 2))
         if not args.no_serve:
@@ -526,6 +567,7 @@ def main():
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched-vs-plain comparison (and serving)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-chains", action="store_true", help="skip the long-vector workload")
     p.add_argument("--serve-requests", type=int, default=2000)
     args = p.parse_args()
     if args.warmup < 3:

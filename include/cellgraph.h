@@ -65,6 +65,11 @@ typedef int cg_status;
                                 or on a GF(2)-linear 64-bit fingerprint (l > 64);
                                 every candidate is verified against the full vector */
 #define CG_STRATEGY_SORTED 2 /* binary search in the sorted cell array */
+#define CG_STRATEGY_PIVOT 3  /* distance-to-pivot bucketing by inequality (⋆) of §3.1:
+                                cells are grouped by their Hamming distances to h
+                                pivot cells, and only the 2^h buckets whose
+                                distances differ by +-1 in every coordinate are
+                                compared, word by word (XOR + popcount) */
 
 /* Message describing the calling thread's last failed call ("" if none). */
 const char* cg_last_error(void);
@@ -112,7 +117,8 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
  *              output of cg_dedup_cells); unsorted input gives unspecified edges.
  *   edges      uint32[edges_cap][2], device.
  *   n_edges    host: receives E.
- *   strategy   CG_STRATEGY_*.
+ *   strategy   CG_STRATEGY_* (PIVOT uses h = 4 pivots, or the value of the
+ *              environment variable CG_PIVOTS when it is set).
  *   ws, ws_bytes  as for cg_dedup_cells.
  * Blocks until done. E > edges_cap gives CG_ERR_CAPACITY with *n_edges = E.
  * ------------------------------------------------------------------------- */
@@ -146,6 +152,30 @@ cg_status cg_ctx_pool_bytes(const cg_ctx* ctx, size_t* bytes);
 cg_status cg_ctx_set_timing(cg_ctx* ctx, int enable);
 cg_status cg_ctx_stage_times(cg_ctx* ctx, double* ms, const char** names, int cap, int* n,
                              int64_t* builds);
+
+/* ---------------------------------------------------------------------------
+ * Tuning. The paper's tunables are the pivot count h of the heuristic and the
+ * digit width of the tree (§3, §5); here a context keeps, per bucket of l,
+ * the lookup strategy of the neighbour search, the pivot count for PIVOT and
+ * the sign kernel, and uses them for cg_build and cg_build_batch (AUTO in
+ * cg_neighbors_h1 uses the library defaults). Every setting gives the same
+ * output; only the speed differs.
+ * Buckets: 0: l <= 16, 1: <= 32, 2: <= 64, 3: <= 128, 4: <= 256, 5: <= 1024,
+ * 6: <= 4096.
+ * Defaults: HASH, h = 4, the fp32 sign kernel.
+ * ------------------------------------------------------------------------- */
+#define CG_TUNE_BUCKETS 7
+typedef struct cg_tune_params {
+  int strategy;    /* CG_STRATEGY_HASH, _SORTED or _PIVOT */
+  int pivots;      /* h for PIVOT: 1 <= h <= min(8, 64 / bits(l)) (clamped) */
+  int sign_kernel; /* 0: fp32 FMA filter with exact fallback; 1: tensor cores
+                      (tcgen05, l <= 64 only; ignored above) */
+} cg_tune_params;
+
+int cg_tune_bucket(int ell); /* bucket of l, or -1 when l is out of range */
+cg_status cg_ctx_tune_get(const cg_ctx* ctx, int bucket, cg_tune_params* out);
+cg_status cg_ctx_tune_set(cg_ctx* ctx, int bucket, const cg_tune_params* p);
+
 
 /* ---------------------------------------------------------------------------
  * Steps 1-4 for one scene: points -> cells -> edges (§2.1, §3.2, §2.2,
@@ -211,6 +241,16 @@ typedef struct cg_batch_out {
 
 cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, cg_batch_out* out,
                          void* stream);
+
+/* Autotuner: for every bucket of l present among the scenes (device arrays,
+ * as for cg_build_batch), times cg_build of those scenes (at most 16 per
+ * bucket) under each candidate setting -- HASH, SORTED, PIVOT with h in
+ * {2, 3, 4}, and for l <= 64 both sign kernels -- `reps` times after one
+ * warm-up, and keeps the fastest setting in the context. chosen_ms
+ * (nullable, host double[CG_TUNE_BUCKETS]) receives the best time per bucket
+ * (0 for buckets without scenes). Blocks until done. */
+cg_status cg_ctx_autotune(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, int reps,
+                          double* chosen_ms);
 
 /* ---------------------------------------------------------------------------
  * Serving: a request loop that builds independent scenes (§2.1-§2.2 per scene)
@@ -302,6 +342,10 @@ cg_status cg_server_copy(cg_server* srv, int64_t ticket, uint64_t* cells, int64_
 cg_status cg_server_release(cg_server* srv, int64_t ticket);
 
 cg_status cg_server_get_stats(cg_server* srv, cg_server_stats* out);
+
+/* Copies the context's tuning (cg_ctx_tune_set / cg_ctx_autotune) into the
+ * server; requests admitted afterwards use it. */
+cg_status cg_server_use_tuning(cg_server* srv, const cg_ctx* ctx);
 
 /* Host-side fault injection for tests: the next `count` device allocations the
  * scheduler makes report failure, so the requests that needed them FAIL with

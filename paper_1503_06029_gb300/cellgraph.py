@@ -29,7 +29,10 @@ ERR_CUDA = 5
 ERR_TIMEOUT = 6
 ERR_INTERNAL = 7
 
-STRATEGY = {"auto": 0, "hash": 1, "sorted": 2}
+STRATEGY = {"auto": 0, "hash": 1, "sorted": 2, "pivot": 3}
+STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
+TUNE_BUCKETS = 7
+TUNE_LIMITS = (16, 32, 64, 128, 256, 1024, 4096)
 
 EXPORTS = [
     "cg_last_error", "cg_version", "cg_launch_count", "cg_pack_signs", "cg_dedup_cells",
@@ -37,7 +40,8 @@ EXPORTS = [
     "cg_build_host", "cg_ctx_set_timing", "cg_ctx_stage_times", "cg_build_batch",
     "cg_server_create", "cg_server_submit", "cg_server_poll", "cg_server_wait",
     "cg_server_result_get", "cg_server_copy", "cg_server_release", "cg_server_get_stats",
-    "cg_server_inject_alloc_failures", "cg_server_destroy",
+    "cg_server_inject_alloc_failures", "cg_server_destroy", "cg_tune_bucket", "cg_ctx_tune_get",
+    "cg_ctx_tune_set", "cg_ctx_autotune", "cg_server_use_tuning",
 ]
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -55,6 +59,12 @@ class CgBatchOut(ctypes.Structure):
                 ("edges", ctypes.c_void_p), ("edges_cap", ctypes.c_int64),
                 ("n_cells", ctypes.c_void_p), ("n_edges", ctypes.c_void_p),
                 ("cells_offset", ctypes.c_void_p), ("edges_offset", ctypes.c_void_p)]
+
+
+class CgTuneParams(ctypes.Structure):
+    """struct cg_tune_params (include/cellgraph.h)."""
+    _fields_ = [("strategy", ctypes.c_int), ("pivots", ctypes.c_int),
+                ("sign_kernel", ctypes.c_int)]
 
 
 class CgServerResult(ctypes.Structure):
@@ -122,6 +132,11 @@ def load_library(path: str = LIB_PATH):
         lib.cg_server_get_stats.argtypes = [P, P]
         lib.cg_server_inject_alloc_failures.argtypes = [P, I]
         lib.cg_server_destroy.argtypes = [P]
+        lib.cg_tune_bucket.argtypes = [I]
+        lib.cg_ctx_tune_get.argtypes = [P, I, P]
+        lib.cg_ctx_tune_set.argtypes = [P, I, P]
+        lib.cg_ctx_autotune.argtypes = [P, P, I, I, P]
+        lib.cg_server_use_tuning.argtypes = [P, P]
         for name in EXPORTS[3:]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -385,6 +400,65 @@ class Context:
                 res.append((c, edges[eoff[i]: eoff[i + 1]]))
             return res
 
+    # ---- tuning (cg_ctx_tune_* / cg_ctx_autotune) ----
+    def tune_get(self, bucket: int) -> dict:
+        p = CgTuneParams()
+        _check(self._lib.cg_ctx_tune_get(self._h, bucket, ctypes.byref(p)))
+        return {"strategy": STRATEGY_NAME[p.strategy], "pivots": p.pivots,
+                "sign_kernel": p.sign_kernel}
+
+    def tune_set(self, bucket: int, strategy: str = "hash", pivots: int = 4,
+                 sign_kernel: int = 0):
+        p = CgTuneParams(STRATEGY[strategy], pivots, sign_kernel)
+        _check(self._lib.cg_ctx_tune_set(self._h, bucket, ctypes.byref(p)))
+
+    def tuning(self) -> list:
+        return [self.tune_get(b) for b in range(TUNE_BUCKETS)]
+
+    def autotune(self, scenes, reps: int = 2) -> dict:
+        """Times the candidate settings on the given (pts, a, b) CUDA-tensor
+        scenes, per bucket of l, and keeps the fastest in the context. Returns
+        {bucket: {"setting": ..., "ms": best ms per pass}} for the buckets
+        that had scenes."""
+        torch = _torch()
+        S = len(scenes)
+        arr = (CgScene * max(1, S))()
+        for i, (pts, a, b) in enumerate(scenes):
+            n, d = pts.shape
+            arr[i] = CgScene(_dev(pts, torch.int32, "pts").value, n, d,
+                             _dev(a, torch.int32, "a").value, _dev(b, torch.int64, "b").value,
+                             a.shape[0])
+        ms = (ctypes.c_double * TUNE_BUCKETS)()
+        _check(self._lib.cg_ctx_autotune(self._h, ctypes.cast(arr, ctypes.c_void_p), S, reps, ms))
+        return {b: {"setting": self.tune_get(b), "ms": ms[b]} for b in range(TUNE_BUCKETS)
+                if ms[b] > 0}
+
+    def save_tuning(self, path: str, gpu_name: str):
+        """Writes the context's tuning to a JSON cache keyed by GPU name."""
+        import json
+
+        data = {}
+        if os.path.exists(path):
+            with open(path) as f:
+                data = json.load(f)
+        data[gpu_name] = {str(b): t for b, t in enumerate(self.tuning())}
+        with open(path, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+
+    def load_tuning(self, path: str, gpu_name: str) -> bool:
+        """Applies the tuning cached for gpu_name; False when there is none."""
+        import json
+
+        if not os.path.exists(path):
+            return False
+        with open(path) as f:
+            entry = json.load(f).get(gpu_name)
+        if not entry:
+            return False
+        for b, t in entry.items():
+            self.tune_set(int(b), t["strategy"], int(t["pivots"]), int(t["sign_kernel"]))
+        return True
+
     def build_host(self, pts: np.ndarray, a: np.ndarray, b: np.ndarray, word_bits: int = 64,
                    stream=None, outputs=None):
         """Same as ``build`` with numpy arrays in and out (the C-ABI copies)."""
@@ -519,6 +593,9 @@ class Server:
         st = CgServerStats()
         _check(self._lib.cg_server_get_stats(self._h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in CgServerStats._fields_}
+
+    def use_tuning(self, ctx: "Context"):
+        _check(self._lib.cg_server_use_tuning(self._h, ctx._h))
 
     def inject_alloc_failures(self, count: int):
         _check(self._lib.cg_server_inject_alloc_failures(self._h, count))

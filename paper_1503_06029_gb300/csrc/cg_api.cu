@@ -240,6 +240,43 @@ WideWs carve_wide(Carve& c, size_t n, size_t cap, size_t ucap, int ell, bool nee
   return w;
 }
 
+// PIVOT neighbour search: keys, sorted keys and cell numbers, bucket table,
+// per-cell edge counts, write cursors and offsets.
+struct PivotWs {
+  uint64_t* kcell;
+  uint64_t* k0;
+  uint64_t* k1;
+  uint32_t* i0;
+  uint32_t* i1;
+  void* radix;
+  uint64_t* tkeys;
+  uint32_t* tvals;
+  size_t tcap;
+  uint32_t* fill;
+  uint32_t* counts;
+  unsigned long long* offsets;
+  void* scan;
+};
+
+PivotWs carve_pivot(Carve& c, size_t ucap, int ell) {
+  PivotWs p{};
+  const size_t u = ucap > 0 ? ucap : 1;
+  p.kcell = c.take<uint64_t>(u);
+  p.k0 = c.take<uint64_t>(u);
+  p.k1 = c.take<uint64_t>(u);
+  p.i0 = c.take<uint32_t>(u);
+  p.i1 = c.take<uint32_t>(u);
+  p.radix = c.take_bytes(radix_scratch_bytes(u));
+  p.tcap = std::max<size_t>(1024, next_pow2(2 * u));
+  p.tkeys = c.take<uint64_t>(p.tcap);
+  p.tvals = c.take<uint32_t>(p.tcap);
+  p.fill = c.take<uint32_t>(u);
+  p.counts = c.take<uint32_t>(u);
+  p.offsets = c.take<unsigned long long>(u);
+  p.scan = c.take_bytes(scan_scratch_bytes(u));
+  return p;
+}
+
 cg_status read_counters(DevCounters* dev, DevCounters* host, cudaStream_t s) {
   CG_CUDA(cudaMemcpyAsync(host, dev, sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
           "reading counters");
@@ -281,6 +318,42 @@ cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t*
                            edges_cap, w.ucap, s),
           "edge output");
   return CG_OK;
+}
+
+// Steps 3-4 with the PIVOT strategy over sorted internal rows (w64 words,
+// U in ctr->n_unique, at most ucap): keys, sort by key, bucket index,
+// counting search, scan, writing search, per-cell ordering.
+cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
+                      const PivotWs& p, size_t ucap, uint32_t* edges, int64_t edges_cap,
+                      cudaStream_t s) {
+  CG_CUDA(launch_fill_u64(p.tkeys, kEmpty, p.tcap, s), "clearing the bucket table");
+  CG_CUDA(launch_pivot_keys(cells, w64, ell, h, ctr, ucap, p.kcell, p.k0, p.i0, s),
+          "pivot distances");
+  bool in1 = false;
+  CG_CUDA(radix_sort_u64(p.k0, p.k1, p.i0, p.i1, &ctr->n_unique, ucap, pivot_sort_bits(ell, h),
+                         p.radix, s, &in1),
+          "sorting by pivot distances");
+  const uint64_t* sk = in1 ? p.k1 : p.k0;
+  const uint32_t* si = in1 ? p.i1 : p.i0;
+  CG_CUDA(launch_pivot_index(sk, ctr, ucap, p.tkeys, p.tvals, p.tcap, ctr, s), "bucket index");
+  CG_CUDA(launch_pivot_search(cells, w64, ell, h, ctr, ucap, p.kcell, sk, si, p.tkeys, p.tvals,
+                              p.tcap, p.counts, nullptr, nullptr, nullptr, 0, false, s),
+          "pivot neighbour search (count)");
+  CG_CUDA(scan_exclusive_u32(p.counts, p.offsets, &ctr->n_unique, ucap, &ctr->n_edges, p.scan, s),
+          "edge offsets");
+  CG_CUDA(launch_pivot_search(cells, w64, ell, h, ctr, ucap, p.kcell, sk, si, p.tkeys, p.tvals,
+                              p.tcap, p.counts, p.offsets, p.fill, edges, edges_cap, true, s),
+          "pivot neighbour search (write)");
+  CG_CUDA(launch_pivot_order(ctr, ucap, p.counts, p.offsets, edges, edges_cap, s),
+          "ordering edges");
+  return CG_OK;
+}
+
+int env_pivots(int ell) {
+  int h = 4;
+  if (const char* v = std::getenv("CG_PIVOTS")) h = std::atoi(v);
+  const int hmax = pivot_max_h(ell);
+  return h < 1 ? 1 : (h > hmax ? hmax : h);
 }
 
 // Step 2 on small vectors already in the table (ulist holds them in insertion
@@ -345,6 +418,8 @@ struct cg_ctx {
   DevCounters* host_ctr = nullptr;  // pinned
   // Table capacity learned per (n, l, d) after an overflow.
   std::map<std::tuple<int64_t, int, int>, size_t> cap_hint;
+  // Tunables per bucket of l (cg_ctx_tune_set / cg_ctx_autotune).
+  cg_tune_params tune[CG_TUNE_BUCKETS];
   // Stage timing (CUDA events on the build's stream), off by default.
   bool timing = false;
   static constexpr int kMaxMarks = 16;
@@ -458,6 +533,7 @@ cg_status cg_ctx_create(cg_ctx** out, int device) {
   DeviceGuard g(device);
   cg_ctx* c = new cg_ctx();
   c->device = device;
+  for (auto& t : c->tune) t = default_tune();
   if (cudaMallocHost(&c->host_ctr, sizeof(DevCounters)) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -603,16 +679,18 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
                           void* ws, size_t* ws_bytes, void* stream) {
   std::string why;
   if (!check_common(n_cells, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
-  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_SORTED)
+  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_PIVOT)
     return fail(CG_ERR_INVALID_ARG, "unknown strategy");
   if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
   const size_t un = size_t(n_cells > 0 ? n_cells : 1);
   const size_t cap = std::max<size_t>(1024, next_pow2(2 * un));
   const bool small = ell <= 64;
+  const bool pivot = strategy == CG_STRATEGY_PIVOT;
   {
     Carve c{nullptr};
     if (small) carve_small(c, cap, un, ell, false, true, true);
     else carve_wide(c, un, cap, un, ell, false, false, false, true);
+    if (pivot) carve_pivot(c, un, ell);
     if (!ws) {
       *ws_bytes = c.off + 256;
       return CG_OK;
@@ -627,14 +705,19 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
   DevCounters host{};
   if (small) {
     SmallWs w = carve_small(c, cap, un, ell, false, true, true);
-    CG_CUDA(launch_clear_build(strategy != CG_STRATEGY_SORTED ? w.tkeys : nullptr,
-                               strategy != CG_STRATEGY_SORTED ? cap : 0, w.status,
+    const bool table = strategy != CG_STRATEGY_SORTED && !pivot;
+    CG_CUDA(launch_clear_build(table ? w.tkeys : nullptr, table ? cap : 0, w.status,
                                ne_status_words(un), w.ctr, s),
             "clearing table");
     CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
-    if (strategy != CG_STRATEGY_SORTED)
-      CG_CUDA(launch_index_small(w.cells, w.table(false), un, s), "indexing cells");
-    cg_status st = neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
+    cg_status st;
+    if (pivot) {
+      st = pivot_steps(w.cells, 1, ell, env_pivots(ell), w.ctr, carve_pivot(c, un, ell), un,
+                       edges, edges_cap, s);
+    } else {
+      if (table) CG_CUDA(launch_index_small(w.cells, w.table(false), un, s), "indexing cells");
+      st = neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
+    }
     if (st) return st;
     st = read_counters(w.ctr, &host, s);
     if (st) return st;
@@ -642,7 +725,9 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     WideWs w = carve_wide(c, un, cap, un, ell, false, false, false, true);
     CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
     CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
-    cg_status st = neighbors_wide_steps(w, ell, strategy, edges, edges_cap, s);
+    cg_status st = pivot ? pivot_steps(w.cells, (ell + 63) / 64, ell, env_pivots(ell), w.ctr,
+                                       carve_pivot(c, un, ell), un, edges, edges_cap, s)
+                         : neighbors_wide_steps(w, ell, strategy, edges, edges_cap, s);
     if (st) return st;
     st = read_counters(w.ctr, &host, s);
     if (st) return st;
@@ -676,7 +761,19 @@ size_t arrangement_bound(int64_t n, int d, int ell) {
 
 namespace cg {
 
-ScenePlan plan_scene(int64_t n, int ell, size_t cap) {
+cg_tune_params default_tune() { return cg_tune_params{CG_STRATEGY_HASH, 4, 0}; }
+
+cg_tune_params sanitize_tune(const cg_tune_params& p, int ell) {
+  cg_tune_params q = p;
+  if (q.strategy != CG_STRATEGY_SORTED && q.strategy != CG_STRATEGY_PIVOT)
+    q.strategy = CG_STRATEGY_HASH;
+  const int hmax = pivot_max_h(ell);
+  q.pivots = q.pivots < 1 ? 1 : (q.pivots > hmax ? hmax : q.pivots);
+  q.sign_kernel = (q.sign_kernel == 1 && ell <= 64) ? 1 : 0;
+  return q;
+}
+
+ScenePlan plan_scene(int64_t n, int ell, size_t cap, const cg_tune_params& tp) {
   ScenePlan p{};
   p.n = n;
   p.ell = ell;
@@ -685,21 +782,28 @@ ScenePlan plan_scene(int64_t n, int ell, size_t cap) {
   p.ucap = std::min(un, cap / 2);
   p.small = ell <= 64;
   p.single = !p.small && ell <= 1024;
+  p.tp = sanitize_tune(tp, ell);
   return p;
 }
 
-void carve_scene(Carve& c, const ScenePlan& p, DevCounters* ext_ctr, SmallWs* sw, WideWs* ww) {
+void carve_scene(Carve& c, const ScenePlan& p, DevCounters* ext_ctr, SmallWs* sw, WideWs* ww,
+                 PivotWs* pw) {
   const size_t un = size_t(p.n > 0 ? p.n : 1);
-  if (p.small) *sw = carve_small(c, p.cap, p.ucap, p.ell, true, true, false, un, ext_ctr);
-  else *ww = carve_wide(c, un, p.cap, p.ucap, p.ell, true, true, false, true, p.single, ext_ctr);
+  const bool pivot = p.tp.strategy == CG_STRATEGY_PIVOT;
+  if (p.small) *sw = carve_small(c, p.cap, p.ucap, p.ell, true, !pivot, false, un, ext_ctr);
+  else
+    *ww = carve_wide(c, un, p.cap, p.ucap, p.ell, true, true, false, !pivot, p.single && !pivot,
+                     ext_ctr);
+  if (pivot) *pw = carve_pivot(c, p.ucap, p.ell);
 }
 
 size_t scene_ws_bytes(const ScenePlan& p) {
   Carve m{nullptr};
   SmallWs sw;
   WideWs ww;
+  PivotWs pw;
   DevCounters dummy;
-  carve_scene(m, p, &dummy, &sw, &ww);
+  carve_scene(m, p, &dummy, &sw, &ww, &pw);
   return m.off + 256;
 }
 
@@ -712,19 +816,23 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   Carve c{ws};
   SmallWs w{};
   WideWs ww{};
-  carve_scene(c, plan, ctr, &w, &ww);
+  PivotWs pw{};
+  carve_scene(c, plan, ctr, &w, &ww, &pw);
   const int64_t n = plan.n;
   const int ell = plan.ell;
+  const int strategy = plan.tp.strategy;
+  const bool pivot = strategy == CG_STRATEGY_PIVOT;
   cg_status st;
   if (plan.small) {
-    CG_CUDA(launch_clear_build(w.tkeys, plan.cap, w.status, ne_status_words(plan.ucap), w.ctr, s),
+    CG_CUDA(launch_clear_build(w.tkeys, plan.cap, pivot ? nullptr : w.status,
+                               pivot ? 0 : ne_status_words(plan.ucap), w.ctr, s),
             "clearing table");
     mark(ctx, "clear", s);
     if (n > 0) {
-      // FMA sign kernel by default; CG_SIGN_KERNEL=tc selects the tensor-core
-      // one (exact as well; slower on the benchmark workload).
+      // The tuned sign kernel; the environment variable CG_SIGN_KERNEL=tc
+      // forces the tensor-core one (both exact).
       const char* sk = std::getenv("CG_SIGN_KERNEL");
-      const bool tc = sk && std::strcmp(sk, "tc") == 0;
+      const bool tc = plan.tp.sign_kernel == 1 || (sk && std::strcmp(sk, "tc") == 0);
       CG_CUDA(tc ? launch_pack_tc_insert(pa, w.table(true), w.spill, s)
                  : launch_pack_insert(pa, w.table(true), s),
               "sign vectors + dedup");
@@ -733,22 +841,50 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     st = dedup_small_tail(w, ell, word_bits, cells, cells_cap, s);
     if (st) return st;
     mark(ctx, "sort_number", s);
-    st = neighbors_small_steps(w, ell, CG_STRATEGY_HASH, edges, edges_cap, s);
+    st = pivot ? pivot_steps(w.cells, 1, ell, plan.tp.pivots, w.ctr, pw, plan.ucap, edges,
+                             edges_cap, s)
+               : neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
     if (st) return st;
     mark(ctx, "neighbors_edges", s);
     return CG_OK;
   }
   const int w64 = (ell + 63) / 64;
-  if (!plan.single) {
+  if (!plan.single || pivot) {
     CG_CUDA(launch_zero_counters(ww.ctr, s), "counters");
     if (n > 0) CG_CUDA(launch_pack_store(pa, 64, ww.keys64, s), "sign vectors");
     mark(ctx, "pack", s);
-    st = dedup_wide_steps(ww, ww.keys64, n, ell, false, s);
-    if (st) return st;
-    CG_CUDA(launch_write_cells(ww.cells, ell, word_bits, cells, cells_cap, ww.ctr, plan.ucap, s),
-            "writing cells");
+    if (plan.single) {
+      // Distinct rows by hash, sorted inside one cluster when they fit.
+      CG_CUDA(launch_fill_u64(ww.slots, kEmpty, plan.cap, s), "clearing table");
+      WideTable dt{ww.slots, uint32_t(plan.cap - 1), ww.idx0, uint32_t(plan.ucap), ww.ctr};
+      CG_CUDA(launch_insert_wide(ww.keys64, n, w64, dt, s), "inserting vectors");
+      ClusterSortOut o{ww.cells, cells, cells_cap, word_bits, ell, SmallTable{}, ww.ctr};
+      bool done = false;
+      CG_CUDA(cluster_sort(ww.keys64, ww.idx0, &ww.ctr->n_unique, plan.ucap, ell, o, s, &done),
+              "sorting cells (cluster)");
+      if (!done) {
+        uint32_t* sorted = nullptr;
+        CG_CUDA(sort_wide(ww.keys64, w64, ell, ww.idx0, ww.idx1, ww.kw0, ww.kw1,
+                          &ww.ctr->n_unique, plan.ucap, ww.radix, s, &sorted),
+                "sorting cells");
+        CG_CUDA(launch_gather_rows(ww.keys64, w64, sorted, &ww.ctr->n_unique, plan.ucap, ww.cells,
+                                   s),
+                "gathering cells");
+        CG_CUDA(launch_write_cells(ww.cells, ell, word_bits, cells, cells_cap, ww.ctr, plan.ucap,
+                                   s),
+                "writing cells");
+      }
+    } else {
+      st = dedup_wide_steps(ww, ww.keys64, n, ell, false, s);
+      if (st) return st;
+      CG_CUDA(launch_write_cells(ww.cells, ell, word_bits, cells, cells_cap, ww.ctr, plan.ucap,
+                                 s),
+              "writing cells");
+    }
     mark(ctx, "dedup_sort", s);
-    st = neighbors_wide_steps(ww, ell, CG_STRATEGY_HASH, edges, edges_cap, s);
+    st = pivot ? pivot_steps(ww.cells, w64, ell, plan.tp.pivots, ww.ctr, pw, plan.ucap, edges,
+                             edges_cap, s)
+               : neighbors_wide_steps(ww, ell, strategy, edges, edges_cap, s);
     if (st) return st;
     mark(ctx, "neighbors_edges", s);
     return CG_OK;
@@ -779,9 +915,10 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   }
   mark(ctx, "dedup_sort", s);
   WideTable it{ww.slots2, uint32_t(plan.cap - 1), nullptr, 0, ww.ctr};
-  CG_CUDA(launch_index_wide(ww.cells, w64, ell, it, ww.fp, plan.ucap, s), "fingerprint index");
-  CG_CUDA(launch_neighbors_emit_wide(ww.cells, w64, ell, it, ww.fp, CG_STRATEGY_HASH, ww.status,
-                                     edges, edges_cap, plan.ucap, s),
+  if (strategy != CG_STRATEGY_SORTED)
+    CG_CUDA(launch_index_wide(ww.cells, w64, ell, it, ww.fp, plan.ucap, s), "fingerprint index");
+  CG_CUDA(launch_neighbors_emit_wide(ww.cells, w64, ell, it, ww.fp, strategy, ww.status, edges,
+                                     edges_cap, plan.ucap, s),
           "neighbour search and edge output");
   mark(ctx, "neighbors_edges", s);
   return CG_OK;
@@ -815,7 +952,7 @@ cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const in
                      const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
                      uint32_t* edges, int64_t edges_cap, size_t cap, cudaStream_t s,
                      DevCounters* host) {
-  const ScenePlan plan = plan_scene(n, ell, cap);
+  const ScenePlan plan = plan_scene(n, ell, cap, ctx->tune[cg_tune_bucket(ell)]);
   cg_status st = ensure_pool(ctx, scene_ws_bytes(plan));
   if (st) return st;
   PackArgs pa{pts, n, d, a, b, ell};
@@ -1071,7 +1208,7 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       if (it != ctx->cap_hint.end()) cap = std::max(cap, it->second);
       cap = std::min(cap, full_cap(sc.n));
       BatchScene& b = bs[size_t(i)];
-      b.plan = plan_scene(sc.n, sc.ell, cap);
+      b.plan = plan_scene(sc.n, sc.ell, cap, ctx->tune[cg_tune_bucket(sc.ell)]);
       b.d = sc.d;
       b.w = (sc.ell + 63) / 64;
       b.ecap = std::max<size_t>(1024, 4 * b.plan.ucap + 64);
@@ -1165,6 +1302,8 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       mixin(uint64_t(sc.n) * 4096 + uint64_t(sc.ell) * 8 + uint64_t(sc.d));
       mixin(bs[size_t(i)].plan.cap);
       mixin(bs[size_t(i)].ecap);
+      const cg_tune_params& tp = bs[size_t(i)].plan.tp;
+      mixin(uint64_t(tp.strategy) * 4096 + uint64_t(tp.pivots) * 16 + uint64_t(tp.sign_kernel));
     }
     if (ctx->bgraph && ctx->bgraph_sig == sig) {
       CG_CUDA(cudaGraphLaunch(ctx->bgraph, s0), "replaying the batch graph");
@@ -1243,4 +1382,152 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     return CG_OK;
   }
   return fail(CG_ERR_INTERNAL, "batch did not settle after repeated resizing");
+}
+
+// --------------------------------- tuning ----------------------------------
+
+extern "C" int cg_tune_bucket(int ell) {
+  static const int kLimit[CG_TUNE_BUCKETS] = {16, 32, 64, 128, 256, 1024, 4096};
+  if (ell < 1) return -1;
+  for (int b = 0; b < CG_TUNE_BUCKETS; ++b)
+    if (ell <= kLimit[b]) return b;
+  return -1;
+}
+
+extern "C" cg_status cg_ctx_tune_get(const cg_ctx* ctx, int bucket, cg_tune_params* out) {
+  if (!ctx || !out) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  if (bucket < 0 || bucket >= CG_TUNE_BUCKETS) return fail(CG_ERR_INVALID_ARG, "no such bucket");
+  *out = ctx->tune[bucket];
+  return CG_OK;
+}
+
+extern "C" cg_status cg_ctx_tune_set(cg_ctx* ctx, int bucket, const cg_tune_params* p) {
+  if (!ctx || !p) return fail(CG_ERR_INVALID_ARG, "NULL argument");
+  if (bucket < 0 || bucket >= CG_TUNE_BUCKETS) return fail(CG_ERR_INVALID_ARG, "no such bucket");
+  if (p->strategy != CG_STRATEGY_HASH && p->strategy != CG_STRATEGY_SORTED &&
+      p->strategy != CG_STRATEGY_PIVOT)
+    return fail(CG_ERR_INVALID_ARG, "strategy must be HASH, SORTED or PIVOT");
+  if (p->pivots < 1 || p->pivots > 8) return fail(CG_ERR_INVALID_ARG, "pivots must be 1..8");
+  if (p->sign_kernel != 0 && p->sign_kernel != 1)
+    return fail(CG_ERR_INVALID_ARG, "sign_kernel must be 0 or 1");
+  ctx->tune[bucket] = *p;
+  return CG_OK;
+}
+
+namespace {
+
+// Device outputs of one scene for the autotuner (grown on CG_ERR_CAPACITY).
+struct TuneOut {
+  void* cells = nullptr;
+  int64_t cells_cap = 0;
+  uint32_t* edges = nullptr;
+  int64_t edges_cap = 0;
+};
+
+cg_status tune_build(cg_ctx* ctx, const cg_scene& sc, TuneOut& o, cudaStream_t s) {
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    int64_t nc = 0, ne = 0;
+    cg_status st = build_checked(ctx, sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell, 64, o.cells,
+                                 o.cells_cap, &nc, o.edges, o.edges_cap, &ne, s);
+    if (st != CG_ERR_CAPACITY) return st;
+    CG_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+    const int w = (sc.ell + 63) / 64;
+    if (nc > o.cells_cap) {
+      cudaFree(o.cells);
+      o.cells = nullptr;
+      o.cells_cap = nc;
+      CG_CUDA(cudaMalloc(&o.cells, size_t(nc) * w * 8 + 8), "autotune outputs");
+    }
+    if (ne > o.edges_cap) {
+      cudaFree(o.edges);
+      o.edges = nullptr;
+      o.edges_cap = ne;
+      CG_CUDA(cudaMalloc(&o.edges, size_t(ne) * 8 + 8), "autotune outputs");
+    }
+  }
+  return fail(CG_ERR_INTERNAL, "autotune outputs did not settle");
+}
+
+}  // namespace
+
+extern "C" cg_status cg_ctx_autotune(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, int reps,
+                                     double* chosen_ms) {
+  if (!ctx || n_scenes < 0 || (n_scenes > 0 && !scenes) || reps < 1)
+    return fail(CG_ERR_INVALID_ARG, "bad argument");
+  for (int i = 0; i < n_scenes; ++i) {
+    const cg_scene& sc = scenes[i];
+    std::string why;
+    if (!check_common(sc.n, sc.ell, 64, &why) || sc.d < 1 || sc.d > 4 ||
+        (sc.n > 0 && (!sc.pts || !sc.a || !sc.b)))
+      return fail(CG_ERR_INVALID_ARG, "scene " + std::to_string(i) + ": invalid");
+  }
+  DeviceGuard g(ctx->device);
+  if (chosen_ms)
+    for (int b = 0; b < CG_TUNE_BUCKETS; ++b) chosen_ms[b] = 0.0;
+  std::vector<std::vector<int>> by_bucket(CG_TUNE_BUCKETS);
+  for (int i = 0; i < n_scenes; ++i) {
+    auto& v = by_bucket[size_t(cg_tune_bucket(scenes[i].ell))];
+    if (v.size() < 16) v.push_back(i);
+  }
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "autotune stream");
+  std::vector<TuneOut> outs(static_cast<size_t>(n_scenes));
+  cg_status result = CG_OK;
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    result = fail(CG_ERR_CUDA, "autotune events");
+  for (int b = 0; b < CG_TUNE_BUCKETS && result == CG_OK; ++b) {
+    if (by_bucket[size_t(b)].empty()) continue;
+    std::vector<cg_tune_params> cand = {{CG_STRATEGY_HASH, 4, 0},
+                                        {CG_STRATEGY_SORTED, 4, 0},
+                                        {CG_STRATEGY_PIVOT, 2, 0},
+                                        {CG_STRATEGY_PIVOT, 3, 0},
+                                        {CG_STRATEGY_PIVOT, 4, 0}};
+    if (b <= 2) {  // l <= 64: the tensor-core sign kernel too
+      const size_t k = cand.size();
+      for (size_t c = 0; c < k; ++c) cand.push_back({cand[c].strategy, cand[c].pivots, 1});
+    }
+    double best = 1e300;
+    cg_tune_params best_p = ctx->tune[b];
+    for (const cg_tune_params& p : cand) {
+      ctx->tune[b] = p;
+      for (int i : by_bucket[size_t(b)]) {  // warm-up (and output sizing)
+        result = tune_build(ctx, scenes[i], outs[size_t(i)], s);
+        if (result) break;
+      }
+      if (result) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && result == CG_OK; ++r)
+        for (int i : by_bucket[size_t(b)]) {
+          result = tune_build(ctx, scenes[i], outs[size_t(i)], s);
+          if (result) break;
+        }
+      cudaEventRecord(e1, s);
+      if (result) break;
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        result = fail(CG_ERR_CUDA, "autotune timing");
+        break;
+      }
+      const double per = double(ms) / reps;
+      if (per < best) {
+        best = per;
+        best_p = p;
+      }
+    }
+    ctx->tune[b] = best_p;
+    if (chosen_ms && result == CG_OK) chosen_ms[b] = best;
+  }
+  ctx->timing = timing;
+  cudaStreamSynchronize(s);
+  for (auto& o : outs) {
+    if (o.cells) cudaFree(o.cells);
+    if (o.edges) cudaFree(o.edges);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  return result;
 }

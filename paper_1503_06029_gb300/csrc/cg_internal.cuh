@@ -315,6 +315,31 @@ cudaError_t launch_neighbors_emit_wide(const uint64_t* cells, int w64, int ell, 
                                        unsigned long long* status, uint32_t* edges,
                                        int64_t edges_cap, size_t max_n, cudaStream_t s);
 
+// PIVOT strategy (cg_pivot.cu): keys of h distances to pivot cells, sorted
+// (radix_sort_u64 over pivot_sort_bits bits), indexed by first position, then
+// a counting and a writing pass of the neighbour search.
+int pivot_max_h(int ell);
+int pivot_sort_bits(int ell, int h);
+cudaError_t launch_pivot_keys(const uint64_t* cells, int w64, int ell, int h,
+                              const DevCounters* ctr, size_t max_n, uint64_t* key_by_cell,
+                              uint64_t* skeys, uint32_t* sidx, cudaStream_t s);
+cudaError_t launch_pivot_index(const uint64_t* skeys, const DevCounters* ctr, size_t max_n,
+                               uint64_t* tkeys, uint32_t* tvals, size_t tcap, DevCounters* wctr,
+                               cudaStream_t s);
+// Counting pass (write = false: counts[i]) or writing pass (write = true:
+// edges at offsets[i] + running fill[i], below edges_cap).
+cudaError_t launch_pivot_search(const uint64_t* cells, int w64, int ell, int h,
+                                const DevCounters* ctr, size_t max_n,
+                                const uint64_t* key_by_cell, const uint64_t* skeys,
+                                const uint32_t* sidx, const uint64_t* tkeys, const uint32_t* tvals,
+                                size_t tcap, uint32_t* counts, const unsigned long long* offsets,
+                                uint32_t* fill, uint32_t* edges, int64_t edges_cap, bool write,
+                                cudaStream_t s);
+// Orders each cell's edge segment by partner.
+cudaError_t launch_pivot_order(const DevCounters* ctr, size_t max_n, const uint32_t* counts,
+                               const unsigned long long* offsets, uint32_t* edges,
+                               int64_t edges_cap, cudaStream_t s);
+
 // Batch gather: per scene, its counters, internal cells (w words per cell,
 // up to ucap cells) and internal edges (up to ecap).
 struct BatchEntry {

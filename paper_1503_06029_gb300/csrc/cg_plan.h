@@ -11,6 +11,11 @@
 
 namespace cg {
 
+// Library defaults of the tunables: HASH lookups, 4 pivots, fp32 sign kernel.
+cg_tune_params default_tune();
+// Valid, clamped copy of p for vectors of l bits (h within 1..pivot_max_h(l)).
+cg_tune_params sanitize_tune(const cg_tune_params& p, int ell);
+
 // One scene's build: sizes and strategy.
 struct ScenePlan {
   int64_t n;
@@ -19,9 +24,10 @@ struct ScenePlan {
   size_t ucap;  // distinct-vector capacity
   bool small;   // l <= 64
   bool single;  // wide, single-pass neighbour kernel and cluster sort
+  cg_tune_params tp;
 };
 
-ScenePlan plan_scene(int64_t n, int ell, size_t cap);
+ScenePlan plan_scene(int64_t n, int ell, size_t cap, const cg_tune_params& tp);
 
 // Device workspace of one scene (without its counters and outputs).
 size_t scene_ws_bytes(const ScenePlan& p);

@@ -54,6 +54,7 @@ struct Req {
   // plan
   size_t cap = 0;
   size_t ecap = 0;
+  cg_tune_params tp{};
   ScenePlan plan{};
   int w = 1;
   size_t in_bytes = 0;  // copied inputs (host inputs only)
@@ -94,6 +95,7 @@ struct cg_server {
   int64_t next_id = 1;
   int64_t submitted = 0, completed = 0, failed = 0, retried = 0;
   int inject_alloc_fail = 0;
+  cg_tune_params tune[CG_TUNE_BUCKETS];
   bool stop = false;
   std::thread th;
 };
@@ -107,7 +109,7 @@ double now_us(const cg_server* s) {
 // Sizes of a request's two blocks for its current capacities.
 void plan_request(Req* r) {
   const cg_scene& sc = r->sc;
-  r->plan = plan_scene(sc.n, sc.ell, r->cap);
+  r->plan = plan_scene(sc.n, sc.ell, r->cap, r->tp);
   r->w = (sc.ell + 63) / 64;
   if (r->ecap == 0) r->ecap = std::max<size_t>(1024, 4 * r->plan.ucap + 64);
   r->in_bytes = r->on_host ? align256(size_t(sc.n) * sc.d * 4) + align256(size_t(sc.ell) * sc.d * 4) +
@@ -391,6 +393,7 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
   s->budget = hbm_budget_bytes;
   s->max_slots = max_inflight;
   s->t0 = Clock::now();
+  for (auto& t : s->tune) t = default_tune();
   auto bail = [&](cudaError_t e, const char* what) {
     cudaGetLastError();
     for (auto st : s->streams) cudaStreamDestroy(st);
@@ -440,6 +443,10 @@ cg_status cg_server_submit(cg_server* srv, const cg_scene* scene, int inputs_on_
   r->on_host = inputs_on_host != 0;
   r->srv = srv;
   r->cap = std::min(initial_cap(sc.n, sc.d, sc.ell), full_cap(sc.n));
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    r->tp = srv->tune[cg_tune_bucket(sc.ell)];
+  }
   plan_request(r);
   {
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -579,6 +586,18 @@ cg_status cg_server_get_stats(cg_server* srv, cg_server_stats* out) {
   out->bytes_in_use = srv->in_use;
   out->peak_bytes = srv->peak;
   out->max_running = srv->max_running;
+  return CG_OK;
+}
+
+cg_status cg_server_use_tuning(cg_server* srv, const cg_ctx* ctx) {
+  if (!srv || !ctx) return srv_fail(CG_ERR_INVALID_ARG, "NULL argument");
+  cg_tune_params t[CG_TUNE_BUCKETS];
+  for (int b = 0; b < CG_TUNE_BUCKETS; ++b) {
+    const cg_status st = cg_ctx_tune_get(ctx, b, &t[b]);
+    if (st) return st;
+  }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  for (int b = 0; b < CG_TUNE_BUCKETS; ++b) srv->tune[b] = t[b];
   return CG_OK;
 }
 

@@ -172,7 +172,7 @@ def test_dedup_all_duplicates_and_empty(dev):
 
 # ------------------------------ steps 3-4 --------------------------------
 
-@pytest.mark.parametrize("strategy", ["hash", "sorted"])
+@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot"])
 @pytest.mark.parametrize("kind,wb", [("lines", 32), ("planes64", 64), ("planes200", 64),
                                      ("planes200", 32), ("chains", 64), ("chains130", 64)])
 def test_neighbors_match_oracle(dev, kind, wb, strategy):
@@ -184,12 +184,44 @@ def test_neighbors_match_oracle(dev, kind, wb, strategy):
     assert len(want) > 0
 
 
-def test_neighbors_hypercube(dev):
+@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot"])
+def test_neighbors_hypercube(dev, strategy):
     ell = 12
     cells = np.arange(1 << ell, dtype=np.uint64).reshape(-1, 1)
-    got = edges_np(cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64))
+    got = edges_np(cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64, strategy=strategy))
     assert len(got) == ell * (1 << (ell - 1))
     assert np.array_equal(got, oracle.neighbors(cells, ell, 64))
+
+
+@pytest.mark.parametrize("pivots", ["1", "2", "5", "8"])
+def test_neighbors_pivot_counts(dev, pivots, monkeypatch):
+    """Any number of pivots gives the same edges (wide and small vectors)."""
+    monkeypatch.setenv("CG_PIVOTS", pivots)
+    for kind, wb in (("planes64", 64), ("chains130", 64), ("planes200", 32)):
+        keys, ell = _dedup_case(kind, wb)
+        cells = oracle.dedup(keys, ell, wb)
+        got = cellgraph.neighbors_h1(words_dev(cells, wb, dev), ell, wb, strategy="pivot")
+        assert np.array_equal(edges_np(got), oracle.neighbors(cells, ell, wb))
+
+
+def test_neighbors_pivot_wide_4096(dev):
+    """The longest vectors (l = 4096, 64 words): random rows plus one-bit
+    variants at every word position."""
+    rng = np.random.default_rng(17)
+    ell = 4096
+    base = rng.integers(0, 2**63, size=(300, 64), dtype=np.int64).astype(np.uint64)
+    rows = [base]
+    for k in range(0, ell, 37):
+        v = base[k % 300].copy()
+        v[k // 64] ^= np.uint64(1) << np.uint64(k % 64)
+        rows.append(v[None])
+    keys = np.concatenate(rows)
+    cells = oracle.dedup(keys, ell, 64)
+    want = oracle.neighbors(cells, ell, 64)
+    assert len(want) > 50
+    for strategy in ("hash", "sorted", "pivot"):
+        got = cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64, strategy=strategy)
+        assert np.array_equal(edges_np(got), want), strategy
 
 
 def test_neighbors_edge_capacity(dev):
@@ -402,6 +434,9 @@ def test_full_size_chains(dev):
     cells = cellgraph.dedup_cells(keys_d, 1024, 64)
     del keys_d
     edges = cellgraph.neighbors_h1(cells, 1024, 64)
+    edges_pivot = cellgraph.neighbors_h1(cells, 1024, 64, strategy="pivot")
+    assert torch.equal(edges_pivot, edges)
+    del edges_pivot
     got_c = words_np(cells, 64)
     got_e = edges_np(edges).astype(np.int64)
     want_c = oracle.dedup(ch.keys, 1024, 64)
@@ -522,3 +557,60 @@ def test_batch_capacity_contract(ctx, dev):
         assert nc[i] == len(want_c) and ne[i] == len(want_e)
     assert co[S] == sum(int(x) * ((s.ell + 63) // 64) for x, s in zip(nc, scenes))
     assert (cells == -7).all() and (edges == -7).all()
+
+
+# ------------------------------ tuning ------------------------------------
+
+def _tuning_scenes():
+    return [inputs.planes_3d(n=60_000, ell=24, seed=31), inputs.planes_3d(n=80_000, ell=64, seed=32),
+            inputs.planes_3d(n=50_000, ell=200, seed=33),
+            inputs.planes_3d(n=20_000, ell=1500, seed=34)]
+
+
+@pytest.mark.parametrize("setting", [("hash", 4, 0), ("sorted", 4, 0), ("pivot", 1, 0),
+                                     ("pivot", 3, 0), ("pivot", 4, 1), ("hash", 4, 1)])
+def test_build_under_every_tuning(dev, setting):
+    strategy, pivots, sk = setting
+    c2 = cellgraph.Context(0)
+    try:
+        for b in range(cellgraph.TUNE_BUCKETS):
+            c2.tune_set(b, strategy, pivots, sk)
+        for sc in _tuning_scenes():
+            cells, edges = c2.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
+            want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+            assert np.array_equal(words_np(cells, 64).reshape(want_c.shape), want_c)
+            assert np.array_equal(edges_np(edges), want_e)
+    finally:
+        c2.close()
+
+
+def test_autotune_keeps_results(dev, tmp_path):
+    scenes = _tuning_scenes() + _batch_scenes(12, 40_000, seed=35)
+    dsc = [(T(s.pts, dev), T(s.a, dev), T(s.b, dev)) for s in scenes]
+    c2 = cellgraph.Context(0)
+    try:
+        chosen = c2.autotune(dsc, reps=1)
+        buckets = {cellgraph.load_library().cg_tune_bucket(int(s.ell)) for s in scenes}
+        assert set(chosen) == buckets
+        path = str(tmp_path / "tune.json")
+        c2.save_tuning(path, "test-gpu")
+        c3 = cellgraph.Context(0)
+        assert c3.load_tuning(path, "test-gpu")
+        assert c3.tuning() == c2.tuning()
+        c3.close()
+        got = c2.build_batch(dsc)
+        for sc, (c, e) in zip(scenes, got):
+            want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+            assert np.array_equal(words_np(c, 64).reshape(want_c.shape), want_c)
+            assert np.array_equal(edges_np(e), want_e)
+        with cellgraph.Server(0, hbm_budget_bytes=4 << 30, max_inflight=4) as srv:
+            srv.use_tuning(c2)
+            ts = [srv.submit(s.pts, s.a, s.b) for s in scenes[:4]]
+            for sc, t in zip(scenes, ts):
+                srv.wait(t, 60.0)
+                cells, edges = srv.fetch(t)
+                want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+                assert np.array_equal(cells.reshape(want_c.shape), want_c)
+                assert np.array_equal(edges, want_e)
+    finally:
+        c2.close()
