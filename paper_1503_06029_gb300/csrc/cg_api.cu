@@ -249,16 +249,16 @@ struct PivotWs {
   uint32_t* i0;
   uint32_t* i1;
   void* radix;
-  uint64_t* tkeys;
-  uint32_t* tvals;
+  void* table;
   size_t tcap;
+  uint32_t* hbuf;
   uint32_t* fill;
   uint32_t* counts;
   unsigned long long* offsets;
   void* scan;
 };
 
-PivotWs carve_pivot(Carve& c, size_t ucap, int ell) {
+PivotWs carve_pivot(Carve& c, size_t ucap) {
   PivotWs p{};
   const size_t u = ucap > 0 ? ucap : 1;
   p.kcell = c.take<uint64_t>(u);
@@ -267,9 +267,9 @@ PivotWs carve_pivot(Carve& c, size_t ucap, int ell) {
   p.i0 = c.take<uint32_t>(u);
   p.i1 = c.take<uint32_t>(u);
   p.radix = c.take_bytes(radix_scratch_bytes(u));
-  p.tcap = std::max<size_t>(1024, next_pow2(2 * u));
-  p.tkeys = c.take<uint64_t>(p.tcap);
-  p.tvals = c.take<uint32_t>(p.tcap);
+  p.tcap = pivot_table_slots(u);
+  p.table = c.take<uint64_t>(2 * p.tcap);
+  p.hbuf = c.take<uint32_t>(pivot_hit_words(u));
   p.fill = c.take<uint32_t>(u);
   p.counts = c.take<uint32_t>(u);
   p.offsets = c.take<unsigned long long>(u);
@@ -326,7 +326,8 @@ cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t*
 cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
                       const PivotWs& p, size_t ucap, uint32_t* edges, int64_t edges_cap,
                       cudaStream_t s) {
-  CG_CUDA(launch_fill_u64(p.tkeys, kEmpty, p.tcap, s), "clearing the bucket table");
+  CG_CUDA(launch_fill_u64(static_cast<uint64_t*>(p.table), kEmpty, 2 * p.tcap, s),
+          "clearing the bucket table");
   CG_CUDA(launch_pivot_keys(cells, w64, ell, h, ctr, ucap, p.kcell, p.k0, p.i0, s),
           "pivot distances");
   bool in1 = false;
@@ -335,17 +336,10 @@ cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounter
           "sorting by pivot distances");
   const uint64_t* sk = in1 ? p.k1 : p.k0;
   const uint32_t* si = in1 ? p.i1 : p.i0;
-  CG_CUDA(launch_pivot_index(sk, ctr, ucap, p.tkeys, p.tvals, p.tcap, ctr, s), "bucket index");
-  CG_CUDA(launch_pivot_search(cells, w64, ell, h, ctr, ucap, p.kcell, sk, si, p.tkeys, p.tvals,
-                              p.tcap, p.counts, nullptr, nullptr, nullptr, 0, false, s),
-          "pivot neighbour search (count)");
-  CG_CUDA(scan_exclusive_u32(p.counts, p.offsets, &ctr->n_unique, ucap, &ctr->n_edges, p.scan, s),
-          "edge offsets");
-  CG_CUDA(launch_pivot_search(cells, w64, ell, h, ctr, ucap, p.kcell, sk, si, p.tkeys, p.tvals,
-                              p.tcap, p.counts, p.offsets, p.fill, edges, edges_cap, true, s),
-          "pivot neighbour search (write)");
-  CG_CUDA(launch_pivot_order(ctr, ucap, p.counts, p.offsets, edges, edges_cap, s),
-          "ordering edges");
+  CG_CUDA(launch_pivot_index(sk, ctr, ucap, p.table, p.tcap, ctr, s), "bucket index");
+  CG_CUDA(launch_pivot_edges(cells, w64, ell, h, ctr, ucap, p.kcell, si, p.table, p.tcap,
+                             p.counts, p.hbuf, p.offsets, p.fill, p.scan, edges, edges_cap, s),
+          "pivot neighbour search and edge output");
   return CG_OK;
 }
 
@@ -690,7 +684,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     Carve c{nullptr};
     if (small) carve_small(c, cap, un, ell, false, true, true);
     else carve_wide(c, un, cap, un, ell, false, false, false, true);
-    if (pivot) carve_pivot(c, un, ell);
+    if (pivot) carve_pivot(c, un);
     if (!ws) {
       *ws_bytes = c.off + 256;
       return CG_OK;
@@ -712,7 +706,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
     cg_status st;
     if (pivot) {
-      st = pivot_steps(w.cells, 1, ell, env_pivots(ell), w.ctr, carve_pivot(c, un, ell), un,
+      st = pivot_steps(w.cells, 1, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un,
                        edges, edges_cap, s);
     } else {
       if (table) CG_CUDA(launch_index_small(w.cells, w.table(false), un, s), "indexing cells");
@@ -726,7 +720,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
     CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
     cg_status st = pivot ? pivot_steps(w.cells, (ell + 63) / 64, ell, env_pivots(ell), w.ctr,
-                                       carve_pivot(c, un, ell), un, edges, edges_cap, s)
+                                       carve_pivot(c, un), un, edges, edges_cap, s)
                          : neighbors_wide_steps(w, ell, strategy, edges, edges_cap, s);
     if (st) return st;
     st = read_counters(w.ctr, &host, s);
@@ -794,7 +788,7 @@ void carve_scene(Carve& c, const ScenePlan& p, DevCounters* ext_ctr, SmallWs* sw
   else
     *ww = carve_wide(c, un, p.cap, p.ucap, p.ell, true, true, false, !pivot, p.single && !pivot,
                      ext_ctr);
-  if (pivot) *pw = carve_pivot(c, p.ucap, p.ell);
+  if (pivot) *pw = carve_pivot(c, p.ucap);
 }
 
 size_t scene_ws_bytes(const ScenePlan& p) {

@@ -428,14 +428,6 @@ __global__ void insert_wide(const uint64_t* __restrict__ keys, int64_t n, int w,
   }
 }
 
-__global__ void gather_word(const uint64_t* __restrict__ keys, int w, int j,
-                            const uint32_t* __restrict__ idx, const unsigned int* n_dev,
-                            uint32_t max_n, uint64_t* __restrict__ out) {
-  const uint32_t n = min(*n_dev, max_n);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    out[i] = keys[uint64_t(idx[i]) * w + j];
-}
-
 __global__ void gather_rows(const uint64_t* __restrict__ keys, int w,
                             const uint32_t* __restrict__ idx, const unsigned int* n_dev,
                             uint32_t max_n, uint64_t* __restrict__ out) {
@@ -978,22 +970,9 @@ cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const W
 cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
                       void* scratch, cudaStream_t s, uint32_t** sorted_idx) {
-  uint32_t* cur = idx0;
-  uint32_t* other = idx1;
-  *sorted_idx = cur;
-  if (max_n == 0) return cudaSuccess;
-  for (int j = 0; j < w64; ++j) {
-    const int bits = (j == w64 - 1) ? ell - 64 * (w64 - 1) : 64;
-    gather_word<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(keys, w64, j, cur, n_dev,
-                                                               uint32_t(max_n), kw0);
-    count_launch();
-    bool in1 = false;
-    cudaError_t e = radix_sort_u64(kw0, kw1, cur, other, n_dev, max_n, bits, scratch, s, &in1);
-    if (e != cudaSuccess) return e;
-    if (in1) std::swap(cur, other);
-  }
-  *sorted_idx = cur;
-  return cudaGetLastError();
+  (void)scratch;
+  return merge_sort_rows(keys, w64, ell, idx0, kw0, kw1, idx0, idx1, n_dev, max_n, s,
+                         sorted_idx);
 }
 
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,

@@ -203,6 +203,16 @@ cudaError_t radix_sort_u64(uint64_t* keys0, uint64_t* keys1, uint32_t* vals0, ui
                            const unsigned int* n_dev, size_t max_n, int bits, void* scratch,
                            cudaStream_t s, bool* result_in_1);
 
+// Value order of U = min(*n_dev, max_n) rows of W = ceil(l / 64) words
+// (l > 64): rows[idx_in[i]] (idx_in nullable: row i). Comparison merge sort
+// on row numbers with the top 64 bits cached; k0/k1 and i0/i1 are ping-pong
+// buffers of max_n items; *sorted_idx receives the buffer holding the sorted
+// row numbers.
+cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32_t* idx_in,
+                            uint64_t* k0, uint64_t* k1, uint32_t* i0, uint32_t* i1,
+                            const unsigned int* n_dev, size_t max_n, cudaStream_t s,
+                            uint32_t** sorted_idx);
+
 // out[i] = sum_{j<i} in[j] for i < *n_dev; *total = sum of all (device).
 cudaError_t scan_exclusive_u32(const uint32_t* in, unsigned long long* out,
                                const unsigned int* n_dev, size_t max_n,
@@ -316,29 +326,26 @@ cudaError_t launch_neighbors_emit_wide(const uint64_t* cells, int w64, int ell, 
                                        int64_t edges_cap, size_t max_n, cudaStream_t s);
 
 // PIVOT strategy (cg_pivot.cu): keys of h distances to pivot cells, sorted
-// (radix_sort_u64 over pivot_sort_bits bits), indexed by first position, then
-// a counting and a writing pass of the neighbour search.
+// (radix_sort_u64 over pivot_sort_bits bits), bucket table, then the
+// neighbour search and edge output.
 int pivot_max_h(int ell);
 int pivot_sort_bits(int ell, int h);
 cudaError_t launch_pivot_keys(const uint64_t* cells, int w64, int ell, int h,
                               const DevCounters* ctr, size_t max_n, uint64_t* key_by_cell,
                               uint64_t* skeys, uint32_t* sidx, cudaStream_t s);
+// Bucket table of pivot_table_slots(max_n) 16-byte entries (filled with
+// all-ones words before use).
+size_t pivot_table_slots(size_t max_n);
 cudaError_t launch_pivot_index(const uint64_t* skeys, const DevCounters* ctr, size_t max_n,
-                               uint64_t* tkeys, uint32_t* tvals, size_t tcap, DevCounters* wctr,
-                               cudaStream_t s);
-// Counting pass (write = false: counts[i]) or writing pass (write = true:
-// edges at offsets[i] + running fill[i], below edges_cap).
-cudaError_t launch_pivot_search(const uint64_t* cells, int w64, int ell, int h,
-                                const DevCounters* ctr, size_t max_n,
-                                const uint64_t* key_by_cell, const uint64_t* skeys,
-                                const uint32_t* sidx, const uint64_t* tkeys, const uint32_t* tvals,
-                                size_t tcap, uint32_t* counts, const unsigned long long* offsets,
-                                uint32_t* fill, uint32_t* edges, int64_t edges_cap, bool write,
-                                cudaStream_t s);
-// Orders each cell's edge segment by partner.
-cudaError_t launch_pivot_order(const DevCounters* ctr, size_t max_n, const uint32_t* counts,
-                               const unsigned long long* offsets, uint32_t* edges,
-                               int64_t edges_cap, cudaStream_t s);
+                               void* table, size_t tcap, DevCounters* wctr, cudaStream_t s);
+// Search + scan + edge output (ctr->n_edges = E); hbuf: pivot_hit_words(max_n)
+// words; scan: scan_scratch_bytes(max_n).
+size_t pivot_hit_words(size_t max_n);
+cudaError_t launch_pivot_edges(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
+                               size_t max_n, const uint64_t* key_by_cell, const uint32_t* sidx,
+                               const void* table, size_t tcap, uint32_t* counts, uint32_t* hbuf,
+                               unsigned long long* offsets, uint32_t* fill, void* scan,
+                               uint32_t* edges, int64_t edges_cap, cudaStream_t s);
 
 // Batch gather: per scene, its counters, internal cells (w words per cell,
 // up to ucap cells) and internal edges (up to ecap).

@@ -12,10 +12,11 @@
 // +-1 in every coordinate. Each candidate in those buckets is compared word
 // by word; a pair with exactly one differing bit k is an edge, reported from
 // the endpoint whose bit k is 0 (the smaller one, as for the other
-// strategies). The search runs twice: once to count each cell's edges (an
-// exclusive scan of the counts gives every cell's first output position), and
-// once, over the cells that have edges, to write them; a last pass orders
-// each cell's few edges by partner.
+// strategies). The search counts each cell's edges and keeps the first few
+// partners in a small per-cell buffer; an exclusive scan of the counts gives
+// every cell's first output position; cells whose partners all fit in the
+// buffer are written from it (in partner order), and only the rare cells with
+// more edges are searched again to write theirs, then ordered.
 //
 // Pivots: h cells spread over the sorted order (cells floor((2d+1) U / 2h)),
 // so that they are far apart in value; the choice does not change the output.
@@ -38,48 +39,64 @@ __device__ __forceinline__ uint32_t pivot_row(int d, int h, uint32_t u) {
   return uint32_t((uint64_t(2 * d + 1) * u) / uint64_t(2 * h));
 }
 
-// key of every cell (thread per cell): h distances of `bits` bits each.
+// Key of every cell: h distances of `bits` bits each. A group of gs lanes
+// (gs = W rounded up to a power of two, at most 32) works on one cell, lanes
+// over words, so that rows are read with coalesced loads.
 __global__ void __launch_bounds__(kThreads)
-    pivot_keys(const uint64_t* __restrict__ cells, int w, int h, int bits,
+    pivot_keys(const uint64_t* __restrict__ cells, int w, int gs, int h, int bits,
                const DevCounters* ctr, uint32_t max_n, uint64_t* __restrict__ key_by_cell,
                uint64_t* __restrict__ skeys, uint32_t* __restrict__ sidx) {
   if (ctr->overflow) return;
   const uint32_t u = min(ctr->n_unique, max_n);
   if (u == 0) return;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
-    const uint64_t* xi = cells + uint64_t(i) * w;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % gs;
+  const uint32_t per_warp = 32 / gs;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t groups = (u + per_warp - 1) / per_warp;
+  for (uint32_t gi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < groups;
+       gi += warps) {
+    const uint32_t i = gi * per_warp + lane / gs;
+    const bool live = i < u;
+    const uint64_t* xi = cells + uint64_t(live ? i : 0) * w;
     uint64_t key = 0;
     for (int d = 0; d < h; ++d) {
       const uint64_t* pd = cells + uint64_t(pivot_row(d, h, u)) * w;
       uint32_t dist = 0;
-      for (int q = 0; q < w; ++q) dist += __popcll(xi[q] ^ pd[q]);
+      if (live)
+        for (int q = sub; q < w; q += gs) dist += __popcll(xi[q] ^ pd[q]);
+      for (int o = gs >> 1; o > 0; o >>= 1) dist += __shfl_xor_sync(0xffffffffu, dist, o);
       key |= uint64_t(dist) << (bits * d);
     }
-    key_by_cell[i] = key;
-    skeys[i] = key;
-    sidx[i] = i;
+    if (live && sub == 0) {
+      key_by_cell[i] = key;
+      skeys[i] = key;
+      sidx[i] = i;
+    }
   }
 }
 
-// First position of every distinct key in the sorted key array, in an
-// open-addressing table (key -> position).
+// Bucket table: for every distinct key of the sorted key array, one
+// 16-byte entry (key, start | count << 32) in an open-addressing table, so
+// that a lookup reads one sector.
 __global__ void __launch_bounds__(kThreads)
     pivot_index(const uint64_t* __restrict__ skeys, const DevCounters* ctr, uint32_t max_n,
-                uint64_t* __restrict__ tkeys, uint32_t* __restrict__ tvals, uint32_t tmask,
-                int tshift, DevCounters* wctr) {
+                ulonglong2* __restrict__ table, uint32_t tmask, int tshift, DevCounters* wctr) {
   if (ctr->overflow) return;
   const uint32_t u = min(ctr->n_unique, max_n);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < u; t += gridDim.x * blockDim.x) {
     const uint64_t key = skeys[t];
     if (t > 0 && skeys[t - 1] == key) continue;
+    uint32_t cnt = 1;
+    while (t + cnt < u && skeys[t + cnt] == key) ++cnt;
     uint32_t slot = home_slot(key, tshift);
     bool placed = false;
     for (uint32_t probe = 0; probe <= tmask; ++probe) {
       const unsigned long long old =
-          atomicCAS(reinterpret_cast<unsigned long long*>(tkeys + slot),
+          atomicCAS(reinterpret_cast<unsigned long long*>(&table[slot].x),
                     static_cast<unsigned long long>(kEmpty), static_cast<unsigned long long>(key));
       if (old == kEmpty) {
-        tvals[slot] = t;
+        table[slot].y = uint64_t(t) | (uint64_t(cnt) << 32);
         placed = true;
         break;
       }
@@ -89,39 +106,39 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-__device__ __forceinline__ int64_t bucket_start(const uint64_t* tkeys, const uint32_t* tvals,
-                                                uint32_t tmask, int tshift, uint64_t key) {
+// (start, count) of a bucket, count 0 when the key is absent.
+__device__ __forceinline__ uint64_t bucket_find(const ulonglong2* table, uint32_t tmask,
+                                                int tshift, uint64_t key) {
   uint32_t slot = home_slot(key, tshift);
   for (uint32_t probe = 0; probe <= tmask; ++probe) {
-    const uint64_t cur = tkeys[slot];
-    if (cur == key) return tvals[slot];
-    if (cur == kEmpty) return -1;
+    const ulonglong2 e = table[slot];
+    if (e.x == key) return e.y;
+    if (e.x == kEmpty) return 0;
     slot = (slot + 1) & tmask;
   }
-  return -1;
+  return 0;
 }
 
-// The search, in two modes. Lanes work on (cell, bucket pattern) pairs in
-// parallel: with P = 2^h patterns, a warp takes 32 / P consecutive cells
-// (P <= 32) or one cell with the patterns strided over the lanes (P > 32).
-// Each lane looks its bucket up and compares every candidate j > i of it
-// with cell i, word by word (XOR + popcount, stopping at the second
-// difference).
-//   kCount: counts[i] = number of hits of cell i.
-//   kWrite: hit (i, j) goes to edges[offsets[i] + fill[i]++] (positions below
-//           cap only); the order inside a cell's segment is fixed afterwards.
-// Cells without hits are skipped in kWrite.
+// The search. Lanes work on (cell, bucket pattern) pairs in parallel: with
+// P = 2^h patterns, a warp takes 32 / P consecutive cells (P <= 32) or one
+// cell with the patterns strided over the lanes (P > 32). Each lane looks its
+// bucket up and compares every candidate j > i of it with cell i, word by
+// word (XOR + popcount, stopping at the second difference).
+//   kCount: counts[i] = number of hits of cell i; the first kHitBuf partners
+//           are kept in hbuf[i][.].
+//   kWrite: cells with more than kHitBuf hits only: hit (i, j) goes to
+//           edges[offsets[i] + fill[i]++] (positions below cap only).
+constexpr int kHitBuf = 4;
 enum { kCount = 0, kWrite = 1 };
 
 template <int kMode>
 __global__ void __launch_bounds__(kThreads)
     pivot_search(const uint64_t* __restrict__ cells, int w, int ell, int h, int bits,
                  const DevCounters* ctr, uint32_t max_n, const uint64_t* __restrict__ key_by_cell,
-                 const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ sidx,
-                 const uint64_t* __restrict__ tkeys, const uint32_t* __restrict__ tvals,
+                 const uint32_t* __restrict__ sidx, const ulonglong2* __restrict__ table,
                  uint32_t tmask, int tshift, uint32_t* __restrict__ counts,
-                 const unsigned long long* __restrict__ offsets, uint32_t* __restrict__ fill,
-                 uint32_t* __restrict__ edges, int64_t cap) {
+                 uint32_t* __restrict__ hbuf, const unsigned long long* __restrict__ offsets,
+                 uint32_t* __restrict__ fill, uint32_t* __restrict__ edges, int64_t cap) {
   if (ctr->overflow) return;
   const uint32_t u = min(ctr->n_unique, max_n);
   const int lane = threadIdx.x & 31;
@@ -135,7 +152,7 @@ __global__ void __launch_bounds__(kThreads)
     const int g = P <= 32 ? lane / P : 0;
     const uint32_t i = gi * G + g;
     if (i >= u) continue;
-    if (kMode == kWrite && counts[i] == 0) continue;
+    if (kMode == kWrite && counts[i] <= uint32_t(kHitBuf)) continue;
     const uint64_t key = key_by_cell[i];
     const uint64_t* xi = cells + uint64_t(i) * w;
     for (int pat = P <= 32 ? lane % P : lane; pat < P; pat += 32) {
@@ -148,9 +165,9 @@ __global__ void __launch_bounds__(kThreads)
         target = up ? target + (1ull << (bits * d)) : target - (1ull << (bits * d));
       }
       if (!ok) continue;
-      const int64_t t0 = bucket_start(tkeys, tvals, tmask, tshift, target);
-      if (t0 < 0) continue;
-      for (uint32_t t = uint32_t(t0); t < u && skeys[t] == target; ++t) {
+      const uint64_t sc = bucket_find(table, tmask, tshift, target);
+      const uint32_t t0 = uint32_t(sc), tn = uint32_t(sc >> 32);
+      for (uint32_t t = t0; t < t0 + tn; ++t) {
         const uint32_t j = sidx[t];
         if (j <= i) continue;
         const uint64_t* xj = cells + uint64_t(j) * w;
@@ -158,7 +175,8 @@ __global__ void __launch_bounds__(kThreads)
         for (int q = 0; q < w && c < 2; ++q) c += __popcll(xj[q] ^ xi[q]);
         if (c != 1) continue;
         if (kMode == kCount) {
-          atomicAdd(&counts[i], 1u);
+          const uint32_t r = atomicAdd(&counts[i], 1u);
+          if (r < uint32_t(kHitBuf)) hbuf[uint64_t(i) * kHitBuf + r] = j;
         } else {
           const unsigned long long pos = offsets[i] + atomicAdd(&fill[i], 1u);
           if (pos < (unsigned long long)cap) {
@@ -171,9 +189,42 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Puts every cell's edges in increasing order of j (insertion sort of the
-// segment; segments are short: at most the cell's degree). Segments that do
-// not lie wholly below cap are left alone (the call then reports capacity).
+// Edges of the cells with at most kHitBuf hits, from the hit buffer, in
+// increasing order of j (thread per cell).
+__global__ void __launch_bounds__(kThreads)
+    pivot_emit(const DevCounters* ctr, uint32_t max_n, const uint32_t* __restrict__ counts,
+               const uint32_t* __restrict__ hbuf, const unsigned long long* __restrict__ offsets,
+               uint32_t* __restrict__ edges, int64_t cap) {
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
+    const uint32_t m = counts[i];
+    if (m == 0 || m > uint32_t(kHitBuf)) continue;
+    uint32_t v[kHitBuf];
+#pragma unroll
+    for (int q = 0; q < kHitBuf; ++q) v[q] = q < int(m) ? hbuf[uint64_t(i) * kHitBuf + q] : ~0u;
+#pragma unroll
+    for (int a = 1; a < kHitBuf; ++a)
+#pragma unroll
+      for (int b = a; b > 0; --b)
+        if (v[b - 1] > v[b]) {
+          const uint32_t t = v[b];
+          v[b] = v[b - 1];
+          v[b - 1] = t;
+        }
+    const unsigned long long o = offsets[i];
+    for (uint32_t q = 0; q < m; ++q)
+      if (o + q < (unsigned long long)cap) {
+        edges[2 * (o + q)] = i;
+        edges[2 * (o + q) + 1] = v[q];
+      }
+  }
+}
+
+// Puts the edges of every cell with more than kHitBuf of them in increasing
+// order of j (insertion sort of the segment, whose length is at most the
+// cell's degree). Segments that do not lie wholly below cap are left alone
+// (the call then reports capacity).
 __global__ void __launch_bounds__(kThreads)
     pivot_order(const DevCounters* ctr, uint32_t max_n, const uint32_t* __restrict__ counts,
                 const unsigned long long* __restrict__ offsets, uint32_t* __restrict__ edges,
@@ -182,7 +233,7 @@ __global__ void __launch_bounds__(kThreads)
   const uint32_t u = min(ctr->n_unique, max_n);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
     const uint32_t m = counts[i];
-    if (m < 2) continue;
+    if (m <= uint32_t(kHitBuf)) continue;
     const unsigned long long o = offsets[i];
     if (o + m > (unsigned long long)cap) continue;
     uint32_t* e = edges + 2 * o;
@@ -217,51 +268,68 @@ cudaError_t launch_pivot_keys(const uint64_t* cells, int w64, int ell, int h,
                               const DevCounters* ctr, size_t max_n, uint64_t* key_by_cell,
                               uint64_t* skeys, uint32_t* sidx, cudaStream_t s) {
   if (max_n == 0) return cudaSuccess;
-  pivot_keys<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(
-      cells, w64, h, key_bits(ell), ctr, uint32_t(max_n), key_by_cell, skeys, sidx);
+  int gs = 1;
+  while (gs < w64 && gs < 32) gs <<= 1;
+  const size_t groups = (max_n + size_t(32 / gs) - 1) / size_t(32 / gs);
+  pivot_keys<<<grid_for(groups, kThreads / 32), kThreads, 0, s>>>(
+      cells, w64, gs, h, key_bits(ell), ctr, uint32_t(max_n), key_by_cell, skeys, sidx);
   count_launch();
   return cudaGetLastError();
+}
+
+size_t pivot_table_slots(size_t max_n) {
+  size_t c = 1024;
+  while (c < 2 * max_n) c <<= 1;
+  return c;
 }
 
 cudaError_t launch_pivot_index(const uint64_t* skeys, const DevCounters* ctr, size_t max_n,
-                               uint64_t* tkeys, uint32_t* tvals, size_t tcap, DevCounters* wctr,
-                               cudaStream_t s) {
+                               void* table, size_t tcap, DevCounters* wctr, cudaStream_t s) {
   if (max_n == 0) return cudaSuccess;
   pivot_index<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(
-      skeys, ctr, uint32_t(max_n), tkeys, tvals, uint32_t(tcap - 1), table_shift(tcap), wctr);
+      skeys, ctr, uint32_t(max_n), static_cast<ulonglong2*>(table), uint32_t(tcap - 1),
+      table_shift(tcap), wctr);
   count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_pivot_search(const uint64_t* cells, int w64, int ell, int h,
-                                const DevCounters* ctr, size_t max_n,
-                                const uint64_t* key_by_cell, const uint64_t* skeys,
-                                const uint32_t* sidx, const uint64_t* tkeys, const uint32_t* tvals,
-                                size_t tcap, uint32_t* counts, const unsigned long long* offsets,
-                                uint32_t* fill, uint32_t* edges, int64_t edges_cap, bool write,
-                                cudaStream_t s) {
+cudaError_t launch_pivot_edges(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
+                               size_t max_n, const uint64_t* key_by_cell, const uint32_t* sidx,
+                               const void* table, size_t tcap, uint32_t* counts, uint32_t* hbuf,
+                               unsigned long long* offsets, uint32_t* fill, void* scan,
+                               uint32_t* edges, int64_t edges_cap, cudaStream_t s) {
   if (max_n == 0) return cudaSuccess;
   if (w64 > kMaxW) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(write ? fill : counts, 0, max_n * sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
   const int P = 1 << h;
   const size_t groups = P <= 32 ? (max_n + size_t(32 / P) - 1) / size_t(32 / P) : max_n;
-  auto kern = write ? pivot_search<kWrite> : pivot_search<kCount>;
-  kern<<<grid_for(groups, kThreads / 32), kThreads, 0, s>>>(
-      cells, w64, ell, h, key_bits(ell), ctr, uint32_t(max_n), key_by_cell, skeys, sidx, tkeys,
-      tvals, uint32_t(tcap - 1), table_shift(tcap), counts, offsets, fill, edges, edges_cap);
+  const int g = grid_for(groups, kThreads / 32);
+  const ulonglong2* tb = static_cast<const ulonglong2*>(table);
+  const uint32_t tmask = uint32_t(tcap - 1);
+  const int tshift = table_shift(tcap);
+  const int bits = key_bits(ell);
+  cudaError_t e = cudaMemsetAsync(counts, 0, max_n * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, max_n * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  pivot_search<kCount><<<g, kThreads, 0, s>>>(cells, w64, ell, h, bits, ctr, uint32_t(max_n),
+                                              key_by_cell, sidx, tb, tmask, tshift, counts, hbuf,
+                                              nullptr, nullptr, nullptr, 0);
   count_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pivot_order(const DevCounters* ctr, size_t max_n, const uint32_t* counts,
-                               const unsigned long long* offsets, uint32_t* edges,
-                               int64_t edges_cap, cudaStream_t s) {
-  if (max_n == 0) return cudaSuccess;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = scan_exclusive_u32(counts, offsets, &ctr->n_unique, max_n, &ctr->n_edges, scan, s);
+  if (e != cudaSuccess) return e;
+  pivot_emit<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(ctr, uint32_t(max_n), counts, hbuf,
+                                                            offsets, edges, edges_cap);
+  count_launch();
+  pivot_search<kWrite><<<g, kThreads, 0, s>>>(cells, w64, ell, h, bits, ctr, uint32_t(max_n),
+                                              key_by_cell, sidx, tb, tmask, tshift, counts, hbuf,
+                                              offsets, fill, edges, edges_cap);
+  count_launch();
   pivot_order<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(ctr, uint32_t(max_n), counts,
                                                              offsets, edges, edges_cap);
   count_launch();
   return cudaGetLastError();
 }
+
+size_t pivot_hit_words(size_t max_n) { return max_n * kHitBuf; }
 
 }  // namespace cg

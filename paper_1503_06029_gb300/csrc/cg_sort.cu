@@ -470,6 +470,186 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
   return cudaSuccess;
 }
 
+// ------------------------- merge sort of wide rows -------------------------
+//
+// Rows of W = ceil(l / 64) words (l > 64), referenced by row number, are put in
+// value order by a comparison merge sort: each item carries the 64 most
+// significant bits of its row (bits [l - 64, l)) as a cached key, and only
+// items with equal cached keys compare their whole rows (most significant
+// word first). Tiles of kMTile items are sorted in shared memory (bitonic
+// network), then runs are merged pairwise (merge path: each block finds its
+// diagonal split by binary search and merges one output tile); ceil(log2)
+// passes, each reading and writing 12 bytes per item.
+
+constexpr int kMThreads = 256;
+constexpr int kMItems = 8;
+constexpr int kMTile = kMThreads * kMItems;  // 2048
+constexpr uint32_t kPad = 0xffffffffu;
+
+struct RowOrder {
+  const uint64_t* rows;
+  int w;
+  // a < b; the padding item (row kPad) is larger than everything.
+  __device__ __forceinline__ bool less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) const {
+    if (ia == kPad) return false;
+    if (ib == kPad) return true;
+    if (ka != kb) return ka < kb;
+    const uint64_t* ra = rows + uint64_t(ia) * w;
+    const uint64_t* rb = rows + uint64_t(ib) * w;
+    for (int q = w - 1; q >= 0; --q)
+      if (ra[q] != rb[q]) return ra[q] < rb[q];
+    return ia < ib;
+  }
+};
+
+__device__ __forceinline__ uint64_t top_bits(const uint64_t* row, int ell) {
+  const int o = ell - 64;  // >= 1
+  const int q = o >> 6, sh = o & 63;
+  const uint64_t lo = row[q] >> sh;
+  return sh ? (lo | (row[q + 1] << (64 - sh))) : lo;
+}
+
+// Tile sort: items [b * kMTile, ...) of idx_in, with their cached keys.
+__global__ void __launch_bounds__(kMThreads)
+    msort_tiles(RowOrder ord, int ell, const uint32_t* __restrict__ idx_in,
+                const unsigned int* n_dev, uint32_t max_n, uint64_t* __restrict__ kout,
+                uint32_t* __restrict__ iout) {
+  __shared__ uint64_t sk[kMTile];
+  __shared__ uint32_t si[kMTile];
+  const uint32_t n = min(*n_dev, max_n);
+  const uint32_t base = blockIdx.x * kMTile;
+  if (base >= n) return;
+  for (int t = threadIdx.x; t < kMTile; t += kMThreads) {
+    const uint32_t g = base + t;
+    if (g < n) {
+      const uint32_t r = idx_in ? idx_in[g] : g;
+      si[t] = r;
+      sk[t] = top_bits(ord.rows + uint64_t(r) * ord.w, ell);
+    } else {
+      si[t] = kPad;
+      sk[t] = ~0ull;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= kMTile; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < kMTile; t += kMThreads) {
+        const int p = t ^ j;
+        if (p > t) {
+          const bool up = (t & k) == 0;
+          const bool swap = up ? ord.less(sk[p], si[p], sk[t], si[t])
+                               : ord.less(sk[t], si[t], sk[p], si[p]);
+          if (swap) {
+            const uint64_t tk = sk[t];
+            sk[t] = sk[p];
+            sk[p] = tk;
+            const uint32_t ti = si[t];
+            si[t] = si[p];
+            si[p] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < kMTile; t += kMThreads) {
+    const uint32_t g = base + t;
+    if (g < n) {
+      kout[g] = sk[t];
+      iout[g] = si[t];
+    }
+  }
+}
+
+// Number of items of A among the first d items of merge(A, B).
+template <class KA, class IA, class KB, class IB>
+__device__ __forceinline__ uint32_t merge_split(const RowOrder& ord, KA ka, IA ia, uint32_t la,
+                                                KB kb, IB ib, uint32_t lb, uint32_t d) {
+  uint32_t lo = d > lb ? d - lb : 0;
+  uint32_t hi = d < la ? d : la;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const uint32_t bj = d - 1 - mid;
+    if (ord.less(kb(bj), ib(bj), ka(mid), ia(mid))) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// One merge pass: sorted runs of `width` items merged pairwise into runs of
+// 2 * width; block b writes output items [b * kMTile, (b + 1) * kMTile).
+__global__ void __launch_bounds__(kMThreads)
+    msort_merge(RowOrder ord, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ iin,
+                uint64_t* __restrict__ kout, uint32_t* __restrict__ iout,
+                const unsigned int* n_dev, uint32_t max_n, uint32_t width) {
+  __shared__ uint64_t sk[kMTile];
+  __shared__ uint32_t si[kMTile];
+  __shared__ uint32_t s_split[2];
+  const uint32_t n = min(*n_dev, max_n);
+  const uint32_t out0 = blockIdx.x * kMTile;
+  if (out0 >= n) return;
+  const uint32_t s0 = (out0 / (2 * width)) * (2 * width);
+  const uint32_t a_beg = s0;
+  const uint32_t a_end = min(s0 + width, n);
+  const uint32_t b_end = min(s0 + 2 * width, n);
+  const uint32_t la = a_end - a_beg, lb = b_end - a_end;
+  const uint32_t d0 = out0 - s0;
+  const uint32_t d1 = min(d0 + uint32_t(kMTile), la + lb);
+  const uint64_t* ka = kin + a_beg;
+  const uint32_t* ia = iin + a_beg;
+  const uint64_t* kb = kin + a_end;
+  const uint32_t* ib = iin + a_end;
+  if (threadIdx.x < 2) {
+    const uint32_t d = threadIdx.x == 0 ? d0 : d1;
+    s_split[threadIdx.x] = merge_split(
+        ord, [&](uint32_t x) { return ka[x]; }, [&](uint32_t x) { return ia[x]; }, la,
+        [&](uint32_t x) { return kb[x]; }, [&](uint32_t x) { return ib[x]; }, lb, d);
+  }
+  __syncthreads();
+  const uint32_t a0 = s_split[0], a1 = s_split[1];
+  const uint32_t b0 = d0 - a0, b1 = d1 - a1;
+  const uint32_t na = a1 - a0, nb = b1 - b0;
+  for (uint32_t t = threadIdx.x; t < na + nb; t += kMThreads) {
+    if (t < na) {
+      sk[t] = ka[a0 + t];
+      si[t] = ia[a0 + t];
+    } else {
+      sk[t] = kb[b0 + t - na];
+      si[t] = ib[b0 + t - na];
+    }
+  }
+  __syncthreads();
+  // Each thread merges kMItems consecutive outputs of this tile.
+  const uint32_t dd = threadIdx.x * kMItems;
+  if (dd < na + nb) {
+    const uint64_t* sa_k = sk;
+    const uint32_t* sa_i = si;
+    const uint64_t* sb_k = sk + na;
+    const uint32_t* sb_i = si + na;
+    uint32_t x = merge_split(
+        ord, [&](uint32_t q) { return sa_k[q]; }, [&](uint32_t q) { return sa_i[q]; }, na,
+        [&](uint32_t q) { return sb_k[q]; }, [&](uint32_t q) { return sb_i[q]; }, nb, dd);
+    uint32_t y = dd - x;
+    const uint32_t end = min(dd + uint32_t(kMItems), na + nb);
+    for (uint32_t o = dd; o < end; ++o) {
+      bool take_a;
+      if (x >= na) take_a = false;
+      else if (y >= nb) take_a = true;
+      else take_a = !ord.less(sb_k[y], sb_i[y], sa_k[x], sa_i[x]);
+      const uint32_t g = out0 + o;
+      if (take_a) {
+        kout[g] = sa_k[x];
+        iout[g] = sa_i[x];
+        ++x;
+      } else {
+        kout[g] = sb_k[y];
+        iout[g] = sb_i[y];
+        ++y;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 size_t scan_scratch_bytes(size_t max_n) {
@@ -560,6 +740,32 @@ cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigne
     case 4: return cluster_sort_w<4>(in, rows, n_dev, max_n, top, o, s, done);
     default: return cudaSuccess;  // longer vectors: multi-launch sort
   }
+}
+
+cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32_t* idx_in,
+                            uint64_t* k0, uint64_t* k1, uint32_t* i0, uint32_t* i1,
+                            const unsigned int* n_dev, size_t max_n, cudaStream_t s,
+                            uint32_t** sorted_idx) {
+  *sorted_idx = i0;
+  if (max_n == 0) return cudaSuccess;
+  if (ell <= 64) return cudaErrorInvalidValue;
+  const RowOrder ord{rows, w64};
+  const unsigned tiles = unsigned((max_n + kMTile - 1) / kMTile);
+  msort_tiles<<<tiles, kMThreads, 0, s>>>(ord, ell, idx_in, n_dev, uint32_t(max_n), k0, i0);
+  count_launch();
+  uint64_t* kin = k0;
+  uint64_t* kout = k1;
+  uint32_t* iin = i0;
+  uint32_t* iout = i1;
+  for (size_t width = kMTile; width < max_n; width *= 2) {
+    msort_merge<<<tiles, kMThreads, 0, s>>>(ord, kin, iin, kout, iout, n_dev, uint32_t(max_n),
+                                             uint32_t(width));
+    count_launch();
+    std::swap(kin, kout);
+    std::swap(iin, iout);
+  }
+  *sorted_idx = iin;
+  return cudaGetLastError();
 }
 
 }  // namespace cg
