@@ -27,6 +27,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The batch overlaps scenes on 32 worker streams; let them map to as many
+# hardware work queues (read when the CUDA context is created).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = ("cell-graph build Mvectors/s (dedup+Hamming-1 edges), %HBM peak; batched vs plain")
 UNIT = "Mvectors/s"
@@ -214,7 +217,7 @@ def batch_compare(ctx, dev, steps: int):
     over the same scenes on the same GPU."""
     import torch
 
-    from paper_1503_06029_gb300 import inputs
+    from paper_1503_06029_gb300 import cellgraph, inputs
 
     spec = inputs.scene_batch_spec()
     scenes = []
@@ -224,6 +227,9 @@ def batch_compare(ctx, dev, steps: int):
                        torch.from_numpy(sc.b).to(dev)))
     total = int(spec.n.sum())
     stream = torch.cuda.current_stream()
+    t_tune = time.perf_counter()
+    tuned = ctx.autotune(scenes, reps=1)
+    t_tune = time.perf_counter() - t_tune
     for _ in range(3):  # sizes learned, then captured, then replayed
         res = ctx.build_batch(scenes)
     cells = sum(int(c.shape[0]) for c, _ in res)
@@ -257,11 +263,14 @@ def batch_compare(ctx, dev, steps: int):
                         "ms_per_batch": batch_ms, "gpu_launches_per_batch": batch_launches},
             "plain": {"value": total / (plain_ms * 1e-3) / 1e6, "unit": UNIT,
                       "ms_per_batch": plain_ms, "calls": len(scenes)},
-            "speedup": plain_ms / batch_ms}
+            "speedup": plain_ms / batch_ms,
+            "autotune": {"seconds": t_tune,
+                         "chosen": {str(cellgraph.TUNE_LIMITS[b]): v["setting"]
+                                    for b, v in tuned.items()}}}
 
 
 def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
-                  loads=(0.25, 0.5, 0.9), pool_scenes: int = 256):
+                  loads=(0.25, 0.5, 0.9), pool_scenes: int = 256, tuned_ctx=None):
     """Serving: Poisson arrivals (exponential gaps, seed 5) of scenes drawn as
     in the batched workload, offered at fractions of the measured batched
     capacity (scenes/s). Requests go through the request server with host
@@ -289,6 +298,8 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
                        f"(a pool of {pool_scenes} scenes, cycled), host inputs in pinned memory",
            "capacity_scenes_per_s": capacity_scenes_per_s, "levels": []}
     with cellgraph.Server(dev.index or 0, hbm_budget_bytes=16 << 30, max_inflight=16) as srv:
+        if tuned_ctx is not None:
+            srv.use_tuning(tuned_ctx)
         for k in range(32):  # warm-up: kernels loaded, pool memory cached
             t = srv.submit(*pool[k % pool_scenes])
             srv.wait(t)
@@ -543,7 +554,8 @@ def run_ours(args):
         line["batch"] = batch_compare(ctx, dev, max(3, args.steps // 2))
         if not args.no_serve:
             cap = len(inputs_spec_n()) / (line["batch"]["batched"]["ms_per_batch"] * 1e-3)
-            line["serve"] = serve_measure(dev, cap, n_requests=args.serve_requests)
+            line["serve"] = serve_measure(dev, cap, n_requests=args.serve_requests,
+                                          tuned_ctx=ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     ctx.close()

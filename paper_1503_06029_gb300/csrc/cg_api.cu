@@ -3,6 +3,7 @@
 //
 // Step order (one scene): sign vectors (§2.1) -> duplicate removal and sorting
 // (§3.2) -> Hamming-1 search from every cell (Algorithm 4) -> edge compaction.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
@@ -224,8 +225,8 @@ WideWs carve_wide(Carve& c, size_t n, size_t cap, size_t ucap, int ell, bool nee
   if (dedup) {
     w.idx0 = c.take<uint32_t>(ucap);
     w.idx1 = c.take<uint32_t>(ucap);
-    w.kw0 = c.take<uint64_t>(ucap);
-    w.kw1 = c.take<uint64_t>(ucap);
+    w.kw0 = c.take<uint64_t>(2 * ucap);  // cached 128-bit sort keys
+    w.kw1 = c.take<uint64_t>(2 * ucap);
     w.radix = c.take_bytes(radix_scratch_bytes(ucap));
   }
   w.cells = c.take<uint64_t>(ucap * w64);
@@ -755,6 +756,39 @@ size_t arrangement_bound(int64_t n, int d, int ell) {
 
 namespace cg {
 
+}  // namespace cg
+
+namespace {
+
+// Distinct rows (representatives in ww.idx0, U in ww.ctr->n_unique) into
+// sorted internal cells and the caller's copy: one-cluster sort when the rows
+// fit in distributed shared memory, else (decided on the device when the
+// capacity bound is larger than a cluster) the merge sort, the gather and the
+// copy.
+cg_status sort_cells_wide(WideWs& ww, int ell, int word_bits, void* cells, int64_t cells_cap,
+                          size_t ucap, cudaStream_t s) {
+  const int w64 = (ell + 63) / 64;
+  ClusterSortOut o{ww.cells, cells, cells_cap, word_bits, ell, SmallTable{}, ww.ctr};
+  bool done = false, tried = false;
+  CG_CUDA(cluster_sort(ww.keys64, ww.idx0, &ww.ctr->n_unique, ucap, ell, o, s, &done, &tried),
+          "sorting cells (cluster)");
+  if (done) return CG_OK;
+  const unsigned int* skip = tried ? &ww.ctr->sorted : nullptr;
+  uint32_t* sorted = nullptr;
+  CG_CUDA(sort_wide(ww.keys64, w64, ell, ww.idx0, ww.idx1, ww.kw0, ww.kw1, &ww.ctr->n_unique,
+                    ucap, ww.radix, s, &sorted, skip),
+          "sorting cells");
+  CG_CUDA(launch_gather_rows(ww.keys64, w64, sorted, &ww.ctr->n_unique, ucap, ww.cells, s, skip),
+          "gathering cells");
+  CG_CUDA(launch_write_cells(ww.cells, ell, word_bits, cells, cells_cap, ww.ctr, ucap, s, skip),
+          "writing cells");
+  return CG_OK;
+}
+
+}  // namespace
+
+namespace cg {
+
 cg_tune_params default_tune() { return cg_tune_params{CG_STRATEGY_HASH, 4, 0}; }
 
 cg_tune_params sanitize_tune(const cg_tune_params& p, int ell) {
@@ -852,22 +886,8 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
       CG_CUDA(launch_fill_u64(ww.slots, kEmpty, plan.cap, s), "clearing table");
       WideTable dt{ww.slots, uint32_t(plan.cap - 1), ww.idx0, uint32_t(plan.ucap), ww.ctr};
       CG_CUDA(launch_insert_wide(ww.keys64, n, w64, dt, s), "inserting vectors");
-      ClusterSortOut o{ww.cells, cells, cells_cap, word_bits, ell, SmallTable{}, ww.ctr};
-      bool done = false;
-      CG_CUDA(cluster_sort(ww.keys64, ww.idx0, &ww.ctr->n_unique, plan.ucap, ell, o, s, &done),
-              "sorting cells (cluster)");
-      if (!done) {
-        uint32_t* sorted = nullptr;
-        CG_CUDA(sort_wide(ww.keys64, w64, ell, ww.idx0, ww.idx1, ww.kw0, ww.kw1,
-                          &ww.ctr->n_unique, plan.ucap, ww.radix, s, &sorted),
-                "sorting cells");
-        CG_CUDA(launch_gather_rows(ww.keys64, w64, sorted, &ww.ctr->n_unique, plan.ucap, ww.cells,
-                                   s),
-                "gathering cells");
-        CG_CUDA(launch_write_cells(ww.cells, ell, word_bits, cells, cells_cap, ww.ctr, plan.ucap,
-                                   s),
-                "writing cells");
-      }
+      st = sort_cells_wide(ww, ell, word_bits, cells, cells_cap, plan.ucap, s);
+      if (st) return st;
     } else {
       st = dedup_wide_steps(ww, ww.keys64, n, ell, false, s);
       if (st) return st;
@@ -893,20 +913,9 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   mark(ctx, "pack", s);
   WideTable dt{ww.slots, uint32_t(plan.cap - 1), ww.idx0, uint32_t(plan.ucap), ww.ctr};
   CG_CUDA(launch_insert_wide(ww.keys64, n, w64, dt, s), "inserting vectors");
-  ClusterSortOut o{ww.cells, cells, cells_cap, word_bits, ell, SmallTable{}, ww.ctr};
-  bool done = false;
-  CG_CUDA(cluster_sort(ww.keys64, ww.idx0, &ww.ctr->n_unique, plan.ucap, ell, o, s, &done),
-          "sorting cells (cluster)");
-  if (!done) {
-    uint32_t* sorted = nullptr;
-    CG_CUDA(sort_wide(ww.keys64, w64, ell, ww.idx0, ww.idx1, ww.kw0, ww.kw1, &ww.ctr->n_unique,
-                      plan.ucap, ww.radix, s, &sorted),
-            "sorting cells");
-    CG_CUDA(launch_gather_rows(ww.keys64, w64, sorted, &ww.ctr->n_unique, plan.ucap, ww.cells, s),
-            "gathering cells");
-    CG_CUDA(launch_write_cells(ww.cells, ell, word_bits, cells, cells_cap, ww.ctr, plan.ucap, s),
-            "writing cells");
-  }
+  mark(ctx, "dedup_insert", s);
+  st = sort_cells_wide(ww, ell, word_bits, cells, cells_cap, plan.ucap, s);
+  if (st) return st;
   mark(ctx, "dedup_sort", s);
   WideTable it{ww.slots2, uint32_t(plan.cap - 1), nullptr, 0, ww.ctr};
   if (strategy != CG_STRATEGY_SORTED)
@@ -1099,7 +1108,7 @@ cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const
 
 namespace {
 
-constexpr int kWorkers = 16;
+constexpr int kWorkers = 32;
 
 cg_status ensure_batch_resources(cg_ctx* ctx, size_t dev_bytes, size_t host_bytes) {
   if (ctx->workers.empty()) {
@@ -1242,6 +1251,25 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
                            reinterpret_cast<const uint32_t*>(base + b.edges_off), uint32_t(b.w),
                            uint32_t(b.plan.ucap), (unsigned long long)b.ecap};
     }
+    // ---- stream assignment: largest scenes first, each to the least loaded
+    // worker stream (longest-processing-time rule), by estimated work ----
+    std::vector<int> order(static_cast<size_t>(S));
+    for (int i = 0; i < S; ++i) order[size_t(i)] = i;
+    auto cost = [&](int i) {
+      return double(scenes[i].n) * double(scenes[i].ell + 64) + 2e5;
+    };
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<int> stream_of(static_cast<size_t>(S));
+    {
+      std::vector<double> load(ctx->workers.size(), 0.0);
+      for (int i : order) {
+        size_t best = 0;
+        for (size_t k = 1; k < load.size(); ++k)
+          if (load[k] < load[best]) best = k;
+        stream_of[size_t(i)] = int(best);
+        load[best] += cost(i);
+      }
+    }
     // ---- enqueue: table upload, fork, per-scene builds, join, gather ----
     auto enqueue = [&]() -> cg_status {
       CG_CUDA(cudaMemcpyAsync(tab, htab, size_t(S) * sizeof(BatchEntry), cudaMemcpyHostToDevice,
@@ -1249,14 +1277,14 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
               "uploading the scene table");
       CG_CUDA(cudaEventRecord(ctx->fork_ev, s0), "fork");
       for (auto& w : ctx->workers) CG_CUDA(cudaStreamWaitEvent(w, ctx->fork_ev, 0), "fork");
-      for (int i = 0; i < S; ++i) {
+      for (int i : order) {
         const cg_scene& sc = scenes[i];
         const BatchScene& b = bs[size_t(i)];
         PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
         cg_status st2 =
             enqueue_scene(nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64, base + b.cells_off,
                           int64_t(b.plan.ucap), reinterpret_cast<uint32_t*>(base + b.edges_off),
-                          int64_t(b.ecap), ctx->workers[size_t(i) % ctx->workers.size()]);
+                          int64_t(b.ecap), ctx->workers[size_t(stream_of[size_t(i)])]);
         if (st2) return st2;
       }
       for (size_t k = 0; k < ctx->workers.size(); ++k) {

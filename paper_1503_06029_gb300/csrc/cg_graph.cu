@@ -82,8 +82,9 @@ __global__ void load_cells(const void* cells, int64_t n, int word_bits, int w_ca
 }
 
 __global__ void write_cells(const uint64_t* cells, int w64, int word_bits, int w_caller,
-                            void* out, int64_t cap, const DevCounters* ctr) {
-  if (ctr->overflow) return;
+                            void* out, int64_t cap, const DevCounters* ctr,
+                            const unsigned int* skip) {
+  if (ctr->overflow || (skip && *skip)) return;
   const int64_t u = ctr->n_unique;
   if (u > cap) return;  // capacity error: the host reports it, nothing is written
   const int64_t total = u * w_caller;
@@ -430,7 +431,9 @@ __global__ void insert_wide(const uint64_t* __restrict__ keys, int64_t n, int w,
 
 __global__ void gather_rows(const uint64_t* __restrict__ keys, int w,
                             const uint32_t* __restrict__ idx, const unsigned int* n_dev,
-                            uint32_t max_n, uint64_t* __restrict__ out) {
+                            uint32_t max_n, uint64_t* __restrict__ out,
+                            const unsigned int* skip) {
+  if (skip && *skip) return;
   const uint64_t total = uint64_t(min(*n_dev, max_n)) * w;
   for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < total;
        t += uint64_t(gridDim.x) * blockDim.x) {
@@ -890,12 +893,13 @@ cudaError_t launch_load_cells(const void* cells, int64_t n, int word_bits, int e
 }
 
 cudaError_t launch_write_cells(const uint64_t* cells, int ell, int word_bits, void* out,
-                               int64_t cap, const DevCounters* ctr, size_t max_n, cudaStream_t s) {
+                               int64_t cap, const DevCounters* ctr, size_t max_n, cudaStream_t s,
+                               const unsigned int* skip) {
   if (max_n == 0 || cap == 0) return cudaSuccess;
   const int w64 = (ell + 63) / 64;
   const int wc = (ell + word_bits - 1) / word_bits;
   write_cells<<<grid_for(max_n * wc, kThreads), kThreads, 0, s>>>(cells, w64, word_bits, wc, out,
-                                                                   cap, ctr);
+                                                                   cap, ctr, skip);
   return finish(0);
 }
 
@@ -969,18 +973,19 @@ cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const W
 
 cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
-                      void* scratch, cudaStream_t s, uint32_t** sorted_idx) {
+                      void* scratch, cudaStream_t s, uint32_t** sorted_idx,
+                      const unsigned int* skip) {
   (void)scratch;
   return merge_sort_rows(keys, w64, ell, idx0, kw0, kw1, idx0, idx1, n_dev, max_n, s,
-                         sorted_idx);
+                         sorted_idx, skip);
 }
 
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,
                                const unsigned int* n_dev, size_t max_n, uint64_t* out,
-                               cudaStream_t s) {
+                               cudaStream_t s, const unsigned int* skip) {
   if (max_n == 0) return cudaSuccess;
   gather_rows<<<grid_for(max_n * w64, kThreads), kThreads, 0, s>>>(keys, w64, idx, n_dev,
-                                                                    uint32_t(max_n), out);
+                                                                    uint32_t(max_n), out, skip);
   return finish(0);
 }
 

@@ -26,7 +26,8 @@ struct DevCounters {
   unsigned int error;         // device-side consistency failures (bit set)
   unsigned int ticket;        // work counter of the single-pass edge kernel
   unsigned int tc_spill;      // tiles the tensor-core sign kernel left to the fp32 one
-  unsigned int pad[7];
+  unsigned int sorted;        // 1: the one-cluster sort handled the distinct vectors
+  unsigned int pad[6];
 };
 
 // Bits of DevCounters::error.
@@ -205,13 +206,14 @@ cudaError_t radix_sort_u64(uint64_t* keys0, uint64_t* keys1, uint32_t* vals0, ui
 
 // Value order of U = min(*n_dev, max_n) rows of W = ceil(l / 64) words
 // (l > 64): rows[idx_in[i]] (idx_in nullable: row i). Comparison merge sort
-// on row numbers with the top 64 bits cached; k0/k1 and i0/i1 are ping-pong
-// buffers of max_n items; *sorted_idx receives the buffer holding the sorted
-// row numbers.
+// on row numbers with the top 128 bits cached; k0/k1 (2 * max_n words each)
+// and i0/i1 (max_n) are ping-pong buffers; *sorted_idx receives the buffer
+// holding the sorted row numbers. With skip != nullptr, every kernel does
+// nothing when *skip is nonzero.
 cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32_t* idx_in,
                             uint64_t* k0, uint64_t* k1, uint32_t* i0, uint32_t* i1,
                             const unsigned int* n_dev, size_t max_n, cudaStream_t s,
-                            uint32_t** sorted_idx);
+                            uint32_t** sorted_idx, const unsigned int* skip = nullptr);
 
 // out[i] = sum_{j<i} in[j] for i < *n_dev; *total = sum of all (device).
 cudaError_t scan_exclusive_u32(const uint32_t* in, unsigned long long* out,
@@ -239,7 +241,8 @@ cudaError_t launch_point_cell_small(const void* keys, int64_t n, int word_bits, 
                                     const SmallTable& t, uint32_t* point_cell, cudaStream_t s);
 // Copy U cells (u64, internal) to the caller's layout when U <= cap.
 cudaError_t launch_write_cells(const uint64_t* cells, int ell, int word_bits, void* out,
-                               int64_t cap, const DevCounters* ctr, size_t max_n, cudaStream_t s);
+                               int64_t cap, const DevCounters* ctr, size_t max_n, cudaStream_t s,
+                               const unsigned int* skip = nullptr);
 // Load caller-layout cells into internal u64 rows; sets ctr->n_unique = n.
 cudaError_t launch_load_cells(const void* cells, int64_t n, int word_bits, int ell,
                               uint64_t* out, DevCounters* ctr, cudaStream_t s);
@@ -265,9 +268,13 @@ struct ClusterSortOut {
   SmallTable t;  // t.keys == nullptr: no numbering
   DevCounters* ctr;
 };
+// *done: the cluster sort certainly handles all vectors (max_n fits). When it
+// does not and *tried is set, the cluster kernel was launched at its full
+// capacity anyway: it sorts when the actual count fits and records the
+// outcome in o.ctr->sorted, which the fallback steps then read (skip flag).
 cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigned int* n_dev,
                          size_t max_n, int ell, const ClusterSortOut& o, cudaStream_t s,
-                         bool* done);
+                         bool* done, bool* tried = nullptr);
 
 // Steps 3-4 in one kernel for l <= 64: hit search, scan with decoupled
 // look-back (status: ceil(max_n / 32) words, zeroed) and edge output.
@@ -298,10 +305,11 @@ cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const W
 // Sort representatives by value: idx0/idx1 permuted, kw0/kw1 word scratch.
 cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
-                      void* scratch, cudaStream_t s, uint32_t** sorted_idx);
+                      void* scratch, cudaStream_t s, uint32_t** sorted_idx,
+                      const unsigned int* skip = nullptr);
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,
                                const unsigned int* n_dev, size_t max_n, uint64_t* out,
-                               cudaStream_t s);
+                               cudaStream_t s, const unsigned int* skip = nullptr);
 cudaError_t launch_rank_by_row(const uint32_t* idx, const unsigned int* n_dev, size_t max_n,
                                uint32_t* rank_by_row, cudaStream_t s);
 cudaError_t launch_point_cell_wide(const uint64_t* keys, int64_t n, int w64, const WideTable& t,

@@ -283,7 +283,11 @@ __global__ void __launch_bounds__(kCThreads)
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const uint32_t n = min(*n_dev, max_n);
+  if (*n_dev > max_n) {  // more vectors than this cluster holds: the fallback sorts them
+    if (r == 0 && tid == 0) o.ctr->sorted = 0u;
+    return;
+  }
+  const uint32_t n = *n_dev;
   const uint32_t per = (n + C - 1) / C;
   const uint32_t lo = min(r * per, n);
   const uint32_t cnt = min(lo + per, n) - lo;
@@ -408,20 +412,26 @@ __global__ void __launch_bounds__(kCThreads)
       }
     }
   }
+  if (r == 0 && tid == 0) o.ctr->sorted = 1u;
 }
 
 template <int W>
 cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsigned int* n_dev,
                            size_t max_n, int top_bits, const ClusterSortOut& o, cudaStream_t s,
-                           bool* done) {
+                           bool* done, bool* tried) {
   constexpr size_t kStaticSmem = 20 * 1024;
   constexpr size_t kMaxDyn = 227 * 1024 - kStaticSmem;
+  constexpr size_t kMaxPer = kMaxDyn / (2 * W * sizeof(uint64_t));
   static int cluster16 = -1;  // 1 if a 16-CTA cluster of this kernel can run
   auto kern = cluster_sort_kernel<W>;
+  const bool certain = max_n <= 8 * kMaxPer || (cluster16 != 0 && max_n <= 16 * kMaxPer);
+  if (!certain && !tried) return cudaSuccess;
   for (int C : {16, 8}) {
-    const size_t per = (max_n + C - 1) / C;
+    // At full capacity when max_n may not fit: the kernel checks the count.
+    const size_t per = certain ? (max_n + C - 1) / C : kMaxPer;
     const size_t dyn = 2 * std::max<size_t>(per, 1) * W * sizeof(uint64_t);
     if (dyn > kMaxDyn) continue;
+    const size_t cap_n = certain ? max_n : per * C;
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void*>(kern), dyn);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -454,7 +464,7 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
       }
       cluster16 = 1;
     }
-    e = cudaLaunchKernelEx(&cfg, kern, in, rows, n_dev, uint32_t(max_n), top_bits, o,
+    e = cudaLaunchKernelEx(&cfg, kern, in, rows, n_dev, uint32_t(cap_n), top_bits, o,
                            uint32_t(per));
     if (e != cudaSuccess && C == 16) {
       // A 16-CTA cluster with this much shared memory does not fit: the launch
@@ -464,7 +474,8 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
     }
     if (e != cudaSuccess) return e;
     count_launch();
-    *done = true;
+    if (certain) *done = true;
+    else *tried = true;
     return cudaGetLastError();
   }
   return cudaSuccess;
@@ -473,13 +484,14 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
 // ------------------------- merge sort of wide rows -------------------------
 //
 // Rows of W = ceil(l / 64) words (l > 64), referenced by row number, are put in
-// value order by a comparison merge sort: each item carries the 64 most
-// significant bits of its row (bits [l - 64, l)) as a cached key, and only
-// items with equal cached keys compare their whole rows (most significant
-// word first). Tiles of kMTile items are sorted in shared memory (bitonic
-// network), then runs are merged pairwise (merge path: each block finds its
-// diagonal split by binary search and merges one output tile); ceil(log2)
-// passes, each reading and writing 12 bytes per item.
+// value order by a comparison merge sort: each item carries the 128 most
+// significant bits of its row (bits [l - 128, l), zero-filled below bit 0) as
+// a cached key, and only items with equal cached keys compare their whole
+// rows (most significant word first); for l <= 128 the cached key is the whole
+// row. Tiles of kMTile items are sorted in shared memory (bitonic network),
+// then runs are merged pairwise (merge path: each block finds its diagonal
+// split by binary search and merges one output tile); ceil(log2(U / kMTile))
+// passes, each reading and writing 20 bytes per item.
 
 constexpr int kMThreads = 256;
 constexpr int kMItems = 8;
@@ -489,11 +501,15 @@ constexpr uint32_t kPad = 0xffffffffu;
 struct RowOrder {
   const uint64_t* rows;
   int w;
+  bool full;  // the cached key is the whole row (l <= 128)
   // a < b; the padding item (row kPad) is larger than everything.
-  __device__ __forceinline__ bool less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) const {
+  __device__ __forceinline__ bool less(const ulonglong2& ka, uint32_t ia, const ulonglong2& kb,
+                                       uint32_t ib) const {
     if (ia == kPad) return false;
     if (ib == kPad) return true;
-    if (ka != kb) return ka < kb;
+    if (ka.x != kb.x) return ka.x < kb.x;
+    if (ka.y != kb.y) return ka.y < kb.y;
+    if (full) return ia < ib;
     const uint64_t* ra = rows + uint64_t(ia) * w;
     const uint64_t* rb = rows + uint64_t(ib) * w;
     for (int q = w - 1; q >= 0; --q)
@@ -502,20 +518,26 @@ struct RowOrder {
   }
 };
 
-__device__ __forceinline__ uint64_t top_bits(const uint64_t* row, int ell) {
-  const int o = ell - 64;  // >= 1
-  const int q = o >> 6, sh = o & 63;
+// Bits [off, off + 64) of a row (positions below 0 read as zero, off > -64).
+__device__ __forceinline__ uint64_t bits64_at(const uint64_t* row, int off) {
+  if (off < 0) return row[0] << (-off);
+  const int q = off >> 6, sh = off & 63;
   const uint64_t lo = row[q] >> sh;
   return sh ? (lo | (row[q + 1] << (64 - sh))) : lo;
+}
+
+__device__ __forceinline__ ulonglong2 top128(const uint64_t* row, int ell) {
+  return make_ulonglong2(bits64_at(row, ell - 64), bits64_at(row, ell - 128));
 }
 
 // Tile sort: items [b * kMTile, ...) of idx_in, with their cached keys.
 __global__ void __launch_bounds__(kMThreads)
     msort_tiles(RowOrder ord, int ell, const uint32_t* __restrict__ idx_in,
-                const unsigned int* n_dev, uint32_t max_n, uint64_t* __restrict__ kout,
-                uint32_t* __restrict__ iout) {
-  __shared__ uint64_t sk[kMTile];
+                const unsigned int* n_dev, uint32_t max_n, ulonglong2* __restrict__ kout,
+                uint32_t* __restrict__ iout, const unsigned int* skip) {
+  __shared__ ulonglong2 sk[kMTile];
   __shared__ uint32_t si[kMTile];
+  if (skip && *skip) return;
   const uint32_t n = min(*n_dev, max_n);
   const uint32_t base = blockIdx.x * kMTile;
   if (base >= n) return;
@@ -524,10 +546,10 @@ __global__ void __launch_bounds__(kMThreads)
     if (g < n) {
       const uint32_t r = idx_in ? idx_in[g] : g;
       si[t] = r;
-      sk[t] = top_bits(ord.rows + uint64_t(r) * ord.w, ell);
+      sk[t] = top128(ord.rows + uint64_t(r) * ord.w, ell);
     } else {
       si[t] = kPad;
-      sk[t] = ~0ull;
+      sk[t] = make_ulonglong2(~0ull, ~0ull);
     }
   }
   __syncthreads();
@@ -540,7 +562,7 @@ __global__ void __launch_bounds__(kMThreads)
           const bool swap = up ? ord.less(sk[p], si[p], sk[t], si[t])
                                : ord.less(sk[t], si[t], sk[p], si[p]);
           if (swap) {
-            const uint64_t tk = sk[t];
+            const ulonglong2 tk = sk[t];
             sk[t] = sk[p];
             sk[p] = tk;
             const uint32_t ti = si[t];
@@ -562,15 +584,16 @@ __global__ void __launch_bounds__(kMThreads)
 }
 
 // Number of items of A among the first d items of merge(A, B).
-template <class KA, class IA, class KB, class IB>
-__device__ __forceinline__ uint32_t merge_split(const RowOrder& ord, KA ka, IA ia, uint32_t la,
-                                                KB kb, IB ib, uint32_t lb, uint32_t d) {
+__device__ __forceinline__ uint32_t merge_split(const RowOrder& ord, const ulonglong2* ka,
+                                                const uint32_t* ia, uint32_t la,
+                                                const ulonglong2* kb, const uint32_t* ib,
+                                                uint32_t lb, uint32_t d) {
   uint32_t lo = d > lb ? d - lb : 0;
   uint32_t hi = d < la ? d : la;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
     const uint32_t bj = d - 1 - mid;
-    if (ord.less(kb(bj), ib(bj), ka(mid), ia(mid))) hi = mid;
+    if (ord.less(kb[bj], ib[bj], ka[mid], ia[mid])) hi = mid;
     else lo = mid + 1;
   }
   return lo;
@@ -579,32 +602,30 @@ __device__ __forceinline__ uint32_t merge_split(const RowOrder& ord, KA ka, IA i
 // One merge pass: sorted runs of `width` items merged pairwise into runs of
 // 2 * width; block b writes output items [b * kMTile, (b + 1) * kMTile).
 __global__ void __launch_bounds__(kMThreads)
-    msort_merge(RowOrder ord, const uint64_t* __restrict__ kin, const uint32_t* __restrict__ iin,
-                uint64_t* __restrict__ kout, uint32_t* __restrict__ iout,
-                const unsigned int* n_dev, uint32_t max_n, uint32_t width) {
-  __shared__ uint64_t sk[kMTile];
+    msort_merge(RowOrder ord, const ulonglong2* __restrict__ kin, const uint32_t* __restrict__ iin,
+                ulonglong2* __restrict__ kout, uint32_t* __restrict__ iout,
+                const unsigned int* n_dev, uint32_t max_n, uint32_t width,
+                const unsigned int* skip) {
+  __shared__ ulonglong2 sk[kMTile];
   __shared__ uint32_t si[kMTile];
   __shared__ uint32_t s_split[2];
+  if (skip && *skip) return;
   const uint32_t n = min(*n_dev, max_n);
   const uint32_t out0 = blockIdx.x * kMTile;
   if (out0 >= n) return;
   const uint32_t s0 = (out0 / (2 * width)) * (2 * width);
-  const uint32_t a_beg = s0;
   const uint32_t a_end = min(s0 + width, n);
   const uint32_t b_end = min(s0 + 2 * width, n);
-  const uint32_t la = a_end - a_beg, lb = b_end - a_end;
+  const uint32_t la = a_end - s0, lb = b_end - a_end;
   const uint32_t d0 = out0 - s0;
   const uint32_t d1 = min(d0 + uint32_t(kMTile), la + lb);
-  const uint64_t* ka = kin + a_beg;
-  const uint32_t* ia = iin + a_beg;
-  const uint64_t* kb = kin + a_end;
+  const ulonglong2* ka = kin + s0;
+  const uint32_t* ia = iin + s0;
+  const ulonglong2* kb = kin + a_end;
   const uint32_t* ib = iin + a_end;
-  if (threadIdx.x < 2) {
-    const uint32_t d = threadIdx.x == 0 ? d0 : d1;
-    s_split[threadIdx.x] = merge_split(
-        ord, [&](uint32_t x) { return ka[x]; }, [&](uint32_t x) { return ia[x]; }, la,
-        [&](uint32_t x) { return kb[x]; }, [&](uint32_t x) { return ib[x]; }, lb, d);
-  }
+  if (threadIdx.x < 2)
+    s_split[threadIdx.x] =
+        merge_split(ord, ka, ia, la, kb, ib, lb, threadIdx.x == 0 ? d0 : d1);
   __syncthreads();
   const uint32_t a0 = s_split[0], a1 = s_split[1];
   const uint32_t b0 = d0 - a0, b1 = d1 - a1;
@@ -622,28 +643,22 @@ __global__ void __launch_bounds__(kMThreads)
   // Each thread merges kMItems consecutive outputs of this tile.
   const uint32_t dd = threadIdx.x * kMItems;
   if (dd < na + nb) {
-    const uint64_t* sa_k = sk;
-    const uint32_t* sa_i = si;
-    const uint64_t* sb_k = sk + na;
-    const uint32_t* sb_i = si + na;
-    uint32_t x = merge_split(
-        ord, [&](uint32_t q) { return sa_k[q]; }, [&](uint32_t q) { return sa_i[q]; }, na,
-        [&](uint32_t q) { return sb_k[q]; }, [&](uint32_t q) { return sb_i[q]; }, nb, dd);
+    uint32_t x = merge_split(ord, sk, si, na, sk + na, si + na, nb, dd);
     uint32_t y = dd - x;
     const uint32_t end = min(dd + uint32_t(kMItems), na + nb);
     for (uint32_t o = dd; o < end; ++o) {
       bool take_a;
       if (x >= na) take_a = false;
       else if (y >= nb) take_a = true;
-      else take_a = !ord.less(sb_k[y], sb_i[y], sa_k[x], sa_i[x]);
+      else take_a = !ord.less(sk[na + y], si[na + y], sk[x], si[x]);
       const uint32_t g = out0 + o;
       if (take_a) {
-        kout[g] = sa_k[x];
-        iout[g] = sa_i[x];
+        kout[g] = sk[x];
+        iout[g] = si[x];
         ++x;
       } else {
-        kout[g] = sb_k[y];
-        iout[g] = sb_i[y];
+        kout[g] = sk[na + y];
+        iout[g] = si[na + y];
         ++y;
       }
     }
@@ -729,15 +744,16 @@ namespace cg {
 
 cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigned int* n_dev,
                          size_t max_n, int ell, const ClusterSortOut& o, cudaStream_t s,
-                         bool* done) {
+                         bool* done, bool* tried) {
   *done = false;
+  if (tried) *tried = false;
   const int w = (ell + 63) / 64;
   const int top = ell - 64 * (w - 1);
   switch (w) {
-    case 1: return cluster_sort_w<1>(in, rows, n_dev, max_n, top, o, s, done);
-    case 2: return cluster_sort_w<2>(in, rows, n_dev, max_n, top, o, s, done);
-    case 3: return cluster_sort_w<3>(in, rows, n_dev, max_n, top, o, s, done);
-    case 4: return cluster_sort_w<4>(in, rows, n_dev, max_n, top, o, s, done);
+    case 1: return cluster_sort_w<1>(in, rows, n_dev, max_n, top, o, s, done, tried);
+    case 2: return cluster_sort_w<2>(in, rows, n_dev, max_n, top, o, s, done, tried);
+    case 3: return cluster_sort_w<3>(in, rows, n_dev, max_n, top, o, s, done, tried);
+    case 4: return cluster_sort_w<4>(in, rows, n_dev, max_n, top, o, s, done, tried);
     default: return cudaSuccess;  // longer vectors: multi-launch sort
   }
 }
@@ -745,21 +761,22 @@ cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigne
 cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32_t* idx_in,
                             uint64_t* k0, uint64_t* k1, uint32_t* i0, uint32_t* i1,
                             const unsigned int* n_dev, size_t max_n, cudaStream_t s,
-                            uint32_t** sorted_idx) {
+                            uint32_t** sorted_idx, const unsigned int* skip) {
   *sorted_idx = i0;
   if (max_n == 0) return cudaSuccess;
   if (ell <= 64) return cudaErrorInvalidValue;
-  const RowOrder ord{rows, w64};
+  const RowOrder ord{rows, w64, ell <= 128};
   const unsigned tiles = unsigned((max_n + kMTile - 1) / kMTile);
-  msort_tiles<<<tiles, kMThreads, 0, s>>>(ord, ell, idx_in, n_dev, uint32_t(max_n), k0, i0);
+  ulonglong2* kin = reinterpret_cast<ulonglong2*>(k0);
+  ulonglong2* kout = reinterpret_cast<ulonglong2*>(k1);
+  msort_tiles<<<tiles, kMThreads, 0, s>>>(ord, ell, idx_in, n_dev, uint32_t(max_n), kin, i0,
+                                          skip);
   count_launch();
-  uint64_t* kin = k0;
-  uint64_t* kout = k1;
   uint32_t* iin = i0;
   uint32_t* iout = i1;
   for (size_t width = kMTile; width < max_n; width *= 2) {
     msort_merge<<<tiles, kMThreads, 0, s>>>(ord, kin, iin, kout, iout, n_dev, uint32_t(max_n),
-                                             uint32_t(width));
+                                             uint32_t(width), skip);
     count_launch();
     std::swap(kin, kout);
     std::swap(iin, iout);
