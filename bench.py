@@ -297,7 +297,7 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
     out = {"workload": "Poisson stream of scenes drawn like the batched workload "
                        f"(a pool of {pool_scenes} scenes, cycled), host inputs in pinned memory",
            "capacity_scenes_per_s": capacity_scenes_per_s, "levels": []}
-    with cellgraph.Server(dev.index or 0, hbm_budget_bytes=16 << 30, max_inflight=16) as srv:
+    with cellgraph.Server(dev.index or 0, hbm_budget_bytes=16 << 30, max_inflight=32) as srv:
         if tuned_ctx is not None:
             srv.use_tuning(tuned_ctx)
         for k in range(32):  # warm-up: kernels loaded, pool memory cached

@@ -3,9 +3,10 @@
 //
 // Threads:
 //   * callers submit, poll, wait, copy and release under `mu`;
-//   * one scheduler thread per server admits queued requests (arrival order)
-//     whenever a slot stream and enough of the budget are free, enqueues each
-//     admitted scene on its slot's stream, and handles completions;
+//   * up to kSchedThreads scheduler threads, each owning a share of the slot
+//     streams, admit queued requests (arrival order, from one shared queue)
+//     whenever one of their slots and enough of the budget are free, enqueue
+//     each admitted scene on its slot's stream, and settle completions;
 //   * a CUDA host callback at the end of each request's stream work records the
 //     completion time and hands the request back to the scheduler.
 // No CUDA call is ever made while `mu` is held: a completion callback takes
@@ -33,6 +34,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr int kMaxSlots = 64;
+constexpr int kSchedThreads = 4;  // scheduler threads (enqueueing is host-bound)
 
 thread_local std::string t_msg;
 
@@ -65,6 +67,7 @@ struct Req {
   char* work = nullptr;
   char* result = nullptr;
   int slot = -1;
+  int worker = -1;
   // outcome
   int64_t n_cells = 0, n_edges = 0;
   double t_submit = 0, t_admit = -1, t_done = 0;
@@ -80,7 +83,6 @@ struct cg_server {
   int max_slots = 1;
   Clock::time_point t0;
   std::vector<cudaStream_t> streams;
-  std::vector<int> free_slots;
   DevCounters* hctr = nullptr;  // pinned, one per slot
   cudaStream_t copy_stream = nullptr;
   cudaMemPool_t pool = nullptr;
@@ -88,7 +90,15 @@ struct cg_server {
   std::condition_variable cv_sched;
   std::condition_variable cv_done;
   std::deque<Req*> queue;
-  std::deque<Req*> finished_gpu;
+  // Scheduler threads: thread k owns the slots k, k + T, k + 2T, ... and
+  // settles the requests that ran on them.
+  struct Worker {
+    std::thread th;
+    std::vector<int> free_slots;
+    std::deque<Req*> finished;
+    int running = 0;
+  };
+  std::vector<Worker> workers;
   std::unordered_map<int64_t, Req*> reqs;
   size_t in_use = 0, peak = 0;
   int running = 0, max_running = 0;
@@ -97,7 +107,6 @@ struct cg_server {
   int inject_alloc_fail = 0;
   cg_tune_params tune[CG_TUNE_BUCKETS];
   bool stop = false;
-  std::thread th;
 };
 
 namespace {
@@ -127,9 +136,9 @@ void CUDART_CB on_complete(void* p) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->t_done = t;
-    s->finished_gpu.push_back(r);
+    s->workers[size_t(r->worker)].finished.push_back(r);
   }
-  s->cv_sched.notify_one();
+  s->cv_sched.notify_all();
 }
 
 // Allocates from the server's pool on stream st (or reports an injected
@@ -256,7 +265,8 @@ void finish_request(cg_server* s, Req* r) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->in_use -= freed_work + freed_result;
-    s->free_slots.push_back(r->slot);
+    s->workers[size_t(r->worker)].free_slots.push_back(r->slot);
+    --s->workers[size_t(r->worker)].running;
     r->slot = -1;
     --s->running;
     if (what == kRetry) {
@@ -277,39 +287,32 @@ void finish_request(cg_server* s, Req* r) {
     }
   }
   s->cv_done.notify_all();
+  s->cv_sched.notify_all();  // memory and a slot are free again
 }
 
-// True when the head of the queue can be admitted now or must be failed.
-bool admissible(const cg_server* s) {
-  if (s->queue.empty() || s->free_slots.empty()) return false;
+// True when the head of the queue can be admitted now by scheduler k (or must
+// be failed).
+bool admissible(const cg_server* s, int k) {
+  if (s->queue.empty() || s->workers[size_t(k)].free_slots.empty()) return false;
   const Req* r = s->queue.front();
   const size_t need = r->work_bytes + r->result_bytes;
   return need > s->budget || s->in_use + need <= s->budget;
 }
 
-void scheduler(cg_server* s) {
+void scheduler(cg_server* s, int k) {
   cudaSetDevice(s->device);
+  cg_server::Worker& me = s->workers[size_t(k)];
   for (;;) {
     std::vector<Req*> fin;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_sched.wait(lk, [&] {
-        return !s->finished_gpu.empty() || (!s->stop && admissible(s)) ||
-               (s->stop && s->running == 0);
+        return !me.finished.empty() || (!s->stop && admissible(s, k)) ||
+               (s->stop && me.running == 0);
       });
-      fin.assign(s->finished_gpu.begin(), s->finished_gpu.end());
-      s->finished_gpu.clear();
-      if (s->stop && s->running == 0 && fin.empty()) {
-        for (Req* r : s->queue) {
-          r->state = CG_REQ_FAILED;
-          r->status = CG_ERR_INVALID_ARG;
-          r->err = "server shut down before the request was admitted";
-          ++s->failed;
-        }
-        s->queue.clear();
-        s->cv_done.notify_all();
-        return;
-      }
+      fin.assign(me.finished.begin(), me.finished.end());
+      me.finished.clear();
+      if (s->stop && me.running == 0 && fin.empty()) return;
     }
     for (Req* r : fin) finish_request(s, r);
     // Admit in arrival order while the head fits.
@@ -317,7 +320,7 @@ void scheduler(cg_server* s) {
       Req* r = nullptr;
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->stop || !admissible(s)) break;
+        if (s->stop || !admissible(s, k)) break;
         r = s->queue.front();
         s->queue.pop_front();
         const size_t need = r->work_bytes + r->result_bytes;
@@ -330,8 +333,10 @@ void scheduler(cg_server* s) {
           s->cv_done.notify_all();
           continue;
         }
-        r->slot = s->free_slots.back();
-        s->free_slots.pop_back();
+        r->worker = k;
+        r->slot = me.free_slots.back();
+        me.free_slots.pop_back();
+        ++me.running;
         s->in_use += need;
         if (s->in_use > s->peak) s->peak = s->in_use;
         ++s->running;
@@ -343,7 +348,8 @@ void scheduler(cg_server* s) {
       if (st != CG_OK) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->in_use -= r->work_bytes + r->result_bytes;
-        s->free_slots.push_back(r->slot);
+        me.free_slots.push_back(r->slot);
+        --me.running;
         r->slot = -1;
         --s->running;
         r->state = CG_REQ_FAILED;
@@ -404,13 +410,16 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
     return srv_fail(CG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
   cudaError_t e;
+  const int n_threads = max_inflight < kSchedThreads ? max_inflight : kSchedThreads;
+  s->workers = std::vector<cg_server::Worker>(static_cast<size_t>(n_threads));
   for (int k = 0; k < max_inflight; ++k) {
     cudaStream_t st;
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
       return bail(e, "creating a slot stream");
     s->streams.push_back(st);
-    s->free_slots.push_back(max_inflight - 1 - k);
   }
+  for (int k = max_inflight - 1; k >= 0; --k)
+    s->workers[size_t(k % n_threads)].free_slots.push_back(k);
   if ((e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(e, "creating the copy stream");
   if ((e = cudaMallocHost(&s->hctr, sizeof(DevCounters) * size_t(max_inflight))) != cudaSuccess)
@@ -423,7 +432,7 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
   if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) return bail(e, "memory pool");
   uint64_t keep = hbm_budget_bytes;  // cached between requests, up to the budget
   cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-  s->th = std::thread(scheduler, s);
+  for (int k = 0; k < n_threads; ++k) s->workers[size_t(k)].th = std::thread(scheduler, s, k);
   *out = s;
   return CG_OK;
 }
@@ -461,7 +470,7 @@ cg_status cg_server_submit(cg_server* srv, const cg_scene* scene, int inputs_on_
     ++srv->submitted;
     *ticket = r->id;
   }
-  srv->cv_sched.notify_one();
+  srv->cv_sched.notify_all();
   return CG_OK;
 }
 
@@ -569,7 +578,7 @@ cg_status cg_server_release(cg_server* srv, int64_t ticket) {
     cudaFreeAsync(r->result, srv->copy_stream);
   }
   delete r;
-  srv->cv_sched.notify_one();
+  srv->cv_sched.notify_all();
   srv->cv_done.notify_all();
   return CG_OK;
 }
@@ -615,7 +624,19 @@ cg_status cg_server_destroy(cg_server* srv) {
     srv->stop = true;
   }
   srv->cv_sched.notify_all();
-  if (srv->th.joinable()) srv->th.join();
+  for (auto& w : srv->workers)
+    if (w.th.joinable()) w.th.join();
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    for (Req* r : srv->queue) {
+      r->state = CG_REQ_FAILED;
+      r->status = CG_ERR_INVALID_ARG;
+      r->err = "server shut down before the request was admitted";
+      ++srv->failed;
+    }
+    srv->queue.clear();
+  }
+  srv->cv_done.notify_all();
   DevGuard g(srv->device);
   for (auto& kv : srv->reqs) {
     Req* r = kv.second;
