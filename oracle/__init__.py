@@ -56,8 +56,10 @@ def _load():
             lib.cgo_dedup.argtypes = [P, I64, I, I, P, P, P]
             lib.cgo_neighbors_h1_rows.argtypes = [P, I64, I, I, P, I64, P, I64, P]
             lib.cgo_neighbors_h1.argtypes = [P, I64, I, I, P, I64, P]
+            lib.cgo_tree.argtypes = [P, I64, I, I, I, I, P, I, P, I64, P]
+            lib.cgo_tree_digits.argtypes = [P, I64, I, I, I, I, P]
             for f in (lib.cgo_pack_signs, lib.cgo_dedup, lib.cgo_neighbors_h1_rows,
-                      lib.cgo_neighbors_h1):
+                      lib.cgo_neighbors_h1, lib.cgo_tree, lib.cgo_tree_digits):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -139,6 +141,49 @@ def neighbors(cells, ell: int, word_bits: int = 64, rows=None) -> np.ndarray:
         if rc:
             raise RuntimeError(f"cgo_neighbors_h1 failed: {rc}")
         return edges[: ne.value].copy()
+
+
+def tree(cells, ell: int, word_bits: int = 64, r: int = 8, order: int = 0, edges: bool = True):
+    """The search tree of §3.2 over sorted unique ``cells``: node counts per
+    level (index 0 is the root) and, with ``edges``, the edges found by the
+    Algorithm 4 walk (uint32[E, 2], same order as ``neighbors``). ``order`` 0
+    is the paper's digit recoding (Figure 2), 1 the value-order recoding."""
+    lib = _load()
+    cells = np.ascontiguousarray(cells, dtype=_wtype(word_bits))
+    u = cells.shape[0]
+    L = (ell + r - 1) // r
+    counts = np.zeros(L + 1, dtype=np.int64)
+    if not edges:
+        rc = lib.cgo_tree(_ptr(cells), u, ell, word_bits, r, order, _ptr(counts), L + 1, None, 0,
+                          ctypes.byref(ctypes.c_int64(0)))
+        if rc:
+            raise RuntimeError(f"cgo_tree failed: {rc}")
+        return counts
+    cap = max(1, u * min(ell, 64) // 2 + 1) if ell <= 64 else max(1, u * 4)
+    while True:
+        out = np.zeros((cap, 2), dtype=np.uint32)
+        ne = ctypes.c_int64(0)
+        rc = lib.cgo_tree(_ptr(cells), u, ell, word_bits, r, order, _ptr(counts), L + 1, _ptr(out),
+                          cap, ctypes.byref(ne))
+        if rc == -2:
+            cap = ne.value
+            continue
+        if rc:
+            raise RuntimeError(f"cgo_tree failed: {rc}")
+        return counts, out[: ne.value].copy()
+
+
+def tree_digits(cells, ell: int, word_bits: int = 64, r: int = 8, order: int = 0) -> np.ndarray:
+    """Digit recoding used by ``tree``: uint32[U, ceil(l / r)]."""
+    lib = _load()
+    cells = np.ascontiguousarray(cells, dtype=_wtype(word_bits))
+    u = cells.shape[0]
+    L = (ell + r - 1) // r
+    out = np.zeros((max(u, 1), L), dtype=np.uint32)
+    rc = lib.cgo_tree_digits(_ptr(cells), u, ell, word_bits, r, order, _ptr(out))
+    if rc:
+        raise RuntimeError(f"cgo_tree_digits failed: {rc}")
+    return out[:u].copy()
 
 
 def build(pts, a, b, word_bits: int = 64):

@@ -18,6 +18,10 @@
 //      and every bit k, the vector x with bit k negated is looked up among the
 //      cells; a hit is an edge. Each unordered pair is reported once (§2.2
 //      asks for pairs i < j, duplicates in X must not repeat pairs).
+//   4. The search tree of §3.2 (Algorithm 3 build, Algorithm 4 walk): the
+//      2^r-ary tree over the r-bit digit recoding of the cells, built level by
+//      level from index ranges of the sorted digit sequences, and the edges it
+//      finds by walking it once per flipped bit.
 //
 // Conventions (the paper fixes none of them):
 //   * bit i of a vector lives in word i / B, bit i % B, with B = 32 or 64
@@ -35,6 +39,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <string>
 #include <unordered_map>
@@ -96,6 +101,69 @@ struct VecHash {
 
 bool bad_words(int ell, int word_bits) {
   return ell < 1 || (word_bits != 32 && word_bits != 64);
+}
+
+// ---- The search tree of §3.2 --------------------------------------------
+//
+// Digit recoding: a vector of l bits is cut into L = ceil(l / r) segments.
+// order = 0 (the paper's, Figure 2): segment h holds bits x(h r) ..
+// x(min(l, (h + 1) r) - 1) and digit h is that bit string read as a binary
+// number, its first bit the most significant (the last segment is shorter
+// when r does not divide l). order = 1 (the library's value order): segment h
+// holds bits [max(0, l - (h + 1) r), l - h r) and digit h is their value with
+// the higher bit more significant, i.e. the same recoding of the vector read
+// from bit l - 1 down.
+std::vector<uint32_t> digits_of(const Vec& v, int ell, int r, int order) {
+  const int L = (ell + r - 1) / r;
+  std::vector<uint32_t> d(size_t(L), 0);
+  for (int h = 0; h < L; ++h) {
+    uint32_t val = 0;
+    if (order == 0) {
+      const int lo = h * r, hi = std::min(ell, (h + 1) * r);
+      for (int k = lo; k < hi; ++k) val = 2 * val + (get_bit(v, k) ? 1u : 0u);
+    } else {
+      const int hi = ell - h * r, lo = std::max(0, ell - (h + 1) * r);
+      for (int k = hi - 1; k >= lo; --k) val = 2 * val + (get_bit(v, k) ? 1u : 0u);
+    }
+    d[size_t(h)] = val;
+  }
+  return d;
+}
+
+// A node of the tree: the range [first, last] of the sorted digit sequences
+// whose first `level` digits equal the node's path, and its children by digit.
+struct TreeNode {
+  int level;
+  int64_t first, last;
+  std::map<uint32_t, int64_t> child;
+};
+
+// Algorithm 3: level 0 is the root holding every sequence; for each level the
+// sets vectors(C, v) are the maximal runs of equal digit h inside C's range
+// (the sequences are sorted, so each set is a range), and every non-empty
+// set becomes the v-child of C.
+std::vector<TreeNode> build_tree(const std::vector<std::vector<uint32_t>>& seq, int L) {
+  std::vector<TreeNode> nodes;
+  nodes.push_back(TreeNode{0, 0, int64_t(seq.size()) - 1, {}});
+  std::vector<int64_t> frontier{0};
+  for (int h = 0; h < L && !seq.empty(); ++h) {
+    std::vector<int64_t> next;
+    for (int64_t c : frontier) {
+      int64_t i = nodes[size_t(c)].first;
+      const int64_t last = nodes[size_t(c)].last;
+      while (i <= last) {
+        int64_t j = i;
+        while (j + 1 <= last && seq[size_t(j + 1)][size_t(h)] == seq[size_t(i)][size_t(h)]) ++j;
+        const int64_t id = int64_t(nodes.size());
+        nodes.push_back(TreeNode{h + 1, i, j, {}});
+        nodes[size_t(c)].child[seq[size_t(i)][size_t(h)]] = id;
+        next.push_back(id);
+        i = j + 1;
+      }
+    }
+    frontier.swap(next);
+  }
+  return nodes;
 }
 
 }  // namespace
@@ -185,6 +253,76 @@ int cgo_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_bits,
                      int64_t edges_cap, int64_t* n_edges) {
   return cgo_neighbors_h1_rows(cells, n_cells, ell, word_bits, nullptr, 0, edges, edges_cap,
                                n_edges);
+}
+
+// Node counts of the search tree per level (counts[0] = 1 for the root, up to
+// counts[L]) and, when edges is non-null, the edges found by Algorithm 4's
+// walk: for every cell and every zero bit k, the digits of the cell with bit
+// k set are followed from the root; reaching the last level is a hit. cells
+// must be sorted and unique (the output of cgo_dedup); edges as for
+// cgo_neighbors_h1 (cell numbers in value order).
+int cgo_tree(const void* cells, int64_t n_cells, int ell, int word_bits, int r, int order,
+             int64_t* counts, int counts_cap, uint32_t* edges, int64_t edges_cap,
+             int64_t* n_edges) {
+  if (n_cells < 0 || bad_words(ell, word_bits) || r < 1 || r > 16 || (order != 0 && order != 1))
+    return -1;
+  const int L = (ell + r - 1) / r;
+  if (counts_cap < L + 1) return -1;
+  std::vector<Vec> u;
+  for (int64_t i = 0; i < n_cells; ++i) u.push_back(load_vec(cells, i, ell, word_bits));
+  // Sort the digit sequences lexicographically, remembering each one's cell.
+  std::vector<std::pair<std::vector<uint32_t>, uint32_t>> tagged;
+  for (int64_t i = 0; i < n_cells; ++i)
+    tagged.emplace_back(digits_of(u[size_t(i)], ell, r, order), uint32_t(i));
+  std::sort(tagged.begin(), tagged.end());
+  std::vector<std::vector<uint32_t>> seq;
+  for (auto& t : tagged) seq.push_back(t.first);
+  const std::vector<TreeNode> nodes = build_tree(seq, L);
+  for (int h = 0; h <= L; ++h) counts[h] = 0;
+  for (const TreeNode& nd : nodes) ++counts[nd.level];
+  if (!edges) return 0;
+  int64_t e = 0;
+  for (int64_t i = 0; i < n_cells; ++i) {
+    for (int k = 0; k < ell; ++k) {
+      if (get_bit(u[size_t(i)], k)) continue;
+      Vec y = u[size_t(i)];
+      flip_bit(y, k);
+      const std::vector<uint32_t> dy = digits_of(y, ell, r, order);
+      int64_t c = 0;
+      bool found = true;
+      for (int h = 0; h < L; ++h) {
+        auto it = nodes[size_t(c)].child.find(dy[size_t(h)]);
+        if (it == nodes[size_t(c)].child.end()) {
+          found = false;
+          break;
+        }
+        c = it->second;
+      }
+      if (!found) continue;
+      const uint32_t j = tagged[size_t(nodes[size_t(c)].first)].second;
+      if (e < edges_cap) {
+        edges[2 * e] = uint32_t(i);
+        edges[2 * e + 1] = j;
+      }
+      ++e;
+    }
+  }
+  *n_edges = e;
+  return e > edges_cap ? -2 : 0;
+}
+
+// Digit recoding of every cell (as used by cgo_tree): digits[i][h], L =
+// ceil(l / r) digits per cell.
+int cgo_tree_digits(const void* cells, int64_t n_cells, int ell, int word_bits, int r, int order,
+                    uint32_t* digits) {
+  if (n_cells < 0 || bad_words(ell, word_bits) || r < 1 || r > 16 || (order != 0 && order != 1))
+    return -1;
+  const int L = (ell + r - 1) / r;
+  for (int64_t i = 0; i < n_cells; ++i) {
+    const std::vector<uint32_t> d = digits_of(load_vec(cells, i, ell, word_bits), ell, r, order);
+    for (int h = 0; h < L; ++h) digits[i * L + h] = d[size_t(h)];
+  }
+  return 0;
 }
 
 // Steps 1-3 for one scene: points -> cells and edges.

@@ -101,6 +101,91 @@ def test_fig2_pairs():
     assert named == [(p("110100"), p("110110")), (p("110110"), p("110111"))]
 
 
+def _read_fig2_tree():
+    out = {}
+    with open(os.path.join(GOLDEN, "fig2_tree_levels.txt")) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            out[t[0]] = [int(x) for x in t[1:]]
+    return out
+
+
+def test_fig2_digit_recoding():
+    """Figure 2 lists every vector's base-4 recoding (r = 2)."""
+    vecs = _read_fig2()
+    cells = ints_to_rows([paper_string_to_int(v) for v, _ in vecs], 6, 64)
+    got = oracle.tree_digits(cells, 6, 64, r=2, order=0)
+    assert ["".join(str(d) for d in row) for row in got.tolist()] == [t for _, t in vecs]
+
+
+def test_fig2_tree_levels_and_edges():
+    """Figure 2's tree has 3, 4 and 6 nodes below the root; its search finds
+    the two Hamming-1 pairs of the example."""
+    vecs = _read_fig2()
+    want = _read_fig2_tree()
+    vals = sorted(paper_string_to_int(v) for v, _ in vecs)
+    cells = ints_to_rows(vals, 6, 64)
+    counts, edges = oracle.tree(cells, 6, 64, r=want["r"][0], order=0)
+    assert counts.tolist() == want["levels"]
+    assert edges.tolist() == oracle.neighbors(cells, 6, 64).tolist()
+    p = paper_string_to_int
+    assert [(vals[i], vals[j]) for i, j in edges.tolist()] == [
+        (p("110100"), p("110110")), (p("110110"), p("110111"))]
+
+
+def _prefix_counts(vals, ell, r, order):
+    """Distinct prefixes of h digits, h = 0..L, from integer arithmetic: the
+    paper's order reads bits from x(0) up, so a prefix is the value modulo
+    2^(h r); the value order reads from bit l - 1 down, so it is the value
+    shifted right by l - h r."""
+    L = (ell + r - 1) // r
+    out = []
+    for h in range(L + 1):
+        nb = min(h * r, ell)
+        if order == 0:
+            out.append(len({v & ((1 << nb) - 1) for v in vals}))
+        else:
+            out.append(len({v >> (ell - nb) for v in vals}))
+    return out
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("r", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("ell", [1, 7, 16, 64, 65, 130])
+def test_tree_levels_and_search_against_lookup(ell, r, order):
+    rng = np.random.default_rng(ell * 100 + r * 10 + order)
+    n = 300
+    vals = set()
+    # clustered vectors, so that the tree has long shared prefixes and many
+    # Hamming-1 pairs
+    base = [int(rng.integers(0, 2**63)) | (int(rng.integers(0, 2**63)) << 63) for _ in range(6)]
+    for _ in range(n):
+        v = base[int(rng.integers(0, 6))]
+        for _ in range(int(rng.integers(0, 4))):
+            v ^= 1 << int(rng.integers(0, ell))
+        vals.add(v & ((1 << ell) - 1))
+    vals = sorted(vals)
+    cells = ints_to_rows(vals, ell, 64)
+    counts, edges = oracle.tree(cells, ell, 64, r=r, order=order)
+    assert counts.tolist() == _prefix_counts(vals, ell, r, order)
+    assert counts[-1] == len(vals) and counts[0] == 1
+    assert np.array_equal(edges, oracle.neighbors(cells, ell, 64))
+    assert len(edges) > 0 or ell == 1
+
+
+@pytest.mark.parametrize("ell,r", [(6, 2), (8, 3), (9, 8)])
+def test_tree_hypercube_levels(ell, r):
+    """All 2^l vectors: every prefix occurs, 2^(min(h r, l)) nodes on level h,
+    and the search finds the l 2^(l-1) cube edges."""
+    cells = np.arange(1 << ell, dtype=np.uint64).reshape(-1, 1)
+    counts, edges = oracle.tree(cells, ell, 64, r=r, order=0)
+    L = (ell + r - 1) // r
+    assert counts.tolist() == [1 << min(h * r, ell) for h in range(L + 1)]
+    assert len(edges) == ell * (1 << (ell - 1))
+
+
 def _python_signs(pts, a, b):
     out = []
     for p in pts.tolist():
