@@ -70,6 +70,9 @@ typedef int cg_status;
                                 pivot cells, and only the 2^h buckets whose
                                 distances differ by +-1 in every coordinate are
                                 compared, word by word (XOR + popcount) */
+#define CG_STRATEGY_TREE 4   /* the 2^r-ary search tree of §3.2 (Algorithms 3-4),
+                                r = 8, built level by level over the sorted
+                                cells and walked once per flipped bit */
 
 /* Message describing the calling thread's last failed call ("" if none). */
 const char* cg_last_error(void);
@@ -166,7 +169,7 @@ cg_status cg_ctx_stage_times(cg_ctx* ctx, double* ms, const char** names, int ca
  * ------------------------------------------------------------------------- */
 #define CG_TUNE_BUCKETS 7
 typedef struct cg_tune_params {
-  int strategy;    /* CG_STRATEGY_HASH, _SORTED or _PIVOT */
+  int strategy;    /* CG_STRATEGY_HASH, _SORTED, _PIVOT or _TREE */
   int pivots;      /* h for PIVOT: 1 <= h <= min(8, 64 / bits(l)) (clamped) */
   int sign_kernel; /* 0: fp32 FMA filter with exact fallback; 1: tensor cores
                       (tcgen05, l <= 64 only; ignored above) */
@@ -244,8 +247,8 @@ cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, cg_b
 
 /* Autotuner: for every bucket of l present among the scenes (device arrays,
  * as for cg_build_batch), times cg_build of those scenes (at most 16 per
- * bucket) under each candidate setting -- HASH, SORTED, PIVOT with h in
- * {2, 3, 4}, and for l <= 64 both sign kernels -- `reps` times after one
+ * bucket) under each candidate setting -- HASH, SORTED, TREE, PIVOT with h
+ * in {2, 3, 4}, and for l <= 64 both sign kernels -- `reps` times after one
  * warm-up, and keeps the fastest setting in the context. chosen_ms
  * (nullable, host double[CG_TUNE_BUCKETS]) receives the best time per bucket
  * (0 for buckets without scenes). Blocks until done. */

@@ -344,6 +344,62 @@ cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounter
   return CG_OK;
 }
 
+// TREE strategy: node array, build scratch, look-back words and (when the
+// single-pass kernel's shared memory does not fit) hit masks, counts,
+// offsets and scan scratch.
+struct TreeWs {
+  TreeNode* nodes;
+  void* scratch;
+  unsigned long long* status;
+  size_t n_status;
+  uint32_t* masks;
+  uint32_t* counts;
+  unsigned long long* offsets;
+  void* scan;
+};
+
+TreeWs carve_treews(Carve& c, size_t ucap, int ell) {
+  TreeWs t{};
+  const size_t u = ucap > 0 ? ucap : 1;
+  const int w64 = (ell + 63) / 64;
+  t.nodes = c.take<TreeNode>(tree_node_capacity(u));
+  t.scratch = c.take_bytes(tree_scratch_bytes(u));
+  if (neighbors_emit_tree_fits(w64, ell)) {
+    t.n_status = ne_status_words(u);
+    t.status = c.take<unsigned long long>(t.n_status);
+  } else {
+    t.masks = c.take<uint32_t>(u * size_t((ell + 31) / 32));
+    t.counts = c.take<uint32_t>(u);
+    t.offsets = c.take<unsigned long long>(u);
+    t.scan = c.take_bytes(scan_scratch_bytes(u));
+  }
+  return t;
+}
+
+// Steps 3-4 with the TREE strategy over sorted internal rows: build the tree
+// (one round of kernels per level), then one walk per flipped bit.
+cg_status tree_steps(const uint64_t* cells, int w64, int ell, DevCounters* ctr, const TreeWs& t,
+                     size_t ucap, uint32_t* edges, int64_t edges_cap, cudaStream_t s) {
+  CG_CUDA(launch_tree_build(cells, w64, ell, ctr, ucap, t.nodes, t.scratch, s), "tree build");
+  if (t.status) {
+    CG_CUDA(cudaMemsetAsync(t.status, 0, t.n_status * sizeof(unsigned long long), s),
+            "look-back words");
+    CG_CUDA(launch_neighbors_emit_tree(cells, w64, ell, t.nodes, ctr, t.status, edges, edges_cap,
+                                       ucap, s),
+            "tree search and edge output");
+  } else {
+    CG_CUDA(launch_neighbors_tree_masks(cells, w64, ell, t.nodes, ctr, t.masks, t.counts, ucap, s),
+            "tree search");
+    CG_CUDA(scan_exclusive_u32(t.counts, t.offsets, &ctr->n_unique, ucap, &ctr->n_edges, t.scan,
+                               s),
+            "edge offsets");
+    CG_CUDA(launch_emit_tree(cells, w64, ell, t.nodes, ctr, t.masks, t.offsets, edges, edges_cap,
+                             ucap, s),
+            "edge output");
+  }
+  return CG_OK;
+}
+
 int env_pivots(int ell) {
   int h = 4;
   if (const char* v = std::getenv("CG_PIVOTS")) h = std::atoi(v);
@@ -674,18 +730,20 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
                           void* ws, size_t* ws_bytes, void* stream) {
   std::string why;
   if (!check_common(n_cells, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
-  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_PIVOT)
+  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_TREE)
     return fail(CG_ERR_INVALID_ARG, "unknown strategy");
   if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
   const size_t un = size_t(n_cells > 0 ? n_cells : 1);
   const size_t cap = std::max<size_t>(1024, next_pow2(2 * un));
   const bool small = ell <= 64;
   const bool pivot = strategy == CG_STRATEGY_PIVOT;
+  const bool tree = strategy == CG_STRATEGY_TREE;
   {
     Carve c{nullptr};
     if (small) carve_small(c, cap, un, ell, false, true, true);
     else carve_wide(c, un, cap, un, ell, false, false, false, true);
     if (pivot) carve_pivot(c, un);
+    if (tree) carve_treews(c, un, ell);
     if (!ws) {
       *ws_bytes = c.off + 256;
       return CG_OK;
@@ -700,7 +758,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
   DevCounters host{};
   if (small) {
     SmallWs w = carve_small(c, cap, un, ell, false, true, true);
-    const bool table = strategy != CG_STRATEGY_SORTED && !pivot;
+    const bool table = strategy != CG_STRATEGY_SORTED && !pivot && !tree;
     CG_CUDA(launch_clear_build(table ? w.tkeys : nullptr, table ? cap : 0, w.status,
                                ne_status_words(un), w.ctr, s),
             "clearing table");
@@ -709,6 +767,8 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     if (pivot) {
       st = pivot_steps(w.cells, 1, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un,
                        edges, edges_cap, s);
+    } else if (tree) {
+      st = tree_steps(w.cells, 1, ell, w.ctr, carve_treews(c, un, ell), un, edges, edges_cap, s);
     } else {
       if (table) CG_CUDA(launch_index_small(w.cells, w.table(false), un, s), "indexing cells");
       st = neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
@@ -720,9 +780,16 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     WideWs w = carve_wide(c, un, cap, un, ell, false, false, false, true);
     CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
     CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
-    cg_status st = pivot ? pivot_steps(w.cells, (ell + 63) / 64, ell, env_pivots(ell), w.ctr,
-                                       carve_pivot(c, un), un, edges, edges_cap, s)
-                         : neighbors_wide_steps(w, ell, strategy, edges, edges_cap, s);
+    const int w64 = (ell + 63) / 64;
+    cg_status st;
+    if (pivot)
+      st = pivot_steps(w.cells, w64, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un, edges,
+                       edges_cap, s);
+    else if (tree)
+      st = tree_steps(w.cells, w64, ell, w.ctr, carve_treews(c, un, ell), un, edges, edges_cap,
+                      s);
+    else
+      st = neighbors_wide_steps(w, ell, strategy, edges, edges_cap, s);
     if (st) return st;
     st = read_counters(w.ctr, &host, s);
     if (st) return st;
@@ -793,7 +860,8 @@ cg_tune_params default_tune() { return cg_tune_params{CG_STRATEGY_HASH, 4, 0}; }
 
 cg_tune_params sanitize_tune(const cg_tune_params& p, int ell) {
   cg_tune_params q = p;
-  if (q.strategy != CG_STRATEGY_SORTED && q.strategy != CG_STRATEGY_PIVOT)
+  if (q.strategy != CG_STRATEGY_SORTED && q.strategy != CG_STRATEGY_PIVOT &&
+      q.strategy != CG_STRATEGY_TREE)
     q.strategy = CG_STRATEGY_HASH;
   const int hmax = pivot_max_h(ell);
   q.pivots = q.pivots < 1 ? 1 : (q.pivots > hmax ? hmax : q.pivots);
@@ -815,14 +883,17 @@ ScenePlan plan_scene(int64_t n, int ell, size_t cap, const cg_tune_params& tp) {
 }
 
 void carve_scene(Carve& c, const ScenePlan& p, DevCounters* ext_ctr, SmallWs* sw, WideWs* ww,
-                 PivotWs* pw) {
+                 PivotWs* pw, TreeWs* tw) {
   const size_t un = size_t(p.n > 0 ? p.n : 1);
   const bool pivot = p.tp.strategy == CG_STRATEGY_PIVOT;
-  if (p.small) *sw = carve_small(c, p.cap, p.ucap, p.ell, true, !pivot, false, un, ext_ctr);
+  const bool tree = p.tp.strategy == CG_STRATEGY_TREE;
+  const bool own = pivot || tree;  // the strategy brings its own search buffers
+  if (p.small) *sw = carve_small(c, p.cap, p.ucap, p.ell, true, !own, false, un, ext_ctr);
   else
-    *ww = carve_wide(c, un, p.cap, p.ucap, p.ell, true, true, false, !pivot, p.single && !pivot,
+    *ww = carve_wide(c, un, p.cap, p.ucap, p.ell, true, true, false, !own, p.single && !own,
                      ext_ctr);
   if (pivot) *pw = carve_pivot(c, p.ucap);
+  if (tree) *tw = carve_treews(c, p.ucap, p.ell);
 }
 
 size_t scene_ws_bytes(const ScenePlan& p) {
@@ -830,8 +901,9 @@ size_t scene_ws_bytes(const ScenePlan& p) {
   SmallWs sw;
   WideWs ww;
   PivotWs pw;
+  TreeWs tw;
   DevCounters dummy;
-  carve_scene(m, p, &dummy, &sw, &ww, &pw);
+  carve_scene(m, p, &dummy, &sw, &ww, &pw, &tw);
   return m.off + 256;
 }
 
@@ -845,15 +917,18 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   SmallWs w{};
   WideWs ww{};
   PivotWs pw{};
-  carve_scene(c, plan, ctr, &w, &ww, &pw);
+  TreeWs tw{};
+  carve_scene(c, plan, ctr, &w, &ww, &pw, &tw);
   const int64_t n = plan.n;
   const int ell = plan.ell;
   const int strategy = plan.tp.strategy;
   const bool pivot = strategy == CG_STRATEGY_PIVOT;
+  const bool tree = strategy == CG_STRATEGY_TREE;
+  const bool own = pivot || tree;
   cg_status st;
   if (plan.small) {
-    CG_CUDA(launch_clear_build(w.tkeys, plan.cap, pivot ? nullptr : w.status,
-                               pivot ? 0 : ne_status_words(plan.ucap), w.ctr, s),
+    CG_CUDA(launch_clear_build(w.tkeys, plan.cap, own ? nullptr : w.status,
+                               own ? 0 : ne_status_words(plan.ucap), w.ctr, s),
             "clearing table");
     mark(ctx, "clear", s);
     if (n > 0) {
@@ -871,13 +946,14 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     mark(ctx, "sort_number", s);
     st = pivot ? pivot_steps(w.cells, 1, ell, plan.tp.pivots, w.ctr, pw, plan.ucap, edges,
                              edges_cap, s)
-               : neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
+         : tree ? tree_steps(w.cells, 1, ell, w.ctr, tw, plan.ucap, edges, edges_cap, s)
+                : neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
     if (st) return st;
     mark(ctx, "neighbors_edges", s);
     return CG_OK;
   }
   const int w64 = (ell + 63) / 64;
-  if (!plan.single || pivot) {
+  if (!plan.single || own) {
     CG_CUDA(launch_zero_counters(ww.ctr, s), "counters");
     if (n > 0) CG_CUDA(launch_pack_store(pa, 64, ww.keys64, s), "sign vectors");
     mark(ctx, "pack", s);
@@ -898,7 +974,8 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     mark(ctx, "dedup_sort", s);
     st = pivot ? pivot_steps(ww.cells, w64, ell, plan.tp.pivots, ww.ctr, pw, plan.ucap, edges,
                              edges_cap, s)
-               : neighbors_wide_steps(ww, ell, strategy, edges, edges_cap, s);
+         : tree ? tree_steps(ww.cells, w64, ell, ww.ctr, tw, plan.ucap, edges, edges_cap, s)
+                : neighbors_wide_steps(ww, ell, strategy, edges, edges_cap, s);
     if (st) return st;
     mark(ctx, "neighbors_edges", s);
     return CG_OK;
@@ -1427,8 +1504,8 @@ extern "C" cg_status cg_ctx_tune_set(cg_ctx* ctx, int bucket, const cg_tune_para
   if (!ctx || !p) return fail(CG_ERR_INVALID_ARG, "NULL argument");
   if (bucket < 0 || bucket >= CG_TUNE_BUCKETS) return fail(CG_ERR_INVALID_ARG, "no such bucket");
   if (p->strategy != CG_STRATEGY_HASH && p->strategy != CG_STRATEGY_SORTED &&
-      p->strategy != CG_STRATEGY_PIVOT)
-    return fail(CG_ERR_INVALID_ARG, "strategy must be HASH, SORTED or PIVOT");
+      p->strategy != CG_STRATEGY_PIVOT && p->strategy != CG_STRATEGY_TREE)
+    return fail(CG_ERR_INVALID_ARG, "strategy must be HASH, SORTED, PIVOT or TREE");
   if (p->pivots < 1 || p->pivots > 8) return fail(CG_ERR_INVALID_ARG, "pivots must be 1..8");
   if (p->sign_kernel != 0 && p->sign_kernel != 1)
     return fail(CG_ERR_INVALID_ARG, "sign_kernel must be 0 or 1");
@@ -1504,6 +1581,7 @@ extern "C" cg_status cg_ctx_autotune(cg_ctx* ctx, const cg_scene* scenes, int n_
     if (by_bucket[size_t(b)].empty()) continue;
     std::vector<cg_tune_params> cand = {{CG_STRATEGY_HASH, 4, 0},
                                         {CG_STRATEGY_SORTED, 4, 0},
+                                        {CG_STRATEGY_TREE, 4, 0},
                                         {CG_STRATEGY_PIVOT, 2, 0},
                                         {CG_STRATEGY_PIVOT, 3, 0},
                                         {CG_STRATEGY_PIVOT, 4, 0}};

@@ -580,6 +580,61 @@ struct WideSorted {
   }
 };
 
+// TREE lookups (Algorithm 4's walk): from the root, follow the child for the
+// query's digit on each node's branching level; a missing child ends the
+// search; a leaf is compared with the whole query.
+struct TreeSmall {
+  const uint64_t* cells;
+  const TreeNode* nodes;
+  int ell;
+  __device__ __forceinline__ int64_t find(uint64_t y) const {
+    uint32_t c = 0;
+    for (int guard = 0; guard <= tree_levels(ell) + 1; ++guard) {
+      const TreeNode& nd = nodes[c];
+      if (nd.cnt <= 1) return (nd.cnt == 1 && cells[nd.lo] == y) ? int64_t(nd.lo) : -1;
+      int lo, hi;
+      tree_digit_bits(ell, int(nd.lv), &lo, &hi);
+      const uint32_t v = uint32_t((y >> lo) & ((1ull << (hi - lo)) - 1ull));
+      const int64_t ch = tree_child(nd, v);
+      if (ch < 0) return -1;
+      c = uint32_t(ch);
+    }
+    return -1;
+  }
+};
+
+struct TreeWide {
+  const uint64_t* cells;
+  const TreeNode* nodes;
+  int w;
+  int ell;
+  // Digit on level lv of cells[i] with bit k flipped.
+  __device__ __forceinline__ uint32_t digit(uint32_t i, int k, int lv) const {
+    int lo, hi;
+    tree_digit_bits(ell, lv, &lo, &hi);
+    const uint64_t* row = cells + uint64_t(i) * w;
+    const int q = lo >> 6, sh = lo & 63;
+    uint64_t a = row[q], b = (sh + (hi - lo) > 64) ? row[q + 1] : 0ull;
+    if ((k >> 6) == q) a ^= 1ull << (k & 63);
+    if ((k >> 6) == q + 1) b ^= 1ull << (k & 63);
+    uint64_t v = a >> sh;
+    if (sh + (hi - lo) > 64) v |= b << (64 - sh);
+    return uint32_t(v & ((1ull << (hi - lo)) - 1ull));
+  }
+  __device__ __forceinline__ int64_t find(uint32_t i, int k, const uint64_t*) const {
+    uint32_t c = 0;
+    for (int guard = 0; guard <= tree_levels(ell) + 1; ++guard) {
+      const TreeNode& nd = nodes[c];
+      if (nd.cnt <= 1)
+        return (nd.cnt == 1 && is_flip(cells, w, i, nd.lo, k)) ? int64_t(nd.lo) : -1;
+      const int64_t ch = tree_child(nd, digit(i, k, int(nd.lv)));
+      if (ch < 0) return -1;
+      c = uint32_t(ch);
+    }
+    return -1;
+  }
+};
+
 template <class L>
 __global__ void __launch_bounds__(kThreads)
     neighbors_wide(const uint64_t* __restrict__ cells, int w, int ell, L look,
@@ -1095,6 +1150,59 @@ cudaError_t launch_batch_gather(const BatchEntry* tab, int n, long long* cells_o
                                                         out_cells, out_edges);
   count_launch(2);
   return cudaGetLastError();
+}
+
+cudaError_t launch_neighbors_emit_tree(const uint64_t* cells, int w64, int ell,
+                                       const TreeNode* nodes, DevCounters* ctr,
+                                       unsigned long long* status, uint32_t* edges,
+                                       int64_t edges_cap, size_t max_n, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const int g = grid_for(max_n, kNECells, 4);
+  if (w64 == 1 && ell <= 64) {
+    neighbors_emit_small<<<g, kNEThreads, 0, s>>>(cells, TreeSmall{cells, nodes, ell}, ctr, ell,
+                                                  status, edges, edges_cap, uint32_t(max_n));
+    return finish(0);
+  }
+  const size_t smem = size_t(ell) * sizeof(uint64_t) + size_t(kNECells) * ell * sizeof(uint32_t);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  auto k = neighbors_emit_wide<TreeWide>;
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k), smem);
+  if (e != cudaSuccess) return e;
+  k<<<g, kNEThreads, smem, s>>>(cells, w64, ell, TreeWide{cells, nodes, w64, ell}, ctr, status,
+                                edges, edges_cap, uint32_t(max_n));
+  return finish(0);
+}
+
+bool neighbors_emit_tree_fits(int w64, int ell) {
+  return (w64 == 1 && ell <= 64) ||
+         size_t(ell) * sizeof(uint64_t) + size_t(kNECells) * ell * sizeof(uint32_t) <= 200 * 1024;
+}
+
+cudaError_t launch_neighbors_tree_masks(const uint64_t* cells, int w64, int ell,
+                                        const TreeNode* nodes, DevCounters* ctr, uint32_t* masks,
+                                        uint32_t* counts, size_t max_n, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const size_t smem = hbits_bytes(ell);
+  auto k = neighbors_wide<TreeWide>;
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k), smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid_for(max_n, kThreads / 32), kThreads, smem, s>>>(
+      cells, w64, ell, TreeWide{cells, nodes, w64, ell}, ctr, masks, counts);
+  return finish(0);
+}
+
+cudaError_t launch_emit_tree(const uint64_t* cells, int w64, int ell, const TreeNode* nodes,
+                             DevCounters* ctr, const uint32_t* masks,
+                             const unsigned long long* offsets, uint32_t* edges,
+                             int64_t edges_cap, size_t max_n, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const size_t smem = hbits_bytes(ell);
+  auto k = emit_wide<TreeWide>;
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k), smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid_for(max_n, kThreads / 32), kThreads, smem, s>>>(
+      cells, w64, ell, TreeWide{cells, nodes, w64, ell}, ctr, masks, offsets, edges, edges_cap);
+  return finish(0);
 }
 
 }  // namespace cg

@@ -355,6 +355,61 @@ cudaError_t launch_pivot_edges(const uint64_t* cells, int w64, int ell, int h, D
                                unsigned long long* offsets, uint32_t* fill, void* scan,
                                uint32_t* edges, int64_t edges_cap, cudaStream_t s);
 
+// TREE strategy (cg_tree.cu): the 2^r-ary search tree of §3.2 (r = 8) over
+// the sorted cells, digits taken from the most significant end of the value
+// order (digit h = bits [max(0, l - 8 (h + 1)), l - 8 h)). Leaf-valued (a node
+// whose range holds one cell is a leaf; the lookup then compares the whole
+// vector) and with single-child chains contracted: an internal node records
+// the level its children branch on. Children of a node are consecutive node
+// ids in digit order; bm marks the digits present.
+struct TreeNode {
+  uint32_t bm[8];
+  uint32_t first;  // id of the first child
+  uint32_t lo;     // first cell of the node's range
+  uint32_t cnt;    // cells in the range (1: leaf of cell lo)
+  uint32_t lv;     // branching level (internal nodes)
+};
+static_assert(sizeof(TreeNode) == 48, "TreeNode layout");
+
+#ifdef __CUDACC__
+__device__ __forceinline__ int tree_levels(int ell) { return (ell + 7) >> 3; }
+// [lo, hi) bit range of digit h.
+__device__ __forceinline__ void tree_digit_bits(int ell, int h, int* lo, int* hi) {
+  *hi = ell - 8 * h;
+  *lo = *hi > 8 ? *hi - 8 : 0;
+}
+// Child of node nd for digit v, or -1.
+__device__ __forceinline__ int64_t tree_child(const TreeNode& nd, uint32_t v) {
+  const uint32_t wv = nd.bm[v >> 5];
+  if (!((wv >> (v & 31)) & 1u)) return -1;
+  uint32_t rank = __popc(wv & ((1u << (v & 31)) - 1u));
+  for (uint32_t q = 0; q < (v >> 5); ++q) rank += __popc(nd.bm[q]);
+  return int64_t(nd.first) + rank;
+}
+#endif
+
+// Workspace of the tree build for up to max_n cells (bytes), and the build
+// itself: nodes (tree_node_capacity(max_n) entries) end up holding the tree,
+// node 0 the root.
+size_t tree_node_capacity(size_t max_n);
+size_t tree_scratch_bytes(size_t max_n);
+cudaError_t launch_tree_build(const uint64_t* cells, int w64, int ell, const DevCounters* ctr,
+                              size_t max_n, TreeNode* nodes, void* scratch, cudaStream_t s);
+// Steps 3-4 with TREE lookups: single pass (like launch_neighbors_emit_*)
+// when neighbors_emit_tree_fits(w64, l), else hit masks + scan + emit.
+bool neighbors_emit_tree_fits(int w64, int ell);
+cudaError_t launch_neighbors_tree_masks(const uint64_t* cells, int w64, int ell,
+                                        const TreeNode* nodes, DevCounters* ctr, uint32_t* masks,
+                                        uint32_t* counts, size_t max_n, cudaStream_t s);
+cudaError_t launch_emit_tree(const uint64_t* cells, int w64, int ell, const TreeNode* nodes,
+                             DevCounters* ctr, const uint32_t* masks,
+                             const unsigned long long* offsets, uint32_t* edges,
+                             int64_t edges_cap, size_t max_n, cudaStream_t s);
+cudaError_t launch_neighbors_emit_tree(const uint64_t* cells, int w64, int ell,
+                                       const TreeNode* nodes, DevCounters* ctr,
+                                       unsigned long long* status, uint32_t* edges,
+                                       int64_t edges_cap, size_t max_n, cudaStream_t s);
+
 // Batch gather: per scene, its counters, internal cells (w words per cell,
 // up to ucap cells) and internal edges (up to ecap).
 struct BatchEntry {

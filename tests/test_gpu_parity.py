@@ -172,7 +172,7 @@ def test_dedup_all_duplicates_and_empty(dev):
 
 # ------------------------------ steps 3-4 --------------------------------
 
-@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot"])
+@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree"])
 @pytest.mark.parametrize("kind,wb", [("lines", 32), ("planes64", 64), ("planes200", 64),
                                      ("planes200", 32), ("chains", 64), ("chains130", 64)])
 def test_neighbors_match_oracle(dev, kind, wb, strategy):
@@ -184,7 +184,7 @@ def test_neighbors_match_oracle(dev, kind, wb, strategy):
     assert len(want) > 0
 
 
-@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot"])
+@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree"])
 def test_neighbors_hypercube(dev, strategy):
     ell = 12
     cells = np.arange(1 << ell, dtype=np.uint64).reshape(-1, 1)
@@ -204,6 +204,18 @@ def test_neighbors_pivot_counts(dev, pivots, monkeypatch):
         assert np.array_equal(edges_np(got), oracle.neighbors(cells, ell, wb))
 
 
+def test_neighbors_tree_degenerate_shapes(dev):
+    """Tree corner cases: one cell, two cells differing in the lowest bit only
+    (a single long shared prefix), l not a multiple of the digit width."""
+    for ell, vals in ((5, [3]), (64, [0, 1]), (70, [0, 1, 1 << 69, (1 << 69) | 1]),
+                      (13, list(range(0, 1 << 13, 3)))):
+        cells = np.array([[v & ((1 << 64) - 1), v >> 64] if ell > 64 else [v] for v in vals],
+                         dtype=np.uint64)
+        want = oracle.neighbors(cells, ell, 64)
+        got = cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64, strategy="tree")
+        assert np.array_equal(edges_np(got), want), ell
+
+
 def test_neighbors_pivot_wide_4096(dev):
     """The longest vectors (l = 4096, 64 words): random rows plus one-bit
     variants at every word position."""
@@ -219,7 +231,7 @@ def test_neighbors_pivot_wide_4096(dev):
     cells = oracle.dedup(keys, ell, 64)
     want = oracle.neighbors(cells, ell, 64)
     assert len(want) > 50
-    for strategy in ("hash", "sorted", "pivot"):
+    for strategy in ("hash", "sorted", "pivot", "tree"):
         got = cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64, strategy=strategy)
         assert np.array_equal(edges_np(got), want), strategy
 
@@ -434,9 +446,10 @@ def test_full_size_chains(dev):
     cells = cellgraph.dedup_cells(keys_d, 1024, 64)
     del keys_d
     edges = cellgraph.neighbors_h1(cells, 1024, 64)
-    edges_pivot = cellgraph.neighbors_h1(cells, 1024, 64, strategy="pivot")
-    assert torch.equal(edges_pivot, edges)
-    del edges_pivot
+    for strategy in ("pivot", "tree"):
+        other = cellgraph.neighbors_h1(cells, 1024, 64, strategy=strategy)
+        assert torch.equal(other, edges), strategy
+        del other
     got_c = words_np(cells, 64)
     got_e = edges_np(edges).astype(np.int64)
     want_c = oracle.dedup(ch.keys, 1024, 64)
@@ -568,7 +581,8 @@ def _tuning_scenes():
 
 
 @pytest.mark.parametrize("setting", [("hash", 4, 0), ("sorted", 4, 0), ("pivot", 1, 0),
-                                     ("pivot", 3, 0), ("pivot", 4, 1), ("hash", 4, 1)])
+                                     ("pivot", 3, 0), ("pivot", 4, 1), ("hash", 4, 1),
+                                     ("tree", 4, 0)])
 def test_build_under_every_tuning(dev, setting):
     strategy, pivots, sk = setting
     c2 = cellgraph.Context(0)
