@@ -42,8 +42,8 @@ WORKLOAD = "planes_3d: l=64 planes, d=3, N=2^24 int32 points in [-2^20,2^20]^3"
 # an ncu capture, with the sha256 of the kernel source they were taken on;
 # reported only while the source is unchanged.
 NCU_TRAFFIC = {
-    "source_sha256": "76b1d8d1ff1767a084d1997cb89e29aba4c34d65ded8c5dbeacd524866489077",
-    "bytes_per_launch": 205150208.0,
+    "source_sha256": "821d4daf6b93a89269c49e8ef2c4a0cb531ca76f2cd1b2870c0dd7d49a398ff1",
+    "bytes_per_launch": 205089280.0,
     "capture": "profiles/pack_fast_kernel_planes_3d.md",
 }
 
@@ -473,7 +473,6 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- device-resident timed region ----
-    ctx.set_timing(True)
     launches0 = cellgraph.launch_count()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
@@ -488,9 +487,15 @@ def run_ours(args):
         if pg:
             pg.barrier()
     launches = cellgraph.launch_count() - launches0
+    ms = max_over_ranks(start.elapsed_time(stop) / args.steps, pg, dev)
+    # Stage split from a separate pass (the stage timers record CUDA events
+    # between the stages and turn off the graph replay of repeated builds).
+    ctx.set_timing(True)
+    for _ in range(args.steps):
+        ctx.build(pts, a, b, 64, outputs=outputs)
+    torch.cuda.synchronize()
     stages, builds = ctx.stage_times()
     ctx.set_timing(False)
-    ms = max_over_ranks(start.elapsed_time(stop) / args.steps, pg, dev)
     value = job_value(world, n, ms * 1e-3)
 
     # ---- end to end through the C-ABI with host buffers ----
@@ -536,7 +541,9 @@ def run_ours(args):
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "peak_note": f"152 SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz')} MHz "
                                   f"({peak_kind} max clock); one MAC = one lane-FMA",
-                     "kernel_ms": k_ms, "work": "N*l*d exact multiply-adds"},
+                     "kernel_ms": k_ms, "work": "N*l*d exact multiply-adds",
+                     "kernel_timing": "CUDA events between the build's stages on its stream, "
+                                      "in a second pass of the same builds"},
         "hbm_step": {"compulsory_bytes": compulsory,
                      "achieved_gbs": compulsory / (ms * 1e-3) / 1e9,
                      "peak_gbs": hbm_peak,

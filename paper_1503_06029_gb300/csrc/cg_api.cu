@@ -278,6 +278,15 @@ PivotWs carve_pivot(Carve& c, size_t ucap) {
   return p;
 }
 
+cg_status check_counters(const DevCounters* host) {
+  if (host->error & kErrTimeout)
+    return fail(CG_ERR_TIMEOUT, "a bounded device-side wait ran out");
+  if (host->error)
+    return fail(CG_ERR_INTERNAL, "device-side consistency check failed (code " +
+                                     std::to_string(host->error) + ")");
+  return CG_OK;
+}
+
 cg_status read_counters(DevCounters* dev, DevCounters* host, cudaStream_t s) {
   CG_CUDA(cudaMemcpyAsync(host, dev, sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
           "reading counters");
@@ -496,6 +505,13 @@ struct cg_ctx {
   uint64_t bgraph_sig = 0;
   uint64_t bgraph_launches = 0;  // kernels inside the graph
   uint64_t last_sig = 0;
+  // Captured single build (same idea, for repeated identical cg_build calls).
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t g_in = nullptr, g_out = nullptr;
+  cudaGraphExec_t sgraph = nullptr;
+  uint64_t sgraph_sig = 0;
+  uint64_t sgraph_launches = 0;
+  uint64_t s_last_sig = 0;
 };
 
 namespace {
@@ -608,6 +624,10 @@ cg_status cg_ctx_destroy(cg_ctx* ctx) {
   for (auto& e : ctx->join_ev) cudaEventDestroy(e);
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+  if (ctx->sgraph) cudaGraphExecDestroy(ctx->sgraph);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  if (ctx->g_in) cudaEventDestroy(ctx->g_in);
+  if (ctx->g_out) cudaEventDestroy(ctx->g_out);
   if (ctx->bpool) cudaFree(ctx->bpool);
   if (ctx->bhost) cudaFreeHost(ctx->bhost);
   if (ctx->host_ctr) cudaFreeHost(ctx->host_ctr);
@@ -1036,10 +1056,82 @@ cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const in
   cg_status st = ensure_pool(ctx, scene_ws_bytes(plan));
   if (st) return st;
   PackArgs pa{pts, n, d, a, b, ell};
-  ctx->n_marks = 0;
-  mark(ctx, "start", s);
   char* ws = static_cast<char*>(ctx->pool);
   DevCounters* ctr = reinterpret_cast<DevCounters*>(ws);
+  if (!ctx->timing) {
+    // A build repeated with the same arguments, outputs, capacity and tuning
+    // is captured into a CUDA graph the second time and replayed afterwards,
+    // on the context's own stream (ordered after and before the caller's).
+    uint64_t sig = 0x243f6a8885a308d3ull;
+    auto mixin = [&](uint64_t v) { sig = mix64(sig ^ v) + 0x632be59bd9b4e019ull; };
+    mixin(reinterpret_cast<uintptr_t>(pts));
+    mixin(uint64_t(n));
+    mixin(uint64_t(d) * 65536 + uint64_t(ell) * 128 + uint64_t(word_bits));
+    mixin(reinterpret_cast<uintptr_t>(a));
+    mixin(reinterpret_cast<uintptr_t>(b));
+    mixin(reinterpret_cast<uintptr_t>(cells));
+    mixin(uint64_t(cells_cap));
+    mixin(reinterpret_cast<uintptr_t>(edges));
+    mixin(uint64_t(edges_cap));
+    mixin(cap);
+    mixin(reinterpret_cast<uintptr_t>(ctx->pool));
+    mixin(reinterpret_cast<uintptr_t>(host));
+    mixin(uint64_t(plan.tp.strategy) * 4096 + uint64_t(plan.tp.pivots) * 16 +
+          uint64_t(plan.tp.sign_kernel));
+    const char* sk = std::getenv("CG_SIGN_KERNEL");
+    mixin(sk && std::strcmp(sk, "tc") == 0 ? 1u : 0u);
+    const bool replay = ctx->sgraph && ctx->sgraph_sig == sig;
+    if (replay || ctx->s_last_sig == sig) {
+      if (!ctx->gstream) {
+        CG_CUDA(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "graph stream");
+        CG_CUDA(cudaEventCreateWithFlags(&ctx->g_in, cudaEventDisableTiming), "graph event");
+        CG_CUDA(cudaEventCreateWithFlags(&ctx->g_out, cudaEventDisableTiming), "graph event");
+      }
+      CG_CUDA(cudaEventRecord(ctx->g_in, s), "ordering after the caller's stream");
+      CG_CUDA(cudaStreamWaitEvent(ctx->gstream, ctx->g_in, 0), "ordering");
+      if (!replay) {
+        if (ctx->sgraph) {
+          cudaGraphExecDestroy(ctx->sgraph);
+          ctx->sgraph = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        const uint64_t before = cg_launch_count();
+        CG_CUDA(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed),
+                "begin capture");
+        st = enqueue_scene(nullptr, ws + 256, ctr, plan, pa, word_bits, cells, cells_cap, edges,
+                           edges_cap, ctx->gstream);
+        cudaError_t ce = cudaSuccess;
+        if (st == CG_OK)
+          ce = cudaMemcpyAsync(host, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                               ctx->gstream);
+        const cudaError_t ee = cudaStreamEndCapture(ctx->gstream, &graph);
+        if (st) {
+          if (graph) cudaGraphDestroy(graph);
+          return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "capturing the counter read-back");
+        if (ee != cudaSuccess) return cuda_fail(ee, "end capture");
+        ce = cudaGraphInstantiate(&ctx->sgraph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+          ctx->sgraph = nullptr;
+          return cuda_fail(ce, "instantiating the build graph");
+        }
+        ctx->sgraph_sig = sig;
+        ctx->sgraph_launches = cg_launch_count() - before;
+        count_launch(-int(ctx->sgraph_launches));  // captured, not yet run
+      }
+      CG_CUDA(cudaGraphLaunch(ctx->sgraph, ctx->gstream), "replaying the build graph");
+      count_launch(int(ctx->sgraph_launches));
+      CG_CUDA(cudaEventRecord(ctx->g_out, ctx->gstream), "ordering");
+      CG_CUDA(cudaStreamWaitEvent(s, ctx->g_out, 0), "ordering the caller's stream");
+      CG_CUDA(cudaStreamSynchronize(ctx->gstream), "synchronising stream");
+      return check_counters(host);
+    }
+    ctx->s_last_sig = sig;
+  }
+  ctx->n_marks = 0;
+  mark(ctx, "start", s);
   st = enqueue_scene(ctx, ws + 256, ctr, plan, pa, word_bits, cells, cells_cap, edges, edges_cap,
                      s);
   if (st) return st;

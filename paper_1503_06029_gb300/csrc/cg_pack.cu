@@ -19,7 +19,8 @@
 // E 2^-e < 1; the scaling is exact, so |t'| >= 2 proves the sign. |t'| >= 2 is
 // exactly "bit 30 of the float is set", which lets one LOP3 accumulate the
 // certainty test of two results; a thread whose accumulated bit 30 is clear
-// re-evaluates the uncertain bits of that 32-constraint chunk exactly.
+// has the uncertain bits of that 32-constraint chunk re-evaluated exactly, by
+// the whole warp together (lanes over constraints).
 //
 // Bits are collected with a funnel shift of the float sign bit (constraints are
 // visited from the highest to the lowest index of the chunk), which yields the
@@ -59,6 +60,48 @@ __device__ __forceinline__ bool exact_ge(const int32_t* __restrict__ a_row, int6
 #pragma unroll
   for (int k = 0; k < D; ++k) s += static_cast<__int128>(int64_t(a_row[k]) * int64_t(p[k]));
   return s >= 0;
+}
+
+// Settles the uncertain bits of one 32-constraint chunk exactly, for every
+// lane of the warp whose chunk test failed (some |t'| < 2). The warp works on
+// one such lane at a time, lane j taking constraint 32 chunk + j of each of
+// that lane's P points (points p_lane0 + L P + q for lane L): it recomputes
+// the fp32 value, and where |t'| < 2 decides the bit with 128-bit integer
+// arithmetic. w[q] holds, as gathered by the main loop, bit j = 1 when point q
+// does not satisfy constraint j. Must be called by the whole warp.
+template <int D, int P, int kQ>
+__device__ __forceinline__ void settle_uncertain(const PackArgs& pa, const float4* cc, int chunk,
+                                                 int64_t p_lane0, bool uncertain,
+                                                 uint32_t (&w)[P]) {
+  const int lane = threadIdx.x & 31;
+  uint32_t todo = __ballot_sync(0xffffffffu, uncertain);
+  const int t = chunk * 32 + lane;
+  const float* f = reinterpret_cast<const float*>(cc + lane * kQ);
+  while (todo) {
+    const int L = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int64_t pL = p_lane0 + int64_t(L) * P;
+#pragma unroll 1
+    for (int q = 0; q < P; ++q) {
+      if (pL + q >= pa.n) break;
+      int32_t pq[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) pq[k] = __ldg(pa.pts + (pL + q) * D + k);
+      float acc = f[2 * D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc = fmaf(f[2 * k], __int2float_rn(pq[k]), acc);
+      const bool unc = t < pa.ell && fabsf(acc) < 2.0f;
+      bool ge = false;
+      if (unc) ge = exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], pq);
+      const uint32_t um = __ballot_sync(0xffffffffu, unc);
+      const uint32_t gm = __ballot_sync(0xffffffffu, ge);
+      if (lane == L) {
+#pragma unroll
+        for (int qq = 0; qq < P; ++qq)
+          if (qq == q) w[qq] = (w[qq] & ~um) | (~gm & um);
+      }
+    }
+  }
 }
 
 // Per-constraint scaled coefficients, duplicated for f32x2:
@@ -227,24 +270,8 @@ __global__ void __launch_bounds__(kThreads)
           cert &= lo & hi;
         }
       }
-      if (!(cert & 0x40000000u)) {
-        // Some |t'| < 2 in this chunk: settle those bits exactly.
-        for (int q = 0; q < kPts; ++q) {
-          if (p0 + q >= n) continue;
-          for (int j = 0; j < 32; ++j) {
-            const int t = chunk * 32 + j;
-            if (t >= pa.ell) break;
-            const float* f = reinterpret_cast<const float*>(cc + j * kQ);
-            float acc = f[2 * D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) acc = fmaf(f[2 * k], __int2float_rn(pi[q][k]), acc);
-            if (fabsf(acc) < 2.0f) {
-              const bool ge = exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], pi[q]);
-              w[q] = ge ? (w[q] & ~(1u << j)) : (w[q] | (1u << j));
-            }
-          }
-        }
-      }
+      settle_uncertain<D, kPts, kQ>(pa, cc, chunk, p0 - int64_t(lane) * kPts,
+                                     !(cert & 0x40000000u), w);
       const bool last = chunk == n_chunks - 1;
 #pragma unroll
       for (int q = 0; q < kPts; ++q) {
@@ -494,29 +521,7 @@ __global__ void __launch_bounds__(kFThreads)
           }
         }
       }
-      if (!(cert & 0x40000000u)) {
-        // Some |t'| < 2 in this chunk: settle those bits exactly.
-#pragma unroll 1
-        for (int q = 0; q < P; ++q) {
-          if (p0 + q >= n) continue;
-          int32_t pq[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) pq[k] = __ldg(pa.pts + (p0 + q) * D + k);
-#pragma unroll 1
-          for (int j = 0; j < 32; ++j) {
-            const int t = c * 32 + j;
-            if (t >= pa.ell) break;
-            const float* f = reinterpret_cast<const float*>(cc + j * kQ);
-            float acc = f[2 * D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) acc = fmaf(f[2 * k], __int2float_rn(pq[k]), acc);
-            if (fabsf(acc) < 2.0f) {
-              const bool ge = exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], pq);
-              w[q] = ge ? (w[q] & ~(1u << j)) : (w[q] | (1u << j));
-            }
-          }
-        }
-      }
+      settle_uncertain<D, P, kQ>(pa, cc, c, p0 - int64_t(lane) * P, !(cert & 0x40000000u), w);
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         if (c == 0) key[q] = ~w[q];
