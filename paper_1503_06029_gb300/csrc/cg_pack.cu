@@ -69,7 +69,7 @@ __device__ __forceinline__ bool exact_ge(const int32_t* __restrict__ a_row, int6
 // the fp32 value, and where |t'| < 2 decides the bit with 128-bit integer
 // arithmetic. w[q] holds, as gathered by the main loop, bit j = 1 when point q
 // does not satisfy constraint j. Must be called by the whole warp.
-template <int D, int P, int kQ>
+template <int D, int P, int kQ, int R = 2>
 __device__ __forceinline__ void settle_uncertain(const PackArgs& pa, const float4* cc, int chunk,
                                                  int64_t p_lane0, bool uncertain,
                                                  uint32_t (&w)[P]) {
@@ -87,9 +87,9 @@ __device__ __forceinline__ void settle_uncertain(const PackArgs& pa, const float
       int32_t pq[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) pq[k] = __ldg(pa.pts + (pL + q) * D + k);
-      float acc = f[2 * D];
+      float acc = f[R * D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) acc = fmaf(f[2 * k], __int2float_rn(pq[k]), acc);
+      for (int k = 0; k < D; ++k) acc = fmaf(f[R * k], __int2float_rn(pq[k]), acc);
       const bool unc = t < pa.ell && fabsf(acc) < 2.0f;
       bool ge = false;
       if (unc) ge = exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], pq);
@@ -104,20 +104,21 @@ __device__ __forceinline__ void settle_uncertain(const PackArgs& pa, const float
   }
 }
 
-// Per-constraint scaled coefficients, duplicated for f32x2:
-// [a0 a0 a1 a1 ... a_{D-1} a_{D-1} c c] padded to whole float4s.
-template <int D>
+// Per-constraint scaled coefficients, each repeated R times (R = 2 for the
+// f32x2 kernels, 1 for the scalar ones): [a0 .. a0 a1 .. a_{D-1} c .. c]
+// padded to whole float4s.
+template <int D, int R = 2>
 struct Coef {
-  static constexpr int kFloats = 2 * (D + 1);
+  static constexpr int kFloats = R * (D + 1);
   static constexpr int kQuads = (kFloats + 3) / 4;
 };
 
 // Writes constraint t's coefficients for a tile whose |p_k| <= M[k].
-template <int D>
+template <int D, int R = 2>
 __device__ void build_coef(const PackArgs& pa, int t, const uint32_t (&M)[D], float4* dst) {
-  float v[Coef<D>::kQuads * 4];
+  float v[Coef<D, R>::kQuads * 4];
 #pragma unroll
-  for (int q = 0; q < Coef<D>::kQuads * 4; ++q) v[q] = 0.0f;
+  for (int q = 0; q < Coef<D, R>::kQuads * 4; ++q) v[q] = 0.0f;
   float c;
   if (t >= pa.ell) {
     c = -4.0f;  // padding: certain, negative, bit 0
@@ -138,16 +139,16 @@ __device__ void build_coef(const PackArgs& pa, int t, const uint32_t (&M)[D], fl
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const float ak = ldexpf(__int2float_rn(ar[k]), -e);
-        v[2 * k] = ak;
-        v[2 * k + 1] = ak;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[R * k + r] = ak;
       }
       c = ldexpf(-__ll2float_rn(bt), -e);
     }
   }
-  v[2 * D] = c;
-  v[2 * D + 1] = c;
 #pragma unroll
-  for (int q = 0; q < Coef<D>::kQuads; ++q)
+  for (int r = 0; r < R; ++r) v[R * D + r] = c;
+#pragma unroll
+  for (int q = 0; q < Coef<D, R>::kQuads; ++q)
     dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
@@ -391,7 +392,8 @@ struct FastInsert {
 template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 8>
 __global__ void __launch_bounds__(kFThreads)
     pack_fast_kernel(PackArgs pa, Sink sink, int vec_ok) {
-  constexpr int kQ = Coef<D>::kQuads;
+  constexpr int R = F2 ? 2 : 1;  // scalar FMAs read each coefficient once
+  constexpr int kQ = Coef<D, R>::kQuads;
   constexpr int kRows = NCH * 32;
   constexpr int kWarpPts = 32 * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(kFThreads)
     Mb[k] = pow2_ceil(mblk[k]);
     Mp[k] = 0;
   }
-  for (int t = threadIdx.x; t < kRows; t += kFThreads) build_coef<D>(pa, t, Mb, blk + t * kQ);
+  for (int t = threadIdx.x; t < kRows; t += kFThreads) build_coef<D, R>(pa, t, Mb, blk + t * kQ);
   __syncthreads();
   bool priv_ok = false;
 
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(kFThreads)
       if (!fits_priv) {
 #pragma unroll
         for (int k = 0; k < D; ++k) Mp[k] = pow2_ceil(mw[k]);
-        for (int t = lane; t < kRows; t += 32) build_coef<D>(pa, t, Mp, priv + t * kQ);
+        for (int t = lane; t < kRows; t += 32) build_coef<D, R>(pa, t, Mp, priv + t * kQ);
         __syncwarp();
         priv_ok = true;
       }
@@ -507,11 +509,11 @@ __global__ void __launch_bounds__(kFThreads)
         } else {
 #pragma unroll
           for (int h = 0; h < P / 2; ++h) {
-            float a0 = f[2 * D], a1 = f[2 * D];
+            float a0 = f[R * D], a1 = f[R * D];
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-              a0 = fmaf(f[2 * k], Xs[2 * h][k], a0);
-              a1 = fmaf(f[2 * k], Xs[2 * h + 1][k], a1);
+              a0 = fmaf(f[R * k], Xs[2 * h][k], a0);
+              a1 = fmaf(f[R * k], Xs[2 * h + 1][k], a1);
             }
             const uint32_t lo = __float_as_uint(a0);
             const uint32_t hi = __float_as_uint(a1);
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(kFThreads)
           }
         }
       }
-      settle_uncertain<D, P, kQ>(pa, cc, c, p0 - int64_t(lane) * P, !(cert & 0x40000000u), w);
+      settle_uncertain<D, P, kQ, R>(pa, cc, c, p0 - int64_t(lane) * P, !(cert & 0x40000000u), w);
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         if (c == 0) key[q] = ~w[q];
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(kFThreads)
 
 template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 8>
 cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
-  const size_t smem = size_t(1 + kFWarps) * NCH * 32 * Coef<D>::kQuads * sizeof(float4);
+  const size_t smem = size_t(1 + kFWarps) * NCH * 32 * Coef<D, F2 ? 2 : 1>::kQuads * sizeof(float4);
   auto kern = pack_fast_kernel<D, NCH, Sink, P, F2, UJ>;
   int per_sm = 0;
   cudaError_t err =
