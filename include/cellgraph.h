@@ -52,7 +52,10 @@ extern "C" {
 
 typedef int cg_status;
 #define CG_OK 0
-#define CG_ERR_INVALID_ARG 1 /* bad pointer, size, word_bits, strategy, ... */
+#define CG_ERR_INVALID_ARG 1 /* bad pointer, size, word_bits, strategy, unsorted
+                                cells given to cg_neighbors_h1, ... */
+#define CG_ERR_RANGE 2       /* reserved: never returned, every int32 coordinate and
+                                normal and int64 offset is evaluated exactly */
 #define CG_ERR_CAPACITY 3    /* an output array is too small; counts were written */
 #define CG_ERR_OOM 4         /* a library-owned allocation failed */
 #define CG_ERR_CUDA 5        /* a CUDA runtime call or kernel launch failed */
@@ -117,7 +120,8 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
  * Algorithm 4): for every cell i and every bit k with x_i(k) = 0, the vector
  * x_i with bit k set is looked up among the cells; each hit j gives edge (i, j).
  *   cells      [n_cells][W] words, device: sorted ascending and unique (the
- *              output of cg_dedup_cells); unsorted input gives unspecified edges.
+ *              output of cg_dedup_cells); other input is detected on the
+ *              device and gives CG_ERR_INVALID_ARG.
  *   edges      uint32[edges_cap][2], device.
  *   n_edges    host: receives E.
  *   strategy   CG_STRATEGY_* (PIVOT uses h = 4 pivots, or the value of the
@@ -194,6 +198,20 @@ cg_status cg_build(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int3
                    const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
                    int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
                    void* stream);
+
+/* Same as cg_build, but nothing waits and nothing is read back: the build is
+ * enqueued on `stream`, followed by a kernel that writes counts[0] = U,
+ * counts[1] = E and counts[2] = a status (CG_OK; CG_ERR_CAPACITY when U >
+ * cells_cap or E > edges_cap, with nothing written past either cap;
+ * CG_ERR_INTERNAL when the dedup table overflowed its first size guess -- run
+ * cg_build once to grow it -- or a device check failed; CG_ERR_TIMEOUT).
+ * counts: device int64[3]. The enqueued work can be captured into a CUDA
+ * graph by the caller; a call that has to grow the context's pool allocates,
+ * so make the first call with a given size outside stream capture. Calls on
+ * one context must be ordered on one stream (they share its pool). */
+cg_status cg_build_dev(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                       const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                       uint32_t* edges, int64_t edges_cap, int64_t* counts, void* stream);
 
 /* Same as cg_build with every array in HOST memory (pinned or pageable): the
  * call copies the inputs to the context's device pool, builds, and copies the

@@ -41,7 +41,7 @@ EXPORTS = [
     "cg_server_create", "cg_server_submit", "cg_server_poll", "cg_server_wait",
     "cg_server_result_get", "cg_server_copy", "cg_server_release", "cg_server_get_stats",
     "cg_server_inject_alloc_failures", "cg_server_destroy", "cg_tune_bucket", "cg_ctx_tune_get",
-    "cg_ctx_tune_set", "cg_ctx_autotune", "cg_server_use_tuning",
+    "cg_ctx_tune_set", "cg_ctx_autotune", "cg_server_use_tuning", "cg_build_dev",
 ]
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH):
         lib.cg_build.argtypes = build_args
         lib.cg_build_host.argtypes = build_args
         lib.cg_build_batch.argtypes = [P, P, I, P, P]
+        lib.cg_build_dev.argtypes = [P, P, I64, I, P, P, I, I, P, I64, P, I64, P, P]
         lib.cg_ctx_set_timing.argtypes = [P, I]
         lib.cg_ctx_stage_times.argtypes = [P, P, P, I, ctypes.POINTER(ctypes.c_int), PI64]
         lib.cg_server_create.argtypes = [I, S, I, ctypes.POINTER(P)]
@@ -343,6 +344,20 @@ class Context:
             _check(rc)
             self._caps[key] = (max(ccap, nc.value), max(ecap, ne.value))
             return cells[: nc.value], edges[: ne.value]
+
+    def build_dev(self, pts, a, b, cells, edges, counts, word_bits: int = 64, stream=None):
+        """Enqueues one build without waiting (cg_build_dev): results go to the
+        given device buffers, and counts (int64 [3] device tensor) receives U,
+        E and a status once the stream reaches it. Capturable in a CUDA graph
+        after a first call of the same size."""
+        torch = _torch()
+        n, d = pts.shape
+        ell = a.shape[0]
+        _check(self._lib.cg_build_dev(
+            self._h, _dev(pts, torch.int32, "pts"), n, d, _dev(a, torch.int32, "a"),
+            _dev(b, torch.int64, "b"), ell, word_bits, _dev(cells, word_dtype(word_bits), "cells"),
+            cells.shape[0], _dev(edges, torch.int32, "edges"), edges.shape[0],
+            _dev(counts, torch.int64, "counts"), _stream_ptr(stream)))
 
     def build_batch(self, scenes, stream=None):
         """Cells and edges of many independent scenes in one batched call.

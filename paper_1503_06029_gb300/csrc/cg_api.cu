@@ -14,6 +14,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/cellgraph.h"
 #include "cg_internal.cuh"
 #include "cg_plan.h"
@@ -88,6 +90,13 @@ using namespace cg;
 namespace {
 
 thread_local std::string t_err;
+
+// NVTX range around a public call (visible in profilers that record NVTX;
+// a few nanoseconds otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 cg_status fail(cg_status st, const std::string& msg) {
   t_err = msg;
@@ -291,6 +300,8 @@ cg_status read_counters(DevCounters* dev, DevCounters* host, cudaStream_t s) {
   CG_CUDA(cudaMemcpyAsync(host, dev, sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
           "reading counters");
   CG_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+  if (host->error & kErrUnsorted)
+    return fail(CG_ERR_INVALID_ARG, "cells are not sorted ascending and unique");
   if (host->error & kErrTimeout)
     return fail(CG_ERR_TIMEOUT, "a bounded device-side wait ran out");
   if (host->error)
@@ -668,6 +679,7 @@ cg_status cg_ctx_pool_bytes(const cg_ctx* ctx, size_t* bytes) {
 
 cg_status cg_pack_signs(const int32_t* pts, int64_t n, int d, const int32_t* a, const int64_t* b,
                         int ell, int word_bits, void* keys, void* stream) {
+  NvtxRange nvtx("cg_pack_signs");
   std::string why;
   if (!check_common(n, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
   if (d < 1 || d > 4) return fail(CG_ERR_INVALID_ARG, "d must satisfy 1 <= d <= 4");
@@ -682,6 +694,7 @@ cg_status cg_pack_signs(const int32_t* pts, int64_t n, int d, const int32_t* a, 
 cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, void* cells,
                          int64_t cells_cap, int64_t* n_cells, uint32_t* point_cell, void* ws,
                          size_t* ws_bytes, void* stream) {
+  NvtxRange nvtx("cg_dedup_cells");
   std::string why;
   if (!check_common(n, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
   if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
@@ -748,6 +761,7 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
 cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_bits,
                           uint32_t* edges, int64_t edges_cap, int64_t* n_edges, int strategy,
                           void* ws, size_t* ws_bytes, void* stream) {
+  NvtxRange nvtx("cg_neighbors_h1");
   std::string why;
   if (!check_common(n_cells, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
   if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_TREE)
@@ -783,6 +797,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
                                ne_status_words(un), w.ctr, s),
             "clearing table");
     CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
+    CG_CUDA(launch_check_sorted(w.cells, 1, w.ctr, un, s), "checking the cell order");
     cg_status st;
     if (pivot) {
       st = pivot_steps(w.cells, 1, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un,
@@ -801,6 +816,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
     CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s), "loading cells");
     const int w64 = (ell + 63) / 64;
+    CG_CUDA(launch_check_sorted(w.cells, w64, w.ctr, un, s), "checking the cell order");
     cg_status st;
     if (pivot)
       st = pivot_steps(w.cells, w64, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un, edges,
@@ -1208,6 +1224,7 @@ cg_status cg_build(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int3
                    const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
                    int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
                    void* stream) {
+  NvtxRange nvtx("cg_build");
   std::string why;
   if (!check_build_args(ctx, pts, n, d, a, b, ell, word_bits, cells, cells_cap, n_cells, edges,
                         edges_cap, n_edges, &why))
@@ -1217,10 +1234,41 @@ cg_status cg_build(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int3
                        edges_cap, n_edges, static_cast<cudaStream_t>(stream));
 }
 
+cg_status cg_build_dev(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
+                       const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
+                       uint32_t* edges, int64_t edges_cap, int64_t* counts, void* stream) {
+  NvtxRange nvtx("cg_build_dev");
+  std::string why;
+  int64_t dummy_c = 0, dummy_e = 0;
+  if (!check_build_args(ctx, pts, n, d, a, b, ell, word_bits, cells, cells_cap, &dummy_c, edges,
+                        edges_cap, &dummy_e, &why))
+    return fail(CG_ERR_INVALID_ARG, why);
+  if (!counts) return fail(CG_ERR_INVALID_ARG, "counts is NULL");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto key = std::make_tuple(n, ell, d);
+  size_t cap = initial_cap(n, d, ell);
+  auto it = ctx->cap_hint.find(key);
+  if (it != ctx->cap_hint.end()) cap = std::max(cap, it->second);
+  cap = std::min(cap, full_cap(n));
+  const ScenePlan plan = plan_scene(n, ell, cap, ctx->tune[cg_tune_bucket(ell)]);
+  cg_status st = ensure_pool(ctx, scene_ws_bytes(plan));
+  if (st) return st;
+  PackArgs pa{pts, n, d, a, b, ell};
+  char* ws = static_cast<char*>(ctx->pool);
+  DevCounters* ctr = reinterpret_cast<DevCounters*>(ws);
+  st = enqueue_scene(nullptr, ws + 256, ctr, plan, pa, word_bits, cells, cells_cap, edges,
+                     edges_cap, s);
+  if (st) return st;
+  CG_CUDA(launch_publish_counts(ctr, counts, cells_cap, edges_cap, s), "publishing counts");
+  return CG_OK;
+}
+
 cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
                         const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
                         int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
                         void* stream) {
+  NvtxRange nvtx("cg_build_host");
   std::string why;
   if (!check_build_args(ctx, pts, n, d, a, b, ell, word_bits, cells, cells_cap, n_cells, edges,
                         edges_cap, n_edges, &why))
@@ -1338,6 +1386,7 @@ struct BatchScene {
 
 extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_scenes,
                                     cg_batch_out* out, void* stream) {
+  NvtxRange nvtx("cg_build_batch");
   if (!ctx || n_scenes < 0 || (n_scenes > 0 && !scenes) || !out)
     return fail(CG_ERR_INVALID_ARG, "NULL argument or negative scene count");
   if (n_scenes > 0 && (!out->n_cells || !out->n_edges))

@@ -11,6 +11,7 @@
 //
 // Every kernel after the dedup step reads U from device memory and returns
 // early if the dedup step overflowed its capacity.
+#include "../../include/cellgraph.h"
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -1202,6 +1203,48 @@ cudaError_t launch_emit_tree(const uint64_t* cells, int w64, int ell, const Tree
   if (e != cudaSuccess) return e;
   k<<<grid_for(max_n, kThreads / 32), kThreads, smem, s>>>(
       cells, w64, ell, TreeWide{cells, nodes, w64, ell}, ctr, masks, offsets, edges, edges_cap);
+  return finish(0);
+}
+
+namespace {
+
+__global__ void check_sorted(const uint64_t* __restrict__ cells, int w, DevCounters* ctr,
+                             uint32_t max_n) {
+  const uint32_t u = min(ctr->n_unique, max_n);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x + 1; i < u;
+       i += gridDim.x * blockDim.x) {
+    const uint64_t* x = cells + uint64_t(i - 1) * w;
+    const uint64_t* y = cells + uint64_t(i) * w;
+    int q = w - 1;
+    while (q > 0 && x[q] == y[q]) --q;
+    if (!(x[q] < y[q])) atomicOr(&ctr->error, kErrUnsorted);
+  }
+}
+
+__global__ void publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
+                               int64_t edges_cap) {
+  int64_t status = CG_OK;
+  if (ctr->error & kErrTimeout) status = CG_ERR_TIMEOUT;
+  else if (ctr->error || ctr->overflow) status = CG_ERR_INTERNAL;
+  else if (int64_t(ctr->n_unique) > cells_cap || int64_t(ctr->n_edges) > edges_cap)
+    status = CG_ERR_CAPACITY;
+  out[0] = int64_t(ctr->n_unique);
+  out[1] = int64_t(ctr->n_edges);
+  out[2] = status;
+}
+
+}  // namespace
+
+cudaError_t launch_check_sorted(const uint64_t* cells, int w64, DevCounters* ctr, size_t max_n,
+                                cudaStream_t s) {
+  if (max_n < 2) return cudaSuccess;
+  check_sorted<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(cells, w64, ctr, uint32_t(max_n));
+  return finish(0);
+}
+
+cudaError_t launch_publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
+                                  int64_t edges_cap, cudaStream_t s) {
+  publish_counts<<<1, 1, 0, s>>>(ctr, out, cells_cap, edges_cap);
   return finish(0);
 }
 

@@ -31,7 +31,8 @@ struct DevCounters {
 };
 
 // Bits of DevCounters::error.
-constexpr unsigned kErrTimeout = 64u;  // a bounded device-side wait ran out
+constexpr unsigned kErrTimeout = 64u;    // a bounded device-side wait ran out
+constexpr unsigned kErrUnsorted = 128u;  // given cells are not ascending and unique
 static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
 
 // ---------------------------------------------------------------------------
@@ -246,6 +247,15 @@ cudaError_t launch_write_cells(const uint64_t* cells, int ell, int word_bits, vo
 // Load caller-layout cells into internal u64 rows; sets ctr->n_unique = n.
 cudaError_t launch_load_cells(const void* cells, int64_t n, int word_bits, int ell,
                               uint64_t* out, DevCounters* ctr, cudaStream_t s);
+
+// Sets kErrUnsorted unless the U = ctr->n_unique rows of w64 words are
+// strictly ascending in value order.
+cudaError_t launch_check_sorted(const uint64_t* cells, int w64, DevCounters* ctr, size_t max_n,
+                                cudaStream_t s);
+// out[0] = U, out[1] = E, out[2] = status (CG_OK, CG_ERR_CAPACITY when a count
+// exceeds its cap, CG_ERR_TIMEOUT / CG_ERR_INTERNAL on device-side failures).
+cudaError_t launch_publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
+                                  int64_t edges_cap, cudaStream_t s);
 
 // Clears a build's table (kEmpty), the look-back status words and the counters.
 // (A second table, table2/cap2, may be cleared in the same launch.)

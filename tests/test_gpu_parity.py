@@ -628,3 +628,63 @@ def test_autotune_keeps_results(dev, tmp_path):
                 assert np.array_equal(edges, want_e)
     finally:
         c2.close()
+
+
+# ---------------------------- asynchronous build ---------------------------
+
+def test_build_dev_matches_and_captures(ctx, dev):
+    sc = inputs.planes_3d(n=300_000, ell=64, seed=41)
+    args = (T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev))
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+    cells = torch.full((len(want_c) + 5, 1), -1, dtype=torch.int64, device=dev)
+    edges = torch.full((len(want_e) + 5, 2), -1, dtype=torch.int32, device=dev)
+    counts = torch.zeros(3, dtype=torch.int64, device=dev)
+    ctx.build_dev(*args, cells, edges, counts)
+    torch.cuda.synchronize()
+    u, e, st = counts.tolist()
+    assert st == 0 and u == len(want_c) and e == len(want_e)
+    assert np.array_equal(words_np(cells[:u], 64), want_c)
+    assert np.array_equal(edges_np(edges[:e]), want_e)
+    # captured by the caller into a CUDA graph and replayed
+    cells.fill_(-1)
+    edges.fill_(-1)
+    counts.zero_()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            ctx.build_dev(*args, cells, edges, counts)
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert counts.tolist() == [u, e, 0]
+    assert np.array_equal(words_np(cells[:u], 64), want_c)
+    assert np.array_equal(edges_np(edges[:e]), want_e)
+
+
+def test_build_dev_capacity_status(ctx, dev):
+    sc = inputs.planes_3d(n=50_000, ell=40, seed=42)
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+    cells = torch.full((30, 1), -7, dtype=torch.int64, device=dev)
+    edges = torch.full((20, 2), -7, dtype=torch.int32, device=dev)
+    counts = torch.zeros(3, dtype=torch.int64, device=dev)
+    # capacities 3 and 2: views of the first rows; nothing may land past them
+    ctx.build_dev(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), cells[:3], edges[:2], counts)
+    torch.cuda.synchronize()
+    assert counts.tolist() == [len(want_c), len(want_e), cellgraph.ERR_CAPACITY]
+    assert (cells[3:] == -7).all() and (edges[2:] == -7).all()
+
+
+def test_neighbors_rejects_unsorted_cells(dev):
+    cells = np.array([[5], [3], [9]], dtype=np.uint64)
+    with pytest.raises(cellgraph.CellGraphError) as ei:
+        cellgraph.neighbors_h1(words_dev(cells, 64, dev), 8, 64)
+    assert ei.value.status == cellgraph.ERR_INVALID_ARG
+    dup = np.array([[1], [2], [2]], dtype=np.uint64)
+    with pytest.raises(cellgraph.CellGraphError):
+        cellgraph.neighbors_h1(words_dev(dup, 64, dev), 8, 64, strategy="sorted")
+    wide = np.array([[0, 2], [5, 1]], dtype=np.uint64)  # row 1 < row 0 (top word)
+    with pytest.raises(cellgraph.CellGraphError):
+        cellgraph.neighbors_h1(words_dev(wide, 64, dev), 100, 64)
