@@ -215,7 +215,11 @@ cg_status cg_build_dev(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const 
 
 /* Same as cg_build with every array in HOST memory (pinned or pageable): the
  * call copies the inputs to the context's device pool, builds, and copies the
- * cells and edges back. Blocks until the copies are done. */
+ * cells and edges back. Blocks until the copies are done. Points in pinned
+ * host memory are read by the sign kernel in place, over the host link,
+ * overlapping the transfer with the arithmetic. The environment variable
+ * CG_HOST_INPUT=pieces copies them in pieces on a second stream instead (each
+ * piece processed as it arrives), CG_HOST_INPUT=copy in one piece first. */
 cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
                         const int64_t* b, int ell, int word_bits, void* cells,
                         int64_t cells_cap, int64_t* n_cells, uint32_t* edges,

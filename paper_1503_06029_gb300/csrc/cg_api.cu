@@ -516,6 +516,10 @@ struct cg_ctx {
   uint64_t bgraph_sig = 0;
   uint64_t bgraph_launches = 0;  // kernels inside the graph
   uint64_t last_sig = 0;
+  // Host-input pipeline: copy stream and one event per piece of points.
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t c_start = nullptr;
+  std::vector<cudaEvent_t> c_ready;
   // Captured single build (same idea, for repeated identical cg_build calls).
   cudaStream_t gstream = nullptr;
   cudaEvent_t g_in = nullptr, g_out = nullptr;
@@ -636,6 +640,9 @@ cg_status cg_ctx_destroy(cg_ctx* ctx) {
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
   if (ctx->sgraph) cudaGraphExecDestroy(ctx->sgraph);
+  if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
+  if (ctx->c_start) cudaEventDestroy(ctx->c_start);
+  for (auto& e : ctx->c_ready) cudaEventDestroy(e);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->g_in) cudaEventDestroy(ctx->g_in);
   if (ctx->g_out) cudaEventDestroy(ctx->g_out);
@@ -948,7 +955,8 @@ size_t scene_ws_bytes(const ScenePlan& p) {
 // U <= cells_cap), edges to `edges` (up to edges_cap).
 cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan& plan,
                         const PackArgs& pa, int word_bits, void* cells, int64_t cells_cap,
-                        uint32_t* edges, int64_t edges_cap, cudaStream_t s) {
+                        uint32_t* edges, int64_t edges_cap, cudaStream_t s,
+                        const PackPieces* pieces) {
   Carve c{ws};
   SmallWs w{};
   WideWs ww{};
@@ -970,11 +978,24 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     if (n > 0) {
       // The tuned sign kernel; the environment variable CG_SIGN_KERNEL=tc
       // forces the tensor-core one (both exact).
+      // Points in pieces always take the fp32 kernel (the tensor-core one keeps
+      // one spill list per build).
       const char* sk = std::getenv("CG_SIGN_KERNEL");
-      const bool tc = plan.tp.sign_kernel == 1 || (sk && std::strcmp(sk, "tc") == 0);
-      CG_CUDA(tc ? launch_pack_tc_insert(pa, w.table(true), w.spill, s)
-                 : launch_pack_insert(pa, w.table(true), s),
-              "sign vectors + dedup");
+      const bool tc = !pieces && (plan.tp.sign_kernel == 1 || (sk && std::strcmp(sk, "tc") == 0));
+      const int np = pieces ? pieces->count : 1;
+      for (int k = 0; k < np; ++k) {
+        PackArgs pk = pa;
+        if (pieces) {
+          const int64_t lo = k * pieces->per;
+          if (lo >= n) break;
+          pk.pts = pa.pts + lo * pa.d;
+          pk.n = std::min<int64_t>(pieces->per, n - lo);
+          CG_CUDA(cudaStreamWaitEvent(s, pieces->ready[k], 0), "waiting for points");
+        }
+        CG_CUDA(tc ? launch_pack_tc_insert(pk, w.table(true), w.spill, s)
+                   : launch_pack_insert(pk, w.table(true), s),
+                "sign vectors + dedup");
+      }
     }
     mark(ctx, "pack_dedup", s);
     st = dedup_small_tail(w, ell, word_bits, cells, cells_cap, s);
@@ -989,6 +1010,9 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     return CG_OK;
   }
   const int w64 = (ell + 63) / 64;
+  if (pieces)
+    for (int k = 0; k < pieces->count; ++k)
+      CG_CUDA(cudaStreamWaitEvent(s, pieces->ready[k], 0), "waiting for points");
   if (!plan.single || own) {
     CG_CUDA(launch_zero_counters(ww.ctr, s), "counters");
     if (n > 0) CG_CUDA(launch_pack_store(pa, 64, ww.keys64, s), "sign vectors");
@@ -1067,14 +1091,14 @@ namespace {
 cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
                      const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
                      uint32_t* edges, int64_t edges_cap, size_t cap, cudaStream_t s,
-                     DevCounters* host) {
+                     DevCounters* host, const PackPieces* pieces = nullptr) {
   const ScenePlan plan = plan_scene(n, ell, cap, ctx->tune[cg_tune_bucket(ell)]);
   cg_status st = ensure_pool(ctx, scene_ws_bytes(plan));
   if (st) return st;
   PackArgs pa{pts, n, d, a, b, ell};
   char* ws = static_cast<char*>(ctx->pool);
   DevCounters* ctr = reinterpret_cast<DevCounters*>(ws);
-  if (!ctx->timing) {
+  if (!ctx->timing && !pieces) {
     // A build repeated with the same arguments, outputs, capacity and tuning
     // is captured into a CUDA graph the second time and replayed afterwards,
     // on the context's own stream (ordered after and before the caller's).
@@ -1149,7 +1173,7 @@ cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const in
   ctx->n_marks = 0;
   mark(ctx, "start", s);
   st = enqueue_scene(ctx, ws + 256, ctr, plan, pa, word_bits, cells, cells_cap, edges, edges_cap,
-                     s);
+                     s, pieces);
   if (st) return st;
   st = read_counters(ctr, host, s);
   if (st == CG_OK) accumulate_marks(ctx);
@@ -1159,7 +1183,7 @@ cg_status build_once(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const in
 cg_status build_checked(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const int32_t* a,
                         const int64_t* b, int ell, int word_bits, void* cells, int64_t cells_cap,
                         int64_t* n_cells, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
-                        cudaStream_t s) {
+                        cudaStream_t s, const PackPieces* pieces = nullptr) {
   const size_t full = full_cap(n);
   const auto key = std::make_tuple(n, ell, d);
   size_t cap = initial_cap(n, d, ell);
@@ -1169,7 +1193,7 @@ cg_status build_checked(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const
   for (;;) {
     DevCounters* host = ctx->host_ctr;
     cg_status st = build_once(ctx, pts, n, d, a, b, ell, word_bits, cells, cells_cap, edges,
-                              edges_cap, cap, s, host);
+                              edges_cap, cap, s, host, pieces);
     if (st) return st;
     if (host->overflow) {
       if (cap >= full) return fail(CG_ERR_INTERNAL, "table overflow at full capacity");
@@ -1294,16 +1318,68 @@ cg_status cg_build_host(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const
   int64_t* db = c.take<int64_t>(size_t(ell));
   void* dcells = c.take_bytes(cell_bytes);
   uint32_t* dedges = static_cast<uint32_t*>(c.take_bytes(edge_bytes));
-  if (n > 0)
-    CG_CUDA(cudaMemcpyAsync(dpts, pts, size_t(n) * d * sizeof(int32_t), cudaMemcpyHostToDevice,
-                            s),
-            "copying points");
+  // The small arrays first: host-to-device copies share one copy engine in
+  // submission order, so these must not queue behind the points.
   CG_CUDA(cudaMemcpyAsync(da, a, size_t(ell) * d * sizeof(int32_t), cudaMemcpyHostToDevice, s),
           "copying normals");
   CG_CUDA(cudaMemcpyAsync(db, b, size_t(ell) * sizeof(int64_t), cudaMemcpyHostToDevice, s),
           "copying offsets");
-  st = build_checked(ctx, dpts, n, d, da, db, ell, word_bits, dcells, cells_cap, n_cells, dedges,
-                     edges_cap, n_edges, s);
+  // Points in pinned (page-locked, mapped) host memory are read by the sign
+  // kernel in place, over the host link (NVLink-C2C on GB300, ~210 GB/s
+  // measured either way), so the transfer and the arithmetic overlap; other
+  // host memory is copied first. CG_HOST_INPUT=pieces instead copies pinned
+  // points in kPieces pieces on the context's copy stream, each piece's sign +
+  // dedup launch starting when it has arrived; CG_HOST_INPUT=copy copies them
+  // in one piece first.
+  constexpr int kPieces = 8;
+  const char* hi = std::getenv("CG_HOST_INPUT");
+  const bool force_copy = hi && std::strcmp(hi, "copy") == 0;
+  const bool want_pieces = hi && std::strcmp(hi, "pieces") == 0;
+  const bool direct = !force_copy && !want_pieces;
+  const int32_t* src_pts = nullptr;
+  PackPieces pieces{0, 0, nullptr};
+  if (n > 0 && direct) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, pts) == cudaSuccess) {
+      if (at.type == cudaMemoryTypeHost && at.devicePointer)
+        src_pts = static_cast<const int32_t*>(at.devicePointer);
+    } else {
+      cudaGetLastError();
+    }
+  }
+  const bool piecewise = want_pieces && n >= int64_t(kPieces) * 65536;
+  if (piecewise) {
+    if (!ctx->cstream) {
+      CG_CUDA(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking), "copy stream");
+      CG_CUDA(cudaEventCreateWithFlags(&ctx->c_start, cudaEventDisableTiming), "copy event");
+      ctx->c_ready.resize(kPieces);
+      for (auto& e : ctx->c_ready)
+        CG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "copy event");
+    }
+    // Whole warp tiles (128 points) per piece.
+    const int64_t per = ((n + kPieces - 1) / kPieces + 127) / 128 * 128;
+    CG_CUDA(cudaEventRecord(ctx->c_start, s), "ordering the copies");
+    CG_CUDA(cudaStreamWaitEvent(ctx->cstream, ctx->c_start, 0), "ordering the copies");
+    for (int k = 0; k < kPieces; ++k) {
+      const int64_t lo = k * per;
+      if (lo < n) {
+        const int64_t cnt = std::min<int64_t>(per, n - lo);
+        CG_CUDA(cudaMemcpyAsync(dpts + lo * d, pts + lo * d, size_t(cnt) * d * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, ctx->cstream),
+                "copying points");
+      }
+      CG_CUDA(cudaEventRecord(ctx->c_ready[size_t(k)], ctx->cstream), "copy event");
+    }
+    pieces = PackPieces{kPieces, per, ctx->c_ready.data()};
+    src_pts = dpts;
+  } else if (n > 0 && !src_pts) {
+    CG_CUDA(cudaMemcpyAsync(dpts, pts, size_t(n) * d * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            s),
+            "copying points");
+    src_pts = dpts;
+  }
+  st = build_checked(ctx, src_pts, n, d, da, db, ell, word_bits, dcells, cells_cap, n_cells,
+                     dedges, edges_cap, n_edges, s, piecewise ? &pieces : nullptr);
   if (st != CG_OK && st != CG_ERR_CAPACITY) return st;
   const size_t u = size_t(std::min<int64_t>(*n_cells, cells_cap));
   const size_t e = size_t(std::min<int64_t>(*n_edges, edges_cap));

@@ -37,12 +37,23 @@ size_t scene_ws_bytes(const ScenePlan& p);
 size_t initial_cap(int64_t n, int d, int ell);
 size_t full_cap(int64_t n);
 
+// Points that arrive in pieces: piece k (points [k * per, min(n, (k + 1) *
+// per))) may be read once `ready[k]` has completed. The sign + dedup step of
+// vectors of l <= 64 bits then runs one launch per piece into the same
+// table; other steps wait for all pieces.
+struct PackPieces {
+  int count;
+  int64_t per;
+  const cudaEvent_t* ready;
+};
+
 // Enqueues one scene's build into workspace `ws` with counters at `ctr`;
 // nothing is read back. Cells go to `cells` (word_bits words, when
 // U <= cells_cap), edges to `edges` (up to edges_cap). ctx (nullable) only
 // receives stage-timing marks.
 cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan& plan,
                         const PackArgs& pa, int word_bits, void* cells, int64_t cells_cap,
-                        uint32_t* edges, int64_t edges_cap, cudaStream_t s);
+                        uint32_t* edges, int64_t edges_cap, cudaStream_t s,
+                        const PackPieces* pieces = nullptr);
 
 }  // namespace cg

@@ -402,6 +402,23 @@ def test_build_capacity_contract(ctx, dev):
     assert (cells[5:] == -7).all() and (edges[8:] == -7).all()
 
 
+@pytest.mark.parametrize("mode", ["direct", "pieces", "copy"])
+def test_build_host_pinned_points(ctx, dev, mode, monkeypatch):
+    """Points in pinned host memory: read in place by the sign kernel
+    (default), copied in pieces overlapping it (CG_HOST_INPUT=pieces) or
+    copied first (CG_HOST_INPUT=copy); same output every way, including a
+    ragged last piece."""
+    if mode != "direct":
+        monkeypatch.setenv("CG_HOST_INPUT", mode)
+    sc = inputs.planes_3d(n=1_000_003, ell=64, seed=43)
+    pts = torch.from_numpy(sc.pts).pin_memory().numpy()
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+    for _ in range(3):  # eager, captured, replayed
+        cells, edges = ctx.build_host(pts, sc.a, sc.b, 64)
+        assert np.array_equal(cells.reshape(want_c.shape), want_c)
+        assert np.array_equal(edges, want_e)
+
+
 def test_build_host_matches_oracle(ctx, dev):
     for sc, wb in [(inputs.lines_2d(), 32), (inputs.planes_3d(n=123_457, ell=64, seed=6), 64)]:
         cells, edges = ctx.build_host(sc.pts, sc.a, sc.b, wb)

@@ -219,3 +219,17 @@ def test_create_without_a_device_is_refused():
     assert lib.cg_server_create(0, 1 << 30, 4, ctypes.byref(h)) != 0
     assert lib.cg_server_create(0, 1 << 30, 0, ctypes.byref(h)) == cellgraph.ERR_INVALID_ARG
     assert lib.cg_server_destroy(None) == 0
+
+
+@pytest.mark.gpu
+def test_pinned_host_inputs(dev, wanted):
+    """Requests whose host arrays are pinned (asynchronous copies into the
+    work block) give the same results."""
+    scenes = _scenes(8, 80_000, seed=28)
+    pin = lambda x: torch.from_numpy(x).pin_memory().numpy()
+    pinned = [(pin(s.pts), pin(s.a), pin(s.b)) for s in scenes]
+    with cellgraph.Server(0, hbm_budget_bytes=2 << 30, max_inflight=4) as srv:
+        ts = [srv.submit(*p) for p in pinned]
+        for i, (t, sc) in enumerate(zip(ts, scenes)):
+            assert srv.wait(t, 60.0)
+            _check(srv, t, sc, wanted(("p", i), sc))
