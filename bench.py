@@ -239,7 +239,7 @@ def batch_compare(ctx, dev, steps: int):
     torch.cuda.synchronize()
     t0.record(stream)
     for _ in range(steps):
-        ctx.build_batch(scenes)
+        ctx.build_batch(scenes, as_views=False)
     t1.record(stream)
     torch.cuda.synchronize()
     batch_ms = t0.elapsed_time(t1) / steps

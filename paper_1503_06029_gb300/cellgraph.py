@@ -359,32 +359,45 @@ class Context:
             cells.shape[0], _dev(edges, torch.int32, "edges"), edges.shape[0],
             _dev(counts, torch.int64, "counts"), _stream_ptr(stream)))
 
-    def build_batch(self, scenes, stream=None):
+    def build_batch(self, scenes, stream=None, as_views: bool = True):
         """Cells and edges of many independent scenes in one batched call.
         ``scenes``: sequence of (pts, a, b) CUDA tensors. Returns a list of
         (cells int64 [U, W], edges int32 [E, 2]) views, W = ceil(l/64), cell
         numbers scene-local. The views share output buffers that the context
         reuses for the next batch of the same scenes (which then replays a
-        captured CUDA graph): copy results that must outlive that call."""
+        captured CUDA graph): copy results that must outlive that call.
+        With ``as_views=False`` returns (cells, edges, cells_offset,
+        edges_offset) instead: the whole output buffers and the per-scene
+        offsets (words / edges), without building per-scene views."""
         torch = _torch()
         S = len(scenes)
         if S == 0:
             return []
-        arr = (CgScene * S)()
-        dev = None
-        words_total = edges_total = 0
-        ws = []
-        for i, (pts, a, b) in enumerate(scenes):
-            n, d = pts.shape
-            ell = a.shape[0]
-            arr[i] = CgScene(_dev(pts, torch.int32, "pts").value, n, d,
-                             _dev(a, torch.int32, "a").value, _dev(b, torch.int64, "b").value, ell)
-            dev = pts.device
-            u = arrangement_cells_bound(n, d, ell)
-            ws.append(words(ell, 64))
-            words_total += u * ws[-1]
-            edges_total += 4 * u
-        key = ("batch", tuple((int(x.n), int(x.d), int(x.ell)) for x in arr))
+        # The scene descriptors of the last batch are reused when the same
+        # tensors come again (the cache holds them, so they stay alive).
+        ids = tuple(id(t) for sc in scenes for t in sc)
+        cached = getattr(self, "_batch_desc", None)
+        if cached is not None and cached[0] == ids:
+            _, arr, dev, words_total, edges_total, ws, key, _keep = cached
+        else:
+            arr = (CgScene * S)()
+            dev = None
+            words_total = edges_total = 0
+            ws = []
+            for i, (pts, a, b) in enumerate(scenes):
+                n, d = pts.shape
+                ell = a.shape[0]
+                arr[i] = CgScene(_dev(pts, torch.int32, "pts").value, n, d,
+                                 _dev(a, torch.int32, "a").value, _dev(b, torch.int64, "b").value,
+                                 ell)
+                dev = pts.device
+                u = arrangement_cells_bound(n, d, ell)
+                ws.append(words(ell, 64))
+                words_total += u * ws[-1]
+                edges_total += 4 * u
+            key = ("batch", tuple((int(x.n), int(x.d), int(x.ell)) for x in arr))
+            self._batch_desc = (ids, arr, dev, words_total, edges_total, ws, key,
+                                [t for sc in scenes for t in sc])
         ccap, ecap = self._caps.get(key, (max(1, words_total), max(1, edges_total)))
         n_cells = np.zeros(S, dtype=np.int64)
         n_edges = np.zeros(S, dtype=np.int64)
@@ -409,6 +422,8 @@ class Context:
                 continue
             _check(rc)
             self._caps[key] = (max(ccap, int(coff[S])), max(ecap, int(eoff[S])))
+            if not as_views:
+                return cells, edges, coff.copy(), eoff.copy()
             res = []
             for i in range(S):
                 c = cells[coff[i]: coff[i + 1]].view(-1, ws[i])

@@ -480,6 +480,13 @@ struct DeviceGuard {
 
 // ------------------------------- context ---------------------------------
 
+// Per-scene capacities of a captured batch (for checking its counters when
+// the graph is replayed without replanning).
+struct BatchPlanCopy {
+  size_t cap;
+  size_t ecap;
+};
+
 struct cg_ctx {
   int device = 0;
   void* pool = nullptr;
@@ -516,6 +523,11 @@ struct cg_ctx {
   uint64_t bgraph_sig = 0;
   uint64_t bgraph_launches = 0;  // kernels inside the graph
   uint64_t last_sig = 0;
+  // Replay without replanning: the quick signature of the batch the graph was
+  // captured for (scenes, outputs, tuning, size hints) and its plan.
+  uint64_t bgraph_quick = 0;
+  std::vector<BatchPlanCopy> bplan;
+  uint64_t hint_version = 0;  // bumped whenever a size hint changes
   // Host-input pipeline: copy stream and one event per piece of points.
   cudaStream_t cstream = nullptr;
   cudaEvent_t c_start = nullptr;
@@ -953,10 +965,39 @@ size_t scene_ws_bytes(const ScenePlan& p) {
 // Enqueues one scene's build (steps 1-4) into workspace `ws` with counters at
 // `ctr`; nothing is read back. Cells go to `cells` (word_bits words, when
 // U <= cells_cap), edges to `edges` (up to edges_cap).
+bool scene_batch_sortable(const ScenePlan& plan) { return plan.small || plan.single; }
+
+BatchSortScene scene_sort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan,
+                               uint64_t* user_cells, int64_t user_cap) {
+  Carve c{ws};
+  SmallWs w{};
+  WideWs ww{};
+  PivotWs pw{};
+  TreeWs tw{};
+  carve_scene(c, plan, ctr, &w, &ww, &pw, &tw);
+  BatchSortScene d{};
+  d.ctr = ctr;
+  d.ucap = uint32_t(plan.ucap);
+  d.w = (plan.ell + 63) / 64;
+  d.ell = plan.ell;
+  d.user_cells = user_cells;
+  d.user_cap = user_cap;
+  if (plan.small) {
+    d.ulist = w.ulist;
+    d.cells = w.sortbuf;
+    d.t = w.table(true);
+  } else {
+    d.keys64 = ww.keys64;
+    d.idx = ww.idx0;
+    d.cells = ww.cells;
+  }
+  return d;
+}
+
 cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan& plan,
                         const PackArgs& pa, int word_bits, void* cells, int64_t cells_cap,
                         uint32_t* edges, int64_t edges_cap, cudaStream_t s,
-                        const PackPieces* pieces) {
+                        const PackPieces* pieces, int phase) {
   Carve c{ws};
   SmallWs w{};
   WideWs ww{};
@@ -970,6 +1011,29 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   const bool tree = strategy == CG_STRATEGY_TREE;
   const bool own = pivot || tree;
   cg_status st;
+  if (phase == kPhaseSearch) {
+    // After a batch sort: the sorted cells (and, for l <= 64, the cell
+    // numbers in the table) are in place.
+    const int w64 = (ell + 63) / 64;
+    if (plan.small) {
+      w.cells = w.sortbuf;
+      if (pivot) return pivot_steps(w.cells, 1, ell, plan.tp.pivots, w.ctr, pw, plan.ucap, edges,
+                                    edges_cap, s);
+      if (tree) return tree_steps(w.cells, 1, ell, w.ctr, tw, plan.ucap, edges, edges_cap, s);
+      return neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
+    }
+    if (pivot) return pivot_steps(ww.cells, w64, ell, plan.tp.pivots, ww.ctr, pw, plan.ucap, edges,
+                                  edges_cap, s);
+    if (tree) return tree_steps(ww.cells, w64, ell, ww.ctr, tw, plan.ucap, edges, edges_cap, s);
+    WideTable it{ww.slots2, uint32_t(plan.cap - 1), nullptr, 0, ww.ctr};
+    if (strategy != CG_STRATEGY_SORTED)
+      CG_CUDA(launch_index_wide(ww.cells, w64, ell, it, ww.fp, plan.ucap, s),
+              "fingerprint index");
+    CG_CUDA(launch_neighbors_emit_wide(ww.cells, w64, ell, it, ww.fp, strategy, ww.status,
+                                       edges, edges_cap, plan.ucap, s),
+            "neighbour search and edge output");
+    return CG_OK;
+  }
   if (plan.small) {
     CG_CUDA(launch_clear_build(w.tkeys, plan.cap, own ? nullptr : w.status,
                                own ? 0 : ne_status_words(plan.ucap), w.ctr, s),
@@ -998,6 +1062,7 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
       }
     }
     mark(ctx, "pack_dedup", s);
+    if (phase == kPhaseInsert) return CG_OK;
     st = dedup_small_tail(w, ell, word_bits, cells, cells_cap, s);
     if (st) return st;
     mark(ctx, "sort_number", s);
@@ -1022,6 +1087,7 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
       CG_CUDA(launch_fill_u64(ww.slots, kEmpty, plan.cap, s), "clearing table");
       WideTable dt{ww.slots, uint32_t(plan.cap - 1), ww.idx0, uint32_t(plan.ucap), ww.ctr};
       CG_CUDA(launch_insert_wide(ww.keys64, n, w64, dt, s), "inserting vectors");
+      if (phase == kPhaseInsert) return CG_OK;
       st = sort_cells_wide(ww, ell, word_bits, cells, cells_cap, plan.ucap, s);
       if (st) return st;
     } else {
@@ -1051,6 +1117,7 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   WideTable dt{ww.slots, uint32_t(plan.cap - 1), ww.idx0, uint32_t(plan.ucap), ww.ctr};
   CG_CUDA(launch_insert_wide(ww.keys64, n, w64, dt, s), "inserting vectors");
   mark(ctx, "dedup_insert", s);
+  if (phase == kPhaseInsert) return CG_OK;
   st = sort_cells_wide(ww, ell, word_bits, cells, cells_cap, plan.ucap, s);
   if (st) return st;
   mark(ctx, "dedup_sort", s);
@@ -1199,6 +1266,7 @@ cg_status build_checked(cg_ctx* ctx, const int32_t* pts, int64_t n, int d, const
       if (cap >= full) return fail(CG_ERR_INTERNAL, "table overflow at full capacity");
       cap = std::min(full, cap * 4);
       ctx->cap_hint[key] = cap;
+      ++ctx->hint_version;
       continue;
     }
     *n_cells = host->n_unique;
@@ -1456,6 +1524,7 @@ struct BatchScene {
   int w;
   size_t ecap;
   size_t ws_off, cells_off, edges_off;
+  bool sorted;  // sorted together with the other scenes (batch sort)
 };
 
 }  // namespace
@@ -1489,6 +1558,100 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   const int S = n_scenes;
   std::vector<BatchScene> bs(static_cast<size_t>(S));
+  // Quick signature of what the plan depends on: scenes, outputs, tuning and
+  // size hints. A batch identical to the captured one replays its graph
+  // without being planned again.
+  uint64_t quick = 0x13198a2e03707344ull;
+  {
+    auto qmix = [&](uint64_t v) { quick = mix64(quick ^ v) + 0x632be59bd9b4e019ull; };
+    qmix(uint64_t(S));
+    qmix(reinterpret_cast<uintptr_t>(out->cells));
+    qmix(uint64_t(out->cells_cap));
+    qmix(reinterpret_cast<uintptr_t>(out->edges));
+    qmix(uint64_t(out->edges_cap));
+    qmix(ctx->hint_version);
+    for (const cg_tune_params& t : ctx->tune)
+      qmix(uint64_t(t.strategy) * 4096 + uint64_t(t.pivots) * 16 + uint64_t(t.sign_kernel));
+    for (int i = 0; i < S; ++i) {
+      const cg_scene& sc = scenes[i];
+      qmix(reinterpret_cast<uintptr_t>(sc.pts));
+      qmix(reinterpret_cast<uintptr_t>(sc.a));
+      qmix(reinterpret_cast<uintptr_t>(sc.b));
+      qmix(uint64_t(sc.n) * 8192 + uint64_t(sc.ell) * 8 + uint64_t(sc.d));
+    }
+    const char* sk = std::getenv("CG_SIGN_KERNEL");
+    qmix(sk && std::strcmp(sk, "tc") == 0 ? 1u : 0u);
+  }
+  // Reads the counters of a finished batch: true when done (*res set), false
+  // when size hints were learned and the batch must be planned and run again.
+  auto settle = [&](const DevCounters* hctr, const long long* hcoff, const long long* heoff,
+                    const int* hok, auto cap_of, auto ecap_of, cg_status* res) -> bool {
+    bool again = false;
+    for (int i = 0; i < S; ++i) {
+      const DevCounters& h = hctr[i];
+      const cg_scene& sc = scenes[i];
+      const auto key = std::make_tuple(sc.n, sc.ell, sc.d);
+      if (h.error & kErrTimeout) {
+        *res = fail(CG_ERR_TIMEOUT, "a bounded device-side wait ran out");
+        return true;
+      }
+      if (h.error) {
+        *res = fail(CG_ERR_INTERNAL, "scene " + std::to_string(i) + ": device check failed");
+        return true;
+      }
+      if (h.overflow) {
+        if (cap_of(i) >= full_cap(sc.n)) {
+          *res = fail(CG_ERR_INTERNAL, "table overflow at full capacity");
+          return true;
+        }
+        ctx->cap_hint[key] = std::min(full_cap(sc.n), cap_of(i) * 4);
+        ++ctx->hint_version;
+        again = true;
+      } else if (h.n_edges > ecap_of(i)) {
+        ctx->edge_hint[key] = size_t(h.n_edges) + 64;
+        ++ctx->hint_version;
+        again = true;
+      }
+    }
+    if (again) return false;
+    for (int i = 0; i < S; ++i) {
+      out->n_cells[i] = hctr[i].n_unique;
+      out->n_edges[i] = int64_t(hctr[i].n_edges);
+    }
+    if (out->cells_offset)
+      for (int i = 0; i <= S; ++i) out->cells_offset[i] = hcoff[i];
+    if (out->edges_offset)
+      for (int i = 0; i <= S; ++i) out->edges_offset[i] = heoff[i];
+    if (!*hok) {
+      *res = fail(CG_ERR_CAPACITY, "batch outputs: " + std::to_string(hcoff[S]) + " words (cap " +
+                                       std::to_string(out->cells_cap) + "), " +
+                                       std::to_string(heoff[S]) + " edges (cap " +
+                                       std::to_string(out->edges_cap) + ")");
+      return true;
+    }
+    *res = CG_OK;
+    return true;
+  };
+  if (!ctx->timing && ctx->bgraph && ctx->bgraph_quick == quick &&
+      ctx->bplan.size() == size_t(S)) {
+    cudaStream_t s0 = ctx->bstream;
+    char* hb = static_cast<char*>(ctx->bhost);
+    DevCounters* hctr = reinterpret_cast<DevCounters*>(hb + size_t(S) * sizeof(BatchEntry));
+    long long* hcoff = reinterpret_cast<long long*>(hctr + S);
+    long long* heoff = hcoff + (S + 1);
+    int* hok = reinterpret_cast<int*>(heoff + (S + 1));
+    CG_CUDA(cudaEventRecord(ctx->in_ev, caller), "ordering after the caller's stream");
+    CG_CUDA(cudaStreamWaitEvent(s0, ctx->in_ev, 0), "ordering after the caller's stream");
+    CG_CUDA(cudaGraphLaunch(ctx->bgraph, s0), "replaying the batch graph");
+    count_launch(int(ctx->bgraph_launches));
+    CG_CUDA(cudaEventRecord(ctx->out_ev, s0), "ordering the caller's stream after the batch");
+    CG_CUDA(cudaStreamWaitEvent(caller, ctx->out_ev, 0), "ordering after the batch");
+    CG_CUDA(cudaStreamSynchronize(s0), "synchronising stream");
+    cg_status res = CG_OK;
+    if (settle(hctr, hcoff, heoff, hok, [&](int i) { return ctx->bplan[size_t(i)].cap; },
+               [&](int i) { return ctx->bplan[size_t(i)].ecap; }, &res))
+      return res;
+  }
   for (int attempt = 0; attempt < 8; ++attempt) {
     // ---- sizes and layout ----
     Carve m{nullptr};
@@ -1497,6 +1660,9 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     m.take<long long>(size_t(S) + 1);
     m.take<long long>(size_t(S) + 1);
     m.take<int>(1);
+    m.take<BatchSortScene>(size_t(S));
+    size_t sort_cap = 0;
+    int n_sorted = 0;
     for (int i = 0; i < S; ++i) {
       const cg_scene& sc = scenes[i];
       const auto key = std::make_tuple(sc.n, sc.ell, sc.d);
@@ -1517,9 +1683,17 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       m.off += b.plan.ucap * size_t(b.w) * sizeof(uint64_t);
       b.edges_off = m.off = (m.off + 255) & ~size_t(255);
       m.off += b.ecap * 2 * sizeof(uint32_t);
+      b.sorted = scene_batch_sortable(b.plan);
+      if (b.sorted) {
+        sort_cap += b.plan.ucap;
+        ++n_sorted;
+      }
     }
+    const size_t sort_off = m.off = (m.off + 255) & ~size_t(255);
+    m.off += batch_sort_bytes(sort_cap, n_sorted);
     const size_t host_bytes = size_t(S) * (sizeof(BatchEntry) + sizeof(DevCounters)) +
-                              2 * (size_t(S) + 1) * sizeof(long long) + 256;
+                              2 * (size_t(S) + 1) * sizeof(long long) + 256 +
+                              size_t(S) * sizeof(BatchSortScene) + 256;
     cg_status st = ensure_batch_resources(ctx, m.off + 256, host_bytes);
     if (st) return st;
     // The batch runs on the context's own stream, after the caller's work.
@@ -1533,17 +1707,24 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     long long* coff = c.take<long long>(size_t(S) + 1);
     long long* eoff = c.take<long long>(size_t(S) + 1);
     int* okp = c.take<int>(1);
+    BatchSortScene* dsort = c.take<BatchSortScene>(size_t(S));
     char* hb = static_cast<char*>(ctx->bhost);
     BatchEntry* htab = reinterpret_cast<BatchEntry*>(hb);
     DevCounters* hctr = reinterpret_cast<DevCounters*>(hb + size_t(S) * sizeof(BatchEntry));
     long long* hcoff = reinterpret_cast<long long*>(hctr + S);
     long long* heoff = hcoff + (S + 1);
     int* hok = reinterpret_cast<int*>(heoff + (S + 1));
-    for (int i = 0; i < S; ++i) {
+    BatchSortScene* hsort = reinterpret_cast<BatchSortScene*>(
+        (reinterpret_cast<uintptr_t>(hok + 1) + 255) & ~uintptr_t(255));
+    for (int i = 0, k = 0; i < S; ++i) {
       const BatchScene& b = bs[size_t(i)];
       htab[i] = BatchEntry{ctrs + i, reinterpret_cast<const uint64_t*>(base + b.cells_off),
                            reinterpret_cast<const uint32_t*>(base + b.edges_off), uint32_t(b.w),
                            uint32_t(b.plan.ucap), (unsigned long long)b.ecap};
+      if (b.sorted)
+        hsort[k++] = scene_sort_desc(base + b.ws_off, ctrs + i, b.plan,
+                                     reinterpret_cast<uint64_t*>(base + b.cells_off),
+                                     int64_t(b.plan.ucap));
     }
     // ---- stream assignment: largest scenes first, each to the least loaded
     // worker stream (longest-processing-time rule), by estimated work ----
@@ -1569,22 +1750,58 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       CG_CUDA(cudaMemcpyAsync(tab, htab, size_t(S) * sizeof(BatchEntry), cudaMemcpyHostToDevice,
                               s0),
               "uploading the scene table");
-      CG_CUDA(cudaEventRecord(ctx->fork_ev, s0), "fork");
-      for (auto& w : ctx->workers) CG_CUDA(cudaStreamWaitEvent(w, ctx->fork_ev, 0), "fork");
+      if (n_sorted)
+        CG_CUDA(cudaMemcpyAsync(dsort, hsort, size_t(n_sorted) * sizeof(BatchSortScene),
+                                cudaMemcpyHostToDevice, s0),
+                "uploading the sort table");
+      auto fork = [&]() -> cg_status {
+        CG_CUDA(cudaEventRecord(ctx->fork_ev, s0), "fork");
+        for (auto& w : ctx->workers) CG_CUDA(cudaStreamWaitEvent(w, ctx->fork_ev, 0), "fork");
+        return CG_OK;
+      };
+      auto join = [&]() -> cg_status {
+        for (size_t k = 0; k < ctx->workers.size(); ++k) {
+          CG_CUDA(cudaEventRecord(ctx->join_ev[k], ctx->workers[k]), "join");
+          CG_CUDA(cudaStreamWaitEvent(s0, ctx->join_ev[k], 0), "join");
+        }
+        return CG_OK;
+      };
+      cg_status st2 = fork();
+      if (st2) return st2;
+      mark(ctx, "batch_start", s0);
+      // Up to the dedup insert (whole builds for the scenes not sorted
+      // together), then one sort of every other scene's distinct vectors,
+      // then their neighbour searches.
       for (int i : order) {
         const cg_scene& sc = scenes[i];
         const BatchScene& b = bs[size_t(i)];
         PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
-        cg_status st2 =
-            enqueue_scene(nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64, base + b.cells_off,
-                          int64_t(b.plan.ucap), reinterpret_cast<uint32_t*>(base + b.edges_off),
-                          int64_t(b.ecap), ctx->workers[size_t(stream_of[size_t(i)])]);
+        st2 = enqueue_scene(nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64, base + b.cells_off,
+                            int64_t(b.plan.ucap), reinterpret_cast<uint32_t*>(base + b.edges_off),
+                            int64_t(b.ecap), ctx->workers[size_t(stream_of[size_t(i)])], nullptr,
+                            b.sorted ? kPhaseInsert : kPhaseAll);
         if (st2) return st2;
       }
-      for (size_t k = 0; k < ctx->workers.size(); ++k) {
-        CG_CUDA(cudaEventRecord(ctx->join_ev[k], ctx->workers[k]), "join");
-        CG_CUDA(cudaStreamWaitEvent(s0, ctx->join_ev[k], 0), "join");
+      if (n_sorted) {
+        if ((st2 = join())) return st2;
+        mark(ctx, "batch_insert", s0);
+        CG_CUDA(batch_sort(dsort, n_sorted, sort_cap, base + sort_off, s0), "batch sort");
+        mark(ctx, "batch_sort", s0);
+        if ((st2 = fork())) return st2;
+        for (int i : order) {
+          const cg_scene& sc = scenes[i];
+          const BatchScene& b = bs[size_t(i)];
+          if (!b.sorted) continue;
+          PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
+          st2 = enqueue_scene(nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64,
+                              base + b.cells_off, int64_t(b.plan.ucap),
+                              reinterpret_cast<uint32_t*>(base + b.edges_off), int64_t(b.ecap),
+                              ctx->workers[size_t(stream_of[size_t(i)])], nullptr, kPhaseSearch);
+          if (st2) return st2;
+        }
       }
+      if ((st2 = join())) return st2;
+      mark(ctx, "batch_search", s0);
       CG_CUDA(launch_batch_gather(tab, S, coff, eoff, okp, out->cells, out->cells_cap,
                                   out->edges, out->edges_cap, s0),
               "gathering outputs");
@@ -1621,13 +1838,18 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       const cg_tune_params& tp = bs[size_t(i)].plan.tp;
       mixin(uint64_t(tp.strategy) * 4096 + uint64_t(tp.pivots) * 16 + uint64_t(tp.sign_kernel));
     }
-    if (ctx->bgraph && ctx->bgraph_sig == sig) {
+    ctx->n_marks = 0;
+    if (ctx->timing) {
+      st = enqueue();
+      if (st) return st;
+    } else if (ctx->bgraph && ctx->bgraph_sig == sig) {
       CG_CUDA(cudaGraphLaunch(ctx->bgraph, s0), "replaying the batch graph");
       count_launch(int(ctx->bgraph_launches));
     } else {
       if (ctx->bgraph) {
         cudaGraphExecDestroy(ctx->bgraph);
         ctx->bgraph = nullptr;
+        ctx->bgraph_quick = 0;
       }
       if (ctx->last_sig == sig) {
         // Second identical batch in a row: capture it once and replay it from
@@ -1649,6 +1871,10 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
           return cuda_fail(ce, "instantiating the batch graph");
         }
         ctx->bgraph_sig = sig;
+        ctx->bgraph_quick = quick;
+        ctx->bplan.resize(size_t(S));
+        for (int i = 0; i < S; ++i)
+          ctx->bplan[size_t(i)] = BatchPlanCopy{bs[size_t(i)].plan.cap, bs[size_t(i)].ecap};
         ctx->bgraph_launches = cg_launch_count() - before;
         count_launch(-int(ctx->bgraph_launches));  // captured, not yet run
         CG_CUDA(cudaGraphLaunch(ctx->bgraph, s0), "launching the batch graph");
@@ -1662,40 +1888,12 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     CG_CUDA(cudaEventRecord(ctx->out_ev, s0), "ordering the caller's stream after the batch");
     CG_CUDA(cudaStreamWaitEvent(caller, ctx->out_ev, 0), "ordering after the batch");
     CG_CUDA(cudaStreamSynchronize(s0), "synchronising stream");
+    accumulate_marks(ctx);
     // ---- check, learn sizes, retry the scenes that did not fit ----
-    bool again = false;
-    for (int i = 0; i < S; ++i) {
-      const DevCounters& h = hctr[i];
-      const cg_scene& sc = scenes[i];
-      const auto key = std::make_tuple(sc.n, sc.ell, sc.d);
-      if (h.error & kErrTimeout) return fail(CG_ERR_TIMEOUT, "a bounded device-side wait ran out");
-      if (h.error)
-        return fail(CG_ERR_INTERNAL, "scene " + std::to_string(i) + ": device check failed");
-      if (h.overflow) {
-        if (bs[size_t(i)].plan.cap >= full_cap(sc.n))
-          return fail(CG_ERR_INTERNAL, "table overflow at full capacity");
-        ctx->cap_hint[key] = std::min(full_cap(sc.n), bs[size_t(i)].plan.cap * 4);
-        again = true;
-      } else if (h.n_edges > bs[size_t(i)].ecap) {
-        ctx->edge_hint[key] = size_t(h.n_edges) + 64;
-        again = true;
-      }
-    }
-    if (again) continue;
-    for (int i = 0; i < S; ++i) {
-      out->n_cells[i] = hctr[i].n_unique;
-      out->n_edges[i] = int64_t(hctr[i].n_edges);
-    }
-    if (out->cells_offset)
-      for (int i = 0; i <= S; ++i) out->cells_offset[i] = hcoff[i];
-    if (out->edges_offset)
-      for (int i = 0; i <= S; ++i) out->edges_offset[i] = heoff[i];
-    if (!*hok)
-      return fail(CG_ERR_CAPACITY, "batch outputs: " + std::to_string(hcoff[S]) + " words (cap " +
-                                       std::to_string(out->cells_cap) + "), " +
-                                       std::to_string(heoff[S]) + " edges (cap " +
-                                       std::to_string(out->edges_cap) + ")");
-    return CG_OK;
+    cg_status res = CG_OK;
+    if (settle(hctr, hcoff, heoff, hok, [&](int i) { return bs[size_t(i)].plan.cap; },
+               [&](int i) { return bs[size_t(i)].ecap; }, &res))
+      return res;
   }
   return fail(CG_ERR_INTERNAL, "batch did not settle after repeated resizing");
 }

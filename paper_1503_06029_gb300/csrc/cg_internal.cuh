@@ -216,6 +216,29 @@ cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32
                             const unsigned int* n_dev, size_t max_n, cudaStream_t s,
                             uint32_t** sorted_idx, const unsigned int* skip = nullptr);
 
+// Batch sort: the distinct vectors of many scenes sorted together, scene by
+// scene (one merge sort on (scene, top 128 bits, whole vector)), then
+// scattered into each scene's sorted cells, the caller's copy and, for
+// l <= 64, the cell numbers in the scene's table. A scene whose table
+// overflowed contributes nothing (the caller re-runs it).
+struct BatchSortScene {
+  DevCounters* ctr;        // n_unique (and overflow)
+  uint32_t ucap;           // at most this many distinct vectors
+  int w;                   // 64-bit words per vector
+  int ell;
+  const uint64_t* ulist;   // l <= 64: distinct vectors, insertion order
+  const uint64_t* keys64;  // l > 64: vectors ...
+  const uint32_t* idx;     // ... and the rows of the distinct ones
+  uint64_t* cells;         // sorted cells, w words each
+  uint64_t* user_cells;    // the caller's copy (64-bit words), nullable
+  int64_t user_cap;        // cells
+  SmallTable t;            // l <= 64: cell numbers into t.vals (t.keys nullable)
+};
+size_t batch_sort_bytes(size_t total_cap, int n_scenes);
+// scenes: device array of n_scenes; total_cap >= sum of their ucap.
+cudaError_t batch_sort(const BatchSortScene* scenes, int n_scenes, size_t total_cap,
+                       void* scratch, cudaStream_t s);
+
 // out[i] = sum_{j<i} in[j] for i < *n_dev; *total = sum of all (device).
 cudaError_t scan_exclusive_u32(const uint32_t* in, unsigned long long* out,
                                const unsigned int* n_dev, size_t max_n,

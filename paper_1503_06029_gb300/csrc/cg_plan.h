@@ -51,9 +51,20 @@ struct PackPieces {
 // nothing is read back. Cells go to `cells` (word_bits words, when
 // U <= cells_cap), edges to `edges` (up to edges_cap). ctx (nullable) only
 // receives stage-timing marks.
+// Phases: the whole build, or (for batches whose sort runs across scenes)
+// everything up to the dedup insert, and everything after the sort.
+enum ScenePhase { kPhaseAll = 0, kPhaseInsert = 1, kPhaseSearch = 2 };
+
 cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan& plan,
                         const PackArgs& pa, int word_bits, void* cells, int64_t cells_cap,
                         uint32_t* edges, int64_t edges_cap, cudaStream_t s,
-                        const PackPieces* pieces = nullptr);
+                        const PackPieces* pieces = nullptr, int phase = kPhaseAll);
+
+// Whether a scene can be split into kPhaseInsert / kPhaseSearch around a
+// batch sort, and its sort descriptor (device pointers into workspace ws,
+// counters ctr, the caller's cells user_cells of capacity user_cap).
+bool scene_batch_sortable(const ScenePlan& plan);
+BatchSortScene scene_sort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan,
+                               uint64_t* user_cells, int64_t user_cap);
 
 }  // namespace cg

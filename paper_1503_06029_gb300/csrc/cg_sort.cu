@@ -488,35 +488,18 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
 // significant bits of its row (bits [l - 128, l), zero-filled below bit 0) as
 // a cached key, and only items with equal cached keys compare their whole
 // rows (most significant word first); for l <= 128 the cached key is the whole
-// row. Tiles of kMTile items are sorted in shared memory (bitonic network),
-// then runs are merged pairwise (merge path: each block finds its diagonal
-// split by binary search and merges one output tile); ceil(log2(U / kMTile))
-// passes, each reading and writing 20 bytes per item.
+// row. Tiles of items are sorted in shared memory (bitonic network), then runs
+// are merged pairwise (merge path: each block finds its diagonal split by
+// binary search and merges one output tile); ceil(log2(U / tile)) passes.
+//
+// The kernels are generic over an order: Ord::Tag is the payload carried with
+// each cached key, Ord::pad() a tag larger than every item, Ord::load(g)
+// produces input item g and Ord::less compares two items. RowOrder sorts one
+// scene's rows; BatchOrder (batch sort) sorts the distinct vectors of many
+// scenes at once, scene by scene.
 
 constexpr int kMThreads = 256;
-constexpr int kMItems = 8;
-constexpr int kMTile = kMThreads * kMItems;  // 2048
 constexpr uint32_t kPad = 0xffffffffu;
-
-struct RowOrder {
-  const uint64_t* rows;
-  int w;
-  bool full;  // the cached key is the whole row (l <= 128)
-  // a < b; the padding item (row kPad) is larger than everything.
-  __device__ __forceinline__ bool less(const ulonglong2& ka, uint32_t ia, const ulonglong2& kb,
-                                       uint32_t ib) const {
-    if (ia == kPad) return false;
-    if (ib == kPad) return true;
-    if (ka.x != kb.x) return ka.x < kb.x;
-    if (ka.y != kb.y) return ka.y < kb.y;
-    if (full) return ia < ib;
-    const uint64_t* ra = rows + uint64_t(ia) * w;
-    const uint64_t* rb = rows + uint64_t(ib) * w;
-    for (int q = w - 1; q >= 0; --q)
-      if (ra[q] != rb[q]) return ra[q] < rb[q];
-    return ia < ib;
-  }
-};
 
 // Bits [off, off + 64) of a row (positions below 0 read as zero, off > -64).
 __device__ __forceinline__ uint64_t bits64_at(const uint64_t* row, int off) {
@@ -530,64 +513,130 @@ __device__ __forceinline__ ulonglong2 top128(const uint64_t* row, int ell) {
   return make_ulonglong2(bits64_at(row, ell - 64), bits64_at(row, ell - 128));
 }
 
-// Tile sort: items [b * kMTile, ...) of idx_in, with their cached keys.
+struct RowOrder {
+  using Tag = uint32_t;  // row number
+  static constexpr int kItems = 8;
+  const uint64_t* rows;
+  int w;
+  int ell;
+  bool full;                // the cached key is the whole row (l <= 128)
+  const uint32_t* idx_in;   // input row numbers (nullable: item g is row g)
+  __device__ __forceinline__ static Tag pad() { return kPad; }
+  __device__ __forceinline__ void load(uint32_t g, ulonglong2* k, Tag* t) const {
+    const uint32_t r = idx_in ? idx_in[g] : g;
+    *t = r;
+    *k = top128(rows + uint64_t(r) * w, ell);
+  }
+  // a < b; the padding item is larger than everything.
+  __device__ __forceinline__ bool less(const ulonglong2& ka, Tag ia, const ulonglong2& kb,
+                                       Tag ib) const {
+    if (ia == kPad) return false;
+    if (ib == kPad) return true;
+    if (ka.x != kb.x) return ka.x < kb.x;
+    if (ka.y != kb.y) return ka.y < kb.y;
+    if (full) return ia < ib;
+    const uint64_t* ra = rows + uint64_t(ia) * w;
+    const uint64_t* rb = rows + uint64_t(ib) * w;
+    for (int q = w - 1; q >= 0; --q)
+      if (ra[q] != rb[q]) return ra[q] < rb[q];
+    return ia < ib;
+  }
+};
+
+struct BatchOrder {
+  using Tag = uint2;  // (scene, index of the distinct vector within it)
+  static constexpr int kItems = 4;
+  const BatchSortScene* scenes;
+  const ulonglong2* keys_in;
+  const uint2* tags_in;
+  __device__ __forceinline__ static Tag pad() { return make_uint2(kPad, kPad); }
+  __device__ __forceinline__ void load(uint32_t g, ulonglong2* k, Tag* t) const {
+    *k = keys_in[g];
+    *t = tags_in[g];
+  }
+  __device__ __forceinline__ bool less(const ulonglong2& ka, Tag ta, const ulonglong2& kb,
+                                       Tag tb) const {
+    if (ta.x != tb.x) return ta.x < tb.x;  // scene first (padding has the largest)
+    if (ta.x == kPad) return false;
+    if (ka.x != kb.x) return ka.x < kb.x;
+    if (ka.y != kb.y) return ka.y < kb.y;
+    const BatchSortScene& sc = scenes[ta.x];
+    if (sc.ell <= 128) return ta.y < tb.y;  // whole vector cached: distinct keys differ
+    const uint64_t* ra = sc.keys64 + uint64_t(sc.idx[ta.y]) * sc.w;
+    const uint64_t* rb = sc.keys64 + uint64_t(sc.idx[tb.y]) * sc.w;
+    for (int q = sc.w - 1; q >= 0; --q)
+      if (ra[q] != rb[q]) return ra[q] < rb[q];
+    return ta.y < tb.y;
+  }
+};
+
+template <class Ord>
+__device__ __forceinline__ bool tag_is_pad(const typename Ord::Tag& t);
+template <>
+__device__ __forceinline__ bool tag_is_pad<RowOrder>(const uint32_t& t) { return t == kPad; }
+template <>
+__device__ __forceinline__ bool tag_is_pad<BatchOrder>(const uint2& t) { return t.x == kPad; }
+
+// Tile sort: input items [b * tile, ...), with their cached keys.
+template <class Ord>
 __global__ void __launch_bounds__(kMThreads)
-    msort_tiles(RowOrder ord, int ell, const uint32_t* __restrict__ idx_in,
-                const unsigned int* n_dev, uint32_t max_n, ulonglong2* __restrict__ kout,
-                uint32_t* __restrict__ iout, const unsigned int* skip) {
-  __shared__ ulonglong2 sk[kMTile];
-  __shared__ uint32_t si[kMTile];
+    msort_tiles(Ord ord, const unsigned int* n_dev, uint32_t max_n, ulonglong2* __restrict__ kout,
+                typename Ord::Tag* __restrict__ tout, const unsigned int* skip) {
+  constexpr int kTile = kMThreads * Ord::kItems;
+  using Tag = typename Ord::Tag;
+  __shared__ ulonglong2 sk[kTile];
+  __shared__ Tag st[kTile];
   if (skip && *skip) return;
   const uint32_t n = min(*n_dev, max_n);
-  const uint32_t base = blockIdx.x * kMTile;
+  const uint32_t base = blockIdx.x * kTile;
   if (base >= n) return;
-  for (int t = threadIdx.x; t < kMTile; t += kMThreads) {
+  for (int t = threadIdx.x; t < kTile; t += kMThreads) {
     const uint32_t g = base + t;
     if (g < n) {
-      const uint32_t r = idx_in ? idx_in[g] : g;
-      si[t] = r;
-      sk[t] = top128(ord.rows + uint64_t(r) * ord.w, ell);
+      ord.load(g, &sk[t], &st[t]);
     } else {
-      si[t] = kPad;
+      st[t] = Ord::pad();
       sk[t] = make_ulonglong2(~0ull, ~0ull);
     }
   }
   __syncthreads();
-  for (int k = 2; k <= kMTile; k <<= 1) {
+  for (int k = 2; k <= kTile; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < kMTile; t += kMThreads) {
+      for (int t = threadIdx.x; t < kTile; t += kMThreads) {
         const int p = t ^ j;
         if (p > t) {
           const bool up = (t & k) == 0;
-          const bool swap = up ? ord.less(sk[p], si[p], sk[t], si[t])
-                               : ord.less(sk[t], si[t], sk[p], si[p]);
+          const bool swap = up ? ord.less(sk[p], st[p], sk[t], st[t])
+                               : ord.less(sk[t], st[t], sk[p], st[p]);
           if (swap) {
             const ulonglong2 tk = sk[t];
             sk[t] = sk[p];
             sk[p] = tk;
-            const uint32_t ti = si[t];
-            si[t] = si[p];
-            si[p] = ti;
+            const Tag tt = st[t];
+            st[t] = st[p];
+            st[p] = tt;
           }
         }
       }
       __syncthreads();
     }
   }
-  for (int t = threadIdx.x; t < kMTile; t += kMThreads) {
+  for (int t = threadIdx.x; t < kTile; t += kMThreads) {
     const uint32_t g = base + t;
     if (g < n) {
       kout[g] = sk[t];
-      iout[g] = si[t];
+      tout[g] = st[t];
     }
   }
 }
 
 // Number of items of A among the first d items of merge(A, B).
-__device__ __forceinline__ uint32_t merge_split(const RowOrder& ord, const ulonglong2* ka,
-                                                const uint32_t* ia, uint32_t la,
-                                                const ulonglong2* kb, const uint32_t* ib,
-                                                uint32_t lb, uint32_t d) {
+template <class Ord>
+__device__ __forceinline__ uint32_t merge_split(const Ord& ord, const ulonglong2* ka,
+                                                const typename Ord::Tag* ia, uint32_t la,
+                                                const ulonglong2* kb,
+                                                const typename Ord::Tag* ib, uint32_t lb,
+                                                uint32_t d) {
   uint32_t lo = d > lb ? d - lb : 0;
   uint32_t hi = d < la ? d : la;
   while (lo < hi) {
@@ -600,29 +649,32 @@ __device__ __forceinline__ uint32_t merge_split(const RowOrder& ord, const ulong
 }
 
 // One merge pass: sorted runs of `width` items merged pairwise into runs of
-// 2 * width; block b writes output items [b * kMTile, (b + 1) * kMTile).
+// 2 * width; block b writes output items [b * tile, (b + 1) * tile).
+template <class Ord>
 __global__ void __launch_bounds__(kMThreads)
-    msort_merge(RowOrder ord, const ulonglong2* __restrict__ kin, const uint32_t* __restrict__ iin,
-                ulonglong2* __restrict__ kout, uint32_t* __restrict__ iout,
-                const unsigned int* n_dev, uint32_t max_n, uint32_t width,
-                const unsigned int* skip) {
-  __shared__ ulonglong2 sk[kMTile];
-  __shared__ uint32_t si[kMTile];
+    msort_merge(Ord ord, const ulonglong2* __restrict__ kin,
+                const typename Ord::Tag* __restrict__ iin, ulonglong2* __restrict__ kout,
+                typename Ord::Tag* __restrict__ iout, const unsigned int* n_dev, uint32_t max_n,
+                uint32_t width, const unsigned int* skip) {
+  constexpr int kTile = kMThreads * Ord::kItems;
+  using Tag = typename Ord::Tag;
+  __shared__ ulonglong2 sk[kTile];
+  __shared__ Tag si[kTile];
   __shared__ uint32_t s_split[2];
   if (skip && *skip) return;
   const uint32_t n = min(*n_dev, max_n);
-  const uint32_t out0 = blockIdx.x * kMTile;
+  const uint32_t out0 = blockIdx.x * kTile;
   if (out0 >= n) return;
   const uint32_t s0 = (out0 / (2 * width)) * (2 * width);
   const uint32_t a_end = min(s0 + width, n);
   const uint32_t b_end = min(s0 + 2 * width, n);
   const uint32_t la = a_end - s0, lb = b_end - a_end;
   const uint32_t d0 = out0 - s0;
-  const uint32_t d1 = min(d0 + uint32_t(kMTile), la + lb);
+  const uint32_t d1 = min(d0 + uint32_t(kTile), la + lb);
   const ulonglong2* ka = kin + s0;
-  const uint32_t* ia = iin + s0;
+  const Tag* ia = iin + s0;
   const ulonglong2* kb = kin + a_end;
-  const uint32_t* ib = iin + a_end;
+  const Tag* ib = iin + a_end;
   if (threadIdx.x < 2)
     s_split[threadIdx.x] =
         merge_split(ord, ka, ia, la, kb, ib, lb, threadIdx.x == 0 ? d0 : d1);
@@ -640,12 +692,12 @@ __global__ void __launch_bounds__(kMThreads)
     }
   }
   __syncthreads();
-  // Each thread merges kMItems consecutive outputs of this tile.
-  const uint32_t dd = threadIdx.x * kMItems;
+  // Each thread merges kItems consecutive outputs of this tile.
+  const uint32_t dd = threadIdx.x * Ord::kItems;
   if (dd < na + nb) {
     uint32_t x = merge_split(ord, sk, si, na, sk + na, si + na, nb, dd);
     uint32_t y = dd - x;
-    const uint32_t end = min(dd + uint32_t(kMItems), na + nb);
+    const uint32_t end = min(dd + uint32_t(Ord::kItems), na + nb);
     for (uint32_t o = dd; o < end; ++o) {
       bool take_a;
       if (x >= na) take_a = false;
@@ -663,6 +715,155 @@ __global__ void __launch_bounds__(kMThreads)
       }
     }
   }
+}
+
+template <class Ord>
+cudaError_t run_merge_sort(const Ord& ord, ulonglong2* k0, ulonglong2* k1,
+                           typename Ord::Tag* t0, typename Ord::Tag* t1,
+                           const unsigned int* n_dev, size_t max_n, cudaStream_t s,
+                           bool* result_in_1, const unsigned int* skip) {
+  constexpr size_t kTile = size_t(kMThreads) * Ord::kItems;
+  const unsigned tiles = unsigned((max_n + kTile - 1) / kTile);
+  msort_tiles<Ord><<<tiles, kMThreads, 0, s>>>(ord, n_dev, uint32_t(max_n), k0, t0, skip);
+  count_launch();
+  bool in1 = false;
+  for (size_t width = kTile; width < max_n; width *= 2) {
+    msort_merge<Ord><<<tiles, kMThreads, 0, s>>>(ord, in1 ? k1 : k0, in1 ? t1 : t0,
+                                                 in1 ? k0 : k1, in1 ? t0 : t1, n_dev,
+                                                 uint32_t(max_n), uint32_t(width), skip);
+    count_launch();
+    in1 = !in1;
+  }
+  *result_in_1 = in1;
+  return cudaGetLastError();
+}
+
+// ------------------------------ batch sort ---------------------------------
+
+__global__ void __launch_bounds__(1024)
+    bsort_offsets(const BatchSortScene* __restrict__ sc, int n, uint32_t* off, unsigned int* total) {
+  __shared__ uint32_t wsum[32];
+  uint32_t carry = 0;
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + threadIdx.x;
+    uint32_t v = 0;
+    if (i < n) v = sc[i].ctr->overflow ? 0u : min(sc[i].ctr->n_unique, sc[i].ucap);
+    uint32_t inc = v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t before = (warp > 0 ? wsum[warp - 1] : 0u) + inc - v;
+    if (i < n) off[i] = carry + before;
+    const uint32_t block_total = wsum[31];
+    __syncthreads();
+    carry += block_total;
+  }
+  if (threadIdx.x == 0) {
+    off[n] = carry;
+    *total = carry;
+  }
+}
+
+__device__ __forceinline__ int scene_of(const uint32_t* off, int n, uint32_t g) {
+  int lo = 0, hi = n - 1;  // last scene s with off[s] <= g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void bsort_items(const BatchSortScene* __restrict__ sc, int n,
+                            const uint32_t* __restrict__ off, const unsigned int* total,
+                            ulonglong2* __restrict__ keys, uint2* __restrict__ tags) {
+  const uint32_t m = *total;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < m; g += gridDim.x * blockDim.x) {
+    const int s = scene_of(off, n, g);
+    const uint32_t i = g - off[s];
+    const BatchSortScene& c = sc[s];
+    keys[g] = c.ell <= 64 ? make_ulonglong2(c.ulist[i], 0ull)
+                          : top128(c.keys64 + uint64_t(c.idx[i]) * c.w, c.ell);
+    tags[g] = make_uint2(uint32_t(s), i);
+  }
+}
+
+__global__ void bsort_scatter(const BatchSortScene* __restrict__ sc,
+                              const uint32_t* __restrict__ off, const unsigned int* total,
+                              const uint2* __restrict__ tags) {
+  const uint32_t m = *total;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < m; g += gridDim.x * blockDim.x) {
+    const uint2 tg = tags[g];
+    const BatchSortScene& c = sc[tg.x];
+    const uint32_t rank = g - off[tg.x];
+    const uint32_t cnt = off[tg.x + 1] - off[tg.x];
+    const bool user = c.user_cells && int64_t(cnt) <= c.user_cap;
+    if (c.ell <= 64) {
+      const uint64_t v = c.ulist[tg.y];
+      c.cells[rank] = v;
+      if (user) c.user_cells[rank] = v;
+      if (c.t.keys) {
+        if (v == kEmpty) {
+          c.ctr->ones_rank = rank;
+        } else {
+          const int64_t slot = small_find_slot(c.t.keys, c.t.mask, c.t.shift, v);
+          if (slot >= 0) c.t.vals[slot] = rank;
+          else atomicOr(&c.ctr->error, 1u);
+        }
+      }
+    } else {
+      const uint64_t* row = c.keys64 + uint64_t(c.idx[tg.y]) * c.w;
+      for (int q = 0; q < c.w; ++q) {
+        c.cells[uint64_t(rank) * c.w + q] = row[q];
+        if (user) c.user_cells[uint64_t(rank) * c.w + q] = row[q];
+      }
+    }
+  }
+}
+
+struct BatchSortWs {
+  uint32_t* off;
+  unsigned int* total;
+  ulonglong2* k0;
+  ulonglong2* k1;
+  uint2* t0;
+  uint2* t1;
+  size_t bytes;
+};
+
+BatchSortWs carve_bsort(void* base, size_t cap, int n) {
+  BatchSortWs w{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    o = (o + 255) & ~size_t(255);
+    void* p = base ? static_cast<char*>(base) + o : nullptr;
+    o += bytes;
+    return p;
+  };
+  const size_t c = cap > 0 ? cap : 1;
+  w.off = static_cast<uint32_t*>(take((size_t(n) + 1) * 4));
+  w.total = static_cast<unsigned int*>(take(4));
+  w.k0 = static_cast<ulonglong2*>(take(c * 16));
+  w.k1 = static_cast<ulonglong2*>(take(c * 16));
+  w.t0 = static_cast<uint2*>(take(c * 8));
+  w.t1 = static_cast<uint2*>(take(c * 8));
+  w.bytes = o + 256;
+  return w;
 }
 
 }  // namespace
@@ -765,23 +966,35 @@ cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32
   *sorted_idx = i0;
   if (max_n == 0) return cudaSuccess;
   if (ell <= 64) return cudaErrorInvalidValue;
-  const RowOrder ord{rows, w64, ell <= 128};
-  const unsigned tiles = unsigned((max_n + kMTile - 1) / kMTile);
-  ulonglong2* kin = reinterpret_cast<ulonglong2*>(k0);
-  ulonglong2* kout = reinterpret_cast<ulonglong2*>(k1);
-  msort_tiles<<<tiles, kMThreads, 0, s>>>(ord, ell, idx_in, n_dev, uint32_t(max_n), kin, i0,
-                                          skip);
+  const RowOrder ord{rows, w64, ell, ell <= 128, idx_in};
+  bool in1 = false;
+  cudaError_t e = run_merge_sort(ord, reinterpret_cast<ulonglong2*>(k0),
+                                 reinterpret_cast<ulonglong2*>(k1), i0, i1, n_dev, max_n, s, &in1,
+                                 skip);
+  *sorted_idx = in1 ? i1 : i0;
+  return e;
+}
+
+size_t batch_sort_bytes(size_t total_cap, int n_scenes) {
+  return carve_bsort(nullptr, total_cap, n_scenes).bytes;
+}
+
+cudaError_t batch_sort(const BatchSortScene* scenes, int n_scenes, size_t total_cap,
+                       void* scratch, cudaStream_t s) {
+  if (n_scenes <= 0) return cudaSuccess;
+  BatchSortWs w = carve_bsort(scratch, total_cap, n_scenes);
+  bsort_offsets<<<1, 1024, 0, s>>>(scenes, n_scenes, w.off, w.total);
   count_launch();
-  uint32_t* iin = i0;
-  uint32_t* iout = i1;
-  for (size_t width = kMTile; width < max_n; width *= 2) {
-    msort_merge<<<tiles, kMThreads, 0, s>>>(ord, kin, iin, kout, iout, n_dev, uint32_t(max_n),
-                                             uint32_t(width), skip);
-    count_launch();
-    std::swap(kin, kout);
-    std::swap(iin, iout);
-  }
-  *sorted_idx = iin;
+  const size_t cap = total_cap > 0 ? total_cap : 1;
+  const int g = int(std::min<size_t>((cap + 255) / 256, size_t(sm_count()) * 8));
+  bsort_items<<<g, 256, 0, s>>>(scenes, n_scenes, w.off, w.total, w.k0, w.t0);
+  count_launch();
+  const BatchOrder ord{scenes, w.k0, w.t0};
+  bool in1 = false;
+  cudaError_t e = run_merge_sort(ord, w.k0, w.k1, w.t0, w.t1, w.total, cap, s, &in1, nullptr);
+  if (e != cudaSuccess) return e;
+  bsort_scatter<<<g, 256, 0, s>>>(scenes, w.off, w.total, in1 ? w.t1 : w.t0);
+  count_launch();
   return cudaGetLastError();
 }
 
