@@ -352,7 +352,7 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
     return out
 
 
-def chains_measure(dev, steps: int, strategies=("hash", "pivot", "tree")):
+def chains_measure(dev, steps: int, strategies=("hash", "pivot", "tree", "halves")):
     """Long vectors: l = 1024 (16 words), 2^18 random seeds with 15-step
     single-flip chains, 25% duplicated, N = 5,242,880 vectors resident on the
     device. One step = cg_dedup_cells + cg_neighbors_h1 (counts read back),

@@ -76,6 +76,13 @@ typedef int cg_status;
 #define CG_STRATEGY_TREE 4   /* the 2^r-ary search tree of §3.2 (Algorithms 3-4),
                                 r = 8, built level by level over the sorted
                                 cells and walked once per flipped bit */
+#define CG_STRATEGY_HALVES 5 /* the O(n l) search named in §6, as two-part
+                                multi-index hashing: with the bits split at
+                                s = floor(l/2), partners that differ below s
+                                share the high part (contiguous in the sorted
+                                cells), partners that differ above s share the
+                                low part (grouped by one stable sort); each
+                                group is compared within itself */
 
 /* Message describing the calling thread's last failed call ("" if none). */
 const char* cg_last_error(void);
@@ -173,7 +180,7 @@ cg_status cg_ctx_stage_times(cg_ctx* ctx, double* ms, const char** names, int ca
  * ------------------------------------------------------------------------- */
 #define CG_TUNE_BUCKETS 7
 typedef struct cg_tune_params {
-  int strategy;    /* CG_STRATEGY_HASH, _SORTED, _PIVOT or _TREE */
+  int strategy;    /* CG_STRATEGY_HASH, _SORTED, _PIVOT, _TREE or _HALVES */
   int pivots;      /* h for PIVOT: 1 <= h <= min(8, 64 / bits(l)) (clamped) */
   int sign_kernel; /* 0: fp32 FMA filter with exact fallback; 1: tensor cores
                       (tcgen05, l <= 64 only; ignored above) */

@@ -29,7 +29,7 @@ ERR_CUDA = 5
 ERR_TIMEOUT = 6
 ERR_INTERNAL = 7
 
-STRATEGY = {"auto": 0, "hash": 1, "sorted": 2, "pivot": 3, "tree": 4}
+STRATEGY = {"auto": 0, "hash": 1, "sorted": 2, "pivot": 3, "tree": 4, "halves": 5}
 STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
 TUNE_BUCKETS = 7
 TUNE_LIMITS = (16, 32, 64, 128, 256, 1024, 4096)

@@ -346,7 +346,25 @@ cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t*
 // counting search, scan, writing search, per-cell ordering.
 cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
                       const PivotWs& p, size_t ucap, uint32_t* edges, int64_t edges_cap,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool halves) {
+  if (halves) {
+    // HALVES: H keys in kcell, the folds in the bucket-table memory (at
+    // least 4 ucap words), the L sort keys through k0/k1 with the cell
+    // numbers, the H folds in sorted order in the spare key buffer.
+    uint64_t* fl = static_cast<uint64_t*>(p.table);
+    uint64_t* fh = fl + ucap;
+    CG_CUDA(launch_halves_keys(cells, w64, ell, ctr, ucap, p.kcell, fl, fh, p.k0, p.i0, s),
+            "part keys");
+    bool in1 = false;
+    CG_CUDA(radix_sort_u64(p.k0, p.k1, p.i0, p.i1, &ctr->n_unique, ucap, halves_sort_bits(ell),
+                           p.radix, s, &in1),
+            "sorting by the low part");
+    CG_CUDA(launch_halves_edges(cells, w64, ell, ctr, ucap, p.kcell, fl, fh, in1 ? p.k1 : p.k0,
+                                in1 ? p.i1 : p.i0, in1 ? p.k0 : p.k1, p.counts, p.hbuf,
+                                p.offsets, p.fill, p.scan, edges, edges_cap, s),
+            "two-part neighbour search and edge output");
+    return CG_OK;
+  }
   CG_CUDA(launch_fill_u64(static_cast<uint64_t*>(p.table), kEmpty, 2 * p.tcap, s),
           "clearing the bucket table");
   CG_CUDA(launch_pivot_keys(cells, w64, ell, h, ctr, ucap, p.kcell, p.k0, p.i0, s),
@@ -457,7 +475,7 @@ cg_status dedup_wide_steps(WideWs& w, const uint64_t* keys64, int64_t n, int ell
   CG_CUDA(launch_insert_wide(keys64, n, w64, t, s), "inserting vectors");
   uint32_t* sorted = nullptr;
   CG_CUDA(sort_wide(keys64, w64, ell, w.idx0, w.idx1, w.kw0, w.kw1, &w.ctr->n_unique, w.ucap,
-                    w.radix, s, &sorted),
+                    w.radix, s, &sorted, nullptr, &w.ctr->msort_done),
           "sorting cells");
   CG_CUDA(launch_gather_rows(keys64, w64, sorted, &w.ctr->n_unique, w.ucap, w.cells, s),
           "gathering cells");
@@ -783,13 +801,14 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
   NvtxRange nvtx("cg_neighbors_h1");
   std::string why;
   if (!check_common(n_cells, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
-  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_TREE)
+  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_HALVES)
     return fail(CG_ERR_INVALID_ARG, "unknown strategy");
   if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
   const size_t un = size_t(n_cells > 0 ? n_cells : 1);
   const size_t cap = std::max<size_t>(1024, next_pow2(2 * un));
   const bool small = ell <= 64;
-  const bool pivot = strategy == CG_STRATEGY_PIVOT;
+  const bool halves = strategy == CG_STRATEGY_HALVES;
+  const bool pivot = strategy == CG_STRATEGY_PIVOT || halves;
   const bool tree = strategy == CG_STRATEGY_TREE;
   {
     Carve c{nullptr};
@@ -820,7 +839,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     cg_status st;
     if (pivot) {
       st = pivot_steps(w.cells, 1, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un,
-                       edges, edges_cap, s);
+                       edges, edges_cap, s, halves);
     } else if (tree) {
       st = tree_steps(w.cells, 1, ell, w.ctr, carve_treews(c, un, ell), un, edges, edges_cap, s);
     } else {
@@ -839,7 +858,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     cg_status st;
     if (pivot)
       st = pivot_steps(w.cells, w64, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un, edges,
-                       edges_cap, s);
+                       edges_cap, s, halves);
     else if (tree)
       st = tree_steps(w.cells, w64, ell, w.ctr, carve_treews(c, un, ell), un, edges, edges_cap,
                       s);
@@ -898,7 +917,7 @@ cg_status sort_cells_wide(WideWs& ww, int ell, int word_bits, void* cells, int64
   const unsigned int* skip = tried ? &ww.ctr->sorted : nullptr;
   uint32_t* sorted = nullptr;
   CG_CUDA(sort_wide(ww.keys64, w64, ell, ww.idx0, ww.idx1, ww.kw0, ww.kw1, &ww.ctr->n_unique,
-                    ucap, ww.radix, s, &sorted, skip),
+                    ucap, ww.radix, s, &sorted, skip, &ww.ctr->msort_done),
           "sorting cells");
   CG_CUDA(launch_gather_rows(ww.keys64, w64, sorted, &ww.ctr->n_unique, ucap, ww.cells, s, skip),
           "gathering cells");
@@ -916,7 +935,7 @@ cg_tune_params default_tune() { return cg_tune_params{CG_STRATEGY_HASH, 4, 0}; }
 cg_tune_params sanitize_tune(const cg_tune_params& p, int ell) {
   cg_tune_params q = p;
   if (q.strategy != CG_STRATEGY_SORTED && q.strategy != CG_STRATEGY_PIVOT &&
-      q.strategy != CG_STRATEGY_TREE)
+      q.strategy != CG_STRATEGY_TREE && q.strategy != CG_STRATEGY_HALVES)
     q.strategy = CG_STRATEGY_HASH;
   const int hmax = pivot_max_h(ell);
   q.pivots = q.pivots < 1 ? 1 : (q.pivots > hmax ? hmax : q.pivots);
@@ -940,7 +959,8 @@ ScenePlan plan_scene(int64_t n, int ell, size_t cap, const cg_tune_params& tp) {
 void carve_scene(Carve& c, const ScenePlan& p, DevCounters* ext_ctr, SmallWs* sw, WideWs* ww,
                  PivotWs* pw, TreeWs* tw) {
   const size_t un = size_t(p.n > 0 ? p.n : 1);
-  const bool pivot = p.tp.strategy == CG_STRATEGY_PIVOT;
+  const bool pivot =
+      p.tp.strategy == CG_STRATEGY_PIVOT || p.tp.strategy == CG_STRATEGY_HALVES;
   const bool tree = p.tp.strategy == CG_STRATEGY_TREE;
   const bool own = pivot || tree;  // the strategy brings its own search buffers
   if (p.small) *sw = carve_small(c, p.cap, p.ucap, p.ell, true, !own, false, un, ext_ctr);
@@ -1007,7 +1027,8 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   const int64_t n = plan.n;
   const int ell = plan.ell;
   const int strategy = plan.tp.strategy;
-  const bool pivot = strategy == CG_STRATEGY_PIVOT;
+  const bool halves = strategy == CG_STRATEGY_HALVES;
+  const bool pivot = strategy == CG_STRATEGY_PIVOT || halves;
   const bool tree = strategy == CG_STRATEGY_TREE;
   const bool own = pivot || tree;
   cg_status st;
@@ -1018,12 +1039,12 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     if (plan.small) {
       w.cells = w.sortbuf;
       if (pivot) return pivot_steps(w.cells, 1, ell, plan.tp.pivots, w.ctr, pw, plan.ucap, edges,
-                                    edges_cap, s);
+                                    edges_cap, s, halves);
       if (tree) return tree_steps(w.cells, 1, ell, w.ctr, tw, plan.ucap, edges, edges_cap, s);
       return neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
     }
     if (pivot) return pivot_steps(ww.cells, w64, ell, plan.tp.pivots, ww.ctr, pw, plan.ucap, edges,
-                                  edges_cap, s);
+                                  edges_cap, s, halves);
     if (tree) return tree_steps(ww.cells, w64, ell, ww.ctr, tw, plan.ucap, edges, edges_cap, s);
     WideTable it{ww.slots2, uint32_t(plan.cap - 1), nullptr, 0, ww.ctr};
     if (strategy != CG_STRATEGY_SORTED)
@@ -1067,7 +1088,7 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     if (st) return st;
     mark(ctx, "sort_number", s);
     st = pivot ? pivot_steps(w.cells, 1, ell, plan.tp.pivots, w.ctr, pw, plan.ucap, edges,
-                             edges_cap, s)
+                             edges_cap, s, halves)
          : tree ? tree_steps(w.cells, 1, ell, w.ctr, tw, plan.ucap, edges, edges_cap, s)
                 : neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
     if (st) return st;
@@ -1099,7 +1120,7 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     }
     mark(ctx, "dedup_sort", s);
     st = pivot ? pivot_steps(ww.cells, w64, ell, plan.tp.pivots, ww.ctr, pw, plan.ucap, edges,
-                             edges_cap, s)
+                             edges_cap, s, halves)
          : tree ? tree_steps(ww.cells, w64, ell, ww.ctr, tw, plan.ucap, edges, edges_cap, s)
                 : neighbors_wide_steps(ww, ell, strategy, edges, edges_cap, s);
     if (st) return st;
@@ -1919,8 +1940,9 @@ extern "C" cg_status cg_ctx_tune_set(cg_ctx* ctx, int bucket, const cg_tune_para
   if (!ctx || !p) return fail(CG_ERR_INVALID_ARG, "NULL argument");
   if (bucket < 0 || bucket >= CG_TUNE_BUCKETS) return fail(CG_ERR_INVALID_ARG, "no such bucket");
   if (p->strategy != CG_STRATEGY_HASH && p->strategy != CG_STRATEGY_SORTED &&
-      p->strategy != CG_STRATEGY_PIVOT && p->strategy != CG_STRATEGY_TREE)
-    return fail(CG_ERR_INVALID_ARG, "strategy must be HASH, SORTED, PIVOT or TREE");
+      p->strategy != CG_STRATEGY_PIVOT && p->strategy != CG_STRATEGY_TREE &&
+      p->strategy != CG_STRATEGY_HALVES)
+    return fail(CG_ERR_INVALID_ARG, "strategy must be HASH, SORTED, PIVOT, TREE or HALVES");
   if (p->pivots < 1 || p->pivots > 8) return fail(CG_ERR_INVALID_ARG, "pivots must be 1..8");
   if (p->sign_kernel != 0 && p->sign_kernel != 1)
     return fail(CG_ERR_INVALID_ARG, "sign_kernel must be 0 or 1");
@@ -1997,6 +2019,7 @@ extern "C" cg_status cg_ctx_autotune(cg_ctx* ctx, const cg_scene* scenes, int n_
     std::vector<cg_tune_params> cand = {{CG_STRATEGY_HASH, 4, 0},
                                         {CG_STRATEGY_SORTED, 4, 0},
                                         {CG_STRATEGY_TREE, 4, 0},
+                                        {CG_STRATEGY_HALVES, 4, 0},
                                         {CG_STRATEGY_PIVOT, 2, 0},
                                         {CG_STRATEGY_PIVOT, 3, 0},
                                         {CG_STRATEGY_PIVOT, 4, 0}};

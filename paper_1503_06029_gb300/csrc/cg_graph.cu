@@ -1030,10 +1030,10 @@ cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const W
 cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
                       void* scratch, cudaStream_t s, uint32_t** sorted_idx,
-                      const unsigned int* skip) {
+                      const unsigned int* skip, unsigned int* flag) {
   (void)scratch;
   return merge_sort_rows(keys, w64, ell, idx0, kw0, kw1, idx0, idx1, n_dev, max_n, s,
-                         sorted_idx, skip);
+                         sorted_idx, skip, flag);
 }
 
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,

@@ -27,7 +27,9 @@ struct DevCounters {
   unsigned int ticket;        // work counter of the single-pass edge kernel
   unsigned int tc_spill;      // tiles the tensor-core sign kernel left to the fp32 one
   unsigned int sorted;        // 1: the one-cluster sort handled the distinct vectors
-  unsigned int pad[6];
+  unsigned int msort_done;    // wide-row merge sort: nonzero when every run of equal
+                              // cached keys was ordered without the full-row pass
+  unsigned int pad[5];
 };
 
 // Bits of DevCounters::error.
@@ -210,11 +212,15 @@ cudaError_t radix_sort_u64(uint64_t* keys0, uint64_t* keys1, uint32_t* vals0, ui
 // on row numbers with the top 128 bits cached; k0/k1 (2 * max_n words each)
 // and i0/i1 (max_n) are ping-pong buffers; *sorted_idx receives the buffer
 // holding the sorted row numbers. With skip != nullptr, every kernel does
-// nothing when *skip is nonzero.
+// nothing when *skip is nonzero. For l > 128 with flag != nullptr (a device
+// word), the rows are sorted by the cached key alone and every short run of
+// equal keys is then ordered by one warp; the full-row comparison sort runs
+// only when some run is too long for that (flag records which).
 cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32_t* idx_in,
                             uint64_t* k0, uint64_t* k1, uint32_t* i0, uint32_t* i1,
                             const unsigned int* n_dev, size_t max_n, cudaStream_t s,
-                            uint32_t** sorted_idx, const unsigned int* skip = nullptr);
+                            uint32_t** sorted_idx, const unsigned int* skip = nullptr,
+                            unsigned int* flag = nullptr);
 
 // Batch sort: the distinct vectors of many scenes sorted together, scene by
 // scene (one merge sort on (scene, top 128 bits, whole vector)), then
@@ -339,7 +345,7 @@ cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const W
 cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
                       void* scratch, cudaStream_t s, uint32_t** sorted_idx,
-                      const unsigned int* skip = nullptr);
+                      const unsigned int* skip = nullptr, unsigned int* flag = nullptr);
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,
                                const unsigned int* n_dev, size_t max_n, uint64_t* out,
                                cudaStream_t s, const unsigned int* skip = nullptr);
@@ -382,6 +388,23 @@ cudaError_t launch_pivot_index(const uint64_t* skeys, const DevCounters* ctr, si
 // Search + scan + edge output (ctr->n_edges = E); hbuf: pivot_hit_words(max_n)
 // words; scan: scan_scratch_bytes(max_n).
 size_t pivot_hit_words(size_t max_n);
+
+// HALVES strategy (cg_pivot.cu): the l bits split at s = halves_split(l);
+// keys, a stable sort of (L key, cell) over halves_sort_bits(l) bits, then the
+// search and edge output. Uses the PIVOT workspace: hkey in key_by_cell, the
+// folds fl and fh in the bucket-table memory, sfh in the sort's spare key
+// buffer.
+int halves_split(int ell);
+int halves_sort_bits(int ell);
+cudaError_t launch_halves_keys(const uint64_t* cells, int w64, int ell, const DevCounters* ctr,
+                               size_t max_n, uint64_t* hkey, uint64_t* fl, uint64_t* fh,
+                               uint64_t* lkey, uint32_t* idx, cudaStream_t s);
+cudaError_t launch_halves_edges(const uint64_t* cells, int w64, int ell, DevCounters* ctr,
+                                size_t max_n, const uint64_t* hkey, const uint64_t* fl,
+                                const uint64_t* fh, const uint64_t* skey, const uint32_t* sidx,
+                                uint64_t* sfh, uint32_t* counts, uint32_t* hbuf,
+                                unsigned long long* offsets, uint32_t* fill, void* scan,
+                                uint32_t* edges, int64_t edges_cap, cudaStream_t s);
 cudaError_t launch_pivot_edges(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
                                size_t max_n, const uint64_t* key_by_cell, const uint32_t* sidx,
                                const void* table, size_t tcap, uint32_t* counts, uint32_t* hbuf,

@@ -20,6 +20,9 @@
 //
 // Pivots: h cells spread over the sorted order (cells floor((2d+1) U / 2h)),
 // so that they are far apart in value; the choice does not change the output.
+//
+// This file also holds the HALVES strategy (two-part multi-index hashing,
+// described below), which shares the hit buffer, scan and ordered output.
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -123,13 +126,34 @@ __device__ __forceinline__ uint64_t bucket_find(const ulonglong2* table, uint32_
 // P = 2^h patterns, a warp takes 32 / P consecutive cells (P <= 32) or one
 // cell with the patterns strided over the lanes (P > 32). Each lane looks its
 // bucket up and compares every candidate j > i of it with cell i, word by
-// word (XOR + popcount, stopping at the second difference).
+// word (XOR + popcount, stopping at the second difference). (A 64-bit fold
+// filter in bucket order, as HALVES uses, was measured slower here: the
+// search is bound by its chain of dependent loads, not by their bytes.)
 //   kCount: counts[i] = number of hits of cell i; the first kHitBuf partners
 //           are kept in hbuf[i][.].
 //   kWrite: cells with more than kHitBuf hits only: hit (i, j) goes to
 //           edges[offsets[i] + fill[i]++] (positions below cap only).
 constexpr int kHitBuf = 4;
 enum { kCount = 0, kWrite = 1 };
+
+// Records the hit (i, j), i < j, of a search pass (see above).
+template <int kMode>
+__device__ __forceinline__ void record_hit(uint32_t i, uint32_t j, uint32_t* __restrict__ counts,
+                                           uint32_t* __restrict__ hbuf,
+                                           const unsigned long long* __restrict__ offsets,
+                                           uint32_t* __restrict__ fill,
+                                           uint32_t* __restrict__ edges, int64_t cap) {
+  if (kMode == kCount) {
+    const uint32_t r = atomicAdd(&counts[i], 1u);
+    if (r < uint32_t(kHitBuf)) hbuf[uint64_t(i) * kHitBuf + r] = j;
+  } else {
+    const unsigned long long pos = offsets[i] + atomicAdd(&fill[i], 1u);
+    if (pos < (unsigned long long)cap) {
+      edges[2 * pos] = i;
+      edges[2 * pos + 1] = j;
+    }
+  }
+}
 
 template <int kMode>
 __global__ void __launch_bounds__(kThreads)
@@ -174,16 +198,146 @@ __global__ void __launch_bounds__(kThreads)
         int c = 0;
         for (int q = 0; q < w && c < 2; ++q) c += __popcll(xj[q] ^ xi[q]);
         if (c != 1) continue;
-        if (kMode == kCount) {
-          const uint32_t r = atomicAdd(&counts[i], 1u);
-          if (r < uint32_t(kHitBuf)) hbuf[uint64_t(i) * kHitBuf + r] = j;
-        } else {
-          const unsigned long long pos = offsets[i] + atomicAdd(&fill[i], 1u);
-          if (pos < (unsigned long long)cap) {
-            edges[2 * pos] = i;
-            edges[2 * pos + 1] = j;
-          }
-        }
+        record_hit<kMode>(i, j, counts, hbuf, offsets, fill, edges, cap);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// HALVES lookup strategy: the pigeonhole split of multi-index hashing
+// (Norouzi, Punjani, Fleet, "Fast search in Hamming space with multi-index
+// hashing", CVPR 2012) with two parts. Split the l bits at s = floor(l / 2)
+// into L = bits [0, s) and H = bits [s, l). Two vectors at distance 1 agree
+// exactly on one part:
+//   * pairs that differ in L have equal H. In value order the cells are
+//     sorted by H first, so these partners are in the same run of equal H,
+//     contiguous in the cell array: cell i scans i + 1, i + 2, ... while the
+//     H keys match;
+//   * pairs that differ in H have equal L. (key of L, cell number) pairs are
+//     sorted stably by an LSD radix sort, so equal L values form runs in
+//     which cell numbers increase; a cell scans the rest of its run.
+// Each group checks its own case exactly (H equal and one differing bit in L,
+// resp. L equal and one differing bit in H), so every edge is found once,
+// from its smaller endpoint, whatever the keys collide on. For one-word cells
+// the keys are the parts themselves and the tests need no row; for wider
+// cells the keys are hashes, and the fold of the other part (XOR of its
+// masked words) rejects nearly every non-partner before the rows are read.
+// Work is the sum of squared run lengths: O(U) when runs are short (random
+// and clustered vectors), up to U^1.5 for the hypercube.
+// ---------------------------------------------------------------------------
+
+// Mask of the bits of word q that lie in L = [0, s).
+__device__ __forceinline__ uint64_t low_mask(int q, int s) {
+  const int lo = 64 * q;
+  if (s >= lo + 64) return ~0ull;
+  if (s <= lo) return 0ull;
+  return (1ull << (s - lo)) - 1;
+}
+
+// Rows x and y agree on one part and differ in exactly one bit of the other
+// (L when in_low, else H).
+__device__ __forceinline__ bool one_bit_in_part(const uint64_t* __restrict__ x,
+                                                const uint64_t* __restrict__ y, int w, int s,
+                                                bool in_low) {
+  int c = 0;
+  for (int q = 0; q < w; ++q) {
+    const uint64_t d = x[q] ^ y[q];
+    const uint64_t m = low_mask(q, s);
+    if (d & (in_low ? ~m : m)) return false;
+    c += __popcll(d);
+    if (c > 1) return false;
+  }
+  return c == 1;
+}
+
+// Per cell: hkey (H itself for one word, else a 64-bit hash of H), the folds
+// fL and fH of the two parts, the sort key of L (L itself for one word, else
+// a 32-bit hash) and the identity permutation.
+__global__ void __launch_bounds__(kThreads)
+    halves_keys(const uint64_t* __restrict__ cells, int w, int s, const DevCounters* ctr,
+                uint32_t max_n, uint64_t* __restrict__ hkey, uint64_t* __restrict__ fl,
+                uint64_t* __restrict__ fh, uint64_t* __restrict__ lkey,
+                uint32_t* __restrict__ idx) {
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
+    const uint64_t* x = cells + uint64_t(i) * w;
+    if (w == 1) {
+      const uint64_t m = low_mask(0, s);
+      hkey[i] = x[0] & ~m;
+      fh[i] = x[0] & ~m;
+      fl[i] = x[0] & m;
+      lkey[i] = x[0] & m;
+    } else {
+      uint64_t hh = 0, hl = 0, a = 0, b = 0;
+      for (int q = 0; q < w; ++q) {
+        const uint64_t m = low_mask(q, s);
+        const uint64_t lo = x[q] & m, hi = x[q] & ~m;
+        const uint64_t salt = 0x9e3779b97f4a7c15ull * uint64_t(q + 1);
+        a ^= lo;
+        b ^= hi;
+        hl ^= mix64(lo + salt);
+        hh ^= mix64(hi + salt);
+      }
+      hkey[i] = hh;
+      fl[i] = a;
+      fh[i] = b;
+      lkey[i] = hl & 0xffffffffull;
+    }
+    idx[i] = i;
+  }
+}
+
+// sfh[t] = fh[sidx[t]]: the H fold of the cell at sorted position t.
+__global__ void __launch_bounds__(kThreads)
+    halves_gather(const DevCounters* ctr, uint32_t max_n, const uint32_t* __restrict__ sidx,
+                  const uint64_t* __restrict__ fh, uint64_t* __restrict__ sfh) {
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < u; t += gridDim.x * blockDim.x)
+    sfh[t] = fh[sidx[t]];
+}
+
+// Items g < U: cell g's partners in its run of equal H; items U + t: the
+// partners of the cell at sorted position t in its run of equal L.
+template <int kMode>
+__global__ void __launch_bounds__(kThreads)
+    halves_search(const uint64_t* __restrict__ cells, int w, int s, const DevCounters* ctr,
+                  uint32_t max_n, const uint64_t* __restrict__ hkey,
+                  const uint64_t* __restrict__ fl, const uint64_t* __restrict__ skey,
+                  const uint32_t* __restrict__ sidx, const uint64_t* __restrict__ sfh,
+                  uint32_t* __restrict__ counts, uint32_t* __restrict__ hbuf,
+                  const unsigned long long* __restrict__ offsets, uint32_t* __restrict__ fill,
+                  uint32_t* __restrict__ edges, int64_t cap) {
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  const uint64_t items = 2ull * u;
+  for (uint64_t g = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; g < items;
+       g += uint64_t(gridDim.x) * blockDim.x) {
+    if (g < u) {
+      const uint32_t i = uint32_t(g);
+      if (kMode == kWrite && counts[i] <= uint32_t(kHitBuf)) continue;
+      const uint64_t hk = hkey[i], f = fl[i];
+      for (uint32_t j = i + 1; j < u && hkey[j] == hk; ++j) {
+        if (__popcll(fl[j] ^ f) != 1) continue;
+        if (w > 1 &&
+            !one_bit_in_part(cells + uint64_t(i) * w, cells + uint64_t(j) * w, w, s, true))
+          continue;
+        record_hit<kMode>(i, j, counts, hbuf, offsets, fill, edges, cap);
+      }
+    } else {
+      const uint32_t t = uint32_t(g - u);
+      const uint32_t i = sidx[t];
+      if (kMode == kWrite && counts[i] <= uint32_t(kHitBuf)) continue;
+      const uint64_t k = skey[t], f = sfh[t];
+      for (uint32_t t2 = t + 1; t2 < u && skey[t2] == k; ++t2) {
+        if (__popcll(sfh[t2] ^ f) != 1) continue;
+        const uint32_t j = sidx[t2];
+        if (w > 1 &&
+            !one_bit_in_part(cells + uint64_t(i) * w, cells + uint64_t(j) * w, w, s, false))
+          continue;
+        record_hit<kMode>(i, j, counts, hbuf, offsets, fill, edges, cap);
       }
     }
   }
@@ -293,11 +447,42 @@ cudaError_t launch_pivot_index(const uint64_t* skeys, const DevCounters* ctr, si
   return cudaGetLastError();
 }
 
+namespace {
+
+// Count pass, scan of the counts, edges of the cells whose hits fit the hit
+// buffer, write pass for the others, their ordering: shared by PIVOT and
+// HALVES. search(mode) launches the strategy's search pass.
+template <class Search>
+cudaError_t hits_to_edges(DevCounters* ctr, size_t max_n, uint32_t* counts, uint32_t* hbuf,
+                          unsigned long long* offsets, uint32_t* fill, void* scan,
+                          uint32_t* edges, int64_t edges_cap, cudaStream_t s, Search search) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, max_n * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, max_n * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  search(kCount);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = scan_exclusive_u32(counts, offsets, &ctr->n_unique, max_n, &ctr->n_edges, scan, s);
+  if (e != cudaSuccess) return e;
+  pivot_emit<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(ctr, uint32_t(max_n), counts, hbuf,
+                                                            offsets, edges, edges_cap);
+  count_launch();
+  search(kWrite);
+  count_launch();
+  pivot_order<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(ctr, uint32_t(max_n), counts,
+                                                             offsets, edges, edges_cap);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_pivot_edges(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
                                size_t max_n, const uint64_t* key_by_cell, const uint32_t* sidx,
-                               const void* table, size_t tcap, uint32_t* counts, uint32_t* hbuf,
-                               unsigned long long* offsets, uint32_t* fill, void* scan,
-                               uint32_t* edges, int64_t edges_cap, cudaStream_t s) {
+                               const void* table, size_t tcap,
+                               uint32_t* counts, uint32_t* hbuf, unsigned long long* offsets,
+                               uint32_t* fill, void* scan, uint32_t* edges, int64_t edges_cap,
+                               cudaStream_t s) {
   if (max_n == 0) return cudaSuccess;
   if (w64 > kMaxW) return cudaErrorInvalidValue;
   const int P = 1 << h;
@@ -307,27 +492,58 @@ cudaError_t launch_pivot_edges(const uint64_t* cells, int w64, int ell, int h, D
   const uint32_t tmask = uint32_t(tcap - 1);
   const int tshift = table_shift(tcap);
   const int bits = key_bits(ell);
-  cudaError_t e = cudaMemsetAsync(counts, 0, max_n * sizeof(uint32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, max_n * sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  pivot_search<kCount><<<g, kThreads, 0, s>>>(cells, w64, ell, h, bits, ctr, uint32_t(max_n),
-                                              key_by_cell, sidx, tb, tmask, tshift, counts, hbuf,
-                                              nullptr, nullptr, nullptr, 0);
-  count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = scan_exclusive_u32(counts, offsets, &ctr->n_unique, max_n, &ctr->n_edges, scan, s);
-  if (e != cudaSuccess) return e;
-  pivot_emit<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(ctr, uint32_t(max_n), counts, hbuf,
-                                                            offsets, edges, edges_cap);
-  count_launch();
-  pivot_search<kWrite><<<g, kThreads, 0, s>>>(cells, w64, ell, h, bits, ctr, uint32_t(max_n),
-                                              key_by_cell, sidx, tb, tmask, tshift, counts, hbuf,
-                                              offsets, fill, edges, edges_cap);
-  count_launch();
-  pivot_order<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(ctr, uint32_t(max_n), counts,
-                                                             offsets, edges, edges_cap);
+  return hits_to_edges(ctr, max_n, counts, hbuf, offsets, fill, scan, edges, edges_cap, s,
+                       [&](int mode) {
+                         if (mode == kCount)
+                           pivot_search<kCount><<<g, kThreads, 0, s>>>(
+                               cells, w64, ell, h, bits, ctr, uint32_t(max_n), key_by_cell, sidx,
+                               tb, tmask, tshift, counts, hbuf, nullptr, nullptr, nullptr,
+                               0);
+                         else
+                           pivot_search<kWrite><<<g, kThreads, 0, s>>>(
+                               cells, w64, ell, h, bits, ctr, uint32_t(max_n), key_by_cell, sidx,
+                               tb, tmask, tshift, counts, hbuf, offsets, fill, edges,
+                               edges_cap);
+                       });
+}
+
+int halves_split(int ell) { return ell / 2; }
+
+int halves_sort_bits(int ell) { return ell <= 64 ? halves_split(ell) : 32; }
+
+cudaError_t launch_halves_keys(const uint64_t* cells, int w64, int ell, const DevCounters* ctr,
+                               size_t max_n, uint64_t* hkey, uint64_t* fl, uint64_t* fh,
+                               uint64_t* lkey, uint32_t* idx, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  halves_keys<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(
+      cells, w64, halves_split(ell), ctr, uint32_t(max_n), hkey, fl, fh, lkey, idx);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_halves_edges(const uint64_t* cells, int w64, int ell, DevCounters* ctr,
+                                size_t max_n, const uint64_t* hkey, const uint64_t* fl,
+                                const uint64_t* fh, const uint64_t* skey, const uint32_t* sidx,
+                                uint64_t* sfh, uint32_t* counts, uint32_t* hbuf,
+                                unsigned long long* offsets, uint32_t* fill, void* scan,
+                                uint32_t* edges, int64_t edges_cap, cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const int sp = halves_split(ell);
+  halves_gather<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(ctr, uint32_t(max_n), sidx, fh,
+                                                               sfh);
+  count_launch();
+  const int g = grid_for(2 * max_n, kThreads);
+  return hits_to_edges(ctr, max_n, counts, hbuf, offsets, fill, scan, edges, edges_cap, s,
+                       [&](int mode) {
+                         if (mode == kCount)
+                           halves_search<kCount><<<g, kThreads, 0, s>>>(
+                               cells, w64, sp, ctr, uint32_t(max_n), hkey, fl, skey, sidx, sfh,
+                               counts, hbuf, nullptr, nullptr, nullptr, 0);
+                         else
+                           halves_search<kWrite><<<g, kThreads, 0, s>>>(
+                               cells, w64, sp, ctr, uint32_t(max_n), hkey, fl, skey, sidx, sfh,
+                               counts, hbuf, offsets, fill, edges, edges_cap);
+                       });
 }
 
 size_t pivot_hit_words(size_t max_n) { return max_n * kHitBuf; }

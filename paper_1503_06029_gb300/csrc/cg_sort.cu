@@ -738,6 +738,96 @@ cudaError_t run_merge_sort(const Ord& ord, ulonglong2* k0, ulonglong2* k1,
   return cudaGetLastError();
 }
 
+// Run fix-up after the key-only sort of rows longer than the cached key.
+// A warp takes 32 sorted positions; for every run of equal keys that starts
+// there (runs end where the key changes, so they are contiguous), it stages
+// the run's rows in shared memory (stride w + 1 words, so that lanes reading
+// the same word of different rows hit different banks), gives every row its
+// rank among the run's rows by full comparison (rows are distinct, so the
+// ranks are a permutation), and writes the row numbers back in that order.
+// A run longer than the warp's share of shared memory holds clears *flag,
+// which makes the full-row comparison sort run afterwards.
+constexpr int kFixWarps = 8;
+constexpr int kFixWords = 1024;  // shared-memory words per warp
+constexpr int kFixMaxRun = 64;   // at most two rows per lane
+
+__device__ __forceinline__ bool srow_less(const uint64_t* a, const uint64_t* b, int w) {
+  for (int q = w - 1; q >= 0; --q)
+    if (a[q] != b[q]) return a[q] < b[q];
+  return false;
+}
+
+__device__ __forceinline__ bool same_key(const ulonglong2& a, const ulonglong2& b) {
+  return a.x == b.x && a.y == b.y;
+}
+
+__global__ void __launch_bounds__(kFixWarps * 32)
+    msort_fix_runs(const ulonglong2* __restrict__ keys, uint32_t* idx,
+                   const uint64_t* __restrict__ rows, int w, const unsigned int* n_dev,
+                   uint32_t max_n, unsigned int* flag, const unsigned int* skip) {
+  extern __shared__ uint64_t fix_sm[];
+  if (skip && *skip) return;
+  const uint32_t n = min(*n_dev, max_n);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint64_t* sr = fix_sm + size_t(wid) * kFixWords;
+  const int stride = w + 1;
+  const uint32_t max_run = uint32_t(min(kFixMaxRun, kFixWords / stride));
+  const uint32_t chunks = (n + 31) / 32;
+  for (uint32_t c = blockIdx.x * kFixWarps + wid; c < chunks; c += gridDim.x * kFixWarps) {
+    const uint32_t t = c * 32 + lane;
+    bool start = false;
+    if (t < n) {
+      const ulonglong2 k = keys[t];
+      start = t + 1 < n && same_key(keys[t + 1], k) && !(t > 0 && same_key(keys[t - 1], k));
+    }
+    uint32_t starts = __ballot_sync(0xffffffffu, start);
+    while (starts) {
+      const uint32_t s0 = c * 32 + uint32_t(__ffs(starts) - 1);
+      starts &= starts - 1;
+      const ulonglong2 k0 = keys[s0];
+      uint32_t m = 1;  // run = [s0, s0 + m)
+      for (uint32_t base = s0 + 1;; base += 32) {
+        const uint32_t p = base + lane;
+        const uint32_t eq = __ballot_sync(0xffffffffu, p < n && same_key(keys[p], k0));
+        const uint32_t lead = eq == 0xffffffffu ? 32u : uint32_t(__ffs(~eq) - 1);
+        m += lead;
+        if (lead < 32 || m > max_run) break;
+      }
+      if (m > max_run) {
+        if (lane == 0) *flag = 0u;
+        continue;
+      }
+      uint32_t mine[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t a = uint32_t(lane) + 32u * j;
+        mine[j] = a < m ? idx[s0 + a] : 0u;
+      }
+      for (uint32_t e = lane; e < m * uint32_t(w); e += 32) {
+        const uint32_t a = e / uint32_t(w), q = e - a * uint32_t(w);
+        sr[a * stride + q] = rows[uint64_t(idx[s0 + a]) * w + q];
+      }
+      __syncwarp();
+      uint32_t rank[2] = {0u, 0u};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t a = uint32_t(lane) + 32u * j;
+        if (a < m)
+          for (uint32_t b = 0; b < m; ++b)
+            rank[j] += (b != a && srow_less(sr + b * stride, sr + a * stride, w)) ? 1u : 0u;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t a = uint32_t(lane) + 32u * j;
+        if (a < m) idx[s0 + rank[j]] = mine[j];
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // ------------------------------ batch sort ---------------------------------
 
 __global__ void __launch_bounds__(1024)
@@ -962,16 +1052,48 @@ cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigne
 cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32_t* idx_in,
                             uint64_t* k0, uint64_t* k1, uint32_t* i0, uint32_t* i1,
                             const unsigned int* n_dev, size_t max_n, cudaStream_t s,
-                            uint32_t** sorted_idx, const unsigned int* skip) {
+                            uint32_t** sorted_idx, const unsigned int* skip,
+                            unsigned int* flag) {
   *sorted_idx = i0;
   if (max_n == 0) return cudaSuccess;
   if (ell <= 64) return cudaErrorInvalidValue;
-  const RowOrder ord{rows, w64, ell, ell <= 128, idx_in};
+  ulonglong2* kk0 = reinterpret_cast<ulonglong2*>(k0);
+  ulonglong2* kk1 = reinterpret_cast<ulonglong2*>(k1);
   bool in1 = false;
-  cudaError_t e = run_merge_sort(ord, reinterpret_cast<ulonglong2*>(k0),
-                                 reinterpret_cast<ulonglong2*>(k1), i0, i1, n_dev, max_n, s, &in1,
-                                 skip);
-  *sorted_idx = in1 ? i1 : i0;
+  if (ell <= 128 || !flag) {
+    const RowOrder ord{rows, w64, ell, ell <= 128, idx_in};
+    cudaError_t e = run_merge_sort(ord, kk0, kk1, i0, i1, n_dev, max_n, s, &in1, skip);
+    *sorted_idx = in1 ? i1 : i0;
+    return e;
+  }
+  // Rows longer than the cached key. Sorting on the key alone (ties in
+  // row-number order) reads no row; each run of rows sharing their top 128
+  // bits is then put in row order by one warp. Only when a run is too long
+  // for that does the full-row comparison sort run (its kernels return at
+  // once while *flag is nonzero). Both sorts make the same number of passes,
+  // so their results land in the same buffer.
+  cudaError_t e = cudaMemsetAsync(flag, 1, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  const RowOrder by_key{rows, w64, ell, true, idx_in};
+  e = run_merge_sort(by_key, kk0, kk1, i0, i1, n_dev, max_n, s, &in1, skip);
+  if (e != cudaSuccess) return e;
+  uint32_t* out = in1 ? i1 : i0;
+  const size_t smem = size_t(kFixWarps) * kFixWords * sizeof(uint64_t);
+  if ((e = ensure_smem_limit(reinterpret_cast<const void*>(msort_fix_runs), smem)) !=
+      cudaSuccess)
+    return e;
+  const size_t chunks = (max_n + 31) / 32;
+  const int g = int(std::max<size_t>(
+      1, std::min<size_t>((chunks + kFixWarps - 1) / kFixWarps, size_t(sm_count()) * 3)));
+  msort_fix_runs<<<g, kFixWarps * 32, smem, s>>>(in1 ? kk1 : kk0, out, rows, w64, n_dev,
+                                                 uint32_t(max_n), flag, skip);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const RowOrder full{rows, w64, ell, false, out};
+  bool in1b = false;
+  e = run_merge_sort(full, kk0, kk1, i0, i1, n_dev, max_n, s, &in1b, flag);
+  if (in1b != in1) return cudaErrorUnknown;  // the pass counts differ: cannot happen
+  *sorted_idx = out;
   return e;
 }
 

@@ -162,6 +162,33 @@ def test_dedup_matches_oracle(dev, kind, wb):
     assert np.array_equal(pc.cpu().numpy().view(np.uint32), want_pc)
 
 
+@pytest.mark.parametrize("ell,runs", [(1024, [2, 3, 31, 32, 33, 59, 60]), (1024, [2, 61]),
+                                      (1024, [2, 5, 200]), (4096, [2, 14, 15]),
+                                      (4096, [3, 16]), (200, [2, 40, 64]), (200, [65, 300])])
+def test_dedup_runs_sharing_the_top_bits(dev, ell, runs):
+    """Rows longer than the cached 128-bit key that share their top 128 bits
+    in runs of the given lengths (shuffled, with duplicates): short runs are
+    ordered by one warp each, a run longer than a warp's share of shared
+    memory sends the whole sort through the full-row comparison pass."""
+    rng = np.random.default_rng(ell + len(runs))
+    w = (ell + 63) // 64
+    rows = []
+    for m in runs:
+        top = rng.integers(0, 2**63, size=w, dtype=np.int64).astype(np.uint64)
+        if ell % 64:
+            top[-1] &= np.uint64((1 << (ell % 64)) - 1)
+        for _ in range(m):
+            r = top.copy()
+            r[: w - 2] = rng.integers(0, 2**63, size=w - 2, dtype=np.int64).astype(np.uint64)
+            r[w - 3] &= np.uint64(0xFF)  # runs differ only far below the top
+            rows.append(r)
+    keys = np.stack(rows)
+    keys = np.concatenate([keys, keys[rng.choice(len(keys), size=len(keys) // 3)]])
+    keys = keys[rng.permutation(len(keys))]
+    cells = cellgraph.dedup_cells(words_dev(keys, 64, dev), ell, 64)
+    assert np.array_equal(words_np(cells, 64), oracle.dedup(keys, ell, 64))
+
+
 def test_dedup_all_duplicates_and_empty(dev):
     keys = np.full((5000, 1), 12345, dtype=np.uint64)
     cells = cellgraph.dedup_cells(words_dev(keys, 64, dev), 20, 64)
@@ -172,7 +199,7 @@ def test_dedup_all_duplicates_and_empty(dev):
 
 # ------------------------------ steps 3-4 --------------------------------
 
-@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree"])
+@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree", "halves"])
 @pytest.mark.parametrize("kind,wb", [("lines", 32), ("planes64", 64), ("planes200", 64),
                                      ("planes200", 32), ("chains", 64), ("chains130", 64)])
 def test_neighbors_match_oracle(dev, kind, wb, strategy):
@@ -184,7 +211,7 @@ def test_neighbors_match_oracle(dev, kind, wb, strategy):
     assert len(want) > 0
 
 
-@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree"])
+@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree", "halves"])
 def test_neighbors_hypercube(dev, strategy):
     ell = 12
     cells = np.arange(1 << ell, dtype=np.uint64).reshape(-1, 1)
@@ -216,6 +243,39 @@ def test_neighbors_tree_degenerate_shapes(dev):
         assert np.array_equal(edges_np(got), want), ell
 
 
+@pytest.mark.parametrize("ell", [1, 2, 3, 17, 63, 64, 65, 127, 128, 129, 200, 1030])
+def test_neighbors_halves_split_positions(dev, ell):
+    """HALVES splits the bits at s = l // 2: partners that differ just below
+    and just above s, at bit 0 and at bit l - 1, inside one word and across
+    word boundaries, plus cells that agree on one part with many others (long
+    runs) and random rows."""
+    rng = np.random.default_rng(ell)
+    w = (ell + 63) // 64
+    s = ell // 2
+
+    def row(v):
+        return [(v >> (64 * q)) & ((1 << 64) - 1) for q in range(w)]
+
+    vals = set()
+    for _ in range(200):
+        base = int(rng.integers(0, 2**62)) | (int(rng.integers(0, 2**62)) << 62)
+        base |= int(rng.integers(0, 2**62)) << 124
+        base &= (1 << ell) - 1
+        vals.add(base)
+        for k in {0, ell - 1, max(s - 1, 0), min(s, ell - 1), min(s + 1, ell - 1),
+                  int(rng.integers(0, ell))}:
+            vals.add(base ^ (1 << k))
+    hi = int(rng.integers(0, 2**62)) << s & ((1 << ell) - 1)
+    for lo in range(min(1 << s, 64)):  # one run of equal high part
+        vals.add(hi | lo)
+    cells = np.array([row(v) for v in sorted(vals)], dtype=np.uint64)
+    want = oracle.neighbors(cells, ell, 64)
+    got = cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64, strategy="halves")
+    assert np.array_equal(edges_np(got), want)
+    if ell > 2:
+        assert len(want) > 0
+
+
 def test_neighbors_pivot_wide_4096(dev):
     """The longest vectors (l = 4096, 64 words): random rows plus one-bit
     variants at every word position."""
@@ -231,7 +291,7 @@ def test_neighbors_pivot_wide_4096(dev):
     cells = oracle.dedup(keys, ell, 64)
     want = oracle.neighbors(cells, ell, 64)
     assert len(want) > 50
-    for strategy in ("hash", "sorted", "pivot", "tree"):
+    for strategy in ("hash", "sorted", "pivot", "tree", "halves"):
         got = cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64, strategy=strategy)
         assert np.array_equal(edges_np(got), want), strategy
 
@@ -463,7 +523,7 @@ def test_full_size_chains(dev):
     cells = cellgraph.dedup_cells(keys_d, 1024, 64)
     del keys_d
     edges = cellgraph.neighbors_h1(cells, 1024, 64)
-    for strategy in ("pivot", "tree"):
+    for strategy in ("pivot", "tree", "halves"):
         other = cellgraph.neighbors_h1(cells, 1024, 64, strategy=strategy)
         assert torch.equal(other, edges), strategy
         del other
@@ -599,7 +659,7 @@ def _tuning_scenes():
 
 @pytest.mark.parametrize("setting", [("hash", 4, 0), ("sorted", 4, 0), ("pivot", 1, 0),
                                      ("pivot", 3, 0), ("pivot", 4, 1), ("hash", 4, 1),
-                                     ("tree", 4, 0)])
+                                     ("tree", 4, 0), ("halves", 4, 0)])
 def test_build_under_every_tuning(dev, setting):
     strategy, pivots, sk = setting
     c2 = cellgraph.Context(0)
