@@ -13,6 +13,9 @@ the Cell Graph":
 * ``dedup``       §3.2: sort the vectors and drop duplicates.
 * ``neighbors``   §2.2 definition of G_X, searched as in Algorithm 4
                   (flip one bit, look the result up).
+* ``heuristic``   §3.1, Algorithms 1-2: pivot distances, inequality (⋆),
+                  segment-wise comparison of the remaining pairs.
+* ``tree``        §3.2, Algorithms 3-4: the 2^r-ary search tree and its walk.
 * ``build``       the three steps for one scene.
 
 Pins (tests that tie these functions to something other than themselves) are in
@@ -58,8 +61,10 @@ def _load():
             lib.cgo_neighbors_h1.argtypes = [P, I64, I, I, P, I64, P]
             lib.cgo_tree.argtypes = [P, I64, I, I, I, I, P, I, P, I64, P]
             lib.cgo_tree_digits.argtypes = [P, I64, I, I, I, I, P]
+            lib.cgo_heuristic.argtypes = [P, I64, I, I, I, I, I, P, I64, P, P]
             for f in (lib.cgo_pack_signs, lib.cgo_dedup, lib.cgo_neighbors_h1_rows,
-                      lib.cgo_neighbors_h1, lib.cgo_tree, lib.cgo_tree_digits):
+                      lib.cgo_neighbors_h1, lib.cgo_tree, lib.cgo_tree_digits,
+                      lib.cgo_heuristic):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -141,6 +146,28 @@ def neighbors(cells, ell: int, word_bits: int = 64, rows=None) -> np.ndarray:
         if rc:
             raise RuntimeError(f"cgo_neighbors_h1 failed: {rc}")
         return edges[: ne.value].copy()
+
+
+def heuristic(cells, ell: int, word_bits: int = 64, h: int = 4, w: int = 32,
+              as_printed: bool = False):
+    """Edges by the heuristic of §3.1 (Algorithms 1-2) with the first h cells
+    as pivots and w-segment comparison: (edges uint32[E][2], pairs that passed
+    the pivot test). as_printed applies Algorithm 2's test as printed ("> 1"),
+    which the oracle reads as inverted."""
+    lib = _load()
+    cells = np.ascontiguousarray(cells)
+    u = cells.shape[0]
+    ne, nt = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib.cgo_heuristic(_ptr(cells), u, ell, word_bits, h, w, int(as_printed), None, 0,
+                           ctypes.byref(ne), ctypes.byref(nt))
+    if rc not in (0, -2):
+        raise RuntimeError(f"cgo_heuristic failed: {rc}")
+    out = np.zeros((ne.value, 2), np.uint32)
+    rc = lib.cgo_heuristic(_ptr(cells), u, ell, word_bits, h, w, int(as_printed), _ptr(out),
+                           ne.value, ctypes.byref(ne), ctypes.byref(nt))
+    if rc != 0:
+        raise RuntimeError(f"cgo_heuristic failed: {rc}")
+    return out, int(nt.value)
 
 
 def tree(cells, ell: int, word_bits: int = 64, r: int = 8, order: int = 0, edges: bool = True):

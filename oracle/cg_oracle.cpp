@@ -18,7 +18,10 @@
 //      and every bit k, the vector x with bit k negated is looked up among the
 //      cells; a hit is an edge. Each unordered pair is reported once (§2.2
 //      asks for pairs i < j, duplicates in X must not repeat pairs).
-//   4. The search tree of §3.2 (Algorithm 3 build, Algorithm 4 walk): the
+//   4. The heuristic of §3.1 (Algorithms 1-2): distances to h pivot vectors,
+//      inequality (⋆) to skip pairs, a segment-wise comparison of the rest; a
+//      second, independent way to the same edges.
+//   5. The search tree of §3.2 (Algorithm 3 build, Algorithm 4 walk): the
 //      2^r-ary tree over the r-bit digit recoding of the cells, built level by
 //      level from index ranges of the sorted digit sequences, and the edges it
 //      finds by walking it once per flipped bit.
@@ -37,6 +40,7 @@
 // required count is still written).
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -253,6 +257,80 @@ int cgo_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_bits,
                      int64_t edges_cap, int64_t* n_edges) {
   return cgo_neighbors_h1_rows(cells, n_cells, ell, word_bits, nullptr, 0, edges, edges_cap,
                                n_edges);
+}
+
+// The heuristic of §3.1 over the cells x_0 .. x_{n-1} (sorted and unique).
+// Algorithm 1 (ComputeDist): dist(x_p, x_j) for every pivot p in [h] (the
+// first h cells) and every cell j, the number of positions where their bits
+// differ. Algorithm 2: every pair i < j is first tested against inequality
+// (⋆) with the pivots; a pair passes when |dist(x_i, x_p) - dist(x_j, x_p)|
+// <= 1 for every p (readings: the printed "> 1" test is inverted --
+// as_printed = 1 applies it literally; pivots are ordinary vertices, so the
+// pair loop starts at 0; dist is filled for every j). A pair that passes is
+// compared the way a block of w threads does it: thread t counts the
+// positions of its segment [t s, min((t + 1) s, l)), s = ceil(l / w), where
+// the bits differ, stopping at 2; the counts are added in thread order,
+// stopping at 2; a total of exactly 1 outputs (i, j). Pairs come out with i
+// ascending, then j ascending. n_tested receives the number of pairs that
+// passed the pivot test (with h = 0 every pair does: the naive method).
+int cgo_heuristic(const void* cells, int64_t n_cells, int ell, int word_bits, int h, int w,
+                  int as_printed, uint32_t* edges, int64_t edges_cap, int64_t* n_edges,
+                  int64_t* n_tested) {
+  if (n_cells < 0 || bad_words(ell, word_bits) || !n_edges || !n_tested || h < 0 || w < 1)
+    return -1;
+  std::vector<Vec> x;
+  x.reserve(size_t(n_cells));
+  for (int64_t i = 0; i < n_cells; ++i) x.push_back(load_vec(cells, i, ell, word_bits));
+  const int64_t pivots = std::min<int64_t>(h, n_cells);
+  // Algorithm 1.
+  std::vector<std::vector<int>> dist(size_t(pivots), std::vector<int>(size_t(n_cells), 0));
+  for (int64_t p = 0; p < pivots; ++p)
+    for (int64_t j = 0; j < n_cells; ++j) {
+      int c = 0;
+      for (int k = 0; k < ell; ++k) c += get_bit(x[size_t(p)], k) != get_bit(x[size_t(j)], k);
+      dist[size_t(p)][size_t(j)] = c;
+    }
+  // Algorithm 2.
+  const int seg = (ell + w - 1) / w;
+  int64_t e = 0, tested = 0;
+  std::vector<int> results(static_cast<size_t>(w));
+  for (int64_t i = 0; i < n_cells; ++i) {
+    for (int64_t j = i + 1; j < n_cells; ++j) {
+      bool pass = true;
+      for (int64_t p = 0; p < pivots; ++p) {
+        const int diff = std::abs(dist[size_t(p)][size_t(i)] - dist[size_t(p)][size_t(j)]);
+        const bool ok = as_printed ? diff > 1 : diff <= 1;
+        if (!ok) {
+          pass = false;
+          break;
+        }
+      }
+      if (!pass) continue;
+      ++tested;
+      for (int t = 0; t < w; ++t) {
+        int c = 0;
+        for (int k = t * seg; k < std::min((t + 1) * seg, ell); ++k) {
+          if (get_bit(x[size_t(i)], k) != get_bit(x[size_t(j)], k)) ++c;
+          if (c >= 2) break;
+        }
+        results[size_t(t)] = c;
+      }
+      int count = 0;
+      for (int t = 0; t < w; ++t) {
+        count += results[size_t(t)];
+        if (count >= 2) break;
+      }
+      if (count != 1) continue;
+      if (e < edges_cap) {
+        edges[2 * e] = uint32_t(i);
+        edges[2 * e + 1] = uint32_t(j);
+      }
+      ++e;
+    }
+  }
+  *n_edges = e;
+  *n_tested = tested;
+  return e > edges_cap ? -2 : 0;
 }
 
 // Node counts of the search tree per level (counts[0] = 1 for the root, up to

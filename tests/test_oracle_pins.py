@@ -16,6 +16,11 @@
   multiset robustness); the arrangement bound sum_{k<=d} C(l,k) on U.
 * Planted chains: surviving planted Hamming-1 pairs are edges; every edge lies
   within one chain.
+* The heuristic of §3.1 (Algorithms 1-2): against brute force for every pivot
+  count (h = 0 is the naive method and must compare every pair), on Figure 2's
+  vectors, on the hypercube's closed form, for any segment count w; and the
+  pivot test as printed ("> 1") finds no edge at all, which is why the oracle
+  reads it as inverted.
 """
 import itertools
 import math
@@ -347,3 +352,75 @@ def test_planted_chains():
     for i, j in edges.tolist():
         assert chain_of[vals[i]] & chain_of[vals[j]]
     assert len(vals) == len(set(base_vals))
+
+
+# ------------------------- heuristic (§3.1, Algorithms 1-2) ------------------
+
+@pytest.mark.parametrize("word_bits", [32, 64])
+@pytest.mark.parametrize("ell", [1, 5, 33, 64, 70, 130])
+@pytest.mark.parametrize("h", [0, 1, 3, 5])
+def test_heuristic_matches_brute_force(ell, word_bits, h):
+    rng = np.random.default_rng(2000 + ell + h)
+    vals = sorted(set(_clustered(rng, 300, ell, 8, 3)))
+    cells = ints_to_rows(vals, ell, word_bits)
+    got, tested = oracle.heuristic(cells, ell, word_bits, h=h)
+    want = brute_force_edges(as_u64_rows(cells, ell, word_bits))
+    assert got.tolist() == want.tolist()
+    u = len(vals)
+    if h == 0:
+        assert tested == u * (u - 1) // 2  # no pivots: every pair is compared
+    else:
+        assert len(want) <= tested <= u * (u - 1) // 2
+
+
+def test_heuristic_pruning_only_shrinks_with_more_pivots():
+    rng = np.random.default_rng(77)
+    vals = sorted(set(_clustered(rng, 500, 96, 20, 4)))
+    cells = ints_to_rows(vals, 96, 64)
+    counts = [oracle.heuristic(cells, 96, 64, h=h)[1] for h in range(0, 7)]
+    # the pivots for h + 1 include those for h, and the test is a conjunction
+    assert all(a >= b for a, b in zip(counts, counts[1:])), counts
+    assert counts[-1] < counts[0] // 4, counts  # and it does prune
+
+
+@pytest.mark.parametrize("w", [1, 2, 7, 32, 64, 200])
+def test_heuristic_any_segment_count(w):
+    rng = np.random.default_rng(5)
+    ell = 70  # not a multiple of most w: the last segment is shorter
+    vals = sorted(set(_clustered(rng, 300, ell, 6, 2)))
+    cells = ints_to_rows(vals, ell, 64)
+    got, _ = oracle.heuristic(cells, ell, 64, h=2, w=w)
+    assert got.tolist() == brute_force_edges(as_u64_rows(cells, ell, 64)).tolist()
+
+
+@pytest.mark.parametrize("h", [0, 1, 2, 3])
+def test_heuristic_fig2_pairs(h):
+    vecs = _read_fig2()
+    vals = sorted(paper_string_to_int(v) for v, _ in vecs)
+    got, _ = oracle.heuristic(ints_to_rows(vals, 6, 64), 6, 64, h=h)
+    p = paper_string_to_int
+    assert [(vals[i], vals[j]) for i, j in got.tolist()] == [(p("110100"), p("110110")),
+                                                             (p("110110"), p("110111"))]
+
+
+@pytest.mark.parametrize("h", [1, 2, 4])
+def test_heuristic_hypercube_closed_form(h):
+    ell = 8
+    got, _ = oracle.heuristic(ints_to_rows(list(range(1 << ell)), ell, 64), ell, 64, h=h)
+    assert len(got) == ell * (1 << (ell - 1))
+
+
+def test_heuristic_test_as_printed_finds_nothing():
+    """Every true edge has |dist(x_i, x_p) - dist(x_j, x_p)| = 1 for every
+    pivot, so Algorithm 2's test as printed ("> 1 for all d") rejects all of
+    them; with h = 0 the test is vacuous and both forms are the naive method."""
+    rng = np.random.default_rng(9)
+    vals = sorted(set(_clustered(rng, 300, 40, 6, 3)))
+    cells = ints_to_rows(vals, 40, 64)
+    want = brute_force_edges(as_u64_rows(cells, 40, 64))
+    assert len(want) > 0
+    for h in (1, 3):
+        got, _ = oracle.heuristic(cells, 40, 64, h=h, as_printed=True)
+        assert len(got) == 0
+    got, _ = oracle.heuristic(cells, 40, 64, h=0, as_printed=True)
+    assert got.tolist() == want.tolist()
