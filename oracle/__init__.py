@@ -16,6 +16,7 @@ the Cell Graph":
 * ``heuristic``   §3.1, Algorithms 1-2: pivot distances, inequality (⋆),
                   segment-wise comparison of the remaining pairs.
 * ``tree``        §3.2, Algorithms 3-4: the 2^r-ary search tree and its walk.
+* ``bfs``         §6 (paths in the cell graph): textbook queue BFS distances.
 * ``build``       the three steps for one scene.
 
 Pins (tests that tie these functions to something other than themselves) are in
@@ -62,9 +63,10 @@ def _load():
             lib.cgo_tree.argtypes = [P, I64, I, I, I, I, P, I, P, I64, P]
             lib.cgo_tree_digits.argtypes = [P, I64, I, I, I, I, P]
             lib.cgo_heuristic.argtypes = [P, I64, I, I, I, I, I, P, I64, P, P]
+            lib.cgo_bfs.argtypes = [P, I64, I64, I64, P]
             for f in (lib.cgo_pack_signs, lib.cgo_dedup, lib.cgo_neighbors_h1_rows,
                       lib.cgo_neighbors_h1, lib.cgo_tree, lib.cgo_tree_digits,
-                      lib.cgo_heuristic):
+                      lib.cgo_heuristic, lib.cgo_bfs):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -168,6 +170,18 @@ def heuristic(cells, ell: int, word_bits: int = 64, h: int = 4, w: int = 32,
     if rc != 0:
         raise RuntimeError(f"cgo_heuristic failed: {rc}")
     return out, int(nt.value)
+
+
+def bfs(edges, n_cells: int, source: int) -> np.ndarray:
+    """Shortest-path distances (in edges) from cell `source` over the
+    undirected edge list, -1 for unreachable cells (int32[n_cells])."""
+    lib = _load()
+    edges = np.ascontiguousarray(edges, dtype=np.uint32).reshape(-1, 2)
+    dist = np.zeros(n_cells, np.int32)
+    rc = lib.cgo_bfs(_ptr(edges), edges.shape[0], n_cells, source, _ptr(dist))
+    if rc != 0:
+        raise RuntimeError(f"cgo_bfs failed: {rc}")
+    return dist
 
 
 def tree(cells, ell: int, word_bits: int = 64, r: int = 8, order: int = 0, edges: bool = True):

@@ -25,6 +25,9 @@
 //      2^r-ary tree over the r-bit digit recoding of the cells, built level by
 //      level from index ranges of the sorted digit sequences, and the edges it
 //      finds by walking it once per flipped bit.
+//   6. Breadth-first search on G_X (§6: a path in the cell graph is an
+//      approximate solution of the motion-planning problem): distances from
+//      one cell by the textbook queue BFS over the undirected edge list.
 //
 // Conventions (the paper fixes none of them):
 //   * bit i of a vector lives in word i / B, bit i % B, with B = 32 or 64
@@ -331,6 +334,35 @@ int cgo_heuristic(const void* cells, int64_t n_cells, int ell, int word_bits, in
   *n_edges = e;
   *n_tested = tested;
   return e > edges_cap ? -2 : 0;
+}
+
+// Breadth-first search (textbook FIFO queue) on the undirected graph with
+// n_cells vertices and the edges (i, j) of the list: dist[v] = number of
+// edges on a shortest path from source to v, -1 when v is unreachable.
+int cgo_bfs(const uint32_t* edges, int64_t n_edges, int64_t n_cells, int64_t source,
+            int32_t* dist) {
+  if (n_edges < 0 || n_cells < 0 || source < 0 || source >= n_cells || !dist) return -1;
+  std::vector<std::vector<uint32_t>> adj(static_cast<size_t>(n_cells));
+  for (int64_t e = 0; e < n_edges; ++e) {
+    const uint32_t i = edges[2 * e], j = edges[2 * e + 1];
+    if (int64_t(i) >= n_cells || int64_t(j) >= n_cells) return -1;
+    adj[i].push_back(j);
+    adj[j].push_back(i);
+  }
+  for (int64_t v = 0; v < n_cells; ++v) dist[v] = -1;
+  std::vector<uint32_t> queue;
+  queue.reserve(size_t(n_cells));
+  dist[source] = 0;
+  queue.push_back(uint32_t(source));
+  for (size_t head = 0; head < queue.size(); ++head) {
+    const uint32_t u = queue[head];
+    for (uint32_t v : adj[u])
+      if (dist[v] < 0) {
+        dist[v] = dist[u] + 1;
+        queue.push_back(v);
+      }
+  }
+  return 0;
 }
 
 // Node counts of the search tree per level (counts[0] = 1 for the root, up to

@@ -21,6 +21,9 @@
   vectors, on the hypercube's closed form, for any segment count w; and the
   pivot test as printed ("> 1") finds no edge at all, which is why the oracle
   reads it as inverted.
+* BFS on G_X (§6): distances on the hypercube are Hamming distances (closed
+  form), on Figure 1's dense arrangement (Q3 minus 000) too, on a path graph
+  |i - s|, and on random small graphs they equal Floyd-Warshall's.
 """
 import itertools
 import math
@@ -424,3 +427,49 @@ def test_heuristic_test_as_printed_finds_nothing():
         assert len(got) == 0
     got, _ = oracle.heuristic(cells, 40, 64, h=0, as_printed=True)
     assert got.tolist() == want.tolist()
+
+
+# ------------------------------ BFS on G_X (§6) -------------------------------
+
+@pytest.mark.parametrize("ell,source", [(1, 0), (4, 5), (9, 0), (9, 300)])
+def test_bfs_hypercube_distances_are_hamming(ell, source):
+    cells = ints_to_rows(list(range(1 << ell)), ell, 64)
+    edges = oracle.neighbors(cells, ell, 64)
+    dist = oracle.bfs(edges, 1 << ell, source)
+    assert dist.tolist() == [bin(v ^ source).count("1") for v in range(1 << ell)]
+
+
+def test_bfs_fig1_dense_arrangement():
+    # Q3 without 000 (§2.1, Figure 1): every remaining pair is still joined by
+    # a path of Hamming length avoiding 000
+    vals = list(range(1, 8))
+    cells = ints_to_rows(vals, 3, 64)
+    edges = oracle.neighbors(cells, 3, 64)
+    for s in range(7):
+        dist = oracle.bfs(edges, 7, s)
+        assert dist.tolist() == [bin(vals[s] ^ v).count("1") for v in vals]
+
+
+def test_bfs_path_and_unreachable():
+    n = 50
+    edges = np.array([[i, i + 1] for i in range(n - 1) if i != 30], np.uint32)
+    dist = oracle.bfs(edges, n, 10)
+    assert dist.tolist() == [abs(i - 10) if i <= 30 else -1 for i in range(n)]
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_bfs_against_floyd_warshall(seed):
+    rng = np.random.default_rng(seed)
+    n = 40
+    pairs = {tuple(sorted(map(int, rng.choice(n, 2, replace=False)))) for _ in range(45)}
+    edges = np.array(sorted(pairs), np.uint32)
+    inf = 10**9
+    d = np.full((n, n), inf, np.int64)
+    np.fill_diagonal(d, 0)
+    for i, j in pairs:
+        d[i, j] = d[j, i] = 1
+    for k in range(n):
+        d = np.minimum(d, d[:, k:k + 1] + d[k:k + 1, :])
+    for s in (0, 7, 39):
+        want = [int(x) if x < inf else -1 for x in d[s]]
+        assert oracle.bfs(edges, n, s).tolist() == want
