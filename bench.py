@@ -391,6 +391,39 @@ def chains_measure(dev, steps: int, strategies=("hash", "pivot", "tree", "halves
     return out
 
 
+def bfs_measure(ctx, dev, steps: int):
+    """Breadth-first search on a cell graph (paths in G_X, §6): the graph of
+    l = 256 planes in 3-space over 2^22 points (drawn like planes_3d), built
+    once; one step = cg_bfs from cell 0 (adjacency build + levels, distances
+    and parents), timed with CUDA events."""
+    import torch
+
+    from paper_1503_06029_gb300 import cellgraph, inputs
+
+    sc = inputs.planes_3d(n=1 << 22, ell=256, seed=12)
+    cells, edges = ctx.build(*(torch.from_numpy(x).to(dev) for x in (sc.pts, sc.a, sc.b)), 64)
+    u, e = int(cells.shape[0]), int(edges.shape[0])
+    for _ in range(2):
+        dist, par, reached, depth = cellgraph.bfs(edges, u, 0)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ms = []
+    for _ in range(steps):
+        ev[0].record(stream)
+        dist, par, reached, depth = cellgraph.bfs(edges, u, 0)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+    t = statistics.median(ms)
+    ed = edges.long()
+    comp = int(((dist[ed[:, 0]] >= 0) & (dist[ed[:, 1]] >= 0)).sum())  # edges searched
+    return {"workload": "cell graph of l=256 planes in 3-space over 2^22 points (like planes_3d), "
+                        "BFS from cell 0 with parents", "cells": u, "edges": e,
+            "reached": reached, "component_edges": comp, "depth": depth, "ms": t,
+            "value": comp / (t * 1e-3) / 1e6,
+            "unit": "Medges/s (undirected edges of the source's component per second)"}
+
+
 def inputs_spec_n():
     from paper_1503_06029_gb300 import inputs
 
@@ -557,6 +590,8 @@ def run_ours(args):
     }
     if not args.no_chains:
         line["chains"] = chains_measure(dev, max(3, args.steps // 4))
+    if not args.no_bfs:
+        line["bfs"] = bfs_measure(ctx, dev, max(5, args.steps // 2))
     if not args.no_batch:
         line["batch"] = batch_compare(ctx, dev, max(3, args.steps // 2))
         if not args.no_serve:
@@ -587,6 +622,7 @@ def main():
                    help="skip the batched-vs-plain comparison (and serving)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-chains", action="store_true", help="skip the long-vector workload")
+    p.add_argument("--no-bfs", action="store_true", help="skip the BFS measurement")
     p.add_argument("--serve-requests", type=int, default=2000)
     args = p.parse_args()
     if args.warmup < 3:

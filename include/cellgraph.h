@@ -83,6 +83,37 @@ typedef int cg_status;
                                 cells), partners that differ above s share the
                                 low part (grouped by one stable sort); each
                                 group is compared within itself */
+#define CG_STRATEGY_ALLPAIRS 6 /* the heuristic of §3.1 in its all-pairs form
+                                (Algorithms 1-2): every pair i < j whose
+                                distances to h pivot cells pass inequality (⋆)
+                                is compared; quadratic, so cg_neighbors_h1
+                                accepts it for at most 2^18 cells (else
+                                CG_ERR_INVALID_ARG) and tuning does not offer it */
+
+/* Breadth-first search on the cell graph G_X (§1 and §6: a path in the cell
+ * graph is an approximate solution of the motion-planning problem; traversing
+ * the graph on the GPU is the paper's next step).
+ *   edges      device uint32[n_edges][2], undirected pairs (i, j) with i != j,
+ *              both < n_cells -- the output of cg_neighbors_h1 / cg_build
+ *              (any order is accepted);
+ *   source     the start cell, 0 <= source < n_cells;
+ *   dist       device int32[n_cells] (caller-owned, written): number of edges
+ *              on a shortest path from source, -1 when unreachable;
+ *   parent     device int32[n_cells] or NULL: the predecessor of every cell
+ *              on one shortest path (a BFS tree; several are valid, any
+ *              neighbour one level closer may be chosen), -1 for the source
+ *              and unreachable cells;
+ *   n_reached, depth  host out-params (nullable): cells reached (source
+ *              included) and the largest finite distance.
+ * Workspace: query with ws = NULL (O(n_cells + n_edges) bytes). The call
+ * builds an adjacency of both directions, then runs level-synchronous kernels
+ * on `stream`, synchronising once per 16 levels; it returns when the search is
+ * done. Errors: CG_ERR_INVALID_ARG for bad sizes, a source out of range, or an
+ * edge with an endpoint >= n_cells or i == j (detected on the device; dist is
+ * then unspecified). */
+cg_status cg_bfs(const uint32_t* edges, int64_t n_edges, int64_t n_cells, int64_t source,
+                 int32_t* dist, int32_t* parent, int64_t* n_reached, int64_t* depth, void* ws,
+                 size_t* ws_bytes, void* stream);
 
 /* Message describing the calling thread's last failed call ("" if none). */
 const char* cg_last_error(void);

@@ -29,7 +29,8 @@ ERR_CUDA = 5
 ERR_TIMEOUT = 6
 ERR_INTERNAL = 7
 
-STRATEGY = {"auto": 0, "hash": 1, "sorted": 2, "pivot": 3, "tree": 4, "halves": 5}
+STRATEGY = {"auto": 0, "hash": 1, "sorted": 2, "pivot": 3, "tree": 4, "halves": 5,
+            "allpairs": 6}
 STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
 TUNE_BUCKETS = 7
 TUNE_LIMITS = (16, 32, 64, 128, 256, 1024, 4096)
@@ -41,7 +42,7 @@ EXPORTS = [
     "cg_server_create", "cg_server_submit", "cg_server_poll", "cg_server_wait",
     "cg_server_result_get", "cg_server_copy", "cg_server_release", "cg_server_get_stats",
     "cg_server_inject_alloc_failures", "cg_server_destroy", "cg_tune_bucket", "cg_ctx_tune_get",
-    "cg_ctx_tune_set", "cg_ctx_autotune", "cg_server_use_tuning", "cg_build_dev",
+    "cg_ctx_tune_set", "cg_ctx_autotune", "cg_server_use_tuning", "cg_build_dev", "cg_bfs",
 ]
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -138,6 +139,7 @@ def load_library(path: str = LIB_PATH):
         lib.cg_ctx_tune_set.argtypes = [P, I, P]
         lib.cg_ctx_autotune.argtypes = [P, P, I, I, P]
         lib.cg_server_use_tuning.argtypes = [P, P]
+        lib.cg_bfs.argtypes = [P, I64, I64, I64, P, P, PI64, PI64, P, PS, P]
         for name in EXPORTS[3:]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -258,6 +260,44 @@ def neighbors_h1(cells, ell: int, word_bits: int = 64, strategy: str = "auto", e
             continue
         _check(rc)
         return edges[: ne.value]
+
+
+def bfs(edges, n_cells: int, source: int, parent: bool = True, stream=None):
+    """Breadth-first search on the cell graph from cell ``source`` (a path in
+    G_X is an approximate motion plan, §6). ``edges``: the int32 [E, 2] device
+    tensor of ``neighbors_h1`` / ``Context.build``. Returns (dist, parent,
+    n_reached, depth): int32 [n_cells] device tensors (dist -1 when
+    unreachable; parent None unless asked for, -1 for the source)."""
+    torch = _torch()
+    lib = load_library()
+    e = edges.reshape(-1, 2)
+    ep = _dev(e, torch.int32, "edges") if e.shape[0] > 0 else ctypes.c_void_p(None)
+    need = ctypes.c_size_t(0)
+    _check(lib.cg_bfs(ep, e.shape[0], n_cells, source, None, None, None, None, None,
+                      ctypes.byref(need), ctypes.c_void_p(None)))
+    dev = edges.device
+    ws = torch.empty(need.value, dtype=torch.uint8, device=dev)
+    dist = torch.empty(n_cells, dtype=torch.int32, device=dev)
+    par = torch.empty(n_cells, dtype=torch.int32, device=dev) if parent else None
+    reached, depth = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.cg_bfs(ep, e.shape[0], n_cells, source, ctypes.c_void_p(dist.data_ptr()),
+                      ctypes.c_void_p(par.data_ptr()) if parent else None,
+                      ctypes.byref(reached), ctypes.byref(depth),
+                      ctypes.c_void_p(ws.data_ptr()), ctypes.byref(need), _stream_ptr(stream)))
+    return dist, par, int(reached.value), int(depth.value)
+
+
+def path_to(parent, source: int, target: int):
+    """Cells on the BFS tree's path from ``source`` to ``target`` (host list),
+    following a ``bfs`` parent array; empty when target was not reached."""
+    par = parent.cpu().numpy() if hasattr(parent, "cpu") else parent
+    out = [int(target)]
+    for _ in range(len(par)):
+        p = int(par[out[-1]])
+        if p < 0:
+            break
+        out.append(p)
+    return out[::-1] if out[-1] == int(source) else []
 
 
 def arrangement_cells_bound(n: int, d: int, ell: int) -> int:

@@ -346,8 +346,16 @@ cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t*
 // counting search, scan, writing search, per-cell ordering.
 cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
                       const PivotWs& p, size_t ucap, uint32_t* edges, int64_t edges_cap,
-                      cudaStream_t s, bool halves) {
-  if (halves) {
+                      cudaStream_t s, int strategy) {
+  if (strategy == CG_STRATEGY_ALLPAIRS) {
+    CG_CUDA(launch_pivot_keys(cells, w64, ell, h, ctr, ucap, p.kcell, p.k0, p.i0, s),
+            "pivot distances");
+    CG_CUDA(launch_allpairs_edges(cells, w64, ell, h, ctr, ucap, p.kcell, p.counts, p.hbuf,
+                                  p.offsets, p.fill, p.scan, edges, edges_cap, s),
+            "all-pairs neighbour search and edge output");
+    return CG_OK;
+  }
+  if (strategy == CG_STRATEGY_HALVES) {
     // HALVES: H keys in kcell, the folds in the bucket-table memory (at
     // least 4 ucap words), the L sort keys through k0/k1 with the cell
     // numbers, the H folds in sorted order in the spare key buffer.
@@ -795,20 +803,81 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
   return CG_OK;
 }
 
+BfsWs carve_bfs(Carve& c, size_t n, size_t n_edges) {
+  BfsWs w{};
+  const size_t u = n > 0 ? n : 1;
+  w.deg = c.take<uint32_t>(u);
+  w.off = c.take<unsigned long long>(u);
+  w.cur = c.take<uint32_t>(u);
+  w.adj = c.take<uint32_t>(2 * (n_edges > 0 ? n_edges : 1));
+  w.f0 = c.take<uint32_t>(u);
+  w.f1 = c.take<uint32_t>(u);
+  w.ctr = c.take<BfsCounters>(1);
+  w.total = c.take<unsigned long long>(1);
+  w.scan = c.take_bytes(scan_scratch_bytes(u));
+  return w;
+}
+
+cg_status cg_bfs(const uint32_t* edges, int64_t n_edges, int64_t n_cells, int64_t source,
+                 int32_t* dist, int32_t* parent, int64_t* n_reached, int64_t* depth, void* ws,
+                 size_t* ws_bytes, void* stream) {
+  NvtxRange nvtx("cg_bfs");
+  if (n_cells < 1 || uint64_t(n_cells) >= 0xffffffffull)
+    return fail(CG_ERR_INVALID_ARG, "n_cells must satisfy 1 <= n_cells < 2^32 - 1");
+  if (n_edges < 0 || uint64_t(n_edges) >= (uint64_t(1) << 40))
+    return fail(CG_ERR_INVALID_ARG, "n_edges out of range");
+  if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
+  {
+    Carve c{nullptr};
+    carve_bfs(c, size_t(n_cells), size_t(n_edges));
+    if (!ws) {
+      *ws_bytes = c.off + 256;
+      return CG_OK;
+    }
+    if (*ws_bytes < c.off) return fail(CG_ERR_INVALID_ARG, "workspace too small");
+  }
+  if (source < 0 || source >= n_cells) return fail(CG_ERR_INVALID_ARG, "source out of range");
+  if (!dist || (n_edges > 0 && !edges)) return fail(CG_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carve c{static_cast<char*>(ws)};
+  const BfsWs w = carve_bfs(c, size_t(n_cells), size_t(n_edges));
+  const uint32_t n = uint32_t(n_cells);
+  CG_CUDA(launch_bfs_init(dist, parent, n, uint32_t(source), w, s), "initialising distances");
+  CG_CUDA(launch_bfs_adjacency(edges, n_edges, n, w, s), "building the adjacency");
+  // Levels in groups of kGroup, then one look at the next frontier's size.
+  constexpr int kGroup = 16;
+  BfsCounters host{};
+  for (int64_t d = 0;; d += kGroup) {
+    if (d > n_cells + kGroup) return fail(CG_ERR_INTERNAL, "BFS did not terminate");
+    CG_CUDA(launch_bfs_levels(int(d), kGroup, n, dist, parent, w, s), "BFS levels");
+    CG_CUDA(cudaMemcpyAsync(&host, w.ctr, sizeof(host), cudaMemcpyDeviceToHost, s),
+            "reading counters");
+    CG_CUDA(cudaStreamSynchronize(s), "BFS");
+    if (host.error) return fail(CG_ERR_INVALID_ARG, "an edge endpoint is >= n_cells or i == j");
+    if (host.frontier[(d + kGroup) % 3] == 0) break;
+  }
+  if (n_reached) *n_reached = int64_t(host.reached);
+  if (depth) *depth = int64_t(host.depth);
+  return CG_OK;
+}
+
 cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_bits,
                           uint32_t* edges, int64_t edges_cap, int64_t* n_edges, int strategy,
                           void* ws, size_t* ws_bytes, void* stream) {
   NvtxRange nvtx("cg_neighbors_h1");
   std::string why;
   if (!check_common(n_cells, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
-  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_HALVES)
+  if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_ALLPAIRS)
     return fail(CG_ERR_INVALID_ARG, "unknown strategy");
+  if (strategy == CG_STRATEGY_ALLPAIRS && n_cells > kAllPairsMaxCells)
+    return fail(CG_ERR_INVALID_ARG, "ALLPAIRS compares every pair: at most " +
+                                        std::to_string(kAllPairsMaxCells) + " cells");
   if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
   const size_t un = size_t(n_cells > 0 ? n_cells : 1);
   const size_t cap = std::max<size_t>(1024, next_pow2(2 * un));
   const bool small = ell <= 64;
-  const bool halves = strategy == CG_STRATEGY_HALVES;
-  const bool pivot = strategy == CG_STRATEGY_PIVOT || halves;
+  const bool pivot = strategy == CG_STRATEGY_PIVOT || strategy == CG_STRATEGY_HALVES ||
+                     strategy == CG_STRATEGY_ALLPAIRS;
   const bool tree = strategy == CG_STRATEGY_TREE;
   {
     Carve c{nullptr};
@@ -839,7 +908,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     cg_status st;
     if (pivot) {
       st = pivot_steps(w.cells, 1, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un,
-                       edges, edges_cap, s, halves);
+                       edges, edges_cap, s, strategy);
     } else if (tree) {
       st = tree_steps(w.cells, 1, ell, w.ctr, carve_treews(c, un, ell), un, edges, edges_cap, s);
     } else {
@@ -858,7 +927,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     cg_status st;
     if (pivot)
       st = pivot_steps(w.cells, w64, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un, edges,
-                       edges_cap, s, halves);
+                       edges_cap, s, strategy);
     else if (tree)
       st = tree_steps(w.cells, w64, ell, w.ctr, carve_treews(c, un, ell), un, edges, edges_cap,
                       s);
@@ -1027,8 +1096,7 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   const int64_t n = plan.n;
   const int ell = plan.ell;
   const int strategy = plan.tp.strategy;
-  const bool halves = strategy == CG_STRATEGY_HALVES;
-  const bool pivot = strategy == CG_STRATEGY_PIVOT || halves;
+  const bool pivot = strategy == CG_STRATEGY_PIVOT || strategy == CG_STRATEGY_HALVES;
   const bool tree = strategy == CG_STRATEGY_TREE;
   const bool own = pivot || tree;
   cg_status st;
@@ -1039,12 +1107,12 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     if (plan.small) {
       w.cells = w.sortbuf;
       if (pivot) return pivot_steps(w.cells, 1, ell, plan.tp.pivots, w.ctr, pw, plan.ucap, edges,
-                                    edges_cap, s, halves);
+                                    edges_cap, s, strategy);
       if (tree) return tree_steps(w.cells, 1, ell, w.ctr, tw, plan.ucap, edges, edges_cap, s);
       return neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
     }
     if (pivot) return pivot_steps(ww.cells, w64, ell, plan.tp.pivots, ww.ctr, pw, plan.ucap, edges,
-                                  edges_cap, s, halves);
+                                  edges_cap, s, strategy);
     if (tree) return tree_steps(ww.cells, w64, ell, ww.ctr, tw, plan.ucap, edges, edges_cap, s);
     WideTable it{ww.slots2, uint32_t(plan.cap - 1), nullptr, 0, ww.ctr};
     if (strategy != CG_STRATEGY_SORTED)
@@ -1088,7 +1156,7 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     if (st) return st;
     mark(ctx, "sort_number", s);
     st = pivot ? pivot_steps(w.cells, 1, ell, plan.tp.pivots, w.ctr, pw, plan.ucap, edges,
-                             edges_cap, s, halves)
+                             edges_cap, s, strategy)
          : tree ? tree_steps(w.cells, 1, ell, w.ctr, tw, plan.ucap, edges, edges_cap, s)
                 : neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
     if (st) return st;
@@ -1120,7 +1188,7 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     }
     mark(ctx, "dedup_sort", s);
     st = pivot ? pivot_steps(ww.cells, w64, ell, plan.tp.pivots, ww.ctr, pw, plan.ucap, edges,
-                             edges_cap, s, halves)
+                             edges_cap, s, strategy)
          : tree ? tree_steps(ww.cells, w64, ell, ww.ctr, tw, plan.ucap, edges, edges_cap, s)
                 : neighbors_wide_steps(ww, ell, strategy, edges, edges_cap, s);
     if (st) return st;

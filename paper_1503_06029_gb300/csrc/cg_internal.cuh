@@ -389,6 +389,43 @@ cudaError_t launch_pivot_index(const uint64_t* skeys, const DevCounters* ctr, si
 // words; scan: scan_scratch_bytes(max_n).
 size_t pivot_hit_words(size_t max_n);
 
+// Breadth-first search on G_X (cg_bfs.cu).
+struct BfsCounters {
+  unsigned int frontier[3];  // rotating frontier sizes (level d reads [d % 3])
+  unsigned int error;        // an edge with an endpoint >= n or a self-loop
+  unsigned int n;            // number of cells (device copy, for the scan)
+  unsigned int reached;      // cells with a distance
+  unsigned int depth;        // last level with a non-empty frontier
+  unsigned int pad;
+};
+struct BfsWs {
+  uint32_t* deg;              // n
+  unsigned long long* off;    // n (row starts)
+  uint32_t* cur;              // n (fill cursors)
+  uint32_t* adj;              // 2 E
+  uint32_t* f0;               // n
+  uint32_t* f1;               // n
+  BfsCounters* ctr;
+  unsigned long long* total;  // 2 E
+  void* scan;                 // scan_scratch_bytes(n)
+};
+cudaError_t launch_bfs_adjacency(const uint32_t* edges, int64_t n_edges, uint32_t n,
+                                 const BfsWs& w, cudaStream_t s);
+cudaError_t launch_bfs_init(int32_t* dist, int32_t* parent, uint32_t n, uint32_t source,
+                            const BfsWs& w, cudaStream_t s);
+// Enqueues levels first .. first + count - 1.
+cudaError_t launch_bfs_levels(int first, int count, uint32_t n, int32_t* dist, int32_t* parent,
+                              const BfsWs& w, cudaStream_t s);
+
+// ALLPAIRS strategy (cg_pivot.cu): keys from launch_pivot_keys, then every
+// pair i < j tested; at most kAllPairsMaxCells cells.
+constexpr int64_t kAllPairsMaxCells = int64_t(1) << 18;
+cudaError_t launch_allpairs_edges(const uint64_t* cells, int w64, int ell, int h,
+                                  DevCounters* ctr, size_t max_n, const uint64_t* key_by_cell,
+                                  uint32_t* counts, uint32_t* hbuf, unsigned long long* offsets,
+                                  uint32_t* fill, void* scan, uint32_t* edges, int64_t edges_cap,
+                                  cudaStream_t s);
+
 // HALVES strategy (cg_pivot.cu): the l bits split at s = halves_split(l);
 // keys, a stable sort of (L key, cell) over halves_sort_bits(l) bits, then the
 // search and edge output. Uses the PIVOT workspace: hkey in key_by_cell, the

@@ -205,6 +205,47 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
+// ALLPAIRS: the heuristic of §3.1 in the paper's own all-pairs form
+// (Algorithm 2), for small U. A warp takes cell i and its lanes the cells
+// j > i, 32 at a time; a pair is compared only when its pivot distances pass
+// inequality (⋆) -- every field of the packed keys differs by exactly 1 (the
+// bound of (⋆) plus the parity of a one-bit change) -- and then word by word
+// like PIVOT's candidates. U (U - 1) / 2 key tests: quadratic, so the library
+// offers it for small U only.
+// ---------------------------------------------------------------------------
+template <int kMode>
+__global__ void __launch_bounds__(kThreads)
+    allpairs_search(const uint64_t* __restrict__ cells, int w, int h, int bits,
+                    const DevCounters* ctr, uint32_t max_n,
+                    const uint64_t* __restrict__ key_by_cell, uint32_t* __restrict__ counts,
+                    uint32_t* __restrict__ hbuf, const unsigned long long* __restrict__ offsets,
+                    uint32_t* __restrict__ fill, uint32_t* __restrict__ edges, int64_t cap) {
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  const uint64_t fmask = (1ull << bits) - 1;
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < u; i += warps) {
+    if (kMode == kWrite && counts[i] <= uint32_t(kHitBuf)) continue;
+    const uint64_t ki = key_by_cell[i];
+    const uint64_t* xi = cells + uint64_t(i) * w;
+    for (uint32_t j = i + 1 + uint32_t(lane); j < u; j += 32) {
+      const uint64_t kj = key_by_cell[j];
+      bool ok = true;
+      for (int d = 0; d < h && ok; ++d) {
+        const uint64_t a = (ki >> (bits * d)) & fmask, b = (kj >> (bits * d)) & fmask;
+        ok = a == b + 1 || b == a + 1;
+      }
+      if (!ok) continue;
+      const uint64_t* xj = cells + uint64_t(j) * w;
+      int c = 0;
+      for (int q = 0; q < w && c < 2; ++q) c += __popcll(xj[q] ^ xi[q]);
+      if (c == 1) record_hit<kMode>(i, j, counts, hbuf, offsets, fill, edges, cap);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // HALVES lookup strategy: the pigeonhole split of multi-index hashing
 // (Norouzi, Punjani, Fleet, "Fast search in Hamming space with multi-index
 // hashing", CVPR 2012) with two parts. Split the l bits at s = floor(l / 2)
@@ -504,6 +545,27 @@ cudaError_t launch_pivot_edges(const uint64_t* cells, int w64, int ell, int h, D
                                cells, w64, ell, h, bits, ctr, uint32_t(max_n), key_by_cell, sidx,
                                tb, tmask, tshift, counts, hbuf, offsets, fill, edges,
                                edges_cap);
+                       });
+}
+
+cudaError_t launch_allpairs_edges(const uint64_t* cells, int w64, int ell, int h,
+                                  DevCounters* ctr, size_t max_n, const uint64_t* key_by_cell,
+                                  uint32_t* counts, uint32_t* hbuf, unsigned long long* offsets,
+                                  uint32_t* fill, void* scan, uint32_t* edges, int64_t edges_cap,
+                                  cudaStream_t s) {
+  if (max_n == 0) return cudaSuccess;
+  const int g = grid_for(max_n, kThreads / 32);
+  const int bits = key_bits(ell);
+  return hits_to_edges(ctr, max_n, counts, hbuf, offsets, fill, scan, edges, edges_cap, s,
+                       [&](int mode) {
+                         if (mode == kCount)
+                           allpairs_search<kCount><<<g, kThreads, 0, s>>>(
+                               cells, w64, h, bits, ctr, uint32_t(max_n), key_by_cell, counts,
+                               hbuf, nullptr, nullptr, nullptr, 0);
+                         else
+                           allpairs_search<kWrite><<<g, kThreads, 0, s>>>(
+                               cells, w64, h, bits, ctr, uint32_t(max_n), key_by_cell, counts,
+                               hbuf, offsets, fill, edges, edges_cap);
                        });
 }
 

@@ -7,10 +7,11 @@
 //     streams, admit queued requests (arrival order, from one shared queue)
 //     whenever one of their slots and enough of the budget are free, enqueue
 //     each admitted scene on its slot's stream, and settle completions;
-//   * a CUDA host callback at the end of each request's stream work records the
-//     completion time and hands the request back to the scheduler.
-// No CUDA call is ever made while `mu` is held: a completion callback takes
-// `mu`, and some runtime calls may wait for earlier work in a stream.
+//   * an event recorded after each request's last operation marks its
+//     completion; the scheduler thread that owns the slot polls it and
+//     settles the request (the completion time is taken when it is seen).
+// No CUDA call is ever made while `mu` is held: some runtime calls may wait
+// for earlier work in a stream.
 //
 // Memory: each request owns two stream-ordered allocations from the server's
 // memory pool: a work block (counters, copied inputs, build workspace) that is
@@ -95,9 +96,10 @@ struct cg_server {
   struct Worker {
     std::thread th;
     std::vector<int> free_slots;
-    std::deque<Req*> finished;
+    std::vector<Req*> active;  // enqueued, completion not yet seen (this thread only)
     int running = 0;
   };
+  std::vector<cudaEvent_t> done_ev;  // per slot: recorded after a request's last operation
   std::vector<Worker> workers;
   std::unordered_map<int64_t, Req*> reqs;
   size_t in_use = 0, peak = 0;
@@ -127,18 +129,6 @@ void plan_request(Req* r) {
   r->work_bytes = align256(sizeof(DevCounters)) + r->in_bytes + align256(scene_ws_bytes(r->plan));
   r->edges_off = align256(r->plan.ucap * size_t(r->w) * 8);
   r->result_bytes = r->edges_off + align256(r->ecap * 8);
-}
-
-void CUDART_CB on_complete(void* p) {
-  Req* r = static_cast<Req*>(p);
-  cg_server* s = r->srv;
-  const double t = now_us(s);
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    r->t_done = t;
-    s->workers[size_t(r->worker)].finished.push_back(r);
-  }
-  s->cv_sched.notify_all();
 }
 
 // Allocates from the server's pool on stream st (or reports an injected
@@ -218,8 +208,8 @@ cg_status start_request(cg_server* s, Req* r) {
   if ((e = cudaMemcpyAsync(&s->hctr[r->slot], ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
                            st)) != cudaSuccess)
     return undo(e, "reading counters");
-  if ((e = cudaLaunchHostFunc(st, on_complete, r)) != cudaSuccess)
-    return undo(e, "completion callback");
+  if ((e = cudaEventRecord(s->done_ev[size_t(r->slot)], st)) != cudaSuccess)
+    return undo(e, "completion event");
   return CG_OK;
 }
 
@@ -299,23 +289,30 @@ bool admissible(const cg_server* s, int k) {
   return need > s->budget || s->in_use + need <= s->budget;
 }
 
+// Scheduler thread k: settles the requests of its slots whose completion
+// event has fired (polled: a host callback per request would put every
+// completion through the driver's single callback thread), then admits queued
+// requests while the head fits; sleeps on the condition variable when idle,
+// or for about 20 us while requests of its own are in flight.
 void scheduler(cg_server* s, int k) {
   cudaSetDevice(s->device);
   cg_server::Worker& me = s->workers[size_t(k)];
   for (;;) {
     std::vector<Req*> fin;
-    {
-      std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_sched.wait(lk, [&] {
-        return !me.finished.empty() || (!s->stop && admissible(s, k)) ||
-               (s->stop && me.running == 0);
-      });
-      fin.assign(me.finished.begin(), me.finished.end());
-      me.finished.clear();
-      if (s->stop && me.running == 0 && fin.empty()) return;
+    for (size_t q = 0; q < me.active.size();) {
+      Req* r = me.active[q];
+      if (cudaEventQuery(s->done_ev[size_t(r->slot)]) == cudaErrorNotReady) {
+        ++q;
+        continue;
+      }
+      r->t_done = now_us(s);
+      fin.push_back(r);
+      me.active[q] = me.active.back();
+      me.active.pop_back();
     }
     for (Req* r : fin) finish_request(s, r);
     // Admit in arrival order while the head fits.
+    bool admitted = false;
     for (;;) {
       Req* r = nullptr;
       {
@@ -345,20 +342,29 @@ void scheduler(cg_server* s, int k) {
         if (r->t_admit < 0) r->t_admit = now_us(s);
       }
       const cg_status st = start_request(s, r);
-      if (st != CG_OK) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->in_use -= r->work_bytes + r->result_bytes;
-        me.free_slots.push_back(r->slot);
-        --me.running;
-        r->slot = -1;
-        --s->running;
-        r->state = CG_REQ_FAILED;
-        r->status = st;
-        r->err = cg_last_error();
-        ++s->failed;
-        s->cv_done.notify_all();
+      if (st == CG_OK) {
+        me.active.push_back(r);
+        admitted = true;
+        continue;
       }
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->in_use -= r->work_bytes + r->result_bytes;
+      me.free_slots.push_back(r->slot);
+      --me.running;
+      r->slot = -1;
+      --s->running;
+      r->state = CG_REQ_FAILED;
+      r->status = st;
+      r->err = cg_last_error();
+      ++s->failed;
+      s->cv_done.notify_all();
     }
+    if (!fin.empty() || admitted) continue;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] { return (!s->stop && admissible(s, k)) || (s->stop && me.active.empty()); };
+    if (me.active.empty()) s->cv_sched.wait(lk, ready);
+    else s->cv_sched.wait_for(lk, std::chrono::microseconds(20), ready);
+    if (s->stop && me.active.empty()) return;
   }
 }
 
@@ -403,6 +409,7 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
   auto bail = [&](cudaError_t e, const char* what) {
     cudaGetLastError();
     for (auto st : s->streams) cudaStreamDestroy(st);
+    for (auto ev : s->done_ev) cudaEventDestroy(ev);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     if (s->hctr) cudaFreeHost(s->hctr);
     if (s->pool) cudaMemPoolDestroy(s->pool);
@@ -417,6 +424,10 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
       return bail(e, "creating a slot stream");
     s->streams.push_back(st);
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return bail(e, "creating a completion event");
+    s->done_ev.push_back(ev);
   }
   for (int k = max_inflight - 1; k >= 0; --k)
     s->workers[size_t(k % n_threads)].free_slots.push_back(k);
@@ -649,6 +660,7 @@ cg_status cg_server_destroy(cg_server* srv) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
+  for (auto ev : srv->done_ev) cudaEventDestroy(ev);
   cudaStreamDestroy(srv->copy_stream);
   cudaMemPoolDestroy(srv->pool);
   cudaFreeHost(srv->hctr);

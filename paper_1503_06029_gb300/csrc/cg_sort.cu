@@ -748,7 +748,7 @@ cudaError_t run_merge_sort(const Ord& ord, ulonglong2* k0, ulonglong2* k1,
 // A run longer than the warp's share of shared memory holds clears *flag,
 // which makes the full-row comparison sort run afterwards.
 constexpr int kFixWarps = 8;
-constexpr int kFixWords = 1024;  // shared-memory words per warp
+constexpr int kFixWords = 512;   // shared-memory words per warp
 constexpr int kFixMaxRun = 64;   // at most two rows per lane
 
 __device__ __forceinline__ bool srow_less(const uint64_t* a, const uint64_t* b, int w) {
@@ -804,9 +804,19 @@ __global__ void __launch_bounds__(kFixWarps * 32)
         const uint32_t a = uint32_t(lane) + 32u * j;
         mine[j] = a < m ? idx[s0 + a] : 0u;
       }
-      for (uint32_t e = lane; e < m * uint32_t(w); e += 32) {
-        const uint32_t a = e / uint32_t(w), q = e - a * uint32_t(w);
-        sr[a * stride + q] = rows[uint64_t(idx[s0 + a]) * w + q];
+      // Stage the rows: element e = (row a, word q); row numbers come from
+      // the lanes that loaded them (a uniform loop, so every lane shuffles).
+      const uint32_t elems = m * uint32_t(w);
+#pragma unroll 4
+      for (uint32_t base = 0; base < elems; base += 32) {
+        const uint32_t e = base + lane;
+        const uint32_t a = e < elems ? e / uint32_t(w) : 0u;
+        const uint32_t r0 = __shfl_sync(0xffffffffu, mine[0], int(a & 31u));
+        const uint32_t r1 = __shfl_sync(0xffffffffu, mine[1], int(a & 31u));
+        if (e < elems) {
+          const uint32_t q = e - a * uint32_t(w);
+          sr[a * stride + q] = rows[uint64_t(a < 32u ? r0 : r1) * w + q];
+        }
       }
       __syncwarp();
       uint32_t rank[2] = {0u, 0u};
@@ -1082,9 +1092,14 @@ cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32
   if ((e = ensure_smem_limit(reinterpret_cast<const void*>(msort_fix_runs), smem)) !=
       cudaSuccess)
     return e;
+  int per_sm = 0;
+  if ((e = blocks_per_sm(reinterpret_cast<const void*>(msort_fix_runs), kFixWarps * 32, smem,
+                         &per_sm)) != cudaSuccess)
+    return e;
   const size_t chunks = (max_n + 31) / 32;
   const int g = int(std::max<size_t>(
-      1, std::min<size_t>((chunks + kFixWarps - 1) / kFixWarps, size_t(sm_count()) * 3)));
+      1, std::min<size_t>((chunks + kFixWarps - 1) / kFixWarps,
+                          size_t(sm_count()) * size_t(per_sm > 0 ? per_sm : 1))));
   msort_fix_runs<<<g, kFixWarps * 32, smem, s>>>(in1 ? kk1 : kk0, out, rows, w64, n_dev,
                                                  uint32_t(max_n), flag, skip);
   count_launch();

@@ -68,6 +68,14 @@ def test_invalid_arguments_rejected_on_host(lib):
     need = ctypes.c_size_t(0)
     st = lib.cg_neighbors_h1(P(1), 10, 16, 64, P(1), 10, None, 9, None, ctypes.byref(need), None)
     assert st == cellgraph.ERR_INVALID_ARG
+    # ALLPAIRS is quadratic: refused above 2^18 cells, before any CUDA call
+    st = lib.cg_neighbors_h1(P(1), (1 << 18) + 1, 16, 64, P(1), 10, None,
+                             cellgraph.STRATEGY["allpairs"], None, ctypes.byref(need), None)
+    assert st == cellgraph.ERR_INVALID_ARG
+    assert b"ALLPAIRS" in lib.cg_last_error()
+    st = lib.cg_neighbors_h1(P(1), 1 << 18, 16, 64, P(1), 10, None,
+                             cellgraph.STRATEGY["allpairs"], None, ctypes.byref(need), None)
+    assert st == 0 and need.value > 0  # the workspace query itself is fine
     st = lib.cg_build(None, P(1), 10, 3, P(1), P(1), 16, 64, P(1), 1, None, P(1), 1, None, None)
     assert st == cellgraph.ERR_INVALID_ARG
 

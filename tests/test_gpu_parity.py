@@ -162,9 +162,9 @@ def test_dedup_matches_oracle(dev, kind, wb):
     assert np.array_equal(pc.cpu().numpy().view(np.uint32), want_pc)
 
 
-@pytest.mark.parametrize("ell,runs", [(1024, [2, 3, 31, 32, 33, 59, 60]), (1024, [2, 61]),
-                                      (1024, [2, 5, 200]), (4096, [2, 14, 15]),
-                                      (4096, [3, 16]), (200, [2, 40, 64]), (200, [65, 300])])
+@pytest.mark.parametrize("ell,runs", [(1024, [2, 3, 17, 29, 30]), (1024, [2, 31]),
+                                      (1024, [2, 5, 200]), (4096, [2, 6, 7]),
+                                      (4096, [3, 8]), (200, [2, 40, 64]), (200, [65, 300])])
 def test_dedup_runs_sharing_the_top_bits(dev, ell, runs):
     """Rows longer than the cached 128-bit key that share their top 128 bits
     in runs of the given lengths (shuffled, with duplicates): short runs are
@@ -199,7 +199,7 @@ def test_dedup_all_duplicates_and_empty(dev):
 
 # ------------------------------ steps 3-4 --------------------------------
 
-@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree", "halves"])
+@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree", "halves", "allpairs"])
 @pytest.mark.parametrize("kind,wb", [("lines", 32), ("planes64", 64), ("planes200", 64),
                                      ("planes200", 32), ("chains", 64), ("chains130", 64)])
 def test_neighbors_match_oracle(dev, kind, wb, strategy):
@@ -211,7 +211,7 @@ def test_neighbors_match_oracle(dev, kind, wb, strategy):
     assert len(want) > 0
 
 
-@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree", "halves"])
+@pytest.mark.parametrize("strategy", ["hash", "sorted", "pivot", "tree", "halves", "allpairs"])
 def test_neighbors_hypercube(dev, strategy):
     ell = 12
     cells = np.arange(1 << ell, dtype=np.uint64).reshape(-1, 1)
@@ -276,6 +276,22 @@ def test_neighbors_halves_split_positions(dev, ell):
         assert len(want) > 0
 
 
+@pytest.mark.parametrize("pivots", ["1", "2", "4", "8"])
+def test_neighbors_allpairs_against_the_heuristic_oracle(dev, pivots, monkeypatch):
+    """ALLPAIRS is Algorithm 2 on the device: its edges equal those of the
+    oracle's literal heuristic (Algorithms 1-2, pivots = the first h cells;
+    the device spreads its pivots over the sorted cells instead -- any
+    pivots give the same edges) for any pivot count."""
+    monkeypatch.setenv("CG_PIVOTS", pivots)
+    for kind, wb in (("lines", 32), ("chains130", 64)):
+        keys, ell = _dedup_case(kind, wb)
+        cells = oracle.dedup(keys, ell, wb)[:3000]
+        want, _ = oracle.heuristic(cells, ell, wb, h=int(pivots))
+        got = cellgraph.neighbors_h1(words_dev(cells, wb, dev), ell, wb, strategy="allpairs")
+        assert np.array_equal(edges_np(got), want), kind
+        assert len(want) > 0
+
+
 def test_neighbors_pivot_wide_4096(dev):
     """The longest vectors (l = 4096, 64 words): random rows plus one-bit
     variants at every word position."""
@@ -291,7 +307,7 @@ def test_neighbors_pivot_wide_4096(dev):
     cells = oracle.dedup(keys, ell, 64)
     want = oracle.neighbors(cells, ell, 64)
     assert len(want) > 50
-    for strategy in ("hash", "sorted", "pivot", "tree", "halves"):
+    for strategy in ("hash", "sorted", "pivot", "tree", "halves", "allpairs"):
         got = cellgraph.neighbors_h1(words_dev(cells, 64, dev), ell, 64, strategy=strategy)
         assert np.array_equal(edges_np(got), want), strategy
 
