@@ -589,7 +589,8 @@ def run_ours(args):
         "clocks": clocks.summary(),
     }
     if not args.no_chains:
-        line["chains"] = chains_measure(dev, max(3, args.steps // 4))
+        line["chains"] = chains_measure(dev, max(3, args.steps // 4),
+                                        tuple(args.chains_strategies.split(",")))
     if not args.no_bfs:
         line["bfs"] = bfs_measure(ctx, dev, max(5, args.steps // 2))
     if not args.no_batch:
@@ -623,6 +624,8 @@ def main():
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-chains", action="store_true", help="skip the long-vector workload")
     p.add_argument("--no-bfs", action="store_true", help="skip the BFS measurement")
+    p.add_argument("--chains-strategies", default="hash,pivot,tree,halves",
+                   help="lookup strategies timed on the long-vector workload")
     p.add_argument("--serve-requests", type=int, default=2000)
     args = p.parse_args()
     if args.warmup < 3:
