@@ -158,12 +158,15 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
  * Algorithm 4): for every cell i and every bit k with x_i(k) = 0, the vector
  * x_i with bit k set is looked up among the cells; each hit j gives edge (i, j).
  *   cells      [n_cells][W] words, device: sorted ascending and unique (the
- *              output of cg_dedup_cells); other input is detected on the
- *              device and gives CG_ERR_INVALID_ARG.
+ *              output of cg_dedup_cells), bits at or above l zero; other
+ *              input is detected on the device and gives CG_ERR_INVALID_ARG.
+ *              With word_bits = 64 and l > 64 the rows are read in place
+ *              (never written); otherwise they are first converted into the
+ *              workspace.
  *   edges      uint32[edges_cap][2], device.
  *   n_edges    host: receives E.
- *   strategy   CG_STRATEGY_* (PIVOT uses h = 4 pivots, or the value of the
- *              environment variable CG_PIVOTS when it is set).
+ *   strategy   CG_STRATEGY_* (PIVOT and ALLPAIRS use h = 4 pivots, or the
+ *              value of the environment variable CG_PIVOTS when it is set).
  *   ws, ws_bytes  as for cg_dedup_cells.
  * Blocks until done. E > edges_cap gives CG_ERR_CAPACITY with *n_edges = E.
  * ------------------------------------------------------------------------- */
@@ -306,12 +309,15 @@ cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, cg_b
                          void* stream);
 
 /* Autotuner: for every bucket of l present among the scenes (device arrays,
- * as for cg_build_batch), times cg_build of those scenes (at most 16 per
- * bucket) under each candidate setting -- HASH, SORTED, TREE, PIVOT with h
- * in {2, 3, 4}, and for l <= 64 both sign kernels -- `reps` times after one
- * warm-up, and keeps the fastest setting in the context. chosen_ms
- * (nullable, host double[CG_TUNE_BUCKETS]) receives the best time per bucket
- * (0 for buckets without scenes). Blocks until done. */
+ * as for cg_build_batch), times those scenes (at most 16 per bucket) under
+ * each candidate setting -- HASH, SORTED, TREE, HALVES, PIVOT with h in
+ * {2, 3, 4}, and for l <= 64 both sign kernels -- and keeps the fastest
+ * setting in the context. Several scenes of a bucket are timed as one
+ * cg_build_batch, `reps` replays after two warm-up calls (device work under
+ * concurrency, as a batch runs them); a lone scene is timed with cg_build,
+ * `reps` times after one warm-up. chosen_ms (nullable, host
+ * double[CG_TUNE_BUCKETS]) receives the best time per bucket (0 for buckets
+ * without scenes). Blocks until done. */
 cg_status cg_ctx_autotune(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, int reps,
                           double* chosen_ms);
 

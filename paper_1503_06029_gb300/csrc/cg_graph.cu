@@ -863,21 +863,56 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// Copies every scene's cells and edges to its place in the outputs (blocks
-// walk the scenes; threads stride within a scene).
+// Copies every scene's cells and edges to its place in the outputs. The
+// output elements (cell words, then edge pairs) are split into equal
+// warp-sized chunks over the whole grid, so one scene with a million edges
+// does not keep a single block busy while the others idle: a warp takes
+// 32 * kCopyPer consecutive elements (lane l every 32nd, coalesced), each
+// lane finds the scene of its first element by binary search over the
+// offsets and advances it as its position passes scene boundaries.
+constexpr int kCopyPer = 16;
+
+template <class Emit>
+__device__ __forceinline__ void copy_segments(const long long* __restrict__ off, int n,
+                                              long long total, Emit emit) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long chunk = 32LL * kCopyPer;
+  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * chunk;
+       base < total; base += warps * chunk) {
+    long long g = base + lane;
+    if (g >= total) continue;
+    int lo = 0, hi = n - 1;  // the last scene s with off[s] <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    int sc = lo;
+    for (int j = 0; j < kCopyPer && g < total; ++j, g += 32) {
+      while (g >= off[sc + 1]) ++sc;
+      emit(sc, g, g - off[sc]);
+    }
+  }
+}
+
+template <bool kPairs64>
 __global__ void batch_copy(const BatchEntry* __restrict__ tab, int n, const long long* cells_off,
                            const long long* edges_off, const int* ok, uint64_t* out_cells,
                            uint32_t* out_edges) {
   if (!*ok) return;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const long long c0 = cells_off[i], c1 = cells_off[i + 1];
-    const long long e0 = edges_off[i], e1 = edges_off[i + 1];
-    const uint64_t* src_c = tab[i].cells;
-    const uint32_t* src_e = tab[i].edges;
-    for (long long t = threadIdx.x; t < c1 - c0; t += blockDim.x) out_cells[c0 + t] = src_c[t];
-    for (long long t = threadIdx.x; t < 2 * (e1 - e0); t += blockDim.x)
-      out_edges[2 * e0 + t] = src_e[t];
-  }
+  copy_segments(cells_off, n, cells_off[n], [&](int sc, long long g, long long t) {
+    out_cells[g] = tab[sc].cells[t];
+  });
+  copy_segments(edges_off, n, edges_off[n], [&](int sc, long long g, long long t) {
+    if (kPairs64) {
+      reinterpret_cast<uint64_t*>(out_edges)[g] =
+          reinterpret_cast<const uint64_t*>(tab[sc].edges)[t];
+    } else {
+      out_edges[2 * g] = tab[sc].edges[2 * t];
+      out_edges[2 * g + 1] = tab[sc].edges[2 * t + 1];
+    }
+  });
 }
 
 template <class F>
@@ -1147,8 +1182,11 @@ cudaError_t launch_batch_gather(const BatchEntry* tab, int n, long long* cells_o
                                 int64_t cells_cap, uint32_t* out_edges, int64_t edges_cap,
                                 cudaStream_t s) {
   batch_offsets<<<1, 1024, 0, s>>>(tab, n, cells_off, edges_off, cells_cap, edges_cap, ok);
-  batch_copy<<<grid_for(size_t(n), 1, 8), 256, 0, s>>>(tab, n, cells_off, edges_off, ok,
-                                                        out_cells, out_edges);
+  const unsigned g = unsigned(sm_count()) * 8;
+  if (reinterpret_cast<uintptr_t>(out_edges) % 8 == 0)
+    batch_copy<true><<<g, 256, 0, s>>>(tab, n, cells_off, edges_off, ok, out_cells, out_edges);
+  else
+    batch_copy<false><<<g, 256, 0, s>>>(tab, n, cells_off, edges_off, ok, out_cells, out_edges);
   count_launch(2);
   return cudaGetLastError();
 }
@@ -1221,6 +1259,21 @@ __global__ void check_sorted(const uint64_t* __restrict__ cells, int w, DevCount
   }
 }
 
+__global__ void adopt_cells(const uint64_t* __restrict__ cells, int w, int ell, uint32_t n,
+                            DevCounters* ctr) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_unique = n;
+  const uint64_t high = (ell & 63) ? ~((1ull << (ell & 63)) - 1) : 0ull;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t* y = cells + uint64_t(i) * w;
+    if (y[w - 1] & high) atomicOr(&ctr->error, kErrHighBits);
+    if (i == 0) continue;
+    const uint64_t* x = y - w;
+    int q = w - 1;
+    while (q > 0 && x[q] == y[q]) --q;
+    if (!(x[q] < y[q])) atomicOr(&ctr->error, kErrUnsorted);
+  }
+}
+
 __global__ void publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
                                int64_t edges_cap) {
   int64_t status = CG_OK;
@@ -1239,6 +1292,13 @@ cudaError_t launch_check_sorted(const uint64_t* cells, int w64, DevCounters* ctr
                                 cudaStream_t s) {
   if (max_n < 2) return cudaSuccess;
   check_sorted<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(cells, w64, ctr, uint32_t(max_n));
+  return finish(0);
+}
+
+cudaError_t launch_adopt_cells(const uint64_t* cells, int64_t n, int ell, DevCounters* ctr,
+                               cudaStream_t s) {
+  adopt_cells<<<grid_for(size_t(n) + 1, kThreads), kThreads, 0, s>>>(cells, (ell + 63) / 64, ell,
+                                                                      uint32_t(n), ctr);
   return finish(0);
 }
 

@@ -35,6 +35,7 @@ struct DevCounters {
 // Bits of DevCounters::error.
 constexpr unsigned kErrTimeout = 64u;    // a bounded device-side wait ran out
 constexpr unsigned kErrUnsorted = 128u;  // given cells are not ascending and unique
+constexpr unsigned kErrHighBits = 256u;  // given cells have bits set at or above l
 static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
 
 // ---------------------------------------------------------------------------
@@ -281,6 +282,11 @@ cudaError_t launch_load_cells(const void* cells, int64_t n, int word_bits, int e
 // strictly ascending in value order.
 cudaError_t launch_check_sorted(const uint64_t* cells, int w64, DevCounters* ctr, size_t max_n,
                                 cudaStream_t s);
+// For a caller's 64-bit cells used in place: sets ctr->n_unique = n, and
+// kErrUnsorted / kErrHighBits unless the rows are strictly ascending and
+// have no bit set at or above l.
+cudaError_t launch_adopt_cells(const uint64_t* cells, int64_t n, int ell, DevCounters* ctr,
+                               cudaStream_t s);
 // out[0] = U, out[1] = E, out[2] = status (CG_OK, CG_ERR_CAPACITY when a count
 // exceeds its cap, CG_ERR_TIMEOUT / CG_ERR_INTERNAL on device-side failures).
 cudaError_t launch_publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,

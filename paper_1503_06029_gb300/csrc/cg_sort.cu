@@ -804,18 +804,23 @@ __global__ void __launch_bounds__(kFixWarps * 32)
         const uint32_t a = uint32_t(lane) + 32u * j;
         mine[j] = a < m ? idx[s0 + a] : 0u;
       }
-      // Stage the rows: element e = (row a, word q); row numbers come from
+      // Stage the rows: element e = base + lane = (row a, word q), advanced
+      // by 32 elements per step without a division; row numbers come from
       // the lanes that loaded them (a uniform loop, so every lane shuffles).
       const uint32_t elems = m * uint32_t(w);
+      uint32_t a = uint32_t(lane) / uint32_t(w), q = uint32_t(lane) - a * uint32_t(w);
+      const uint32_t da = 32u / uint32_t(w), dq = 32u - da * uint32_t(w);
 #pragma unroll 4
       for (uint32_t base = 0; base < elems; base += 32) {
-        const uint32_t e = base + lane;
-        const uint32_t a = e < elems ? e / uint32_t(w) : 0u;
+        const bool live = base + uint32_t(lane) < elems;
         const uint32_t r0 = __shfl_sync(0xffffffffu, mine[0], int(a & 31u));
         const uint32_t r1 = __shfl_sync(0xffffffffu, mine[1], int(a & 31u));
-        if (e < elems) {
-          const uint32_t q = e - a * uint32_t(w);
-          sr[a * stride + q] = rows[uint64_t(a < 32u ? r0 : r1) * w + q];
+        if (live) sr[a * stride + q] = rows[uint64_t(a < 32u ? r0 : r1) * w + q];
+        a += da;
+        q += dq;
+        if (q >= uint32_t(w)) {
+          q -= uint32_t(w);
+          ++a;
         }
       }
       __syncwarp();

@@ -292,6 +292,21 @@ def test_neighbors_allpairs_against_the_heuristic_oracle(dev, pivots, monkeypatc
         assert len(want) > 0
 
 
+def test_neighbors_reject_bits_above_l(dev):
+    """Cells whose last word has a bit at or above l are invalid input (the
+    wide search reads 64-bit rows in place and checks them)."""
+    rng = np.random.default_rng(3)
+    vals = sorted({int(v) for v in rng.integers(0, 2**62, size=50)})
+    cells = np.array([[v, 0] for v in vals], dtype=np.uint64)
+    ok = cellgraph.neighbors_h1(words_dev(cells, 64, dev), 100, 64, strategy="halves")
+    assert np.array_equal(edges_np(ok), oracle.neighbors(cells, 100, 64))
+    bad = cells.copy()
+    bad[-1, 1] = np.uint64(1) << np.uint64(40)  # bit 104 >= l = 100
+    for strategy in ("hash", "halves", "tree"):
+        with pytest.raises(cellgraph.CellGraphError, match="at or above"):
+            cellgraph.neighbors_h1(words_dev(bad, 64, dev), 100, 64, strategy=strategy)
+
+
 def test_neighbors_pivot_wide_4096(dev):
     """The longest vectors (l = 4096, 64 words): random rows plus one-bit
     variants at every word position."""
