@@ -360,7 +360,7 @@ typedef struct cg_server_result {
   const uint32_t* edges;  /* device, valid until cg_server_release */
   double submit_us;       /* host steady clock, microseconds since server creation: */
   double admit_us;        /*   submitted, admitted (first time), and the moment the */
-  double done_us;         /*   device finished the last step (completion callback) */
+  double done_us;         /*   scheduler saw the request's completion flag */
   int retries;            /* re-runs after a capacity overflow */
 } cg_server_result;
 
@@ -374,7 +374,9 @@ typedef struct cg_server_stats {
 
 /* Creates a server on `device` that holds at most hbm_budget_bytes of device
  * memory for requests and runs at most max_inflight requests at once
- * (1..64). Starts the scheduler thread. */
+ * (1..64). The budget is reserved on the device at creation (one arena,
+ * sub-allocated by the server; CG_ERR_OOM when it cannot be reserved).
+ * Starts the scheduler threads. */
 cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight,
                            cg_server** out);
 

@@ -1274,6 +1274,21 @@ __global__ void adopt_cells(const uint64_t* __restrict__ cells, int w, int ell, 
   }
 }
 
+__global__ void publish_done(const DevCounters* __restrict__ ctr, DevCounters* host_ctr,
+                             unsigned int* host_flag, unsigned int seq) {
+  static_assert(sizeof(DevCounters) % sizeof(unsigned int) == 0, "DevCounters words");
+  constexpr int kWords = int(sizeof(DevCounters) / sizeof(unsigned int));
+  const unsigned int* src = reinterpret_cast<const unsigned int*>(ctr);
+  unsigned int* dst = reinterpret_cast<unsigned int*>(host_ctr);
+  if (threadIdx.x < kWords) dst[threadIdx.x] = src[threadIdx.x];
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    *reinterpret_cast<volatile unsigned int*>(host_flag) = seq;
+  }
+}
+
 __global__ void publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
                                int64_t edges_cap) {
   int64_t status = CG_OK;
@@ -1299,6 +1314,12 @@ cudaError_t launch_adopt_cells(const uint64_t* cells, int64_t n, int ell, DevCou
                                cudaStream_t s) {
   adopt_cells<<<grid_for(size_t(n) + 1, kThreads), kThreads, 0, s>>>(cells, (ell + 63) / 64, ell,
                                                                       uint32_t(n), ctr);
+  return finish(0);
+}
+
+cudaError_t launch_publish_done(const DevCounters* ctr, DevCounters* host_ctr,
+                                unsigned int* host_flag, unsigned int seq, cudaStream_t s) {
+  publish_done<<<1, 32, 0, s>>>(ctr, host_ctr, host_flag, seq);
   return finish(0);
 }
 

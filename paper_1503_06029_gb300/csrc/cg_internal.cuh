@@ -287,6 +287,11 @@ cudaError_t launch_check_sorted(const uint64_t* cells, int w64, DevCounters* ctr
 // have no bit set at or above l.
 cudaError_t launch_adopt_cells(const uint64_t* cells, int64_t n, int ell, DevCounters* ctr,
                                cudaStream_t s);
+// Copies *ctr to host_ctr (mapped pinned memory, device address), then, after
+// a system-wide fence, writes seq to *host_flag: a host thread that reads
+// seq from the flag (with acquire ordering) sees the counters.
+cudaError_t launch_publish_done(const DevCounters* ctr, DevCounters* host_ctr,
+                                unsigned int* host_flag, unsigned int seq, cudaStream_t s);
 // out[0] = U, out[1] = E, out[2] = status (CG_OK, CG_ERR_CAPACITY when a count
 // exceeds its cap, CG_ERR_TIMEOUT / CG_ERR_INTERNAL on device-side failures).
 cudaError_t launch_publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,

@@ -7,20 +7,29 @@
 //     streams, admit queued requests (arrival order, from one shared queue)
 //     whenever one of their slots and enough of the budget are free, enqueue
 //     each admitted scene on its slot's stream, and settle completions;
-//   * an event recorded after each request's last operation marks its
-//     completion; the scheduler thread that owns the slot polls it and
+//   * a one-warp kernel at the end of each request's stream work copies its
+//     counters into mapped pinned host memory and then writes the request's
+//     sequence number to its slot's host flag; the scheduler thread that owns
+//     the slot polls the flag (a plain memory read, no driver call) and
 //     settles the request (the completion time is taken when it is seen).
 // No CUDA call is ever made while `mu` is held: some runtime calls may wait
 // for earlier work in a stream.
 //
-// Memory: each request owns two stream-ordered allocations from the server's
-// memory pool: a work block (counters, copied inputs, build workspace) that is
-// freed when the request completes, and a result block (cells and edges at
-// capacity) that is freed by cg_server_release. Both are charged against the
-// budget from admission until they are freed.
+// Memory: one device arena of the budget's size is reserved at creation and
+// sub-allocated on the host (first fit in address order, 256-byte blocks,
+// neighbours merged on free), so admitting and settling a request makes no
+// allocation call. Each request owns two blocks: a work block (counters,
+// copied inputs, build workspace) that is freed when the request completes,
+// and a result block (cells and edges at capacity) that is freed by
+// cg_server_release; blocks are freed only after the device work that used
+// them has finished. A request that fits the budget but not the arena's free
+// blocks (fragmentation) waits, like one that does not fit the budget, until a
+// block is freed.
 #include <chrono>
+#include <cstring>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -69,6 +78,8 @@ struct Req {
   char* result = nullptr;
   int slot = -1;
   int worker = -1;
+  unsigned int seq = 0;  // value its completion writes to the slot's host flag
+  bool stream_error = false;
   // outcome
   int64_t n_cells = 0, n_edges = 0;
   double t_submit = 0, t_admit = -1, t_done = 0;
@@ -84,9 +95,16 @@ struct cg_server {
   int max_slots = 1;
   Clock::time_point t0;
   std::vector<cudaStream_t> streams;
-  DevCounters* hctr = nullptr;  // pinned, one per slot
+  DevCounters* hctr = nullptr;    // mapped pinned, one per slot (host address)
+  DevCounters* dctr = nullptr;    // the same memory, device address
+  unsigned int* hflag = nullptr;  // mapped pinned completion flags, one per slot
+  unsigned int* dflag = nullptr;
+  std::vector<unsigned int> slot_seq;
   cudaStream_t copy_stream = nullptr;
-  cudaMemPool_t pool = nullptr;
+  char* arena = nullptr;                  // device memory of the budget's size
+  std::map<size_t, size_t> free_blocks;   // offset -> size, address order
+  uint64_t free_gen = 0;                  // bumped on every free
+  uint64_t blocked_gen = ~uint64_t(0);    // free_gen when an allocation last failed
   std::mutex mu;
   std::condition_variable cv_sched;
   std::condition_variable cv_done;
@@ -99,7 +117,6 @@ struct cg_server {
     std::vector<Req*> active;  // enqueued, completion not yet seen (this thread only)
     int running = 0;
   };
-  std::vector<cudaEvent_t> done_ev;  // per slot: recorded after a request's last operation
   std::vector<Worker> workers;
   std::unordered_map<int64_t, Req*> reqs;
   size_t in_use = 0, peak = 0;
@@ -131,37 +148,46 @@ void plan_request(Req* r) {
   r->result_bytes = r->edges_off + align256(r->ecap * 8);
 }
 
-// Allocates from the server's pool on stream st (or reports an injected
-// failure).
-cudaError_t pool_alloc(cg_server* s, void** p, size_t bytes, cudaStream_t st) {
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->inject_alloc_fail > 0) {
-      --s->inject_alloc_fail;
-      return cudaErrorMemoryAllocation;
+// Arena blocks (mu held). First fit in address order.
+bool arena_alloc(cg_server* s, size_t bytes, char** out) {
+  bytes = align256(bytes > 0 ? bytes : 1);
+  for (auto it = s->free_blocks.begin(); it != s->free_blocks.end(); ++it) {
+    if (it->second < bytes) continue;
+    const size_t off = it->first, size = it->second;
+    s->free_blocks.erase(it);
+    if (size > bytes) s->free_blocks.emplace(off + bytes, size - bytes);
+    *out = s->arena + off;
+    return true;
+  }
+  return false;
+}
+
+void arena_free(cg_server* s, char* p, size_t bytes) {
+  if (!p) return;
+  bytes = align256(bytes > 0 ? bytes : 1);
+  size_t off = size_t(p - s->arena);
+  auto next = s->free_blocks.lower_bound(off);
+  if (next != s->free_blocks.end() && off + bytes == next->first) {
+    bytes += next->second;
+    next = s->free_blocks.erase(next);
+  }
+  ++s->free_gen;
+  if (next != s->free_blocks.begin()) {
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == off) {
+      prev->second += bytes;
+      return;
     }
   }
-  return cudaMallocFromPoolAsync(p, bytes, s->pool, st);
+  s->free_blocks.emplace(off, bytes);
 }
 
 // Enqueues an admitted request on its slot's stream. No lock held.
 cg_status start_request(cg_server* s, Req* r) {
   cudaStream_t st = s->streams[size_t(r->slot)];
-  void* wp = nullptr;
-  void* rp = nullptr;
-  cudaError_t e = pool_alloc(s, &wp, r->work_bytes, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return srv_fail(CG_ERR_OOM, "request work block: " + std::string(cudaGetErrorString(e)));
-  }
-  e = pool_alloc(s, &rp, r->result_bytes, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    cudaFreeAsync(wp, st);
-    return srv_fail(CG_ERR_OOM, "request result block: " + std::string(cudaGetErrorString(e)));
-  }
-  r->work = static_cast<char*>(wp);
-  r->result = static_cast<char*>(rp);
+  if (!r->work || !r->result)
+    return srv_fail(CG_ERR_OOM, "request blocks: injected allocation failure");
+  cudaError_t e = cudaSuccess;
   const cg_scene& sc = r->sc;
   char* base = r->work;
   DevCounters* ctr = reinterpret_cast<DevCounters*>(base);
@@ -170,9 +196,6 @@ cg_status start_request(cg_server* s, Req* r) {
   const int32_t* a = sc.a;
   const int64_t* b = sc.b;
   auto undo = [&](cudaError_t err, const char* what) {
-    cudaFreeAsync(r->work, st);
-    cudaFreeAsync(r->result, st);
-    r->work = r->result = nullptr;
     return srv_fail(CG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
   };
   if (r->on_host) {
@@ -199,28 +222,24 @@ cg_status start_request(cg_server* s, Req* r) {
   const cg_status cs =
       enqueue_scene(nullptr, base + off, ctr, r->plan, pa, 64, r->result, int64_t(r->plan.ucap),
                     reinterpret_cast<uint32_t*>(r->result + r->edges_off), int64_t(r->ecap), st);
-  if (cs != CG_OK) {
-    cudaFreeAsync(r->work, st);
-    cudaFreeAsync(r->result, st);
-    r->work = r->result = nullptr;
-    return cs;
-  }
-  if ((e = cudaMemcpyAsync(&s->hctr[r->slot], ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
-                           st)) != cudaSuccess)
-    return undo(e, "reading counters");
-  if ((e = cudaEventRecord(s->done_ev[size_t(r->slot)], st)) != cudaSuccess)
-    return undo(e, "completion event");
+  if (cs != CG_OK) return cs;
+  if ((e = launch_publish_done(ctr, s->dctr + r->slot, s->dflag + r->slot, r->seq, st)) !=
+      cudaSuccess)
+    return undo(e, "completion flag");
   return CG_OK;
 }
 
 // Settles a request whose stream work has finished. No lock held on entry.
 void finish_request(cg_server* s, Req* r) {
-  cudaStream_t st = s->streams[size_t(r->slot)];
   const DevCounters h = s->hctr[r->slot];
   enum { kOk, kRetry, kFail } what = kOk;
   cg_status fst = CG_OK;
   std::string msg;
-  if (h.error & kErrTimeout) {
+  if (r->stream_error) {
+    what = kFail;
+    fst = CG_ERR_CUDA;
+    msg = "the request's stream reported an error";
+  } else if (h.error & kErrTimeout) {
     what = kFail;
     fst = CG_ERR_TIMEOUT;
     msg = "a bounded device-side wait ran out";
@@ -241,12 +260,11 @@ void finish_request(cg_server* s, Req* r) {
   }
   const size_t freed_work = r->work_bytes;
   const size_t freed_result = what == kOk ? 0 : r->result_bytes;
-  cudaFreeAsync(r->work, st);
+  char* work = r->work;
+  char* result = what == kOk ? nullptr : r->result;
   r->work = nullptr;
-  if (what != kOk) {
-    cudaFreeAsync(r->result, st);
-    r->result = nullptr;
-  }
+  if (what != kOk) r->result = nullptr;
+  const size_t work_bytes = r->work_bytes, result_bytes = r->result_bytes;
   if (what == kRetry) {
     if (h.overflow) r->cap = std::min(full_cap(r->sc.n), r->cap * 4);
     else r->ecap = size_t(h.n_edges) + 64;
@@ -254,6 +272,8 @@ void finish_request(cg_server* s, Req* r) {
   }
   {
     std::lock_guard<std::mutex> lk(s->mu);
+    arena_free(s, work, work_bytes);
+    arena_free(s, result, result_bytes);
     s->in_use -= freed_work + freed_result;
     s->workers[size_t(r->worker)].free_slots.push_back(r->slot);
     --s->workers[size_t(r->worker)].running;
@@ -284,32 +304,47 @@ void finish_request(cg_server* s, Req* r) {
 // be failed).
 bool admissible(const cg_server* s, int k) {
   if (s->queue.empty() || s->workers[size_t(k)].free_slots.empty()) return false;
+  if (s->blocked_gen == s->free_gen) return false;  // the arena had no room; no free since
   const Req* r = s->queue.front();
   const size_t need = r->work_bytes + r->result_bytes;
   return need > s->budget || s->in_use + need <= s->budget;
 }
 
-// Scheduler thread k: settles the requests of its slots whose completion
-// event has fired (polled: a host callback per request would put every
-// completion through the driver's single callback thread), then admits queued
-// requests while the head fits; sleeps on the condition variable when idle,
-// or for about 20 us while requests of its own are in flight.
+// Scheduler thread k: settles the requests of its slots whose completion flag
+// has been written (a read of mapped host memory: neither a host callback,
+// whose single driver thread capped completions, nor an event query per
+// request and poll, which competed with launches for the driver), then admits
+// queued requests while the head fits; sleeps on the condition variable when
+// idle, or for about 10 us while requests of its own are in flight. When no
+// request of its own has finished for 100 ms, it asks the driver about their
+// streams, so that a request whose stream failed is settled as failed.
 void scheduler(cg_server* s, int k) {
   cudaSetDevice(s->device);
   cg_server::Worker& me = s->workers[size_t(k)];
+  Clock::time_point last_progress = Clock::now();
   for (;;) {
     std::vector<Req*> fin;
+    const bool check_streams =
+        !me.active.empty() && Clock::now() - last_progress > std::chrono::milliseconds(100);
     for (size_t q = 0; q < me.active.size();) {
       Req* r = me.active[q];
-      if (cudaEventQuery(s->done_ev[size_t(r->slot)]) == cudaErrorNotReady) {
-        ++q;
-        continue;
+      if (__atomic_load_n(&s->hflag[r->slot], __ATOMIC_ACQUIRE) != r->seq) {
+        if (check_streams) {
+          const cudaError_t e = cudaStreamQuery(s->streams[size_t(r->slot)]);
+          if (e != cudaSuccess && e != cudaErrorNotReady) r->stream_error = true;
+        }
+        if (!r->stream_error) {
+          ++q;
+          continue;
+        }
       }
       r->t_done = now_us(s);
       fin.push_back(r);
       me.active[q] = me.active.back();
       me.active.pop_back();
     }
+    if (check_streams) last_progress = Clock::now();
+    if (!fin.empty()) last_progress = Clock::now();
     for (Req* r : fin) finish_request(s, r);
     // Admit in arrival order while the head fits.
     bool admitted = false;
@@ -319,8 +354,30 @@ void scheduler(cg_server* s, int k) {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop || !admissible(s, k)) break;
         r = s->queue.front();
-        s->queue.pop_front();
         const size_t need = r->work_bytes + r->result_bytes;
+        if (need <= s->budget) {
+          bool injected = false;
+          if (s->inject_alloc_fail > 0) {
+            --s->inject_alloc_fail;
+            injected = true;
+          }
+          char* wp = nullptr;
+          char* rp = nullptr;
+          if (!injected) {
+            if (!arena_alloc(s, r->work_bytes, &wp)) {
+              s->blocked_gen = s->free_gen;
+              break;
+            }
+            if (!arena_alloc(s, r->result_bytes, &rp)) {
+              arena_free(s, wp, r->work_bytes);
+              s->blocked_gen = s->free_gen;
+              break;
+            }
+          }
+          r->work = wp;
+          r->result = rp;
+        }
+        s->queue.pop_front();
         if (need > s->budget) {
           r->state = CG_REQ_FAILED;
           r->status = CG_ERR_CAPACITY;
@@ -333,6 +390,7 @@ void scheduler(cg_server* s, int k) {
         r->worker = k;
         r->slot = me.free_slots.back();
         me.free_slots.pop_back();
+        r->seq = ++s->slot_seq[size_t(r->slot)];
         ++me.running;
         s->in_use += need;
         if (s->in_use > s->peak) s->peak = s->in_use;
@@ -347,7 +405,14 @@ void scheduler(cg_server* s, int k) {
         admitted = true;
         continue;
       }
+      // Part of the request may have been enqueued: its blocks are reused only
+      // after that work has drained.
+      cudaStreamSynchronize(s->streams[size_t(r->slot)]);
+      cudaGetLastError();
       std::lock_guard<std::mutex> lk(s->mu);
+      arena_free(s, r->work, r->work_bytes);
+      arena_free(s, r->result, r->result_bytes);
+      r->work = r->result = nullptr;
       s->in_use -= r->work_bytes + r->result_bytes;
       me.free_slots.push_back(r->slot);
       --me.running;
@@ -363,7 +428,7 @@ void scheduler(cg_server* s, int k) {
     std::unique_lock<std::mutex> lk(s->mu);
     auto ready = [&] { return (!s->stop && admissible(s, k)) || (s->stop && me.active.empty()); };
     if (me.active.empty()) s->cv_sched.wait(lk, ready);
-    else s->cv_sched.wait_for(lk, std::chrono::microseconds(20), ready);
+    else s->cv_sched.wait_for(lk, std::chrono::microseconds(10), ready);
     if (s->stop && me.active.empty()) return;
   }
 }
@@ -409,10 +474,10 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
   auto bail = [&](cudaError_t e, const char* what) {
     cudaGetLastError();
     for (auto st : s->streams) cudaStreamDestroy(st);
-    for (auto ev : s->done_ev) cudaEventDestroy(ev);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     if (s->hctr) cudaFreeHost(s->hctr);
-    if (s->pool) cudaMemPoolDestroy(s->pool);
+    if (s->hflag) cudaFreeHost(s->hflag);
+    if (s->arena) cudaFree(s->arena);
     delete s;
     return srv_fail(CG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
@@ -424,25 +489,38 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
       return bail(e, "creating a slot stream");
     s->streams.push_back(st);
-    cudaEvent_t ev;
-    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
-      return bail(e, "creating a completion event");
-    s->done_ev.push_back(ev);
   }
+  s->slot_seq.assign(size_t(max_inflight), 0u);
   for (int k = max_inflight - 1; k >= 0; --k)
     s->workers[size_t(k % n_threads)].free_slots.push_back(k);
   if ((e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(e, "creating the copy stream");
-  if ((e = cudaMallocHost(&s->hctr, sizeof(DevCounters) * size_t(max_inflight))) != cudaSuccess)
+  if ((e = cudaHostAlloc(reinterpret_cast<void**>(&s->hctr),
+                         sizeof(DevCounters) * size_t(max_inflight), cudaHostAllocMapped)) !=
+      cudaSuccess)
     return bail(e, "pinned counters");
-  cudaMemPoolProps props{};
-  props.allocType = cudaMemAllocationTypePinned;
-  props.handleTypes = cudaMemHandleTypeNone;
-  props.location.type = cudaMemLocationTypeDevice;
-  props.location.id = device;
-  if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) return bail(e, "memory pool");
-  uint64_t keep = hbm_budget_bytes;  // cached between requests, up to the budget
-  cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  if ((e = cudaHostAlloc(reinterpret_cast<void**>(&s->hflag),
+                         sizeof(unsigned int) * size_t(max_inflight), cudaHostAllocMapped)) !=
+      cudaSuccess)
+    return bail(e, "pinned completion flags");
+  std::memset(s->hflag, 0, sizeof(unsigned int) * size_t(max_inflight));
+  if ((e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->dctr), s->hctr, 0)) !=
+          cudaSuccess ||
+      (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->dflag), s->hflag, 0)) !=
+          cudaSuccess)
+    return bail(e, "device addresses of the pinned words");
+  const size_t arena_bytes = align256(hbm_budget_bytes);
+  if ((e = cudaMalloc(reinterpret_cast<void**>(&s->arena), arena_bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    for (auto st : s->streams) cudaStreamDestroy(st);
+    cudaStreamDestroy(s->copy_stream);
+    cudaFreeHost(s->hctr);
+    cudaFreeHost(s->hflag);
+    delete s;
+    return srv_fail(CG_ERR_OOM, "cannot reserve the budget (" + std::to_string(hbm_budget_bytes) +
+                                    " bytes) on the device");
+  }
+  s->free_blocks.emplace(size_t(0), arena_bytes);
   for (int k = 0; k < n_threads; ++k) s->workers[size_t(k)].th = std::thread(scheduler, s, k);
   *out = s;
   return CG_OK;
@@ -582,11 +660,11 @@ cg_status cg_server_release(cg_server* srv, int64_t ticket) {
     if (r->state != CG_REQ_DONE && r->state != CG_REQ_FAILED)
       return srv_fail(CG_ERR_INVALID_ARG, "request not finished");
     srv->reqs.erase(ticket);
-    if (r->result) srv->in_use -= r->result_bytes;
-  }
-  if (r->result) {
-    DevGuard g(srv->device);
-    cudaFreeAsync(r->result, srv->copy_stream);
+    if (r->result) {
+      srv->in_use -= r->result_bytes;
+      arena_free(srv, r->result, r->result_bytes);
+      r->result = nullptr;
+    }
   }
   delete r;
   srv->cv_sched.notify_all();
@@ -649,21 +727,17 @@ cg_status cg_server_destroy(cg_server* srv) {
   }
   srv->cv_done.notify_all();
   DevGuard g(srv->device);
-  for (auto& kv : srv->reqs) {
-    Req* r = kv.second;
-    if (r->result) cudaFreeAsync(r->result, srv->copy_stream);
-    delete r;
-  }
+  for (auto& kv : srv->reqs) delete kv.second;
   srv->reqs.clear();
   cudaStreamSynchronize(srv->copy_stream);
   for (auto st : srv->streams) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
-  for (auto ev : srv->done_ev) cudaEventDestroy(ev);
   cudaStreamDestroy(srv->copy_stream);
-  cudaMemPoolDestroy(srv->pool);
+  cudaFree(srv->arena);
   cudaFreeHost(srv->hctr);
+  cudaFreeHost(srv->hflag);
   delete srv;
   return CG_OK;
 }
