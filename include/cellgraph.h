@@ -106,9 +106,12 @@ typedef int cg_status;
  *   n_reached, depth  host out-params (nullable): cells reached (source
  *              included) and the largest finite distance.
  * Workspace: query with ws = NULL (O(n_cells + n_edges) bytes). The call
- * builds an adjacency of both directions, then runs level-synchronous kernels
- * on `stream`, synchronising once per 16 levels; it returns when the search is
- * done. Errors: CG_ERR_INVALID_ARG for bad sizes, a source out of range, or an
+ * builds an adjacency of both directions, then searches level by level: all
+ * levels in one cooperative launch with grid barriers between them where the
+ * device allows it, else one launch per level with a look at the host once
+ * per 16 levels (the environment variable CG_BFS_LEVELS=1 selects the latter);
+ * it returns when the search is done. A grid-barrier wait that runs out (it
+ * cannot in a co-resident grid) gives CG_ERR_TIMEOUT. Errors: CG_ERR_INVALID_ARG for bad sizes, a source out of range, or an
  * edge with an endpoint >= n_cells or i == j (detected on the device; dist is
  * then unspecified). */
 cg_status cg_bfs(const uint32_t* edges, int64_t n_edges, int64_t n_cells, int64_t source,

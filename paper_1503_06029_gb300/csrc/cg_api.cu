@@ -846,9 +846,25 @@ cg_status cg_bfs(const uint32_t* edges, int64_t n_edges, int64_t n_cells, int64_
   const uint32_t n = uint32_t(n_cells);
   CG_CUDA(launch_bfs_init(dist, parent, n, uint32_t(source), w, s), "initialising distances");
   CG_CUDA(launch_bfs_adjacency(edges, n_edges, n, w, s), "building the adjacency");
+  BfsCounters host{};
+  bool single = false;
+  // CG_BFS_LEVELS=1 selects the per-level launches even where the single
+  // cooperative launch is available (both give the same distances).
+  const char* lv = std::getenv("CG_BFS_LEVELS");
+  if (!(lv && std::strcmp(lv, "1") == 0))
+    CG_CUDA(launch_bfs_single(n, dist, parent, w, s, &single), "BFS (single launch)");
+  if (single) {
+    CG_CUDA(cudaMemcpyAsync(&host, w.ctr, sizeof(host), cudaMemcpyDeviceToHost, s),
+            "reading counters");
+    CG_CUDA(cudaStreamSynchronize(s), "BFS");
+    if (host.error & 1u) return fail(CG_ERR_INVALID_ARG, "an edge endpoint is >= n_cells or i == j");
+    if (host.error & 2u) return fail(CG_ERR_TIMEOUT, "a BFS grid-barrier wait ran out");
+    if (n_reached) *n_reached = int64_t(host.reached);
+    if (depth) *depth = int64_t(host.depth);
+    return CG_OK;
+  }
   // Levels in groups of kGroup, then one look at the next frontier's size.
   constexpr int kGroup = 16;
-  BfsCounters host{};
   for (int64_t d = 0;; d += kGroup) {
     if (d > n_cells + kGroup) return fail(CG_ERR_INTERNAL, "BFS did not terminate");
     CG_CUDA(launch_bfs_levels(int(d), kGroup, n, dist, parent, w, s), "BFS levels");

@@ -21,6 +21,14 @@
 //
 // Distances are unique; parents are one valid BFS tree among several (any
 // neighbour one level closer). Work: O(U + E) per search.
+//
+// Single launch: the same levels in one cooperative launch (one block per
+// SM, all co-resident), separated by a grid barrier of this file (an arrival
+// counter and a generation word; the last block to arrive resets the counter
+// and bumps the generation). Every barrier wait is bounded: when it runs out
+// the block sets an error bit and leaves, and every other block leaves at its
+// next barrier (which then cannot complete and runs out too), so the launch
+// always ends. A level costs a barrier instead of a kernel launch.
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -49,7 +57,7 @@ __global__ void bfs_init(int32_t* __restrict__ dist, int32_t* __restrict__ paren
     c->frontier[2] = 0;
     c->error = 0;
     c->n = n;
-    c->reached = 1;
+    c->reached = 0;  // each level adds its frontier's size
     c->depth = 0;
   }
 }
@@ -80,6 +88,54 @@ __global__ void bfs_fill(const uint32_t* __restrict__ edges, uint64_t n_edges, u
   }
 }
 
+// One level: the frontier cells f_in[0, cnt) at distance d claim their
+// unvisited neighbours. Eight lanes take one frontier cell (lanes over its
+// neighbours, so a cell's few neighbours are looked at in parallel, not one
+// after the other); a warp appends the cells it claimed with one atomic.
+// Loops are warp-uniform (the ballots need every lane).
+constexpr int kLanesPerCell = 8;
+
+__device__ __forceinline__ void expand_level(int d, uint32_t cnt,
+                                             const unsigned long long* __restrict__ off,
+                                             const uint32_t* __restrict__ deg,
+                                             const uint32_t* __restrict__ adj, int32_t* dist,
+                                             int32_t* __restrict__ parent,
+                                             const uint32_t* __restrict__ f_in,
+                                             uint32_t* __restrict__ f_out, unsigned int* out_cnt) {
+  constexpr uint32_t kCellsPerWarp = 32 / kLanesPerCell;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % kLanesPerCell;
+  const uint64_t warp0 = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
+  const uint64_t warps = uint64_t(gridDim.x) * blockDim.x / 32;
+  for (uint64_t k0 = warp0 * kCellsPerWarp; k0 < cnt; k0 += warps * kCellsPerWarp) {
+    const uint64_t k = k0 + uint64_t(lane / kLanesPerCell);
+    const bool live = k < cnt;
+    const uint32_t u = live ? f_in[k] : 0u;
+    const unsigned long long p0 = live ? off[u] : 0ull;
+    const uint32_t m = live ? deg[u] : 0u;
+    const uint32_t mmax = __reduce_max_sync(0xffffffffu, m);
+    for (uint32_t r = 0; r < mmax; r += kLanesPerCell) {
+      const uint32_t q = r + uint32_t(sub);
+      bool won = false;
+      uint32_t v = 0;
+      if (q < m) {
+        v = adj[p0 + q];
+        won = reinterpret_cast<volatile int32_t*>(dist)[v] < 0 &&
+              atomicCAS(&dist[v], -1, d + 1) == -1;
+      }
+      const uint32_t mask = __ballot_sync(0xffffffffu, won);
+      if (mask == 0) continue;
+      uint32_t base = 0;
+      if (lane == __ffs(mask) - 1) base = atomicAdd(out_cnt, uint32_t(__popc(mask)));
+      base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+      if (won) {
+        if (parent) parent[v] = int32_t(u);
+        f_out[base + uint32_t(__popc(mask & ((1u << lane) - 1)))] = v;
+      }
+    }
+  }
+}
+
 __global__ void bfs_level(int d, const unsigned long long* __restrict__ off,
                           const uint32_t* __restrict__ deg, const uint32_t* __restrict__ adj,
                           int32_t* dist, int32_t* __restrict__ parent,
@@ -88,26 +144,105 @@ __global__ void bfs_level(int d, const unsigned long long* __restrict__ off,
   const uint32_t cnt = c->frontier[d % 3];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->frontier[(d + 2) % 3] = 0;
-    if (cnt > 0) c->depth = uint32_t(d);
+    if (cnt > 0) {
+      c->depth = uint32_t(d);
+      c->reached += cnt;  // the cells at distance d
+    }
   }
   if (cnt == 0) return;
-  uint32_t* out_cnt = &c->frontier[(d + 1) % 3];
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-    const uint32_t u = f_in[k];
-    const unsigned long long p0 = off[u];
-    const uint32_t m = deg[u];
-    for (uint32_t q = 0; q < m; ++q) {
-      const uint32_t v = adj[p0 + q];
-      if (dist[v] >= 0) continue;
-      if (atomicCAS(&dist[v], -1, d + 1) != -1) continue;
-      if (parent) parent[v] = int32_t(u);
-      f_out[atomicAdd(out_cnt, 1u)] = v;
-      atomicAdd(&c->reached, 1u);
+  expand_level(d, cnt, off, deg, adj, dist, parent, f_in, f_out, &c->frontier[(d + 1) % 3]);
+}
+
+// Grid barrier for a co-resident grid. Returns false when it gave up (or an
+// earlier barrier did): the caller must then leave.
+// The bound only has to end a wait that can never complete; a level of a
+// legitimately huge frontier must not reach it: 2^26 polls of >= 64 ns.
+constexpr unsigned kBarrierSpins = 1u << 26;
+
+__device__ __forceinline__ bool grid_barrier(BfsCounters* c) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &c->bar_gen;
+    volatile unsigned int* err = &c->error;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(&c->bar_count, 1u) == gridDim.x - 1) {
+      c->bar_count = 0;
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+      ok = 1;
+    } else {
+      ok = 0;
+      for (unsigned int i = 0; i < kBarrierSpins; ++i) {
+        if (*gen != g) {
+          ok = 1;
+          break;
+        }
+        if (*err & 2u) break;
+        __nanosleep(64);
+      }
+      if (!ok) atomicOr(&c->error, 2u);
     }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    bfs_all_levels(const unsigned long long* __restrict__ off, const uint32_t* __restrict__ deg,
+                   const uint32_t* __restrict__ adj, int32_t* dist, int32_t* __restrict__ parent,
+                   uint32_t* f0, uint32_t* f1, BfsCounters* c, uint32_t n) {
+  for (int d = 0; d <= int(n); ++d) {
+    const uint32_t cnt = *reinterpret_cast<volatile unsigned int*>(&c->frontier[d % 3]);
+    if (cnt == 0) return;  // the same value in every block: all leave together
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      c->frontier[(d + 2) % 3] = 0;
+      c->depth = uint32_t(d);
+      c->reached += cnt;  // the cells at distance d
+    }
+    expand_level(d, cnt, off, deg, adj, dist, parent, (d & 1) ? f1 : f0, (d & 1) ? f0 : f1,
+                 &c->frontier[(d + 1) % 3]);
+    if (!grid_barrier(c)) return;
   }
 }
 
 }  // namespace
+
+cudaError_t launch_bfs_single(uint32_t n, int32_t* dist, int32_t* parent, const BfsWs& w,
+                              cudaStream_t s, bool* launched) {
+  *launched = false;
+  int dev = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e != cudaSuccess) return e;
+  if (!coop) return cudaSuccess;
+  int per_sm = 0;
+  e = blocks_per_sm(reinterpret_cast<const void*>(bfs_all_levels), kThreads, 0, &per_sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaSuccess;
+  const unsigned grid = unsigned(sm_count());  // one block per SM: co-resident, cheap barrier
+  e = cudaMemsetAsync(&w.ctr->bar_count, 0, 2 * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  const unsigned long long* off = w.off;
+  const uint32_t* deg = w.deg;
+  const uint32_t* adj = w.adj;
+  uint32_t* f0 = w.f0;
+  uint32_t* f1 = w.f1;
+  BfsCounters* c = w.ctr;
+  void* args[] = {&off, &deg, &adj, &dist, &parent, &f0, &f1, &c, &n};
+  e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(bfs_all_levels), dim3(grid),
+                                  dim3(kThreads), args, 0, s);
+  if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  if (e != cudaSuccess) return e;
+  count_launch();
+  *launched = true;
+  return cudaSuccess;
+}
 
 cudaError_t launch_bfs_adjacency(const uint32_t* edges, int64_t n_edges, uint32_t n,
                                  const BfsWs& w, cudaStream_t s) {

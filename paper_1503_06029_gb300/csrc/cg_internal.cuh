@@ -403,11 +403,14 @@ size_t pivot_hit_words(size_t max_n);
 // Breadth-first search on G_X (cg_bfs.cu).
 struct BfsCounters {
   unsigned int frontier[3];  // rotating frontier sizes (level d reads [d % 3])
-  unsigned int error;        // an edge with an endpoint >= n or a self-loop
+  unsigned int error;        // 1: an edge with an endpoint >= n or a self-loop;
+                             // 2: a grid-barrier wait ran out (single-launch search)
   unsigned int n;            // number of cells (device copy, for the scan)
   unsigned int reached;      // cells with a distance
   unsigned int depth;        // last level with a non-empty frontier
-  unsigned int pad;
+  unsigned int bar_count;    // grid barrier of the single-launch search:
+  unsigned int bar_gen;      //   arrivals, generation
+  unsigned int pad[3];
 };
 struct BfsWs {
   uint32_t* deg;              // n
@@ -427,6 +430,11 @@ cudaError_t launch_bfs_init(int32_t* dist, int32_t* parent, uint32_t n, uint32_t
 // Enqueues levels first .. first + count - 1.
 cudaError_t launch_bfs_levels(int first, int count, uint32_t n, int32_t* dist, int32_t* parent,
                               const BfsWs& w, cudaStream_t s);
+// All levels in one cooperative launch (grid barriers between levels). Sets
+// *launched = false, with nothing enqueued, when the device or the launch
+// does not allow it (the caller then enqueues levels).
+cudaError_t launch_bfs_single(uint32_t n, int32_t* dist, int32_t* parent, const BfsWs& w,
+                              cudaStream_t s, bool* launched);
 
 // ALLPAIRS strategy (cg_pivot.cu): keys from launch_pivot_keys, then every
 // pair i < j tested; at most kAllPairsMaxCells cells.

@@ -6,6 +6,9 @@ validity instead: every reached cell other than the source has a parent that
 is its neighbour and one level closer. The edge lists are the oracle's (never
 the CUDA path's), uploaded to the device.
 """
+import functools
+import os
+
 import numpy as np
 import pytest
 
@@ -15,14 +18,25 @@ from paper_1503_06029_gb300 import cellgraph, inputs
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def dev():
+@pytest.fixture(scope="module", params=["single", "levels"])
+def dev(request):
+    """Every test runs on both search forms: one cooperative launch for all
+    levels, and one launch per level (CG_BFS_LEVELS=1)."""
+    if request.param == "levels":
+        os.environ["CG_BFS_LEVELS"] = "1"
+    else:
+        os.environ.pop("CG_BFS_LEVELS", None)
+    yield from _device()
+    os.environ.pop("CG_BFS_LEVELS", None)
+
+
+def _device():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import __graft_entry__
 
     __graft_entry__.build()
-    return torch.device("cuda:0")
+    yield torch.device("cuda:0")
 
 
 def _edges_dev(edges, dev):
@@ -102,11 +116,16 @@ def test_bfs_degenerate_graphs(dev):
         cellgraph.bfs(_edges_dev(np.array([[0, 1]], np.uint32), dev), 2, 2)  # source >= n
 
 
+@functools.lru_cache(maxsize=1)
+def _benchmark_graph():
+    sc = inputs.planes_3d()
+    return oracle.build(sc.pts, sc.a, sc.b, 64)
+
+
 @pytest.mark.gpu
 def test_bfs_on_the_benchmark_graph(dev):
     """The 2^24-point planes_3d scene's graph (8,365 cells), every source
     distance checked, from two sources."""
-    sc = inputs.planes_3d()
-    cells, edges = oracle.build(sc.pts, sc.a, sc.b, 64)
+    cells, edges = _benchmark_graph()
     for source in (0, cells.shape[0] - 1):
         _check(dev, edges, cells.shape[0], source)
