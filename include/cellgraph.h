@@ -63,7 +63,7 @@ typedef int cg_status;
 #define CG_ERR_INTERNAL 7    /* a device-side consistency check failed */
 
 /* Lookup strategies for the neighbour search (cg_neighbors_h1). */
-#define CG_STRATEGY_AUTO 0   /* library choice (currently HASH) */
+#define CG_STRATEGY_AUTO 0   /* library choice: HASH for l <= 128, HALVES above */
 #define CG_STRATEGY_HASH 1   /* open-addressing table keyed on the vector (l <= 64)
                                 or on a GF(2)-linear 64-bit fingerprint (l > 64);
                                 every candidate is verified against the full vector */
@@ -213,7 +213,8 @@ cg_status cg_ctx_stage_times(cg_ctx* ctx, double* ms, const char** names, int ca
  * output; only the speed differs.
  * Buckets: 0: l <= 16, 1: <= 32, 2: <= 64, 3: <= 128, 4: <= 256, 5: <= 1024,
  * 6: <= 4096.
- * Defaults: HASH, h = 4, the fp32 sign kernel.
+ * Defaults: HASH for l <= 128 and HALVES above (the AUTO choice), h = 4, the
+ * fp32 sign kernel.
  * ------------------------------------------------------------------------- */
 #define CG_TUNE_BUCKETS 7
 typedef struct cg_tune_params {

@@ -655,7 +655,7 @@ cg_status cg_ctx_create(cg_ctx** out, int device) {
   DeviceGuard g(device);
   cg_ctx* c = new cg_ctx();
   c->device = device;
-  for (auto& t : c->tune) t = default_tune();
+  for (int b = 0; b < CG_TUNE_BUCKETS; ++b) c->tune[b] = default_tune(b);
   if (cudaMallocHost(&c->host_ctr, sizeof(DevCounters)) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -887,6 +887,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
   if (!check_common(n_cells, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
   if (strategy < CG_STRATEGY_AUTO || strategy > CG_STRATEGY_ALLPAIRS)
     return fail(CG_ERR_INVALID_ARG, "unknown strategy");
+  if (strategy == CG_STRATEGY_AUTO) strategy = auto_strategy(ell);
   if (strategy == CG_STRATEGY_ALLPAIRS && n_cells > kAllPairsMaxCells)
     return fail(CG_ERR_INVALID_ARG, "ALLPAIRS compares every pair: at most " +
                                         std::to_string(kAllPairsMaxCells) + " cells");
@@ -1024,7 +1025,12 @@ cg_status sort_cells_wide(WideWs& ww, int ell, int word_bits, void* cells, int64
 
 namespace cg {
 
-cg_tune_params default_tune() { return cg_tune_params{CG_STRATEGY_HASH, 4, 0}; }
+int auto_strategy(int ell) { return ell <= 128 ? CG_STRATEGY_HASH : CG_STRATEGY_HALVES; }
+
+cg_tune_params default_tune(int bucket) {
+  const int ell = bucket <= 0 ? 16 : bucket == 1 ? 32 : bucket == 2 ? 64 : bucket == 3 ? 128 : 256;
+  return cg_tune_params{auto_strategy(ell), 4, 0};
+}
 
 cg_tune_params sanitize_tune(const cg_tune_params& p, int ell) {
   cg_tune_params q = p;

@@ -12,7 +12,12 @@
 namespace cg {
 
 // Library defaults of the tunables: HASH lookups, 4 pivots, fp32 sign kernel.
-cg_tune_params default_tune();
+// The library's default setting for bucket b (CG_TUNE_BUCKETS): HASH for
+// l <= 128, HALVES above (measured faster from l = 200 on: l * U probes grow
+// with l, HALVES' work does not).
+cg_tune_params default_tune(int bucket);
+// The lookup strategy CG_STRATEGY_AUTO stands for at length l.
+int auto_strategy(int ell);
 // Valid, clamped copy of p for vectors of l bits (h within 1..pivot_max_h(l)).
 cg_tune_params sanitize_tune(const cg_tune_params& p, int ell);
 

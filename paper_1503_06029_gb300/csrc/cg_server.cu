@@ -470,7 +470,7 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
   s->budget = hbm_budget_bytes;
   s->max_slots = max_inflight;
   s->t0 = Clock::now();
-  for (auto& t : s->tune) t = default_tune();
+  for (int b = 0; b < CG_TUNE_BUCKETS; ++b) s->tune[b] = default_tune(b);
   auto bail = [&](cudaError_t e, const char* what) {
     cudaGetLastError();
     for (auto st : s->streams) cudaStreamDestroy(st);

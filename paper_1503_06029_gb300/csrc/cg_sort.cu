@@ -761,10 +761,13 @@ __device__ __forceinline__ bool same_key(const ulonglong2& a, const ulonglong2& 
   return a.x == b.x && a.y == b.y;
 }
 
+constexpr int kLongMax = 2048;  // longest run msort_fix_long sorts (rows <= 256 bits)
+
 __global__ void __launch_bounds__(kFixWarps * 32)
     msort_fix_runs(const ulonglong2* __restrict__ keys, uint32_t* idx,
                    const uint64_t* __restrict__ rows, int w, const unsigned int* n_dev,
-                   uint32_t max_n, unsigned int* flag, const unsigned int* skip) {
+                   uint32_t max_n, unsigned int* flag, const unsigned int* skip,
+                   uint2* __restrict__ long_runs, unsigned int* long_count) {
   extern __shared__ uint64_t fix_sm[];
   if (skip && *skip) return;
   const uint32_t n = min(*n_dev, max_n);
@@ -786,16 +789,29 @@ __global__ void __launch_bounds__(kFixWarps * 32)
       const uint32_t s0 = c * 32 + uint32_t(__ffs(starts) - 1);
       starts &= starts - 1;
       const ulonglong2 k0 = keys[s0];
-      uint32_t m = 1;  // run = [s0, s0 + m)
+      // Run = [s0, s0 + m). The scan stops once the run is too long for the
+      // path that would take it: past max_run without the long-run list,
+      // past kLongMax with it (whose block then needs the whole length).
+      const uint32_t scan_limit = long_runs && w <= 4 ? uint32_t(kLongMax) : max_run;
+      uint32_t m = 1;
       for (uint32_t base = s0 + 1;; base += 32) {
         const uint32_t p = base + lane;
         const uint32_t eq = __ballot_sync(0xffffffffu, p < n && same_key(keys[p], k0));
         const uint32_t lead = eq == 0xffffffffu ? 32u : uint32_t(__ffs(~eq) - 1);
         m += lead;
-        if (lead < 32 || m > max_run) break;
+        if (lead < 32 || m > scan_limit) break;
       }
       if (m > max_run) {
-        if (lane == 0) *flag = 0u;
+        if (lane == 0) {
+          // Rows of at most 256 bits: one block sorts the run by its low key
+          // (msort_fix_long); longer rows or runs: the full-row pass.
+          if (long_runs && w <= 4 && m <= uint32_t(kLongMax)) {
+            const unsigned int k = atomicAdd(long_count, 1u);
+            long_runs[k] = make_uint2(s0, m);
+          } else {
+            *flag = 0u;
+          }
+        }
         continue;
       }
       uint32_t mine[2];
@@ -840,6 +856,78 @@ __global__ void __launch_bounds__(kFixWarps * 32)
       }
       __syncwarp();
     }
+  }
+}
+
+// Long runs of rows of at most 256 bits (listed by msort_fix_runs): the rows
+// of a run agree on their top 128 bits, so the remaining l - 128 <= 128 bits
+// (the low key) order them exactly. One block per run: (low key, row) pairs
+// in shared memory, padded to a power of two with keys above every real one,
+// sorted by a bitonic network, row numbers written back in order.
+constexpr int kLongThreads = 256;
+
+__device__ __forceinline__ ulonglong2 low_key(const uint64_t* row, int ell) {
+  const int L = ell - 128;  // 1 .. 128 bits below the top 128
+  const uint64_t lo = L >= 64 ? row[0] : (row[0] & ((1ull << L) - 1));
+  const uint64_t hi = L <= 64 ? 0ull : (L - 64 >= 64 ? row[1] : (row[1] & ((1ull << (L - 64)) - 1)));
+  return make_ulonglong2(hi, lo);
+}
+
+// (key, row) order. A run's rows have distinct low keys, but at l = 256 a
+// real key can equal the padding key (all ones): the padding's row number
+// 0xffffffff keeps it after every real row.
+__device__ __forceinline__ bool key_less(const ulonglong2& a, uint32_t ra, const ulonglong2& b,
+                                         uint32_t rb) {
+  if (a.x != b.x) return a.x < b.x;
+  if (a.y != b.y) return a.y < b.y;
+  return ra < rb;
+}
+
+__global__ void __launch_bounds__(kLongThreads)
+    msort_fix_long(const uint2* __restrict__ long_runs, const unsigned int* long_count,
+                   uint32_t* idx, const uint64_t* __restrict__ rows, int w, int ell,
+                   const unsigned int* skip) {
+  __shared__ ulonglong2 sk[kLongMax];
+  __shared__ uint32_t sr[kLongMax];
+  if (skip && *skip) return;
+  const unsigned int count = *long_count;
+  for (unsigned int k = blockIdx.x; k < count; k += gridDim.x) {
+    const uint2 run = long_runs[k];
+    const uint32_t s0 = run.x, m = run.y;
+    uint32_t p2 = 1;
+    while (p2 < m) p2 <<= 1;
+    for (uint32_t t = threadIdx.x; t < p2; t += kLongThreads) {
+      if (t < m) {
+        const uint32_t r = idx[s0 + t];
+        sr[t] = r;
+        sk[t] = low_key(rows + uint64_t(r) * w, ell);
+      } else {
+        sr[t] = 0xffffffffu;
+        sk[t] = make_ulonglong2(~0ull, ~0ull);
+      }
+    }
+    __syncthreads();
+    for (uint32_t size = 2; size <= p2; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t t = threadIdx.x; t < p2; t += kLongThreads) {
+          const uint32_t o = t ^ stride;
+          if (o > t) {
+            const bool up = (t & size) == 0;
+            if (key_less(sk[o], sr[o], sk[t], sr[t]) == up) {
+              const ulonglong2 tk = sk[t];
+              sk[t] = sk[o];
+              sk[o] = tk;
+              const uint32_t tr = sr[t];
+              sr[t] = sr[o];
+              sr[o] = tr;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t t = threadIdx.x; t < m; t += kLongThreads) idx[s0 + t] = sr[t];
+    __syncthreads();
   }
 }
 
@@ -1105,10 +1193,27 @@ cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32
   const int g = int(std::max<size_t>(
       1, std::min<size_t>((chunks + kFixWarps - 1) / kFixWarps,
                           size_t(sm_count()) * size_t(per_sm > 0 ? per_sm : 1))));
+  // The list of long runs lives in the key buffer the sort did not end in:
+  // its first 16 bytes hold the count.
+  ulonglong2* spare = in1 ? kk0 : kk1;
+  unsigned int* long_count = reinterpret_cast<unsigned int*>(spare);
+  uint2* long_runs = reinterpret_cast<uint2*>(spare + 1);
+  const bool use_long = w64 <= 4;
+  if (use_long && (e = cudaMemsetAsync(long_count, 0, sizeof(ulonglong2), s)) != cudaSuccess)
+    return e;
   msort_fix_runs<<<g, kFixWarps * 32, smem, s>>>(in1 ? kk1 : kk0, out, rows, w64, n_dev,
-                                                 uint32_t(max_n), flag, skip);
+                                                 uint32_t(max_n), flag, skip,
+                                                 use_long ? long_runs : nullptr, long_count);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (use_long) {
+    const unsigned lg = unsigned(std::max<size_t>(1, std::min<size_t>(
+                                                         (max_n + kLongMax - 1) / kLongMax,
+                                                         size_t(sm_count()) * 2)));
+    msort_fix_long<<<lg, kLongThreads, 0, s>>>(long_runs, long_count, out, rows, w64, ell, skip);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const RowOrder full{rows, w64, ell, false, out};
   bool in1b = false;
   e = run_merge_sort(full, kk0, kk1, i0, i1, n_dev, max_n, s, &in1b, flag);

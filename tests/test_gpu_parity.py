@@ -164,7 +164,9 @@ def test_dedup_matches_oracle(dev, kind, wb):
 
 @pytest.mark.parametrize("ell,runs", [(1024, [2, 3, 17, 29, 30]), (1024, [2, 31]),
                                       (1024, [2, 5, 200]), (4096, [2, 6, 7]),
-                                      (4096, [3, 8]), (200, [2, 40, 64]), (200, [65, 300])])
+                                      (4096, [3, 8]), (200, [2, 40, 64]), (200, [65, 300]),
+                                      (256, [64, 65, 340, 2048]), (256, [3, 2049]),
+                                      (140, [70, 500])])
 def test_dedup_runs_sharing_the_top_bits(dev, ell, runs):
     """Rows longer than the cached 128-bit key that share their top 128 bits
     in runs of the given lengths (shuffled, with duplicates): short runs are
