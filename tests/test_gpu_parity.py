@@ -11,6 +11,7 @@ cases run the workloads at the sizes the benchmark times: the whole 2^24-point
 through sampled rows plus properties that hold at any size.
 """
 import ctypes
+import functools
 
 import numpy as np
 import pytest
@@ -362,6 +363,20 @@ def test_build_matches_oracle(ctx, dev, kind, n, ell, wb):
     assert np.array_equal(edges_np(edges), want_e)
 
 
+@pytest.mark.parametrize("d,ell,n,wb", [(4, 4096, 3000, 64), (1, 300, 5000, 32),
+                                        (2, 2000, 8000, 32), (4, 129, 20_000, 64),
+                                        (1, 4096, 2000, 32)])
+def test_build_any_dimension_and_length(ctx, dev, d, ell, n, wb):
+    """Every point dimension up to 4 with long vectors, up to the longest
+    l = 4096 (the multi-pass wide path), in both word widths."""
+    sc = random_scene(ell + 7 * d, n, d, ell)
+    cells, edges = ctx.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), wb)
+    want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, wb)
+    assert np.array_equal(words_np(cells, wb), want_c)
+    assert np.array_equal(edges_np(edges), want_e)
+    assert len(want_c) > 1
+
+
 def test_build_ties_and_extremes(ctx, dev):
     for d, ell in [(2, 40), (3, 64), (4, 97)]:
         sc = tie_scene(200 + d, 30_000, d, ell)
@@ -687,7 +702,14 @@ def test_batch_capacity_contract(ctx, dev):
 def _tuning_scenes():
     return [inputs.planes_3d(n=60_000, ell=24, seed=31), inputs.planes_3d(n=80_000, ell=64, seed=32),
             inputs.planes_3d(n=50_000, ell=200, seed=33),
-            inputs.planes_3d(n=20_000, ell=1500, seed=34)]
+            inputs.planes_3d(n=20_000, ell=1500, seed=34),
+            random_scene(35, 3000, 4, 4096)]
+
+
+@functools.lru_cache(maxsize=None)
+def _tuning_want(k):
+    sc = _tuning_scenes()[k]
+    return oracle.build(sc.pts, sc.a, sc.b, 64)
 
 
 @pytest.mark.parametrize("setting", [("hash", 4, 0), ("sorted", 4, 0), ("pivot", 1, 0),
@@ -699,9 +721,9 @@ def test_build_under_every_tuning(dev, setting):
     try:
         for b in range(cellgraph.TUNE_BUCKETS):
             c2.tune_set(b, strategy, pivots, sk)
-        for sc in _tuning_scenes():
+        for k, sc in enumerate(_tuning_scenes()):
             cells, edges = c2.build(T(sc.pts, dev), T(sc.a, dev), T(sc.b, dev), 64)
-            want_c, want_e = oracle.build(sc.pts, sc.a, sc.b, 64)
+            want_c, want_e = _tuning_want(k)
             assert np.array_equal(words_np(cells, 64).reshape(want_c.shape), want_c)
             assert np.array_equal(edges_np(edges), want_e)
     finally:
