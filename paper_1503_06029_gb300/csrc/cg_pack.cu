@@ -335,6 +335,44 @@ __device__ __forceinline__ void load_points(const PackArgs& pa, int64_t p0, int 
   }
 }
 
+// A warp's whole tile of 32 P points read coalesced (lane l takes 16-byte
+// words l, l + 32, ... of the tile) and handed to the lanes through shared
+// memory (lane l gets points l P .. l P + P - 1). Reading each lane's P points
+// itself puts 16 P D bytes between consecutive lanes' requests; over the host
+// link (points read in place from pinned host memory) that pattern measured
+// 189 GB/s against 211 GB/s coalesced, and on device memory both are alike.
+// A tile that is not whole or not 16-byte aligned takes load_points.
+template <int D, int P>
+__device__ __forceinline__ void load_points_warp(const PackArgs& pa, int64_t warp_p0, int vec_ok,
+                                                 int4* __restrict__ stage,
+                                                 int32_t (&pi)[P][D]) {
+  constexpr int K = P * D / 4;  // 16-byte words per lane
+  static_assert((P * D) % 4 == 0, "whole 16-byte words per lane");
+  const int lane = threadIdx.x & 31;
+  if (!vec_ok || warp_p0 + 32 * P > pa.n) {
+    load_points<D, P>(pa, warp_p0 + lane * P, vec_ok, pi);
+    return;
+  }
+  const int4* src = reinterpret_cast<const int4*>(pa.pts + warp_p0 * D);
+#pragma unroll
+  for (int k = 0; k < K; ++k) stage[k * 32 + lane] = __ldg(src + k * 32 + lane);
+  __syncwarp();
+  int32_t tmp[P * D];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int4 v = stage[lane * K + k];
+    tmp[4 * k] = v.x;
+    tmp[4 * k + 1] = v.y;
+    tmp[4 * k + 2] = v.z;
+    tmp[4 * k + 3] = v.w;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < P; ++q)
+#pragma unroll
+    for (int k = 0; k < D; ++k) pi[q][k] = tmp[q * D + k];
+}
+
 // Words of l <= 64 vectors written to keys (64-bit: one word per point;
 // 32-bit: NCH words per point).
 template <int NCH>
@@ -400,6 +438,8 @@ __global__ void __launch_bounds__(kFThreads)
   float4* blk = reinterpret_cast<float4*>(smem_raw);
   float4* priv = blk + (1 + (threadIdx.x >> 5)) * (kRows * kQ);
   __shared__ uint32_t mblk[D];
+  __shared__ int4 stage_all[kFWarps][32 * (P * D / 4)];
+  int4* stage = stage_all[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t n = pa.n;
   // Work items: all warp tiles, or (when a tile list is given, P == 4) the
@@ -417,7 +457,7 @@ __global__ void __launch_bounds__(kFThreads)
   {
     int32_t pi[P][D];
     const int64_t wt0 = it < n_wt ? (listed ? int64_t(pa.tiles[it]) : it) : n_all;
-    load_points<D, P>(pa, wt0 * kWarpPts + lane * P, vec_ok, pi);
+    load_points_warp<D, P>(pa, wt0 * kWarpPts, vec_ok, stage, pi);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       uint32_t m = 0;
@@ -442,7 +482,7 @@ __global__ void __launch_bounds__(kFThreads)
     const int64_t wt = listed ? int64_t(pa.tiles[it]) : it;
     const int64_t p0 = wt * kWarpPts + int64_t(lane) * P;
     int32_t pi[P][D];
-    load_points<D, P>(pa, p0, vec_ok, pi);
+    load_points_warp<D, P>(pa, wt * kWarpPts, vec_ok, stage, pi);
     uint32_t mw[D];
     bool fits_blk = true, fits_priv = priv_ok;
 #pragma unroll
