@@ -148,9 +148,6 @@ __device__ __forceinline__ uint64_t pack2u(uint32_t lo, uint32_t hi) {
 __device__ __forceinline__ uint32_t uabs32(int32_t v) {
   return v < 0 ? 0u - uint32_t(v) : uint32_t(v);
 }
-__device__ __forceinline__ uint64_t uabs64(int64_t v) {
-  return v < 0 ? 0ull - uint64_t(v) : uint64_t(v);
-}
 
 template <int D>
 __device__ __forceinline__ bool exact_ge(const int32_t* __restrict__ a_row, int64_t b,

@@ -570,13 +570,6 @@ struct BatchOrder {
   }
 };
 
-template <class Ord>
-__device__ __forceinline__ bool tag_is_pad(const typename Ord::Tag& t);
-template <>
-__device__ __forceinline__ bool tag_is_pad<RowOrder>(const uint32_t& t) { return t == kPad; }
-template <>
-__device__ __forceinline__ bool tag_is_pad<BatchOrder>(const uint2& t) { return t.x == kPad; }
-
 // Tile sort: input items [b * tile, ...), with their cached keys.
 template <class Ord>
 __global__ void __launch_bounds__(kMThreads)
