@@ -90,34 +90,6 @@ typedef int cg_status;
                                 accepts it for at most 2^18 cells (else
                                 CG_ERR_INVALID_ARG) and tuning does not offer it */
 
-/* Breadth-first search on the cell graph G_X (§1 and §6: a path in the cell
- * graph is an approximate solution of the motion-planning problem; traversing
- * the graph on the GPU is the paper's next step).
- *   edges      device uint32[n_edges][2], undirected pairs (i, j) with i != j,
- *              both < n_cells -- the output of cg_neighbors_h1 / cg_build
- *              (any order is accepted);
- *   source     the start cell, 0 <= source < n_cells;
- *   dist       device int32[n_cells] (caller-owned, written): number of edges
- *              on a shortest path from source, -1 when unreachable;
- *   parent     device int32[n_cells] or NULL: the predecessor of every cell
- *              on one shortest path (a BFS tree; several are valid, any
- *              neighbour one level closer may be chosen), -1 for the source
- *              and unreachable cells;
- *   n_reached, depth  host out-params (nullable): cells reached (source
- *              included) and the largest finite distance.
- * Workspace: query with ws = NULL (O(n_cells + n_edges) bytes). The call
- * builds an adjacency of both directions, then searches level by level: all
- * levels in one cooperative launch with grid barriers between them where the
- * device allows it, else one launch per level with a look at the host once
- * per 16 levels (the environment variable CG_BFS_LEVELS=1 selects the latter);
- * it returns when the search is done. A grid-barrier wait that runs out (it
- * cannot in a co-resident grid) gives CG_ERR_TIMEOUT. Errors: CG_ERR_INVALID_ARG for bad sizes, a source out of range, or an
- * edge with an endpoint >= n_cells or i == j (detected on the device; dist is
- * then unspecified). */
-cg_status cg_bfs(const uint32_t* edges, int64_t n_edges, int64_t n_cells, int64_t source,
-                 int32_t* dist, int32_t* parent, int64_t* n_reached, int64_t* depth, void* ws,
-                 size_t* ws_bytes, void* stream);
-
 /* Message describing the calling thread's last failed call ("" if none). */
 const char* cg_last_error(void);
 
@@ -324,6 +296,38 @@ cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, cg_b
  * without scenes). Blocks until done. */
 cg_status cg_ctx_autotune(cg_ctx* ctx, const cg_scene* scenes, int n_scenes, int reps,
                           double* chosen_ms);
+
+/* ---------------------------------------------------------------------------
+ * Paths in the cell graph.
+ * ------------------------------------------------------------------------- */
+/* Breadth-first search on the cell graph G_X (§1 and §6: a path in the cell
+ * graph is an approximate solution of the motion-planning problem; traversing
+ * the graph on the GPU is the paper's next step).
+ *   edges      device uint32[n_edges][2], undirected pairs (i, j) with i != j,
+ *              both < n_cells -- the output of cg_neighbors_h1 / cg_build
+ *              (any order is accepted);
+ *   source     the start cell, 0 <= source < n_cells;
+ *   dist       device int32[n_cells] (caller-owned, written): number of edges
+ *              on a shortest path from source, -1 when unreachable;
+ *   parent     device int32[n_cells] or NULL: the predecessor of every cell
+ *              on one shortest path (a BFS tree; several are valid, any
+ *              neighbour one level closer may be chosen), -1 for the source
+ *              and unreachable cells;
+ *   n_reached, depth  host out-params (nullable): cells reached (source
+ *              included) and the largest finite distance.
+ * Workspace: query with ws = NULL (O(n_cells + n_edges) bytes). The call
+ * builds an adjacency of both directions, then searches level by level: all
+ * levels in one cooperative launch with grid barriers between them where the
+ * device allows it, else one launch per level with a look at the host once
+ * per 16 levels (the environment variable CG_BFS_LEVELS=1 selects the latter);
+ * it returns when the search is done. A grid-barrier wait that runs out (it
+ * cannot in a co-resident grid) gives CG_ERR_TIMEOUT. Errors: CG_ERR_INVALID_ARG for bad sizes, a source out of range, or an
+ * edge with an endpoint >= n_cells or i == j (detected on the device; dist is
+ * then unspecified). */
+cg_status cg_bfs(const uint32_t* edges, int64_t n_edges, int64_t n_cells, int64_t source,
+                 int32_t* dist, int32_t* parent, int64_t* n_reached, int64_t* depth, void* ws,
+                 size_t* ws_bytes, void* stream);
+
 
 /* ---------------------------------------------------------------------------
  * Serving: a request loop that builds independent scenes (§2.1-§2.2 per scene)
