@@ -113,3 +113,28 @@ def test_oracle_and_library_share_no_sources():
     assert "#include \"" not in ora  # only standard headers
     for f in os.listdir(os.path.join(ROOT, "paper_1503_06029_gb300", "csrc")):
         assert "oracle" not in open(os.path.join(ROOT, "paper_1503_06029_gb300", "csrc", f)).read()
+
+
+def test_path_to_follows_parents():
+    """cellgraph.path_to walks a BFS parent array back to the source (host
+    logic, no device): a path, the source itself, and an unreachable cell."""
+    import numpy as np
+
+    parent = np.array([-1, 0, 1, 1, 3, -1, 5], np.int32)  # 0-1-3-4 and 1-2; 5-6 apart
+    assert cellgraph.path_to(parent, 0, 4) == [0, 1, 3, 4]
+    assert cellgraph.path_to(parent, 0, 2) == [0, 1, 2]
+    assert cellgraph.path_to(parent, 0, 0) == [0]
+    assert cellgraph.path_to(parent, 0, 6) == []  # its tree ends at 5, not at the source
+
+
+def test_bfs_arguments_rejected_on_host(lib):
+    P = ctypes.c_void_p
+    need = ctypes.c_size_t(0)
+    assert lib.cg_bfs(P(1), 4, 0, 0, P(1), None, None, None, None, ctypes.byref(need),
+                      None) == cellgraph.ERR_INVALID_ARG  # no cells
+    assert lib.cg_bfs(P(1), -1, 5, 0, P(1), None, None, None, None, ctypes.byref(need),
+                      None) == cellgraph.ERR_INVALID_ARG  # negative edge count
+    assert lib.cg_bfs(P(1), 4, 5, 0, P(1), None, None, None, None, ctypes.byref(need),
+                      None) == 0 and need.value > 0  # workspace query
+    assert lib.cg_bfs(P(1), 4, 5, 9, P(1), None, None, None, P(1), ctypes.byref(need),
+                      None) == cellgraph.ERR_INVALID_ARG  # source out of range
