@@ -199,6 +199,28 @@ def _dist():
     return world, rank, local
 
 
+def host_description() -> dict:
+    """The host the CPU baseline ran on: architecture, CPU model (from
+    /proc/cpuinfo where it has one) and logical core count."""
+    import platform
+
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                key = key.strip().lower()
+                if key in ("model name", "cpu model", "hardware") and val.strip():
+                    model = val.strip()
+                    break
+                if key == "cpu part" and model is None:
+                    model = f"cpu part {val.strip()}"
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "model": model or platform.processor() or None,
+            "logical_cores": os.cpu_count()}
+
+
 def cpu_baseline(sample_points: int, seed: int = 2):
     """Times the CPU oracle (single thread) on the first ``sample_points``
     points of the workload."""
@@ -213,7 +235,8 @@ def cpu_baseline(sample_points: int, seed: int = 2):
     dt = time.perf_counter() - t0
     return {"value": sample_points / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {sample_points} points of the workload scene "
-                      f"({len(cells)} cells, {len(edges)} edges), {dt:.2f} s single-threaded"}
+                      f"({len(cells)} cells, {len(edges)} edges), {dt:.2f} s single-threaded",
+            "host": host_description()}
 
 
 def batch_compare(ctx, dev, steps: int):
@@ -464,7 +487,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} consecutive points of the workload scene per step"},
+                         "sample": f"{sample} consecutive points of the workload scene per step",
+                         "host": host_description()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -69,3 +69,12 @@ def test_single_process_reduction_is_identity():
 
     assert bench.max_over_ranks(3.25) == 3.25
     assert bench.job_value(1, 2_000_000, 0.5) == pytest.approx(4.0)
+
+
+def test_host_description_names_the_cpu():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = bench.host_description()
+    assert set(h) == {"machine", "model", "logical_cores"}
+    assert h["logical_cores"] >= 1 and h["machine"]
