@@ -70,6 +70,9 @@ __global__ void keys_to_u64(const void* keys, int64_t n, int word_bits, int w_ca
   }
 }
 
+// A caller's cells must have every bit at or above l clear: a set one is
+// reported (kErrHighBits) rather than cleared, so the same bad row is refused
+// whatever the word width and whether or not the rows are read in place.
 __global__ void load_cells(const void* cells, int64_t n, int word_bits, int w_caller, int w64,
                            int ell, uint64_t* out, DevCounters* ctr) {
   if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_unique = unsigned(n);
@@ -78,7 +81,10 @@ __global__ void load_cells(const void* cells, int64_t n, int word_bits, int w_ca
        t += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = t / w64;
     const int j = int(t - r * w64);
-    out[t] = load_word(cells, r, j, word_bits, w_caller) & valid_bits(j, w64, ell);
+    const uint64_t raw = load_word(cells, r, j, word_bits, w_caller);
+    const uint64_t kept = raw & valid_bits(j, w64, ell);
+    if (kept != raw) atomicOr(&ctr->error, kErrHighBits);
+    out[t] = kept;
   }
 }
 
@@ -284,13 +290,14 @@ constexpr int kNECells = 32;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
+// Polls of the look-back before it gives up (a wait that can never end).
 constexpr unsigned kSpinLimit = 1u << 22;
 
 template <class L>
 __global__ void __launch_bounds__(kNEThreads)
     neighbors_emit_small(const uint64_t* __restrict__ cells, L look, DevCounters* ctr, int ell,
                          unsigned long long* status, uint32_t* __restrict__ edges, int64_t cap,
-                         uint32_t max_n) {
+                         uint32_t max_n, uint32_t polls) {
   __shared__ uint32_t hits[kNECells][64];
   __shared__ uint32_t cnt[kNECells];
   __shared__ uint32_t off[kNECells];
@@ -342,16 +349,16 @@ __global__ void __launch_bounds__(kNEThreads)
         } else {
           atomicExch(&status[c], kFlagAgg | T);
           int64_t p = int64_t(c) - 1;
-          unsigned iters = 0;
+          uint32_t looked = 0;
           while (p >= 0) {
+            if (looked++ >= polls) {  // every look counts; 0 polls gives up at once
+              atomicOr(&ctr->error, kErrTimeout);
+              break;
+            }
             const unsigned long long sv =
                 *reinterpret_cast<volatile unsigned long long*>(&status[p]);
             const unsigned long long f = sv & ~kValMask;
             if (f == 0) {
-              if (++iters > kSpinLimit) {
-                atomicOr(&ctr->error, kErrTimeout);
-                break;
-              }
               __nanosleep(64);
               continue;
             }
@@ -702,7 +709,8 @@ template <class L>
 __global__ void __launch_bounds__(kNEThreads)
     neighbors_emit_wide(const uint64_t* __restrict__ cells, int w, int ell, L look,
                         DevCounters* ctr, unsigned long long* status,
-                        uint32_t* __restrict__ edges, int64_t cap, uint32_t max_n) {
+                        uint32_t* __restrict__ edges, int64_t cap, uint32_t max_n,
+                        uint32_t polls) {
   extern __shared__ uint64_t dsm[];
   uint64_t* hbits = dsm;
   uint32_t* hits = reinterpret_cast<uint32_t*>(dsm + ell);  // [kNECells][ell]
@@ -757,16 +765,16 @@ __global__ void __launch_bounds__(kNEThreads)
         } else {
           atomicExch(&status[c], kFlagAgg | T);
           int64_t p = int64_t(c) - 1;
-          unsigned iters = 0;
+          uint32_t looked = 0;
           while (p >= 0) {
+            if (looked++ >= polls) {  // every look counts; 0 polls gives up at once
+              atomicOr(&ctr->error, kErrTimeout);
+              break;
+            }
             const unsigned long long sv =
                 *reinterpret_cast<volatile unsigned long long*>(&status[p]);
             const unsigned long long f = sv & ~kValMask;
             if (f == 0) {
-              if (++iters > kSpinLimit) {
-                atomicOr(&ctr->error, kErrTimeout);
-                break;
-              }
               __nanosleep(64);
               continue;
             }
@@ -955,11 +963,12 @@ cudaError_t launch_neighbors_emit_small(const uint64_t* cells, const SmallTable&
   const int g = grid_for(max_n, kNECells, 4);
   if (strategy == 2) {
     neighbors_emit_small<<<g, kNEThreads, 0, s>>>(cells, SmallSorted{cells, t.ctr}, t.ctr, ell,
-                                                  status, edges, edges_cap, uint32_t(max_n));
+                                                  status, edges, edges_cap, uint32_t(max_n),
+                                                  wait_limit(kSpinLimit));
   } else {
     neighbors_emit_small<<<g, kNEThreads, 0, s>>>(
         cells, SmallHash{t.keys, t.vals, t.mask, t.shift, t.ctr}, t.ctr, ell, status, edges,
-        edges_cap, uint32_t(max_n));
+        edges_cap, uint32_t(max_n), wait_limit(kSpinLimit));
   }
   return finish(0);
 }
@@ -1167,12 +1176,14 @@ cudaError_t launch_neighbors_emit_wide(const uint64_t* cells, int w64, int ell, 
     auto k = neighbors_emit_wide<WideSorted>;
     if ((e = allow_smem(reinterpret_cast<const void*>(k), smem)) != cudaSuccess) return e;
     k<<<g, kNEThreads, smem, s>>>(cells, w64, ell, WideSorted{cells, t.ctr, w64}, t.ctr, status,
-                                  edges, edges_cap, uint32_t(max_n));
+                                  edges, edges_cap, uint32_t(max_n),
+                                  wait_limit(kSpinLimit));
   } else {
     auto k = neighbors_emit_wide<WideHash>;
     if ((e = allow_smem(reinterpret_cast<const void*>(k), smem)) != cudaSuccess) return e;
     k<<<g, kNEThreads, smem, s>>>(cells, w64, ell, WideHash{cells, fp, t.slots, t.mask, w64},
-                                  t.ctr, status, edges, edges_cap, uint32_t(max_n));
+                                  t.ctr, status, edges, edges_cap, uint32_t(max_n),
+                                  wait_limit(kSpinLimit));
   }
   return finish(0);
 }
@@ -1199,7 +1210,8 @@ cudaError_t launch_neighbors_emit_tree(const uint64_t* cells, int w64, int ell,
   const int g = grid_for(max_n, kNECells, 4);
   if (w64 == 1 && ell <= 64) {
     neighbors_emit_small<<<g, kNEThreads, 0, s>>>(cells, TreeSmall{cells, nodes, ell}, ctr, ell,
-                                                  status, edges, edges_cap, uint32_t(max_n));
+                                                  status, edges, edges_cap, uint32_t(max_n),
+                                                  wait_limit(kSpinLimit));
     return finish(0);
   }
   const size_t smem = size_t(ell) * sizeof(uint64_t) + size_t(kNECells) * ell * sizeof(uint32_t);
@@ -1208,7 +1220,8 @@ cudaError_t launch_neighbors_emit_tree(const uint64_t* cells, int w64, int ell,
   cudaError_t e = allow_smem(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
   k<<<g, kNEThreads, smem, s>>>(cells, w64, ell, TreeWide{cells, nodes, w64, ell}, ctr, status,
-                                edges, edges_cap, uint32_t(max_n));
+                                edges, edges_cap, uint32_t(max_n),
+                                wait_limit(kSpinLimit));
   return finish(0);
 }
 

@@ -17,6 +17,10 @@
 //   * Set-up: the first call on a device, with that device current, looks up
 //     the array's device address with cudaGetSymbolAddress (once per device,
 //     under a lock). Make that first call before any stream capture.
+//   * Like cg_neighbors_h1, the call waits for its work on the stream to
+//     finish before it returns E through the host pointer.
+//   * Input checks are those of cg_neighbors_h1: rows that are not strictly
+//     ascending, or that have bits at or above l, give CG_ERR_INVALID_ARG.
 //   * Sharing: every call uses the same array and leaves its contents behind;
 //     each call first clears what must start from zero (table, counters,
 //     look-back words). Calls whose work overlaps on the GPU (different
@@ -105,6 +109,8 @@ cg_status cg_neighbors_h1_noalloc(const void* cells, int64_t n_cells, int ell, i
   const size_t un = size_t(n_cells > 0 ? n_cells : 1);
   cudaError_t e = launch_clear_build(tkeys, kTableCap, status, ne_status_words(un), ctr, s);
   if (e == cudaSuccess) e = launch_load_cells(cells, n_cells, word_bits, ell, icells, ctr, s);
+  // The same precondition check as cg_neighbors_h1: strictly ascending rows.
+  if (e == cudaSuccess) e = launch_check_sorted(icells, 1, ctr, un, s);
   if (e == cudaSuccess) e = launch_index_small(icells, t, un, s);
   if (e == cudaSuccess)
     e = launch_neighbors_emit_small(icells, t, ell, CG_STRATEGY_HASH, status, edges, edges_cap,
@@ -117,11 +123,20 @@ cg_status cg_neighbors_h1_noalloc(const void* cells, int64_t n_cells, int ell, i
     cg::set_last_error((std::string("cg_neighbors_h1_noalloc: ") + cudaGetErrorString(e)).c_str());
     return CG_ERR_CUDA;
   }
+  // Error bits in the order cg_neighbors_h1 reports them.
+  if (host.error & kErrUnsorted)
+    return noalloc_fail(CG_ERR_INVALID_ARG,
+                        "cg_neighbors_h1_noalloc: cells are not sorted ascending and unique");
+  if (host.error & kErrHighBits)
+    return noalloc_fail(CG_ERR_INVALID_ARG,
+                        "cg_neighbors_h1_noalloc: cells have bits set at or above l");
   if (host.error & kErrTimeout)
     return noalloc_fail(CG_ERR_TIMEOUT, "cg_neighbors_h1_noalloc: a bounded wait ran out");
-  if (host.error || host.overflow)
+  if (host.error)
     return noalloc_fail(CG_ERR_INTERNAL,
-                        "cg_neighbors_h1_noalloc: repeated cells or a device check failed");
+                        "cg_neighbors_h1_noalloc: a device-side consistency check failed");
+  if (host.overflow)
+    return noalloc_fail(CG_ERR_INTERNAL, "cg_neighbors_h1_noalloc: lookup table overflow");
   *n_edges = int64_t(host.n_edges);
   if (int64_t(host.n_edges) > edges_cap)
     return noalloc_fail(CG_ERR_CAPACITY, "cg_neighbors_h1_noalloc: edges_cap too small");
