@@ -100,6 +100,21 @@ const char* cg_version(void);
  * all threads). Host-side counter; used to report launches per step. */
 uint64_t cg_launch_count(void);
 
+/* Test control of the library's bounded device-side waits (the paper has no
+ * counterpart): every wait on another block's progress -- the edge kernels'
+ * look-back for their output offset, the BFS grid barrier, the tensor-core
+ * sign kernel's wait for its MMA -- gives up after a fixed number of polls,
+ * sets an error bit and returns, so a wait that
+ * can never end yields CG_ERR_TIMEOUT instead of a hung GPU. cg_set_wait_limit
+ * lowers that number for kernels launched afterwards by any thread of the
+ * process: `polls` = 0 makes every such wait give up before its first poll
+ * (the call then returns CG_ERR_TIMEOUT whenever the wait was needed);
+ * `polls` < 0 restores the built-in limits. Outputs of a call that timed out
+ * are unspecified (but stay within their capacities). A CUDA graph the library
+ * captured (repeated cg_build / cg_build_batch calls) keeps the limit it was
+ * captured with. For tests only. */
+cg_status cg_set_wait_limit(int64_t polls);
+
 /* ---------------------------------------------------------------------------
  * Step 1 -- sign vectors (§2.1, Figure 1).
  * keys[p] = packed [a_i . pts[p] >= b_i] for i = 0..l-1, evaluated exactly.
@@ -116,6 +131,7 @@ cg_status cg_pack_signs(const int32_t* pts, int64_t n, int d, const int32_t* a,
 /* ---------------------------------------------------------------------------
  * Step 2 -- cells: sort the multiset of vectors and remove duplicates (§3.2).
  *   keys        [n][W] words (word_bits), device, read only.
+ *               Bits at or above l in a key are ignored.
  *   cells       [cells_cap][W] words, device: the U distinct vectors in order.
  *   n_cells     host: receives U.
  *   point_cell  nullable, uint32[n], device: cell number of every input vector.
@@ -450,6 +466,9 @@ cg_status cg_server_destroy(cg_server* srv);
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture;
+ *   - like cg_neighbors_h1 it blocks until its work on `stream` is done (E is
+ *     returned through a host pointer); unsorted or repeated rows and rows
+ *     with bits at or above l give CG_ERR_INVALID_ARG, as there;
  *   - every call reuses the same array (each call clears what must start at
  *     zero); calls whose work overlaps on the GPU race and give undefined
  *     results, so serialise them.

@@ -43,6 +43,7 @@ EXPORTS = [
     "cg_server_result_get", "cg_server_copy", "cg_server_release", "cg_server_get_stats",
     "cg_server_inject_alloc_failures", "cg_server_destroy", "cg_tune_bucket", "cg_ctx_tune_get",
     "cg_ctx_tune_set", "cg_ctx_autotune", "cg_server_use_tuning", "cg_build_dev", "cg_bfs",
+    "cg_set_wait_limit",
 ]
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -140,6 +141,7 @@ def load_library(path: str = LIB_PATH):
         lib.cg_ctx_autotune.argtypes = [P, P, I, I, P]
         lib.cg_server_use_tuning.argtypes = [P, P]
         lib.cg_bfs.argtypes = [P, I64, I64, I64, P, P, PI64, PI64, P, PS, P]
+        lib.cg_set_wait_limit.argtypes = [I64]
         for name in EXPORTS[3:]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -157,6 +159,13 @@ def version() -> str:
 
 def launch_count() -> int:
     return int(load_library().cg_launch_count())
+
+
+def set_wait_limit(polls: int) -> None:
+    """Test control: bounded device-side waits of kernels launched afterwards
+    give up after ``polls`` polls (0: before the first one); a negative value
+    restores the built-in limits."""
+    _check(load_library().cg_set_wait_limit(int(polls)))
 
 
 def _torch():

@@ -635,8 +635,18 @@ static cg_status ensure_io(cg_ctx* ctx, size_t bytes) {
   return CG_OK;
 }
 
+namespace {
+// Test limit on the polls of bounded device-side waits (-1: none).
+std::atomic<int64_t> g_wait_limit{-1};
+}  // namespace
+
 namespace cg {
 void set_last_error(const char* msg) { t_err = msg; }
+
+uint32_t wait_limit(uint32_t dflt) {
+  const int64_t v = g_wait_limit.load(std::memory_order_relaxed);
+  return v < 0 || uint64_t(v) >= dflt ? dflt : uint32_t(v);
+}
 }  // namespace cg
 
 extern "C" {
@@ -646,6 +656,11 @@ const char* cg_last_error(void) { return t_err.c_str(); }
 const char* cg_version(void) { return "cellgraph 0.1 (sm_103a)"; }
 
 uint64_t cg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+cg_status cg_set_wait_limit(int64_t polls) {
+  g_wait_limit.store(polls < 0 ? -1 : polls, std::memory_order_relaxed);
+  return CG_OK;
+}
 
 cg_status cg_ctx_create(cg_ctx** out, int device) {
   if (!out) return fail(CG_ERR_INVALID_ARG, "out is NULL");

@@ -159,7 +159,7 @@ __global__ void bfs_level(int d, const unsigned long long* __restrict__ off,
 // legitimately huge frontier must not reach it: 2^26 polls of >= 64 ns.
 constexpr unsigned kBarrierSpins = 1u << 26;
 
-__device__ __forceinline__ bool grid_barrier(BfsCounters* c) {
+__device__ __forceinline__ bool grid_barrier(BfsCounters* c, uint32_t polls) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -174,7 +174,7 @@ __device__ __forceinline__ bool grid_barrier(BfsCounters* c) {
       ok = 1;
     } else {
       ok = 0;
-      for (unsigned int i = 0; i < kBarrierSpins; ++i) {
+      for (uint32_t i = 0; i < polls; ++i) {  // 0 polls gives up at once
         if (*gen != g) {
           ok = 1;
           break;
@@ -193,7 +193,7 @@ __device__ __forceinline__ bool grid_barrier(BfsCounters* c) {
 __global__ void __launch_bounds__(kThreads)
     bfs_all_levels(const unsigned long long* __restrict__ off, const uint32_t* __restrict__ deg,
                    const uint32_t* __restrict__ adj, int32_t* dist, int32_t* __restrict__ parent,
-                   uint32_t* f0, uint32_t* f1, BfsCounters* c, uint32_t n) {
+                   uint32_t* f0, uint32_t* f1, BfsCounters* c, uint32_t n, uint32_t polls) {
   for (int d = 0; d <= int(n); ++d) {
     const uint32_t cnt = *reinterpret_cast<volatile unsigned int*>(&c->frontier[d % 3]);
     if (cnt == 0) return;  // the same value in every block: all leave together
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     expand_level(d, cnt, off, deg, adj, dist, parent, (d & 1) ? f1 : f0, (d & 1) ? f0 : f1,
                  &c->frontier[(d + 1) % 3]);
-    if (!grid_barrier(c)) return;
+    if (!grid_barrier(c, polls)) return;
   }
 }
 
@@ -231,7 +231,8 @@ cudaError_t launch_bfs_single(uint32_t n, int32_t* dist, int32_t* parent, const 
   uint32_t* f0 = w.f0;
   uint32_t* f1 = w.f1;
   BfsCounters* c = w.ctr;
-  void* args[] = {&off, &deg, &adj, &dist, &parent, &f0, &f1, &c, &n};
+  uint32_t polls = wait_limit(kBarrierSpins);
+  void* args[] = {&off, &deg, &adj, &dist, &parent, &f0, &f1, &c, &n, &polls};
   e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(bfs_all_levels), dim3(grid),
                                   dim3(kThreads), args, 0, s);
   if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {

@@ -71,6 +71,9 @@ __host__ __device__ __forceinline__ uint64_t fp_bit(int k) {
 // ---------------------------------------------------------------------------
 void count_launch(int n = 1);
 void set_last_error(const char* msg);  // message returned by cg_last_error()
+// Polls a bounded device-side wait of a kernel launched now may make before it
+// gives up: `dflt`, or the smaller test limit set with cg_set_wait_limit.
+uint32_t wait_limit(uint32_t dflt);
 int sm_count();  // SMs of the current device (cached per device)
 // Raises kern's dynamic shared memory limit on the current device to at least
 // `bytes` (a runtime call only the first time a larger size is needed;

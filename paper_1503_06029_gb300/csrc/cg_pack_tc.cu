@@ -242,7 +242,7 @@ __device__ __forceinline__ void load_point(const PackArgs& pa, int64_t tile, int
 
 template <int D, int NC, class Sink>
 __global__ void __launch_bounds__(kTThreads)
-    pack_tc_kernel(PackArgs pa, Sink sink, TcSpill spill, unsigned int* error) {
+    pack_tc_kernel(PackArgs pa, Sink sink, TcSpill spill, unsigned int* error, uint32_t polls) {
   constexpr int kL = NC / 2;  // constraint slots (32 or 64)
   constexpr int kCh = kL / 32;
   static_assert(D >= 1 && D <= 4, "d");
@@ -335,8 +335,10 @@ __global__ void __launch_bounds__(kTThreads)
     write_row<D>(sh.a, tid, pts);
     fence_proxy_async();
     fence_before_sync();
-    __syncthreads();
-    bool in_range = all_ok && !timed_out;
+    // After a wait of any warp ran out, no warp starts another MMA (the
+    // decision is the same in every thread of the block).
+    const bool stop = __syncthreads_or(timed_out ? 1 : 0) != 0;
+    bool in_range = all_ok && !stop;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const uint32_t M = max(max(sh.wmax[buf][0][k], sh.wmax[buf][1][k]),
@@ -383,13 +385,9 @@ __global__ void __launch_bounds__(kTThreads)
     bool had = false;
     if (cur_mma) {
       if (lane == 0) {
-        uint32_t spins = 0;
-        while (!mbar_try_wait(mbar, phase)) {
-          if (++spins > kSpinLimit) {
-            timed_out = true;
-            break;
-          }
-        }
+        bool done = false;  // `polls` tries at most; 0 gives up at once
+        for (uint32_t spins = 0; spins < polls && !done; ++spins) done = mbar_try_wait(mbar, phase);
+        if (!done) timed_out = true;
       }
       __syncwarp();
       timed_out = __shfl_sync(0xffffffffu, timed_out ? 1 : 0, 0) != 0;
@@ -449,7 +447,8 @@ __global__ void __launch_bounds__(kTThreads)
   if (pend) sink.finish(pend_key, pend_slot, pend_cur);
   if (timed_out) {
     // An MMA that did not complete in time may still write TMEM: wait for it
-    // (bounded) before giving the columns back.
+    // (bounded, with the full limit whatever the test limit) before giving the
+    // columns back. No MMA is started after the one given up on.
     for (uint32_t spins = 0; spins < kSpinLimit && !mbar_try_wait(mbar, phase); ++spins) {
     }
   }
@@ -473,7 +472,7 @@ cudaError_t launch_tc_dn(const PackArgs& pa, const Sink& sink, TcSpill spill, un
   if (err != cudaSuccess) return err;
   const int64_t ntiles = (pa.n + kTilePts - 1) / kTilePts;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, int64_t(sm_count()) * kPerSm));
-  kern<<<unsigned(grid), kTThreads, smem, s>>>(pa, sink, spill, error);
+  kern<<<unsigned(grid), kTThreads, smem, s>>>(pa, sink, spill, error, wait_limit(kSpinLimit));
   count_launch();
   return cudaGetLastError();
 }
