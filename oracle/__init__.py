@@ -10,6 +10,8 @@ ctypes. Every function follows the paper "Massively Parallel Construction of
 the Cell Graph":
 
 * ``pack_signs``  §2.1 / Figure 1: bit i = [a_i . p >= b_i], exact.
+* ``pack_signs_quadric``  §2.1 with curved boundaries: bit i = [q_i(p) +
+                  a_i . p >= b_i], q_i an integer quadratic form, exact.
 * ``dedup``       §3.2: sort the vectors and drop duplicates.
 * ``neighbors``   §2.2 definition of G_X, searched as in Algorithm 4
                   (flip one bit, look the result up).
@@ -57,6 +59,7 @@ def _load():
             I64 = ctypes.c_int64
             I = ctypes.c_int
             lib.cgo_pack_signs.argtypes = [P, I64, I, P, P, I, I, P]
+            lib.cgo_pack_signs_quadric.argtypes = [P, I64, I, P, P, P, I, I, P]
             lib.cgo_dedup.argtypes = [P, I64, I, I, P, P, P]
             lib.cgo_neighbors_h1_rows.argtypes = [P, I64, I, I, P, I64, P, I64, P]
             lib.cgo_neighbors_h1.argtypes = [P, I64, I, I, P, I64, P]
@@ -64,7 +67,7 @@ def _load():
             lib.cgo_tree_digits.argtypes = [P, I64, I, I, I, I, P]
             lib.cgo_heuristic.argtypes = [P, I64, I, I, I, I, I, P, I64, P, P]
             lib.cgo_bfs.argtypes = [P, I64, I64, I64, P]
-            for f in (lib.cgo_pack_signs, lib.cgo_dedup, lib.cgo_neighbors_h1_rows,
+            for f in (lib.cgo_pack_signs, lib.cgo_pack_signs_quadric, lib.cgo_dedup, lib.cgo_neighbors_h1_rows,
                       lib.cgo_neighbors_h1, lib.cgo_tree, lib.cgo_tree_digits,
                       lib.cgo_heuristic, lib.cgo_bfs):
                 f.restype = ctypes.c_int
@@ -102,6 +105,35 @@ def pack_signs(pts, a, b, word_bits: int = 64) -> np.ndarray:
     if rc:
         raise RuntimeError(f"cgo_pack_signs failed: {rc}")
     return keys
+
+
+def pack_signs_quadric(pts, q, a, b, word_bits: int = 64) -> np.ndarray:
+    """Packed sign vectors of quadric constraints (bit i = [sum_{j<=k}
+    q[i, jk] p_j p_k + a[i] . p >= b[i]], exact), shape [N, ceil(l/word_bits)].
+    ``q`` int32 [l, d(d+1)/2]: monomial coefficients, (j, k) with j <= k in
+    row-major order."""
+    lib = _load()
+    pts = np.ascontiguousarray(pts, dtype=np.int32)
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    b = np.ascontiguousarray(b, dtype=np.int64)
+    n, d = pts.shape
+    ell = a.shape[0]
+    assert a.shape[1] == d and b.shape == (ell,) and q.shape == (ell, d * (d + 1) // 2)
+    keys = np.zeros((n, words(ell, word_bits)), dtype=_wtype(word_bits))
+    rc = lib.cgo_pack_signs_quadric(_ptr(pts), n, d, _ptr(q), _ptr(a), _ptr(b), ell, word_bits,
+                                    _ptr(keys))
+    if rc:
+        raise RuntimeError(f"cgo_pack_signs_quadric failed: {rc}")
+    return keys
+
+
+def build_quadric(pts, q, a, b, word_bits: int = 64):
+    """(cells, edges) of one scene of quadric constraints."""
+    keys = pack_signs_quadric(pts, q, a, b, word_bits)
+    ell = np.asarray(a).shape[0]
+    cells = dedup(keys, ell, word_bits)
+    return cells, neighbors(cells, ell, word_bits)
 
 
 def dedup(keys, ell: int, word_bits: int = 64, point_cell: bool = False):

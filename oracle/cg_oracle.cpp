@@ -25,6 +25,9 @@
 //      2^r-ary tree over the r-bit digit recoding of the cells, built level by
 //      level from index ranges of the sorted digit sequences, and the edges it
 //      finds by walking it once per flipped bit.
+//   1b. Sign vectors for quadric constraints (curved boundaries, §2.1):
+//      the same packing with bit i = [q_i(p) + a_i . p >= b_i], q_i a
+//      quadratic form with integer coefficients, in exact 128-bit arithmetic.
 //   6. Breadth-first search on G_X (§6: a path in the cell graph is an
 //      approximate solution of the motion-planning problem): distances from
 //      one cell by the textbook queue BFS over the undirected edge list.
@@ -187,6 +190,40 @@ int cgo_pack_signs(const int32_t* pts, int64_t n, int d, const int32_t* a, const
     for (int i = 0; i < ell; ++i) {
       __int128 s = 0;
       for (int k = 0; k < d; ++k) s += __int128(a[int64_t(i) * d + k]) * pts[p * d + k];
+      s -= b[i];
+      if (s >= 0) v[i / 64] |= uint64_t(1) << (i % 64);
+    }
+    store_vec(keys, p, v, ell, word_bits);
+  }
+  return 0;
+}
+
+// Step 1 for curved boundaries (§2.1: the constraints c_i are inequalities
+// whose boundaries bound the cells; §2 notes that the method carries over to
+// more complicated settings than lines): bit i of point p is
+//   [ sum_{j<=k} q_i,jk p_j p_k + sum_k a_ik p_k >= b_i ],
+// a quadric inequality with integer coefficients, evaluated exactly in 128-bit
+// integers. q int32[l][d(d+1)/2] holds the coefficient of the monomial
+// p_j p_k for j <= k, in the order (0,0), (0,1), ..., (0,d-1), (1,1), ...,
+// (d-1,d-1); a int32[l][d]; b int64[l]. With q = 0 this is cgo_pack_signs.
+int cgo_pack_signs_quadric(const int32_t* pts, int64_t n, int d, const int32_t* q,
+                           const int32_t* a, const int64_t* b, int ell, int word_bits,
+                           void* keys) {
+  if (n < 0 || d < 1 || bad_words(ell, word_bits)) return -1;
+  const int m = d * (d + 1) / 2;
+  for (int64_t p = 0; p < n; ++p) {
+    const int32_t* x = pts + p * d;
+    Vec v(words_for(ell, 64), 0);
+    for (int i = 0; i < ell; ++i) {
+      __int128 s = 0;
+      int t = 0;
+      for (int j = 0; j < d; ++j) {
+        for (int k = j; k < d; ++k, ++t) {
+          const __int128 mono = __int128(int64_t(x[j]) * int64_t(x[k]));
+          s += __int128(q[int64_t(i) * m + t]) * mono;
+        }
+      }
+      for (int k = 0; k < d; ++k) s += __int128(a[int64_t(i) * d + k]) * x[k];
       s -= b[i];
       if (s >= 0) v[i / 64] |= uint64_t(1) << (i % 64);
     }

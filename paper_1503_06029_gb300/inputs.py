@@ -20,6 +20,10 @@ Workloads (sizes are the defaults; every function takes smaller sizes for tests)
                     (rounded up to a multiple of 8) and N log-uniform in
                     [1e3, 1e6].
 * ``poisson_arrivals`` exponential inter-arrival gaps for a request stream.
+* ``spheres_3d``    l=64 spheres in 3-space (curved boundaries; bit i: outside
+                    or on sphere i), N=2**24 integer points.
+* ``quadrics_3d``   l general quadric surfaces with small integer monomial
+                    coefficients, each passing through a random anchor point.
 
 Layouts: points ``int32[N][d]`` row-major, constraint normals ``int32[l][d]``,
 offsets ``int64[l]``; packed vectors ``uint64[N][ceil(l/64)]`` with bit i of a
@@ -155,3 +159,66 @@ def poisson_arrivals(n_requests: int, rate_per_s: float, seed: int = 5) -> np.nd
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n_requests))
 
+
+
+@dataclass
+class QuadricScene:
+    """Points plus l quadric constraints: constraint i is satisfied by p iff
+    sum_{j<=k} q[i, jk] p_j p_k + a[i] . p >= b[i] (§2.1 with curved
+    boundaries). ``q`` holds the coefficient of the monomial p_j p_k for
+    j <= k, in the order (0,0), (0,1), ..., (0,d-1), (1,1), ..., (d-1,d-1)."""
+
+    pts: np.ndarray  # int32 [N, d]
+    q: np.ndarray  # int32 [l, d(d+1)/2]
+    a: np.ndarray  # int32 [l, d]
+    b: np.ndarray  # int64 [l]
+
+    @property
+    def n(self) -> int:
+        return int(self.pts.shape[0])
+
+    @property
+    def ell(self) -> int:
+        return int(self.a.shape[0])
+
+
+def _diagonal_monomials(d: int) -> list:
+    """Positions of p_j^2 in the monomial order of QuadricScene.q."""
+    pos, t = [], 0
+    for j in range(d):
+        pos.append(t)
+        t += d - j
+    return pos
+
+
+def spheres_3d(n: int = 1 << 24, ell: int = 64, seed: int = 13, d: int = 3) -> QuadricScene:
+    """l spheres: centres ~ U{-2^20..2^20}^d, radii ~ U{2^19..2^21}; bit i is 1
+    when the point lies on or outside sphere i, i.e. |p - c_i|^2 >= r_i^2,
+    written as the quadric |p|^2 - 2 c_i . p >= r_i^2 - |c_i|^2. Points ~
+    U{-2^20..2^20}^d."""
+    rng = np.random.default_rng(seed)
+    c = _uniform_int(rng, -(1 << 20), 1 << 20, (ell, d), np.int64)
+    r = _uniform_int(rng, 1 << 19, 1 << 21, (ell,), np.int64)
+    q = np.zeros((ell, d * (d + 1) // 2), np.int32)
+    q[:, _diagonal_monomials(d)] = 1
+    a = (-2 * c).astype(np.int32)
+    b = (r * r - (c * c).sum(axis=1)).astype(np.int64)
+    pts = _uniform_int(rng, -(1 << 20), 1 << 20, (n, d), np.int32)
+    return QuadricScene(pts=pts, q=q, a=a, b=b)
+
+
+def quadrics_3d(n: int = 1 << 20, ell: int = 64, seed: int = 14, d: int = 3,
+                qcoef: int = 16, coord: int = 1 << 20) -> QuadricScene:
+    """l general quadrics (ellipsoids, hyperboloids, paraboloids, saddles):
+    monomial coefficients ~ U{-qcoef..qcoef}, a ~ U{-2^20..2^20}^d, and b
+    chosen so that surface i passes through an anchor point z_i ~
+    U{-coord..coord}^d (b_i = q_i(z_i) + a_i . z_i). Points ~ U{-coord..coord}^d."""
+    rng = np.random.default_rng(seed)
+    m = d * (d + 1) // 2
+    q = _uniform_int(rng, -qcoef, qcoef, (ell, m), np.int32)
+    a = _uniform_int(rng, -(1 << 20), 1 << 20, (ell, d), np.int32)
+    z = _uniform_int(rng, -coord, coord, (ell, d), np.int64)
+    mono = np.stack([z[:, j] * z[:, k] for j in range(d) for k in range(j, d)], axis=1)
+    b = ((q.astype(np.int64) * mono).sum(axis=1) + (a.astype(np.int64) * z).sum(axis=1))
+    pts = _uniform_int(rng, -coord, coord, (n, d), np.int32)
+    return QuadricScene(pts=pts, q=q, a=a, b=b.astype(np.int64))

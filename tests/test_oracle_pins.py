@@ -21,6 +21,11 @@
   vectors, on the hypercube's closed form, for any segment count w; and the
   pivot test as printed ("> 1") finds no edge at all, which is why the oracle
   reads it as inverted.
+* Quadric constraints (curved boundaries, §2.1): with a zero quadratic form
+  they equal the half-space oracle; nested concentric spheres give the closed
+  form (l + 1 thermometer cells on a path of l edges, ties satisfied); spheres
+  written as monomials agree with the distance form in Python integers near
+  the int32 limits; renaming coordinates leaves every vector unchanged.
 * BFS on G_X (§6): distances on the hypercube are Hamming distances (closed
   form), on Figure 1's dense arrangement (Q3 minus 000) too, on a path graph
   |i - s|, and on random small graphs they equal Floyd-Warshall's.
@@ -473,3 +478,106 @@ def test_bfs_against_floyd_warshall(seed):
     for s in (0, 7, 39):
         want = [int(x) if x < inf else -1 for x in d[s]]
         assert oracle.bfs(edges, n, s).tolist() == want
+
+
+# --------------------- quadric constraints (curved boundaries) ---------------------
+
+def _monomials(d):
+    return [(j, k) for j in range(d) for k in range(j, d)]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("ell,word_bits", [(7, 32), (40, 64), (130, 64), (33, 32)])
+def test_quadric_with_zero_form_is_the_linear_oracle(d, ell, word_bits):
+    # q = 0 reduces the quadric test to the half-space test, a separate function.
+    sc = inputs.arrangement(70 + d, 3000, d, ell, 1 << 20, 1 << 40, (1 << 31) - 1)
+    q = np.zeros((ell, d * (d + 1) // 2), np.int32)
+    got = oracle.pack_signs_quadric(sc.pts, q, sc.a, sc.b, word_bits)
+    assert np.array_equal(got, oracle.pack_signs(sc.pts, sc.a, sc.b, word_bits))
+
+
+def _sphere_quadric(c, r):
+    d = c.shape[1]
+    q = np.zeros((c.shape[0], d * (d + 1) // 2), np.int32)
+    for t, (j, k) in enumerate(_monomials(d)):
+        if j == k:
+            q[:, t] = 1
+    a = (-2 * c).astype(np.int32)
+    b = np.array([int(rr) ** 2 - sum(int(x) ** 2 for x in cc) for cc, rr in zip(c, r)],
+                 dtype=np.int64)
+    return q, a, b
+
+
+def test_quadric_nested_spheres_closed_form():
+    # Concentric spheres of radii r_0 < ... < r_{l-1}: a point at distance rho
+    # from the centre has bit i = [rho >= r_i], so the cells are the l + 1
+    # "thermometer" vectors 0, 1, 11, ..., 1...1, and consecutive ones differ in
+    # one bit: the cell graph is a path with l edges. Points are placed between
+    # consecutive radii and exactly on them (a tie counts as satisfied).
+    ell, d = 50, 3
+    centre = np.array([[123456, -654321, 99999]], np.int64)
+    radii = np.cumsum(np.arange(1, ell + 1) * 1000).astype(np.int64)
+    q, a, b = _sphere_quadric(np.repeat(centre, ell, axis=0), radii)
+    rho = np.concatenate([[0], radii - 1, radii, radii + 7])
+    pts = []
+    for i, r in enumerate(rho):
+        axis = i % d
+        p = centre[0].copy()
+        p[axis] += r if i % 2 else -r
+        pts.append(p)
+    pts = np.array(pts, np.int32)
+    keys = oracle.pack_signs_quadric(pts, q, a, b, 64)
+    cells = oracle.dedup(keys, ell, 64)
+    edges = oracle.neighbors(cells, ell, 64)
+    want = [(1 << i) - 1 for i in range(ell + 1)]
+    assert rows_to_ints(cells, 64) == want
+    assert edges.tolist() == [[i, i + 1] for i in range(ell)]
+    # each point's vector counts the radii it reaches
+    for p, k in zip(rho, rows_to_ints(keys, 64)):
+        assert k == (1 << int((radii <= p).sum())) - 1
+
+
+def test_quadric_spheres_match_distance_form_at_extremes():
+    # Spheres written as monomials (|p|^2 - 2 c.p >= r^2 - |c|^2) against the
+    # distance form sum_k (p_k - c_k)^2 >= r^2 in Python integers, with
+    # coordinates near the int32 limits (products near 2^62).
+    rng = np.random.default_rng(75)
+    ell, d = 70, 3
+    c = rng.integers(-(1 << 30) + 1, 1 << 30, size=(ell, d), dtype=np.int64)
+    r = rng.integers(0, 1 << 31, size=ell, dtype=np.int64)
+    q, a, b = _sphere_quadric(c, r)
+    lim = (1 << 31) - 1
+    pts = rng.integers(-lim, lim, size=(400, d), dtype=np.int64, endpoint=True)
+    pts[:8] = [[lim, lim, lim], [-lim - 1, -lim - 1, -lim - 1], [0, 0, 0], [lim, -lim - 1, 0],
+               c[0], c[1] + [int(r[1]), 0, 0], c[2] + [0, int(r[2]) - 1, 0], c[3]]
+    pts = pts.astype(np.int32)
+    keys = oracle.pack_signs_quadric(pts, q, a, b, 64)
+    got = rows_to_ints(keys, 64)
+    for p, k in zip(pts.tolist(), got):
+        want = 0
+        for i in range(ell):
+            dist2 = sum((int(p[t]) - int(c[i][t])) ** 2 for t in range(d))
+            if dist2 >= int(r[i]) ** 2:
+                want |= 1 << i
+        assert k == want
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_quadric_invariant_under_coordinate_permutation(d):
+    # Renaming the coordinates (points, linear terms and the monomial indices
+    # together) describes the same sets: a mixed-up monomial index fails this.
+    sc = inputs.quadrics_3d(n=2000, ell=45, seed=80 + d, d=d, coord=1 << 16)
+    perm = np.random.default_rng(d).permutation(d)
+    mono = _monomials(d)
+    where = {jk: t for t, jk in enumerate(mono)}
+    q2 = np.zeros_like(sc.q)
+    for t, (j, k) in enumerate(mono):
+        pj, pk = sorted((int(np.flatnonzero(perm == j)[0]), int(np.flatnonzero(perm == k)[0])))
+        q2[:, where[(pj, pk)]] = sc.q[:, t]
+    # new coordinate i is old coordinate perm[i]
+    a2 = sc.a[:, perm]
+    pts2 = sc.pts[:, perm]
+    k1 = oracle.pack_signs_quadric(sc.pts, sc.q, sc.a, sc.b, 64)
+    k2 = oracle.pack_signs_quadric(pts2, q2, a2, sc.b, 64)
+    assert np.array_equal(k1, k2)
+    assert len(set(rows_to_ints(k1, 64))) > 20
