@@ -129,6 +129,26 @@ cg_status cg_pack_signs(const int32_t* pts, int64_t n, int d, const int32_t* a,
                         void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Step 1 for curved boundaries -- sign vectors of quadric constraints (§2.1:
+ * the constraints are inequalities whose boundaries partition the space into
+ * cells; the paper's figure uses lines, motion-planning scenes need curves).
+ * keys[p] = packed [ sum_{j<=k} q_i,jk p_j p_k + a_i . pts[p] >= b_i ] for
+ * i = 0..l-1, evaluated exactly for every int32 input and int64 offset.
+ *   pts   int32[n][d] row-major, device.
+ *   q     int32[l][d(d+1)/2] row-major, device: coefficient of the monomial
+ *         p_j p_k (j <= k), in the order (0,0), (0,1), ..., (0,d-1), (1,1),
+ *         ..., (d-1,d-1). A sphere |p - c|^2 >= r^2 is q = 1 on the squares,
+ *         0 elsewhere, a = -2c, b = r^2 - |c|^2.
+ *   a     int32[l][d] row-major, device.    b  int64[l], device.
+ *   keys  [n][W] words of word_bits bits, device, written entirely.
+ * 1 <= d <= 4, 1 <= l <= 4096. n = 0 is allowed. No workspace; asynchronous.
+ * The keys feed cg_dedup_cells and cg_neighbors_h1 unchanged.
+ * ------------------------------------------------------------------------- */
+cg_status cg_pack_signs_quadric(const int32_t* pts, int64_t n, int d, const int32_t* q,
+                                const int32_t* a, const int64_t* b, int ell, int word_bits,
+                                void* keys, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Step 2 -- cells: sort the multiset of vectors and remove duplicates (§3.2).
  *   keys        [n][W] words (word_bits), device, read only.
  *               Bits at or above l in a key are ignored.

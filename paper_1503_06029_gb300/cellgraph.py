@@ -43,7 +43,7 @@ EXPORTS = [
     "cg_server_result_get", "cg_server_copy", "cg_server_release", "cg_server_get_stats",
     "cg_server_inject_alloc_failures", "cg_server_destroy", "cg_tune_bucket", "cg_ctx_tune_get",
     "cg_ctx_tune_set", "cg_ctx_autotune", "cg_server_use_tuning", "cg_build_dev", "cg_bfs",
-    "cg_set_wait_limit",
+    "cg_set_wait_limit", "cg_pack_signs_quadric",
 ]
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -142,6 +142,7 @@ def load_library(path: str = LIB_PATH):
         lib.cg_server_use_tuning.argtypes = [P, P]
         lib.cg_bfs.argtypes = [P, I64, I64, I64, P, P, PI64, PI64, P, PS, P]
         lib.cg_set_wait_limit.argtypes = [I64]
+        lib.cg_pack_signs_quadric.argtypes = [P, I64, I, P, P, P, I, I, P, P]
         for name in EXPORTS[3:]:
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -216,6 +217,34 @@ def pack_signs(pts, a, b, word_bits: int = 64, out=None, stream=None):
                              _dev(b, torch.int64, "b"), ell, word_bits,
                              _dev(out, word_dtype(word_bits), "keys"), _stream_ptr(stream)))
     return out
+
+
+def pack_signs_quadric(pts, q, a, b, word_bits: int = 64, out=None, stream=None):
+    """Sign vectors of quadric constraints (§2.1 with curved boundaries):
+    bit i = [sum_{j<=k} q[i, jk] p_j p_k + a[i] . p >= b[i]], exact. ``q`` is
+    int32 [l, d(d+1)/2] (monomial coefficients, (j, k) with j <= k in
+    row-major order). Returns [N, W] words on the device."""
+    torch = _torch()
+    lib = load_library()
+    n, d = pts.shape
+    ell = a.shape[0]
+    if out is None:
+        out = torch.empty((n, words(ell, word_bits)), dtype=word_dtype(word_bits),
+                          device=pts.device)
+    _check(lib.cg_pack_signs_quadric(
+        _dev(pts, torch.int32, "pts"), n, d, _dev(q, torch.int32, "q"),
+        _dev(a, torch.int32, "a"), _dev(b, torch.int64, "b"), ell, word_bits,
+        _dev(out, word_dtype(word_bits), "keys"), _stream_ptr(stream)))
+    return out
+
+
+def build_quadric(pts, q, a, b, word_bits: int = 64, strategy: str = "auto", stream=None):
+    """Cells and edges of a scene of quadric constraints: cg_pack_signs_quadric,
+    cg_dedup_cells and cg_neighbors_h1 in turn (device tensors in and out)."""
+    ell = a.shape[0]
+    keys = pack_signs_quadric(pts, q, a, b, word_bits, stream=stream)
+    cells = dedup_cells(keys, ell, word_bits, stream=stream)
+    return cells, neighbors_h1(cells, ell, word_bits, strategy=strategy, stream=stream)
 
 
 def dedup_cells(keys, ell: int, word_bits: int = 64, point_cell: bool = False, stream=None):
