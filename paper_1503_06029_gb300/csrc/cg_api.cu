@@ -783,7 +783,8 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
   DevCounters host{};
   if (small) {
     SmallWs w = carve_small(c, cap, ucap, ell, true, false, false);
-    CG_CUDA(launch_clear_build(w.tkeys, cap, nullptr, 0, w.ctr, s), "clearing table");
+    CG_CUDA(launch_clear_build(w.tkeys, cap, nullptr, 0, w.ctr, s, nullptr, 0, w.tvals, cap),
+            "clearing table");
     SmallTable t = w.table(true);
     CG_CUDA(launch_insert_small(keys, n, word_bits, ell, t, s), "inserting vectors");
     cg_status st = dedup_small_tail(w, ell, word_bits, cells, cells_cap, s);
@@ -1170,8 +1171,11 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
     return CG_OK;
   }
   if (plan.small) {
+    // The table values start at zero: the rank sort of few distinct vectors
+    // accumulates each cell's number there.
     CG_CUDA(launch_clear_build(w.tkeys, plan.cap, own ? nullptr : w.status,
-                               own ? 0 : ne_status_words(plan.ucap), w.ctr, s),
+                               own ? 0 : ne_status_words(plan.ucap), w.ctr, s, nullptr, 0,
+                               w.tvals, plan.cap),
             "clearing table");
     mark(ctx, "clear", s);
     if (n > 0) {

@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 __global__ void clear_build(uint64_t* table, size_t cap, uint64_t* table2, size_t cap2,
-                            unsigned long long* status, size_t n_status, DevCounters* ctr) {
+                            unsigned long long* status, size_t n_status, DevCounters* ctr,
+                            uint32_t* zero32, size_t n_zero32) {
   if (blockIdx.x == 0 && threadIdx.x < sizeof(DevCounters) / 4)
     reinterpret_cast<uint32_t*>(ctr)[threadIdx.x] = 0;
   const size_t stride = size_t(gridDim.x) * blockDim.x;
@@ -276,6 +277,8 @@ __global__ void clear_build(uint64_t* table, size_t cap, uint64_t* table2, size_
     table2[i] = kEmpty;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n_status; i += stride)
     status[i] = 0;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n_zero32; i += stride)
+    zero32[i] = 0;
 }
 
 // Steps 3-4 in one pass (l <= 64). Work is handed out in chunks of 32 cells
@@ -946,9 +949,11 @@ cudaError_t launch_zero_counters(DevCounters* c, cudaStream_t s) {
 
 cudaError_t launch_clear_build(uint64_t* table, size_t cap, unsigned long long* status,
                                size_t n_status, DevCounters* ctr, cudaStream_t s,
-                               uint64_t* table2, size_t cap2) {
-  clear_build<<<grid_for(std::max(std::max(cap, cap2), n_status) + 1, kThreads * 4, 16), kThreads,
-                0, s>>>(table, cap, table2, cap2, status, n_status, ctr);
+                               uint64_t* table2, size_t cap2, uint32_t* zero32,
+                               size_t n_zero32) {
+  const size_t most = std::max(std::max(std::max(cap, cap2), n_status), n_zero32);
+  clear_build<<<grid_for(most + 1, kThreads * 4, 16), kThreads, 0, s>>>(
+      table, cap, table2, cap2, status, n_status, ctr, zero32, n_zero32);
   return finish(0);
 }
 

@@ -301,10 +301,12 @@ cudaError_t launch_publish_counts(const DevCounters* ctr, int64_t* out, int64_t 
                                   int64_t edges_cap, cudaStream_t s);
 
 // Clears a build's table (kEmpty), the look-back status words and the counters.
-// (A second table, table2/cap2, may be cleared in the same launch.)
+// (A second table, table2/cap2, and an array of 32-bit words to be zeroed,
+// zero32/n_zero32, may be cleared in the same launch.)
 cudaError_t launch_clear_build(uint64_t* table, size_t cap, unsigned long long* status,
                                size_t n_status, DevCounters* ctr, cudaStream_t s,
-                               uint64_t* table2 = nullptr, size_t cap2 = 0);
+                               uint64_t* table2 = nullptr, size_t cap2 = 0,
+                               uint32_t* zero32 = nullptr, size_t n_zero32 = 0);
 
 // Sorts U = min(*n_dev, max_n) distinct vectors of W = ceil(l/64) <= 4 words
 // inside one thread-block cluster (keys held in distributed shared memory),

@@ -277,7 +277,9 @@ __global__ void __launch_bounds__(kCThreads)
   __shared__ uint32_t toff[256];
   __shared__ uint32_t wtot[8];
   __shared__ int skip;
-  if (o.ctr->overflow) return;  // same value for every CTA of the cluster
+  // Same values for every CTA of the cluster: a table overflow, or the rank
+  // sort (few distinct vectors) already did this work.
+  if (o.ctr->overflow || o.ctr->sorted) return;
   const uint32_t C = cluster.num_blocks();
   const uint32_t r = cluster.block_rank();
   const int tid = threadIdx.x;
@@ -479,6 +481,99 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
     return cudaGetLastError();
   }
   return cudaSuccess;
+}
+
+// ------------------------- rank sort of few vectors -------------------------
+//
+// For up to kRankMax distinct vectors of one word the cluster sort's eight
+// barrier-separated passes cost more than counting: the rank of key k_i among
+// distinct keys is #{j : k_j < k_i}. rank_count splits the n^2 comparisons
+// over (256 keys) x (one of kRankSplits slices of all keys) blocks: a block
+// stages its slice in shared memory (every thread reads the same entry, a
+// broadcast) and adds each key's partial count to the key's value slot in
+// the dedup table (zeroed by the build's clear; the all-ones vector, which
+// has no slot, counts in ctr->ones_rank). rank_place then writes every key at
+// its rank, with the same outputs as the cluster sort (internal cells, the
+// caller's copy, the cell number already in the table).
+constexpr uint32_t kRankMax = 12288;
+constexpr int kRankSplits = 16;
+constexpr uint32_t kRankSlice = (kRankMax + kRankSplits - 1) / kRankSplits;  // 768
+constexpr int kRankThreads = 256;
+
+__device__ __forceinline__ bool rank_applies(const ClusterSortOut& o, uint32_t n, uint32_t max_n) {
+  return !o.ctr->overflow && n <= kRankMax && n <= max_n && o.t.keys != nullptr;
+}
+
+__global__ void __launch_bounds__(kRankThreads)
+    rank_count(const uint64_t* __restrict__ in, const unsigned int* n_dev, uint32_t max_n,
+               ClusterSortOut o) {
+  __shared__ ulonglong2 sk[kRankSlice / 2 + 1];
+  const uint32_t n = *n_dev;
+  if (!rank_applies(o, n, max_n)) return;  // the cluster sort takes it
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) o.ctr->sorted = 1u;
+  const uint32_t i0 = blockIdx.x * kRankThreads;
+  if (i0 >= n) return;
+  const uint32_t per = (n + kRankSplits - 1) / kRankSplits;
+  const uint32_t j0 = min(n, blockIdx.y * per);
+  const uint32_t m = min(n, j0 + per) - j0;
+  uint64_t* flat = reinterpret_cast<uint64_t*>(sk);
+  for (uint32_t t = threadIdx.x; t < m; t += kRankThreads) flat[t] = __ldg(in + j0 + t);
+  if (threadIdx.x == 0) flat[m] = kEmpty;  // pad: no key is above the all-ones value
+  __syncthreads();
+  const uint32_t i = i0 + threadIdx.x;
+  if (i >= n || m == 0) return;
+  const uint64_t ki = __ldg(in + i);
+  uint32_t c0 = 0, c1 = 0;
+  const uint32_t pairs = (m + 1) / 2;
+#pragma unroll 8
+  for (uint32_t q = 0; q < pairs; ++q) {
+    const ulonglong2 v = sk[q];
+    c0 += v.x < ki;
+    c1 += v.y < ki;
+  }
+  const uint32_t c = c0 + c1;
+  if (c == 0) return;
+  if (ki == kEmpty) {
+    atomicAdd(&o.ctr->ones_rank, c);
+  } else {
+    const int64_t slot = small_find_slot(o.t.keys, o.t.mask, o.t.shift, ki);
+    if (slot >= 0) atomicAdd(&o.t.vals[slot], c);
+    else atomicOr(&o.ctr->error, 1u);
+  }
+}
+
+__global__ void __launch_bounds__(kRankThreads)
+    rank_place(const uint64_t* __restrict__ in, const unsigned int* n_dev, uint32_t max_n,
+               ClusterSortOut o) {
+  const uint32_t n = *n_dev;
+  if (!rank_applies(o, n, max_n)) return;
+  const bool user = o.user_cells && int64_t(n) <= o.user_cap;
+  for (uint32_t i = blockIdx.x * kRankThreads + threadIdx.x; i < n;
+       i += gridDim.x * kRankThreads) {
+    const uint64_t ki = in[i];
+    uint32_t g;
+    if (ki == kEmpty) {
+      g = o.ctr->ones_rank;
+    } else {
+      const int64_t slot = small_find_slot(o.t.keys, o.t.mask, o.t.shift, ki);
+      if (slot < 0) continue;  // reported by rank_count
+      g = o.t.vals[slot];
+    }
+    if (g >= n) {
+      atomicOr(&o.ctr->error, 1u);
+      continue;
+    }
+    o.cells[g] = ki;
+    if (user) {
+      if (o.word_bits == 64) {
+        static_cast<uint64_t*>(o.user_cells)[g] = ki;
+      } else {
+        const int wc = (o.ell + 31) / 32;
+        uint32_t* u32 = static_cast<uint32_t*>(o.user_cells) + uint64_t(g) * wc;
+        for (int c = 0; c < wc; ++c) u32[c] = uint32_t(ki >> (32 * c));
+      }
+    }
+  }
 }
 
 // ------------------------- merge sort of wide rows -------------------------
@@ -1136,6 +1231,22 @@ cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigne
   if (tried) *tried = false;
   const int w = (ell + 63) / 64;
   const int top = ell - 64 * (w - 1);
+  if (w == 1 && !rows && max_n > 0 && o.t.keys) {
+    // Decided on the device: a count above kRankMax leaves the work (and
+    // o.ctr->sorted) to the cluster sort launched next.
+    const uint32_t cap = uint32_t(std::min<size_t>(max_n, kRankMax));
+    const dim3 grid((cap + kRankThreads - 1) / kRankThreads, kRankSplits);
+    rank_count<<<grid, kRankThreads, 0, s>>>(in, n_dev, uint32_t(max_n), o);
+    rank_place<<<(cap + kRankThreads - 1) / kRankThreads, kRankThreads, 0, s>>>(
+        in, n_dev, uint32_t(max_n), o);
+    count_launch(2);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (max_n <= kRankMax) {
+      *done = true;
+      return cudaSuccess;
+    }
+  }
   switch (w) {
     case 1: return cluster_sort_w<1>(in, rows, n_dev, max_n, top, o, s, done, tried);
     case 2: return cluster_sort_w<2>(in, rows, n_dev, max_n, top, o, s, done, tried);
