@@ -346,9 +346,12 @@ cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t*
 // Steps 3-4 with the PIVOT strategy over sorted internal rows (w64 words,
 // U in ctr->n_unique, at most ucap): keys, sort by key, bucket index,
 // counting search, scan, writing search, per-cell ordering.
+// part: 0 = everything; 1 = up to the (key, cell) pairs in k0/i0, unsorted;
+// 2 = the rest, with those pairs already sorted in k0/i0 (a batch sorts the
+// pairs of all its scenes at once between parts 1 and 2).
 cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
                       const PivotWs& p, size_t ucap, uint32_t* edges, int64_t edges_cap,
-                      cudaStream_t s, int strategy) {
+                      cudaStream_t s, int strategy, int part = 0) {
   if (strategy == CG_STRATEGY_ALLPAIRS) {
     CG_CUDA(launch_pivot_keys(cells, w64, ell, h, ctr, ucap, p.kcell, p.k0, p.i0, s),
             "pivot distances");
@@ -363,26 +366,33 @@ cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounter
     // numbers, the H folds in sorted order in the spare key buffer.
     uint64_t* fl = static_cast<uint64_t*>(p.table);
     uint64_t* fh = fl + ucap;
-    CG_CUDA(launch_halves_keys(cells, w64, ell, ctr, ucap, p.kcell, fl, fh, p.k0, p.i0, s),
-            "part keys");
+    if (part != 2)
+      CG_CUDA(launch_halves_keys(cells, w64, ell, ctr, ucap, p.kcell, fl, fh, p.k0, p.i0, s),
+              "part keys");
+    if (part == 1) return CG_OK;
     bool in1 = false;
-    CG_CUDA(radix_sort_u64(p.k0, p.k1, p.i0, p.i1, &ctr->n_unique, ucap, halves_sort_bits(ell),
-                           p.radix, s, &in1),
-            "sorting by the low part");
+    if (part == 0)
+      CG_CUDA(radix_sort_u64(p.k0, p.k1, p.i0, p.i1, &ctr->n_unique, ucap,
+                             halves_sort_bits(ell), p.radix, s, &in1),
+              "sorting by the low part");
     CG_CUDA(launch_halves_edges(cells, w64, ell, ctr, ucap, p.kcell, fl, fh, in1 ? p.k1 : p.k0,
                                 in1 ? p.i1 : p.i0, in1 ? p.k0 : p.k1, p.counts, p.hbuf,
                                 p.offsets, p.fill, p.scan, edges, edges_cap, s),
             "two-part neighbour search and edge output");
     return CG_OK;
   }
-  CG_CUDA(launch_fill_u64(static_cast<uint64_t*>(p.table), kEmpty, 2 * p.tcap, s),
-          "clearing the bucket table");
-  CG_CUDA(launch_pivot_keys(cells, w64, ell, h, ctr, ucap, p.kcell, p.k0, p.i0, s),
-          "pivot distances");
+  if (part != 2) {
+    CG_CUDA(launch_fill_u64(static_cast<uint64_t*>(p.table), kEmpty, 2 * p.tcap, s),
+            "clearing the bucket table");
+    CG_CUDA(launch_pivot_keys(cells, w64, ell, h, ctr, ucap, p.kcell, p.k0, p.i0, s),
+            "pivot distances");
+  }
+  if (part == 1) return CG_OK;
   bool in1 = false;
-  CG_CUDA(radix_sort_u64(p.k0, p.k1, p.i0, p.i1, &ctr->n_unique, ucap, pivot_sort_bits(ell, h),
-                         p.radix, s, &in1),
-          "sorting by pivot distances");
+  if (part == 0)
+    CG_CUDA(radix_sort_u64(p.k0, p.k1, p.i0, p.i1, &ctr->n_unique, ucap,
+                           pivot_sort_bits(ell, h), p.radix, s, &in1),
+            "sorting by pivot distances");
   const uint64_t* sk = in1 ? p.k1 : p.k0;
   const uint32_t* si = in1 ? p.i1 : p.i0;
   CG_CUDA(launch_pivot_index(sk, ctr, ucap, p.table, p.tcap, ctr, s), "bucket index");
@@ -1103,6 +1113,47 @@ size_t scene_ws_bytes(const ScenePlan& p) {
 // U <= cells_cap), edges to `edges` (up to edges_cap).
 bool scene_batch_sortable(const ScenePlan& plan) { return plan.small || plan.single; }
 
+bool keysort_strategy(int strategy) {
+  return strategy == CG_STRATEGY_PIVOT || strategy == CG_STRATEGY_HALVES;
+}
+
+int scene_key_bits(const ScenePlan& plan) {
+  return plan.tp.strategy == CG_STRATEGY_HALVES ? halves_sort_bits(plan.ell)
+                                                : pivot_sort_bits(plan.ell, plan.tp.pivots);
+}
+
+// Descriptors of a scene of l <= 64 (plan.small) for the segmented batch
+// kernels: its clear, its sign + insert, and its single-pass search (HASH or
+// SORTED; edges to `edges`, at most edges_cap).
+void scene_small_descs(char* ws, DevCounters* ctr, const ScenePlan& plan, const PackArgs& pa,
+                       uint64_t tile0, uint32_t* edges, int64_t edges_cap, SegClear* clr,
+                       SegPackScene* pk, SegSearchScene* se) {
+  Carve c{ws};
+  SmallWs w{};
+  WideWs ww{};
+  PivotWs pw{};
+  TreeWs tw{};
+  carve_scene(c, plan, ctr, &w, &ww, &pw, &tw);
+  const bool own = plan.tp.strategy == CG_STRATEGY_PIVOT ||
+                   plan.tp.strategy == CG_STRATEGY_HALVES || plan.tp.strategy == CG_STRATEGY_TREE;
+  if (clr)
+    *clr = SegClear{w.tkeys, w.tvals, plan.cap, own ? nullptr : w.status,
+                    own ? 0 : ne_status_words(plan.ucap), ctr};
+  if (pk) *pk = SegPackScene{pa.pts, pa.n, pa.a, pa.b, pa.ell, w.table(true), tile0};
+  if (se) *se = SegSearchScene{w.sortbuf, w.table(false), w.status, edges, edges_cap, plan.ell,
+                               uint32_t(plan.ucap)};
+}
+
+SegSortScene scene_keysort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan) {
+  Carve c{ws};
+  SmallWs w{};
+  WideWs ww{};
+  PivotWs pw{};
+  TreeWs tw{};
+  carve_scene(c, plan, ctr, &w, &ww, &pw, &tw);
+  return SegSortScene{pw.k0, pw.i0, &ctr->n_unique, uint32_t(plan.ucap)};
+}
+
 BatchSortScene scene_sort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan,
                                uint64_t* user_cells, int64_t user_cap) {
   Carve c{ws};
@@ -1147,19 +1198,25 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   const bool tree = strategy == CG_STRATEGY_TREE;
   const bool own = pivot || tree;
   cg_status st;
-  if (phase == kPhaseSearch) {
+  if (phase == kPhaseSearch || phase == kPhaseSearchKeys || phase == kPhaseSearchRest) {
     // After a batch sort: the sorted cells (and, for l <= 64, the cell
-    // numbers in the table) are in place.
+    // numbers in the table) are in place. With the key phases, a PIVOT or
+    // HALVES search stops at its (key, cell) pairs and resumes once the
+    // batch has sorted every scene's pairs; other searches run whole in
+    // kPhaseSearchKeys.
     const int w64 = (ell + 63) / 64;
+    const bool split = keysort_strategy(strategy);
+    if (phase == kPhaseSearchRest && !split) return CG_OK;
+    const int part = !split ? 0 : phase == kPhaseSearchKeys ? 1 : phase == kPhaseSearchRest ? 2 : 0;
     if (plan.small) {
       w.cells = w.sortbuf;
       if (pivot) return pivot_steps(w.cells, 1, ell, plan.tp.pivots, w.ctr, pw, plan.ucap, edges,
-                                    edges_cap, s, strategy);
+                                    edges_cap, s, strategy, part);
       if (tree) return tree_steps(w.cells, 1, ell, w.ctr, tw, plan.ucap, edges, edges_cap, s);
       return neighbors_small_steps(w, ell, strategy, edges, edges_cap, s);
     }
     if (pivot) return pivot_steps(ww.cells, w64, ell, plan.tp.pivots, ww.ctr, pw, plan.ucap, edges,
-                                  edges_cap, s, strategy);
+                                  edges_cap, s, strategy, part);
     if (tree) return tree_steps(ww.cells, w64, ell, ww.ctr, tw, plan.ucap, edges, edges_cap, s);
     WideTable it{ww.slots2, uint32_t(plan.cap - 1), nullptr, 0, ww.ctr};
     if (strategy != CG_STRATEGY_SORTED)
@@ -1663,7 +1720,10 @@ struct BatchScene {
   int w;
   size_t ecap;
   size_t ws_off, cells_off, edges_off;
-  bool sorted;  // sorted together with the other scenes (batch sort)
+  bool sorted;   // sorted together with the other scenes (batch sort)
+  bool keysort;  // PIVOT / HALVES: its (key, cell) pairs sorted with the others' (seg_sort)
+  bool seg_insert;  // l <= 64, fp32 sign kernel: cleared and packed by the segmented kernels
+  bool seg_search;  // l <= 64, HASH or SORTED: searched by the segmented edge kernel
 };
 
 }  // namespace
@@ -1800,8 +1860,15 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     m.take<long long>(size_t(S) + 1);
     m.take<int>(1);
     m.take<BatchSortScene>(size_t(S));
-    size_t sort_cap = 0;
-    int n_sorted = 0;
+    m.take<SegSortScene>(size_t(S));
+    m.take<SegClear>(size_t(S));
+    m.take<SegPackScene>(size_t(S));
+    m.take<SegSearchScene>(size_t(S));
+    m.take<unsigned int>(2 * (size_t(S) + 2));
+    size_t sort_cap = 0, ks_cap = 0;
+    int n_sorted = 0, n_ks = 0, ks_bits = 1;
+    const char* sk_env = std::getenv("CG_SIGN_KERNEL");
+    const bool env_tc = sk_env && std::strcmp(sk_env, "tc") == 0;
     for (int i = 0; i < S; ++i) {
       const cg_scene& sc = scenes[i];
       const auto key = std::make_tuple(sc.n, sc.ell, sc.d);
@@ -1827,12 +1894,36 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
         sort_cap += b.plan.ucap;
         ++n_sorted;
       }
+      b.keysort = b.sorted && keysort_strategy(b.plan.tp.strategy);
+      b.seg_insert = b.sorted && b.plan.small && !env_tc && b.plan.tp.sign_kernel != 1;
+      b.seg_search = b.sorted && b.plan.small && (b.plan.tp.strategy == CG_STRATEGY_HASH ||
+                                                  b.plan.tp.strategy == CG_STRATEGY_SORTED);
+      if (b.keysort) {
+        ks_cap += b.plan.ucap;
+        ++n_ks;
+        ks_bits = std::max(ks_bits, scene_key_bits(b.plan));
+      }
+    }
+    {
+      // The scene number goes above the key bits of the segmented sort.
+      int scene_bits = 0;
+      while ((1 << scene_bits) < n_ks) ++scene_bits;
+      if (n_ks && ks_bits + scene_bits > 64) {
+        for (BatchScene& b : bs) b.keysort = false;
+        n_ks = 0;
+        ks_cap = 0;
+      }
     }
     const size_t sort_off = m.off = (m.off + 255) & ~size_t(255);
     m.off += batch_sort_bytes(sort_cap, n_sorted);
+    const size_t ks_off = m.off = (m.off + 255) & ~size_t(255);
+    if (n_ks) m.off += seg_sort_bytes(ks_cap, n_ks);
     const size_t host_bytes = size_t(S) * (sizeof(BatchEntry) + sizeof(DevCounters)) +
                               2 * (size_t(S) + 1) * sizeof(long long) + 256 +
-                              size_t(S) * sizeof(BatchSortScene) + 256;
+                              size_t(S) * sizeof(BatchSortScene) + 256 +
+                              size_t(S) * sizeof(SegSortScene) + 256 +
+                              size_t(S) * (sizeof(SegClear) + sizeof(SegPackScene) +
+                                           sizeof(SegSearchScene)) + 3 * 256;
     cg_status st = ensure_batch_resources(ctx, m.off + 256, host_bytes);
     if (st) return st;
     // The batch runs on the context's own stream, after the caller's work.
@@ -1847,6 +1938,11 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     long long* eoff = c.take<long long>(size_t(S) + 1);
     int* okp = c.take<int>(1);
     BatchSortScene* dsort = c.take<BatchSortScene>(size_t(S));
+    SegSortScene* dks = c.take<SegSortScene>(size_t(S));
+    SegClear* dclr = c.take<SegClear>(size_t(S));
+    SegPackScene* dpk = c.take<SegPackScene>(size_t(S));
+    SegSearchScene* dse = c.take<SegSearchScene>(size_t(S));
+    unsigned int* dse_scratch = c.take<unsigned int>(2 * (size_t(S) + 2));
     char* hb = static_cast<char*>(ctx->bhost);
     BatchEntry* htab = reinterpret_cast<BatchEntry*>(hb);
     DevCounters* hctr = reinterpret_cast<DevCounters*>(hb + size_t(S) * sizeof(BatchEntry));
@@ -1855,6 +1951,63 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     int* hok = reinterpret_cast<int*>(heoff + (S + 1));
     BatchSortScene* hsort = reinterpret_cast<BatchSortScene*>(
         (reinterpret_cast<uintptr_t>(hok + 1) + 255) & ~uintptr_t(255));
+    SegSortScene* hks = reinterpret_cast<SegSortScene*>(
+        (reinterpret_cast<uintptr_t>(hsort + S) + 255) & ~uintptr_t(255));
+    for (int i = 0, k = 0; i < S; ++i) {
+      const BatchScene& b = bs[size_t(i)];
+      if (b.keysort) hks[k++] = scene_keysort_desc(base + b.ws_off, ctrs + i, b.plan);
+    }
+    SegClear* hclr = reinterpret_cast<SegClear*>(
+        (reinterpret_cast<uintptr_t>(hks + S) + 255) & ~uintptr_t(255));
+    SegPackScene* hpk = reinterpret_cast<SegPackScene*>(
+        (reinterpret_cast<uintptr_t>(hclr + S) + 255) & ~uintptr_t(255));
+    SegSearchScene* hse = reinterpret_cast<SegSearchScene*>(
+        (reinterpret_cast<uintptr_t>(hpk + S) + 255) & ~uintptr_t(255));
+    // Segmented small scenes: clears; packs grouped by (d, constraint chunks),
+    // each group numbering its 128-point tiles from 0; searches, HASH first.
+    struct PackGroup {
+      int d, nch, first, count;
+      uint64_t tiles;
+    };
+    std::vector<PackGroup> pgroups;
+    int n_clr = 0, n_pk = 0, n_se_hash = 0, n_se_sorted = 0;
+    size_t se_chunks_hash = 0, se_chunks_sorted = 0;
+    for (int d = 1; d <= 4; ++d)
+      for (int nch = 1; nch <= 2; ++nch) {
+        PackGroup gr{d, nch, n_pk, 0, 0};
+        for (int i = 0; i < S; ++i) {
+          const BatchScene& b = bs[size_t(i)];
+          const cg_scene& sc = scenes[i];
+          if (!b.seg_insert || sc.d != d || (sc.ell > 32 ? 2 : 1) != nch) continue;
+          const PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
+          scene_small_descs(base + b.ws_off, ctrs + i, b.plan, pa, gr.tiles, nullptr, 0,
+                            &hclr[n_clr++], sc.n > 0 ? &hpk[n_pk] : nullptr, nullptr);
+          if (sc.n > 0) {
+            ++n_pk;
+            ++gr.count;
+            gr.tiles += uint64_t((sc.n + 127) / 128);
+          }
+        }
+        if (gr.count) pgroups.push_back(gr);
+      }
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i < S; ++i) {
+        const BatchScene& b = bs[size_t(i)];
+        if (!b.seg_search || (b.plan.tp.strategy == CG_STRATEGY_SORTED) != (pass == 1)) continue;
+        const cg_scene& sc = scenes[i];
+        const PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
+        scene_small_descs(base + b.ws_off, ctrs + i, b.plan, pa, 0,
+                          reinterpret_cast<uint32_t*>(base + b.edges_off), int64_t(b.ecap),
+                          nullptr, nullptr, &hse[n_se_hash + n_se_sorted]);
+        const size_t chunks = (b.plan.ucap + 31) / 32;
+        if (pass == 0) {
+          ++n_se_hash;
+          se_chunks_hash += chunks;
+        } else {
+          ++n_se_sorted;
+          se_chunks_sorted += chunks;
+        }
+      }
     for (int i = 0, k = 0; i < S; ++i) {
       const BatchScene& b = bs[size_t(i)];
       htab[i] = BatchEntry{ctrs + i, reinterpret_cast<const uint64_t*>(base + b.cells_off),
@@ -1893,6 +2046,22 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
         CG_CUDA(cudaMemcpyAsync(dsort, hsort, size_t(n_sorted) * sizeof(BatchSortScene),
                                 cudaMemcpyHostToDevice, s0),
                 "uploading the sort table");
+      if (n_ks)
+        CG_CUDA(cudaMemcpyAsync(dks, hks, size_t(n_ks) * sizeof(SegSortScene),
+                                cudaMemcpyHostToDevice, s0),
+                "uploading the key-sort table");
+      if (n_clr)
+        CG_CUDA(cudaMemcpyAsync(dclr, hclr, size_t(n_clr) * sizeof(SegClear),
+                                cudaMemcpyHostToDevice, s0),
+                "uploading the clear table");
+      if (n_pk)
+        CG_CUDA(cudaMemcpyAsync(dpk, hpk, size_t(n_pk) * sizeof(SegPackScene),
+                                cudaMemcpyHostToDevice, s0),
+                "uploading the sign table");
+      if (n_se_hash + n_se_sorted)
+        CG_CUDA(cudaMemcpyAsync(dse, hse, size_t(n_se_hash + n_se_sorted) * sizeof(SegSearchScene),
+                                cudaMemcpyHostToDevice, s0),
+                "uploading the search table");
       auto fork = [&]() -> cg_status {
         CG_CUDA(cudaEventRecord(ctx->fork_ev, s0), "fork");
         for (auto& w : ctx->workers) CG_CUDA(cudaStreamWaitEvent(w, ctx->fork_ev, 0), "fork");
@@ -1910,10 +2079,16 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       mark(ctx, "batch_start", s0);
       // Up to the dedup insert (whole builds for the scenes not sorted
       // together), then one sort of every other scene's distinct vectors,
-      // then their neighbour searches.
+      // then their neighbour searches. The scenes of l <= 64 are cleared and
+      // packed by a few segmented launches on the batch stream meanwhile.
+      if (n_clr) CG_CUDA(launch_clear_seg(dclr, n_clr, s0), "clearing small scenes");
+      for (const PackGroup& gr : pgroups)
+        CG_CUDA(launch_pack_insert_seg(dpk + gr.first, gr.count, gr.tiles, gr.d, gr.nch, s0),
+                "sign vectors + dedup (small scenes)");
       for (int i : order) {
         const cg_scene& sc = scenes[i];
         const BatchScene& b = bs[size_t(i)];
+        if (b.seg_insert) continue;
         PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
         st2 = enqueue_scene(nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64, base + b.cells_off,
                             int64_t(b.plan.ucap), reinterpret_cast<uint32_t*>(base + b.edges_off),
@@ -1927,16 +2102,38 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
         CG_CUDA(batch_sort(dsort, n_sorted, sort_cap, base + sort_off, s0), "batch sort");
         mark(ctx, "batch_sort", s0);
         if ((st2 = fork())) return st2;
-        for (int i : order) {
-          const cg_scene& sc = scenes[i];
-          const BatchScene& b = bs[size_t(i)];
-          if (!b.sorted) continue;
-          PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
-          st2 = enqueue_scene(nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64,
-                              base + b.cells_off, int64_t(b.plan.ucap),
-                              reinterpret_cast<uint32_t*>(base + b.edges_off), int64_t(b.ecap),
-                              ctx->workers[size_t(stream_of[size_t(i)])], nullptr, kPhaseSearch);
-          if (st2) return st2;
+        // Searches; PIVOT / HALVES scenes stop at their (key, cell) pairs,
+        // which one segmented sort orders for all of them, then resume.
+        auto search = [&](int phase, bool only_keysort) -> cg_status {
+          for (int i : order) {
+            const cg_scene& sc = scenes[i];
+            const BatchScene& b = bs[size_t(i)];
+            if (!b.sorted || b.seg_search || (only_keysort && !b.keysort)) continue;
+            PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
+            const cg_status r = enqueue_scene(
+                nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64, base + b.cells_off,
+                int64_t(b.plan.ucap), reinterpret_cast<uint32_t*>(base + b.edges_off),
+                int64_t(b.ecap), ctx->workers[size_t(stream_of[size_t(i)])], nullptr, phase);
+            if (r) return r;
+          }
+          return CG_OK;
+        };
+        if (n_se_hash)
+          CG_CUDA(launch_neighbors_seg_small(dse, n_se_hash, se_chunks_hash, false, dse_scratch,
+                                             s0),
+                  "neighbour search (small scenes, HASH)");
+        if (n_se_sorted)
+          CG_CUDA(launch_neighbors_seg_small(dse + n_se_hash, n_se_sorted, se_chunks_sorted, true,
+                                             dse_scratch + (S + 2), s0),
+                  "neighbour search (small scenes, SORTED)");
+        if ((st2 = search(kPhaseSearchKeys, false))) return st2;
+        if (n_ks) {
+          if ((st2 = join())) return st2;
+          mark(ctx, "batch_search_keys", s0);
+          CG_CUDA(seg_sort(dks, n_ks, ks_cap, ks_bits, base + ks_off, s0), "batch key sort");
+          mark(ctx, "batch_key_sort", s0);
+          if ((st2 = fork())) return st2;
+          if ((st2 = search(kPhaseSearchRest, true))) return st2;
         }
       }
       if ((st2 = join())) return st2;

@@ -296,101 +296,211 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 // Polls of the look-back before it gives up (a wait that can never end).
 constexpr unsigned kSpinLimit = 1u << 22;
 
+struct EmitShared {
+  uint32_t hits[kNECells][64];
+  uint32_t cnt[kNECells];
+  uint32_t off[kNECells];
+  uint32_t chunk;
+  unsigned long long base;
+};
+
+// Chunk c (< nchunks) of the U = u sorted cells: every warp finds the hits of
+// its cells (one lane per bit, kept in shared memory), warp 0 scans the 32
+// counts, publishes the chunk's total and looks back over the predecessors'
+// totals (decoupled look-back, Merrill & Garland 2016; at most `polls` polls)
+// for the chunk's first edge position, then the block writes its edges.
+// Called by the whole block.
+template <class L>
+__device__ __forceinline__ void emit_small_chunk(EmitShared& sm,
+                                                 const uint64_t* __restrict__ cells, const L& look,
+                                                 DevCounters* ctr, int ell,
+                                                 unsigned long long* status,
+                                                 uint32_t* __restrict__ edges, int64_t cap,
+                                                 uint32_t u, uint32_t nchunks, uint32_t c,
+                                                 uint32_t polls) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int nh = (ell + 31) >> 5;
+  for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
+    const uint32_t i = c * kNECells + cl;
+    uint32_t total = 0;
+    if (i < u) {
+      const uint64_t x = cells[i];
+      for (int h = 0; h < nh; ++h) {
+        const int k = h * 32 + lane;
+        int64_t j = -1;
+        if (k < ell && !((x >> k) & 1ull)) j = look.find(x | (1ull << k));
+        const uint32_t m = __ballot_sync(0xffffffffu, j >= 0);
+        if (j >= 0) sm.hits[cl][total + __popc(m & lanemask_lt())] = uint32_t(j);
+        total += __popc(m);
+      }
+    }
+    if (lane == 0) sm.cnt[cl] = total;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t v = sm.cnt[lane];
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    sm.off[lane] = inc - v;
+    const unsigned long long T = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == 0) {
+      unsigned long long base = 0;
+      if (c == 0) {
+        atomicExch(&status[0], kFlagPre | T);
+      } else {
+        atomicExch(&status[c], kFlagAgg | T);
+        int64_t p = int64_t(c) - 1;
+        uint32_t looked = 0;
+        while (p >= 0) {
+          if (looked++ >= polls) {  // every look counts; 0 polls gives up at once
+            atomicOr(&ctr->error, kErrTimeout);
+            break;
+          }
+          const unsigned long long sv =
+              *reinterpret_cast<volatile unsigned long long*>(&status[p]);
+          const unsigned long long f = sv & ~kValMask;
+          if (f == 0) {
+            __nanosleep(64);
+            continue;
+          }
+          base += sv & kValMask;
+          if (f == kFlagPre) break;
+          --p;
+        }
+        atomicExch(&status[c], kFlagPre | (base + T));
+      }
+      sm.base = base;
+      if (c == nchunks - 1) ctr->n_edges = base + T;
+    }
+  }
+  __syncthreads();
+  const unsigned long long base = sm.base;
+  for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
+    const uint32_t i = c * kNECells + cl;
+    const uint32_t m = sm.cnt[cl];
+    const unsigned long long o = base + sm.off[cl];
+    for (uint32_t r = lane; r < m; r += 32) {
+      const unsigned long long e = o + r;
+      if (e < (unsigned long long)cap) {
+        edges[2 * e] = i;
+        edges[2 * e + 1] = sm.hits[cl][r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <class L>
 __global__ void __launch_bounds__(kNEThreads)
     neighbors_emit_small(const uint64_t* __restrict__ cells, L look, DevCounters* ctr, int ell,
                          unsigned long long* status, uint32_t* __restrict__ edges, int64_t cap,
                          uint32_t max_n, uint32_t polls) {
-  __shared__ uint32_t hits[kNECells][64];
-  __shared__ uint32_t cnt[kNECells];
-  __shared__ uint32_t off[kNECells];
-  __shared__ uint32_t s_chunk;
-  __shared__ unsigned long long s_base;
+  __shared__ EmitShared sm;
   if (ctr->overflow) return;
   const uint32_t u = min(ctr->n_unique, max_n);
   const uint32_t nchunks = (u + kNECells - 1) / kNECells;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int warp = tid >> 5;
-  const int nh = (ell + 31) >> 5;
   for (;;) {
-    if (tid == 0) s_chunk = atomicAdd(&ctr->ticket, 1u);
+    if (threadIdx.x == 0) sm.chunk = atomicAdd(&ctr->ticket, 1u);
     __syncthreads();
-    const uint32_t c = s_chunk;
+    const uint32_t c = sm.chunk;
     if (c >= nchunks) break;
-    for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
-      const uint32_t i = c * kNECells + cl;
-      uint32_t total = 0;
-      if (i < u) {
-        const uint64_t x = cells[i];
-        for (int h = 0; h < nh; ++h) {
-          const int k = h * 32 + lane;
-          int64_t j = -1;
-          if (k < ell && !((x >> k) & 1ull)) j = look.find(x | (1ull << k));
-          const uint32_t m = __ballot_sync(0xffffffffu, j >= 0);
-          if (j >= 0) hits[cl][total + __popc(m & lanemask_lt())] = uint32_t(j);
-          total += __popc(m);
-        }
-      }
-      if (lane == 0) cnt[cl] = total;
+    emit_small_chunk(sm, cells, look, ctr, ell, status, edges, cap, u, nchunks, c, polls);
+  }
+}
+
+// ------------------------- many scenes per launch -------------------------
+//
+// Batches: the single-pass edge kernel over the chunks of every scene of
+// l <= 64 at once. A global ticket hands out (scene, chunk) items in scene
+// order, so every chunk's predecessors in its own scene were handed out
+// earlier and are running; the look-back stays within the scene's own status
+// words, and each scene's last chunk writes its edge count.
+__global__ void __launch_bounds__(1024)
+    seg_emit_offsets(const SegSearchScene* __restrict__ sc, int n_scenes, unsigned int* off) {
+  __shared__ unsigned long long wsum[32];
+  unsigned long long carry = 0;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  for (int base = 0; base < n_scenes; base += 1024) {
+    const int i = base + int(threadIdx.x);
+    unsigned long long c = 0;
+    if (i < n_scenes && !sc[i].t.ctr->overflow)
+      c = (min(sc[i].t.ctr->n_unique, sc[i].ucap) + kNECells - 1) / kNECells;
+    unsigned long long inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
     }
+    if (lane == 31) wsum[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-      const uint32_t v = cnt[lane];
-      uint32_t inc = v;
+      unsigned long long v = wsum[lane];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
       }
-      off[lane] = inc - v;
-      const unsigned long long T = __shfl_sync(0xffffffffu, inc, 31);
-      if (lane == 0) {
-        unsigned long long base = 0;
-        if (c == 0) {
-          atomicExch(&status[0], kFlagPre | T);
-        } else {
-          atomicExch(&status[c], kFlagAgg | T);
-          int64_t p = int64_t(c) - 1;
-          uint32_t looked = 0;
-          while (p >= 0) {
-            if (looked++ >= polls) {  // every look counts; 0 polls gives up at once
-              atomicOr(&ctr->error, kErrTimeout);
-              break;
-            }
-            const unsigned long long sv =
-                *reinterpret_cast<volatile unsigned long long*>(&status[p]);
-            const unsigned long long f = sv & ~kValMask;
-            if (f == 0) {
-              __nanosleep(64);
-              continue;
-            }
-            base += sv & kValMask;
-            if (f == kFlagPre) break;
-            --p;
-          }
-          atomicExch(&status[c], kFlagPre | (base + T));
-        }
-        s_base = base;
-        if (c == nchunks - 1) ctr->n_edges = base + T;
-      }
+      wsum[lane] = v;
     }
     __syncthreads();
-    const unsigned long long base = s_base;
-    for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
-      const uint32_t i = c * kNECells + cl;
-      const uint32_t m = cnt[cl];
-      const unsigned long long o = base + off[cl];
-      for (uint32_t r = lane; r < m; r += 32) {
-        const unsigned long long e = o + r;
-        if (e < (unsigned long long)cap) {
-          edges[2 * e] = i;
-          edges[2 * e + 1] = hits[cl][r];
-        }
-      }
-    }
+    const unsigned long long before = warp > 0 ? wsum[warp - 1] : 0ull;
+    if (i < n_scenes) off[i] = unsigned(carry + before + inc - c);
+    carry += wsum[31];
     __syncthreads();
   }
+  if (threadIdx.x == 0) {
+    off[n_scenes] = unsigned(carry);  // chunks in all
+    off[n_scenes + 1] = 0u;           // ticket
+  }
+}
+
+template <bool kSorted>
+__global__ void __launch_bounds__(kNEThreads)
+    neighbors_seg_small(const SegSearchScene* __restrict__ sc, int n_scenes, unsigned int* off,
+                        uint32_t polls) {
+  __shared__ EmitShared sm;
+  const uint32_t total = off[n_scenes];
+  for (;;) {
+    if (threadIdx.x == 0) sm.chunk = atomicAdd(&off[n_scenes + 1], 1u);
+    __syncthreads();
+    const uint32_t g = sm.chunk;
+    if (g >= total) break;
+    int lo = 0, hi = n_scenes - 1;  // the last scene whose first chunk is <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const SegSearchScene& z = sc[lo];
+    const uint32_t u = min(z.t.ctr->n_unique, z.ucap);
+    const uint32_t nchunks = (u + kNECells - 1) / kNECells;
+    if (kSorted)
+      emit_small_chunk(sm, z.cells, SmallSorted{z.cells, z.t.ctr}, z.t.ctr, z.ell, z.status,
+                       z.edges, z.edges_cap, u, nchunks, g - off[lo], polls);
+    else
+      emit_small_chunk(sm, z.cells, SmallHash{z.t.keys, z.t.vals, z.t.mask, z.t.shift, z.t.ctr},
+                       z.t.ctr, z.ell, z.status, z.edges, z.edges_cap, u, nchunks, g - off[lo],
+                       polls);
+  }
+}
+
+// One block per scene: its table (kEmpty), table values and look-back words
+// (zero) and counters.
+__global__ void __launch_bounds__(1024) clear_seg(const SegClear* __restrict__ sc) {
+  const SegClear& z = sc[blockIdx.x];
+  if (threadIdx.x < sizeof(DevCounters) / 4) reinterpret_cast<uint32_t*>(z.ctr)[threadIdx.x] = 0;
+  for (size_t i = threadIdx.x; i < z.cap; i += blockDim.x) {
+    z.keys[i] = kEmpty;
+    z.vals[i] = 0u;
+  }
+  for (size_t i = threadIdx.x; i < z.n_status; i += blockDim.x) z.status[i] = 0ull;
 }
 
 // ------------------------------- wide path -------------------------------
@@ -975,6 +1085,29 @@ cudaError_t launch_neighbors_emit_small(const uint64_t* cells, const SmallTable&
         cells, SmallHash{t.keys, t.vals, t.mask, t.shift, t.ctr}, t.ctr, ell, status, edges,
         edges_cap, uint32_t(max_n), wait_limit(kSpinLimit));
   }
+  return finish(0);
+}
+
+cudaError_t launch_neighbors_seg_small(const SegSearchScene* scenes, int n_scenes,
+                                       size_t total_chunks, bool sorted_lookup,
+                                       unsigned int* scratch, cudaStream_t s) {
+  if (n_scenes <= 0) return cudaSuccess;
+  seg_emit_offsets<<<1, 1024, 0, s>>>(scenes, n_scenes, scratch);
+  const int g = int(std::max<size_t>(
+      1, std::min<size_t>(total_chunks, size_t(sm_count()) * 4)));
+  if (sorted_lookup)
+    neighbors_seg_small<true><<<g, kNEThreads, 0, s>>>(scenes, n_scenes, scratch,
+                                                       wait_limit(kSpinLimit));
+  else
+    neighbors_seg_small<false><<<g, kNEThreads, 0, s>>>(scenes, n_scenes, scratch,
+                                                        wait_limit(kSpinLimit));
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clear_seg(const SegClear* scenes, int n_scenes, cudaStream_t s) {
+  if (n_scenes <= 0) return cudaSuccess;
+  clear_seg<<<unsigned(n_scenes), 1024, 0, s>>>(scenes);
   return finish(0);
 }
 

@@ -124,6 +124,22 @@ inline int table_shift(size_t cap) {
 // Fused steps 1-2 for l <= 64: every vector goes straight into the table
 // (no vector is written to memory); distinct vectors are appended to ulist.
 cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStream_t s);
+// The same for many scenes in one launch (a batch): scene s (device array)
+// owns the 128-point warp tiles [tile0, next scene's tile0) of the batch's
+// tile numbering, total_tiles in all; every scene has dimension d and at most
+// 32 nch constraints (nch = 1 or 2). A warp takes a contiguous range of tiles
+// and rebuilds its constraint rows when the scene or the tile bound changes.
+struct SegPackScene {
+  const int32_t* pts;
+  int64_t n;
+  const int32_t* a;
+  const int64_t* b;
+  int ell;
+  SmallTable t;
+  uint64_t tile0;
+};
+cudaError_t launch_pack_insert_seg(const SegPackScene* scenes, int n_scenes, uint64_t total_tiles,
+                                   int d, int nch, cudaStream_t s);
 // Same on the tensor cores (cg_pack_tc.cu): l <= 64, d <= 4; tiles outside the
 // exact-split ranges are evaluated in fp32 with exact re-evaluation.
 // spill_tiles: ceil(n / 128) words of scratch.
@@ -249,6 +265,20 @@ size_t batch_sort_bytes(size_t total_cap, int n_scenes);
 cudaError_t batch_sort(const BatchSortScene* scenes, int n_scenes, size_t total_cap,
                        void* scratch, cudaStream_t s);
 
+// Segmented key sort: many scenes' (key, value) arrays, each sorted by key
+// (stable) in place, with one radix sort over all of them. Scene s holds
+// min(*n, cap) items; every key is below 2^key_bits.
+struct SegSortScene {
+  uint64_t* keys;
+  uint32_t* vals;
+  const unsigned int* n;
+  uint32_t cap;
+};
+size_t seg_sort_bytes(size_t total_cap, int n_scenes);
+// scenes: device array of n_scenes; total_cap >= the sum of their cap.
+cudaError_t seg_sort(const SegSortScene* scenes, int n_scenes, size_t total_cap, int key_bits,
+                     void* scratch, cudaStream_t s);
+
 // out[i] = sum_{j<i} in[j] for i < *n_dev; *total = sum of all (device).
 cudaError_t scan_exclusive_u32(const uint32_t* in, unsigned long long* out,
                                const unsigned int* n_dev, size_t max_n,
@@ -299,6 +329,32 @@ cudaError_t launch_publish_done(const DevCounters* ctr, DevCounters* host_ctr,
 // exceeds its cap, CG_ERR_TIMEOUT / CG_ERR_INTERNAL on device-side failures).
 cudaError_t launch_publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
                                   int64_t edges_cap, cudaStream_t s);
+
+// Batches: the single-pass edge kernel over many scenes of l <= 64 in one
+// launch (HASH lookups in each scene's table, or SORTED binary search in its
+// cells). scratch: n_scenes + 2 words (chunk offsets, total, ticket).
+struct SegSearchScene {
+  const uint64_t* cells;  // sorted cells
+  SmallTable t;           // the scene's table (HASH) and counters (t.ctr)
+  unsigned long long* status;
+  uint32_t* edges;
+  int64_t edges_cap;
+  int ell;
+  uint32_t ucap;
+};
+cudaError_t launch_neighbors_seg_small(const SegSearchScene* scenes, int n_scenes,
+                                       size_t total_chunks, bool sorted_lookup,
+                                       unsigned int* scratch, cudaStream_t s);
+// Batches: the clears of many l <= 64 scenes in one launch (one block each).
+struct SegClear {
+  uint64_t* keys;
+  uint32_t* vals;
+  size_t cap;
+  unsigned long long* status;
+  size_t n_status;
+  DevCounters* ctr;
+};
+cudaError_t launch_clear_seg(const SegClear* scenes, int n_scenes, cudaStream_t s);
 
 // Clears a build's table (kEmpty), the look-back status words and the counters.
 // (A second table, table2/cap2, and an array of 32-bit words to be zeroed,

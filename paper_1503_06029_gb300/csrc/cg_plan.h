@@ -58,7 +58,15 @@ struct PackPieces {
 // receives stage-timing marks.
 // Phases: the whole build, or (for batches whose sort runs across scenes)
 // everything up to the dedup insert, and everything after the sort.
-enum ScenePhase { kPhaseAll = 0, kPhaseInsert = 1, kPhaseSearch = 2 };
+// kPhaseSearchKeys / kPhaseSearchRest split kPhaseSearch of a PIVOT or HALVES
+// scene around a batch-wide sort of its (key, cell) pairs (seg_sort).
+enum ScenePhase {
+  kPhaseAll = 0,
+  kPhaseInsert = 1,
+  kPhaseSearch = 2,
+  kPhaseSearchKeys = 3,
+  kPhaseSearchRest = 4
+};
 
 cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan& plan,
                         const PackArgs& pa, int word_bits, void* cells, int64_t cells_cap,
@@ -71,5 +79,11 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
 bool scene_batch_sortable(const ScenePlan& plan);
 BatchSortScene scene_sort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan,
                                uint64_t* user_cells, int64_t user_cap);
+
+// Whether a strategy sorts (key, cell) pairs (PIVOT, HALVES), the key width of
+// a scene's pairs, and the descriptor of those pairs in workspace ws.
+bool keysort_strategy(int strategy);
+int scene_key_bits(const ScenePlan& plan);
+SegSortScene scene_keysort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan);
 
 }  // namespace cg

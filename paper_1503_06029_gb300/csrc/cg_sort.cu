@@ -1349,4 +1349,125 @@ cudaError_t batch_sort(const BatchSortScene* scenes, int n_scenes, size_t total_
   return cudaGetLastError();
 }
 
+// --------------------------- segmented key sort ----------------------------
+//
+// The lookup strategies that bucket cells by a key (PIVOT: distances to the
+// pivots; HALVES: the low part) sort each scene's (key, cell) pairs. In a
+// batch, hundreds of such small sorts are each a chain of latency-bound
+// launches. Here the pairs of every scene are gathered into one array with
+// the scene's number above the key bits, sorted by one LSD radix sort (so
+// every scene's items end up contiguous, in key order, ties in input order),
+// and scattered back into each scene's arrays.
+namespace {
+
+struct SegSortWs {
+  unsigned int* off;  // [S + 1] item offsets; off[S] is the total
+  uint64_t* k0;
+  uint64_t* k1;
+  uint32_t* v0;
+  uint32_t* v1;
+  void* radix;
+  size_t bytes;
+};
+
+SegSortWs carve_segsort(void* base, size_t total_cap, int n_scenes) {
+  SegSortWs w{};
+  char* p = static_cast<char*>(base);
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* r = p ? p + off : nullptr;
+    off = (off + bytes + 255) & ~size_t(255);
+    return r;
+  };
+  const size_t cap = total_cap > 0 ? total_cap : 1;
+  w.off = reinterpret_cast<unsigned int*>(take((size_t(n_scenes) + 1) * sizeof(unsigned int)));
+  w.k0 = reinterpret_cast<uint64_t*>(take(cap * sizeof(uint64_t)));
+  w.k1 = reinterpret_cast<uint64_t*>(take(cap * sizeof(uint64_t)));
+  w.v0 = reinterpret_cast<uint32_t*>(take(cap * sizeof(uint32_t)));
+  w.v1 = reinterpret_cast<uint32_t*>(take(cap * sizeof(uint32_t)));
+  w.radix = take(radix_scratch_bytes(cap));
+  w.bytes = off;
+  return w;
+}
+
+__global__ void __launch_bounds__(1024)
+    segsort_offsets(const SegSortScene* __restrict__ sc, int n_scenes, unsigned int* off) {
+  unsigned long long carry = 0;
+  for (int base = 0; base < n_scenes; base += 1024) {
+    const int i = base + int(threadIdx.x);
+    const unsigned long long c = i < n_scenes ? min(*sc[i].n, sc[i].cap) : 0u;
+    unsigned long long tot = 0;
+    const unsigned long long ex = block_excl(c, &tot);
+    if (i < n_scenes) off[i] = unsigned(carry + ex);
+    carry += tot;
+  }
+  if (threadIdx.x == 0) off[n_scenes] = unsigned(carry);
+}
+
+// Scene of item g: the last s with off[s] <= g.
+__device__ __forceinline__ int segsort_scene(const unsigned int* off, int n_scenes, uint32_t g) {
+  int lo = 0, hi = n_scenes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void segsort_gather(const SegSortScene* __restrict__ sc, int n_scenes,
+                               const unsigned int* __restrict__ off, int key_bits, uint64_t* k,
+                               uint32_t* v) {
+  const uint32_t total = off[n_scenes];
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += gridDim.x * blockDim.x) {
+    const int s = segsort_scene(off, n_scenes, g);
+    const uint32_t j = g - off[s];
+    k[g] = (uint64_t(s) << key_bits) | sc[s].keys[j];
+    v[g] = sc[s].vals[j];
+  }
+}
+
+__global__ void segsort_scatter(const SegSortScene* __restrict__ sc,
+                                const unsigned int* __restrict__ off, int n_scenes, int key_bits,
+                                const uint64_t* __restrict__ k, const uint32_t* __restrict__ v) {
+  const uint32_t total = off[n_scenes];
+  const uint64_t mask = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1);
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += gridDim.x * blockDim.x) {
+    const uint64_t key = k[g];
+    const int s = int(key >> key_bits);
+    const uint32_t j = g - off[s];  // scene s occupies [off[s], off[s + 1]) once sorted
+    sc[s].keys[j] = key & mask;
+    sc[s].vals[j] = v[g];
+  }
+}
+
+}  // namespace
+
+size_t seg_sort_bytes(size_t total_cap, int n_scenes) {
+  return carve_segsort(nullptr, total_cap, n_scenes).bytes;
+}
+
+cudaError_t seg_sort(const SegSortScene* scenes, int n_scenes, size_t total_cap, int key_bits,
+                     void* scratch, cudaStream_t s) {
+  if (n_scenes <= 0 || total_cap == 0) return cudaSuccess;
+  int scene_bits = 0;
+  while ((1 << scene_bits) < n_scenes) ++scene_bits;
+  if (key_bits < 1 || key_bits + scene_bits > 64) return cudaErrorInvalidValue;
+  SegSortWs w = carve_segsort(scratch, total_cap, n_scenes);
+  segsort_offsets<<<1, 1024, 0, s>>>(scenes, n_scenes, w.off);
+  const int g = int(std::min<size_t>((total_cap + 255) / 256, size_t(sm_count()) * 8));
+  segsort_gather<<<g, 256, 0, s>>>(scenes, n_scenes, w.off, key_bits, w.k0, w.v0);
+  count_launch(2);
+  bool in1 = false;
+  cudaError_t e = radix_sort_u64(w.k0, w.k1, w.v0, w.v1, &w.off[n_scenes], total_cap,
+                                 key_bits + scene_bits, w.radix, s, &in1);
+  if (e != cudaSuccess) return e;
+  segsort_scatter<<<g, 256, 0, s>>>(scenes, w.off, n_scenes, key_bits, in1 ? w.k1 : w.k0,
+                                    in1 ? w.v1 : w.v0);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace cg
