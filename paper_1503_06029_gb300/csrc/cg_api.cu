@@ -556,6 +556,10 @@ struct cg_ctx {
   cudaEvent_t fork_ev = nullptr;
   std::vector<cudaEvent_t> join_ev;
   std::map<std::tuple<int64_t, int, int>, size_t> edge_hint;
+  // Batches: table capacities learned from a finished run's cell counts
+  // (smaller than the arrangement-bound guess; a scene that overflows one
+  // takes the resize path, whose cap_hint wins).
+  std::map<std::tuple<int64_t, int, int>, size_t> tight_hint;
   // Captured batch: replayed while the batch signature is unchanged.
   cudaGraphExec_t bgraph = nullptr;
   uint64_t bgraph_sig = 0;
@@ -1151,7 +1155,7 @@ SegSortScene scene_keysort_desc(char* ws, DevCounters* ctr, const ScenePlan& pla
   PivotWs pw{};
   TreeWs tw{};
   carve_scene(c, plan, ctr, &w, &ww, &pw, &tw);
-  return SegSortScene{pw.k0, pw.i0, &ctr->n_unique, uint32_t(plan.ucap)};
+  return SegSortScene{pw.k0, pw.i0, ctr, uint32_t(plan.ucap)};
 }
 
 BatchSortScene scene_sort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan,
@@ -1816,6 +1820,16 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     for (int i = 0; i < S; ++i) {
       out->n_cells[i] = hctr[i].n_unique;
       out->n_edges[i] = int64_t(hctr[i].n_edges);
+      // A table of about 2.5 U slots (half-full at most) for the next run of
+      // a scene of the same sizes: smaller tables, workspaces and sorts.
+      const cg_scene& sc = scenes[i];
+      const auto key = std::make_tuple(sc.n, sc.ell, sc.d);
+      const size_t u = hctr[i].n_unique;
+      const size_t want = std::max<size_t>(1024, next_pow2(2 * u + u / 2 + 1));
+      if (want < cap_of(i) && !ctx->tight_hint.count(key)) {
+        ctx->tight_hint[key] = want;
+        ++ctx->hint_version;
+      }
     }
     if (out->cells_offset)
       for (int i = 0; i <= S; ++i) out->cells_offset[i] = hcoff[i];
@@ -1873,6 +1887,8 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       const cg_scene& sc = scenes[i];
       const auto key = std::make_tuple(sc.n, sc.ell, sc.d);
       size_t cap = initial_cap(sc.n, sc.d, sc.ell);
+      auto th = ctx->tight_hint.find(key);
+      if (th != ctx->tight_hint.end()) cap = std::min(cap, th->second);
       auto it = ctx->cap_hint.find(key);
       if (it != ctx->cap_hint.end()) cap = std::max(cap, it->second);
       cap = std::min(cap, full_cap(sc.n));

@@ -267,11 +267,12 @@ cudaError_t batch_sort(const BatchSortScene* scenes, int n_scenes, size_t total_
 
 // Segmented key sort: many scenes' (key, value) arrays, each sorted by key
 // (stable) in place, with one radix sort over all of them. Scene s holds
-// min(*n, cap) items; every key is below 2^key_bits.
+// min(ctr->n_unique, cap) items, none when its table overflowed (its keys were
+// never written); only the low key_bits bits of a key take part.
 struct SegSortScene {
   uint64_t* keys;
   uint32_t* vals;
-  const unsigned int* n;
+  const DevCounters* ctr;
   uint32_t cap;
 };
 size_t seg_sort_bytes(size_t total_cap, int n_scenes);

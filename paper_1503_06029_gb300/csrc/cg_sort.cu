@@ -736,8 +736,43 @@ __device__ __forceinline__ uint32_t merge_split(const Ord& ord, const ulonglong2
   return lo;
 }
 
+// merge_split by one whole warp: 33-way search instead of a binary one (each
+// round the lanes test 32 points of the remaining range along the diagonal),
+// so a split over runs of millions of items costs about five dependent
+// rounds of loads instead of twenty-odd. Every lane returns the result.
+template <class Ord>
+__device__ __forceinline__ uint32_t merge_split_warp(const Ord& ord, const ulonglong2* ka,
+                                                     const typename Ord::Tag* ia, uint32_t la,
+                                                     const ulonglong2* kb,
+                                                     const typename Ord::Tag* ib, uint32_t lb,
+                                                     uint32_t d) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t lo = d > lb ? d - lb : 0;
+  uint32_t hi = d < la ? d : la;
+  // Answer: the first i in [lo, hi) with less(B[d - 1 - i], A[i]), else hi.
+  while (lo < hi) {
+    const uint32_t len = hi - lo;
+    const bool few = len <= 32;
+    const uint32_t p = few ? lo + lane : lo + uint32_t((uint64_t(len) * (lane + 1)) / 33);
+    const bool live = few ? lane < len : true;
+    const bool f = live && ord.less(kb[d - 1 - p], ib[d - 1 - p], ka[p], ia[p]);
+    const uint32_t m = __ballot_sync(0xffffffffu, f);
+    if (few) return m ? lo + uint32_t(__ffs(m) - 1) : hi;
+    if (m == 0) {
+      lo = __shfl_sync(0xffffffffu, p, 31) + 1;
+    } else {
+      const int j = __ffs(m) - 1;
+      hi = __shfl_sync(0xffffffffu, p, j);
+      if (j > 0) lo = __shfl_sync(0xffffffffu, p, j - 1) + 1;
+    }
+  }
+  return lo;
+}
+
 // One merge pass: sorted runs of `width` items merged pairwise into runs of
-// 2 * width; block b writes output items [b * tile, (b + 1) * tile).
+// 2 * width; block b writes output items [b * tile, (b + 1) * tile). Warps 0
+// and 1 find the block's two splits; every thread merges kItems outputs into
+// registers, which go back through shared memory for coalesced stores.
 template <class Ord>
 __global__ void __launch_bounds__(kMThreads)
     msort_merge(Ord ord, const ulonglong2* __restrict__ kin,
@@ -763,9 +798,11 @@ __global__ void __launch_bounds__(kMThreads)
   const Tag* ia = iin + s0;
   const ulonglong2* kb = kin + a_end;
   const Tag* ib = iin + a_end;
-  if (threadIdx.x < 2)
-    s_split[threadIdx.x] =
-        merge_split(ord, ka, ia, la, kb, ib, lb, threadIdx.x == 0 ? d0 : d1);
+  if (threadIdx.x < 64) {
+    const uint32_t sp =
+        merge_split_warp(ord, ka, ia, la, kb, ib, lb, threadIdx.x < 32 ? d0 : d1);
+    if ((threadIdx.x & 31) == 0) s_split[threadIdx.x >> 5] = sp;
+  }
   __syncthreads();
   const uint32_t a0 = s_split[0], a1 = s_split[1];
   const uint32_t b0 = d0 - a0, b1 = d1 - a1;
@@ -782,26 +819,43 @@ __global__ void __launch_bounds__(kMThreads)
   __syncthreads();
   // Each thread merges kItems consecutive outputs of this tile.
   const uint32_t dd = threadIdx.x * Ord::kItems;
-  if (dd < na + nb) {
+  const uint32_t tot = na + nb;
+  ulonglong2 ok[Ord::kItems];
+  Tag ot[Ord::kItems];
+  if (dd < tot) {
     uint32_t x = merge_split(ord, sk, si, na, sk + na, si + na, nb, dd);
     uint32_t y = dd - x;
-    const uint32_t end = min(dd + uint32_t(Ord::kItems), na + nb);
-    for (uint32_t o = dd; o < end; ++o) {
+#pragma unroll
+    for (int o = 0; o < Ord::kItems; ++o) {
+      if (dd + o >= tot) break;
       bool take_a;
       if (x >= na) take_a = false;
       else if (y >= nb) take_a = true;
       else take_a = !ord.less(sk[na + y], si[na + y], sk[x], si[x]);
-      const uint32_t g = out0 + o;
       if (take_a) {
-        kout[g] = sk[x];
-        iout[g] = si[x];
+        ok[o] = sk[x];
+        ot[o] = si[x];
         ++x;
       } else {
-        kout[g] = sk[na + y];
-        iout[g] = si[na + y];
+        ok[o] = sk[na + y];
+        ot[o] = si[na + y];
         ++y;
       }
     }
+  }
+  __syncthreads();  // every thread is done reading the inputs
+  if (dd < tot) {
+#pragma unroll
+    for (int o = 0; o < Ord::kItems; ++o) {
+      if (dd + o >= tot) break;
+      sk[dd + o] = ok[o];
+      si[dd + o] = ot[o];
+    }
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < tot; t += kMThreads) {
+    kout[out0 + t] = sk[t];
+    iout[out0 + t] = si[t];
   }
 }
 
@@ -1395,7 +1449,8 @@ __global__ void __launch_bounds__(1024)
   unsigned long long carry = 0;
   for (int base = 0; base < n_scenes; base += 1024) {
     const int i = base + int(threadIdx.x);
-    const unsigned long long c = i < n_scenes ? min(*sc[i].n, sc[i].cap) : 0u;
+    const unsigned long long c =
+        i < n_scenes && !sc[i].ctr->overflow ? min(sc[i].ctr->n_unique, sc[i].cap) : 0u;
     unsigned long long tot = 0;
     const unsigned long long ex = block_excl(c, &tot);
     if (i < n_scenes) off[i] = unsigned(carry + ex);
@@ -1419,11 +1474,12 @@ __global__ void segsort_gather(const SegSortScene* __restrict__ sc, int n_scenes
                                const unsigned int* __restrict__ off, int key_bits, uint64_t* k,
                                uint32_t* v) {
   const uint32_t total = off[n_scenes];
+  const uint64_t mask = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1);
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += gridDim.x * blockDim.x) {
     const int s = segsort_scene(off, n_scenes, g);
     const uint32_t j = g - off[s];
-    k[g] = (uint64_t(s) << key_bits) | sc[s].keys[j];
+    k[g] = (uint64_t(s) << key_bits) | (sc[s].keys[j] & mask);
     v[g] = sc[s].vals[j];
   }
 }
@@ -1436,8 +1492,10 @@ __global__ void segsort_scatter(const SegSortScene* __restrict__ sc,
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += gridDim.x * blockDim.x) {
     const uint64_t key = k[g];
-    const int s = int(key >> key_bits);
+    const uint64_t s = key_bits >= 64 ? 0 : key >> key_bits;
+    if (s >= uint64_t(n_scenes)) continue;  // cannot happen: every item carries its scene
     const uint32_t j = g - off[s];  // scene s occupies [off[s], off[s + 1]) once sorted
+    if (j >= sc[s].cap) continue;
     sc[s].keys[j] = key & mask;
     sc[s].vals[j] = v[g];
   }
