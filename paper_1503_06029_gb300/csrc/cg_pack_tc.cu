@@ -27,9 +27,10 @@
 // Per tile: threads write their row of P~ to shared memory (no-swizzle K-major
 // core-matrix layout), one thread issues tcgen05.mma (M = 128, N = NC, K = 16)
 // into this block's TMEM columns and commits to an mbarrier; every thread then
-// reads its point's row of S with tcgen05.ld, combines hi and lo with packed
-// fp32 FMAs, and collects the sign bits. Up to 512 / NC blocks share an SM
-// (TMEM has 512 columns), so one block's MMA overlaps the others' epilogues.
+// reads its point's row of S with tcgen05.ld, combines hi and lo with one fp32
+// FMA per constraint, and collects the sign bits. Up to 512 / NC blocks share
+// an SM (TMEM has 512 columns), so one block's MMA overlaps the others'
+// epilogues.
 #include <cuda_fp16.h>
 
 #include "cg_internal.cuh"
@@ -135,16 +136,6 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-__device__ __forceinline__ uint64_t pack2u(uint32_t lo, uint32_t hi) {
-  return uint64_t(lo) | (uint64_t(hi) << 32);
-}
-
 __device__ __forceinline__ uint32_t uabs32(int32_t v) {
   return v < 0 ? 0u - uint32_t(v) : uint32_t(v);
 }
@@ -240,30 +231,15 @@ __device__ __forceinline__ void load_point(const PackArgs& pa, int64_t tile, int
   for (int k = 0; k < D; ++k) pi[k] = ok ? __ldg(pa.pts + p * D + k) : 0;
 }
 
-template <int D, int NC, class Sink>
-__global__ void __launch_bounds__(kTThreads)
-    pack_tc_kernel(PackArgs pa, Sink sink, TcSpill spill, unsigned int* error, uint32_t polls) {
-  constexpr int kL = NC / 2;  // constraint slots (32 or 64)
-  constexpr int kCh = kL / 32;
-  static_assert(D >= 1 && D <= 4, "d");
-  extern __shared__ __align__(16) unsigned char dyn[];
-  const uint32_t base = smem_u32(dyn);
-  TcShared& sh = *reinterpret_cast<TcShared*>(dyn + (((base + 1023u) & ~1023u) - base));
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  const int lane = tid & 31;
-  const int64_t ntiles = (pa.n + kTilePts - 1) / kTilePts;
-  const int64_t stride = gridDim.x;
-  const uint32_t mbar = smem_u32(&sh.mbar);
-
-  // ---- set-up: TMEM columns, mbarrier, A~ in shared memory ----
-  if (warp == 0) {
-    tmem_alloc(smem_u32(&sh.tmem), NC);
-    fence_before_sync();
-  }
-  if (tid == 0) mbar_init(mbar, 1);
+// Rows of A~ (the constraints' split coefficients, NC rows of 16 halves) in
+// the no-swizzle K-major layout, written by threads tid, tid + nthreads, ...;
+// returns 0 when a constraint of this thread is outside the exact-split ranges.
+template <int D, int NC>
+__device__ __forceinline__ int stage_b_rows(const PackArgs& pa, unsigned char* b, int tid,
+                                            int nthreads) {
+  constexpr int kL = NC / 2;
   int ok = 1;
-  for (int row = tid; row < NC; row += kTThreads) {
+  for (int row = tid; row < NC; row += nthreads) {
     const bool lo_half = row >= kL;
     const int c = lo_half ? row - kL : row;
     float v[16];
@@ -305,9 +281,35 @@ __global__ void __launch_bounds__(kTThreads)
     q1.y = h2(v[10], v[11]);
     q1.z = h2(v[12], v[13]);
     q1.w = h2(v[14], v[15]);
-    *reinterpret_cast<uint4*>(sh.b + kmajor_offset(row, 0)) = q0;
-    *reinterpret_cast<uint4*>(sh.b + kmajor_offset(row, 1)) = q1;
+    *reinterpret_cast<uint4*>(b + kmajor_offset(row, 0)) = q0;
+    *reinterpret_cast<uint4*>(b + kmajor_offset(row, 1)) = q1;
   }
+  return ok;
+}
+
+template <int D, int NC, class Sink>
+__global__ void __launch_bounds__(kTThreads)
+    pack_tc_kernel(PackArgs pa, Sink sink, TcSpill spill, unsigned int* error, uint32_t polls) {
+  constexpr int kL = NC / 2;  // constraint slots (32 or 64)
+  constexpr int kCh = kL / 32;
+  static_assert(D >= 1 && D <= 4, "d");
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const uint32_t base = smem_u32(dyn);
+  TcShared& sh = *reinterpret_cast<TcShared*>(dyn + (((base + 1023u) & ~1023u) - base));
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int64_t ntiles = (pa.n + kTilePts - 1) / kTilePts;
+  const int64_t stride = gridDim.x;
+  const uint32_t mbar = smem_u32(&sh.mbar);
+
+  // ---- set-up: TMEM columns, mbarrier, A~ in shared memory ----
+  if (warp == 0) {
+    tmem_alloc(smem_u32(&sh.tmem), NC);
+    fence_before_sync();
+  }
+  if (tid == 0) mbar_init(mbar, 1);
+  const int ok = stage_b_rows<D, NC>(pa, sh.b, tid, kTThreads);
   fence_proxy_async();
   const bool all_ok = __syncthreads_and(ok) != 0;
   fence_after_sync();
@@ -316,7 +318,6 @@ __global__ void __launch_bounds__(kTThreads)
   const uint64_t bdesc = smem_desc(smem_u32(sh.b), kLBO, kSBO);
   const uint64_t adesc = smem_desc(smem_u32(sh.a), kLBO, kSBO);
   constexpr uint32_t idesc = instr_desc(NC);
-  const uint64_t k2048 = pack2u(0x45000000u, 0x45000000u);  // 2048.0f twice
   uint32_t phase = 0;
   bool timed_out = false;
   int it = 0;
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(kTThreads)
     const bool valid = p < pa.n;
     const int64_t next = tile + stride;
     load_point<D>(pa, next + stride, ntiles, tid, nxt2);
-    float comb[kL];
+    uint64_t key = 0;
     bool had = false;
     if (cur_mma) {
       if (lane == 0) {
@@ -395,18 +396,29 @@ __global__ void __launch_bounds__(kTThreads)
       if (!timed_out) {
         phase ^= 1u;
         had = true;
+        // Per 32 constraints: hi and lo results from TMEM, fl(2048 hi + lo)
+        // (one rounding of a value that is never 0, so its sign bit is exact),
+        // sign bits gathered in four independent chains of 8, then packed.
 #pragma unroll
         for (int ch = 0; ch < kCh; ++ch) {
           uint32_t hi[32], lo[32];
           tmem_ld32(taddr + uint32_t(ch * 32), hi);
           tmem_ld32(taddr + uint32_t(kL + ch * 32), lo);
           tmem_wait_ld();
+          uint32_t w[4];
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const uint64_t r = ffma2(pack2u(hi[j], hi[j + 1]), k2048, pack2u(lo[j], lo[j + 1]));
-            comb[ch * 32 + j] = __uint_as_float(uint32_t(r));
-            comb[ch * 32 + j + 1] = __uint_as_float(uint32_t(r >> 32));
+          for (int g = 0; g < 4; ++g) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int j = 8 * g + 7; j >= 8 * g; --j) {
+              const float v = fmaf(__uint_as_float(hi[j]), 2048.0f, __uint_as_float(lo[j]));
+              acc = __funnelshift_l(__float_as_uint(v), acc, 1);
+            }
+            w[g] = ~acc;
           }
+          const uint32_t word = __byte_perm(__byte_perm(w[0], w[1], 0x0040),
+                                            __byte_perm(w[2], w[3], 0x0040), 0x5410);
+          key |= uint64_t(word) << (32 * ch);
         }
       } else if (lane == 0 && error) {
         atomicOr(error, kErrTimeout);
@@ -422,23 +434,6 @@ __global__ void __launch_bounds__(kTThreads)
       pend = false;
     }
     if (had && valid) {
-      // Sign bits in groups of 8 constraints (independent chains), packed.
-      uint64_t key = 0;
-#pragma unroll
-      for (int ch = 0; ch < kCh; ++ch) {
-        uint32_t w[4];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          uint32_t acc = 0;
-#pragma unroll
-          for (int j = 8 * g + 7; j >= 8 * g; --j)
-            acc = __funnelshift_l(__float_as_uint(comb[ch * 32 + j]), acc, 1);
-          w[g] = ~acc;
-        }
-        const uint32_t word = __byte_perm(__byte_perm(w[0], w[1], 0x0040),
-                                          __byte_perm(w[2], w[3], 0x0040), 0x5410);
-        key |= uint64_t(word) << (32 * ch);
-      }
       sink.probe(key, pend_slot, pend_cur);
       pend_key = key;
       pend = true;
