@@ -50,8 +50,31 @@ WORKLOAD = "planes_3d: l=64 planes, d=3, N=2^24 int32 points in [-2^20,2^20]^3"
 NCU_TRAFFIC = {
     "source_sha256": "6d174fba8c6bccf87165a8a3244cd560eb2356ee3af1dd13194f9f55d6c6d690",
     "bytes_per_launch": 205142528.0,
-    "capture": "profiles/pack_fast_kernel_planes_3d.md",
 }
+
+# SHA-256 digests of the CPU oracle's complete outputs on the full-size
+# workloads, written by a script that calls only the oracle.
+DIGESTS = os.path.join(ROOT, "tests", "golden", "full_size_digests.json")
+
+
+def golden_digests() -> dict:
+    with open(DIGESTS) as f:
+        return json.load(f)
+
+
+def digest_of(arr) -> str:
+    """SHA-256 of an array's bytes (a CUDA tensor is copied to the host)."""
+    import numpy as np
+
+    if hasattr(arr, "cpu"):
+        arr = arr.cpu().numpy()
+    return hashlib.sha256(np.ascontiguousarray(arr).tobytes()).hexdigest()
+
+
+def digest_mismatch(entry: dict, cells, edges) -> bool:
+    return (cells.shape[0] != entry["n_cells"] or edges.shape[0] != entry["n_edges"]
+            or digest_of(cells) != entry["cells_sha256"]
+            or digest_of(edges) != entry["edges_sha256"])
 
 
 def _peaks():
@@ -286,8 +309,13 @@ def batch_compare(ctx, dev, steps: int):
     t1.record(stream)
     torch.cuda.synchronize()
     plain_ms = t0.elapsed_time(t1) / passes
+    # Every scene of the replayed batch against the oracle's digests.
+    entries = golden_digests()["batch_scenes"]
+    res = ctx.build_batch(scenes)
+    bad = sum(digest_mismatch(entries[i], c, e) for i, (c, e) in enumerate(res))
     return {"workload": "1,024 scenes, l in [8,256], N in [1e3,1e6] log-uniform, d=3",
             "points": total, "cells": cells, "edges": edges,
+            "oracle_digest_mismatches": int(bad),
             "batched": {"value": total / (batch_ms * 1e-3) / 1e6, "unit": UNIT,
                         "ms_per_batch": batch_ms, "gpu_launches_per_batch": batch_launches},
             "plain": {"value": total / (plain_ms * 1e-3) / 1e6, "unit": UNIT,
@@ -303,10 +331,11 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
     """Serving: Poisson arrivals (exponential gaps, seed 5) of scenes drawn as
     in the batched workload, offered at fractions of the measured batched
     capacity (scenes/s). Requests go through the request server with host
-    inputs in pinned memory (copied by the server after admission); a second
-    when the level's submissions are done, each request is waited for in
-    arrival order, its counts are checked against a plain build of the same
-    scene, and it is released (the budget holds every result of a level, so
+    inputs in pinned memory (copied by the server after admission). When a
+    level's submissions are done, each request is waited for in arrival
+    order; once all have finished, each one's cells and edges are fetched,
+    their SHA-256 digests compared with the oracle's for the same scene, and
+    the request is released (the budget holds every result of a level, so
     admission never waits for a release; keeping the Python client off the
     interpreter lock while submitting is what lets the offered rate be met).
     Latency = completion on the device (server stamp) minus submission on the
@@ -321,12 +350,7 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
     for s in range(pool_scenes):
         sc = inputs.batch_scene(spec, s)
         pool.append(tuple(torch.from_numpy(x).pin_memory().numpy() for x in (sc.pts, sc.a, sc.b)))
-    ctx = cellgraph.Context(dev.index or 0)
-    want = []
-    for pts, a, b in pool:
-        c, e = ctx.build(*(torch.from_numpy(x).to(dev) for x in (pts, a, b)), 64)
-        want.append((int(c.shape[0]), int(e.shape[0])))
-    ctx.close()
+    want = golden_digests()["batch_scenes"]  # the oracle's outputs of these scenes
     out = {"workload": "Poisson stream of scenes drawn like the batched workload "
                        f"(a pool of {pool_scenes} scenes, cycled), host inputs in pinned memory",
            "capacity_scenes_per_s": capacity_scenes_per_s, "levels": []}
@@ -354,12 +378,17 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
             for i in range(n_requests):
                 srv.wait(tickets[i])
                 r = srv.result(tickets[i])
-                if r["status"] or (r["n_cells"], r["n_edges"]) != want[i % pool_scenes]:
-                    mism[0] += 1
+                mism[0] += int(r["status"] != 0)
                 lat.append(r["done_us"] - r["submit_us"])
                 if first_submit[0] is None:
                     first_submit[0] = r["submit_us"]
                 last_done[0] = max(last_done[0], r["done_us"])
+            # Once every request of the level has finished (the budget holds all
+            # results), each one's cells and edges against the oracle's digests.
+            for i in range(n_requests):
+                if srv.result(tickets[i])["status"] == 0:
+                    cells, edges = srv.fetch(tickets[i])
+                    mism[0] += digest_mismatch(want[i % pool_scenes], cells, edges)
                 srv.release(tickets[i])
             pts_total = sum(int(pool[i % pool_scenes][0].shape[0]) for i in range(n_requests))
             span_s = (last_done[0] - first_submit[0]) * 1e-6
@@ -372,7 +401,7 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
                 "mean_ms": float(lat_ms.mean()),
                 "sustained": {"value": pts_total / span_s / 1e6, "unit": UNIT,
                               "scenes_per_s": n_requests / span_s},
-                "count_mismatches": mism[0], "max_running": st["max_running"],
+                "oracle_digest_mismatches": mism[0], "max_running": st["max_running"],
                 "peak_bytes": st["peak_bytes"]})
     return out
 
@@ -413,6 +442,60 @@ def chains_measure(dev, steps: int, strategies=("hash", "pivot", "tree", "halves
         out["strategies"][strat] = {"value": n / ((d_ms + n_ms) * 1e-3) / 1e6, "unit": UNIT,
                                     "ms_per_step": d_ms + n_ms, "dedup_ms": d_ms,
                                     "neighbors_ms": n_ms}
+    return out
+
+
+def _alu_peak_tmacs() -> float:
+    """FP32 lane peak in T multiply-adds/s: 152 SMs x 128 lanes x the
+    measured maximum SM clock (MEASURED_PEAKS.json), one MAC per lane-FMA."""
+    peaks, _ = _peaks()
+    return 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def quadric_measure(dev, steps: int):
+    """Curved boundaries: l = 64 spheres in 3-space (the quadric form of
+    |p - c_i|^2 >= r_i^2), N = 2^24 points, device-resident. One step =
+    cg_pack_signs_quadric + cg_dedup_cells + cg_neighbors_h1 (the last two read
+    their counts back). Reports Mvectors/s, the quadric sign kernel's time and
+    its fraction of the FP32 lane peak (N l F multiply-adds, F = 9 features:
+    six monomials and three coordinates), and checks the output against the
+    oracle's digest when one is stored."""
+    import torch
+
+    from paper_1503_06029_gb300 import cellgraph, inputs
+
+    sc = inputs.spheres_3d()
+    n, ell = sc.n, sc.ell
+    t = [torch.from_numpy(x).to(dev) for x in (sc.pts, sc.q, sc.a, sc.b)]
+    del sc
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(2):
+        cells, edges = cellgraph.build_quadric(*t, 64)
+    pack_ms = step_ms = 0.0
+    for _ in range(steps):
+        ev[0].record(stream)
+        keys = cellgraph.pack_signs_quadric(*t, 64)
+        ev[1].record(stream)
+        cells = cellgraph.dedup_cells(keys, ell, 64)
+        edges = cellgraph.neighbors_h1(cells, ell, 64)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        pack_ms += ev[0].elapsed_time(ev[1]) / steps
+        step_ms += ev[0].elapsed_time(ev[2]) / steps
+    peak = _alu_peak_tmacs()
+    work = float(n) * ell * 9
+    out = {"workload": "spheres_3d: l=64 spheres (quadrics), d=3, N=2^24 int32 points in "
+                       "[-2^20,2^20]^3, radii in [2^19,2^21]",
+           "value": n / (step_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": step_ms,
+           "cells": int(cells.shape[0]), "edges": int(edges.shape[0]),
+           "sign_kernel": {"ms": pack_ms, "achieved": work / (pack_ms * 1e-3) / 1e12,
+                           "peak": peak, "unit": "TMAC/s",
+                           "frac": work / (pack_ms * 1e-3) / 1e12 / peak,
+                           "work": "N*l*F exact multiply-adds, F = 9"}}
+    entry = golden_digests().get("spheres_3d")
+    if entry is not None:
+        out["oracle_digest_mismatch"] = bool(digest_mismatch(entry, cells, edges))
     return out
 
 
@@ -645,6 +728,8 @@ def run_ours(args):
                                         tuple(args.chains_strategies.split(",")))
     if not args.no_bfs:
         line["bfs"] = bfs_measure(ctx, dev, max(5, args.steps // 2))
+    if not args.no_quadric:
+        line["quadric"] = quadric_measure(dev, max(5, args.steps // 2))
     if not args.no_batch:
         line["batch"] = batch_compare(ctx, dev, max(3, args.steps // 2))
         if not args.no_serve:
@@ -676,6 +761,8 @@ def main():
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-chains", action="store_true", help="skip the long-vector workload")
     p.add_argument("--no-bfs", action="store_true", help="skip the BFS measurement")
+    p.add_argument("--no-quadric", action="store_true",
+                   help="skip the quadric-constraint (spheres) measurement")
     p.add_argument("--chains-strategies", default="hash,pivot,tree,halves",
                    help="lookup strategies timed on the long-vector workload")
     p.add_argument("--serve-requests", type=int, default=2000)

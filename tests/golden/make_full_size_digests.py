@@ -13,7 +13,8 @@ Workloads:
     l log-uniform in 8..256, N log-uniform in 1e3..1e6, seed 4), 64-bit words;
     the serving stream draws its requests from the first of these scenes;
   * planes_3d (l = 64, N = 2^24, seed 2) and lines_2d (l = 16, N = 20,000,
-    seed 1, 32-bit words).
+    seed 1, 32-bit words);
+  * spheres_3d: l = 64 spheres as quadric constraints, N = 2^24, seed 13.
 
 Digest convention (shared with the checks that read the file): the cells are
 hashed as their little-endian words, row-major [U][W] (W words of word_bits
@@ -21,7 +22,9 @@ bits), the edges as little-endian uint32 pairs [E][2] in canonical (i, j)
 order; cells and edges have separate digests.
 
 Run: ``python tests/golden/make_full_size_digests.py [--jobs J]``. The oracle
-is single-threaded; scenes are spread over J worker processes.
+is single-threaded; scenes are spread over J worker processes. ``--only
+NAME`` recomputes one of the single-workload entries (planes_3d, lines_2d,
+chains, spheres_3d) and keeps the others.
 """
 from __future__ import annotations
 
@@ -72,6 +75,15 @@ def _chains_job(_=None) -> dict:
     return _entry(cells, edges, ell=1024, n=int(ch.keys.shape[0]), seed=3)
 
 
+def _spheres_job(_=None) -> dict:
+    import oracle
+    from paper_1503_06029_gb300 import inputs
+
+    sc = inputs.spheres_3d()
+    cells, edges = oracle.build_quadric(sc.pts, sc.q, sc.a, sc.b, 64)
+    return _entry(cells, edges, ell=int(sc.ell), n=int(sc.n), seed=13, word_bits=64)
+
+
 def _plain_job(name: str) -> dict:
     import oracle
     from paper_1503_06029_gb300 import inputs
@@ -85,14 +97,38 @@ def _plain_job(name: str) -> dict:
                   word_bits=wb)
 
 
+SINGLE = ("convention", "planes_3d", "lines_2d", "chains", "spheres_3d", "batch")
+
+
+def _write(out: dict, scenes_out: list) -> None:
+    with open(OUT, "w") as f:
+        # One line per record keeps the file diffable.
+        f.write("{\n")
+        for k in SINGLE:
+            if k in out:
+                f.write(f"{json.dumps(k)}: {json.dumps(out[k], sort_keys=True)},\n")
+        f.write('"batch_scenes": [\n')
+        f.write(",\n".join(json.dumps(e, sort_keys=True) for e in scenes_out))
+        f.write("\n]\n}\n")
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
+    ap.add_argument("--only", choices=["planes_3d", "lines_2d", "chains", "spheres_3d"])
     args = ap.parse_args()
     import oracle
 
     oracle.compile_library()
     t0 = time.time()
+    if args.only:
+        with open(OUT) as f:
+            out = json.load(f)
+        job = {"chains": _chains_job, "spheres_3d": _spheres_job}.get(args.only)
+        out[args.only] = job() if job else _plain_job(args.only)
+        _write(out, out.pop("batch_scenes"))
+        print(f"updated {args.only} in {OUT} in {time.time() - t0:.0f} s")
+        return
     ctx = mp.get_context("spawn")
     with ctx.Pool(args.jobs) as pool:
         chains = pool.apply_async(_chains_job)
@@ -104,23 +140,17 @@ def main() -> None:
         order = sorted(range(len(spec.n)), key=lambda s: -int(spec.n[s]) * int(spec.ell[s]))
         scenes = {s: pool.apply_async(_scene_job, (s,)) for s in order}
         batch = [scenes[s].get() for s in range(len(spec.n))]
+        spheres = pool.apply_async(_spheres_job)
         out = {
             "convention": "sha256 of little-endian cells [U][W] words and of uint32 edges "
                           "[E][2] in canonical (i, j) order, from the CPU oracle",
             "planes_3d": plain["planes_3d"].get(),
             "lines_2d": plain["lines_2d"].get(),
-            "batch": {"seed": 4, "word_bits": 64, "scenes": batch},
+            "batch": {"seed": 4, "word_bits": 64},
             "chains": chains.get(),
+            "spheres_3d": spheres.get(),
         }
-    scenes_out = out["batch"].pop("scenes")
-    with open(OUT, "w") as f:
-        # One line per record keeps the file diffable.
-        f.write("{\n")
-        for k in ("convention", "planes_3d", "lines_2d", "chains", "batch"):
-            f.write(f"{json.dumps(k)}: {json.dumps(out[k], sort_keys=True)},\n")
-        f.write('"batch_scenes": [\n')
-        f.write(",\n".join(json.dumps(e, sort_keys=True) for e in scenes_out))
-        f.write("\n]\n}\n")
+    _write(out, batch)
     print(f"wrote {OUT} in {time.time() - t0:.0f} s")
 
 

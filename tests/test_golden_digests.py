@@ -34,6 +34,8 @@ def test_digest_file_covers_the_workloads():
     ch = g["chains"]
     assert (ch["n"], ch["ell"], ch["n_cells"], ch["n_edges"]) == (5 * 2**20, 1024, 4190741, 3932003)
     assert g["planes_3d"]["n"] == 2**24 and g["planes_3d"]["n_cells"] <= 43745
+    sp = g["spheres_3d"]
+    assert (sp["n"], sp["ell"]) == (2**24, 64) and 0 < sp["n_edges"] <= sp["n_cells"] * 32
 
 
 def test_digests_match_the_oracle_on_small_workloads():

@@ -61,6 +61,15 @@ def test_planes_3d_full_size_digest(dev, golden):
         ctx.close()
 
 
+def test_spheres_full_size_digest(dev, golden):
+    """Quadric constraints at full size: l = 64 spheres over 2^24 points,
+    through cg_pack_signs_quadric, cg_dedup_cells and cg_neighbors_h1."""
+    sc = inputs.spheres_3d()
+    args = [torch.from_numpy(x).to(dev) for x in (sc.pts, sc.q, sc.a, sc.b)]
+    cells, edges = cellgraph.build_quadric(*args, 64)
+    check(golden["spheres_3d"], cells, edges)
+
+
 @pytest.mark.parametrize("strategy", ["hash", "pivot", "halves", "tree"])
 def test_chains_full_size_digest(dev, golden, strategy):
     """l = 1024, N = 5,242,880 vectors: all 4,190,741 cells and all 3,932,003
