@@ -487,8 +487,10 @@ cg_status dedup_small_tail(SmallWs& w, int ell, int word_bits, void* user_cells,
 }
 
 // Step 2 for wide vectors in keys64: insert, sort representatives, gather rows.
+// direct (nullable): the caller's 64-bit-word cells of capacity direct_cap,
+// written by the gather itself instead of the internal w.cells.
 cg_status dedup_wide_steps(WideWs& w, const uint64_t* keys64, int64_t n, int ell, bool rank,
-                           cudaStream_t s) {
+                           cudaStream_t s, uint64_t* direct = nullptr, int64_t direct_cap = -1) {
   const int w64 = (ell + 63) / 64;
   WideTable t{w.slots, uint32_t(w.cap - 1), w.idx0, uint32_t(w.ucap), w.ctr};
   CG_CUDA(launch_fill_u64(w.slots, kEmpty, w.cap, s), "clearing table");
@@ -497,8 +499,13 @@ cg_status dedup_wide_steps(WideWs& w, const uint64_t* keys64, int64_t n, int ell
   CG_CUDA(sort_wide(keys64, w64, ell, w.idx0, w.idx1, w.kw0, w.kw1, &w.ctr->n_unique, w.ucap,
                     w.radix, s, &sorted, nullptr, &w.ctr->msort_done),
           "sorting cells");
-  CG_CUDA(launch_gather_rows(keys64, w64, sorted, &w.ctr->n_unique, w.ucap, w.cells, s),
-          "gathering cells");
+  if (direct)
+    CG_CUDA(launch_gather_rows(keys64, w64, sorted, &w.ctr->n_unique, w.ucap, direct, s,
+                               nullptr, direct_cap),
+            "gathering cells");
+  else
+    CG_CUDA(launch_gather_rows(keys64, w64, sorted, &w.ctr->n_unique, w.ucap, w.cells, s),
+            "gathering cells");
   if (rank) CG_CUDA(launch_rank_by_row(sorted, &w.ctr->n_unique, w.ucap, w.rank, s), "ranks");
   return CG_OK;
 }
@@ -815,10 +822,16 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
       k64 = w.keys64;
     }
     CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
-    cg_status st = dedup_wide_steps(w, k64, n, ell, point_cell != nullptr, s);
+    // 64-bit words: the sorted rows are gathered straight into the caller's
+    // cells (one pass over them instead of two).
+    const bool direct = word_bits == 64 && cells_cap > 0;
+    cg_status st = dedup_wide_steps(w, k64, n, ell, point_cell != nullptr, s,
+                                    direct ? static_cast<uint64_t*>(cells) : nullptr,
+                                    direct ? cells_cap : -1);
     if (st) return st;
-    CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
-            "writing cells");
+    if (!direct)
+      CG_CUDA(launch_write_cells(w.cells, ell, word_bits, cells, cells_cap, w.ctr, ucap, s),
+              "writing cells");
     if (point_cell) {
       WideTable t{w.slots, uint32_t(cap - 1), w.idx0, uint32_t(ucap), w.ctr};
       CG_CUDA(launch_point_cell_wide(k64, n, (ell + 63) / 64, t, w.rank, point_cell, s),
@@ -1879,7 +1892,7 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     m.take<SegPackScene>(size_t(S));
     m.take<SegSearchScene>(size_t(S));
     m.take<unsigned int>(2 * (size_t(S) + 2));
-    size_t sort_cap = 0, ks_cap = 0;
+    size_t sort_cap = 0, ks_cap = 0, sort_seg = 1024;
     int n_sorted = 0, n_ks = 0, ks_bits = 1;
     const char* sk_env = std::getenv("CG_SIGN_KERNEL");
     const bool env_tc = sk_env && std::strcmp(sk_env, "tc") == 0;
@@ -1907,7 +1920,9 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       m.off += b.ecap * 2 * sizeof(uint32_t);
       b.sorted = scene_batch_sortable(b.plan);
       if (b.sorted) {
-        sort_cap += b.plan.ucap;
+        const size_t seg = batch_sort_seg_size(b.plan.ucap);
+        sort_cap += seg;
+        sort_seg = std::max(sort_seg, seg);
         ++n_sorted;
       }
       b.keysort = b.sorted && keysort_strategy(b.plan.tp.strategy);
@@ -2115,7 +2130,8 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       if (n_sorted) {
         if ((st2 = join())) return st2;
         mark(ctx, "batch_insert", s0);
-        CG_CUDA(batch_sort(dsort, n_sorted, sort_cap, base + sort_off, s0), "batch sort");
+        CG_CUDA(batch_sort(dsort, n_sorted, sort_cap, sort_seg, base + sort_off, s0),
+                "batch sort");
         mark(ctx, "batch_sort", s0);
         if ((st2 = fork())) return st2;
         // Searches; PIVOT / HALVES scenes stop at their (key, cell) pairs,

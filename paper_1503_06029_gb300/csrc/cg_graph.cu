@@ -268,6 +268,8 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void clear_build(uint64_t* table, size_t cap, uint64_t* table2, size_t cap2,
                             unsigned long long* status, size_t n_status, DevCounters* ctr,
                             uint32_t* zero32, size_t n_zero32) {
+  griddep_wait();  // the previous build's kernels may still read this table
+  griddep_release();
   if (blockIdx.x == 0 && threadIdx.x < sizeof(DevCounters) / 4)
     reinterpret_cast<uint32_t*>(ctr)[threadIdx.x] = 0;
   const size_t stride = size_t(gridDim.x) * blockDim.x;
@@ -402,6 +404,8 @@ __global__ void __launch_bounds__(kNEThreads)
                          unsigned long long* status, uint32_t* __restrict__ edges, int64_t cap,
                          uint32_t max_n, uint32_t polls) {
   __shared__ EmitShared sm;
+  griddep_wait();
+  griddep_release();
   if (ctr->overflow) return;
   const uint32_t u = min(ctr->n_unique, max_n);
   const uint32_t nchunks = (u + kNECells - 1) / kNECells;
@@ -550,12 +554,24 @@ __global__ void insert_wide(const uint64_t* __restrict__ keys, int64_t n, int w,
   }
 }
 
+// Rows idx[0 .. U) of keys, in that order, to out (nothing when out_cap >= 0
+// and U > out_cap: the caller reports the capacity error).
 __global__ void gather_rows(const uint64_t* __restrict__ keys, int w,
                             const uint32_t* __restrict__ idx, const unsigned int* n_dev,
                             uint32_t max_n, uint64_t* __restrict__ out,
-                            const unsigned int* skip) {
+                            const unsigned int* skip, int64_t out_cap) {
   if (skip && *skip) return;
-  const uint64_t total = uint64_t(min(*n_dev, max_n)) * w;
+  const uint32_t u = min(*n_dev, max_n);
+  if (out_cap >= 0 && int64_t(u) > out_cap) return;
+  const uint64_t total = uint64_t(u) * w;
+  if (total < (1ull << 32)) {  // 32-bit index arithmetic
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < uint32_t(total);
+         t += gridDim.x * blockDim.x) {
+      const uint32_t r = t / uint32_t(w);
+      out[t] = keys[uint64_t(idx[r]) * w + (t - r * uint32_t(w))];
+    }
+    return;
+  }
   for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < total;
        t += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t r = t / w;
@@ -1062,9 +1078,11 @@ cudaError_t launch_clear_build(uint64_t* table, size_t cap, unsigned long long* 
                                uint64_t* table2, size_t cap2, uint32_t* zero32,
                                size_t n_zero32) {
   const size_t most = std::max(std::max(std::max(cap, cap2), n_status), n_zero32);
-  clear_build<<<grid_for(most + 1, kThreads * 4, 16), kThreads, 0, s>>>(
-      table, cap, table2, cap2, status, n_status, ctr, zero32, n_zero32);
-  return finish(0);
+  const cudaError_t e = launch_dep(clear_build, dim3(grid_for(most + 1, kThreads * 4, 16)),
+                                   dim3(kThreads), 0, s, table, cap, table2, cap2, status,
+                                   n_status, ctr, zero32, n_zero32);
+  count_launch();
+  return e;
 }
 
 size_t ne_status_words(size_t max_n) { return (max_n + kNECells - 1) / kNECells + 1; }
@@ -1076,16 +1094,18 @@ cudaError_t launch_neighbors_emit_small(const uint64_t* cells, const SmallTable&
   if (max_n == 0) return cudaSuccess;
   if (ell > 64) return cudaErrorInvalidValue;
   const int g = grid_for(max_n, kNECells, 4);
+  cudaError_t e;
   if (strategy == 2) {
-    neighbors_emit_small<<<g, kNEThreads, 0, s>>>(cells, SmallSorted{cells, t.ctr}, t.ctr, ell,
-                                                  status, edges, edges_cap, uint32_t(max_n),
-                                                  wait_limit(kSpinLimit));
+    e = launch_dep(neighbors_emit_small<SmallSorted>, dim3(g), dim3(kNEThreads), 0, s, cells,
+                   SmallSorted{cells, t.ctr}, t.ctr, ell, status, edges, edges_cap,
+                   uint32_t(max_n), wait_limit(kSpinLimit));
   } else {
-    neighbors_emit_small<<<g, kNEThreads, 0, s>>>(
-        cells, SmallHash{t.keys, t.vals, t.mask, t.shift, t.ctr}, t.ctr, ell, status, edges,
-        edges_cap, uint32_t(max_n), wait_limit(kSpinLimit));
+    e = launch_dep(neighbors_emit_small<SmallHash>, dim3(g), dim3(kNEThreads), 0, s, cells,
+                   SmallHash{t.keys, t.vals, t.mask, t.shift, t.ctr}, t.ctr, ell, status, edges,
+                   edges_cap, uint32_t(max_n), wait_limit(kSpinLimit));
   }
-  return finish(0);
+  count_launch();
+  return e;
 }
 
 cudaError_t launch_neighbors_seg_small(const SegSearchScene* scenes, int n_scenes,
@@ -1220,10 +1240,10 @@ cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, ui
 
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,
                                const unsigned int* n_dev, size_t max_n, uint64_t* out,
-                               cudaStream_t s, const unsigned int* skip) {
+                               cudaStream_t s, const unsigned int* skip, int64_t out_cap) {
   if (max_n == 0) return cudaSuccess;
-  gather_rows<<<grid_for(max_n * w64, kThreads), kThreads, 0, s>>>(keys, w64, idx, n_dev,
-                                                                    uint32_t(max_n), out, skip);
+  gather_rows<<<grid_for(max_n * w64, kThreads), kThreads, 0, s>>>(
+      keys, w64, idx, n_dev, uint32_t(max_n), out, skip, out_cap);
   return finish(0);
 }
 
@@ -1442,6 +1462,7 @@ __global__ void publish_done(const DevCounters* __restrict__ ctr, DevCounters* h
 
 __global__ void publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
                                int64_t edges_cap) {
+  griddep_wait();
   int64_t status = CG_OK;
   if (ctr->error & kErrTimeout) status = CG_ERR_TIMEOUT;
   else if (ctr->error || ctr->overflow) status = CG_ERR_INTERNAL;
@@ -1476,8 +1497,10 @@ cudaError_t launch_publish_done(const DevCounters* ctr, DevCounters* host_ctr,
 
 cudaError_t launch_publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
                                   int64_t edges_cap, cudaStream_t s) {
-  publish_counts<<<1, 1, 0, s>>>(ctr, out, cells_cap, edges_cap);
-  return finish(0);
+  const cudaError_t e = launch_dep(publish_counts, dim3(1), dim3(1), 0, s, ctr, out, cells_cap,
+                                   edges_cap);
+  count_launch();
+  return e;
 }
 
 }  // namespace cg

@@ -147,6 +147,39 @@ cudaError_t launch_pack_tc_insert(const PackArgs& pa, const SmallTable& t, uint3
                                   cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch. Kernels of a build's chain are launched with
+// launch_dep: the next kernel may be launched while the previous one still
+// runs, and its blocks start with griddep_wait(), which returns once every
+// earlier kernel of the stream has completed and its writes are visible (a
+// no-op for a kernel launched without the attribute). griddep_release() lets
+// the next kernel's launch begin early; it orders nothing.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+cudaError_t launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+#endif
+
+// ---------------------------------------------------------------------------
 // Device helpers used by several translation units.
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
@@ -260,10 +293,14 @@ struct BatchSortScene {
   int64_t user_cap;        // cells
   SmallTable t;            // l <= 64: cell numbers into t.vals (t.keys nullable)
 };
+// Each scene is sorted in a segment of batch_sort_seg_size(ucap) positions
+// (a power of two, at least 1024).
+size_t batch_sort_seg_size(size_t ucap);
 size_t batch_sort_bytes(size_t total_cap, int n_scenes);
-// scenes: device array of n_scenes; total_cap >= sum of their ucap.
+// scenes: device array of n_scenes; total_cap >= the sum of their segment
+// sizes, max_seg >= the largest.
 cudaError_t batch_sort(const BatchSortScene* scenes, int n_scenes, size_t total_cap,
-                       void* scratch, cudaStream_t s);
+                       size_t max_seg, void* scratch, cudaStream_t s);
 
 // Segmented key sort: many scenes' (key, value) arrays, each sorted by key
 // (stable) in place, with one radix sort over all of them. Scene s holds
@@ -419,9 +456,12 @@ cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, ui
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
                       void* scratch, cudaStream_t s, uint32_t** sorted_idx,
                       const unsigned int* skip = nullptr, unsigned int* flag = nullptr);
+// out_cap >= 0: out is a caller's buffer of that many rows, written only when
+// all U rows fit.
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,
                                const unsigned int* n_dev, size_t max_n, uint64_t* out,
-                               cudaStream_t s, const unsigned int* skip = nullptr);
+                               cudaStream_t s, const unsigned int* skip = nullptr,
+                               int64_t out_cap = -1);
 cudaError_t launch_rank_by_row(const uint32_t* idx, const unsigned int* n_dev, size_t max_n,
                                uint32_t* rank_by_row, cudaStream_t s);
 cudaError_t launch_point_cell_wide(const uint64_t* keys, int64_t n, int w64, const WideTable& t,

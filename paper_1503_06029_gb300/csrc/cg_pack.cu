@@ -517,6 +517,8 @@ __global__ void __launch_bounds__(kFThreads)
   float4* priv = blk + (1 + (threadIdx.x >> 5)) * (kRows * kQ);
   __shared__ uint32_t mblk[D];
   __shared__ int4 stage_all[kFWarps][32 * (P * D / 4)];
+  griddep_wait();  // the table was cleared by the previous kernel
+  griddep_release();
   int4* stage = stage_all[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t n = pa.n;
@@ -665,9 +667,9 @@ cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
   const int64_t want = (n_wt + kFWarps - 1) / kFWarps;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sm_count()) * per_sm));
   const int vec_ok = (reinterpret_cast<uintptr_t>(pa.pts) % 16) == 0;
-  kern<<<unsigned(grid), kFThreads, smem, s>>>(pa, sink, vec_ok);
+  err = launch_dep(kern, dim3(unsigned(grid)), dim3(kFThreads), smem, s, pa, sink, vec_ok);
   count_launch();
-  return cudaGetLastError();
+  return err;
 }
 
 // Many scenes of l <= 64 in one launch (batches): warp w takes the contiguous

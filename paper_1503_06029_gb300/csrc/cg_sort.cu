@@ -277,6 +277,8 @@ __global__ void __launch_bounds__(kCThreads)
   __shared__ uint32_t toff[256];
   __shared__ uint32_t wtot[8];
   __shared__ int skip;
+  griddep_wait();
+  griddep_release();
   // Same values for every CTA of the cluster: a table overflow, or the rank
   // sort (few distinct vectors) already did this work.
   if (o.ctr->overflow || o.ctr->sorted) return;
@@ -441,13 +443,15 @@ cudaError_t cluster_sort_w(const uint64_t* in, const uint32_t* rows, const unsig
     cfg.blockDim = dim3(kCThreads, 1, 1);
     cfg.dynamicSmemBytes = dyn;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     if (C == 16 && cluster16 == 0) continue;
     if (C == 16 && cluster16 < 0) {
       // First use: allow 16-CTA clusters and check that one fits on an SM set.
@@ -508,6 +512,8 @@ __global__ void __launch_bounds__(kRankThreads)
     rank_count(const uint64_t* __restrict__ in, const unsigned int* n_dev, uint32_t max_n,
                ClusterSortOut o) {
   __shared__ ulonglong2 sk[kRankSlice / 2 + 1];
+  griddep_wait();
+  griddep_release();
   const uint32_t n = *n_dev;
   if (!rank_applies(o, n, max_n)) return;  // the cluster sort takes it
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) o.ctr->sorted = 1u;
@@ -545,6 +551,8 @@ __global__ void __launch_bounds__(kRankThreads)
 __global__ void __launch_bounds__(kRankThreads)
     rank_place(const uint64_t* __restrict__ in, const unsigned int* n_dev, uint32_t max_n,
                ClusterSortOut o) {
+  griddep_wait();
+  griddep_release();
   const uint32_t n = *n_dev;
   if (!rank_applies(o, n, max_n)) return;
   const bool user = o.user_cells && int64_t(n) <= o.user_cap;
@@ -665,6 +673,18 @@ struct BatchOrder {
   }
 };
 
+// Segmented merge sorts (the batch sort): segments of 2^e positions, e = 10 ..
+// 31, laid out largest first; classes[2 e], classes[2 e + 1] bound the
+// positions of the segments of size 2^e.
+constexpr int kSegClasses = 32;
+
+// Segment size (2^e) at position g, from the class table.
+__device__ __forceinline__ uint32_t seg_size_at(const uint32_t* classes, uint32_t g) {
+  for (int e = kSegClasses - 1; e >= 10; --e)
+    if (g >= classes[2 * e] && g < classes[2 * e + 1]) return 1u << e;
+  return 0u;
+}
+
 // Tile sort: input items [b * tile, ...), with their cached keys.
 template <class Ord>
 __global__ void __launch_bounds__(kMThreads)
@@ -778,7 +798,7 @@ __global__ void __launch_bounds__(kMThreads)
     msort_merge(Ord ord, const ulonglong2* __restrict__ kin,
                 const typename Ord::Tag* __restrict__ iin, ulonglong2* __restrict__ kout,
                 typename Ord::Tag* __restrict__ iout, const unsigned int* n_dev, uint32_t max_n,
-                uint32_t width, const unsigned int* skip) {
+                uint32_t width, const unsigned int* skip, const uint32_t* seg_classes) {
   constexpr int kTile = kMThreads * Ord::kItems;
   using Tag = typename Ord::Tag;
   __shared__ ulonglong2 sk[kTile];
@@ -788,6 +808,8 @@ __global__ void __launch_bounds__(kMThreads)
   const uint32_t n = min(*n_dev, max_n);
   const uint32_t out0 = blockIdx.x * kTile;
   if (out0 >= n) return;
+  // Segmented sort: a segment no larger than the run width is sorted already.
+  if (seg_classes && seg_size_at(seg_classes, out0) <= width) return;
   const uint32_t s0 = (out0 / (2 * width)) * (2 * width);
   const uint32_t a_end = min(s0 + width, n);
   const uint32_t b_end = min(s0 + 2 * width, n);
@@ -859,20 +881,26 @@ __global__ void __launch_bounds__(kMThreads)
   }
 }
 
+// seg_classes (nullable): the segmented form; passes run while the run width
+// is below max_width (the largest segment), and every segment ends in the
+// buffer of the parity of its own pass count.
 template <class Ord>
 cudaError_t run_merge_sort(const Ord& ord, ulonglong2* k0, ulonglong2* k1,
                            typename Ord::Tag* t0, typename Ord::Tag* t1,
                            const unsigned int* n_dev, size_t max_n, cudaStream_t s,
-                           bool* result_in_1, const unsigned int* skip) {
+                           bool* result_in_1, const unsigned int* skip,
+                           const uint32_t* seg_classes = nullptr, size_t max_width = 0) {
   constexpr size_t kTile = size_t(kMThreads) * Ord::kItems;
   const unsigned tiles = unsigned((max_n + kTile - 1) / kTile);
   msort_tiles<Ord><<<tiles, kMThreads, 0, s>>>(ord, n_dev, uint32_t(max_n), k0, t0, skip);
   count_launch();
   bool in1 = false;
-  for (size_t width = kTile; width < max_n; width *= 2) {
+  const size_t limit = seg_classes ? max_width : max_n;
+  for (size_t width = kTile; width < limit; width *= 2) {
     msort_merge<Ord><<<tiles, kMThreads, 0, s>>>(ord, in1 ? k1 : k0, in1 ? t1 : t0,
                                                  in1 ? k0 : k1, in1 ? t0 : t1, n_dev,
-                                                 uint32_t(max_n), uint32_t(width), skip);
+                                                 uint32_t(max_n), uint32_t(width), skip,
+                                                 seg_classes);
     count_launch();
     in1 = !in1;
   }
@@ -1074,79 +1102,118 @@ __global__ void __launch_bounds__(kLongThreads)
 }
 
 // ------------------------------ batch sort ---------------------------------
+//
+// Every scene's distinct vectors are sorted by one merge sort, each scene in
+// a segment of its own: scene s with u_s vectors gets P_s = max(1024,
+// 2^ceil(log2 u_s)) positions (the rest padding items that sort last), and
+// the segments are laid out largest first, so each one starts at a multiple
+// of its size. A merge pass of run width w then only has work in segments
+// larger than w: blocks over smaller (already sorted) segments return, and
+// scene s is sorted after log2(P_s / 1024) passes, its result left in the
+// buffer of that parity. The work is sum_s P_s log2(P_s / 1024) items instead
+// of (sum_s u_s) log2(sum_s u_s / 1024), and the pass count follows the
+// largest scene.
+
+struct BatchSortWs {
+  uint32_t* off;        // [n] segment start of each scene
+  uint32_t* cnt;        // [n] its vectors
+  uint32_t* order;      // [n] scenes by segment start
+  uint32_t* starts;     // [n + 1] segment starts in that order; starts[n] = total
+  uint32_t* classes;    // [2 * kSegClasses]: first and end position of the segments of size 2^e
+  unsigned int* total;  // padded item count
+  ulonglong2* k0;
+  ulonglong2* k1;
+  uint2* t0;
+  uint2* t1;
+  size_t bytes;
+};
+
+__device__ __forceinline__ uint32_t seg_exp(uint32_t u) {
+  // log2 of max(1024, the next power of two >= u); 0 for an empty scene
+  return u == 0 ? 0u : min(31u, max(10u, 32u - __clz(u - 1u)));
+}
 
 __global__ void __launch_bounds__(1024)
-    bsort_offsets(const BatchSortScene* __restrict__ sc, int n, uint32_t* off, unsigned int* total) {
-  __shared__ uint32_t wsum[32];
-  uint32_t carry = 0;
-  for (int base = 0; base < n; base += 1024) {
-    const int i = base + threadIdx.x;
-    uint32_t v = 0;
-    if (i < n) v = sc[i].ctr->overflow ? 0u : min(sc[i].ctr->n_unique, sc[i].ucap);
-    uint32_t inc = v;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += t;
-    }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += t;
-      }
-      wsum[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t before = (warp > 0 ? wsum[warp - 1] : 0u) + inc - v;
-    if (i < n) off[i] = carry + before;
-    const uint32_t block_total = wsum[31];
-    __syncthreads();
-    carry += block_total;
+    bsort_layout(const BatchSortScene* __restrict__ sc, int n, BatchSortWs w) {
+  __shared__ unsigned int count[kSegClasses];
+  __shared__ unsigned int base[kSegClasses];
+  __shared__ unsigned int first[kSegClasses];
+  __shared__ unsigned int fill[kSegClasses];
+  if (threadIdx.x < kSegClasses) {
+    count[threadIdx.x] = 0;
+    fill[threadIdx.x] = 0;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t u = sc[i].ctr->overflow ? 0u : min(sc[i].ctr->n_unique, sc[i].ucap);
+    w.cnt[i] = u;
+    atomicAdd(&count[seg_exp(u)], 1u);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    off[n] = carry;
-    *total = carry;
+    uint64_t pos = 0;
+    unsigned int k = 0;
+    for (int e = kSegClasses - 1; e >= 10; --e) {  // largest segments first
+      base[e] = unsigned(pos);
+      first[e] = k;
+      pos += uint64_t(count[e]) << e;
+      k += count[e];
+      w.classes[2 * e] = base[e];
+      w.classes[2 * e + 1] = unsigned(pos);
+    }
+    first[0] = k;  // empty scenes last (no positions)
+    for (int e = 0; e < 10; ++e) w.classes[2 * e] = w.classes[2 * e + 1] = unsigned(pos);
+    w.starts[n] = unsigned(pos);
+    *w.total = unsigned(pos);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t e = seg_exp(w.cnt[i]);
+    const unsigned int r = atomicAdd(&fill[e], 1u);
+    const uint32_t o = e == 0 ? w.starts[n] : base[e] + uint32_t(uint64_t(r) << e);
+    w.off[i] = o;
+    w.order[first[e] + r] = uint32_t(i);
+    w.starts[first[e] + r] = o;
   }
 }
 
-__device__ __forceinline__ int scene_of(const uint32_t* off, int n, uint32_t g) {
-  int lo = 0, hi = n - 1;  // last scene s with off[s] <= g
+__device__ __forceinline__ int seg_index_at(const uint32_t* starts, int n, uint32_t g) {
+  int lo = 0, hi = n - 1;  // last k with starts[k] <= g
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= g) lo = mid;
+    if (starts[mid] <= g) lo = mid;
     else hi = mid - 1;
   }
   return lo;
 }
 
-__global__ void bsort_items(const BatchSortScene* __restrict__ sc, int n,
-                            const uint32_t* __restrict__ off, const unsigned int* total,
-                            ulonglong2* __restrict__ keys, uint2* __restrict__ tags) {
-  const uint32_t m = *total;
+__global__ void bsort_items(const BatchSortScene* __restrict__ sc, int n, BatchSortWs w) {
+  const uint32_t m = *w.total;
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < m; g += gridDim.x * blockDim.x) {
-    const int s = scene_of(off, n, g);
-    const uint32_t i = g - off[s];
-    const BatchSortScene& c = sc[s];
-    keys[g] = c.ell <= 64 ? make_ulonglong2(c.ulist[i], 0ull)
-                          : top128(c.keys64 + uint64_t(c.idx[i]) * c.w, c.ell);
-    tags[g] = make_uint2(uint32_t(s), i);
+    const int s = int(w.order[seg_index_at(w.starts, n, g)]);
+    const uint32_t i = g - w.off[s];
+    if (i < w.cnt[s]) {
+      const BatchSortScene& c = sc[s];
+      w.k0[g] = c.ell <= 64 ? make_ulonglong2(c.ulist[i], 0ull)
+                            : top128(c.keys64 + uint64_t(c.idx[i]) * c.w, c.ell);
+      w.t0[g] = make_uint2(uint32_t(s), i);
+    } else {
+      w.k0[g] = make_ulonglong2(~0ull, ~0ull);  // padding: sorts after every real item
+      w.t0[g] = make_uint2(kPad, kPad);
+    }
   }
 }
 
-__global__ void bsort_scatter(const BatchSortScene* __restrict__ sc,
-                              const uint32_t* __restrict__ off, const unsigned int* total,
-                              const uint2* __restrict__ tags) {
-  const uint32_t m = *total;
+__global__ void bsort_scatter(const BatchSortScene* __restrict__ sc, int n, BatchSortWs w) {
+  const uint32_t m = *w.total;
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < m; g += gridDim.x * blockDim.x) {
-    const uint2 tg = tags[g];
-    const BatchSortScene& c = sc[tg.x];
-    const uint32_t rank = g - off[tg.x];
-    const uint32_t cnt = off[tg.x + 1] - off[tg.x];
+    const int s = int(w.order[seg_index_at(w.starts, n, g)]);
+    const uint32_t rank = g - w.off[s];
+    const uint32_t cnt = w.cnt[s];
+    if (rank >= cnt) continue;
+    // The segment's result is in the buffer of the parity of its pass count.
+    const uint2 tg = (seg_exp(cnt) - 10u) & 1u ? w.t1[g] : w.t0[g];
+    const BatchSortScene& c = sc[s];
     const bool user = c.user_cells && int64_t(cnt) <= c.user_cap;
     if (c.ell <= 64) {
       const uint64_t v = c.ulist[tg.y];
@@ -1171,16 +1238,6 @@ __global__ void bsort_scatter(const BatchSortScene* __restrict__ sc,
   }
 }
 
-struct BatchSortWs {
-  uint32_t* off;
-  unsigned int* total;
-  ulonglong2* k0;
-  ulonglong2* k1;
-  uint2* t0;
-  uint2* t1;
-  size_t bytes;
-};
-
 BatchSortWs carve_bsort(void* base, size_t cap, int n) {
   BatchSortWs w{};
   size_t o = 0;
@@ -1191,7 +1248,12 @@ BatchSortWs carve_bsort(void* base, size_t cap, int n) {
     return p;
   };
   const size_t c = cap > 0 ? cap : 1;
-  w.off = static_cast<uint32_t*>(take((size_t(n) + 1) * 4));
+  const size_t sn = size_t(n) + 1;
+  w.off = static_cast<uint32_t*>(take(sn * 4));
+  w.cnt = static_cast<uint32_t*>(take(sn * 4));
+  w.order = static_cast<uint32_t*>(take(sn * 4));
+  w.starts = static_cast<uint32_t*>(take(sn * 4));
+  w.classes = static_cast<uint32_t*>(take(2 * kSegClasses * 4));
   w.total = static_cast<unsigned int*>(take(4));
   w.k0 = static_cast<ulonglong2*>(take(c * 16));
   w.k1 = static_cast<ulonglong2*>(take(c * 16));
@@ -1290,11 +1352,12 @@ cudaError_t cluster_sort(const uint64_t* in, const uint32_t* rows, const unsigne
     // o.ctr->sorted) to the cluster sort launched next.
     const uint32_t cap = uint32_t(std::min<size_t>(max_n, kRankMax));
     const dim3 grid((cap + kRankThreads - 1) / kRankThreads, kRankSplits);
-    rank_count<<<grid, kRankThreads, 0, s>>>(in, n_dev, uint32_t(max_n), o);
-    rank_place<<<(cap + kRankThreads - 1) / kRankThreads, kRankThreads, 0, s>>>(
-        in, n_dev, uint32_t(max_n), o);
+    cudaError_t e = launch_dep(rank_count, grid, dim3(kRankThreads), 0, s, in, n_dev,
+                               uint32_t(max_n), o);
+    if (e == cudaSuccess)
+      e = launch_dep(rank_place, dim3((cap + kRankThreads - 1) / kRankThreads),
+                     dim3(kRankThreads), 0, s, in, n_dev, uint32_t(max_n), o);
     count_launch(2);
-    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (max_n <= kRankMax) {
       *done = true;
@@ -1380,25 +1443,33 @@ cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32
   return e;
 }
 
+size_t batch_sort_seg_size(size_t ucap) {
+  size_t p = 1024;
+  while (p < ucap) p <<= 1;
+  return p;
+}
+
 size_t batch_sort_bytes(size_t total_cap, int n_scenes) {
   return carve_bsort(nullptr, total_cap, n_scenes).bytes;
 }
 
 cudaError_t batch_sort(const BatchSortScene* scenes, int n_scenes, size_t total_cap,
-                       void* scratch, cudaStream_t s) {
+                       size_t max_seg, void* scratch, cudaStream_t s) {
   if (n_scenes <= 0) return cudaSuccess;
   BatchSortWs w = carve_bsort(scratch, total_cap, n_scenes);
-  bsort_offsets<<<1, 1024, 0, s>>>(scenes, n_scenes, w.off, w.total);
+  bsort_layout<<<1, 1024, 0, s>>>(scenes, n_scenes, w);
   count_launch();
   const size_t cap = total_cap > 0 ? total_cap : 1;
   const int g = int(std::min<size_t>((cap + 255) / 256, size_t(sm_count()) * 8));
-  bsort_items<<<g, 256, 0, s>>>(scenes, n_scenes, w.off, w.total, w.k0, w.t0);
+  bsort_items<<<g, 256, 0, s>>>(scenes, n_scenes, w);
   count_launch();
+  // The padding items are in place, so the tile sort reads w.k0/w.t0 as they are.
   const BatchOrder ord{scenes, w.k0, w.t0};
   bool in1 = false;
-  cudaError_t e = run_merge_sort(ord, w.k0, w.k1, w.t0, w.t1, w.total, cap, s, &in1, nullptr);
+  cudaError_t e = run_merge_sort(ord, w.k0, w.k1, w.t0, w.t1, w.total, cap, s, &in1, nullptr,
+                                 w.classes, max_seg);
   if (e != cudaSuccess) return e;
-  bsort_scatter<<<g, 256, 0, s>>>(scenes, w.off, w.total, in1 ? w.t1 : w.t0);
+  bsort_scatter<<<g, 256, 0, s>>>(scenes, n_scenes, w);
   count_launch();
   return cudaGetLastError();
 }
