@@ -504,8 +504,9 @@ __device__ __forceinline__ void eval_tile(const PackArgs& pa, const float4* cf, 
 }
 
 // P points per thread (P/2 f32x2 pairs when F2, else scalar FFMA); the
-// 32-constraint loop is unrolled UJ times.
-template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 8>
+// 32-constraint loop is unrolled UJ times (fully by default: the row offsets
+// become immediates, which measured about 4% faster than 8 on l = 64, d = 3).
+template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 32>
 __global__ void __launch_bounds__(kFThreads)
     pack_fast_kernel(PackArgs pa, Sink sink, int vec_ok) {
   constexpr int R = F2 ? 2 : 1;  // scalar FMAs read each coefficient once
@@ -654,7 +655,7 @@ __global__ void __launch_bounds__(kFThreads)
   }
 }
 
-template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 8>
+template <int D, int NCH, class Sink, int P = 4, bool F2 = false, int UJ = 32>
 cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
   const size_t smem = size_t(1 + kFWarps) * NCH * 32 * Coef<D, F2 ? 2 : 1>::kQuads * sizeof(float4);
   auto kern = pack_fast_kernel<D, NCH, Sink, P, F2, UJ>;
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(kFThreads)
     }
     const int64_t p0 = wp0 + int64_t(lane) * P;
     uint64_t key[P];
-    eval_tile<D, NCH, P, false, 8>(pa, rows, p0, pi, key);
+    eval_tile<D, NCH, P, false, 32>(pa, rows, p0, pi, key);
     FastInsert{S.t}.template finish<P>(p0, S.n, key);
   }
 }
