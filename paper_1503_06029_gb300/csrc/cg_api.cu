@@ -492,12 +492,20 @@ cg_status dedup_small_tail(SmallWs& w, int ell, int word_bits, void* user_cells,
 cg_status dedup_wide_steps(WideWs& w, const uint64_t* keys64, int64_t n, int ell, bool rank,
                            cudaStream_t s, uint64_t* direct = nullptr, int64_t direct_cap = -1) {
   const int w64 = (ell + 63) / 64;
+  // The insert also records each representative's top 128 bits and the
+  // bucket counts of the sort, which then reads neither from the rows.
   WideTable t{w.slots, uint32_t(w.cap - 1), w.idx0, uint32_t(w.ucap), w.ctr};
+  t.ukeys = reinterpret_cast<ulonglong2*>(w.kw1);
+  t.bucket_count = bucket_sort_counts(w.radix, w.ucap);
+  t.bucket_bits = bucket_sort_bits(w.ucap);
+  t.ell = ell;
   CG_CUDA(launch_fill_u64(w.slots, kEmpty, w.cap, s), "clearing table");
+  CG_CUDA(cudaMemsetAsync(t.bucket_count, 0, (size_t(1) << t.bucket_bits) * sizeof(uint32_t), s),
+          "clearing bucket counts");
   CG_CUDA(launch_insert_wide(keys64, n, w64, t, s), "inserting vectors");
   uint32_t* sorted = nullptr;
   CG_CUDA(sort_wide(keys64, w64, ell, w.idx0, w.idx1, w.kw0, w.kw1, &w.ctr->n_unique, w.ucap,
-                    w.radix, s, &sorted, nullptr, &w.ctr->msort_done),
+                    w.radix, s, &sorted, nullptr, &w.ctr->msort_done, t.ukeys),
           "sorting cells");
   if (direct)
     CG_CUDA(launch_gather_rows(keys64, w64, sorted, &w.ctr->n_unique, w.ucap, direct, s,
@@ -782,9 +790,9 @@ cg_status cg_dedup_cells(const void* keys, int64_t n, int ell, int word_bits, vo
   if (!check_common(n, ell, word_bits, &why)) return fail(CG_ERR_INVALID_ARG, why);
   if (!ws_bytes) return fail(CG_ERR_INVALID_ARG, "ws_bytes is NULL");
   const size_t un = size_t(n > 0 ? n : 1);
+  const bool small = ell <= 64;
   const size_t cap = std::max<size_t>(1024, next_pow2(2 * un));
   const size_t ucap = un;
-  const bool small = ell <= 64;
   const bool convert = !small && word_bits == 32;
   {
     Carve c{nullptr};

@@ -509,10 +509,14 @@ __global__ void __launch_bounds__(1024) clear_seg(const SegClear* __restrict__ s
 
 // ------------------------------- wide path -------------------------------
 
+// Row hash: every word mixed on its own (salted by its position) and the
+// results folded, so that the multiplies of different words overlap instead
+// of forming one dependent chain through the row.
 __device__ __forceinline__ uint64_t hash_row(const uint64_t* r, int w) {
   uint64_t h = 0x9e3779b97f4a7c15ull * uint64_t(w);
-  for (int j = 0; j < w; ++j) h = mix64(h ^ r[j]);
-  return h;
+#pragma unroll 4
+  for (int j = 0; j < w; ++j) h ^= mix64(r[j] + 0xd1b54a32d192ed03ull * uint64_t(j + 1));
+  return mix64(h);
 }
 
 __device__ __forceinline__ bool rows_equal(const uint64_t* x, const uint64_t* y, int w) {
@@ -521,37 +525,47 @@ __device__ __forceinline__ bool rows_equal(const uint64_t* x, const uint64_t* y,
   return true;
 }
 
+// Insertion of row p (kp: its words, in global or shared memory) into the
+// table of distinct rows; a row found equal to a stored one is dropped.
+__device__ __forceinline__ void insert_row(const uint64_t* __restrict__ keys, int w,
+                                           const WideTable& t, int64_t p, const uint64_t* kp) {
+  const uint64_t h = hash_row(kp, w);
+  const uint32_t tag = uint32_t(h >> 32);
+  const uint64_t entry = (uint64_t(tag) << 32) | uint64_t(p);
+  uint32_t slot = uint32_t(h) & t.mask;
+  for (uint32_t probe = 0; probe <= t.mask; ++probe) {
+    uint64_t cur = t.slots[slot];
+    if (cur == kEmpty) {
+      cur = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + slot),
+                      static_cast<unsigned long long>(kEmpty),
+                      static_cast<unsigned long long>(entry));
+      if (cur == kEmpty) {
+        const unsigned int idx = atomicAdd(&t.ctr->n_unique, 1u);
+        if (idx < t.ucap) {
+          t.ulist[idx] = uint32_t(p);
+          if (t.ukeys) {
+            const ulonglong2 k = top128(kp, t.ell);
+            t.ukeys[idx] = k;
+            atomicAdd(&t.bucket_count[t.bucket_bits ? uint32_t(k.x >> (64 - t.bucket_bits)) : 0u],
+                      1u);
+          }
+        } else {
+          atomicOr(&t.ctr->overflow, 1u);
+        }
+        return;
+      }
+    }
+    if (uint32_t(cur >> 32) == tag && rows_equal(keys + uint64_t(uint32_t(cur)) * w, kp, w))
+      return;
+    slot = (slot + 1) & t.mask;
+  }
+  atomicOr(&t.ctr->overflow, 1u);
+}
+
 __global__ void insert_wide(const uint64_t* __restrict__ keys, int64_t n, int w, WideTable t) {
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n;
-       p += int64_t(gridDim.x) * blockDim.x) {
-    const uint64_t* kp = keys + p * w;
-    const uint64_t h = hash_row(kp, w);
-    const uint32_t tag = uint32_t(h >> 32);
-    const uint64_t entry = (uint64_t(tag) << 32) | uint64_t(p);
-    uint32_t slot = uint32_t(h) & t.mask;
-    bool done = false;
-    for (uint32_t probe = 0; probe <= t.mask && !done; ++probe) {
-      uint64_t cur = t.slots[slot];
-      if (cur == kEmpty) {
-        cur = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + slot),
-                        static_cast<unsigned long long>(kEmpty),
-                        static_cast<unsigned long long>(entry));
-        if (cur == kEmpty) {
-          const unsigned int idx = atomicAdd(&t.ctr->n_unique, 1u);
-          if (idx < t.ucap) t.ulist[idx] = uint32_t(p);
-          else atomicOr(&t.ctr->overflow, 1u);
-          done = true;
-          break;
-        }
-      }
-      if (uint32_t(cur >> 32) == tag && rows_equal(keys + uint64_t(uint32_t(cur)) * w, kp, w)) {
-        done = true;
-        break;
-      }
-      slot = (slot + 1) & t.mask;
-    }
-    if (!done) atomicOr(&t.ctr->overflow, 1u);
-  }
+       p += int64_t(gridDim.x) * blockDim.x)
+    insert_row(keys, w, t, p, keys + p * w);
 }
 
 // Rows idx[0 .. U) of keys, in that order, to out (nothing when out_cap >= 0
@@ -1232,10 +1246,10 @@ cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const W
 cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
                       void* scratch, cudaStream_t s, uint32_t** sorted_idx,
-                      const unsigned int* skip, unsigned int* flag) {
-  (void)scratch;
+                      const unsigned int* skip, unsigned int* flag, const void* ukeys) {
   return merge_sort_rows(keys, w64, ell, idx0, kw0, kw1, idx0, idx1, n_dev, max_n, s,
-                         sorted_idx, skip, flag);
+                         sorted_idx, skip, flag, scratch, radix_scratch_bytes(max_n),
+                         static_cast<const ulonglong2*>(ukeys));
 }
 
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,
@@ -1445,6 +1459,50 @@ __global__ void adopt_cells(const uint64_t* __restrict__ cells, int w, int ell, 
   }
 }
 
+// Rows of 2 .. 32 words checked with lanes over words: a warp step covers
+// R = 32 / w consecutive rows (lane l: row r0 + l / w, word l % w), reading
+// each row coalesced and the row before it (cached, the previous lanes' row).
+// Row i is after row i - 1 when they differ and the highest differing word
+// is larger in row i; bits at or above l in the top word are an error too
+// (high = the mask of those bits, or 0 to skip that check).
+__device__ __forceinline__ void check_rows_warp(const uint64_t* __restrict__ cells, int w,
+                                                uint32_t n, uint64_t high, DevCounters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const int R = 32 / w;
+  const int a = lane / w, q = lane - a * w;
+  const uint32_t seg_mask = w == 32 ? 0xffffffffu : ((1u << w) - 1u);
+  const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  const uint64_t wg = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  for (uint64_t r0 = wg * R; r0 < n; r0 += warps * R) {
+    const uint64_t i = r0 + a;
+    const bool live = a < R && i < n;
+    uint64_t y = 0, x = 0;
+    if (live) {
+      y = cells[i * w + q];
+      if (i > 0) x = cells[(i - 1) * w + q];
+    }
+    const uint32_t diff = __ballot_sync(0xffffffffu, live && i > 0 && x != y);
+    const uint32_t lt = __ballot_sync(0xffffffffu, x < y);
+    if (live && i > 0 && q == 0) {
+      const uint32_t seg = (diff >> (a * w)) & seg_mask;
+      if (seg == 0 || !((lt >> (a * w + 31 - __clz(seg))) & 1u))
+        atomicOr(&ctr->error, kErrUnsorted);
+    }
+    if (live && q == w - 1 && (y & high)) atomicOr(&ctr->error, kErrHighBits);
+  }
+}
+
+__global__ void adopt_cells_warp(const uint64_t* __restrict__ cells, int w, int ell, uint32_t n,
+                                 DevCounters* ctr) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_unique = n;
+  check_rows_warp(cells, w, n, (ell & 63) ? ~((1ull << (ell & 63)) - 1) : 0ull, ctr);
+}
+
+__global__ void check_sorted_warp(const uint64_t* __restrict__ cells, int w, DevCounters* ctr,
+                                  uint32_t max_n) {
+  check_rows_warp(cells, w, min(ctr->n_unique, max_n), 0ull, ctr);
+}
+
 __global__ void publish_done(const DevCounters* __restrict__ ctr, DevCounters* host_ctr,
                              unsigned int* host_flag, unsigned int seq) {
   static_assert(sizeof(DevCounters) % sizeof(unsigned int) == 0, "DevCounters words");
@@ -1478,13 +1536,26 @@ __global__ void publish_counts(const DevCounters* ctr, int64_t* out, int64_t cel
 cudaError_t launch_check_sorted(const uint64_t* cells, int w64, DevCounters* ctr, size_t max_n,
                                 cudaStream_t s) {
   if (max_n < 2) return cudaSuccess;
+  if (w64 >= 2 && w64 <= 32) {
+    const size_t steps = (max_n + (32 / w64) - 1) / (32 / w64);
+    check_sorted_warp<<<grid_for(steps, kThreads / 32), kThreads, 0, s>>>(cells, w64, ctr,
+                                                                         uint32_t(max_n));
+    return finish(0);
+  }
   check_sorted<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(cells, w64, ctr, uint32_t(max_n));
   return finish(0);
 }
 
 cudaError_t launch_adopt_cells(const uint64_t* cells, int64_t n, int ell, DevCounters* ctr,
                                cudaStream_t s) {
-  adopt_cells<<<grid_for(size_t(n) + 1, kThreads), kThreads, 0, s>>>(cells, (ell + 63) / 64, ell,
+  const int w64 = (ell + 63) / 64;
+  if (w64 >= 2 && w64 <= 32) {
+    const size_t steps = (size_t(n) + (32 / w64) - 1) / (32 / w64) + 1;
+    adopt_cells_warp<<<grid_for(steps, kThreads / 32), kThreads, 0, s>>>(cells, w64, ell,
+                                                                        uint32_t(n), ctr);
+    return finish(0);
+  }
+  adopt_cells<<<grid_for(size_t(n) + 1, kThreads), kThreads, 0, s>>>(cells, w64, ell,
                                                                       uint32_t(n), ctr);
   return finish(0);
 }

@@ -52,6 +52,21 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   return x;
 }
 
+// 64 bits of a row of 64-bit words starting at bit off (-64 < off <= l - 64;
+// below bit 0 reads as zeros), and the top 128 bits of a row of l > 64 bits as
+// (high, low): the cached sort key of the wide sorts (whole vector when
+// l <= 128).
+__device__ __forceinline__ uint64_t bits64_at(const uint64_t* row, int off) {
+  if (off < 0) return row[0] << (-off);
+  const int q = off >> 6, sh = off & 63;
+  const uint64_t lo = row[q] >> sh;
+  return sh ? (lo | (row[q + 1] << (64 - sh))) : lo;
+}
+
+__device__ __forceinline__ ulonglong2 top128(const uint64_t* row, int ell) {
+  return make_ulonglong2(bits64_at(row, ell - 64), bits64_at(row, ell - 128));
+}
+
 __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   z += 0x9e3779b97f4a7c15ull;
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -268,12 +283,16 @@ cudaError_t radix_sort_u64(uint64_t* keys0, uint64_t* keys1, uint32_t* vals0, ui
 // nothing when *skip is nonzero. For l > 128 with flag != nullptr (a device
 // word), the rows are sorted by the cached key alone and every short run of
 // equal keys is then ordered by one warp; the full-row comparison sort runs
-// only when some run is too long for that (flag records which).
+// only when some run is too long for that (flag records which). With scratch
+// (scratch_bytes of device memory, radix_scratch_bytes(max_n) is enough) a
+// bucket sort on the top bits runs first, and the merge sort only when some
+// bucket is too large for it.
 cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32_t* idx_in,
                             uint64_t* k0, uint64_t* k1, uint32_t* i0, uint32_t* i1,
                             const unsigned int* n_dev, size_t max_n, cudaStream_t s,
                             uint32_t** sorted_idx, const unsigned int* skip = nullptr,
-                            unsigned int* flag = nullptr);
+                            unsigned int* flag = nullptr, void* scratch = nullptr,
+                            size_t scratch_bytes = 0, const ulonglong2* ukeys = nullptr);
 
 // Batch sort: the distinct vectors of many scenes sorted together, scene by
 // scene (one merge sort on (scene, top 128 bits, whole vector)), then
@@ -448,6 +467,13 @@ struct WideTable {
   uint32_t* ulist;  // [ucap] representative input rows, insertion order
   uint32_t ucap;
   DevCounters* ctr;
+  // Optional (insert only): the top 128 bits of each representative, in
+  // ulist order, and counts of the representatives per value of their top
+  // bucket_bits bits (the bucket sort's histogram, cleared beforehand).
+  ulonglong2* ukeys = nullptr;
+  uint32_t* bucket_count = nullptr;
+  int bucket_bits = 0;
+  int ell = 0;
 };
 cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const WideTable& t,
                                cudaStream_t s);
@@ -455,7 +481,15 @@ cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const W
 cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,
                       void* scratch, cudaStream_t s, uint32_t** sorted_idx,
-                      const unsigned int* skip = nullptr, unsigned int* flag = nullptr);
+                      const unsigned int* skip = nullptr, unsigned int* flag = nullptr,
+                      const void* ukeys = nullptr);
+// The bucket sort inside sort_wide / merge_sort_rows (scratch of
+// radix_scratch_bytes(max_n) bytes): its bucket bits and its count array,
+// which an insert can fill (WideTable::bucket_count, cleared first) together
+// with the top-128-bit keys in ulist order (WideTable::ukeys, passed on as
+// ukeys) so that the sort reads neither from the rows.
+int bucket_sort_bits(size_t max_n);
+uint32_t* bucket_sort_counts(void* scratch, size_t max_n);
 // out_cap >= 0: out is a caller's buffer of that many rows, written only when
 // all U rows fit.
 cudaError_t launch_gather_rows(const uint64_t* keys, int w64, const uint32_t* idx,

@@ -605,17 +605,6 @@ constexpr int kMThreads = 256;
 constexpr uint32_t kPad = 0xffffffffu;
 
 // Bits [off, off + 64) of a row (positions below 0 read as zero, off > -64).
-__device__ __forceinline__ uint64_t bits64_at(const uint64_t* row, int off) {
-  if (off < 0) return row[0] << (-off);
-  const int q = off >> 6, sh = off & 63;
-  const uint64_t lo = row[q] >> sh;
-  return sh ? (lo | (row[q + 1] << (64 - sh))) : lo;
-}
-
-__device__ __forceinline__ ulonglong2 top128(const uint64_t* row, int ell) {
-  return make_ulonglong2(bits64_at(row, ell - 64), bits64_at(row, ell - 128));
-}
-
 struct RowOrder {
   using Tag = uint32_t;  // row number
   static constexpr int kItems = 8;
@@ -1263,6 +1252,272 @@ BatchSortWs carve_bsort(void* base, size_t cap, int n) {
   return w;
 }
 
+// ---------------------------------------------------------------------------
+// Bucket sort of rows of l > 64 bits (the distinct vectors of step 2, §3.2,
+// ordered as integers with bit l-1 the most significant). The top B bits of a
+// row pick one of 2^B buckets (B from the capacity: about kBucketAvg rows a
+// bucket when the distinct rows fill it). A histogram, one scan and one
+// scatter put every (top 128 bits, row number) pair in its bucket's range;
+// one block per bucket then orders the range in shared memory with a bitonic
+// network on the top 128 bits, whole rows breaking ties. The plan kernel
+// checks every bucket against kBucketMax before anything is written: when one
+// is larger (top bits far from uniform, as the signs of a few planes are),
+// the merge sort runs instead, so such inputs cost time, never correctness.
+// ---------------------------------------------------------------------------
+constexpr int kBucketAvg = 512;
+constexpr int kBucketMax = 2048;
+constexpr int kBucketThreads = 256;
+constexpr int kBucketMaxBits = 14;
+
+struct BucketWs {
+  unsigned int* ok;       // 1: every bucket fits, the bucket sort runs
+  unsigned int* fb_skip;  // nonzero: the merge sort's kernels return at once
+  uint32_t* count;        // [2^bits]
+  uint32_t* start;        // [2^bits + 1]
+  uint32_t* cursor;       // [2^bits]
+  int bits;
+};
+
+size_t bucket_ws_bytes(int bits) { return 16 + (3 * (size_t(1) << bits) + 1) * sizeof(uint32_t); }
+
+BucketWs carve_bucket(void* scratch, int bits) {
+  char* p = static_cast<char*>(scratch);
+  const size_t nb = size_t(1) << bits;
+  BucketWs b;
+  b.ok = reinterpret_cast<unsigned int*>(p);
+  b.fb_skip = b.ok + 1;
+  b.count = reinterpret_cast<uint32_t*>(p + 16);
+  b.start = b.count + nb;
+  b.cursor = b.start + nb + 1;
+  b.bits = bits;
+  return b;
+}
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t top, int bits) {
+  return bits ? uint32_t(top >> (64 - bits)) : 0u;
+}
+
+__global__ void __launch_bounds__(kBucketThreads)
+    bucket_hist(const uint64_t* __restrict__ rows, int w, int ell,
+                const uint32_t* __restrict__ idx_in, const unsigned int* n_dev, uint32_t max_n,
+                BucketWs b, const unsigned int* skip) {
+  if (skip && *skip) return;
+  const uint32_t u = min(*n_dev, max_n);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
+    const uint32_t r = idx_in ? idx_in[i] : i;
+    atomicAdd(&b.count[bucket_of(bits64_at(rows + uint64_t(r) * w, ell - 64), b.bits)], 1u);
+  }
+}
+
+// One block: bucket starts (exclusive scan of the counts), cursors cleared,
+// and the decision between the bucket sort and the merge sort.
+__global__ void __launch_bounds__(1024) bucket_plan(BucketWs b, const unsigned int* skip) {
+  __shared__ uint32_t part[1024];
+  __shared__ int too_big;
+  if (skip && *skip) {
+    if (threadIdx.x == 0) {
+      *b.ok = 0u;
+      *b.fb_skip = 1u;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) too_big = 0;
+  const uint32_t nb = 1u << b.bits;
+  const uint32_t per = (nb + 1023) / 1024;
+  const uint32_t j0 = threadIdx.x * per;
+  const uint32_t j1 = min(j0 + per, nb);
+  uint32_t sum = 0;
+  bool big = false;
+  for (uint32_t j = j0; j < j1; ++j) {
+    const uint32_t c = b.count[j];
+    sum += c;
+    big |= c > uint32_t(kBucketMax);
+  }
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (big) too_big = 1;
+  for (int off = 1; off < 1024; off <<= 1) {
+    const uint32_t v = int(threadIdx.x) >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (uint32_t j = j0; j < j1; ++j) {
+    b.start[j] = run;
+    run += b.count[j];
+    b.cursor[j] = 0u;
+  }
+  if (threadIdx.x == 1023) b.start[nb] = part[1023];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *b.ok = too_big ? 0u : 1u;
+    *b.fb_skip = too_big ? 0u : 1u;
+  }
+}
+
+__global__ void __launch_bounds__(kBucketThreads)
+    bucket_scatter(const uint64_t* __restrict__ rows, int w, int ell,
+                   const uint32_t* __restrict__ idx_in, const unsigned int* n_dev, uint32_t max_n,
+                   BucketWs b, const ulonglong2* __restrict__ ukeys,
+                   ulonglong2* __restrict__ kout, uint32_t* __restrict__ xout) {
+  if (!*b.ok) return;
+  const uint32_t u = min(*n_dev, max_n);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
+    const uint32_t r = idx_in ? idx_in[i] : i;
+    const ulonglong2 k = ukeys ? ukeys[i] : top128(rows + uint64_t(r) * w, ell);
+    const uint32_t bk = bucket_of(k.x, b.bits);
+    const uint32_t pos = b.start[bk] + atomicAdd(&b.cursor[bk], 1u);
+    if (pos < b.start[bk + 1]) {  // always: the counts came from the same items
+      kout[pos] = k;
+      xout[pos] = r;
+    }
+  }
+}
+
+size_t bucket_local_smem() {
+  return size_t(kBucketMax) * (sizeof(ulonglong2) + sizeof(uint32_t)) + 3 * 256 * sizeof(uint32_t);
+}
+
+// (key, row number) order of the bucket sort; padding items (key all ones,
+// row number kPad) come after every real item.
+__device__ __forceinline__ bool bkey_less(const ulonglong2& ka, uint32_t ia, const ulonglong2& kb,
+                                          uint32_t ib) {
+  if (ka.x != kb.x) return ka.x < kb.x;
+  if (ka.y != kb.y) return ka.y < kb.y;
+  return ia < ib;
+}
+
+// One block per bucket (grid-stride over buckets), ordered by (top 128 bits,
+// row number); keys go to kout and row numbers to out in that order. Rows
+// longer than 128 bits that share their top 128 bits are left in row-number
+// order here, as the key-only merge sort leaves them; the run fix-up orders
+// them afterwards. The usual case is a counting sort on the 8 bits below the
+// bucket's own bits (256 sub-buckets, a few items each when the bits are
+// spread), each sub-bucket then put in order by one thread's insertion sort;
+// when some sub-bucket holds more than kSubMax items, the block sorts the
+// whole bucket with a bitonic network instead.
+constexpr uint32_t kSubMax = 32;
+
+__global__ void __launch_bounds__(kBucketThreads)
+    bucket_local(const uint64_t* __restrict__ rows, int w, int ell, BucketWs b,
+                 const ulonglong2* kin, const uint32_t* xin, ulonglong2* kout, uint32_t* out) {
+  static_assert(kBucketThreads == 256, "one thread per sub-bucket");
+  extern __shared__ __align__(16) unsigned char bucket_sm[];
+  ulonglong2* sk = reinterpret_cast<ulonglong2*>(bucket_sm);
+  uint32_t* si = reinterpret_cast<uint32_t*>(sk + kBucketMax);
+  uint32_t* hist = si + kBucketMax;  // [256]
+  uint32_t* off = hist + 256;        // [256]
+  uint32_t* cur = off + 256;         // [256]
+  __shared__ uint32_t wsum[kBucketThreads / 32];
+  __shared__ int big;
+  (void)rows;
+  (void)w;
+  (void)ell;
+  if (!*b.ok) return;
+  const uint32_t nb = 1u << b.bits;
+  const int dshift = 56 - b.bits;  // the 8 bits below the bucket's bits
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint32_t bk = blockIdx.x; bk < nb; bk += gridDim.x) {
+    const uint32_t lo = b.start[bk];
+    const uint32_t cnt = min(b.start[bk + 1] - lo, uint32_t(kBucketMax));
+    if (cnt <= 1) {
+      if (cnt == 1 && threadIdx.x == 0) {
+        const ulonglong2 k = kin[lo];
+        const uint32_t r = xin[lo];
+        kout[lo] = k;
+        out[lo] = r;
+      }
+      continue;
+    }
+    hist[threadIdx.x] = 0u;
+    cur[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) big = 0;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x)
+      atomicAdd(&hist[uint32_t(kin[lo + t].x >> dshift) & 0xffu], 1u);
+    __syncthreads();
+    {
+      const uint32_t v = hist[threadIdx.x];
+      uint32_t incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+      }
+      if (lane == 31) wsum[wid] = incl;
+      __syncthreads();
+      uint32_t before = 0;
+      for (int k = 0; k < wid; ++k) before += wsum[k];
+      off[threadIdx.x] = before + incl - v;
+      if (v > kSubMax) big = 1;
+    }
+    __syncthreads();
+    if (!big) {
+      for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const ulonglong2 k = kin[lo + t];
+        const uint32_t d = uint32_t(k.x >> dshift) & 0xffu;
+        const uint32_t pos = off[d] + atomicAdd(&cur[d], 1u);
+        sk[pos] = k;
+        si[pos] = xin[lo + t];
+      }
+      __syncthreads();
+      {
+        const uint32_t s0 = off[threadIdx.x], c = hist[threadIdx.x];
+        for (uint32_t i = s0 + 1; i < s0 + c; ++i) {
+          const ulonglong2 k = sk[i];
+          const uint32_t r = si[i];
+          uint32_t j = i;
+          while (j > s0 && bkey_less(k, r, sk[j - 1], si[j - 1])) {
+            sk[j] = sk[j - 1];
+            si[j] = si[j - 1];
+            --j;
+          }
+          sk[j] = k;
+          si[j] = r;
+        }
+      }
+      __syncthreads();
+    } else {
+      uint32_t p2 = 2;
+      while (p2 < cnt) p2 <<= 1;
+      for (uint32_t t = threadIdx.x; t < p2; t += blockDim.x) {
+        if (t < cnt) {
+          sk[t] = kin[lo + t];
+          si[t] = xin[lo + t];
+        } else {
+          sk[t] = make_ulonglong2(~0ull, ~0ull);
+          si[t] = kPad;
+        }
+      }
+      __syncthreads();
+      for (uint32_t size = 2; size <= p2; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t t = threadIdx.x; t < p2 / 2; t += blockDim.x) {
+            const uint32_t i = 2 * t - (t & (stride - 1));
+            const uint32_t j = i + stride;
+            const bool up = (i & size) == 0;
+            if (bkey_less(sk[j], si[j], sk[i], si[i]) == up) {
+              const ulonglong2 tk = sk[i];
+              sk[i] = sk[j];
+              sk[j] = tk;
+              const uint32_t tr = si[i];
+              si[i] = si[j];
+              si[j] = tr;
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+    for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+      kout[lo + t] = sk[t];
+      out[lo + t] = si[t];
+    }
+    __syncthreads();  // the next bucket reuses the shared arrays
+  }
+}
+
 }  // namespace
 
 size_t scan_scratch_bytes(size_t max_n) {
@@ -1279,6 +1534,16 @@ size_t radix_scratch_bytes(size_t max_n) {
     bytes += scan_scratch_bytes(256 * tiles);
   }
   return bytes;
+}
+
+int bucket_sort_bits(size_t max_n) {
+  int bits = 0;
+  while (bits < kBucketMaxBits && (size_t(kBucketAvg) << bits) < max_n) ++bits;
+  return bits;
+}
+
+uint32_t* bucket_sort_counts(void* scratch, size_t max_n) {
+  return carve_bucket(scratch, bucket_sort_bits(max_n)).count;
 }
 
 cudaError_t scan_exclusive_u32(const uint32_t* in, unsigned long long* out,
@@ -1377,13 +1642,56 @@ cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32
                             uint64_t* k0, uint64_t* k1, uint32_t* i0, uint32_t* i1,
                             const unsigned int* n_dev, size_t max_n, cudaStream_t s,
                             uint32_t** sorted_idx, const unsigned int* skip,
-                            unsigned int* flag) {
+                            unsigned int* flag, void* scratch, size_t scratch_bytes,
+                            const ulonglong2* ukeys) {
   *sorted_idx = i0;
   if (max_n == 0) return cudaSuccess;
   if (ell <= 64) return cudaErrorInvalidValue;
   ulonglong2* kk0 = reinterpret_cast<ulonglong2*>(k0);
   ulonglong2* kk1 = reinterpret_cast<ulonglong2*>(k1);
   bool in1 = false;
+  const int bits = bucket_sort_bits(max_n);
+  const unsigned int* ext_skip = skip;
+  if (max_n < (1ull << 32) && scratch && bucket_ws_bytes(bits) <= scratch_bytes) {
+    // The bucket sort first; the (key-only) merge sort below runs only when a
+    // bucket is too large (b.fb_skip). Its keys and row numbers go to the
+    // buffers the merge sort would end in, the row numbers through a buffer
+    // other than idx_in, which the merge sort may still need.
+    const BucketWs b = carve_bucket(scratch, bits);
+    bool par = false;
+    for (size_t width = size_t(kMThreads) * RowOrder::kItems; width < max_n; width *= 2)
+      par = !par;
+    uint32_t* out = par ? i1 : i0;
+    uint32_t* x = out != idx_in ? out : (out == i0 ? i1 : i0);
+    cudaError_t e;
+    const int g = int(std::max<size_t>(
+        1, std::min<size_t>((max_n + kBucketThreads - 1) / kBucketThreads,
+                            size_t(sm_count()) * 8)));
+    if (!ukeys) {  // counts from the rows (else the insert made them)
+      e = cudaMemsetAsync(b.count, 0, (size_t(1) << bits) * sizeof(uint32_t), s);
+      if (e != cudaSuccess) return e;
+      bucket_hist<<<g, kBucketThreads, 0, s>>>(rows, w64, ell, idx_in, n_dev, uint32_t(max_n), b,
+                                               skip);
+      count_launch();
+    }
+    bucket_plan<<<1, 1024, 0, s>>>(b, skip);
+    bucket_scatter<<<g, kBucketThreads, 0, s>>>(rows, w64, ell, idx_in, n_dev, uint32_t(max_n),
+                                                b, ukeys, kk0, x);
+    const size_t smem = bucket_local_smem();
+    if ((e = ensure_smem_limit(reinterpret_cast<const void*>(bucket_local), smem)) != cudaSuccess)
+      return e;
+    int per_sm = 0;
+    if ((e = blocks_per_sm(reinterpret_cast<const void*>(bucket_local), kBucketThreads, smem,
+                           &per_sm)) != cudaSuccess)
+      return e;
+    const int gl = int(std::min<size_t>(size_t(1) << bits,
+                                        size_t(sm_count()) * size_t(per_sm > 0 ? per_sm : 1)));
+    bucket_local<<<gl, kBucketThreads, smem, s>>>(rows, w64, ell, b, kk0, x, par ? kk1 : kk0,
+                                                  out);
+    count_launch(3);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    skip = b.fb_skip;
+  }
   if (ell <= 128 || !flag) {
     const RowOrder ord{rows, w64, ell, ell <= 128, idx_in};
     cudaError_t e = run_merge_sort(ord, kk0, kk1, i0, i1, n_dev, max_n, s, &in1, skip);
@@ -1423,7 +1731,7 @@ cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32
   if (use_long && (e = cudaMemsetAsync(long_count, 0, sizeof(ulonglong2), s)) != cudaSuccess)
     return e;
   msort_fix_runs<<<g, kFixWarps * 32, smem, s>>>(in1 ? kk1 : kk0, out, rows, w64, n_dev,
-                                                 uint32_t(max_n), flag, skip,
+                                                 uint32_t(max_n), flag, ext_skip,
                                                  use_long ? long_runs : nullptr, long_count);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1431,7 +1739,8 @@ cudaError_t merge_sort_rows(const uint64_t* rows, int w64, int ell, const uint32
     const unsigned lg = unsigned(std::max<size_t>(1, std::min<size_t>(
                                                          (max_n + kLongMax - 1) / kLongMax,
                                                          size_t(sm_count()) * 2)));
-    msort_fix_long<<<lg, kLongThreads, 0, s>>>(long_runs, long_count, out, rows, w64, ell, skip);
+    msort_fix_long<<<lg, kLongThreads, 0, s>>>(long_runs, long_count, out, rows, w64, ell,
+                                               ext_skip);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
