@@ -910,12 +910,6 @@ constexpr int kFixWarps = 8;
 constexpr int kFixWords = 512;   // shared-memory words per warp
 constexpr int kFixMaxRun = 64;   // at most two rows per lane
 
-__device__ __forceinline__ bool srow_less(const uint64_t* a, const uint64_t* b, int w) {
-  for (int q = w - 1; q >= 0; --q)
-    if (a[q] != b[q]) return a[q] < b[q];
-  return false;
-}
-
 __device__ __forceinline__ bool same_key(const ulonglong2& a, const ulonglong2& b) {
   return a.x == b.x && a.y == b.y;
 }
@@ -928,11 +922,13 @@ __global__ void __launch_bounds__(kFixWarps * 32)
                    uint32_t max_n, unsigned int* flag, const unsigned int* skip,
                    uint2* __restrict__ long_runs, unsigned int* long_count) {
   extern __shared__ uint64_t fix_sm[];
+  __shared__ int8_t hd_all[kFixWarps][kFixMaxRun];
   if (skip && *skip) return;
   const uint32_t n = min(*n_dev, max_n);
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   uint64_t* sr = fix_sm + size_t(wid) * kFixWords;
+  int8_t* hd_sm = hd_all[wid];
   const int stride = w + 1;
   const uint32_t max_run = uint32_t(min(kFixMaxRun, kFixWords / stride));
   const uint32_t chunks = (n + 31) / 32;
@@ -999,13 +995,53 @@ __global__ void __launch_bounds__(kFixWarps * 32)
         }
       }
       __syncwarp();
+      // Each row's highest word that differs from the run's first row (the
+      // pivot; -1 for the pivot). Two rows whose highest words differ are
+      // ordered by the higher one alone (there the other row agrees with the
+      // pivot); rows with the same highest word compare that word and, only
+      // when it is equal too, the words below it.
+      int hd[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t a = uint32_t(lane) + 32u * j;
+        int q = -1;
+        if (a < m && a > 0) {
+          q = w - 1;
+          while (q >= 0 && sr[a * stride + q] == sr[q]) --q;
+        }
+        hd[j] = q;
+        if (a < m) hd_sm[a] = int8_t(q);
+      }
+      __syncwarp();
       uint32_t rank[2] = {0u, 0u};
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const uint32_t a = uint32_t(lane) + 32u * j;
-        if (a < m)
-          for (uint32_t b = 0; b < m; ++b)
-            rank[j] += (b != a && srow_less(sr + b * stride, sr + a * stride, w)) ? 1u : 0u;
+        if (a < m) {
+          const uint64_t* ra = sr + a * stride;
+          const int da = hd[j];
+          for (uint32_t b = 0; b < m; ++b) {
+            if (b == a) continue;
+            const uint64_t* rb = sr + b * stride;
+            const int db = hd_sm[b];
+            bool lt;
+            if (db > da) {
+              lt = rb[db] < sr[db];
+            } else if (da > db) {
+              lt = ra[da] > sr[da];
+            } else if (rb[db] != ra[db]) {
+              lt = rb[db] < ra[db];
+            } else {
+              lt = false;
+              for (int q = db - 1; q >= 0; --q)
+                if (rb[q] != ra[q]) {
+                  lt = rb[q] < ra[q];
+                  break;
+                }
+            }
+            rank[j] += lt ? 1u : 0u;
+          }
+        }
       }
       __syncwarp();
 #pragma unroll
