@@ -402,7 +402,8 @@ def serve_measure(dev, capacity_scenes_per_s: float, n_requests: int = 2000,
                 "sustained": {"value": pts_total / span_s / 1e6, "unit": UNIT,
                               "scenes_per_s": n_requests / span_s},
                 "oracle_digest_mismatches": mism[0], "max_running": st["max_running"],
-                "peak_bytes": st["peak_bytes"]})
+                "peak_bytes": st["peak_bytes"], "groups_so_far": st["groups"],
+                "grouped_so_far": st["grouped"]})
     return out
 
 

@@ -414,6 +414,8 @@ typedef struct cg_server_stats {
   size_t bytes_in_use;            /* charged against the budget now */
   size_t peak_bytes;              /* maximum of bytes_in_use so far */
   int max_running;                /* most requests running at once so far */
+  int64_t groups;                 /* launches of admitted requests together ... */
+  int64_t grouped;                /* ... and the requests started that way */
 } cg_server_stats;
 
 /* Creates a server on `device` that holds at most hbm_budget_bytes of device

@@ -84,7 +84,8 @@ class CgServerStats(ctypes.Structure):
                 ("failed", ctypes.c_int64), ("retried", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
-                ("max_running", ctypes.c_int)]
+                ("max_running", ctypes.c_int), ("groups", ctypes.c_int64),
+                ("grouped", ctypes.c_int64)]
 
 
 class CellGraphError(RuntimeError):

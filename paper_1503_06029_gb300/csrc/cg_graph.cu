@@ -1518,6 +1518,22 @@ __global__ void publish_done(const DevCounters* __restrict__ ctr, DevCounters* h
   }
 }
 
+// publish_done for several requests at once: block i publishes entry i.
+__global__ void publish_group(const PublishEntry* __restrict__ e, int n) {
+  constexpr int kWords = int(sizeof(DevCounters) / sizeof(unsigned int));
+  if (int(blockIdx.x) >= n) return;
+  const PublishEntry p = e[blockIdx.x];
+  const unsigned int* src = reinterpret_cast<const unsigned int*>(p.ctr);
+  unsigned int* dst = reinterpret_cast<unsigned int*>(p.host_ctr);
+  if (threadIdx.x < kWords) dst[threadIdx.x] = src[threadIdx.x];
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    *reinterpret_cast<volatile unsigned int*>(p.host_flag) = p.seq;
+  }
+}
+
 __global__ void publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,
                                int64_t edges_cap) {
   griddep_wait();
@@ -1563,6 +1579,12 @@ cudaError_t launch_adopt_cells(const uint64_t* cells, int64_t n, int ell, DevCou
 cudaError_t launch_publish_done(const DevCounters* ctr, DevCounters* host_ctr,
                                 unsigned int* host_flag, unsigned int seq, cudaStream_t s) {
   publish_done<<<1, 32, 0, s>>>(ctr, host_ctr, host_flag, seq);
+  return finish(0);
+}
+
+cudaError_t launch_publish_group(const PublishEntry* e, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  publish_group<<<n, 32, 0, s>>>(e, n);
   return finish(0);
 }
 

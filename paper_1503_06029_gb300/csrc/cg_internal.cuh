@@ -382,6 +382,14 @@ cudaError_t launch_adopt_cells(const uint64_t* cells, int64_t n, int ell, DevCou
 // seq from the flag (with acquire ordering) sees the counters.
 cudaError_t launch_publish_done(const DevCounters* ctr, DevCounters* host_ctr,
                                 unsigned int* host_flag, unsigned int seq, cudaStream_t s);
+// The same for several requests in one launch (one block per entry).
+struct PublishEntry {
+  const DevCounters* ctr;
+  DevCounters* host_ctr;
+  unsigned int* host_flag;
+  unsigned int seq;
+};
+cudaError_t launch_publish_group(const PublishEntry* e, int n, cudaStream_t s);
 // out[0] = U, out[1] = E, out[2] = status (CG_OK, CG_ERR_CAPACITY when a count
 // exceeds its cap, CG_ERR_TIMEOUT / CG_ERR_INTERNAL on device-side failures).
 cudaError_t launch_publish_counts(const DevCounters* ctr, int64_t* out, int64_t cells_cap,

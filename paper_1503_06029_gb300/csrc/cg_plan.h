@@ -80,6 +80,14 @@ bool scene_batch_sortable(const ScenePlan& plan);
 BatchSortScene scene_sort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan,
                                uint64_t* user_cells, int64_t user_cap);
 
+// Descriptors of a scene of l <= 64 (plan.small) for the segmented kernels:
+// its clear, its sign + insert (tiles numbered from tile0 in its launch), and
+// its single-pass search (HASH or SORTED; edges to `edges`, at most
+// edges_cap). Null outputs are skipped.
+void scene_small_descs(char* ws, DevCounters* ctr, const ScenePlan& plan, const PackArgs& pa,
+                       uint64_t tile0, uint32_t* edges, int64_t edges_cap, SegClear* clr,
+                       SegPackScene* pk, SegSearchScene* se);
+
 // Whether a strategy sorts (key, cell) pairs (PIVOT, HALVES), the key width of
 // a scene's pairs, and the descriptor of those pairs in workspace ws.
 bool keysort_strategy(int strategy);

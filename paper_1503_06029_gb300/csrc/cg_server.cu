@@ -26,6 +26,7 @@
 // blocks (fragmentation) waits, like one that does not fit the budget, until a
 // block is freed.
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <condition_variable>
 #include <deque>
@@ -45,6 +46,14 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int kMaxSlots = 64;
 constexpr int kSchedThreads = 4;  // scheduler threads (enqueueing is host-bound)
+// Requests admitted in one pass that the segmented kernels can take (l <= 64,
+// HASH or SORTED lookups, fp32 sign kernel) start together when there are at
+// least kGroupMin of them: about 10 launches and one upload for the group
+// instead of about 7 launches and 3 copies per request. Admission itself is
+// not held back to form groups (measured: waiting for free slots cost more
+// than the launches it saved), so groups form when requests arrive in bursts.
+constexpr int kGroupMin = 4;
+constexpr int kGroupMax = 64;
 
 thread_local std::string t_msg;
 
@@ -78,6 +87,8 @@ struct Req {
   char* result = nullptr;
   int slot = -1;
   int worker = -1;
+  int run_slot = -1;  // the slot whose stream carries the work (own, or its group's)
+  struct Group* group = nullptr;        // the group it ran in, if any
   unsigned int seq = 0;  // value its completion writes to the slot's host flag
   bool stream_error = false;
   // outcome
@@ -85,6 +96,16 @@ struct Req {
   double t_submit = 0, t_admit = -1, t_done = 0;
   int retries = 0;
   cg_server* srv = nullptr;
+};
+
+// Requests started together through the segmented kernels share one device
+// block (descriptors, constraint arrays, sort scratch), freed when the last
+// of them is settled.
+struct Group {
+  char* block = nullptr;
+  size_t bytes = 0;
+  int pending = 0;            // members not yet settled (changed under the server's mu)
+  std::vector<char> staging;  // host copy of the uploaded descriptors
 };
 
 }  // namespace
@@ -123,6 +144,7 @@ struct cg_server {
   int running = 0, max_running = 0;
   int64_t next_id = 1;
   int64_t submitted = 0, completed = 0, failed = 0, retried = 0;
+  int64_t groups = 0, grouped = 0;
   int inject_alloc_fail = 0;
   cg_tune_params tune[CG_TUNE_BUCKETS];
   bool stop = false;
@@ -133,6 +155,20 @@ namespace {
 double now_us(const cg_server* s) {
   return std::chrono::duration<double, std::micro>(Clock::now() - s->t0).count();
 }
+
+// Whether the segmented kernels can take a request (see kGroupMin), before
+// and after it has its blocks.
+bool group_candidate(const Req* r) {
+  const ScenePlan& p = r->plan;
+  static const bool tc_forced = [] {
+    const char* sk = std::getenv("CG_SIGN_KERNEL");
+    return sk && std::strcmp(sk, "tc") == 0;
+  }();
+  return r->sc.n > 0 && p.small && scene_batch_sortable(p) && p.tp.sign_kernel != 1 &&
+         !tc_forced && (p.tp.strategy == CG_STRATEGY_HASH || p.tp.strategy == CG_STRATEGY_SORTED);
+}
+
+bool group_eligible(const Req* r) { return r->work && r->result && group_candidate(r); }
 
 // Sizes of a request's two blocks for its current capacities.
 void plan_request(Req* r) {
@@ -229,6 +265,163 @@ cg_status start_request(cg_server* s, Req* r) {
   return CG_OK;
 }
 
+// Device layout of a group's block: descriptors, the constraint arrays of
+// host-input requests, the searches' scratch and the sort's scratch.
+struct GroupLayout {
+  size_t clr, pk, sort, se, pub, scr, bs, desc_bytes, bytes;
+  std::vector<size_t> a, b;
+  size_t sort_cap, sort_seg;
+};
+
+GroupLayout group_layout(const std::vector<Req*>& g) {
+  GroupLayout L{};
+  const size_t K = g.size();
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + (bytes > 0 ? bytes : 1));
+    return o;
+  };
+  L.clr = take(K * sizeof(SegClear));
+  L.pk = take(K * sizeof(SegPackScene));
+  L.sort = take(K * sizeof(BatchSortScene));
+  L.se = take(K * sizeof(SegSearchScene));
+  L.pub = take(K * sizeof(PublishEntry));
+  L.scr = take(2 * (K + 2) * sizeof(unsigned int));
+  L.a.assign(K, 0);
+  L.b.assign(K, 0);
+  for (size_t i = 0; i < K; ++i)
+    if (g[i]->on_host) {
+      L.a[i] = take(size_t(g[i]->sc.ell) * g[i]->sc.d * 4);
+      L.b[i] = take(size_t(g[i]->sc.ell) * 8);
+    }
+  L.desc_bytes = off;
+  L.sort_cap = 0;
+  L.sort_seg = 1024;
+  for (const Req* r : g) {
+    const size_t seg = batch_sort_seg_size(r->plan.ucap);
+    L.sort_cap += seg;
+    L.sort_seg = std::max(L.sort_seg, seg);
+  }
+  L.bs = take(batch_sort_bytes(L.sort_cap, int(K)));
+  L.bytes = off;
+  return L;
+}
+
+// Starts the requests of g (admitted, blocks and slots assigned, each with
+// run_slot = g[0]->slot) together on g[0]'s slot stream: one upload of their
+// descriptors and constraint arrays (staged in `staging`, which must live
+// until the work is done), host points copied into each request's work
+// block; then the clears, a sign + insert launch per (d,
+// constraint chunks), one sort of every request's distinct vectors, the
+// searches (HASH, then SORTED) and one completion launch. No lock held.
+cg_status start_group(cg_server* s, const std::vector<Req*>& g, char* block,
+                      const GroupLayout& L, std::vector<char>& staging) {
+  const int K = int(g.size());
+  cudaStream_t st = s->streams[size_t(g[0]->slot)];
+  auto undo = [&](cudaError_t err, const char* what) {
+    return srv_fail(CG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
+  };
+  staging.assign(L.desc_bytes, 0);
+  char* hb = staging.data();
+  SegClear* hclr = reinterpret_cast<SegClear*>(hb + L.clr);
+  SegPackScene* hpk = reinterpret_cast<SegPackScene*>(hb + L.pk);
+  BatchSortScene* hsort = reinterpret_cast<BatchSortScene*>(hb + L.sort);
+  SegSearchScene* hse = reinterpret_cast<SegSearchScene*>(hb + L.se);
+  PublishEntry* hpub = reinterpret_cast<PublishEntry*>(hb + L.pub);
+  std::vector<PackArgs> pa(size_t(K), PackArgs{nullptr, 0, 0, nullptr, nullptr, 0});
+  std::vector<char*> ws(static_cast<size_t>(K), nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < K; ++i) {
+    Req* r = g[size_t(i)];
+    const cg_scene& sc = r->sc;
+    const int32_t* pts = sc.pts;
+    const int32_t* a = sc.a;
+    const int64_t* b = sc.b;
+    const size_t off0 = align256(sizeof(DevCounters));
+    if (r->on_host) {
+      // Copied, not read in place from pinned memory: copies by the copy
+      // engines served more scenes per second than sign kernels reading the
+      // host link (31.1 k against 27.4 k scenes/s at half load).
+      int32_t* dp = reinterpret_cast<int32_t*>(r->work + off0);
+      if ((e = cudaMemcpyAsync(dp, sc.pts, size_t(sc.n) * sc.d * 4, cudaMemcpyHostToDevice,
+                               st)) != cudaSuccess)
+        return undo(e, "copying points");
+      pts = dp;
+      std::memcpy(hb + L.a[size_t(i)], sc.a, size_t(sc.ell) * sc.d * 4);
+      std::memcpy(hb + L.b[size_t(i)], sc.b, size_t(sc.ell) * 8);
+      a = reinterpret_cast<const int32_t*>(block + L.a[size_t(i)]);
+      b = reinterpret_cast<const int64_t*>(block + L.b[size_t(i)]);
+    }
+    pa[size_t(i)] = PackArgs{pts, sc.n, sc.d, a, b, sc.ell};
+    ws[size_t(i)] = r->work + off0 + r->in_bytes;
+    DevCounters* ctr = reinterpret_cast<DevCounters*>(r->work);
+    scene_small_descs(ws[size_t(i)], ctr, r->plan, pa[size_t(i)], 0, nullptr, 0, &hclr[i],
+                      nullptr, nullptr);
+    hsort[i] = scene_sort_desc(ws[size_t(i)], ctr, r->plan, reinterpret_cast<uint64_t*>(r->result),
+                               int64_t(r->plan.ucap));
+    hpub[i] = PublishEntry{ctr, s->dctr + r->slot, s->dflag + r->slot, r->seq};
+  }
+  // Sign + insert descriptors grouped by (d, constraint chunks), each group
+  // numbering its 128-point tiles from 0; searches HASH first.
+  struct PackGroup {
+    int d, nch, first, count;
+    uint64_t tiles;
+  };
+  std::vector<PackGroup> pgroups;
+  int n_pk = 0;
+  for (int d = 1; d <= 4; ++d)
+    for (int nch = 1; nch <= 2; ++nch) {
+      PackGroup gr{d, nch, n_pk, 0, 0};
+      for (int i = 0; i < K; ++i) {
+        const Req* r = g[size_t(i)];
+        if (r->sc.d != d || (r->sc.ell > 32 ? 2 : 1) != nch) continue;
+        scene_small_descs(ws[size_t(i)], reinterpret_cast<DevCounters*>(r->work), r->plan,
+                          pa[size_t(i)], gr.tiles, nullptr, 0, nullptr, &hpk[n_pk], nullptr);
+        ++n_pk;
+        ++gr.count;
+        gr.tiles += uint64_t((r->sc.n + 127) / 128);
+      }
+      if (gr.count) pgroups.push_back(gr);
+    }
+  int n_se[2] = {0, 0};
+  size_t chunks[2] = {0, 0};
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < K; ++i) {
+      const Req* r = g[size_t(i)];
+      if ((r->plan.tp.strategy == CG_STRATEGY_SORTED) != (pass == 1)) continue;
+      scene_small_descs(ws[size_t(i)], reinterpret_cast<DevCounters*>(r->work), r->plan,
+                        pa[size_t(i)], 0, reinterpret_cast<uint32_t*>(r->result + r->edges_off),
+                        int64_t(r->ecap), nullptr, nullptr, &hse[n_se[0] + n_se[1]]);
+      ++n_se[pass];
+      chunks[pass] += (r->plan.ucap + 31) / 32;
+    }
+  if ((e = cudaMemcpyAsync(block, hb, L.desc_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return undo(e, "uploading the group's descriptors");
+  const SegClear* dclr = reinterpret_cast<const SegClear*>(block + L.clr);
+  const SegPackScene* dpk = reinterpret_cast<const SegPackScene*>(block + L.pk);
+  const BatchSortScene* dsort = reinterpret_cast<const BatchSortScene*>(block + L.sort);
+  const SegSearchScene* dse = reinterpret_cast<const SegSearchScene*>(block + L.se);
+  const PublishEntry* dpub = reinterpret_cast<const PublishEntry*>(block + L.pub);
+  unsigned int* dscr = reinterpret_cast<unsigned int*>(block + L.scr);
+  if ((e = launch_clear_seg(dclr, K, st)) != cudaSuccess) return undo(e, "clearing");
+  for (const PackGroup& gr : pgroups)
+    if ((e = launch_pack_insert_seg(dpk + gr.first, gr.count, gr.tiles, gr.d, gr.nch, st)) !=
+        cudaSuccess)
+      return undo(e, "sign vectors + dedup");
+  if ((e = batch_sort(dsort, K, L.sort_cap, L.sort_seg, block + L.bs, st)) != cudaSuccess)
+    return undo(e, "sorting cells");
+  if (n_se[0] && (e = launch_neighbors_seg_small(dse, n_se[0], chunks[0], false, dscr, st)) !=
+                     cudaSuccess)
+    return undo(e, "neighbour search");
+  if (n_se[1] && (e = launch_neighbors_seg_small(dse + n_se[0], n_se[1], chunks[1], true,
+                                                 dscr + (K + 2), st)) != cudaSuccess)
+    return undo(e, "neighbour search");
+  if ((e = launch_publish_group(dpub, K, st)) != cudaSuccess) return undo(e, "completion flags");
+  return CG_OK;
+}
+
+
 // Settles a request whose stream work has finished. No lock held on entry.
 void finish_request(cg_server* s, Req* r) {
   const DevCounters h = s->hctr[r->slot];
@@ -275,6 +468,14 @@ void finish_request(cg_server* s, Req* r) {
     arena_free(s, work, work_bytes);
     arena_free(s, result, result_bytes);
     s->in_use -= freed_work + freed_result;
+    if (Group* G = r->group) {
+      r->group = nullptr;
+      if (--G->pending == 0) {
+        arena_free(s, G->block, G->bytes);
+        s->in_use -= G->bytes;
+        delete G;
+      }
+    }
     s->workers[size_t(r->worker)].free_slots.push_back(r->slot);
     --s->workers[size_t(r->worker)].running;
     r->slot = -1;
@@ -303,7 +504,8 @@ void finish_request(cg_server* s, Req* r) {
 // True when the head of the queue can be admitted now by scheduler k (or must
 // be failed).
 bool admissible(const cg_server* s, int k) {
-  if (s->queue.empty() || s->workers[size_t(k)].free_slots.empty()) return false;
+  const cg_server::Worker& me = s->workers[size_t(k)];
+  if (s->queue.empty() || me.free_slots.empty()) return false;
   if (s->blocked_gen == s->free_gen) return false;  // the arena had no room; no free since
   const Req* r = s->queue.front();
   const size_t need = r->work_bytes + r->result_bytes;
@@ -321,6 +523,95 @@ bool admissible(const cg_server* s, int k) {
 void scheduler(cg_server* s, int k) {
   cudaSetDevice(s->device);
   cg_server::Worker& me = s->workers[size_t(k)];
+  // An admitted request whose start failed part-way (after its stream has
+  // drained): blocks and slot back, request failed. No lock held on entry.
+  auto fail_started = [&](Req* r, cg_status st, const std::string& err) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    arena_free(s, r->work, r->work_bytes);
+    arena_free(s, r->result, r->result_bytes);
+    r->work = r->result = nullptr;
+    s->in_use -= r->work_bytes + r->result_bytes;
+    me.free_slots.push_back(r->slot);
+    --me.running;
+    r->slot = -1;
+    --s->running;
+    r->state = CG_REQ_FAILED;
+    r->status = st;
+    r->err = err;
+    ++s->failed;
+    s->cv_done.notify_all();
+  };
+  auto start_one = [&](Req* r) {
+    const cg_status st = start_request(s, r);
+    if (st == CG_OK) {
+      me.active.push_back(r);
+      return;
+    }
+    // Part of the request may have been enqueued: its blocks are reused only
+    // after that work has drained.
+    const std::string err = cg_last_error();
+    cudaStreamSynchronize(s->streams[size_t(r->slot)]);
+    cudaGetLastError();
+    fail_started(r, st, err);
+  };
+  // Admitted requests for the segmented kernels, started together (or one
+  // by one when fewer than kGroupMin, or when the arena has no room for the
+  // group's block).
+  std::vector<Req*> pend;
+  auto flush_group = [&]() {
+    if (pend.empty()) return;
+    if (int(pend.size()) >= kGroupMin) {
+      const GroupLayout L = group_layout(pend);
+      char* blk = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (arena_alloc(s, L.bytes, &blk)) {
+          s->in_use += L.bytes;
+          if (s->in_use > s->peak) s->peak = s->in_use;
+        } else {
+          blk = nullptr;
+        }
+      }
+      if (blk) {
+        Group* G = new Group();
+        G->block = blk;
+        G->bytes = L.bytes;
+        G->pending = int(pend.size());
+        for (Req* r : pend) {
+          r->group = G;
+          r->run_slot = pend[0]->slot;
+        }
+        const cg_status st = start_group(s, pend, blk, L, G->staging);
+        if (st == CG_OK) {
+          for (Req* r : pend) me.active.push_back(r);
+          {
+            std::lock_guard<std::mutex> lk(s->mu);
+            ++s->groups;
+            s->grouped += int64_t(pend.size());
+          }
+          pend.clear();
+          return;
+        }
+        const std::string err = cg_last_error();
+        cudaStreamSynchronize(s->streams[size_t(pend[0]->slot)]);
+        cudaGetLastError();
+        for (Req* r : pend) {
+          r->group = nullptr;
+          fail_started(r, st, err);
+        }
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          arena_free(s, blk, L.bytes);
+          s->in_use -= L.bytes;
+        }
+        delete G;
+        pend.clear();
+        return;
+      }
+    }
+    for (Req* r : pend) start_one(r);
+    pend.clear();
+  };
   Clock::time_point last_progress = Clock::now();
   for (;;) {
     std::vector<Req*> fin;
@@ -330,7 +621,7 @@ void scheduler(cg_server* s, int k) {
       Req* r = me.active[q];
       if (__atomic_load_n(&s->hflag[r->slot], __ATOMIC_ACQUIRE) != r->seq) {
         if (check_streams) {
-          const cudaError_t e = cudaStreamQuery(s->streams[size_t(r->slot)]);
+          const cudaError_t e = cudaStreamQuery(s->streams[size_t(r->run_slot)]);
           if (e != cudaSuccess && e != cudaErrorNotReady) r->stream_error = true;
         }
         if (!r->stream_error) {
@@ -399,31 +690,16 @@ void scheduler(cg_server* s, int k) {
         r->state = CG_REQ_RUNNING;
         if (r->t_admit < 0) r->t_admit = now_us(s);
       }
-      const cg_status st = start_request(s, r);
-      if (st == CG_OK) {
-        me.active.push_back(r);
-        admitted = true;
+      r->run_slot = r->slot;
+      admitted = true;
+      if (group_eligible(r)) {
+        pend.push_back(r);
+        if (int(pend.size()) >= kGroupMax) flush_group();
         continue;
       }
-      // Part of the request may have been enqueued: its blocks are reused only
-      // after that work has drained.
-      cudaStreamSynchronize(s->streams[size_t(r->slot)]);
-      cudaGetLastError();
-      std::lock_guard<std::mutex> lk(s->mu);
-      arena_free(s, r->work, r->work_bytes);
-      arena_free(s, r->result, r->result_bytes);
-      r->work = r->result = nullptr;
-      s->in_use -= r->work_bytes + r->result_bytes;
-      me.free_slots.push_back(r->slot);
-      --me.running;
-      r->slot = -1;
-      --s->running;
-      r->state = CG_REQ_FAILED;
-      r->status = st;
-      r->err = cg_last_error();
-      ++s->failed;
-      s->cv_done.notify_all();
+      start_one(r);
     }
+    flush_group();
     if (!fin.empty() || admitted) continue;
     std::unique_lock<std::mutex> lk(s->mu);
     auto ready = [&] { return (!s->stop && admissible(s, k)) || (s->stop && me.active.empty()); };
@@ -491,8 +767,9 @@ cg_status cg_server_create(int device, size_t hbm_budget_bytes, int max_inflight
     s->streams.push_back(st);
   }
   s->slot_seq.assign(size_t(max_inflight), 0u);
-  for (int k = max_inflight - 1; k >= 0; --k)
+  for (int k = max_inflight - 1; k >= 0; --k) {
     s->workers[size_t(k % n_threads)].free_slots.push_back(k);
+  }
   if ((e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(e, "creating the copy stream");
   if ((e = cudaHostAlloc(reinterpret_cast<void**>(&s->hctr),
@@ -684,6 +961,8 @@ cg_status cg_server_get_stats(cg_server* srv, cg_server_stats* out) {
   out->bytes_in_use = srv->in_use;
   out->peak_bytes = srv->peak;
   out->max_running = srv->max_running;
+  out->groups = srv->groups;
+  out->grouped = srv->grouped;
   return CG_OK;
 }
 

@@ -233,3 +233,34 @@ def test_pinned_host_inputs(dev, wanted):
         for i, (t, sc) in enumerate(zip(ts, scenes)):
             assert srv.wait(t, 60.0)
             _check(srv, t, sc, wanted(("p", i), sc))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("where", ["host", "pinned", "device"])
+def test_requests_started_together_match_the_oracle(dev, wanted, where):
+    """Many l <= 64 scenes at once: the scheduler starts the requests it admits
+    in one pass together through the segmented kernels (one sign + insert
+    launch, one sort and one search for all of them). Every result is the
+    oracle's, whether the inputs are pageable or pinned host arrays (copied
+    into each request's block) or device arrays."""
+    spec = inputs.scene_batch_spec(n_scenes=48, seed=31, ell_hi=64, n_hi=30_000)
+    scenes = [inputs.batch_scene(spec, s) for s in range(48)]
+    if where == "host":
+        args = [(s.pts, s.a, s.b) for s in scenes]
+    elif where == "pinned":
+        pin = lambda x: torch.from_numpy(x).pin_memory().numpy()
+        args = [(pin(s.pts), pin(s.a), pin(s.b)) for s in scenes]
+    else:
+        args = [tuple(torch.from_numpy(x).to(dev) for x in (s.pts, s.a, s.b)) for s in scenes]
+        torch.cuda.synchronize()
+    with cellgraph.Server(0, hbm_budget_bytes=4 << 30, max_inflight=64) as srv:
+        for _ in range(2):
+            ts = [srv.submit(*a) for a in args]
+            for i, (t, sc) in enumerate(zip(ts, scenes)):
+                assert srv.wait(t, 120.0)
+                _check(srv, t, sc, wanted(("g", i), sc))
+                srv.release(t)
+        st = srv.stats()
+        assert st["failed"] == 0
+        assert st["grouped"] >= 4 and st["groups"] >= 1, st
+        assert st["bytes_in_use"] == 0
