@@ -1169,6 +1169,45 @@ void scene_small_descs(char* ws, DevCounters* ctr, const ScenePlan& plan, const 
                                uint32_t(plan.ucap)};
 }
 
+// Descriptors of a batch-sorted scene of l > 64 (plan.single) for the
+// segmented clear, sign (its vectors written to its keys64) and insert; p0 is
+// its first point in the insert launch's numbering.
+void scene_wide_descs(char* ws, DevCounters* ctr, const ScenePlan& plan, const PackArgs& pa,
+                      uint64_t tile0, uint64_t p0, SegClear* clr, SegPackScene* pk,
+                      SegInsertWide* ins) {
+  Carve c{ws};
+  SmallWs w{};
+  WideWs ww{};
+  PivotWs pw{};
+  TreeWs tw{};
+  carve_scene(c, plan, ctr, &w, &ww, &pw, &tw);
+  const bool own = plan.tp.strategy == CG_STRATEGY_PIVOT ||
+                   plan.tp.strategy == CG_STRATEGY_HALVES || plan.tp.strategy == CG_STRATEGY_TREE;
+  if (clr) {
+    // As enqueue_scene clears a single-pass wide scene: the table and the
+    // counters, and for its own edge kernel the fingerprint table and the
+    // look-back words too.
+    SegClear z{ww.slots, nullptr, plan.cap, nullptr, 0, ctr};
+    if (!own) {
+      z.status = ww.status;
+      z.n_status = ne_status_words(plan.ucap);
+      z.keys2 = ww.slots2;
+      z.cap2 = plan.cap;
+    }
+    *clr = z;
+  }
+  if (pk) {
+    SegPackScene z{pa.pts, pa.n, pa.a, pa.b, pa.ell, SmallTable{}, tile0};
+    z.keys64 = ww.keys64;
+    *pk = z;
+  }
+  if (ins)
+    *ins = SegInsertWide{ww.keys64, pa.n, (plan.ell + 63) / 64,
+                         WideTable{ww.slots, uint32_t(plan.cap - 1), ww.idx0,
+                                   uint32_t(plan.ucap), ctr},
+                         p0};
+}
+
 SegSortScene scene_keysort_desc(char* ws, DevCounters* ctr, const ScenePlan& plan) {
   Carve c{ws};
   SmallWs w{};
@@ -1749,6 +1788,7 @@ struct BatchScene {
   bool keysort;  // PIVOT / HALVES: its (key, cell) pairs sorted with the others' (seg_sort)
   bool seg_insert;  // l <= 64, fp32 sign kernel: cleared and packed by the segmented kernels
   bool seg_search;  // l <= 64, HASH or SORTED: searched by the segmented edge kernel
+  bool seg_wide;    // 64 < l <= 256, d <= 3: cleared, packed and inserted by the segmented kernels
 };
 
 }  // namespace
@@ -1899,6 +1939,7 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     m.take<SegClear>(size_t(S));
     m.take<SegPackScene>(size_t(S));
     m.take<SegSearchScene>(size_t(S));
+    m.take<SegInsertWide>(size_t(S));
     m.take<unsigned int>(2 * (size_t(S) + 2));
     size_t sort_cap = 0, ks_cap = 0, sort_seg = 1024;
     int n_sorted = 0, n_ks = 0, ks_bits = 1;
@@ -1937,6 +1978,8 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       b.seg_insert = b.sorted && b.plan.small && !env_tc && b.plan.tp.sign_kernel != 1;
       b.seg_search = b.sorted && b.plan.small && (b.plan.tp.strategy == CG_STRATEGY_HASH ||
                                                   b.plan.tp.strategy == CG_STRATEGY_SORTED);
+      b.seg_wide = b.sorted && !b.plan.small && b.plan.single && sc.n > 0 && sc.d <= 3 &&
+                   b.w >= 2 && b.w <= 4;
       if (b.keysort) {
         ks_cap += b.plan.ucap;
         ++n_ks;
@@ -1962,7 +2005,8 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
                               size_t(S) * sizeof(BatchSortScene) + 256 +
                               size_t(S) * sizeof(SegSortScene) + 256 +
                               size_t(S) * (sizeof(SegClear) + sizeof(SegPackScene) +
-                                           sizeof(SegSearchScene)) + 3 * 256;
+                                           sizeof(SegSearchScene) + sizeof(SegInsertWide)) +
+                              4 * 256;
     cg_status st = ensure_batch_resources(ctx, m.off + 256, host_bytes);
     if (st) return st;
     // The batch runs on the context's own stream, after the caller's work.
@@ -1981,6 +2025,7 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
     SegClear* dclr = c.take<SegClear>(size_t(S));
     SegPackScene* dpk = c.take<SegPackScene>(size_t(S));
     SegSearchScene* dse = c.take<SegSearchScene>(size_t(S));
+    SegInsertWide* dins = c.take<SegInsertWide>(size_t(S));
     unsigned int* dse_scratch = c.take<unsigned int>(2 * (size_t(S) + 2));
     char* hb = static_cast<char*>(ctx->bhost);
     BatchEntry* htab = reinterpret_cast<BatchEntry*>(hb);
@@ -2002,6 +2047,8 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
         (reinterpret_cast<uintptr_t>(hclr + S) + 255) & ~uintptr_t(255));
     SegSearchScene* hse = reinterpret_cast<SegSearchScene*>(
         (reinterpret_cast<uintptr_t>(hpk + S) + 255) & ~uintptr_t(255));
+    SegInsertWide* hins = reinterpret_cast<SegInsertWide*>(
+        (reinterpret_cast<uintptr_t>(hse + S) + 255) & ~uintptr_t(255));
     // Segmented small scenes: clears; packs grouped by (d, constraint chunks),
     // each group numbering its 128-point tiles from 0; searches, HASH first.
     struct PackGroup {
@@ -2028,6 +2075,31 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
           }
         }
         if (gr.count) pgroups.push_back(gr);
+      }
+    // Segmented wide scenes (64 < l <= 256), grouped by (d, words): per group
+    // a clear, a sign launch and an insert launch (which numbers the group's
+    // points from 0), the groups on different worker streams.
+    struct WideGroup {
+      int d, w, first, count, clr_first, ins_first;
+      uint64_t tiles, points;
+    };
+    std::vector<WideGroup> wgroups;
+    int n_ins = 0;
+    for (int d = 1; d <= 3; ++d)
+      for (int w = 2; w <= 4; ++w) {
+        WideGroup gr{d, w, n_pk, 0, n_clr, n_ins, 0, 0};
+        for (int i = 0; i < S; ++i) {
+          const BatchScene& b = bs[size_t(i)];
+          const cg_scene& sc = scenes[i];
+          if (!b.seg_wide || sc.d != d || b.w != w) continue;
+          const PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
+          scene_wide_descs(base + b.ws_off, ctrs + i, b.plan, pa, gr.tiles, gr.points,
+                           &hclr[n_clr++], &hpk[n_pk++], &hins[n_ins++]);
+          ++gr.count;
+          gr.tiles += uint64_t((sc.n + 127) / 128);
+          gr.points += uint64_t(sc.n);
+        }
+        if (gr.count) wgroups.push_back(gr);
       }
     for (int pass = 0; pass < 2; ++pass)
       for (int i = 0; i < S; ++i) {
@@ -2097,6 +2169,10 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
         CG_CUDA(cudaMemcpyAsync(dpk, hpk, size_t(n_pk) * sizeof(SegPackScene),
                                 cudaMemcpyHostToDevice, s0),
                 "uploading the sign table");
+      if (n_ins)
+        CG_CUDA(cudaMemcpyAsync(dins, hins, size_t(n_ins) * sizeof(SegInsertWide),
+                                cudaMemcpyHostToDevice, s0),
+                "uploading the insert table");
       if (n_se_hash + n_se_sorted)
         CG_CUDA(cudaMemcpyAsync(dse, hse, size_t(n_se_hash + n_se_sorted) * sizeof(SegSearchScene),
                                 cudaMemcpyHostToDevice, s0),
@@ -2119,15 +2195,28 @@ extern "C" cg_status cg_build_batch(cg_ctx* ctx, const cg_scene* scenes, int n_s
       // Up to the dedup insert (whole builds for the scenes not sorted
       // together), then one sort of every other scene's distinct vectors,
       // then their neighbour searches. The scenes of l <= 64 are cleared and
-      // packed by a few segmented launches on the batch stream meanwhile.
-      if (n_clr) CG_CUDA(launch_clear_seg(dclr, n_clr, s0), "clearing small scenes");
+      // packed by a few segmented launches on the batch stream meanwhile, and
+      // each group of segmented wide scenes is cleared, packed and inserted
+      // on a worker stream of its own, so that these chains overlap.
+      const int n_clr_small = n_clr - n_ins;
+      if (n_clr_small)
+        CG_CUDA(launch_clear_seg(dclr, n_clr_small, s0), "clearing small scenes");
       for (const PackGroup& gr : pgroups)
         CG_CUDA(launch_pack_insert_seg(dpk + gr.first, gr.count, gr.tiles, gr.d, gr.nch, s0),
                 "sign vectors + dedup (small scenes)");
+      for (size_t g = 0; g < wgroups.size(); ++g) {
+        const WideGroup& gr = wgroups[g];
+        cudaStream_t ws = ctx->workers.empty() ? s0 : ctx->workers[g % ctx->workers.size()];
+        CG_CUDA(launch_clear_seg(dclr + gr.clr_first, gr.count, ws), "clearing wide scenes");
+        CG_CUDA(launch_pack_store_seg(dpk + gr.first, gr.count, gr.tiles, gr.d, gr.w, ws),
+                "sign vectors (wide scenes)");
+        CG_CUDA(launch_insert_wide_seg(dins + gr.ins_first, gr.count, gr.points, ws),
+                "dedup insert (wide scenes)");
+      }
       for (int i : order) {
         const cg_scene& sc = scenes[i];
         const BatchScene& b = bs[size_t(i)];
-        if (b.seg_insert) continue;
+        if (b.seg_insert || b.seg_wide) continue;
         PackArgs pa{sc.pts, sc.n, sc.d, sc.a, sc.b, sc.ell};
         st2 = enqueue_scene(nullptr, base + b.ws_off, ctrs + i, b.plan, pa, 64, base + b.cells_off,
                             int64_t(b.plan.ucap), reinterpret_cast<uint32_t*>(base + b.edges_off),

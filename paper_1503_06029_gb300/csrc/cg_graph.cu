@@ -502,8 +502,9 @@ __global__ void __launch_bounds__(1024) clear_seg(const SegClear* __restrict__ s
   if (threadIdx.x < sizeof(DevCounters) / 4) reinterpret_cast<uint32_t*>(z.ctr)[threadIdx.x] = 0;
   for (size_t i = threadIdx.x; i < z.cap; i += blockDim.x) {
     z.keys[i] = kEmpty;
-    z.vals[i] = 0u;
+    if (z.vals) z.vals[i] = 0u;
   }
+  for (size_t i = threadIdx.x; i < z.cap2; i += blockDim.x) z.keys2[i] = kEmpty;
   for (size_t i = threadIdx.x; i < z.n_status; i += blockDim.x) z.status[i] = 0ull;
 }
 
@@ -566,6 +567,24 @@ __global__ void insert_wide(const uint64_t* __restrict__ keys, int64_t n, int w,
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n;
        p += int64_t(gridDim.x) * blockDim.x)
     insert_row(keys, w, t, p, keys + p * w);
+}
+
+// The inserts of many scenes: point g of the batch numbering belongs to the
+// last scene whose p0 is <= g (binary search over the scene table).
+__global__ void insert_wide_seg(const SegInsertWide* __restrict__ sc, int n_scenes,
+                                uint64_t total) {
+  for (uint64_t g = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; g < total;
+       g += uint64_t(gridDim.x) * blockDim.x) {
+    int lo = 0, hi = n_scenes - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sc[mid].p0 <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const SegInsertWide& z = sc[lo];
+    const int64_t p = int64_t(g - z.p0);
+    if (p < z.n) insert_row(z.keys64, z.w, z.t, p, z.keys64 + p * z.w);
+  }
 }
 
 // Rows idx[0 .. U) of keys, in that order, to out (nothing when out_cap >= 0
@@ -1137,6 +1156,14 @@ cudaError_t launch_neighbors_seg_small(const SegSearchScene* scenes, int n_scene
                                                         wait_limit(kSpinLimit));
   count_launch(2);
   return cudaGetLastError();
+}
+
+cudaError_t launch_insert_wide_seg(const SegInsertWide* scenes, int n_scenes,
+                                   uint64_t total_points, cudaStream_t s) {
+  if (n_scenes <= 0 || total_points == 0) return cudaSuccess;
+  insert_wide_seg<<<grid_for(size_t(total_points), kThreads), kThreads, 0, s>>>(
+      scenes, n_scenes, total_points);
+  return finish(0);
 }
 
 cudaError_t launch_clear_seg(const SegClear* scenes, int n_scenes, cudaStream_t s) {

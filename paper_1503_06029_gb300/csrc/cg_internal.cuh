@@ -152,9 +152,14 @@ struct SegPackScene {
   int ell;
   SmallTable t;
   uint64_t tile0;
+  uint64_t* keys64 = nullptr;  // 64 < l <= 256: the vectors are written here instead
 };
 cudaError_t launch_pack_insert_seg(const SegPackScene* scenes, int n_scenes, uint64_t total_tiles,
                                    int d, int nch, cudaStream_t s);
+// Many scenes of 64 < l <= 256 (W = w64 = 2..4 words) and d <= 3 in one
+// launch: each scene's sign vectors written to its keys64 (W words a point).
+cudaError_t launch_pack_store_seg(const SegPackScene* scenes, int n_scenes, uint64_t total_tiles,
+                                  int d, int w64, cudaStream_t s);
 // Same on the tensor cores (cg_pack_tc.cu): l <= 64, d <= 4; tiles outside the
 // exact-split ranges are evaluated in fp32 with exact re-evaluation.
 // spill_tiles: ceil(n / 128) words of scratch.
@@ -413,11 +418,13 @@ cudaError_t launch_neighbors_seg_small(const SegSearchScene* scenes, int n_scene
 // Batches: the clears of many l <= 64 scenes in one launch (one block each).
 struct SegClear {
   uint64_t* keys;
-  uint32_t* vals;
+  uint32_t* vals;  // nullable
   size_t cap;
   unsigned long long* status;
   size_t n_status;
   DevCounters* ctr;
+  uint64_t* keys2 = nullptr;  // a second table (kEmpty), cap2 slots
+  size_t cap2 = 0;
 };
 cudaError_t launch_clear_seg(const SegClear* scenes, int n_scenes, cudaStream_t s);
 
@@ -485,6 +492,18 @@ struct WideTable {
 };
 cudaError_t launch_insert_wide(const uint64_t* keys, int64_t n, int w64, const WideTable& t,
                                cudaStream_t s);
+// Batches: the dedup inserts of many scenes of l > 64 in one launch (their
+// vectors written by launch_pack_store_seg); p0 numbers the points of all
+// scenes in order.
+struct SegInsertWide {
+  const uint64_t* keys64;
+  int64_t n;
+  int w;
+  WideTable t;
+  uint64_t p0;
+};
+cudaError_t launch_insert_wide_seg(const SegInsertWide* scenes, int n_scenes,
+                                   uint64_t total_points, cudaStream_t s);
 // Sort representatives by value: idx0/idx1 permuted, kw0/kw1 word scratch.
 cudaError_t sort_wide(const uint64_t* keys, int w64, int ell, uint32_t* idx0, uint32_t* idx1,
                       uint64_t* kw0, uint64_t* kw1, const unsigned int* n_dev, size_t max_n,

@@ -29,6 +29,8 @@
 // visited from the highest to the lowest index of the chunk), which yields the
 // complement of the vector; padding constraints (i >= l) evaluate to -4 and so
 // produce 0 bits.
+#include <type_traits>
+
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -433,7 +435,8 @@ struct FastInsert {
 // Uncertain chunks are settled exactly by the whole warp (call from all lanes).
 template <int D, int NCH, int P, bool F2, int UJ>
 __device__ __forceinline__ void eval_tile(const PackArgs& pa, const float4* cf, int64_t p0,
-                                          const int32_t (&pi)[P][D], uint64_t (&key)[P]) {
+                                          const int32_t (&pi)[P][D], uint64_t (&key)[P],
+                                          int c0 = 0) {
   constexpr int R = F2 ? 2 : 1;
   constexpr int kQ = Coef<D, R>::kQuads;
   const int lane = threadIdx.x & 31;
@@ -454,7 +457,7 @@ __device__ __forceinline__ void eval_tile(const PackArgs& pa, const float4* cf, 
 #pragma unroll
     for (int q = 0; q < P; ++q) w[q] = 0;
     uint32_t cert = 0xffffffffu;
-    const float4* cc = cf + c * 32 * kQ;
+    const float4* cc = cf + (c0 + c) * 32 * kQ;
 #pragma unroll UJ
     for (int j = 31; j >= 0; --j) {
       float4 q4[kQ];
@@ -494,7 +497,8 @@ __device__ __forceinline__ void eval_tile(const PackArgs& pa, const float4* cf, 
         }
       }
     }
-    settle_uncertain<D, P, kQ, R>(pa, cc, c, p0 - int64_t(lane) * P, !(cert & 0x40000000u), w);
+    settle_uncertain<D, P, kQ, R>(pa, cc, c0 + c, p0 - int64_t(lane) * P,
+                                  !(cert & 0x40000000u), w);
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       if (c == 0) key[q] = ~w[q];
@@ -679,13 +683,15 @@ cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
 // only moves forward), reads the 128 points coalesced, and rebuilds its
 // private constraint rows when the scene changes or the tile's coordinates
 // exceed the bound the rows were built for. Evaluation and insertion are the
-// single-scene kernel's (eval_tile, FastInsert).
-template <int D, int NCH>
+// single-scene kernel's (eval_tile, FastInsert). With W > 0 (scenes of
+// 64 < l <= 64 W) the W words of each vector are evaluated two chunks at a
+// time and written to the scene's keys64 instead of inserted.
+template <int D, int NCH, int W = 0>
 __global__ void __launch_bounds__(kFThreads)
     pack_seg_kernel(const SegPackScene* __restrict__ sc, int n_scenes, uint64_t total_tiles) {
   constexpr int P = 4;
   constexpr int kQ = Coef<D, 1>::kQuads;
-  constexpr int kRows = NCH * 32;
+  constexpr int kRows = (W > 0 ? 2 * W : NCH) * 32;
   constexpr int kWarpPts = 32 * P;
   __shared__ float4 rows_all[kFWarps][kRows * kQ];
   __shared__ int4 stage_all[kFWarps][32 * (P * D / 4)];
@@ -740,15 +746,25 @@ __global__ void __launch_bounds__(kFThreads)
     }
     const int64_t p0 = wp0 + int64_t(lane) * P;
     uint64_t key[P];
-    eval_tile<D, NCH, P, false, 32>(pa, rows, p0, pi, key);
-    FastInsert{S.t}.template finish<P>(p0, S.n, key);
+    if (W == 0) {
+      eval_tile<D, NCH, P, false, 32>(pa, rows, p0, pi, key);
+      FastInsert{S.t}.template finish<P>(p0, S.n, key);
+    } else {
+#pragma unroll 1
+      for (int q = 0; q < W; ++q) {
+        eval_tile<D, 2, P, false, 32>(pa, rows, p0, pi, key, 2 * q);
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+          if (p0 + k < S.n) S.keys64[uint64_t(p0 + k) * W + q] = key[k];
+      }
+    }
   }
 }
 
-template <int D, int NCH>
+template <int D, int NCH, int W = 0>
 cudaError_t launch_seg_dn(const SegPackScene* scenes, int n_scenes, uint64_t total_tiles,
                           cudaStream_t s) {
-  auto kern = pack_seg_kernel<D, NCH>;
+  auto kern = pack_seg_kernel<D, NCH, W>;
   int per_sm = 0;
   cudaError_t err = blocks_per_sm(reinterpret_cast<const void*>(kern), kFThreads, 0, &per_sm);
   if (err != cudaSuccess) return err;
@@ -841,6 +857,26 @@ cudaError_t launch_pack_insert_seg(const SegPackScene* scenes, int n_scenes, uin
                             : launch_seg_dn<3, 1>(scenes, n_scenes, total_tiles, s);
     case 4: return nch == 2 ? launch_seg_dn<4, 2>(scenes, n_scenes, total_tiles, s)
                             : launch_seg_dn<4, 1>(scenes, n_scenes, total_tiles, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pack_store_seg(const SegPackScene* scenes, int n_scenes, uint64_t total_tiles,
+                                  int d, int w64, cudaStream_t s) {
+  if (n_scenes <= 0 || total_tiles == 0) return cudaSuccess;
+  auto by_w = [&](auto dtag) -> cudaError_t {
+    constexpr int D = decltype(dtag)::value;
+    switch (w64) {
+      case 2: return launch_seg_dn<D, 2, 2>(scenes, n_scenes, total_tiles, s);
+      case 3: return launch_seg_dn<D, 2, 3>(scenes, n_scenes, total_tiles, s);
+      case 4: return launch_seg_dn<D, 2, 4>(scenes, n_scenes, total_tiles, s);
+      default: return cudaErrorInvalidValue;
+    }
+  };
+  switch (d) {
+    case 1: return by_w(std::integral_constant<int, 1>{});
+    case 2: return by_w(std::integral_constant<int, 2>{});
+    case 3: return by_w(std::integral_constant<int, 3>{});
     default: return cudaErrorInvalidValue;
   }
 }
