@@ -724,6 +724,14 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
+    # Batch and serving first: the server's host threads measured slower (and
+    # more variable) after the long-vector section had run in the process.
+    if not args.no_batch:
+        line["batch"] = batch_compare(ctx, dev, max(3, args.steps // 2))
+        if not args.no_serve:
+            cap = len(inputs_spec_n()) / (line["batch"]["batched"]["ms_per_batch"] * 1e-3)
+            line["serve"] = serve_measure(dev, cap, n_requests=args.serve_requests,
+                                          tuned_ctx=ctx)
     if not args.no_chains:
         line["chains"] = chains_measure(dev, max(3, args.steps // 4),
                                         tuple(args.chains_strategies.split(",")))
@@ -731,12 +739,6 @@ def run_ours(args):
         line["bfs"] = bfs_measure(ctx, dev, max(5, args.steps // 2))
     if not args.no_quadric:
         line["quadric"] = quadric_measure(dev, max(5, args.steps // 2))
-    if not args.no_batch:
-        line["batch"] = batch_compare(ctx, dev, max(3, args.steps // 2))
-        if not args.no_serve:
-            cap = len(inputs_spec_n()) / (line["batch"]["batched"]["ms_per_batch"] * 1e-3)
-            line["serve"] = serve_measure(dev, cap, n_requests=args.serve_requests,
-                                          tuned_ctx=ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     ctx.close()
