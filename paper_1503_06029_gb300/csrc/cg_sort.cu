@@ -608,6 +608,8 @@ constexpr uint32_t kPad = 0xffffffffu;
 struct RowOrder {
   using Tag = uint32_t;  // row number
   static constexpr int kItems = 8;
+  static constexpr bool kPadAware = false;
+  __device__ __forceinline__ static bool is_pad(const Tag&) { return false; }
   const uint64_t* rows;
   int w;
   int ell;
@@ -642,6 +644,11 @@ struct BatchOrder {
   const ulonglong2* keys_in;
   const uint2* tags_in;
   __device__ __forceinline__ static Tag pad() { return make_uint2(kPad, kPad); }
+  // Each scene's items sit at the front of its segment and padding after
+  // them, in both buffers and after every pass: a tile or merge block whose
+  // first position holds padding is all padding and has nothing to do.
+  static constexpr bool kPadAware = true;
+  __device__ __forceinline__ static bool is_pad(const Tag& t) { return t.x == kPad; }
   __device__ __forceinline__ void load(uint32_t g, ulonglong2* k, Tag* t) const {
     *k = keys_in[g];
     *t = tags_in[g];
@@ -687,6 +694,10 @@ __global__ void __launch_bounds__(kMThreads)
   const uint32_t n = min(*n_dev, max_n);
   const uint32_t base = blockIdx.x * kTile;
   if (base >= n) return;
+  if constexpr (Ord::kPadAware) {
+    // Sorted in place (the input is kout/tout): a padding tile stays as it is.
+    if (Ord::is_pad(tout[base])) return;
+  }
   for (int t = threadIdx.x; t < kTile; t += kMThreads) {
     const uint32_t g = base + t;
     if (g < n) {
@@ -799,6 +810,10 @@ __global__ void __launch_bounds__(kMThreads)
   if (out0 >= n) return;
   // Segmented sort: a segment no larger than the run width is sorted already.
   if (seg_classes && seg_size_at(seg_classes, out0) <= width) return;
+  if constexpr (Ord::kPadAware) {
+    // Padding from here to the end of the tile, and already in kout/iout.
+    if (Ord::is_pad(iin[out0])) return;
+  }
   const uint32_t s0 = (out0 / (2 * width)) * (2 * width);
   const uint32_t a_end = min(s0 + width, n);
   const uint32_t b_end = min(s0 + 2 * width, n);
@@ -1223,8 +1238,12 @@ __global__ void bsort_items(const BatchSortScene* __restrict__ sc, int n, BatchS
                             : top128(c.keys64 + uint64_t(c.idx[i]) * c.w, c.ell);
       w.t0[g] = make_uint2(uint32_t(s), i);
     } else {
-      w.k0[g] = make_ulonglong2(~0ull, ~0ull);  // padding: sorts after every real item
+      // Padding (sorts after every real item), in both buffers: the merge
+      // passes skip the blocks that would only copy it.
+      w.k0[g] = make_ulonglong2(~0ull, ~0ull);
       w.t0[g] = make_uint2(kPad, kPad);
+      w.k1[g] = make_ulonglong2(~0ull, ~0ull);
+      w.t1[g] = make_uint2(kPad, kPad);
     }
   }
 }
