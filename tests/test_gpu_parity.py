@@ -650,6 +650,24 @@ def test_batch_matches_oracle_and_plain(ctx, dev):
         assert torch.equal(pc, c) and torch.equal(pe, e)
 
 
+def test_batch_mixed_dimensions_and_widths(ctx, dev):
+    """Scenes of every dimension and of 1 to 5 words in one batch: those of
+    64 < l <= 256 and d <= 3 take the segmented wide path (one chain per
+    (d, words) group on its own stream), d = 4 and l > 256 their per-scene
+    pipelines, l <= 64 the segmented small path; each equals the oracle."""
+    cases = [(1, 70), (1, 200), (2, 65), (2, 129), (2, 256), (3, 96), (3, 160), (3, 250),
+             (4, 100), (3, 300), (1, 20), (2, 64), (3, 40), (4, 48), (2, 190), (3, 128)]
+    scenes = [inputs.arrangement((7, i), 4_000 + 1_500 * i, d, ell, 1000, 1_000_000, 1000)
+              for i, (d, ell) in enumerate(cases)]
+    dscenes = [(T(s.pts, dev), T(s.a, dev), T(s.b, dev)) for s in scenes]
+    wanted = [oracle.build(sc.pts, sc.a, sc.b, 64) for sc in scenes]
+    for _ in range(3):  # eager, then captured, then replayed
+        got = ctx.build_batch(dscenes)
+        for (want_c, want_e), (c, e) in zip(wanted, got):
+            assert np.array_equal(words_np(c, 64).reshape(want_c.shape), want_c)
+            assert np.array_equal(edges_np(e), want_e)
+
+
 def test_batch_repeated_and_resized(ctx, dev):
     """Repeating a batch gives the same bytes; a degenerate scene whose cell
     count exceeds the first table-size guess is resized and rerun inside the
