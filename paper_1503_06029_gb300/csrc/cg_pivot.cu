@@ -330,6 +330,65 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// The same for cells of 2 .. kKeysStageW words: a warp reads 32 consecutive
+// cells coalesced (lane l takes words l, l + 32, ... of the 32 rows) into
+// shared memory, stride w + 1 words, and lane l then computes cell l's keys
+// from there (a thread reading its own row puts w * 8 bytes between the
+// addresses of consecutive lanes).
+constexpr int kKeysStageW = 16;
+
+__global__ void __launch_bounds__(kThreads)
+    halves_keys_staged(const uint64_t* __restrict__ cells, int w, int s, const DevCounters* ctr,
+                       uint32_t max_n, uint64_t* __restrict__ hkey, uint64_t* __restrict__ fl,
+                       uint64_t* __restrict__ fh, uint64_t* __restrict__ lkey,
+                       uint32_t* __restrict__ idx) {
+  extern __shared__ uint64_t keys_stage[];
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int stride = w + 1;
+  uint64_t* sr = keys_stage + size_t(warp) * 32 * stride;
+  const int da = 32 / w, dq = 32 % w;
+  for (uint64_t r0 = (uint64_t(blockIdx.x) * (kThreads / 32) + warp) * 32; r0 < u;
+       r0 += uint64_t(gridDim.x) * kThreads) {
+    const uint32_t rows = uint32_t(min(uint64_t(32), u - r0));
+    const uint32_t elems = rows * uint32_t(w);
+    const uint64_t* src = cells + r0 * w;
+    int a = lane / w, q = lane - a * w;
+    for (uint32_t e = lane; e < elems; e += 32) {
+      sr[a * stride + q] = __ldg(src + e);
+      a += da;
+      q += dq;
+      if (q >= w) {
+        q -= w;
+        ++a;
+      }
+    }
+    __syncwarp();
+    if (uint32_t(lane) < rows) {
+      const uint64_t* x = sr + lane * stride;
+      uint64_t hh = 0, hl = 0, fa = 0, fb = 0;
+      for (int k = 0; k < w; ++k) {
+        const uint64_t m = low_mask(k, s);
+        const uint64_t lo = x[k] & m, hi = x[k] & ~m;
+        const uint64_t salt = 0x9e3779b97f4a7c15ull * uint64_t(k + 1);
+        fa ^= lo;
+        fb ^= hi;
+        hl ^= mix64(lo + salt);
+        hh ^= mix64(hi + salt);
+      }
+      const uint64_t i = r0 + uint64_t(lane);
+      hkey[i] = hh;
+      fl[i] = fa;
+      fh[i] = fb;
+      lkey[i] = hl & 0xffffffffull;
+      idx[i] = uint32_t(i);
+    }
+    __syncwarp();
+  }
+}
+
 // sfh[t] = fh[sidx[t]]: the H fold of the cell at sorted position t.
 __global__ void __launch_bounds__(kThreads)
     halves_gather(const DevCounters* ctr, uint32_t max_n, const uint32_t* __restrict__ sidx,
@@ -577,8 +636,14 @@ cudaError_t launch_halves_keys(const uint64_t* cells, int w64, int ell, const De
                                size_t max_n, uint64_t* hkey, uint64_t* fl, uint64_t* fh,
                                uint64_t* lkey, uint32_t* idx, cudaStream_t s) {
   if (max_n == 0) return cudaSuccess;
-  halves_keys<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(
-      cells, w64, halves_split(ell), ctr, uint32_t(max_n), hkey, fl, fh, lkey, idx);
+  if (w64 >= 2 && w64 <= kKeysStageW) {
+    const size_t smem = size_t(kThreads) * (w64 + 1) * sizeof(uint64_t);
+    halves_keys_staged<<<grid_for((max_n + 31) / 32, kThreads / 32), kThreads, smem, s>>>(
+        cells, w64, halves_split(ell), ctr, uint32_t(max_n), hkey, fl, fh, lkey, idx);
+  } else {
+    halves_keys<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(
+        cells, w64, halves_split(ell), ctr, uint32_t(max_n), hkey, fl, fh, lkey, idx);
+  }
   count_launch();
   return cudaGetLastError();
 }
