@@ -2511,8 +2511,13 @@ extern "C" cg_status cg_ctx_autotune(cg_ctx* ctx, const cg_scene* scenes, int n_
       const size_t k = cand.size();
       for (size_t c = 0; c < k; ++c) cand.push_back({cand[c].strategy, cand[c].pivots, 1});
     }
-    double best = 1e300;
-    cg_tune_params best_p = ctx->tune[b];
+    // Best per sign kernel: the tensor-core one is chosen only when it beats
+    // the best fp32 candidate by more than 10 % (the fp32 kernel is also what
+    // lets batches and served groups take the segmented path, so a
+    // within-noise win of the tensor-core kernel on the tuning scenes cost
+    // far more elsewhere).
+    double best_k[2] = {1e300, 1e300};
+    cg_tune_params best_pk[2] = {ctx->tune[b], ctx->tune[b]};
     // Several scenes are timed the way a batch runs them: one cg_build_batch
     // of the bucket's scenes, replayed from its graph after two warm-up calls
     // (the first sizes the outputs, the second captures), so the choice
@@ -2553,12 +2558,15 @@ extern "C" cg_status cg_ctx_autotune(cg_ctx* ctx, const cg_scene* scenes, int n_
         break;
       }
       const double per = double(ms) / reps;
-      if (per < best) {
-        best = per;
-        best_p = p;
+      const int k = p.sign_kernel == 1 ? 1 : 0;
+      if (per < best_k[k]) {
+        best_k[k] = per;
+        best_pk[k] = p;
       }
     }
-    ctx->tune[b] = best_p;
+    const int pick = best_k[1] < 0.9 * best_k[0] ? 1 : 0;
+    const double best = best_k[pick];
+    ctx->tune[b] = best_pk[pick];
     if (chosen_ms && result == CG_OK) chosen_ms[b] = best;
     cudaStreamSynchronize(s);
     if (tb.cells) cudaFree(tb.cells);
