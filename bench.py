@@ -286,6 +286,11 @@ def batch_compare(ctx, dev, steps: int):
         res = ctx.build_batch(scenes)
     cells = sum(int(c.shape[0]) for c, _ in res)
     edges = sum(int(e.shape[0]) for _, e in res)
+    # Compulsory bytes: each scene's points read once (4 d B each), its cells
+    # (8 W B each) and edges (8 B each) written once.
+    compulsory = sum(4.0 * int(pts.shape[1]) * int(pts.shape[0]) +
+                     8.0 * ((int(a.shape[0]) + 63) // 64) * int(c.shape[0]) + 8.0 * int(e.shape[0])
+                     for (pts, a, _), (c, e) in zip(scenes, res))
     launches0 = cg_launches()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -317,7 +322,9 @@ def batch_compare(ctx, dev, steps: int):
             "points": total, "cells": cells, "edges": edges,
             "oracle_digest_mismatches": int(bad),
             "batched": {"value": total / (batch_ms * 1e-3) / 1e6, "unit": UNIT,
-                        "ms_per_batch": batch_ms, "gpu_launches_per_batch": batch_launches},
+                        "ms_per_batch": batch_ms, "gpu_launches_per_batch": batch_launches,
+                        "compulsory_bytes": compulsory,
+                        "hbm_frac": compulsory / (batch_ms * 1e-3) / 1e9 / _hbm_peak_gbs()},
             "plain": {"value": total / (plain_ms * 1e-3) / 1e6, "unit": UNIT,
                       "ms_per_batch": plain_ms, "calls": len(scenes)},
             "speedup": plain_ms / batch_ms,
@@ -440,10 +447,21 @@ def chains_measure(dev, steps: int, strategies=("hash", "pivot", "tree", "halves
             d_ms += ev[0].elapsed_time(ev[1]) / steps
             n_ms += ev[1].elapsed_time(ev[2]) / steps
         out["cells"], out["edges"] = int(cells.shape[0]), int(edges.shape[0])
+        # Compulsory bytes: the vectors read once, the cells and edges written once.
+        compulsory = 128.0 * n + 128.0 * out["cells"] + 8.0 * out["edges"]
+        out["compulsory_bytes"] = compulsory
         out["strategies"][strat] = {"value": n / ((d_ms + n_ms) * 1e-3) / 1e6, "unit": UNIT,
                                     "ms_per_step": d_ms + n_ms, "dedup_ms": d_ms,
-                                    "neighbors_ms": n_ms}
+                                    "neighbors_ms": n_ms,
+                                    "hbm_frac": compulsory / ((d_ms + n_ms) * 1e-3) / 1e9 /
+                                    _hbm_peak_gbs()}
     return out
+
+
+def _hbm_peak_gbs() -> float:
+    """Measured HBM copy rate (MEASURED_PEAKS.json), GB/s."""
+    peaks, _ = _peaks()
+    return float(peaks.get("hbm_gbs", 6800.0))
 
 
 def _alu_peak_tmacs() -> float:
