@@ -351,7 +351,7 @@ cg_status neighbors_wide_steps(const WideWs& w, int ell, int strategy, uint32_t*
 // pairs of all its scenes at once between parts 1 and 2).
 cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounters* ctr,
                       const PivotWs& p, size_t ucap, uint32_t* edges, int64_t edges_cap,
-                      cudaStream_t s, int strategy, int part = 0) {
+                      cudaStream_t s, int strategy, int part = 0, int64_t adopt_n = -1) {
   if (strategy == CG_STRATEGY_ALLPAIRS) {
     CG_CUDA(launch_pivot_keys(cells, w64, ell, h, ctr, ucap, p.kcell, p.k0, p.i0, s),
             "pivot distances");
@@ -367,7 +367,8 @@ cg_status pivot_steps(const uint64_t* cells, int w64, int ell, int h, DevCounter
     uint64_t* fl = static_cast<uint64_t*>(p.table);
     uint64_t* fh = fl + ucap;
     if (part != 2)
-      CG_CUDA(launch_halves_keys(cells, w64, ell, ctr, ucap, p.kcell, fl, fh, p.k0, p.i0, s),
+      CG_CUDA(launch_halves_keys(cells, w64, ell, ctr, ucap, p.kcell, fl, fh, p.k0, p.i0, s,
+                                 adopt_n),
               "part keys");
     if (part == 1) return CG_OK;
     bool in1 = false;
@@ -992,10 +993,14 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     WideWs w = carve_wide(c, un, cap, un, ell, false, false, false, true);
     CG_CUDA(launch_zero_counters(w.ctr, s), "counters");
     const int w64 = (ell + 63) / 64;
+    // HALVES over a caller's rows of 2..16 words checks them in its key pass.
+    const bool adopt_in_keys = word_bits == 64 && n_cells > 0 &&
+                               strategy == CG_STRATEGY_HALVES && halves_keys_can_adopt(w64);
     if (word_bits == 64 && n_cells > 0) {
       // The search only reads its cells: use the caller's rows in place.
       w.cells = const_cast<uint64_t*>(static_cast<const uint64_t*>(cells));
-      CG_CUDA(launch_adopt_cells(w.cells, n_cells, ell, w.ctr, s), "checking the cells");
+      if (!adopt_in_keys)
+        CG_CUDA(launch_adopt_cells(w.cells, n_cells, ell, w.ctr, s), "checking the cells");
     } else {
       CG_CUDA(launch_load_cells(cells, n_cells, word_bits, ell, w.cells, w.ctr, s),
               "loading cells");
@@ -1004,7 +1009,7 @@ cg_status cg_neighbors_h1(const void* cells, int64_t n_cells, int ell, int word_
     cg_status st;
     if (pivot)
       st = pivot_steps(w.cells, w64, ell, env_pivots(ell), w.ctr, carve_pivot(c, un), un, edges,
-                       edges_cap, s, strategy);
+                       edges_cap, s, strategy, 0, adopt_in_keys ? n_cells : -1);
     else if (tree)
       st = tree_steps(w.cells, w64, ell, w.ctr, carve_treews(c, un, ell), un, edges, edges_cap,
                       s);

@@ -615,9 +615,15 @@ cudaError_t launch_allpairs_edges(const uint64_t* cells, int w64, int ell, int h
 // buffer.
 int halves_split(int ell);
 int halves_sort_bits(int ell);
-cudaError_t launch_halves_keys(const uint64_t* cells, int w64, int ell, const DevCounters* ctr,
+// adopt_n >= 0 (2 <= w64 <= 16 only): cells are a caller's rows used in place;
+// U = adopt_n is written to ctr->n_unique and the rows are checked as
+// launch_adopt_cells checks them, in the same pass.
+cudaError_t launch_halves_keys(const uint64_t* cells, int w64, int ell, DevCounters* ctr,
                                size_t max_n, uint64_t* hkey, uint64_t* fl, uint64_t* fh,
-                               uint64_t* lkey, uint32_t* idx, cudaStream_t s);
+                               uint64_t* lkey, uint32_t* idx, cudaStream_t s,
+                               int64_t adopt_n = -1);
+// Whether launch_halves_keys can check adopted rows of w64 words itself.
+inline bool halves_keys_can_adopt(int w64) { return w64 >= 2 && w64 <= 16; }
 cudaError_t launch_halves_edges(const uint64_t* cells, int w64, int ell, DevCounters* ctr,
                                 size_t max_n, const uint64_t* hkey, const uint64_t* fl,
                                 const uint64_t* fh, const uint64_t* skey, const uint32_t* sidx,

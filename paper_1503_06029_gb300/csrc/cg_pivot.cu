@@ -337,14 +337,20 @@ __global__ void __launch_bounds__(kThreads)
 // addresses of consecutive lanes).
 constexpr int kKeysStageW = 16;
 
+// adopt_n >= 0: the cells are a caller's rows used in place (U = adopt_n);
+// the kernel also sets ctr->n_unique and checks what adopt_cells checks (rows
+// strictly ascending, no bit at or above l), from the rows it has staged.
 __global__ void __launch_bounds__(kThreads)
-    halves_keys_staged(const uint64_t* __restrict__ cells, int w, int s, const DevCounters* ctr,
+    halves_keys_staged(const uint64_t* __restrict__ cells, int w, int s, DevCounters* ctr,
                        uint32_t max_n, uint64_t* __restrict__ hkey, uint64_t* __restrict__ fl,
                        uint64_t* __restrict__ fh, uint64_t* __restrict__ lkey,
-                       uint32_t* __restrict__ idx) {
+                       uint32_t* __restrict__ idx, int64_t adopt_n, int ell) {
   extern __shared__ uint64_t keys_stage[];
   if (ctr->overflow) return;
-  const uint32_t u = min(ctr->n_unique, max_n);
+  const uint32_t u = adopt_n >= 0 ? uint32_t(min(uint64_t(adopt_n), uint64_t(max_n)))
+                                  : min(ctr->n_unique, max_n);
+  if (adopt_n >= 0 && blockIdx.x == 0 && threadIdx.x == 0) ctr->n_unique = uint32_t(adopt_n);
+  const uint64_t high = (ell & 63) ? ~((1ull << (ell & 63)) - 1) : 0ull;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int stride = w + 1;
@@ -368,6 +374,16 @@ __global__ void __launch_bounds__(kThreads)
     __syncwarp();
     if (uint32_t(lane) < rows) {
       const uint64_t* x = sr + lane * stride;
+      if (adopt_n >= 0) {
+        const uint64_t i = r0 + uint64_t(lane);
+        if (x[w - 1] & high) atomicOr(&ctr->error, kErrHighBits);
+        if (i > 0) {
+          const uint64_t* y = lane > 0 ? sr + (lane - 1) * stride : cells + (i - 1) * w;
+          int q = w - 1;
+          while (q > 0 && y[q] == x[q]) --q;
+          if (!(y[q] < x[q])) atomicOr(&ctr->error, kErrUnsorted);
+        }
+      }
       uint64_t hh = 0, hl = 0, fa = 0, fb = 0;
       for (int k = 0; k < w; ++k) {
         const uint64_t m = low_mask(k, s);
@@ -632,14 +648,16 @@ int halves_split(int ell) { return ell / 2; }
 
 int halves_sort_bits(int ell) { return ell <= 64 ? halves_split(ell) : 32; }
 
-cudaError_t launch_halves_keys(const uint64_t* cells, int w64, int ell, const DevCounters* ctr,
+cudaError_t launch_halves_keys(const uint64_t* cells, int w64, int ell, DevCounters* ctr,
                                size_t max_n, uint64_t* hkey, uint64_t* fl, uint64_t* fh,
-                               uint64_t* lkey, uint32_t* idx, cudaStream_t s) {
+                               uint64_t* lkey, uint32_t* idx, cudaStream_t s, int64_t adopt_n) {
   if (max_n == 0) return cudaSuccess;
+  if (adopt_n >= 0 && !(w64 >= 2 && w64 <= kKeysStageW)) return cudaErrorInvalidValue;
   if (w64 >= 2 && w64 <= kKeysStageW) {
     const size_t smem = size_t(kThreads) * (w64 + 1) * sizeof(uint64_t);
     halves_keys_staged<<<grid_for((max_n + 31) / 32, kThreads / 32), kThreads, smem, s>>>(
-        cells, w64, halves_split(ell), ctr, uint32_t(max_n), hkey, fl, fh, lkey, idx);
+        cells, w64, halves_split(ell), ctr, uint32_t(max_n), hkey, fl, fh, lkey, idx, adopt_n,
+        ell);
   } else {
     halves_keys<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(
         cells, w64, halves_split(ell), ctr, uint32_t(max_n), hkey, fl, fh, lkey, idx);

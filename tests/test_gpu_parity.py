@@ -838,3 +838,33 @@ def test_neighbors_rejects_unsorted_cells(dev):
     wide = np.array([[0, 2], [5, 1]], dtype=np.uint64)  # row 1 < row 0 (top word)
     with pytest.raises(cellgraph.CellGraphError):
         cellgraph.neighbors_h1(words_dev(wide, 64, dev), 100, 64)
+
+
+@pytest.mark.parametrize("ell", [100, 1024, 1030])
+def test_neighbors_halves_checks_given_rows(dev, ell):
+    """HALVES over 64-bit rows given in place checks their order in its key
+    pass (2 to 16 words) or before it (more words): rows out of order within a
+    warp's 32 rows or across two warps' rows, and a repeated row, are
+    CG_ERR_INVALID_ARG; the sorted rows give the oracle's edges."""
+    rng = np.random.default_rng(ell)
+    w = (ell + 63) // 64
+    rows = rng.integers(0, 2**63, size=(70, w), dtype=np.int64).astype(np.uint64)
+    if ell % 64:
+        rows[:, -1] &= np.uint64((1 << (ell % 64)) - 1)
+    rows = np.unique(rows, axis=0)
+    order = np.lexsort(rows.T)  # last word most significant
+    rows = np.ascontiguousarray(rows[order])
+    got = cellgraph.neighbors_h1(words_dev(rows, 64, dev), ell, 64, strategy="halves")
+    assert np.array_equal(edges_np(got), oracle.neighbors(rows, ell, 64))
+    bad = []
+    for i, j in ((5, 6), (31, 32)):
+        b = rows.copy()
+        b[[i, j]] = b[[j, i]]
+        bad.append(b)
+    dup = rows.copy()
+    dup[32] = dup[31]
+    bad.append(dup)
+    for b in bad:
+        with pytest.raises(cellgraph.CellGraphError) as ei:
+            cellgraph.neighbors_h1(words_dev(b, 64, dev), ell, 64, strategy="halves")
+        assert ei.value.status == cellgraph.ERR_INVALID_ARG
