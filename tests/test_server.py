@@ -264,3 +264,24 @@ def test_requests_started_together_match_the_oracle(dev, wanted, where):
         assert st["failed"] == 0
         assert st["grouped"] >= 4 and st["groups"] >= 1, st
         assert st["bytes_in_use"] == 0
+
+
+@pytest.mark.gpu
+def test_requests_started_together_are_retried_one_by_one(dev, wanted, monkeypatch):
+    """Requests started together whose first table guess (1,024 slots) is too
+    small overflow inside the group; each is settled on its own, re-queued
+    with a larger table, and still gives the oracle's output."""
+    monkeypatch.setenv("CG_FIRST_TABLE_CAP", "1024")
+    spec = inputs.scene_batch_spec(n_scenes=32, seed=33, ell_lo=24, ell_hi=64, n_lo=2e4, n_hi=6e4)
+    scenes = [inputs.batch_scene(spec, s) for s in range(32)]
+    with cellgraph.Server(0, hbm_budget_bytes=4 << 30, max_inflight=64) as srv:
+        ts = [srv.submit(s.pts, s.a, s.b) for s in scenes]
+        for i, (t, sc) in enumerate(zip(ts, scenes)):
+            assert srv.wait(t, 120.0)
+            _check(srv, t, sc, wanted(("gr", i), sc))
+            srv.release(t)
+        st = srv.stats()
+        assert st["failed"] == 0
+        assert st["grouped"] >= 4, st
+        assert st["retried"] >= 1, st
+        assert st["bytes_in_use"] == 0
