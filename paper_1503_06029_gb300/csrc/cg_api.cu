@@ -1095,7 +1095,8 @@ cg_tune_params sanitize_tune(const cg_tune_params& p, int ell) {
     q.strategy = CG_STRATEGY_HASH;
   const int hmax = pivot_max_h(ell);
   q.pivots = q.pivots < 1 ? 1 : (q.pivots > hmax ? hmax : q.pivots);
-  q.sign_kernel = (q.sign_kernel == 1 && ell <= 64) ? 1 : 0;
+  if (q.sign_kernel == 1) q.sign_kernel = ell <= 64 ? 1 : 0;
+  else if (q.sign_kernel != 2 && q.sign_kernel != 3) q.sign_kernel = 0;
   return q;
 }
 
@@ -1109,11 +1110,14 @@ ScenePlan plan_scene(int64_t n, int ell, size_t cap, const cg_tune_params& tp) {
   p.small = ell <= 64;
   p.single = !p.small && ell <= 1024;
   p.tp = sanitize_tune(tp, ell);
+  p.grid_bits = p.small && (p.tp.sign_kernel == 0 || p.tp.sign_kernel == 2)
+                    ? pack_grid_bits(n, p.tp.sign_kernel == 2)
+                    : 0;
   return p;
 }
 
 void carve_scene(Carve& c, const ScenePlan& p, DevCounters* ext_ctr, SmallWs* sw, WideWs* ww,
-                 PivotWs* pw, TreeWs* tw) {
+                 PivotWs* pw, TreeWs* tw, PackGrid* grid = nullptr) {
   const size_t un = size_t(p.n > 0 ? p.n : 1);
   const bool pivot =
       p.tp.strategy == CG_STRATEGY_PIVOT || p.tp.strategy == CG_STRATEGY_HALVES;
@@ -1125,6 +1129,14 @@ void carve_scene(Carve& c, const ScenePlan& p, DevCounters* ext_ctr, SmallWs* sw
                      ext_ctr);
   if (pivot) *pw = carve_pivot(c, p.ucap);
   if (tree) *tw = carve_treews(c, p.ucap, p.ell);
+  if (p.grid_bits > 0) {
+    GridCell* cells = c.take<GridCell>(size_t(1) << p.grid_bits);
+    GridGeom* geom = c.take<GridGeom>(1);
+    if (grid) {
+      grid->cells = cells;
+      grid->geom = geom;
+    }
+  }
 }
 
 size_t scene_ws_bytes(const ScenePlan& p) {
@@ -1259,7 +1271,8 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
   WideWs ww{};
   PivotWs pw{};
   TreeWs tw{};
-  carve_scene(c, plan, ctr, &w, &ww, &pw, &tw);
+  PackGrid grid{};
+  carve_scene(c, plan, ctr, &w, &ww, &pw, &tw, &grid);
   const int64_t n = plan.n;
   const int ell = plan.ell;
   const int strategy = plan.tp.strategy;
@@ -1321,9 +1334,18 @@ cg_status enqueue_scene(cg_ctx* ctx, char* ws, DevCounters* ctr, const ScenePlan
           pk.n = std::min<int64_t>(pieces->per, n - lo);
           CG_CUDA(cudaStreamWaitEvent(s, pieces->ready[k], 0), "waiting for points");
         }
-        CG_CUDA(tc ? launch_pack_tc_insert(pk, w.table(true), w.spill, s)
-                   : launch_pack_insert(pk, w.table(true), s),
-                "sign vectors + dedup");
+        // Points in pieces arrive over time: the grid's sample would read
+        // pieces not yet there, so they test every constraint.
+        if (!tc && !pieces && plan.grid_bits > 0) {
+          grid.total_bits = plan.grid_bits;
+          CG_CUDA(launch_pack_grid_setup(pk, grid, s), "box grid");
+          mark(ctx, "grid", s);
+          CG_CUDA(launch_pack_insert_grid(pk, w.table(true), grid, s), "sign vectors + dedup");
+        } else {
+          CG_CUDA(tc ? launch_pack_tc_insert(pk, w.table(true), w.spill, s)
+                     : launch_pack_insert(pk, w.table(true), s),
+                  "sign vectors + dedup");
+        }
       }
     }
     mark(ctx, "pack_dedup", s);
@@ -2393,8 +2415,8 @@ extern "C" cg_status cg_ctx_tune_set(cg_ctx* ctx, int bucket, const cg_tune_para
       p->strategy != CG_STRATEGY_HALVES)
     return fail(CG_ERR_INVALID_ARG, "strategy must be HASH, SORTED, PIVOT, TREE or HALVES");
   if (p->pivots < 1 || p->pivots > 8) return fail(CG_ERR_INVALID_ARG, "pivots must be 1..8");
-  if (p->sign_kernel != 0 && p->sign_kernel != 1)
-    return fail(CG_ERR_INVALID_ARG, "sign_kernel must be 0 or 1");
+  if (p->sign_kernel < 0 || p->sign_kernel > 3)
+    return fail(CG_ERR_INVALID_ARG, "sign_kernel must be 0, 1, 2 or 3");
   ctx->tune[bucket] = *p;
   return CG_OK;
 }

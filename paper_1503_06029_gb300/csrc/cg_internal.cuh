@@ -139,6 +139,37 @@ inline int table_shift(size_t cap) {
 // Fused steps 1-2 for l <= 64: every vector goes straight into the table
 // (no vector is written to memory); distinct vectors are appended to ulist.
 cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStream_t s);
+
+// Box grid over the points for the sign step (l <= 64): count[k] slabs of
+// 2^shift[k] integers along axis k, starting at lo[k]. Cell (g_0 .. g_{d-1}),
+// stored at g_0 + count[0] (g_1 + count[1] (g_2 + ...)), is the integer box
+// of its slabs; `base` holds bit i when a_i . p >= b_i at every point of that
+// box, `cross` bit i when the sign may change inside it.
+// A point's vector is then base plus the exact tests of its cell's crossing
+// constraints only. lo and shift are chosen on the device from a sample of
+// the points (a point outside the grid tests every constraint).
+struct GridCell {
+  uint64_t base;
+  uint64_t cross;
+};
+struct GridGeom {
+  int32_t lo[4];
+  int32_t shift[4];
+  int32_t count[4];
+};
+struct PackGrid {
+  GridCell* cells;  // [2^total_bits] (the grid uses at most that many)
+  GridGeom* geom;   // written by the set-up kernel
+  int total_bits;
+};
+// log2 of the cell budget of the grid for a scene of n points (0: no grid);
+// `always` asks for one even where it does not pay (tests).
+int pack_grid_bits(int64_t n, bool always);
+// The grid's set-up (sample box, placement, cell classification), and the
+// sign + insert kernel that reads it (enqueue it after the set-up on s).
+cudaError_t launch_pack_grid_setup(const PackArgs& pa, const PackGrid& g, cudaStream_t s);
+cudaError_t launch_pack_insert_grid(const PackArgs& pa, const SmallTable& t, const PackGrid& g,
+                                    cudaStream_t s);
 // The same for many scenes in one launch (a batch): scene s (device array)
 // owns the 128-point warp tiles [tile0, next scene's tile0) of the batch's
 // tile numbering, total_tiles in all; every scene has dimension d and at most

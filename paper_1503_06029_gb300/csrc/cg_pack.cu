@@ -118,9 +118,13 @@ struct Coef {
   static constexpr int kQuads = (kFloats + 3) / 4;
 };
 
-// Writes constraint t's coefficients for a tile whose |p_k| <= M[k].
+// Writes constraint t's coefficients for a tile whose |p_k| <= M[k]. When
+// scale is given it receives the factor 2^-e the row was scaled by (0 for a
+// padding row or one whose values are all exactly zero).
 template <int D, int R = 2>
-__device__ void build_coef(const PackArgs& pa, int t, const uint32_t (&M)[D], float4* dst) {
+__device__ void build_coef(const PackArgs& pa, int t, const uint32_t (&M)[D], float4* dst,
+                           float* scale = nullptr) {
+  if (scale) *scale = 0.0f;
   float v[Coef<D, R>::kQuads * 4];
 #pragma unroll
   for (int q = 0; q < Coef<D, R>::kQuads * 4; ++q) v[q] = 0.0f;
@@ -148,6 +152,7 @@ __device__ void build_coef(const PackArgs& pa, int t, const uint32_t (&M)[D], fl
         for (int r = 0; r < R; ++r) v[R * k + r] = ak;
       }
       c = ldexpf(-__ll2float_rn(bt), -e);
+      if (scale) *scale = ldexpf(1.0f, -e);
     }
   }
 #pragma unroll
@@ -677,6 +682,473 @@ cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
   return err;
 }
 
+// ---------------------------------------------------------------------------
+// Box grid (l <= 64). A set-up kernel lays a grid of integer boxes over the
+// points and classifies, per cell, each constraint as holding on the whole
+// cell (`base`), failing on the whole cell, or crossing it (`cross`); the
+// sign kernel then tests each point against its cell's crossing constraints
+// only and takes the other bits from the cell.
+//
+// Placement: per axis, G slabs of 2^s integers covering the range of 1,024
+// evenly spaced sample points and 1/256 of it on each side; s is raised on
+// the axis with the most slabs until the cells fit the workspace and axis 0
+// has at most kMaxSweep slabs. The grid's box stays inside the int32 range,
+// so a point's slab (p - lo) >> s computed modulo 2^32 is below G exactly
+// when the point lies in the box; a point outside it tests every constraint
+// in exact integer arithmetic.
+//
+// Soundness of a cell's classification. The rows are built as for a tile
+// with |p_k| <= M_k, M_k the largest |coordinate| of the grid's box, so for
+// any real point x of the box the FMA chain at fl(x) is within 1 of
+// s (a . x - b) (s = 2^-e the row's scale; the error bound in the header
+// covers rounded inputs, in any order of the chain). At the centre c of a
+// cell of half-widths h_k every point p of the cell has
+// |s (a . p - b) - s (a . c - b)| <= s sum_k |a_k| h_k <= R (R rounded
+// upwards), so with v the chain at fl(c): v >= 2 + R proves bit 1 on the
+// whole cell and v <= -(2 + R) proves bit 0.
+//
+// The cells of one column (fixed slabs on axes 1..d-1, every slab g of axis
+// 0) are classified together. Along axis 0 the exact value a . p - b moves
+// monotonically with g (in the direction of the sign of a_0), so a cell
+// proven "bit 1" proves every cell beyond it in that direction, and likewise
+// for "bit 0". Per (column, constraint) a thread estimates both boundaries
+// from the chain, walks each to the last cell the test still proves, and
+// marks the runs in per-column difference words (XOR at each end of a run); a
+// prefix XOR along the column then gives every cell's words.
+// ---------------------------------------------------------------------------
+constexpr int kGridSample = 1024;  // points whose box places the grid
+constexpr int kGridThreads = 256;
+constexpr int kMaxSweep = 512;  // slabs along axis 0
+
+enum : int { kCellCross = 0, kCellOne = 1, kCellZero = 2 };
+
+// Centre of slab g (2^s integers from lo + g 2^s), rounded once to fp32:
+// twice the centre is an integer, rounded to fp32 and halved exactly.
+__device__ __forceinline__ float slab_centre(int32_t lo, int s, int g) {
+  const int64_t c2 = 2 * (int64_t(lo) + (int64_t(g) << s)) + ((int64_t(1) << s) - 1);
+  return 0.5f * __ll2float_rn(c2);
+}
+
+// The test at a cell centre whose axis-0 coordinate is x0, c1 the chain over
+// the other axes (started from the row's constant).
+__device__ __forceinline__ int cell_test(float f0, float x0, float c1, float q) {
+  const float v = fmaf(f0, x0, c1);
+  return v >= q ? kCellOne : (v <= -q ? kCellZero : kCellCross);
+}
+
+__device__ __forceinline__ int clamp_slab(float g, int lo, int hi) {
+  g = fminf(fmaxf(g, float(lo)), float(hi));  // also maps NaN to lo
+  return int(g);
+}
+
+template <int D, int NCH>
+__global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, PackGrid g) {
+  constexpr int kQ = Coef<D, 1>::kQuads;
+  constexpr int kRows = NCH * 32;
+  constexpr int kCols = kGridThreads / kRows;  // columns classified together
+  constexpr int kWords = 2 * NCH;              // base, then cross, 32 bits each
+  __shared__ float4 rows[kRows * kQ];
+  __shared__ float qlim[kRows];
+  __shared__ int32_t red[2][kGridThreads / 32][D];
+  __shared__ int32_t geo_lo[D], geo_sh[D], geo_n[D];
+  __shared__ uint32_t diff[kCols][kWords][kMaxSweep + 1];
+  __shared__ float cen0[kMaxSweep];  // centres of the axis-0 slabs
+  griddep_wait();  // the previous build may still read the grid
+  griddep_release();
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t n = pa.n;
+
+  // 1. Box of the sample (every block computes the same) and the placement.
+  int32_t mn[D], mx[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    mn[k] = INT32_MAX;
+    mx[k] = INT32_MIN;
+  }
+  for (int j = threadIdx.x; j < kGridSample; j += kGridThreads) {
+    const int64_t i = n <= kGridSample ? int64_t(j) : int64_t(j) * (n - 1) / (kGridSample - 1);
+    if (i < n) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int32_t v = __ldg(pa.pts + i * D + k);
+        mn[k] = min(mn[k], v);
+        mx[k] = max(mx[k], v);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    mn[k] = __reduce_min_sync(0xffffffffu, mn[k]);
+    mx[k] = __reduce_max_sync(0xffffffffu, mx[k]);
+    if (lane == 0) {
+      red[0][warp][k] = mn[k];
+      red[1][warp][k] = mx[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t first[D], ext[D], want[D], cnt[D];
+    int s[D];
+    for (int k = 0; k < D; ++k) {
+      int32_t a = INT32_MAX, b = INT32_MIN;
+      for (int w = 0; w < kGridThreads / 32; ++w) {
+        a = min(a, red[0][w][k]);
+        b = max(b, red[1][w][k]);
+      }
+      if (a > b) a = b = 0;
+      first[k] = a;
+      ext[k] = int64_t(b) - int64_t(a) + 1;
+      want[k] = min(ext[k] + ext[k] / 128 + 2, int64_t(1) << 32);
+      s[k] = 0;
+      cnt[k] = want[k];
+    }
+    const double budget = double(int64_t(1) << g.total_bits);
+    // Every step raises one s (at most 31 per axis); with every s at 31 the
+    // grid has at most 2^d cells, so the loop ends inside the budget.
+    for (int guard = 0; guard < 32 * D; ++guard) {
+      double prod = 1.0;
+      for (int k = 0; k < D; ++k) prod *= double(cnt[k]);
+      int kk = -1;
+      if (cnt[0] > kMaxSweep) {
+        kk = 0;
+      } else if (prod > budget) {
+        for (int k = 0; k < D; ++k)
+          if (s[k] < 31 && (kk < 0 || cnt[k] > cnt[kk])) kk = k;
+      }
+      if (kk < 0) break;
+      ++s[kk];
+      cnt[kk] = (want[kk] + (int64_t(1) << s[kk]) - 1) >> s[kk];
+    }
+    for (int k = 0; k < D; ++k) {
+      int64_t span = cnt[k] << s[k];
+      if (span > (int64_t(1) << 32)) {
+        cnt[k] = (int64_t(1) << 32) >> s[k];
+        span = cnt[k] << s[k];
+      }
+      int64_t lo = first[k] - (span - ext[k]) / 2;
+      if (lo < int64_t(INT32_MIN)) lo = INT32_MIN;
+      if (lo + span > (int64_t(1) << 31)) lo = (int64_t(1) << 31) - span;
+      geo_lo[k] = int32_t(lo);
+      geo_sh[k] = s[k];
+      geo_n[k] = int32_t(cnt[k]);
+      if (blockIdx.x == 0) {
+        g.geom->lo[k] = int32_t(lo);
+        g.geom->shift[k] = s[k];
+        g.geom->count[k] = int32_t(cnt[k]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // 2. Rows for the box and each row's threshold q = 2 + R.
+  {
+    uint32_t M[D];
+    float hh[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int64_t lo = geo_lo[k];
+      const int64_t hi = lo + (int64_t(geo_n[k]) << geo_sh[k]) - 1;
+      M[k] = max(uabs32(int32_t(lo)), uabs32(int32_t(hi)));
+      hh[k] = 0.5f * __ull2float_ru((1ull << geo_sh[k]) - 1ull);
+    }
+    for (int t = threadIdx.x; t < kRows; t += kGridThreads) {
+      float sc;
+      build_coef<D, 1>(pa, t, M, rows + t * kQ, &sc);
+      float R = 0.0f;
+      if (sc != 0.0f) {
+        const int32_t* ar = pa.a + int64_t(t) * D;
+#pragma unroll
+        for (int k = 0; k < D; ++k) R = __fmaf_ru(__uint2float_ru(uabs32(ar[k])), hh[k], R);
+        R = __fmul_ru(R, sc);
+      }
+      qlim[t] = __fadd_ru(2.0f, R);
+    }
+  }
+  __syncthreads();
+
+  // 3. Columns, kCols at a time: thread (c, i) classifies constraint i on
+  // column c's cells.
+  const int G0 = geo_n[0];
+  uint32_t n_cols = 1;
+#pragma unroll
+  for (int k = 1; k < D; ++k) n_cols *= uint32_t(geo_n[k]);
+  const int c = threadIdx.x / kRows;
+  const int i = threadIdx.x % kRows;
+  const float* f = reinterpret_cast<const float*>(rows + i * kQ);
+  const float f0 = f[0];
+  const float q = qlim[i];
+  const int32_t lo0 = geo_lo[0];
+  const int s0 = geo_sh[0];
+  for (int t = threadIdx.x; t < G0; t += kGridThreads) cen0[t] = slab_centre(lo0, s0, t);
+  const float x00 = slab_centre(lo0, s0, 0);
+  const float rw0 = ldexpf(1.0f, -s0);  // 1 / slab width (exact)
+  const float rf0 = f0 != 0.0f ? 1.0f / f0 : 0.0f;
+  const int h = i >> 5;
+  const uint32_t bit = 1u << (i & 31);
+  for (uint32_t col0 = blockIdx.x * kCols; col0 < n_cols; col0 += gridDim.x * kCols) {
+    for (int r = warp; r < kCols * kWords; r += kGridThreads / 32)
+      for (int x = lane; x <= G0; x += 32) diff[r / kWords][r % kWords][x] = 0;
+    __syncthreads();
+    const uint32_t col = col0 + uint32_t(c);
+    if (col < n_cols && i < pa.ell) {
+      float c1 = f[D];
+      uint32_t rest = col;
+#pragma unroll
+      for (int k = 1; k < D; ++k) {
+        const uint32_t nxt = k + 1 < D ? rest / uint32_t(geo_n[k]) : 0u;
+        const uint32_t gk = rest - nxt * uint32_t(geo_n[k]);
+        rest = nxt;
+        c1 = fmaf(f[k], slab_centre(geo_lo[k], geo_sh[k], int(gk)), c1);
+      }
+      auto test = [&](int gg) { return cell_test(f0, cen0[gg], c1, q); };
+      int one_lo = 0, one_hi = 0, zero_lo = 0, zero_hi = 0, cr_lo = 0, cr_hi = 0;
+      if (f0 == 0.0f) {
+        const int t = test(0);  // the same value on every cell of the column
+        if (t == kCellOne) one_hi = G0;
+        else if (t == kCellZero) zero_hi = G0;
+        else cr_hi = G0;
+      } else {
+        // estimates only: the walks below decide
+        const float g_one = ((q - c1) * rf0 - x00) * rw0;    // where v = q
+        const float g_zero = ((-q - c1) * rf0 - x00) * rw0;  // where v = -q
+        if (f0 > 0.0f) {
+          // bit 1 on [a, G0): the first proven cell at or after the estimate,
+          // then back while the cell before is proven too
+          int a = clamp_slab(ceilf(g_one), 0, G0);
+          while (a < G0 && test(a) != kCellOne) ++a;
+          while (a > 0 && a < G0 && test(a - 1) == kCellOne) --a;
+          // bit 0 on [0, z)
+          int z = clamp_slab(floorf(g_zero), -1, G0 - 1);
+          while (z >= 0 && test(z) != kCellZero) --z;
+          while (z >= 0 && z < G0 - 1 && test(z + 1) == kCellZero) ++z;
+          one_lo = a, one_hi = G0, zero_lo = 0, zero_hi = z + 1;
+          cr_lo = z + 1, cr_hi = max(a, z + 1);
+        } else {
+          // bit 1 on [0, a + 1)
+          int a = clamp_slab(floorf(g_one), -1, G0 - 1);
+          while (a >= 0 && test(a) != kCellOne) --a;
+          while (a >= 0 && a < G0 - 1 && test(a + 1) == kCellOne) ++a;
+          // bit 0 on [z, G0)
+          int z = clamp_slab(ceilf(g_zero), 0, G0);
+          while (z < G0 && test(z) != kCellZero) ++z;
+          while (z > 0 && z < G0 && test(z - 1) == kCellZero) --z;
+          one_lo = 0, one_hi = a + 1, zero_lo = z, zero_hi = G0;
+          cr_lo = a + 1, cr_hi = max(z, a + 1);
+        }
+      }
+      (void)zero_lo;
+      (void)zero_hi;
+      if (one_lo < one_hi) {
+        atomicXor(&diff[c][h][one_lo], bit);
+        atomicXor(&diff[c][h][one_hi], bit);
+      }
+      if (cr_lo < cr_hi) {
+        atomicXor(&diff[c][NCH + h][cr_lo], bit);
+        atomicXor(&diff[c][NCH + h][cr_hi], bit);
+      }
+    }
+    __syncthreads();
+    // Prefix XOR along every column's words (a warp per word array).
+    const int per = (G0 + 31) / 32;
+    for (int p = warp; p < kCols * kWords; p += kGridThreads / 32) {
+      uint32_t* a = diff[p / kWords][p % kWords];
+      const int b0 = lane * per;
+      uint32_t acc = 0;
+      for (int t = 0; t < per; ++t)
+        if (b0 + t < G0) {
+          acc ^= a[b0 + t];
+          a[b0 + t] = acc;
+        }
+      uint32_t x = acc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x ^= y;
+      }
+      const uint32_t before = x ^ acc;
+      for (int t = 0; t < per; ++t)
+        if (b0 + t < G0) a[b0 + t] ^= before;
+    }
+    __syncthreads();
+    // The group's cells (axis 0 fastest: cell g0 + G0 * column).
+    for (int t = threadIdx.x; t < kCols * kMaxSweep; t += kGridThreads) {
+      const int cc = t / kMaxSweep;
+      const int g0 = t % kMaxSweep;
+      const uint32_t cl = col0 + uint32_t(cc);
+      if (g0 < G0 && cl < n_cols) {
+        GridCell e;
+        e.base = diff[cc][0][g0];
+        e.cross = diff[cc][NCH][g0];
+        if (NCH == 2) {
+          e.base |= uint64_t(diff[cc][1][g0]) << 32;
+          e.cross |= uint64_t(diff[cc][3][g0]) << 32;
+        }
+        g.cells[size_t(g0) + size_t(G0) * cl] = e;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// [a_t . p >= b_t] for every constraint t < l, in 128-bit integers (points
+// outside the grid).
+template <int D>
+__device__ __noinline__ uint64_t exact_vector(const PackArgs& pa, int32_t p0, int32_t p1,
+                                              int32_t p2, int32_t p3) {
+  const int32_t p[4] = {p0, p1, p2, p3};
+  int32_t pd[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) pd[k] = p[k];
+  uint64_t kw = 0;
+  for (int t = 0; t < pa.ell; ++t)
+    if (exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], pd)) kw |= 1ull << t;
+  return kw;
+}
+
+// Exact decision of the crossing constraints of one point whose fp32 value
+// was too close to zero (|t'| < 2): the values recomputed, the uncertain ones
+// settled in 128-bit integers.
+template <int D, int kQ>
+__device__ __forceinline__ uint64_t grid_settle(const PackArgs& pa, const float4* rows,
+                                                uint64_t cross, const float (&x)[D],
+                                                const int32_t (&p)[D], uint64_t kw) {
+  while (cross) {
+    const int j = 63 - __clzll(cross);
+    cross ^= 1ull << j;
+    const float* f = reinterpret_cast<const float*>(rows + j * kQ);
+    float v = f[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) v = fmaf(f[k], x[k], v);
+    if (!(__float_as_uint(v) & 0x40000000u)) {
+      const bool ge = exact_ge<D>(pa.a + int64_t(j) * D, pa.b[j], p);
+      kw = ge ? (kw | (1ull << j)) : (kw & ~(1ull << j));
+    }
+  }
+  return kw;
+}
+
+// Sign + insert with the grid: per point its cell's entry (one 16-byte load
+// from the L2-resident grid) and a loop over the cell's crossing constraints,
+// with one set of rows built for the grid's box.
+template <int D, int NCH, class Sink>
+__global__ void __launch_bounds__(kFThreads, 4)
+    pack_grid_kernel(PackArgs pa, Sink sink, PackGrid g, int vec_ok) {
+  constexpr int P = 4;
+  constexpr int kQ = Coef<D, 1>::kQuads;
+  constexpr int kRows = NCH * 32;
+  constexpr int kWarpPts = 32 * P;
+  __shared__ float4 rows[kRows * kQ];
+  __shared__ int4 stage_all[kFWarps][32 * (P * D / 4)];
+  griddep_wait();  // the table cleared and the grid classified
+  griddep_release();
+  int4* stage = stage_all[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int64_t n = pa.n;
+  uint32_t glo[D], gsh[D], gcnt[D], gmul[D], M[D];
+  {
+    uint32_t mul = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int32_t lo = g.geom->lo[k];
+      const int32_t sh = g.geom->shift[k];
+      const int32_t cnt = g.geom->count[k];
+      glo[k] = uint32_t(lo);
+      gsh[k] = uint32_t(sh);
+      gcnt[k] = uint32_t(cnt);
+      gmul[k] = mul;
+      mul *= uint32_t(cnt);
+      const int64_t hi = int64_t(lo) + (int64_t(cnt) << sh) - 1;
+      M[k] = max(uabs32(lo), uabs32(int32_t(hi)));
+    }
+  }
+  for (int t = threadIdx.x; t < kRows; t += kFThreads) build_coef<D, 1>(pa, t, M, rows + t * kQ);
+  __syncthreads();
+
+  const int64_t n_wt = (n + kWarpPts - 1) / kWarpPts;
+  const int64_t stride = int64_t(gridDim.x) * kFWarps;
+  for (int64_t it = int64_t(blockIdx.x) * kFWarps + (threadIdx.x >> 5); it < n_wt; it += stride) {
+    const int64_t p0 = it * kWarpPts + int64_t(lane) * P;
+    int32_t pi[P][D];
+    load_points_warp<D, P>(pa, it * kWarpPts, vec_ok, stage, pi);
+    GridCell e[P];
+    bool outside[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      bool in = p0 + q < n;
+      uint32_t idx = 0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const uint32_t gk = (uint32_t(pi[q][k]) - glo[k]) >> gsh[k];
+        in = in && gk < gcnt[k];
+        idx += gk * gmul[k];
+      }
+      outside[q] = !in && p0 + q < n;
+      e[q] = in ? g.cells[idx] : GridCell{0ull, 0ull};
+    }
+    uint64_t key[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      float x[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) x[k] = __int2float_rn(pi[q][k]);
+      uint64_t kw = e[q].base;
+      uint64_t m = e[q].cross;
+      uint32_t cert = 0xffffffffu;
+      while (m) {
+        const int j = 63 - __clzll(m);
+        m ^= 1ull << j;
+        float4 q4[kQ];
+#pragma unroll
+        for (int r = 0; r < kQ; ++r) q4[r] = rows[j * kQ + r];
+        const float* f = reinterpret_cast<const float*>(q4);
+        float v = f[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) v = fmaf(f[k], x[k], v);
+        const uint32_t u = __float_as_uint(v);
+        kw |= uint64_t(~u >> 31) << j;
+        cert &= u;
+      }
+      if (!(cert & 0x40000000u)) kw = grid_settle<D, kQ>(pa, rows, e[q].cross, x, pi[q], kw);
+      if (outside[q])
+        kw = exact_vector<D>(pa, pi[q][0], pi[q][D > 1 ? 1 : 0], pi[q][D > 2 ? 2 : 0],
+                             pi[q][D > 3 ? 3 : 0]);
+      key[q] = kw;
+    }
+    sink.template finish<P>(p0, n, key);
+  }
+}
+
+template <int D, int NCH>
+cudaError_t launch_grid_setup_dn(const PackArgs& pa, const PackGrid& g, cudaStream_t s) {
+  // Columns in groups of 256 / (32 NCH); at most 2^total_bits cells.
+  constexpr int kCols = kGridThreads / (NCH * 32);
+  const int64_t groups = ((int64_t(1) << g.total_bits) + kCols - 1) / kCols;
+  const int64_t sg = std::max<int64_t>(1, std::min<int64_t>(groups, int64_t(sm_count()) * 4));
+  const cudaError_t err = launch_dep(grid_setup_kernel<D, NCH>, dim3(unsigned(sg)),
+                                     dim3(kGridThreads), 0, s, pa, g);
+  count_launch();
+  return err;
+}
+
+template <int D, int NCH>
+cudaError_t launch_grid_dn(const PackArgs& pa, const SmallTable& t, const PackGrid& g,
+                           cudaStream_t s) {
+  auto kern = pack_grid_kernel<D, NCH, FastInsert>;
+  int per_sm = 0;
+  cudaError_t err = blocks_per_sm(reinterpret_cast<const void*>(kern), kFThreads, 0, &per_sm);
+  if (err != cudaSuccess) return err;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const int64_t n_wt = (pa.n + 127) / 128;
+  const int64_t want = (n_wt + kFWarps - 1) / kFWarps;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sm_count()) * per_sm));
+  const int vec_ok = (reinterpret_cast<uintptr_t>(pa.pts) % 16) == 0;
+  err = launch_dep(kern, dim3(unsigned(grid)), dim3(kFThreads), 0, s, pa, FastInsert{t}, g,
+                   vec_ok);
+  count_launch();
+  return err;
+}
+
 // Many scenes of l <= 64 in one launch (batches): warp w takes the contiguous
 // tile range [w per, (w + 1) per) of the batch's tile numbering; per tile it
 // finds the scene (tiles are visited in increasing order, so the scene index
@@ -885,6 +1357,40 @@ cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStre
   if (pa.ell > 64) return cudaErrorInvalidValue;
   if (pa.n == 0) return cudaSuccess;
   return launch_fast_any(pa, MakeInsert{t}, s);
+}
+
+int pack_grid_bits(int64_t n, bool always) {
+  if (!always) return 0;  // opt-in (tuning sign_kernel 2) until it beats the plain kernel
+  int lg = 0;
+  while ((int64_t(2) << lg) <= n) ++lg;  // floor(log2 n)
+  return std::max(6, std::min(20, lg - 4));
+}
+
+cudaError_t launch_pack_grid_setup(const PackArgs& pa, const PackGrid& g, cudaStream_t s) {
+  if (pa.ell > 64) return cudaErrorInvalidValue;
+  if (pa.n == 0) return cudaSuccess;
+  const bool two = pa.ell > 32;
+  switch (pa.d) {
+    case 1: return two ? launch_grid_setup_dn<1, 2>(pa, g, s) : launch_grid_setup_dn<1, 1>(pa, g, s);
+    case 2: return two ? launch_grid_setup_dn<2, 2>(pa, g, s) : launch_grid_setup_dn<2, 1>(pa, g, s);
+    case 3: return two ? launch_grid_setup_dn<3, 2>(pa, g, s) : launch_grid_setup_dn<3, 1>(pa, g, s);
+    case 4: return two ? launch_grid_setup_dn<4, 2>(pa, g, s) : launch_grid_setup_dn<4, 1>(pa, g, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pack_insert_grid(const PackArgs& pa, const SmallTable& t, const PackGrid& g,
+                                    cudaStream_t s) {
+  if (pa.ell > 64) return cudaErrorInvalidValue;
+  if (pa.n == 0) return cudaSuccess;
+  const bool two = pa.ell > 32;
+  switch (pa.d) {
+    case 1: return two ? launch_grid_dn<1, 2>(pa, t, g, s) : launch_grid_dn<1, 1>(pa, t, g, s);
+    case 2: return two ? launch_grid_dn<2, 2>(pa, t, g, s) : launch_grid_dn<2, 1>(pa, t, g, s);
+    case 3: return two ? launch_grid_dn<3, 2>(pa, t, g, s) : launch_grid_dn<3, 1>(pa, t, g, s);
+    case 4: return two ? launch_grid_dn<4, 2>(pa, t, g, s) : launch_grid_dn<4, 1>(pa, t, g, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace cg

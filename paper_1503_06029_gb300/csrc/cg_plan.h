@@ -29,6 +29,7 @@ struct ScenePlan {
   size_t ucap;  // distinct-vector capacity
   bool small;   // l <= 64
   bool single;  // wide, single-pass neighbour kernel and cluster sort
+  int grid_bits;  // log2 cells of the sign step's box grid (0: none)
   cg_tune_params tp;
 };
 

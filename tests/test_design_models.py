@@ -10,6 +10,11 @@ argument fails here before it can reach a GPU:
   of a stable sort, and each group checking its own case exactly finds every
   edge once -- even when the low-part key collides (here a deliberately weak
   key is used as well as the exact one).
+* Box grid of the sign step: with the grid's box kept inside the int32 range,
+  a point's slab (p - lo) >> s computed modulo 2^32 is below 2^bits exactly
+  when lo <= p < lo + 2^(bits + s), so one unsigned subtraction and one
+  compare place any int32 point, inside the grid or not; the box covers the
+  sample's range it was placed on.
 * BFS frontier counters: level d reads count[d % 3], appends to
   count[(d + 1) % 3] and clears count[(d + 2) % 3] even when its own frontier
   is empty; with the host looking only after every 16th level, no stale count
@@ -120,3 +125,52 @@ def test_bfs_counter_rotation_model(seed):
         if count[d % 3] == 0:  # the host's look after the group
             break
     assert seen == want
+
+
+def _grid_axis(lo_s, hi_s, s, cnt):
+    """The grid's placement on one axis: cnt slabs of 2^s integers around the
+    sample range [lo_s, hi_s], kept inside the int32 range (model of the
+    set-up kernel's last step)."""
+    ext = hi_s - lo_s + 1
+    span = cnt << s
+    if span > 2**32:
+        cnt = 2**32 >> s
+        span = cnt << s
+    lo = max(lo_s - (span - ext) // 2, -2**31)
+    if lo + span > 2**31:
+        lo = 2**31 - span
+    return lo, cnt, span
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_grid_slab_test_model(seed):
+    rng = np.random.default_rng(seed)
+    I32 = (-2**31, 2**31 - 1)
+    ranges = [(0, 0), I32, (I32[0], I32[0]), (I32[1], I32[1]), (-5, 5), (I32[1] - 3, I32[1]),
+              (I32[0], I32[0] + 1000)]
+    for _ in range(30):
+        x, y = sorted(int(v) for v in rng.integers(I32[0], I32[1] + 1, 2, dtype=np.int64))
+        ranges.append((x, y))
+        c = int(rng.integers(-2**20, 2**20))
+        ranges.append((c, c + int(rng.integers(0, 2**12))))
+    for lo_s, hi_s in ranges:
+        ext = hi_s - lo_s + 1
+        want = min(ext + ext // 128 + 2, 2**32)
+        for s in (0, 1, 5, 16, 30, 31):
+            cnt0 = -(-want // (1 << s))  # slabs covering want
+            for cnt in {cnt0, max(1, cnt0 // 3)}:
+                if cnt > 2**20:
+                    continue
+                lo, cnt, span = _grid_axis(lo_s, hi_s, s, cnt)
+                assert -2**31 <= lo and lo + span <= 2**31  # inside the int32 range
+                if cnt == cnt0:
+                    assert lo <= lo_s and hi_s < lo + span  # covers the sample
+                probes = {lo - 1, lo, lo + span - 1, lo + span, lo_s, hi_s, *I32, 0}
+                probes |= {int(v) for v in rng.integers(I32[0], I32[1] + 1, 48, dtype=np.int64)}
+                for p in probes:
+                    if not I32[0] <= p <= I32[1]:
+                        continue
+                    g = ((p - lo) % 2**32) >> s  # uint32 subtraction, then the shift
+                    assert (g < cnt) == (lo <= p < lo + span)
+                    if g < cnt:  # and the slab's integers hold p
+                        assert lo + (g << s) <= p <= lo + ((g + 1) << s) - 1
