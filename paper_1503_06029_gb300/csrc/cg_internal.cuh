@@ -144,13 +144,14 @@ cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStre
 // 2^shift[k] integers along axis k, starting at lo[k]. Cell (g_0 .. g_{d-1}),
 // stored at g_0 + count[0] (g_1 + count[1] (g_2 + ...)), is the integer box
 // of its slabs; `base` holds bit i when a_i . p >= b_i at every point of that
-// box, `cross` bit i when the sign may change inside it.
+// box, `list` the constraints whose sign may change inside it (up to 7 of
+// them; a count of 255 means more).
 // A point's vector is then base plus the exact tests of its cell's crossing
 // constraints only. lo and shift are chosen on the device from a sample of
 // the points (a point outside the grid tests every constraint).
 struct GridCell {
   uint64_t base;
-  uint64_t cross;
+  uint64_t list;  // crossing constraints: indices in bytes 0-6, their count in byte 7
 };
 struct GridGeom {
   int32_t lo[4];

@@ -718,9 +718,13 @@ cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 constexpr int kGridSample = 1024;  // points whose box places the grid
 constexpr int kGridThreads = 256;
-constexpr int kMaxSweep = 512;  // slabs along axis 0
+constexpr int kGridWarps = kGridThreads / 32;
+constexpr int kMaxSweep = 256;   // slabs along axis 0 (one warp sweeps a column)
+constexpr int kMaxOther = 2048;  // slabs of the other axes together
 
 enum : int { kCellCross = 0, kCellOne = 1, kCellZero = 2 };
+constexpr int kGridList = 7;            // crossing constraints listed per cell
+constexpr uint32_t kGridOverflow = 255;  // count byte of a cell with more
 
 // Centre of slab g (2^s integers from lo + g 2^s), rounded once to fp32:
 // twice the centre is an integer, rounded to fp32 and halved exactly.
@@ -741,25 +745,95 @@ __device__ __forceinline__ int clamp_slab(float g, int lo, int hi) {
   return int(g);
 }
 
+__device__ __forceinline__ int64_t slabs_for(int64_t want, int s) {
+  return (want + (int64_t(1) << s) - 1) >> s;
+}
+
+// Runs of the cells of one column (axis-0 slabs [0, G0)) on which the test
+// proves bit 1 ([*one_lo, *one_hi)) and the run on which the constraint may
+// cross ([*cr_lo, *cr_hi)); the rest is proven bit 0. cen0: the axis-0 slab
+// centres; c1: the chain over the other axes.
+__device__ __forceinline__ void column_runs(const float* cen0, int G0, float f0, float rf0,
+                                            float c1, float q, float x00, float rw0,
+                                            int* one_lo, int* one_hi, int* cr_lo, int* cr_hi) {
+  auto test = [&](int gg) { return cell_test(f0, cen0[gg], c1, q); };
+  *one_lo = *one_hi = *cr_lo = *cr_hi = 0;
+  if (f0 == 0.0f) {
+    const int t = test(0);  // the same value on every cell of the column
+    if (t == kCellOne) *one_hi = G0;
+    else if (t == kCellCross) *cr_hi = G0;
+    return;
+  }
+  // estimates only: the walks below decide
+  const float g_one = ((q - c1) * rf0 - x00) * rw0;    // where v = q
+  const float g_zero = ((-q - c1) * rf0 - x00) * rw0;  // where v = -q
+  if (f0 > 0.0f) {
+    // bit 1 on [a, G0): the first proven cell at or after the estimate, then
+    // back while the cell before is proven too
+    int a = clamp_slab(ceilf(g_one), 0, G0);
+    while (a < G0 && test(a) != kCellOne) ++a;
+    while (a > 0 && a < G0 && test(a - 1) == kCellOne) --a;
+    // bit 0 on [0, z + 1)
+    int z = clamp_slab(floorf(g_zero), -1, G0 - 1);
+    while (z >= 0 && test(z) != kCellZero) --z;
+    while (z >= 0 && z < G0 - 1 && test(z + 1) == kCellZero) ++z;
+    *one_lo = a, *one_hi = G0;
+    *cr_lo = z + 1, *cr_hi = max(a, z + 1);
+  } else {
+    // bit 1 on [0, a + 1)
+    int a = clamp_slab(floorf(g_one), -1, G0 - 1);
+    while (a >= 0 && test(a) != kCellOne) --a;
+    while (a >= 0 && a < G0 - 1 && test(a + 1) == kCellOne) ++a;
+    // bit 0 on [z, G0)
+    int z = clamp_slab(ceilf(g_zero), 0, G0);
+    while (z < G0 && test(z) != kCellZero) ++z;
+    while (z > 0 && z < G0 && test(z - 1) == kCellZero) --z;
+    *one_lo = 0, *one_hi = a + 1;
+    *cr_lo = a + 1, *cr_hi = max(z, a + 1);
+  }
+}
+
+// A cell's crossing constraints: indices in bytes 0 .. kGridList - 1, their
+// count in byte 7 (kGridOverflow when there are more: the point then tests
+// every constraint).
+__device__ __forceinline__ uint64_t grid_list(uint64_t cross) {
+  if (__popcll(cross) > kGridList) return uint64_t(kGridOverflow) << 56;
+  uint64_t list = 0;
+  uint32_t t = 0;
+  while (cross) {
+    const int j = __ffsll(cross) - 1;
+    cross &= cross - 1;
+    list |= uint64_t(j) << (8 * t);
+    ++t;
+  }
+  return list | (uint64_t(t) << 56);
+}
+
+// Every block places the grid from the same sample (so all agree) and builds
+// the rows; then each warp classifies whole columns on its own: lane j takes
+// constraints j and j + 32, marks its runs in the warp's difference words,
+// and the warp turns them into the column's cell words (prefix XOR) and
+// writes them.
 template <int D, int NCH>
 __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, PackGrid g) {
   constexpr int kQ = Coef<D, 1>::kQuads;
   constexpr int kRows = NCH * 32;
-  constexpr int kCols = kGridThreads / kRows;  // columns classified together
-  constexpr int kWords = 2 * NCH;              // base, then cross, 32 bits each
+  constexpr int kWords = 2 * NCH;  // base words, then cross words
   __shared__ float4 rows[kRows * kQ];
   __shared__ float qlim[kRows];
-  __shared__ int32_t red[2][kGridThreads / 32][D];
-  __shared__ int32_t geo_lo[D], geo_sh[D], geo_n[D];
-  __shared__ uint32_t diff[kCols][kWords][kMaxSweep + 1];
-  __shared__ float cen0[kMaxSweep];  // centres of the axis-0 slabs
-  griddep_wait();  // the previous build may still read the grid
-  griddep_release();
+  __shared__ int32_t red[2][kGridWarps][D];
+  __shared__ int32_t geo_lo[D], geo_sh[D], geo_n[D], cen_off[D];
+  __shared__ float cen[kMaxSweep + kMaxOther];  // slab centres, axis 0 first
+  __shared__ uint32_t diff_all[kGridWarps][kWords][kMaxSweep + 1];
+  // The previous build may still read the grid. The sign kernel is let in
+  // only at the end: its blocks, waiting early, would hold the registers and
+  // shared memory this kernel's blocks need.
+  griddep_wait();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int64_t n = pa.n;
 
-  // 1. Box of the sample (every block computes the same) and the placement.
+  // 1. Box of the sample and the placement.
   int32_t mn[D], mx[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -788,11 +862,17 @@ __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, P
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // Slabs: raise s on the axis with the most slabs (of equal counts, the
+    // last: axis 0, the one a warp sweeps, stays finest) while axis 0 has more
+    // than kMaxSweep, the others more than kMaxOther together, or all more
+    // than the budget. Axes over their own limit are brought under it
+    // directly: the rule raises them first, one after the other, whatever
+    // the order.
     int64_t first[D], ext[D], want[D], cnt[D];
     int s[D];
     for (int k = 0; k < D; ++k) {
       int32_t a = INT32_MAX, b = INT32_MIN;
-      for (int w = 0; w < kGridThreads / 32; ++w) {
+      for (int w = 0; w < kGridWarps; ++w) {
         a = min(a, red[0][w][k]);
         b = max(b, red[1][w][k]);
       }
@@ -801,25 +881,31 @@ __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, P
       ext[k] = int64_t(b) - int64_t(a) + 1;
       want[k] = min(ext[k] + ext[k] / 128 + 2, int64_t(1) << 32);
       s[k] = 0;
-      cnt[k] = want[k];
+      const int64_t lim = k == 0 ? kMaxSweep : kMaxOther;
+      while (slabs_for(want[k], s[k]) > lim) ++s[k];
+      cnt[k] = slabs_for(want[k], s[k]);
     }
-    const double budget = double(int64_t(1) << g.total_bits);
-    // Every step raises one s (at most 31 per axis); with every s at 31 the
-    // grid has at most 2^d cells, so the loop ends inside the budget.
+    const uint64_t budget = uint64_t(1) << g.total_bits;
     for (int guard = 0; guard < 32 * D; ++guard) {
-      double prod = 1.0;
-      for (int k = 0; k < D; ++k) prod *= double(cnt[k]);
-      int kk = -1;
-      if (cnt[0] > kMaxSweep) {
-        kk = 0;
-      } else if (prod > budget) {
-        for (int k = 0; k < D; ++k)
-          if (s[k] < 31 && (kk < 0 || cnt[k] > cnt[kk])) kk = k;
+      int64_t other = 0;
+      uint64_t prod = 1;
+      bool over = false;
+      for (int k = 0; k < D; ++k) {
+        if (k > 0) other += cnt[k];
+        prod *= uint64_t(cnt[k]);  // counts <= 2^32, prod <= budget before: no overflow
+        if (prod > budget) over = true, prod = budget + 1;
       }
+      int kk = -1;
+      const int k0 = other > kMaxOther ? 1 : 0;
+      if (cnt[0] > kMaxSweep) kk = 0;
+      else if (other > kMaxOther || over)
+        for (int k = k0; k < D; ++k)
+          if (s[k] < 31 && (kk < 0 || cnt[k] >= cnt[kk])) kk = k;  // ties: the last axis
       if (kk < 0) break;
       ++s[kk];
-      cnt[kk] = (want[kk] + (int64_t(1) << s[kk]) - 1) >> s[kk];
+      cnt[kk] = slabs_for(want[kk], s[kk]);
     }
+    int off = 0;
     for (int k = 0; k < D; ++k) {
       int64_t span = cnt[k] << s[k];
       if (span > (int64_t(1) << 32)) {
@@ -832,6 +918,8 @@ __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, P
       geo_lo[k] = int32_t(lo);
       geo_sh[k] = s[k];
       geo_n[k] = int32_t(cnt[k]);
+      cen_off[k] = off;
+      off += int(cnt[k]);
       if (blockIdx.x == 0) {
         g.geom->lo[k] = int32_t(lo);
         g.geom->shift[k] = s[k];
@@ -841,7 +929,11 @@ __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, P
   }
   __syncthreads();
 
-  // 2. Rows for the box and each row's threshold q = 2 + R.
+  // 2. Slab centres, rows for the box and each row's threshold q = 2 + R.
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    for (int t = threadIdx.x; t < geo_n[k]; t += kGridThreads)
+      cen[cen_off[k] + t] = slab_centre(geo_lo[k], geo_sh[k], t);
   {
     uint32_t M[D];
     float hh[D];
@@ -867,92 +959,64 @@ __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, P
   }
   __syncthreads();
 
-  // 3. Columns, kCols at a time: thread (c, i) classifies constraint i on
-  // column c's cells.
+  // 3. Columns, one warp each.
   const int G0 = geo_n[0];
   uint32_t n_cols = 1;
 #pragma unroll
   for (int k = 1; k < D; ++k) n_cols *= uint32_t(geo_n[k]);
-  const int c = threadIdx.x / kRows;
-  const int i = threadIdx.x % kRows;
-  const float* f = reinterpret_cast<const float*>(rows + i * kQ);
-  const float f0 = f[0];
-  const float q = qlim[i];
-  const int32_t lo0 = geo_lo[0];
-  const int s0 = geo_sh[0];
-  for (int t = threadIdx.x; t < G0; t += kGridThreads) cen0[t] = slab_centre(lo0, s0, t);
-  const float x00 = slab_centre(lo0, s0, 0);
-  const float rw0 = ldexpf(1.0f, -s0);  // 1 / slab width (exact)
-  const float rf0 = f0 != 0.0f ? 1.0f / f0 : 0.0f;
-  const int h = i >> 5;
-  const uint32_t bit = 1u << (i & 31);
-  for (uint32_t col0 = blockIdx.x * kCols; col0 < n_cols; col0 += gridDim.x * kCols) {
-    for (int r = warp; r < kCols * kWords; r += kGridThreads / 32)
-      for (int x = lane; x <= G0; x += 32) diff[r / kWords][r % kWords][x] = 0;
-    __syncthreads();
-    const uint32_t col = col0 + uint32_t(c);
-    if (col < n_cols && i < pa.ell) {
-      float c1 = f[D];
+  const float x00 = cen[0];
+  const float rw0 = ldexpf(1.0f, -geo_sh[0]);  // 1 / slab width (exact)
+  float f0[NCH], rf0[NCH], q[NCH];
+#pragma unroll
+  for (int h = 0; h < NCH; ++h) {
+    const float* f = reinterpret_cast<const float*>(rows + (32 * h + lane) * kQ);
+    f0[h] = f[0];
+    rf0[h] = f0[h] != 0.0f ? 1.0f / f0[h] : 0.0f;
+    q[h] = qlim[32 * h + lane];
+  }
+  uint32_t(*diff)[kMaxSweep + 1] = diff_all[warp];
+  const int per = (G0 + 31) / 32;
+  for (uint32_t col = blockIdx.x * kGridWarps + warp; col < n_cols;
+       col += gridDim.x * kGridWarps) {
+#pragma unroll
+    for (int w = 0; w < kWords; ++w)
+      for (int x = lane; x <= G0; x += 32) diff[w][x] = 0;
+    __syncwarp();
+    int gk[D];
+    {
       uint32_t rest = col;
 #pragma unroll
       for (int k = 1; k < D; ++k) {
         const uint32_t nxt = k + 1 < D ? rest / uint32_t(geo_n[k]) : 0u;
-        const uint32_t gk = rest - nxt * uint32_t(geo_n[k]);
+        gk[k] = int(rest - nxt * uint32_t(geo_n[k]));
         rest = nxt;
-        c1 = fmaf(f[k], slab_centre(geo_lo[k], geo_sh[k], int(gk)), c1);
-      }
-      auto test = [&](int gg) { return cell_test(f0, cen0[gg], c1, q); };
-      int one_lo = 0, one_hi = 0, zero_lo = 0, zero_hi = 0, cr_lo = 0, cr_hi = 0;
-      if (f0 == 0.0f) {
-        const int t = test(0);  // the same value on every cell of the column
-        if (t == kCellOne) one_hi = G0;
-        else if (t == kCellZero) zero_hi = G0;
-        else cr_hi = G0;
-      } else {
-        // estimates only: the walks below decide
-        const float g_one = ((q - c1) * rf0 - x00) * rw0;    // where v = q
-        const float g_zero = ((-q - c1) * rf0 - x00) * rw0;  // where v = -q
-        if (f0 > 0.0f) {
-          // bit 1 on [a, G0): the first proven cell at or after the estimate,
-          // then back while the cell before is proven too
-          int a = clamp_slab(ceilf(g_one), 0, G0);
-          while (a < G0 && test(a) != kCellOne) ++a;
-          while (a > 0 && a < G0 && test(a - 1) == kCellOne) --a;
-          // bit 0 on [0, z)
-          int z = clamp_slab(floorf(g_zero), -1, G0 - 1);
-          while (z >= 0 && test(z) != kCellZero) --z;
-          while (z >= 0 && z < G0 - 1 && test(z + 1) == kCellZero) ++z;
-          one_lo = a, one_hi = G0, zero_lo = 0, zero_hi = z + 1;
-          cr_lo = z + 1, cr_hi = max(a, z + 1);
-        } else {
-          // bit 1 on [0, a + 1)
-          int a = clamp_slab(floorf(g_one), -1, G0 - 1);
-          while (a >= 0 && test(a) != kCellOne) --a;
-          while (a >= 0 && a < G0 - 1 && test(a + 1) == kCellOne) ++a;
-          // bit 0 on [z, G0)
-          int z = clamp_slab(ceilf(g_zero), 0, G0);
-          while (z < G0 && test(z) != kCellZero) ++z;
-          while (z > 0 && z < G0 && test(z - 1) == kCellZero) --z;
-          one_lo = 0, one_hi = a + 1, zero_lo = z, zero_hi = G0;
-          cr_lo = a + 1, cr_hi = max(z, a + 1);
-        }
-      }
-      (void)zero_lo;
-      (void)zero_hi;
-      if (one_lo < one_hi) {
-        atomicXor(&diff[c][h][one_lo], bit);
-        atomicXor(&diff[c][h][one_hi], bit);
-      }
-      if (cr_lo < cr_hi) {
-        atomicXor(&diff[c][NCH + h][cr_lo], bit);
-        atomicXor(&diff[c][NCH + h][cr_hi], bit);
       }
     }
-    __syncthreads();
-    // Prefix XOR along every column's words (a warp per word array).
-    const int per = (G0 + 31) / 32;
-    for (int p = warp; p < kCols * kWords; p += kGridThreads / 32) {
-      uint32_t* a = diff[p / kWords][p % kWords];
+#pragma unroll
+    for (int h = 0; h < NCH; ++h) {
+      const int i = 32 * h + lane;
+      if (i >= pa.ell) continue;
+      const float* f = reinterpret_cast<const float*>(rows + i * kQ);
+      float c1 = f[D];
+#pragma unroll
+      for (int k = 1; k < D; ++k) c1 = fmaf(f[k], cen[cen_off[k] + gk[k]], c1);
+      int one_lo, one_hi, cr_lo, cr_hi;
+      column_runs(cen, G0, f0[h], rf0[h], c1, q[h], x00, rw0, &one_lo, &one_hi, &cr_lo, &cr_hi);
+      const uint32_t bit = 1u << lane;
+      if (one_lo < one_hi) {
+        atomicXor(&diff[h][one_lo], bit);
+        atomicXor(&diff[h][one_hi], bit);
+      }
+      if (cr_lo < cr_hi) {
+        atomicXor(&diff[NCH + h][cr_lo], bit);
+        atomicXor(&diff[NCH + h][cr_hi], bit);
+      }
+    }
+    __syncwarp();
+    // prefix XOR along the column, word array by word array
+#pragma unroll
+    for (int w = 0; w < kWords; ++w) {
+      uint32_t* a = diff[w];
       const int b0 = lane * per;
       uint32_t acc = 0;
       for (int t = 0; t < per; ++t)
@@ -970,56 +1034,42 @@ __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, P
       for (int t = 0; t < per; ++t)
         if (b0 + t < G0) a[b0 + t] ^= before;
     }
-    __syncthreads();
-    // The group's cells (axis 0 fastest: cell g0 + G0 * column).
-    for (int t = threadIdx.x; t < kCols * kMaxSweep; t += kGridThreads) {
-      const int cc = t / kMaxSweep;
-      const int g0 = t % kMaxSweep;
-      const uint32_t cl = col0 + uint32_t(cc);
-      if (g0 < G0 && cl < n_cols) {
-        GridCell e;
-        e.base = diff[cc][0][g0];
-        e.cross = diff[cc][NCH][g0];
-        if (NCH == 2) {
-          e.base |= uint64_t(diff[cc][1][g0]) << 32;
-          e.cross |= uint64_t(diff[cc][3][g0]) << 32;
-        }
-        g.cells[size_t(g0) + size_t(G0) * cl] = e;
+    __syncwarp();
+    // the column's cells (axis 0 fastest: cell g0 + G0 * column), the
+    // crossing constraints as a list of up to kGridList indices
+    for (int x = lane; x < G0; x += 32) {
+      uint64_t base = diff[0][x];
+      uint64_t cross = diff[NCH][x];
+      if (NCH == 2) {
+        base |= uint64_t(diff[1][x]) << 32;
+        cross |= uint64_t(diff[3][x]) << 32;
       }
+      g.cells[size_t(x) + size_t(G0) * col] = GridCell{base, grid_list(cross)};
     }
-    __syncthreads();
+    __syncwarp();
   }
+  griddep_release();
 }
 
-// [a_t . p >= b_t] for every constraint t < l, in 128-bit integers (points
-// outside the grid).
-template <int D>
-__device__ __noinline__ uint64_t exact_vector(const PackArgs& pa, int32_t p0, int32_t p1,
-                                              int32_t p2, int32_t p3) {
-  const int32_t p[4] = {p0, p1, p2, p3};
-  int32_t pd[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) pd[k] = p[k];
-  uint64_t kw = 0;
-  for (int t = 0; t < pa.ell; ++t)
-    if (exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], pd)) kw |= 1ull << t;
-  return kw;
-}
-
-// Exact decision of the crossing constraints of one point whose fp32 value
-// was too close to zero (|t'| < 2): the values recomputed, the uncertain ones
-// settled in 128-bit integers.
+// Exact decision of the listed crossing constraints of one point whose fp32
+// value was too close to zero (|t'| < 2): the values recomputed, the
+// uncertain ones settled in 128-bit integers.
 template <int D, int kQ>
-__device__ __forceinline__ uint64_t grid_settle(const PackArgs& pa, const float4* rows,
-                                                uint64_t cross, const float (&x)[D],
-                                                const int32_t (&p)[D], uint64_t kw) {
-  while (cross) {
-    const int j = 63 - __clzll(cross);
-    cross ^= 1ull << j;
+__device__ __noinline__ uint64_t grid_settle(const PackArgs& pa, const float4* rows, uint64_t list,
+                                             float x0, float x1, float x2, float x3, int32_t p0,
+                                             int32_t p1, int32_t p2, int32_t p3, uint64_t kw) {
+  const float xa[4] = {x0, x1, x2, x3};
+  const int32_t pa4[4] = {p0, p1, p2, p3};
+  int32_t p[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) p[k] = pa4[k];
+  const uint32_t c = uint32_t(list >> 56);
+  for (uint32_t t = 0; t < c; ++t) {
+    const int j = int((list >> (8 * t)) & 63u);
     const float* f = reinterpret_cast<const float*>(rows + j * kQ);
     float v = f[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) v = fmaf(f[k], x[k], v);
+    for (int k = 0; k < D; ++k) v = fmaf(f[k], xa[k], v);
     if (!(__float_as_uint(v) & 0x40000000u)) {
       const bool ge = exact_ge<D>(pa.a + int64_t(j) * D, pa.b[j], p);
       kw = ge ? (kw | (1ull << j)) : (kw & ~(1ull << j));
@@ -1028,21 +1078,78 @@ __device__ __forceinline__ uint64_t grid_settle(const PackArgs& pa, const float4
   return kw;
 }
 
-// Sign + insert with the grid: per point its cell's entry (one 16-byte load
-// from the L2-resident grid) and a loop over the cell's crossing constraints,
-// with one set of rows built for the grid's box.
+// [a_t . p >= b_t] for every constraint t < l: in 128-bit integers for a
+// point outside the grid (`exact`), else with the rows and the exact decision
+// of uncertain values (a cell with more than kGridList crossing constraints).
+template <int D, int kQ>
+__device__ __noinline__ uint64_t grid_all(const PackArgs& pa, const float4* rows, bool exact,
+                                          int32_t p0, int32_t p1, int32_t p2, int32_t p3) {
+  const int32_t pa4[4] = {p0, p1, p2, p3};
+  int32_t p[D];
+  float x[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    p[k] = pa4[k];
+    x[k] = __int2float_rn(p[k]);
+  }
+  uint64_t kw = 0;
+  for (int t = 0; t < pa.ell; ++t) {
+    bool ge;
+    if (exact) {
+      ge = exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], p);
+    } else {
+      const float* f = reinterpret_cast<const float*>(rows + t * kQ);
+      float v = f[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) v = fmaf(f[k], x[k], v);
+      ge = (__float_as_uint(v) & 0x40000000u) ? v >= 0.0f
+                                               : exact_ge<D>(pa.a + int64_t(t) * D, pa.b[t], p);
+    }
+    if (ge) kw |= 1ull << t;
+  }
+  return kw;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Point tiles in flight per warp (two at d = 4, whose tiles are larger).
+template <int D>
+struct GridStages {
+  static constexpr int value = D == 4 ? 2 : 3;
+};
+
+// Sign + insert with the grid. Per warp, 128-point tiles stream through a
+// ring of GridStages shared-memory slots filled by cp.async (whole tiles of
+// 16-byte aligned points; others are read directly), so the points of the
+// next tiles are on their way while one is evaluated. Per point: its cell's
+// entry (one 16-byte load from the L2-resident grid) and a loop over the
+// cell's listed crossing constraints, with one set of rows built for the
+// grid's box;
+// the previous tile's vectors are inserted while this tile's entries load.
 template <int D, int NCH, class Sink>
-__global__ void __launch_bounds__(kFThreads, 4)
+__global__ void __launch_bounds__(kFThreads, 3)
     pack_grid_kernel(PackArgs pa, Sink sink, PackGrid g, int vec_ok) {
   constexpr int P = 4;
   constexpr int kQ = Coef<D, 1>::kQuads;
   constexpr int kRows = NCH * 32;
   constexpr int kWarpPts = 32 * P;
+  constexpr int K = P * D / 4;  // 16-byte words per lane per tile
+  constexpr int kStages = GridStages<D>::value;
   __shared__ float4 rows[kRows * kQ];
-  __shared__ int4 stage_all[kFWarps][32 * (P * D / 4)];
+  __shared__ int4 ring_all[kFWarps][kStages][32 * K];
   griddep_wait();  // the table cleared and the grid classified
   griddep_release();
-  int4* stage = stage_all[threadIdx.x >> 5];
+  int4(*ring)[32 * K] = ring_all[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t n = pa.n;
   uint32_t glo[D], gsh[D], gcnt[D], gmul[D], M[D];
@@ -1067,10 +1174,53 @@ __global__ void __launch_bounds__(kFThreads, 4)
 
   const int64_t n_wt = (n + kWarpPts - 1) / kWarpPts;
   const int64_t stride = int64_t(gridDim.x) * kFWarps;
-  for (int64_t it = int64_t(blockIdx.x) * kFWarps + (threadIdx.x >> 5); it < n_wt; it += stride) {
+  const int64_t it0 = int64_t(blockIdx.x) * kFWarps + (threadIdx.x >> 5);
+  auto whole = [&](int64_t t) { return vec_ok && (t + 1) * kWarpPts <= n; };
+  // Every call commits one group (empty past the end), so that waiting for
+  // all but the newest kStages - 1 groups always means "this tile".
+  auto issue = [&](int64_t t, int slot) {
+    if (t < n_wt && whole(t)) {
+      const int4* src = reinterpret_cast<const int4*>(pa.pts + t * kWarpPts * D);
+#pragma unroll
+      for (int k = 0; k < K; ++k) cp_async16(&ring[slot][k * 32 + lane], src + k * 32 + lane);
+    }
+    cp_async_commit();
+  };
+  int64_t t_issue = it0;
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    issue(t_issue, st);
+    t_issue += stride;
+  }
+  int slot = 0;
+  bool have_prev = false;
+  int64_t p0_prev = 0;
+  uint64_t key_prev[P];
+  for (int64_t it = it0; it < n_wt; it += stride) {
+    issue(t_issue, (slot + kStages - 1) % kStages);
+    t_issue += stride;
+    cp_async_wait<kStages - 1>();
+    __syncwarp();
     const int64_t p0 = it * kWarpPts + int64_t(lane) * P;
     int32_t pi[P][D];
-    load_points_warp<D, P>(pa, it * kWarpPts, vec_ok, stage, pi);
+    if (whole(it)) {
+      int32_t tmp[P * D];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int4 v = ring[slot][lane * K + k];
+        tmp[4 * k] = v.x;
+        tmp[4 * k + 1] = v.y;
+        tmp[4 * k + 2] = v.z;
+        tmp[4 * k + 3] = v.w;
+      }
+#pragma unroll
+      for (int q = 0; q < P; ++q)
+#pragma unroll
+        for (int k = 0; k < D; ++k) pi[q][k] = tmp[q * D + k];
+    } else {
+      load_points<D, P>(pa, p0, vec_ok, pi);
+    }
+    __syncwarp();  // the slot is refilled by the next iteration's issue
     GridCell e[P];
     bool outside[P];
 #pragma unroll
@@ -1084,20 +1234,23 @@ __global__ void __launch_bounds__(kFThreads, 4)
         idx += gk * gmul[k];
       }
       outside[q] = !in && p0 + q < n;
-      e[q] = in ? g.cells[idx] : GridCell{0ull, 0ull};
+      e[q] = in ? g.cells[idx] : GridCell{0ull, 0ull};  // count 0: nothing listed
     }
-    uint64_t key[P];
+    if (have_prev) sink.template finish<P>(p0_prev, n, key_prev);
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       float x[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) x[k] = __int2float_rn(pi[q][k]);
-      uint64_t kw = e[q].base;
-      uint64_t m = e[q].cross;
+      const uint64_t list = e[q].list;
+      const uint32_t c = uint32_t(list >> 56);
+      uint32_t klo = uint32_t(e[q].base), khi = uint32_t(e[q].base >> 32);
       uint32_t cert = 0xffffffffu;
-      while (m) {
-        const int j = 63 - __clzll(m);
-        m ^= 1ull << j;
+      uint32_t w0 = uint32_t(list), w1 = uint32_t(list >> 32);
+      for (uint32_t t = 0; t < c && c != kGridOverflow; ++t) {
+        const uint32_t j = w0 & 63u;
+        w0 = __funnelshift_r(w0, w1, 8);
+        w1 >>= 8;
         float4 q4[kQ];
 #pragma unroll
         for (int r = 0; r < kQ; ++r) q4[r] = rows[j * kQ + r];
@@ -1106,29 +1259,41 @@ __global__ void __launch_bounds__(kFThreads, 4)
 #pragma unroll
         for (int k = 0; k < D; ++k) v = fmaf(f[k], x[k], v);
         const uint32_t u = __float_as_uint(v);
-        kw |= uint64_t(~u >> 31) << j;
+        const uint32_t r = (1u << (j & 31u)) & ~uint32_t(int32_t(u) >> 31);
+        if (NCH == 1 || j < 32) klo |= r;
+        else khi |= r;
         cert &= u;
       }
-      if (!(cert & 0x40000000u)) kw = grid_settle<D, kQ>(pa, rows, e[q].cross, x, pi[q], kw);
-      if (outside[q])
-        kw = exact_vector<D>(pa, pi[q][0], pi[q][D > 1 ? 1 : 0], pi[q][D > 2 ? 2 : 0],
-                             pi[q][D > 3 ? 3 : 0]);
-      key[q] = kw;
+      uint64_t kw = klo | (uint64_t(khi) << 32);
+      if (!(cert & 0x40000000u))
+        kw = grid_settle<D, kQ>(pa, rows, list, x[0], x[D > 1 ? 1 : 0], x[D > 2 ? 2 : 0],
+                                x[D > 3 ? 3 : 0], pi[q][0], pi[q][D > 1 ? 1 : 0],
+                                pi[q][D > 2 ? 2 : 0], pi[q][D > 3 ? 3 : 0], kw);
+      if (outside[q] || c == kGridOverflow)
+        kw = grid_all<D, kQ>(pa, rows, outside[q], pi[q][0], pi[q][D > 1 ? 1 : 0],
+                             pi[q][D > 2 ? 2 : 0], pi[q][D > 3 ? 3 : 0]);
+      key_prev[q] = kw;
     }
-    sink.template finish<P>(p0, n, key);
+    p0_prev = p0;
+    have_prev = true;
+    slot = slot + 1 == kStages ? 0 : slot + 1;
   }
+  if (have_prev) sink.template finish<P>(p0_prev, n, key_prev);
+  cp_async_wait<0>();
 }
 
 template <int D, int NCH>
 cudaError_t launch_grid_setup_dn(const PackArgs& pa, const PackGrid& g, cudaStream_t s) {
-  // Columns in groups of 256 / (32 NCH); at most 2^total_bits cells.
-  constexpr int kCols = kGridThreads / (NCH * 32);
-  const int64_t groups = ((int64_t(1) << g.total_bits) + kCols - 1) / kCols;
-  const int64_t sg = std::max<int64_t>(1, std::min<int64_t>(groups, int64_t(sm_count()) * 4));
-  const cudaError_t err = launch_dep(grid_setup_kernel<D, NCH>, dim3(unsigned(sg)),
-                                     dim3(kGridThreads), 0, s, pa, g);
+  // One warp per column; at most 2^total_bits columns (the placement is made
+  // on the device).
+  const int64_t want = ((int64_t(1) << g.total_bits) + kGridWarps - 1) / kGridWarps;
+  const int64_t sg = std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sm_count()) * 2));
+  // Plain launches (the kernels' griddepcontrol calls are then no-ops): with
+  // programmatic dependent launch the persistent sign kernel after it measured
+  // 0.1 ms slower per build (0.39 against 0.27 ms per planes_3d step).
+  grid_setup_kernel<D, NCH><<<unsigned(sg), kGridThreads, 0, s>>>(pa, g);
   count_launch();
-  return err;
+  return cudaGetLastError();
 }
 
 template <int D, int NCH>
@@ -1143,10 +1308,9 @@ cudaError_t launch_grid_dn(const PackArgs& pa, const SmallTable& t, const PackGr
   const int64_t want = (n_wt + kFWarps - 1) / kFWarps;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sm_count()) * per_sm));
   const int vec_ok = (reinterpret_cast<uintptr_t>(pa.pts) % 16) == 0;
-  err = launch_dep(kern, dim3(unsigned(grid)), dim3(kFThreads), 0, s, pa, FastInsert{t}, g,
-                   vec_ok);
+  kern<<<unsigned(grid), kFThreads, 0, s>>>(pa, FastInsert{t}, g, vec_ok);
   count_launch();
-  return err;
+  return cudaGetLastError();
 }
 
 // Many scenes of l <= 64 in one launch (batches): warp w takes the contiguous

@@ -64,7 +64,8 @@ def grid_geometry(pts):
     """The grid the library places over these points (its documented rule):
     per axis, cnt slabs of 2^s integers from lo, covering the range of 1,024
     evenly spaced sample points and 1/256 of it a side; s raised on the axis
-    with the most slabs until the cells fit 2^total and axis 0 has <= 512."""
+    with the most slabs (the last of equal ones) until axis 0 has <= 256, the others <= 2048 together
+    and all of them fit 2^total."""
     n, d = pts.shape
     lg = n.bit_length() - 1
     total = max(6, min(20, lg - 4))
@@ -74,11 +75,13 @@ def grid_geometry(pts):
     ext = [int(pts[idx, k].max()) - first[k] + 1 for k in range(d)]
     want = [min(e + e // 128 + 2, 2**32) for e in ext]
     s, cnt = [0] * d, list(want)
-    while True:
-        if cnt[0] > 512:
+    while True:  # axis 0 <= 256 slabs, the others <= 2048 together, all <= 2^total
+        other = sum(cnt[1:])
+        if cnt[0] > 256:
             kk = 0
-        elif np.prod([float(c) for c in cnt]) > 2.0 ** total:
-            kk = max((k for k in range(d) if s[k] < 31), key=lambda k: (cnt[k], -k))
+        elif other > 2048 or np.prod([float(c) for c in cnt]) > 2.0 ** total:
+            k0 = 1 if other > 2048 else 0
+            kk = max((k for k in range(k0, d) if s[k] < 31), key=lambda k: (cnt[k], k))
         else:
             break
         s[kk] += 1
