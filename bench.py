@@ -624,6 +624,10 @@ def run_ours(args):
     a = torch.from_numpy(sc.a).to(dev)
     b = torch.from_numpy(sc.b).to(dev)
     ctx = cellgraph.Context(local)
+    if args.sign_kernel >= 0:  # one sign kernel for every bucket of l
+        for bucket in range(cellgraph.TUNE_BUCKETS):
+            t = ctx.tune_get(bucket)
+            ctx.tune_set(bucket, t["strategy"], t["pivots"], args.sign_kernel)
     cells, edges = ctx.build(pts, a, b, 64)  # sizes the outputs
     u, e = cells.shape[0], edges.shape[0]
     outputs = (torch.empty((u, 1), dtype=torch.int64, device=dev),
@@ -795,6 +799,9 @@ def main():
     p.add_argument("--cpu-sample", type=int, default=1 << 24)
     p.add_argument("--ref-sample", type=int, default=1 << 20)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sign-kernel", type=int, default=-1,
+                   help="headline builds with this tuning sign_kernel (0 fp32 default, 1 tensor "
+                        "cores, 2 box grid, 3 all constraints); -1: the library default")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched-vs-plain comparison (and serving)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
