@@ -292,6 +292,10 @@ __global__ void clear_build(uint64_t* table, size_t cap, uint64_t* table2, size_
 // then the block writes its edges. The look-back wait is bounded.
 constexpr int kNEThreads = 256;
 constexpr int kNECells = 32;
+// Blocks of the one-word kernels: one warp per cell of a chunk, so a chunk's
+// table probes are all in flight at once (with 256 threads each warp walked 4
+// cells one after another: 16 dependent L2 round trips per chunk).
+constexpr int kNESmallThreads = 32 * kNECells;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -312,7 +316,7 @@ struct EmitShared {
 // totals (decoupled look-back, Merrill & Garland 2016; at most `polls` polls)
 // for the chunk's first edge position, then the block writes its edges.
 // Called by the whole block.
-template <class L>
+template <class L, int T = kNESmallThreads>
 __device__ __forceinline__ void emit_small_chunk(EmitShared& sm,
                                                  const uint64_t* __restrict__ cells, const L& look,
                                                  DevCounters* ctr, int ell,
@@ -324,7 +328,7 @@ __device__ __forceinline__ void emit_small_chunk(EmitShared& sm,
   const int lane = tid & 31;
   const int warp = tid >> 5;
   const int nh = (ell + 31) >> 5;
-  for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
+  for (int cl = warp; cl < kNECells; cl += T / 32) {
     const uint32_t i = c * kNECells + cl;
     uint32_t total = 0;
     if (i < u) {
@@ -383,7 +387,7 @@ __device__ __forceinline__ void emit_small_chunk(EmitShared& sm,
   }
   __syncthreads();
   const unsigned long long base = sm.base;
-  for (int cl = warp; cl < kNECells; cl += kNEThreads / 32) {
+  for (int cl = warp; cl < kNECells; cl += T / 32) {
     const uint32_t i = c * kNECells + cl;
     const uint32_t m = sm.cnt[cl];
     const unsigned long long o = base + sm.off[cl];
@@ -399,7 +403,7 @@ __device__ __forceinline__ void emit_small_chunk(EmitShared& sm,
 }
 
 template <class L>
-__global__ void __launch_bounds__(kNEThreads)
+__global__ void __launch_bounds__(kNESmallThreads)
     neighbors_emit_small(const uint64_t* __restrict__ cells, L look, DevCounters* ctr, int ell,
                          unsigned long long* status, uint32_t* __restrict__ edges, int64_t cap,
                          uint32_t max_n, uint32_t polls) {
@@ -466,7 +470,7 @@ __global__ void __launch_bounds__(1024)
 }
 
 template <bool kSorted>
-__global__ void __launch_bounds__(kNEThreads)
+__global__ void __launch_bounds__(kNESmallThreads)
     neighbors_seg_small(const SegSearchScene* __restrict__ sc, int n_scenes, unsigned int* off,
                         uint32_t polls) {
   __shared__ EmitShared sm;
@@ -1126,14 +1130,14 @@ cudaError_t launch_neighbors_emit_small(const uint64_t* cells, const SmallTable&
                                         cudaStream_t s) {
   if (max_n == 0) return cudaSuccess;
   if (ell > 64) return cudaErrorInvalidValue;
-  const int g = grid_for(max_n, kNECells, 4);
+  const int g = grid_for(max_n, kNECells, 2048 / kNESmallThreads);
   cudaError_t e;
   if (strategy == 2) {
-    e = launch_dep(neighbors_emit_small<SmallSorted>, dim3(g), dim3(kNEThreads), 0, s, cells,
+    e = launch_dep(neighbors_emit_small<SmallSorted>, dim3(g), dim3(kNESmallThreads), 0, s, cells,
                    SmallSorted{cells, t.ctr}, t.ctr, ell, status, edges, edges_cap,
                    uint32_t(max_n), wait_limit(kSpinLimit));
   } else {
-    e = launch_dep(neighbors_emit_small<SmallHash>, dim3(g), dim3(kNEThreads), 0, s, cells,
+    e = launch_dep(neighbors_emit_small<SmallHash>, dim3(g), dim3(kNESmallThreads), 0, s, cells,
                    SmallHash{t.keys, t.vals, t.mask, t.shift, t.ctr}, t.ctr, ell, status, edges,
                    edges_cap, uint32_t(max_n), wait_limit(kSpinLimit));
   }
@@ -1147,13 +1151,13 @@ cudaError_t launch_neighbors_seg_small(const SegSearchScene* scenes, int n_scene
   if (n_scenes <= 0) return cudaSuccess;
   seg_emit_offsets<<<1, 1024, 0, s>>>(scenes, n_scenes, scratch);
   const int g = int(std::max<size_t>(
-      1, std::min<size_t>(total_chunks, size_t(sm_count()) * 4)));
+      1, std::min<size_t>(total_chunks, size_t(sm_count()) * (2048 / kNESmallThreads))));
   if (sorted_lookup)
-    neighbors_seg_small<true><<<g, kNEThreads, 0, s>>>(scenes, n_scenes, scratch,
-                                                       wait_limit(kSpinLimit));
+    neighbors_seg_small<true><<<g, kNESmallThreads, 0, s>>>(scenes, n_scenes, scratch,
+                                                            wait_limit(kSpinLimit));
   else
-    neighbors_seg_small<false><<<g, kNEThreads, 0, s>>>(scenes, n_scenes, scratch,
-                                                        wait_limit(kSpinLimit));
+    neighbors_seg_small<false><<<g, kNESmallThreads, 0, s>>>(scenes, n_scenes, scratch,
+                                                             wait_limit(kSpinLimit));
   count_launch(2);
   return cudaGetLastError();
 }
@@ -1406,11 +1410,11 @@ cudaError_t launch_neighbors_emit_tree(const uint64_t* cells, int w64, int ell,
                                        unsigned long long* status, uint32_t* edges,
                                        int64_t edges_cap, size_t max_n, cudaStream_t s) {
   if (max_n == 0) return cudaSuccess;
-  const int g = grid_for(max_n, kNECells, 4);
   if (w64 == 1 && ell <= 64) {
-    neighbors_emit_small<<<g, kNEThreads, 0, s>>>(cells, TreeSmall{cells, nodes, ell}, ctr, ell,
-                                                  status, edges, edges_cap, uint32_t(max_n),
-                                                  wait_limit(kSpinLimit));
+    const int g = grid_for(max_n, kNECells, 2048 / kNESmallThreads);
+    neighbors_emit_small<<<g, kNESmallThreads, 0, s>>>(cells, TreeSmall{cells, nodes, ell}, ctr,
+                                                       ell, status, edges, edges_cap,
+                                                       uint32_t(max_n), wait_limit(kSpinLimit));
     return finish(0);
   }
   const size_t smem = size_t(ell) * sizeof(uint64_t) + size_t(kNECells) * ell * sizeof(uint32_t);
@@ -1418,6 +1422,7 @@ cudaError_t launch_neighbors_emit_tree(const uint64_t* cells, int w64, int ell,
   auto k = neighbors_emit_wide<TreeWide>;
   cudaError_t e = allow_smem(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
+  const int g = grid_for(max_n, kNECells, 4);
   k<<<g, kNEThreads, smem, s>>>(cells, w64, ell, TreeWide{cells, nodes, w64, ell}, ctr, status,
                                 edges, edges_cap, uint32_t(max_n),
                                 wait_limit(kSpinLimit));
