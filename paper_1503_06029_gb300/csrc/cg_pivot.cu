@@ -459,38 +459,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Edges of the cells with at most kHitBuf hits, from the hit buffer, in
-// increasing order of j (thread per cell).
-__global__ void __launch_bounds__(kThreads)
-    pivot_emit(const DevCounters* ctr, uint32_t max_n, const uint32_t* __restrict__ counts,
-               const uint32_t* __restrict__ hbuf, const unsigned long long* __restrict__ offsets,
-               uint32_t* __restrict__ edges, int64_t cap) {
-  if (ctr->overflow) return;
-  const uint32_t u = min(ctr->n_unique, max_n);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < u; i += gridDim.x * blockDim.x) {
-    const uint32_t m = counts[i];
-    if (m == 0 || m > uint32_t(kHitBuf)) continue;
-    uint32_t v[kHitBuf];
-#pragma unroll
-    for (int q = 0; q < kHitBuf; ++q) v[q] = q < int(m) ? hbuf[uint64_t(i) * kHitBuf + q] : ~0u;
-#pragma unroll
-    for (int a = 1; a < kHitBuf; ++a)
-#pragma unroll
-      for (int b = a; b > 0; --b)
-        if (v[b - 1] > v[b]) {
-          const uint32_t t = v[b];
-          v[b] = v[b - 1];
-          v[b - 1] = t;
-        }
-    const unsigned long long o = offsets[i];
-    for (uint32_t q = 0; q < m; ++q)
-      if (o + q < (unsigned long long)cap) {
-        edges[2 * (o + q)] = i;
-        edges[2 * (o + q) + 1] = v[q];
-      }
-  }
-}
-
 // Puts the edges of every cell with more than kHitBuf of them in increasing
 // order of j (insertion sort of the segment, whose length is at most the
 // cell's degree). Segments that do not lie wholly below cap are left alone
@@ -565,23 +533,167 @@ cudaError_t launch_pivot_index(const uint64_t* skeys, const DevCounters* ctr, si
 
 namespace {
 
-// Count pass, scan of the counts, edges of the cells whose hits fit the hit
-// buffer, write pass for the others, their ordering: shared by PIVOT and
-// HALVES. search(mode) launches the strategy's search pass.
+// Edge offsets of every cell and the edges of the cells whose hits fit the hit
+// buffer, in one pass: chunks of kHEChunk cells handed out in order by a
+// ticket (status[0]), a block scan of the chunk's counts, and a decoupled
+// look-back (Merrill & Garland 2016) over the earlier chunks' published
+// totals (status[1 + c]) for the chunk's first edge. The look-back wait is
+// bounded: after `polls` looks it sets the timeout bit and gives up.
+constexpr int kHEThreads = 512;
+constexpr int kHEPer = 8;
+constexpr uint32_t kHEChunk = kHEThreads * kHEPer;  // 4096 cells
+constexpr unsigned long long kHEAgg = 1ull << 62;
+constexpr unsigned long long kHEPre = 2ull << 62;
+constexpr unsigned long long kHEVal = (1ull << 62) - 1;
+constexpr unsigned kHESpinLimit = 1u << 22;
+
+__global__ void __launch_bounds__(kHEThreads)
+    hits_emit(DevCounters* ctr, uint32_t max_n, const uint32_t* __restrict__ counts,
+              const uint32_t* __restrict__ hbuf, unsigned long long* __restrict__ offsets,
+              unsigned long long* status, uint32_t* __restrict__ edges, int64_t cap,
+              uint32_t polls) {
+  __shared__ unsigned long long wsum[kHEThreads / 32];
+  __shared__ uint32_t chunk_s;
+  __shared__ unsigned long long base_s;
+  if (ctr->overflow) return;
+  const uint32_t u = min(ctr->n_unique, max_n);
+  const uint32_t nchunks = (u + kHEChunk - 1) / kHEChunk;
+  if (u == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_edges = 0;
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) chunk_s = atomicAdd(reinterpret_cast<unsigned int*>(status), 1u);
+    __syncthreads();
+    const uint32_t c = chunk_s;
+    if (c >= nchunks) break;
+    const uint32_t i0 = c * kHEChunk + threadIdx.x * kHEPer;
+    uint32_t m[kHEPer];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kHEPer; ++q) {
+      m[q] = i0 + q < u ? counts[i0 + q] : 0u;
+      sum += m[q];
+    }
+    unsigned long long inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long v = lane < kHEThreads / 32 ? wsum[lane] : 0ull;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane < kHEThreads / 32) wsum[lane] = v;
+    }
+    __syncthreads();
+    const unsigned long long before = (warp > 0 ? wsum[warp - 1] : 0ull) + inc - sum;
+    const unsigned long long T = wsum[kHEThreads / 32 - 1];
+    if (threadIdx.x == 0) {
+      unsigned long long base = 0;
+      unsigned long long* st = status + 1;
+      if (c == 0) {
+        atomicExch(&st[0], kHEPre | T);
+      } else {
+        atomicExch(&st[c], kHEAgg | T);
+        int64_t p = int64_t(c) - 1;
+        uint32_t looked = 0;
+        while (p >= 0) {
+          if (looked++ >= polls) {  // every look counts; 0 polls gives up at once
+            atomicOr(&ctr->error, kErrTimeout);
+            break;
+          }
+          const unsigned long long sv = *reinterpret_cast<volatile unsigned long long*>(&st[p]);
+          const unsigned long long f = sv & ~kHEVal;
+          if (f == 0) {
+            __nanosleep(64);
+            continue;
+          }
+          base += sv & kHEVal;
+          if (f == kHEPre) break;
+          --p;
+        }
+        atomicExch(&st[c], kHEPre | (base + T));
+      }
+      base_s = base;
+      if (c == nchunks - 1) ctr->n_edges = base + T;
+    }
+    __syncthreads();
+    unsigned long long o = base_s + before;
+#pragma unroll
+    for (int q = 0; q < kHEPer; ++q) {
+      const uint32_t i = i0 + q;
+      if (i >= u) break;
+      offsets[i] = o;
+      const uint32_t mq = m[q];
+      if (mq > 0 && mq <= uint32_t(kHitBuf)) {
+        uint32_t v[kHitBuf];
+#pragma unroll
+        for (int r = 0; r < kHitBuf; ++r) v[r] = r < int(mq) ? hbuf[uint64_t(i) * kHitBuf + r] : ~0u;
+#pragma unroll
+        for (int a = 1; a < kHitBuf; ++a)
+#pragma unroll
+          for (int b = a; b > 0; --b)
+            if (v[b - 1] > v[b]) {
+              const uint32_t t = v[b];
+              v[b] = v[b - 1];
+              v[b - 1] = t;
+            }
+        for (uint32_t r = 0; r < mq; ++r)
+          if (o + r < (unsigned long long)cap) {
+            edges[2 * (o + r)] = i;
+            edges[2 * (o + r) + 1] = v[r];
+          }
+      }
+      o += mq;
+    }
+    __syncthreads();  // chunk_s and wsum are reused by the next chunk
+  }
+}
+
+// Zeroes the hit counters, the write cursors and the one-pass emit's ticket
+// and status words in one launch.
+__global__ void __launch_bounds__(kThreads)
+    zero_hit_state(uint32_t* __restrict__ counts, uint32_t* __restrict__ fill, uint32_t n,
+                   unsigned long long* __restrict__ status, uint32_t n_status) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    counts[i] = 0u;
+    fill[i] = 0u;
+  }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_status; i += stride)
+    status[i] = 0ull;
+}
+
+// Count pass, the one-pass offsets and edges of the cells whose hits fit the
+// hit buffer, write pass for the others, their ordering: shared by PIVOT,
+// HALVES and ALLPAIRS. search(mode) launches the strategy's search pass;
+// `scan` holds the emit's ticket and status words (one word per chunk + 1).
 template <class Search>
 cudaError_t hits_to_edges(DevCounters* ctr, size_t max_n, uint32_t* counts, uint32_t* hbuf,
                           unsigned long long* offsets, uint32_t* fill, void* scan,
                           uint32_t* edges, int64_t edges_cap, cudaStream_t s, Search search) {
-  cudaError_t e = cudaMemsetAsync(counts, 0, max_n * sizeof(uint32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, max_n * sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
+  unsigned long long* status = static_cast<unsigned long long*>(scan);
+  const uint32_t n_status = uint32_t((max_n + kHEChunk - 1) / kHEChunk + 1);
+  zero_hit_state<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(counts, fill, uint32_t(max_n),
+                                                                 status, n_status);
+  count_launch();
+  cudaError_t e;
   search(kCount);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = scan_exclusive_u32(counts, offsets, &ctr->n_unique, max_n, &ctr->n_edges, scan, s);
-  if (e != cudaSuccess) return e;
-  pivot_emit<<<grid_for(max_n, kThreads), kThreads, 0, s>>>(ctr, uint32_t(max_n), counts, hbuf,
-                                                            offsets, edges, edges_cap);
+  const int ge = int(std::max<size_t>(
+      1, std::min<size_t>(n_status - 1, size_t(sm_count()) * (2048 / kHEThreads))));
+  hits_emit<<<ge, kHEThreads, 0, s>>>(ctr, uint32_t(max_n), counts, hbuf, offsets, status, edges,
+                                     edges_cap, wait_limit(kHESpinLimit));
   count_launch();
   search(kWrite);
   count_launch();

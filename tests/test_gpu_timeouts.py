@@ -1,9 +1,9 @@
 """Bounded device-side waits run out cleanly.
 
 Every wait of the library on another block's progress (the edge kernels'
-decoupled look-back, the BFS grid barrier, the tensor-core sign kernel's wait
-for its MMA) gives up after a fixed number of polls, sets an error bit and
-returns. These tests lower the limit to 0 polls with cg_set_wait_limit, so
+decoupled look-back, also in the one-pass edge output of PIVOT and HALVES;
+the BFS grid barrier; the tensor-core sign kernel's wait for its MMA) gives
+up after a fixed number of polls, sets an error bit and returns. These tests lower the limit to 0 polls with cg_set_wait_limit, so
 that each wait gives up before it looks (a wait that nothing will end), check
 that the public call returns CG_ERR_TIMEOUT and that the GPU context stays
 usable, then restore the limit and check the same call against the oracle.
@@ -42,11 +42,14 @@ def _cells_dev(cells, dev):
     return torch.from_numpy(np.ascontiguousarray(cells).view(np.int64)).to(dev)
 
 
-@pytest.mark.parametrize("ell,strategy", [(64, "hash"), (64, "sorted")])
+@pytest.mark.parametrize("ell,strategy", [(64, "hash"), (64, "sorted"), (64, "pivot"),
+                                          (64, "halves")])
 def test_lookback_wait_runs_out(dev, ell, strategy):
     sc = inputs.planes_3d(n=300_000, ell=ell, seed=61)
     cells = oracle.dedup(oracle.pack_signs(sc.pts, sc.a, sc.b, 64), ell, 64)
-    assert len(cells) > 64 * 32  # many 32-cell chunks, so chunks look back
+    # more than one chunk (32 cells for HASH and SORTED, 4,096 for the edge
+    # pass of PIVOT and HALVES), so later chunks look back
+    assert len(cells) > 4096
     cd = _cells_dev(cells, dev)
     cellgraph.set_wait_limit(0)
     try:
