@@ -153,14 +153,25 @@ struct GridCell {
   uint64_t base;
   uint64_t list;  // crossing constraints: indices in bytes 0-6, their count in byte 7
 };
+constexpr int kGridMaxRows = 64;       // l <= 64
+constexpr int kGridMaxQuads = 2;       // float4s per constraint row (d <= 4)
+constexpr int kGridMaxCentres = 2304;  // slabs of all axes together
+// The grid's placement and what its classification reads, written once per
+// build by the placement kernel: slabs per axis, the constraint rows scaled
+// for the grid's box with each row's threshold 2 + R, and the slab centres
+// (axis k's from cen_off[k]).
 struct GridGeom {
   int32_t lo[4];
   int32_t shift[4];
   int32_t count[4];
+  int32_t cen_off[4];
+  float4 rows[kGridMaxRows * kGridMaxQuads];
+  float qlim[kGridMaxRows];
+  float cen[kGridMaxCentres];
 };
 struct PackGrid {
   GridCell* cells;  // [2^total_bits] (the grid uses at most that many)
-  GridGeom* geom;   // written by the set-up kernel
+  GridGeom* geom;   // written by the placement kernel
   int total_bits;
 };
 // log2 of the cell budget of the grid for a scene of n points (0: no grid);

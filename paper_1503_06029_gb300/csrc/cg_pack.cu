@@ -809,38 +809,32 @@ __device__ __forceinline__ uint64_t grid_list(uint64_t cross) {
   return list | (uint64_t(t) << 56);
 }
 
-// Every block places the grid from the same sample (so all agree) and builds
-// the rows; then each warp classifies whole columns on its own: lane j takes
-// constraints j and j + 32, marks its runs in the warp's difference words,
-// and the warp turns them into the column's cell words (prefix XOR) and
-// writes them.
+constexpr int kPlaceThreads = 1024;
+static_assert(kMaxSweep + kMaxOther <= kGridMaxCentres, "centre table");
+
+// Placement (one block): the box of the sample, the slabs per axis, the slab
+// centres, the rows for the grid's box and each row's threshold q = 2 + R,
+// all written to g.geom for the classification and the sign kernel.
 template <int D, int NCH>
-__global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, PackGrid g) {
+__global__ void __launch_bounds__(kPlaceThreads) grid_place_kernel(PackArgs pa, PackGrid g) {
   constexpr int kQ = Coef<D, 1>::kQuads;
   constexpr int kRows = NCH * 32;
-  constexpr int kWords = 2 * NCH;  // base words, then cross words
-  __shared__ float4 rows[kRows * kQ];
-  __shared__ float qlim[kRows];
-  __shared__ int32_t red[2][kGridWarps][D];
+  static_assert(kQ <= kGridMaxQuads && kRows <= kGridMaxRows, "grid rows");
+  __shared__ int32_t red[2][kPlaceThreads / 32][D];
   __shared__ int32_t geo_lo[D], geo_sh[D], geo_n[D], cen_off[D];
-  __shared__ float cen[kMaxSweep + kMaxOther];  // slab centres, axis 0 first
-  __shared__ uint32_t diff_all[kGridWarps][kWords][kMaxSweep + 1];
-  // The previous build may still read the grid. The sign kernel is let in
-  // only at the end: its blocks, waiting early, would hold the registers and
-  // shared memory this kernel's blocks need.
-  griddep_wait();
+  griddep_wait();  // the previous build may still read the grid
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int64_t n = pa.n;
+  GridGeom* geo = g.geom;
 
-  // 1. Box of the sample and the placement.
   int32_t mn[D], mx[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     mn[k] = INT32_MAX;
     mx[k] = INT32_MIN;
   }
-  for (int j = threadIdx.x; j < kGridSample; j += kGridThreads) {
+  for (int j = threadIdx.x; j < kGridSample; j += kPlaceThreads) {
     const int64_t i = n <= kGridSample ? int64_t(j) : int64_t(j) * (n - 1) / (kGridSample - 1);
     if (i < n) {
 #pragma unroll
@@ -872,7 +866,7 @@ __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, P
     int s[D];
     for (int k = 0; k < D; ++k) {
       int32_t a = INT32_MAX, b = INT32_MIN;
-      for (int w = 0; w < kGridWarps; ++w) {
+      for (int w = 0; w < kPlaceThreads / 32; ++w) {
         a = min(a, red[0][w][k]);
         b = max(b, red[1][w][k]);
       }
@@ -920,43 +914,69 @@ __global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, P
       geo_n[k] = int32_t(cnt[k]);
       cen_off[k] = off;
       off += int(cnt[k]);
-      if (blockIdx.x == 0) {
-        g.geom->lo[k] = int32_t(lo);
-        g.geom->shift[k] = s[k];
-        g.geom->count[k] = int32_t(cnt[k]);
-      }
+      geo->lo[k] = int32_t(lo);
+      geo->shift[k] = s[k];
+      geo->count[k] = int32_t(cnt[k]);
+      geo->cen_off[k] = cen_off[k];
     }
   }
   __syncthreads();
-
-  // 2. Slab centres, rows for the box and each row's threshold q = 2 + R.
 #pragma unroll
   for (int k = 0; k < D; ++k)
-    for (int t = threadIdx.x; t < geo_n[k]; t += kGridThreads)
-      cen[cen_off[k] + t] = slab_centre(geo_lo[k], geo_sh[k], t);
-  {
-    uint32_t M[D];
-    float hh[D];
+    for (int t = threadIdx.x; t < geo_n[k]; t += kPlaceThreads)
+      geo->cen[cen_off[k] + t] = slab_centre(geo_lo[k], geo_sh[k], t);
+  uint32_t M[D];
+  float hh[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const int64_t lo = geo_lo[k];
-      const int64_t hi = lo + (int64_t(geo_n[k]) << geo_sh[k]) - 1;
-      M[k] = max(uabs32(int32_t(lo)), uabs32(int32_t(hi)));
-      hh[k] = 0.5f * __ull2float_ru((1ull << geo_sh[k]) - 1ull);
-    }
-    for (int t = threadIdx.x; t < kRows; t += kGridThreads) {
-      float sc;
-      build_coef<D, 1>(pa, t, M, rows + t * kQ, &sc);
-      float R = 0.0f;
-      if (sc != 0.0f) {
-        const int32_t* ar = pa.a + int64_t(t) * D;
-#pragma unroll
-        for (int k = 0; k < D; ++k) R = __fmaf_ru(__uint2float_ru(uabs32(ar[k])), hh[k], R);
-        R = __fmul_ru(R, sc);
-      }
-      qlim[t] = __fadd_ru(2.0f, R);
-    }
+  for (int k = 0; k < D; ++k) {
+    const int64_t lo = geo_lo[k];
+    const int64_t hi = lo + (int64_t(geo_n[k]) << geo_sh[k]) - 1;
+    M[k] = max(uabs32(int32_t(lo)), uabs32(int32_t(hi)));
+    hh[k] = 0.5f * __ull2float_ru((1ull << geo_sh[k]) - 1ull);
   }
+  for (int t = threadIdx.x; t < kRows; t += kPlaceThreads) {
+    float sc;
+    build_coef<D, 1>(pa, t, M, geo->rows + t * kQ, &sc);
+    float R = 0.0f;
+    if (sc != 0.0f) {
+      const int32_t* ar = pa.a + int64_t(t) * D;
+#pragma unroll
+      for (int k = 0; k < D; ++k) R = __fmaf_ru(__uint2float_ru(uabs32(ar[k])), hh[k], R);
+      R = __fmul_ru(R, sc);
+    }
+    geo->qlim[t] = __fadd_ru(2.0f, R);
+  }
+}
+
+// Classification: each warp takes whole columns: lane j takes constraints j
+// and j + 32, marks its runs in the warp's difference words, and the warp
+// turns them into the column's cell words (prefix XOR) and writes them.
+template <int D, int NCH>
+__global__ void __launch_bounds__(kGridThreads) grid_setup_kernel(PackArgs pa, PackGrid g) {
+  constexpr int kQ = Coef<D, 1>::kQuads;
+  constexpr int kRows = NCH * 32;
+  constexpr int kWords = 2 * NCH;  // base words, then cross words
+  __shared__ float4 rows[kRows * kQ];
+  __shared__ float qlim[kRows];
+  __shared__ int32_t geo_lo[D], geo_sh[D], geo_n[D], cen_off[D];
+  __shared__ float cen[kMaxSweep + kMaxOther];  // slab centres, axis 0 first
+  __shared__ uint32_t diff_all[kGridWarps][kWords][kMaxSweep + 1];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const GridGeom* geo = g.geom;
+  if (threadIdx.x < D) {
+    geo_lo[threadIdx.x] = geo->lo[threadIdx.x];
+    geo_sh[threadIdx.x] = geo->shift[threadIdx.x];
+    geo_n[threadIdx.x] = geo->count[threadIdx.x];
+    cen_off[threadIdx.x] = geo->cen_off[threadIdx.x];
+  }
+  for (int t = threadIdx.x; t < kRows * kQ; t += kGridThreads) rows[t] = geo->rows[t];
+  for (int t = threadIdx.x; t < kRows; t += kGridThreads) qlim[t] = geo->qlim[t];
+  __syncthreads();
+  int n_cen = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) n_cen += geo_n[k];
+  for (int t = threadIdx.x; t < n_cen; t += kGridThreads) cen[t] = geo->cen[t];
   __syncthreads();
 
   // 3. Columns, one warp each.
@@ -1137,7 +1157,7 @@ struct GridStages {
 // grid's box;
 // the previous tile's vectors are inserted while this tile's entries load.
 template <int D, int NCH, class Sink>
-__global__ void __launch_bounds__(kFThreads, 3)
+__global__ void __launch_bounds__(kFThreads, 4)
     pack_grid_kernel(PackArgs pa, Sink sink, PackGrid g, int vec_ok) {
   constexpr int P = 4;
   constexpr int kQ = Coef<D, 1>::kQuads;
@@ -1152,24 +1172,20 @@ __global__ void __launch_bounds__(kFThreads, 3)
   int4(*ring)[32 * K] = ring_all[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t n = pa.n;
-  uint32_t glo[D], gsh[D], gcnt[D], gmul[D], M[D];
+  uint32_t glo[D], gsh[D], gcnt[D], gmul[D];
   {
     uint32_t mul = 1;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const int32_t lo = g.geom->lo[k];
-      const int32_t sh = g.geom->shift[k];
-      const int32_t cnt = g.geom->count[k];
-      glo[k] = uint32_t(lo);
-      gsh[k] = uint32_t(sh);
-      gcnt[k] = uint32_t(cnt);
+      glo[k] = uint32_t(g.geom->lo[k]);
+      gsh[k] = uint32_t(g.geom->shift[k]);
+      gcnt[k] = uint32_t(g.geom->count[k]);
       gmul[k] = mul;
-      mul *= uint32_t(cnt);
-      const int64_t hi = int64_t(lo) + (int64_t(cnt) << sh) - 1;
-      M[k] = max(uabs32(lo), uabs32(int32_t(hi)));
+      mul *= gcnt[k];
     }
   }
-  for (int t = threadIdx.x; t < kRows; t += kFThreads) build_coef<D, 1>(pa, t, M, rows + t * kQ);
+  // the rows the placement built for the grid's box
+  for (int t = threadIdx.x; t < kRows * kQ; t += kFThreads) rows[t] = g.geom->rows[t];
   __syncthreads();
 
   const int64_t n_wt = (n + kWarpPts - 1) / kWarpPts;
@@ -1291,8 +1307,9 @@ cudaError_t launch_grid_setup_dn(const PackArgs& pa, const PackGrid& g, cudaStre
   // Plain launches (the kernels' griddepcontrol calls are then no-ops): with
   // programmatic dependent launch the persistent sign kernel after it measured
   // 0.1 ms slower per build (0.39 against 0.27 ms per planes_3d step).
+  grid_place_kernel<D, NCH><<<1, kPlaceThreads, 0, s>>>(pa, g);
   grid_setup_kernel<D, NCH><<<unsigned(sg), kGridThreads, 0, s>>>(pa, g);
-  count_launch();
+  count_launch(2);
   return cudaGetLastError();
 }
 
