@@ -228,13 +228,16 @@ cg_status cg_ctx_stage_times(cg_ctx* ctx, double* ms, const char** names, int ca
 typedef struct cg_tune_params {
   int strategy;    /* CG_STRATEGY_HASH, _SORTED, _PIVOT, _TREE or _HALVES */
   int pivots;      /* h for PIVOT: 1 <= h <= min(8, 64 / bits(l)) (clamped) */
-  int sign_kernel; /* 0: the library's choice of the fp32 forms below;
+  int sign_kernel; /* 0: the library's choice of the fp32 forms below: 2
+                         for l <= 64, n >= 2^18 and points in device memory,
+                         else 3;
                       1: tensor cores (tcgen05, l <= 64 only; ignored above);
                       2: fp32 FMA filter with exact fallback behind a box grid
                          over the points (l <= 64: each point tests only the
                          constraints that cross its grid cell);
                       3: fp32 FMA filter with exact fallback on every
-                         constraint (what 0 currently chooses) */
+                         constraint (also what points read in place from host
+                         memory by cg_build_host get under 0 or 2) */
 } cg_tune_params;
 
 int cg_tune_bucket(int ell); /* bucket of l, or -1 when l is out of range */

@@ -1540,13 +1540,6 @@ cudaError_t launch_pack_insert(const PackArgs& pa, const SmallTable& t, cudaStre
   return launch_fast_any(pa, MakeInsert{t}, s);
 }
 
-int pack_grid_bits(int64_t n, bool always) {
-  if (!always) return 0;  // opt-in (tuning sign_kernel 2) until it beats the plain kernel
-  int lg = 0;
-  while ((int64_t(2) << lg) <= n) ++lg;  // floor(log2 n)
-  return std::max(6, std::min(20, lg - 4));
-}
-
 cudaError_t launch_pack_grid_setup(const PackArgs& pa, const PackGrid& g, cudaStream_t s) {
   if (pa.ell > 64) return cudaErrorInvalidValue;
   if (pa.n == 0) return cudaSuccess;

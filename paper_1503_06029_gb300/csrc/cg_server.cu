@@ -174,6 +174,9 @@ bool group_eligible(const Req* r) { return r->work && r->result && group_candida
 void plan_request(Req* r) {
   const cg_scene& sc = r->sc;
   r->plan = plan_scene(sc.n, sc.ell, r->cap, r->tp);
+  // A served request's sign step stays one launch: the server's rate is set
+  // by the CUDA calls each request start makes, and the box grid adds two.
+  if (r->tp.sign_kernel != 2) r->plan.grid_bits = 0;
   r->w = (sc.ell + 63) / 64;
   if (r->ecap == 0) r->ecap = std::max<size_t>(1024, 4 * r->plan.ucap + 64);
   r->in_bytes = r->on_host ? align256(size_t(sc.n) * sc.d * 4) + align256(size_t(sc.ell) * sc.d * 4) +

@@ -1,8 +1,9 @@
 """The sign step's box grid against the oracle, bit for bit.
 
-With the grid (tuning sign_kernel 2; 3 never uses it), most bits of a vector
-come from the cell of a grid laid over the points, and only the constraints
-that cross the cell are tested per point. The cells are classified a column
+With the grid (tuning sign_kernel 2; 0, the default, from 2^18 points in
+device memory on; 3 never uses it), most bits of a vector come from the cell
+of a grid laid over the points, and only the constraints that cross the cell
+are tested per point. The cells are classified a column
 at a time from a few tests per (column, constraint), relying on the value
 moving monotonically along the column. The cases aim at what that adds:
 planes through cell corners with points on and next to them, points outside
@@ -188,8 +189,8 @@ def test_grid_degenerate_inputs(gctx, dev):
 
 
 def test_grid_default_and_never_agree(dev):
-    """The default setting and the grid switched off give the oracle's output
-    on a scene of 300,001 points."""
+    """The default setting (the grid from 2^18 points on) and the grid
+    switched off give the oracle's output on a scene of 300,001 points."""
     sc = inputs.planes_3d(n=300_001, ell=64, seed=88)
     for sk in (0, GRID_NEVER):
         c = _ctx(sk)
