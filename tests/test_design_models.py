@@ -15,12 +15,19 @@ argument fails here before it can reach a GPU:
   when lo <= p < lo + 2^(bits + s), so one unsigned subtraction and one
   compare place any int32 point, inside the grid or not; the box covers the
   sample's range it was placed on.
+* Box grid classification: with fp32 arithmetic emulated exactly (rows
+  scaled so the FMA chain's error bound is below 1, the threshold 2 + R with
+  R >= s sum |a_k| h_k rounded upwards, the rounded cell centre), every cell
+  the column walk proves "bit 1" has a . p >= b at every integer point of its
+  box and every cell it proves "bit 0" has a . p < b there.
 * BFS frontier counters: level d reads count[d % 3], appends to
   count[(d + 1) % 3] and clears count[(d + 2) % 3] even when its own frontier
   is empty; with the host looking only after every 16th level, no stale count
   is ever read.
 """
 import collections
+import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -174,3 +181,158 @@ def test_grid_slab_test_model(seed):
                     assert (g < cnt) == (lo <= p < lo + span)
                     if g < cnt:  # and the slab's integers hold p
                         assert lo + (g << s) <= p <= lo + ((g + 1) << s) - 1
+
+
+# ---- fp32 emulated exactly on rationals (round to nearest even, round up) ----
+
+def _rn32(x):
+    x = Fraction(x)
+    if x == 0:
+        return Fraction(0)
+    sign, x = (-1 if x < 0 else 1), abs(x)
+    e = x.numerator.bit_length() - x.denominator.bit_length()
+    if Fraction(2) ** e > x:
+        e -= 1  # now 2^e <= x < 2^(e + 1)
+    ulp = Fraction(2) ** (e - 23)
+    q = x / ulp
+    n = math.floor(q)
+    r = q - n
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return sign * n * ulp
+
+
+def _ru32(x):
+    """Round towards +infinity (the inputs here are never negative)."""
+    x = Fraction(x)
+    assert x >= 0
+    if x == 0:
+        return Fraction(0)
+    e = x.numerator.bit_length() - x.denominator.bit_length()
+    if Fraction(2) ** e > x:
+        e -= 1
+    ulp = Fraction(2) ** (e - 23)
+    return math.ceil(x / ulp) * ulp
+
+
+def _fma(a, b, c):
+    return _rn32(a * b + c)
+
+
+def _row(a, b, M, d):
+    """The sign step's scaled row for a box with |p_k| <= M_k: (f, c, scale)."""
+    T = Fraction(0)
+    for k in range(d):
+        T = _ru32(_ru32(abs(a[k])) * _ru32(M[k]) + T)
+    T = _ru32(T + _ru32(abs(b)))
+    if T == 0:
+        return [Fraction(0)] * d, Fraction(4), Fraction(0)
+    E = _ru32(T * Fraction(d + 4, 2 ** 24))
+    e = E.numerator.bit_length() - E.denominator.bit_length()
+    if Fraction(2) ** e > E:
+        e -= 1
+    e += 1  # E = m 2^e, 1/2 <= m < 1
+    sc = Fraction(2) ** -e
+    return [_rn32(a[k]) * sc for k in range(d)], -_rn32(b) * sc, sc
+
+
+def _column_runs(cen0, s0, f0, c1, q):
+    """Model of the set-up kernel's walk along one column: (one_lo, one_hi,
+    cr_lo, cr_hi); every other cell is proven bit 0."""
+    G0 = len(cen0)
+
+    def test(g):
+        v = _fma(f0, cen0[g], c1)
+        return 1 if v >= q else (2 if v <= -q else 0)
+
+    if f0 == 0:
+        t = test(0)
+        return (0, G0, 0, 0) if t == 1 else ((0, 0, 0, G0) if t == 0 else (0, 0, 0, 0))
+    w0 = 2.0 ** s0  # the slab width (exact; the rounded centres may coincide)
+    g_one = (float(q - c1) / float(f0) - float(cen0[0])) / w0
+    g_zero = (float(-q - c1) / float(f0) - float(cen0[0])) / w0
+    clamp = lambda g, lo, hi: int(min(max(g, lo), hi))
+    if f0 > 0:
+        a = clamp(math.ceil(g_one), 0, G0)
+        while a < G0 and test(a) != 1:
+            a += 1
+        while 0 < a < G0 and test(a - 1) == 1:
+            a -= 1
+        z = clamp(math.floor(g_zero), -1, G0 - 1)
+        while z >= 0 and test(z) != 2:
+            z -= 1
+        while 0 <= z < G0 - 1 and test(z + 1) == 2:
+            z += 1
+        return a, G0, z + 1, max(a, z + 1)
+    a = clamp(math.floor(g_one), -1, G0 - 1)
+    while a >= 0 and test(a) != 1:
+        a -= 1
+    while 0 <= a < G0 - 1 and test(a + 1) == 1:
+        a += 1
+    z = clamp(math.ceil(g_zero), 0, G0)
+    while z < G0 and test(z) != 2:
+        z += 1
+    while 0 < z < G0 and test(z - 1) == 2:
+        z -= 1
+    return 0, a + 1, a + 1, max(z, a + 1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_grid_classification_model_is_sound(seed):
+    rng = np.random.default_rng(100 + seed)
+    d = 2 + seed % 2
+    checked = 0
+    for _case in range(4):
+        s = [int(rng.integers(0, 21)) for _ in range(d)]
+        cnt = [int(rng.integers(2, 25 if k == 0 else 5)) for k in range(d)]
+        lo = []
+        for k in range(d):
+            span = cnt[k] << s[k]
+            lo.append(int(rng.integers(-2**31, 2**31 - span + 1)))
+        M = [max(abs(lo[k]), abs(lo[k] + (cnt[k] << s[k]) - 1)) for k in range(d)]
+        hh = [Fraction(1, 2) * _ru32((1 << s[k]) - 1) for k in range(d)]
+
+        def centre(k, g):
+            return Fraction(1, 2) * _rn32(2 * (lo[k] + (g << s[k])) + (1 << s[k]) - 1)
+
+        for _plane in range(12):
+            kind = int(rng.integers(0, 3))
+            if kind == 0:
+                a = [int(x) for x in rng.integers(-3, 4, d)]
+            elif kind == 1:
+                a = [int(x) for x in rng.integers(-1024, 1025, d)]
+            else:
+                a = [int(x) for x in rng.integers(-2**31, 2**31, d, dtype=np.int64)]
+            # through (or one unit off) a cell corner, or anywhere
+            corner = [lo[k] + (int(rng.integers(0, cnt[k] + 1)) << s[k]) for k in range(d)]
+            b = sum(a[k] * corner[k] for k in range(d)) + int(rng.integers(-2, 3))
+            if int(rng.integers(0, 4)) == 0:
+                b = int(rng.integers(-2**62, 2**62))
+            f, c, sc = _row(a, b, M, d)
+            R = Fraction(0)
+            if sc != 0:
+                for k in range(d):
+                    R = _ru32(_ru32(abs(a[k])) * hh[k] + R)
+                R = _ru32(R * sc)
+            q = _ru32(2 + R)
+            cen0 = [centre(0, g) for g in range(cnt[0])]
+            for col in range(int(np.prod(cnt[1:]))):
+                gk, rest = [0] * d, col
+                for k in range(1, d):
+                    gk[k], rest = rest % cnt[k], rest // cnt[k]
+                c1 = c
+                for k in range(1, d):
+                    c1 = _fma(f[k], centre(k, gk[k]), c1)
+                one_lo, one_hi, cr_lo, cr_hi = _column_runs(cen0, s[0], f[0], c1, q)
+                for g0 in range(cnt[0]):
+                    gk[0] = g0
+                    box = [(lo[k] + (gk[k] << s[k]), lo[k] + ((gk[k] + 1) << s[k]) - 1)
+                           for k in range(d)]
+                    vmin = sum(min(a[k] * box[k][0], a[k] * box[k][1]) for k in range(d)) - b
+                    vmax = sum(max(a[k] * box[k][0], a[k] * box[k][1]) for k in range(d)) - b
+                    if one_lo <= g0 < one_hi:
+                        assert vmin >= 0, (a, b, box)
+                    elif not cr_lo <= g0 < cr_hi:
+                        assert vmax < 0, (a, b, box)
+                    checked += 1
+    assert checked > 500
