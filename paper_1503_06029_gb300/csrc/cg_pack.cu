@@ -683,16 +683,18 @@ cudaError_t launch_fast(const PackArgs& pa, const Sink& sink, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Box grid (l <= 64). A set-up kernel lays a grid of integer boxes over the
-// points and classifies, per cell, each constraint as holding on the whole
-// cell (`base`), failing on the whole cell, or crossing it (`cross`); the
-// sign kernel then tests each point against its cell's crossing constraints
-// only and takes the other bits from the cell.
+// Box grid (l <= 64). A placement kernel lays a grid of integer boxes over
+// the points, a classification kernel marks, per cell, each constraint as
+// holding on the whole cell (`base`), failing on the whole cell, or crossing
+// it (listed in `list`, up to kGridList of them); the sign kernel then tests
+// each point against its cell's listed constraints only and takes the other
+// bits from the cell.
 //
 // Placement: per axis, G slabs of 2^s integers covering the range of 1,024
 // evenly spaced sample points and 1/256 of it on each side; s is raised on
-// the axis with the most slabs until the cells fit the workspace and axis 0
-// has at most kMaxSweep slabs. The grid's box stays inside the int32 range,
+// the axis with the most slabs (the last of equal ones) while axis 0 has more
+// than kMaxSweep slabs, the others more than kMaxOther together, or all more
+// cells than the workspace holds. The grid's box stays inside the int32 range,
 // so a point's slab (p - lo) >> s computed modulo 2^32 is below G exactly
 // when the point lies in the box; a point outside it tests every constraint
 // in exact integer arithmetic.
@@ -822,7 +824,10 @@ __global__ void __launch_bounds__(kPlaceThreads) grid_place_kernel(PackArgs pa, 
   static_assert(kQ <= kGridMaxQuads && kRows <= kGridMaxRows, "grid rows");
   __shared__ int32_t red[2][kPlaceThreads / 32][D];
   __shared__ int32_t geo_lo[D], geo_sh[D], geo_n[D], cen_off[D];
-  griddep_wait();  // the previous build may still read the grid
+  // Launched plainly after the stream's earlier kernels (the previous build's
+  // reads of the grid are over); with a programmatic launch this wait would
+  // order it.
+  griddep_wait();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int64_t n = pa.n;
