@@ -518,6 +518,9 @@ class Context:
 
     def tune_set(self, bucket: int, strategy: str = "hash", pivots: int = 4,
                  sign_kernel: int = 0):
+        """Setting of one bucket of l (cg_ctx_tune_set). sign_kernel: 0 the
+        library's choice, 1 tensor cores, 2 fp32 filter behind the box grid,
+        3 fp32 filter on every constraint (see cg_tune_params)."""
         p = CgTuneParams(STRATEGY[strategy], pivots, sign_kernel)
         _check(self._lib.cg_ctx_tune_set(self._h, bucket, ctypes.byref(p)))
 
